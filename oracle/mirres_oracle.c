@@ -1,0 +1,1378 @@
+/*
+ * MIRReS stage-2 oracle -- TEST INFRASTRUCTURE ONLY (see mirres_oracle.h).
+ *
+ * A plain, slow FP64 restatement of the method, written for a reader checking it against the
+ * paper by eye: one path sample at a time, no wavefronts, no blocking, no fused kernels.
+ * Its own BVH is a top-down median split (not the LBVH the product builds), so the two share
+ * no acceleration-structure code; the LBVH restatement at the end exists only so that the
+ * product's build can be compared bit for bit.
+ *
+ * Compiled with -ffp-contract=off so that the FP32 Morton-code arithmetic has a fixed
+ * operation order on every host.
+ */
+#define _GNU_SOURCE
+#include "mirres_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI 3.14159265358979323846
+
+/* decision-margin scales: a decision whose normalised distance to its threshold is below 1
+ * is one an FP32 evaluation of the same formulas may take the other way */
+#define TAU_BARY 4e-6   /* barycentric distance to an edge, scaled by cos(angle) * size / (distance + size) */
+#define TAU_TMIN 1e-3   /* relative distance of t to the self-intersection threshold */
+#define TAU_TDEPTH 2e-6 /* relative depth difference between two hit triangles */
+#define TAU_ACC 2e-5    /* WRS accept: |u w_sum - gamma| / w_sum */
+#define TAU_CDF 1e-12   /* distance of a uniform to a CDF boundary */
+#define TAU_LOBE 2e-6   /* distance of the lobe uniform to a material-dependent threshold */
+#define TAU_FLIP 2e-5   /* |n . d| when the face normal is flipped towards the viewer */
+#define TAU_ENV 3e-6    /* distance to a texel boundary of the env lookup, in u (or v) units */
+#define TAU_FRAME 1e-5  /* |n.z| in the orthonormal-basis sign choice */
+
+enum { MK_NONE = 0, MK_BARY, MK_TMIN, MK_TDEPTH, MK_ACC, MK_CDF, MK_LOBE, MK_FLIP, MK_ENV, MK_FRAME };
+
+/* ---------------------------------------------------------------------------------------
+ * small vector algebra (FP64)
+ * ------------------------------------------------------------------------------------- */
+typedef struct { double x, y, z; } v3;
+static v3 V3(double x, double y, double z) { v3 r = {x, y, z}; return r; }
+static v3 vadd(v3 a, v3 b) { return V3(a.x + b.x, a.y + b.y, a.z + b.z); }
+static v3 vsub(v3 a, v3 b) { return V3(a.x - b.x, a.y - b.y, a.z - b.z); }
+static v3 vscale(v3 a, double s) { return V3(a.x * s, a.y * s, a.z * s); }
+static double vdot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static v3 vcross(v3 a, v3 b) { return V3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+static double vlen(v3 a) { return sqrt(vdot(a, a)); }
+static v3 vnorm(v3 a) { return vscale(a, 1.0 / vlen(a)); }
+static v3 vload(const double* p) { return V3(p[0], p[1], p[2]); }
+static void vstore(double* p, v3 a) { p[0] = a.x; p[1] = a.y; p[2] = a.z; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+static double lum(const double c[3]) { return (c[0] + c[1] + c[2]) / 3.0; } /* Y = (r+g+b)/3 */
+
+/* ---------------------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3",
+ * SC'11): ten rounds of two 32x32->64 multiplies, key bumped by the Weyl constants.
+ * ------------------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* top 24 bits -> exact uniform in [0, 1) */
+double orc_uniform(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+/* 16-bit sub-texel offsets, cell midpoints in (0, 1) */
+static double sub_hi(uint32_t x) { return ((double)(x >> 16) + 0.5) / 65536.0; }
+static double sub_lo(uint32_t x) { return ((double)(x & 0xFFFFu) + 0.5) / 65536.0; }
+
+enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2 };
+
+/* ---------------------------------------------------------------------------------------
+ * scene, env tables, median-split BVH
+ * ------------------------------------------------------------------------------------- */
+typedef struct { double lo[3], hi[3]; int32_t left, right, first, count; } Node;
+
+struct orc_scene {
+    int nv, nf;
+    double* V; int32_t* F; double* UV;
+    int tw, th; double* alb; double* rgh; double* met;
+    int ew, eh; double* env;
+    double* cond; double* marg; double* prob; double total; int env_ok;
+    double tmin, diag;
+    int nnodes; Node* nodes; int32_t* order;
+};
+
+static __thread const double* g_cent;
+static __thread int g_axis;
+static int cmp_cent(const void* a, const void* b)
+{
+    int32_t ia = *(const int32_t*)a, ib = *(const int32_t*)b;
+    double ca = g_cent[3 * ia + g_axis], cb = g_cent[3 * ib + g_axis];
+    if (ca < cb) return -1;
+    if (ca > cb) return 1;
+    return (ia > ib) - (ia < ib);
+}
+
+static void tri_verts(const orc_scene* s, int tri, v3* a, v3* b, v3* c)
+{
+    *a = vload(s->V + 3 * s->F[3 * tri + 0]);
+    *b = vload(s->V + 3 * s->F[3 * tri + 1]);
+    *c = vload(s->V + 3 * s->F[3 * tri + 2]);
+}
+
+static int bvh_build(orc_scene* s, const double* cent, int first, int count)
+{
+    int ni = s->nnodes++;
+    Node nd;
+    for (int k = 0; k < 3; ++k) { nd.lo[k] = INFINITY; nd.hi[k] = -INFINITY; }
+    for (int i = first; i < first + count; ++i) {
+        v3 p[3];
+        tri_verts(s, s->order[i], &p[0], &p[1], &p[2]);
+        for (int j = 0; j < 3; ++j) {
+            const double q[3] = {p[j].x, p[j].y, p[j].z};
+            for (int k = 0; k < 3; ++k) { nd.lo[k] = dmin(nd.lo[k], q[k]); nd.hi[k] = dmax(nd.hi[k], q[k]); }
+        }
+    }
+    /* conservative inflation far above FP64 rounding */
+    double pad = 1e-9 * (s->diag + 1e-30);
+    for (int k = 0; k < 3; ++k) { nd.lo[k] -= pad; nd.hi[k] += pad; }
+    nd.left = nd.right = -1; nd.first = first; nd.count = count;
+    if (count <= 4) { s->nodes[ni] = nd; return ni; }
+    double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = first; i < first + count; ++i)
+        for (int k = 0; k < 3; ++k) {
+            clo[k] = dmin(clo[k], cent[3 * s->order[i] + k]);
+            chi[k] = dmax(chi[k], cent[3 * s->order[i] + k]);
+        }
+    int axis = 0;
+    for (int k = 1; k < 3; ++k) if (chi[k] - clo[k] > chi[axis] - clo[axis]) axis = k;
+    g_cent = cent; g_axis = axis;
+    qsort(s->order + first, (size_t)count, sizeof(int32_t), cmp_cent);
+    int half = count / 2;
+    nd.count = 0;
+    int l = bvh_build(s, cent, first, half);
+    int r = bvh_build(s, cent, first + half, count - half);
+    nd.left = l; nd.right = r;
+    s->nodes[ni] = nd;
+    return ni;
+}
+
+/* Environment sampling distribution, the proposal q_dir "proportional to L_env" of Sec. 4.1:
+ * texel weight Y(L) * sin(theta_row), a marginal CDF over rows and a conditional CDF per row,
+ * built in FP64 by sequential prefix sums. */
+static void env_build(orc_scene* s)
+{
+    int W = s->ew, H = s->eh;
+    double* w = (double*)malloc(sizeof(double) * (size_t)W * H);
+    double* rowsum = (double*)malloc(sizeof(double) * (size_t)H);
+    s->total = 0.0;
+    for (int r = 0; r < H; ++r) {
+        double st = sin(PI * (r + 0.5) / H);
+        double acc = 0.0;
+        for (int c = 0; c < W; ++c) {
+            double y = lum(s->env + 3 * ((size_t)r * W + c)) * st;
+            w[(size_t)r * W + c] = y;
+            acc += y;
+        }
+        rowsum[r] = acc;
+    }
+    for (int r = 0; r < H; ++r) s->total += rowsum[r];
+    s->env_ok = s->total > 0.0;
+    for (int r = 0; r < H; ++r) {
+        double* cr = s->cond + (size_t)r * (W + 1);
+        double acc = 0.0;
+        for (int c = 0; c <= W; ++c) {
+            if (rowsum[r] > 0.0) cr[c] = (c == W) ? 1.0 : acc / rowsum[r];
+            else cr[c] = (double)c / W;
+            if (c < W) acc += w[(size_t)r * W + c];
+        }
+    }
+    double acc = 0.0;
+    for (int r = 0; r <= H; ++r) {
+        if (s->env_ok) s->marg[r] = (r == H) ? 1.0 : acc / s->total;
+        else s->marg[r] = (double)r / H;
+        if (r < H) acc += rowsum[r];
+    }
+    for (size_t i = 0; i < (size_t)W * H; ++i) s->prob[i] = s->env_ok ? w[i] / s->total : 0.0;
+    free(w);
+    free(rowsum);
+}
+
+static double* to_double(const float* p, size_t n)
+{
+    double* d = (double*)malloc(sizeof(double) * (n ? n : 1));
+    for (size_t i = 0; i < n; ++i) d[i] = (double)p[i];
+    return d;
+}
+
+orc_scene* orc_scene_new(const orc_scene_desc* d)
+{
+    if (!d || d->n_tris < 0 || d->n_verts < 0 || d->tex_w < 1 || d->tex_h < 1 || d->env_w < 1 || d->env_h < 1)
+        return NULL;
+    orc_scene* s = (orc_scene*)calloc(1, sizeof(orc_scene));
+    s->nv = d->n_verts; s->nf = d->n_tris;
+    s->V = to_double(d->verts, (size_t)3 * s->nv);
+    s->F = (int32_t*)malloc(sizeof(int32_t) * (size_t)3 * (s->nf ? s->nf : 1));
+    if (s->nf) memcpy(s->F, d->tris, sizeof(int32_t) * (size_t)3 * s->nf);
+    s->UV = to_double(d->tri_uv, (size_t)6 * s->nf);
+    s->tw = d->tex_w; s->th = d->tex_h;
+    size_t tn = (size_t)s->tw * s->th;
+    s->alb = to_double(d->albedo, 3 * tn);
+    s->rgh = to_double(d->roughness, tn);
+    s->met = to_double(d->metallic, tn);
+    s->ew = d->env_w; s->eh = d->env_h;
+    s->env = to_double(d->env, (size_t)3 * s->ew * s->eh);
+    s->cond = (double*)malloc(sizeof(double) * (size_t)s->eh * (s->ew + 1));
+    s->marg = (double*)malloc(sizeof(double) * (size_t)(s->eh + 1));
+    s->prob = (double*)malloc(sizeof(double) * (size_t)s->eh * s->ew);
+    env_build(s);
+    /* scene extent: AABB of all vertices referenced by triangles */
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < 3 * s->nf; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = dmin(lo[k], s->V[3 * s->F[i] + k]);
+            hi[k] = dmax(hi[k], s->V[3 * s->F[i] + k]);
+        }
+    s->diag = s->nf ? sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                           (hi[2] - lo[2]) * (hi[2] - lo[2])) : 0.0;
+    s->tmin = 1e-5 * s->diag; /* self-intersection threshold: 1e-5 of the scene diagonal */
+    /* median-split BVH */
+    s->order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->nf ? s->nf : 1));
+    s->nodes = (Node*)malloc(sizeof(Node) * (size_t)(2 * s->nf + 1));
+    s->nnodes = 0;
+    if (s->nf) {
+        double* cent = (double*)malloc(sizeof(double) * (size_t)3 * s->nf);
+        for (int t = 0; t < s->nf; ++t) {
+            v3 a, b, c;
+            tri_verts(s, t, &a, &b, &c);
+            v3 m = vscale(vadd(vadd(a, b), c), 1.0 / 3.0);
+            vstore(cent + 3 * t, m);
+            s->order[t] = t;
+        }
+        bvh_build(s, cent, 0, s->nf);
+        free(cent);
+    }
+    return s;
+}
+
+void orc_scene_free(orc_scene* s)
+{
+    if (!s) return;
+    free(s->V); free(s->F); free(s->UV); free(s->alb); free(s->rgh); free(s->met); free(s->env);
+    free(s->cond); free(s->marg); free(s->prob); free(s->nodes); free(s->order);
+    free(s);
+}
+
+double orc_scene_tmin(const orc_scene* s) { return s->tmin; }
+
+double orc_env_tables(const orc_scene* s, double* cond, double* marg, double* prob)
+{
+    if (cond) memcpy(cond, s->cond, sizeof(double) * (size_t)s->eh * (s->ew + 1));
+    if (marg) memcpy(marg, s->marg, sizeof(double) * (size_t)(s->eh + 1));
+    if (prob) memcpy(prob, s->prob, sizeof(double) * (size_t)s->eh * s->ew);
+    return s->total;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * decision margins
+ * ------------------------------------------------------------------------------------- */
+typedef struct { double m; int kind; } Margin;
+static void note(Margin* mg, double ratio, int kind)
+{
+    if (mg && ratio < mg->m) { mg->m = ratio; mg->kind = kind; }
+}
+
+/* ---------------------------------------------------------------------------------------
+ * ray-mesh intersection (Appendix A "Visibility estimation"): Moller-Trumbore in FP64
+ * ------------------------------------------------------------------------------------- */
+typedef struct { int tri; double t, u, v; } Hit;
+
+/* plane intersection of the ray with triangle `tri`; returns 0 if the ray is parallel */
+static int tri_solve(const orc_scene* s, int tri, v3 o, v3 d, double* t, double* u, double* v, double* mscale)
+{
+    v3 a, b, c;
+    tri_verts(s, tri, &a, &b, &c);
+    v3 e1 = vsub(b, a), e2 = vsub(c, a);
+    v3 p = vcross(d, e2);
+    double det = vdot(e1, p);
+    if (det == 0.0) return 0;
+    double inv = 1.0 / det;
+    v3 sv = vsub(o, a);
+    *u = vdot(sv, p) * inv;
+    v3 q = vcross(sv, e1);
+    *v = vdot(d, q) * inv;
+    *t = vdot(e2, q) * inv;
+    if (mscale) {
+        double area2 = vlen(vcross(e1, e2));
+        double ell = sqrt(area2);
+        double cosang = fabs(det) / (vlen(d) * area2);
+        *mscale = cosang * ell / (vlen(sv) + ell);
+    }
+    return 1;
+}
+
+static int inside(double u, double v) { return u >= 0.0 && v >= 0.0 && u + v <= 1.0; }
+
+static int slab(const Node* n, v3 o, v3 d, double tmin, double tmax)
+{
+    const double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+    double t0 = tmin, t1 = tmax;
+    for (int k = 0; k < 3; ++k) {
+        if (dd[k] == 0.0) {
+            if (oo[k] < n->lo[k] || oo[k] > n->hi[k]) return 0;
+            continue;
+        }
+        double a = (n->lo[k] - oo[k]) / dd[k], b = (n->hi[k] - oo[k]) / dd[k];
+        if (a > b) { double tt = a; a = b; b = tt; }
+        t0 = dmax(t0, a);
+        t1 = dmin(t1, b);
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+/* closest hit: smallest t in (tmin, inf); equal t -> smaller triangle id */
+static void bvh_closest(const orc_scene* s, v3 o, v3 d, int skip, Hit* best, int64_t* cnt)
+{
+    best->tri = -1; best->t = INFINITY; best->u = best->v = 0.0;
+    if (!s->nf) return;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const Node* n = &s->nodes[stack[--sp]];
+        if (cnt) cnt[3]++;
+        if (!slab(n, o, d, 0.5 * s->tmin, best->t * (1.0 + 1e-9) + 1e-300)) continue;
+        if (n->count) {
+            for (int i = n->first; i < n->first + n->count; ++i) {
+                int tri = s->order[i];
+                if (tri == skip) continue;
+                if (cnt) cnt[4]++;
+                double t, u, v;
+                if (!tri_solve(s, tri, o, d, &t, &u, &v, NULL)) continue;
+                if (!inside(u, v) || !(t > s->tmin)) continue;
+                if (t < best->t || (t == best->t && tri < best->tri)) {
+                    best->tri = tri; best->t = t; best->u = u; best->v = v;
+                }
+            }
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+}
+
+/* margins of a closest-hit decision: every triangle that could be the first hit */
+static void closest_margins(const orc_scene* s, v3 o, v3 d, int skip, const Hit* best, Margin* mg)
+{
+    if (!mg || !s->nf) return;
+    double tcut = (best->tri >= 0) ? best->t * (1.0 + 1e-6) : INFINITY;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const Node* n = &s->nodes[stack[--sp]];
+        if (!slab(n, o, d, 0.25 * s->tmin, tcut * (1.0 + 1e-9) + 1e-300)) continue;
+        if (n->count) {
+            for (int i = n->first; i < n->first + n->count; ++i) {
+                int tri = s->order[i];
+                if (tri == skip) continue;
+                double t, u, v, ms;
+                if (!tri_solve(s, tri, o, d, &t, &u, &v, &ms)) continue;
+                double e = dmin(dmin(u, v), 1.0 - u - v);
+                if (t > 0.5 * s->tmin && t < tcut) note(mg, fabs(e) * ms / TAU_BARY, MK_BARY);
+                if (e >= 0.0 && t > 0.25 * s->tmin && t < 4.0 * s->tmin)
+                    note(mg, fabs(t - s->tmin) / (s->tmin * TAU_TMIN), MK_TMIN);
+                if (best->tri >= 0 && tri != best->tri && e >= 0.0 && t > s->tmin && t < tcut)
+                    note(mg, fabs(t - best->t) / (dmax(t, best->t) * TAU_TDEPTH), MK_TDEPTH);
+            }
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+}
+
+/* any hit in (tmin, inf): visibility V of Eq. (incident) */
+static int bvh_any(const orc_scene* s, v3 o, v3 d, int skip, int64_t* cnt, Margin* mg)
+{
+    if (!s->nf) return 0;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    int hit = 0;
+    double best_in = -1.0, best_out = INFINITY; /* robustness of a hit / closeness of a miss */
+    while (sp) {
+        const Node* n = &s->nodes[stack[--sp]];
+        if (cnt) cnt[3]++;
+        if (!slab(n, o, d, 0.5 * s->tmin, INFINITY)) continue;
+        if (n->count) {
+            for (int i = n->first; i < n->first + n->count; ++i) {
+                int tri = s->order[i];
+                if (tri == skip) continue;
+                if (cnt) cnt[4]++;
+                double t, u, v, ms;
+                if (!tri_solve(s, tri, o, d, &t, &u, &v, &ms)) continue;
+                int h = inside(u, v) && t > s->tmin;
+                if (mg && t > 0.5 * s->tmin) {
+                    double e = dmin(dmin(u, v), 1.0 - u - v);
+                    double r = fabs(e) * ms / TAU_BARY;
+                    if (e >= 0.0 && t > 0.25 * s->tmin && t < 4.0 * s->tmin)
+                        r = dmin(r, fabs(t - s->tmin) / (s->tmin * TAU_TMIN));
+                    if (h) best_in = dmax(best_in, r); else best_out = dmin(best_out, r);
+                }
+                if (h) {
+                    hit = 1;
+                    if (!mg) return 1;
+                }
+            }
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+    if (mg) {
+        if (hit) note(mg, best_in, MK_BARY);
+        else note(mg, best_out, MK_BARY);
+    }
+    return hit;
+}
+
+static void brute_closest(const orc_scene* s, v3 o, v3 d, int skip, Hit* best)
+{
+    best->tri = -1; best->t = INFINITY; best->u = best->v = 0.0;
+    for (int tri = 0; tri < s->nf; ++tri) {
+        if (tri == skip) continue;
+        double t, u, v;
+        if (!tri_solve(s, tri, o, d, &t, &u, &v, NULL)) continue;
+        if (!inside(u, v) || !(t > s->tmin)) continue;
+        if (t < best->t || (t == best->t && tri < best->tri)) { best->tri = tri; best->t = t; best->u = u; best->v = v; }
+    }
+}
+
+int orc_trace(const orc_scene* s, const double* rays, const int32_t* skip_tri, int32_t n, int32_t mode,
+              int32_t* out_tri, double* out_tuv, double* out_margin)
+{
+    for (int i = 0; i < n; ++i) {
+        v3 o = vload(rays + 6 * i), d = vload(rays + 6 * i + 3);
+        int skip = skip_tri ? skip_tri[i] : -1;
+        Margin mg = {INFINITY, 0};
+        Hit h;
+        if (mode == 0 || mode == 2) {
+            if (mode == 0) bvh_closest(s, o, d, skip, &h, NULL);
+            else brute_closest(s, o, d, skip, &h);
+            if (out_margin) closest_margins(s, o, d, skip, &h, &mg);
+            out_tri[i] = h.tri;
+            if (out_tuv) { out_tuv[3 * i] = h.t; out_tuv[3 * i + 1] = h.u; out_tuv[3 * i + 2] = h.v; }
+        } else {
+            int hit = 0;
+            if (mode == 1) hit = bvh_any(s, o, d, skip, NULL, out_margin ? &mg : NULL);
+            else {
+                for (int tri = 0; tri < s->nf && !hit; ++tri) {
+                    double t, u, v;
+                    if (tri == skip || !tri_solve(s, tri, o, d, &t, &u, &v, NULL)) continue;
+                    hit = inside(u, v) && t > s->tmin;
+                }
+            }
+            out_tri[i] = hit ? 1 : -1;
+        }
+        if (out_margin) out_margin[i] = mg.m;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * environment map: lat-long lookup and importance sampling (Sec. 3.2 env map; Sec. 4.1 q_dir)
+ * direction (theta, phi): d = (sin t sin p, cos t, -sin t cos p); u = phi/2pi + 1/2, v = theta/pi
+ * ------------------------------------------------------------------------------------- */
+static int env_texel_m(const orc_scene* s, v3 d, Margin* mg)
+{
+    double u = atan2(d.x, -d.z) / (2.0 * PI) + 0.5;
+    double v = acos(dmax(-1.0, dmin(1.0, d.y))) / PI;
+    double fx = u * s->ew, fy = v * s->eh;
+    int c = (int)floor(fx), r = (int)floor(fy);
+    if (c > s->ew - 1) c = s->ew - 1;
+    if (c < 0) c = 0;
+    if (r > s->eh - 1) r = s->eh - 1;
+    if (r < 0) r = 0;
+    if (mg) {
+        double dx = fabs(fx - floor(fx + 0.5));
+        double dy = (fy > 0.5 && fy < s->eh - 0.5) ? fabs(fy - floor(fy + 0.5)) : INFINITY;
+        if (s->ew > 1) note(mg, dx / (TAU_ENV * s->ew), MK_ENV);
+        if (s->eh > 1) note(mg, dy / (TAU_ENV * s->eh), MK_ENV);
+    }
+    return r * s->ew + c;
+}
+
+int32_t orc_env_texel(const orc_scene* s, const double dir[3]) { return env_texel_m(s, vload(dir), NULL); }
+
+/* solid-angle density of the env proposal at direction d */
+static double env_pdf_m(const orc_scene* s, v3 d, Margin* mg)
+{
+    if (!s->env_ok) return 0.0;
+    int tex = env_texel_m(s, d, mg);
+    double st = sqrt(dmax(0.0, 1.0 - d.y * d.y));
+    if (st <= 0.0) return 0.0;
+    return s->prob[tex] * s->ew * s->eh / (2.0 * PI * PI * st);
+}
+
+double orc_env_pdf(const orc_scene* s, const double dir[3]) { return env_pdf_m(s, vload(dir), NULL); }
+
+/* largest index i in [0, n-1] with cdf[i] <= u */
+static int cdf_search(const double* cdf, int n, double u)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (cdf[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* inverse-CDF sample: row from the marginal, column from the row's conditional, a uniform
+ * position inside the texel from a 16+16-bit word; returns the solid-angle pdf */
+static double env_sample_m(const orc_scene* s, double urow, double ucol, uint32_t sub, v3* dir, int* texel, Margin* mg)
+{
+    int W = s->ew, H = s->eh;
+    int r = cdf_search(s->marg, H, urow);
+    const double* cr = s->cond + (size_t)r * (W + 1);
+    int c = cdf_search(cr, W, ucol);
+    if (mg) {
+        note(mg, dmin(urow - s->marg[r], s->marg[r + 1] - urow) / TAU_CDF, MK_CDF);
+        note(mg, dmin(ucol - cr[c], cr[c + 1] - ucol) / TAU_CDF, MK_CDF);
+    }
+    double uu = (c + sub_hi(sub)) / W, vv = (r + sub_lo(sub)) / H;
+    double phi = 2.0 * PI * (uu - 0.5), theta = PI * vv;
+    double st = sin(theta);
+    *dir = V3(st * sin(phi), cos(theta), -st * cos(phi));
+    *texel = r * W + c;
+    return s->prob[r * W + c] * W * H / (2.0 * PI * PI * st);
+}
+
+double orc_env_sample(const orc_scene* s, const uint32_t x[4], double out_dir[3], int32_t* out_texel)
+{
+    v3 d;
+    int t;
+    double p = env_sample_m(s, orc_uniform(x[0]), orc_uniform(x[1]), x[3], &d, &t, NULL);
+    vstore(out_dir, d);
+    *out_texel = t;
+    return p;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * BRDF (Sec. 3.2 "Intrinsic decomposition": Disney-style albedo + roughness, metallic added
+ * for OWL, Sec. 5.3): Lambert (1-m) a / pi + GGX D * Smith height-correlated G2 * Schlick F
+ * / (4 cos_i cos_o), F0 = 0.04 (1-m) + m a, alpha = max(r^2, 1e-3)
+ * ------------------------------------------------------------------------------------- */
+static double alpha_of(double r) { return dmax(r * r, 1e-3); }
+
+double orc_ggx_d(double a, double cnh)
+{
+    double a2 = a * a;
+    double k = cnh * cnh * (a2 - 1.0) + 1.0;
+    return a2 / (PI * k * k);
+}
+
+/* A(c) = sqrt(a^2 + (1 - a^2) c^2) = c * sqrt(1 + a^2 tan^2) */
+static double smith_a(double a, double c) { return sqrt(a * a + (1.0 - a * a) * c * c); }
+
+double orc_smith_g1(double a, double c) { return 2.0 * c / (c + smith_a(a, c)); }
+
+/* f_r * max(0, n.wi): returns 0 outside the upper hemispheres */
+static void brdf_cos(v3 n, v3 wo, v3 wi, const double alb[3], double r, double m, int kind, double out[3])
+{
+    double co = vdot(n, wo), ci = vdot(n, wi);
+    out[0] = out[1] = out[2] = 0.0;
+    if (co <= 0.0 || ci <= 0.0) return;
+    if (kind == 1) {
+        for (int k = 0; k < 3; ++k) out[k] = alb[k] / PI * ci;
+        return;
+    }
+    double a = alpha_of(r);
+    v3 h = vnorm(vadd(wo, wi));
+    double cnh = vdot(n, h), coh = vdot(wo, h);
+    double D = orc_ggx_d(a, cnh);
+    double vis = 0.5 / (ci * smith_a(a, co) + co * smith_a(a, ci)); /* G2 / (4 ci co) */
+    double w5 = pow(1.0 - coh, 5.0);
+    for (int k = 0; k < 3; ++k) {
+        double kd = (1.0 - m) * alb[k];
+        double f0 = 0.04 * (1.0 - m) + m * alb[k];
+        double F = f0 + (1.0 - f0) * w5;
+        out[k] = (kd / PI + D * vis * F) * ci;
+    }
+}
+
+void orc_brdf_cos(const double n[3], const double wo[3], const double wi[3], const double albedo[3],
+                  double rough, double metal, int32_t kind, double out[3])
+{
+    brdf_cos(vload(n), vload(wo), vload(wi), albedo, rough, metal, kind, out);
+}
+
+/* Analytic gradient of sum_k g_k * (f_r cos)_k with respect to (albedo[3], r, m, n[3]),
+ * n treated as a free 3-vector (h depends only on wo, wi). Written out term by term. */
+static void brdf_cos_grad(v3 n, v3 wo, v3 wi, const double alb[3], double r, double m, int kind,
+                          const double g[3], double out[8])
+{
+    for (int k = 0; k < 8; ++k) out[k] = 0.0;
+    double co = vdot(n, wo), ci = vdot(n, wi);
+    if (co <= 0.0 || ci <= 0.0) return;
+    if (kind == 1) {
+        double dci = 0.0;
+        for (int k = 0; k < 3; ++k) { out[k] = g[k] * ci / PI; dci += g[k] * alb[k] / PI; }
+        out[5] = dci * wi.x; out[6] = dci * wi.y; out[7] = dci * wi.z;
+        return;
+    }
+    double a = alpha_of(r);
+    double dadr = (r * r > 1e-3) ? 2.0 * r : 0.0;
+    v3 h = vnorm(vadd(wo, wi));
+    double cnh = vdot(n, h), coh = vdot(wo, h);
+    double a2 = a * a;
+    double kk = cnh * cnh * (a2 - 1.0) + 1.0;
+    double D = a2 / (PI * kk * kk);
+    double dD_da = 2.0 * a / (PI * kk * kk) - 4.0 * a * a2 * cnh * cnh / (PI * kk * kk * kk);
+    double dD_dcnh = -4.0 * a2 * cnh * (a2 - 1.0) / (PI * kk * kk * kk);
+    double Ao = smith_a(a, co), Ai = smith_a(a, ci);
+    double den = ci * Ao + co * Ai;
+    double vis = 0.5 / den;
+    double dvis_dden = -0.5 / (den * den);
+    double dden_dci = Ao + co * (1.0 - a2) * ci / Ai;
+    double dden_dco = Ai + ci * (1.0 - a2) * co / Ao;
+    double dden_da = ci * a * (1.0 - co * co) / Ao + co * a * (1.0 - ci * ci) / Ai;
+    double w5 = pow(1.0 - coh, 5.0);
+    /* value Q_k = (kd_k/pi + D vis F_k) ci */
+    double sum_gF = 0.0, sum_gdiff = 0.0;
+    double dm = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double kd = (1.0 - m) * alb[k];
+        double f0 = 0.04 * (1.0 - m) + m * alb[k];
+        double F = f0 + (1.0 - f0) * w5;
+        /* dQ/dalb_k = ((1-m)/pi + D vis m (1 - w5)) ci */
+        out[k] = g[k] * ((1.0 - m) / PI + D * vis * m * (1.0 - w5)) * ci;
+        /* dQ/dm = (-alb/pi + D vis (alb - 0.04)(1 - w5)) ci */
+        dm += g[k] * (-alb[k] / PI + D * vis * (alb[k] - 0.04) * (1.0 - w5)) * ci;
+        sum_gF += g[k] * F;
+        sum_gdiff += g[k] * kd / PI;
+    }
+    out[4] = dm;
+    /* specular part S = D vis * sum_gF * ci ; diffuse part = sum_gdiff * ci */
+    double dS_da = (dD_da * vis + D * dvis_dden * dden_da) * sum_gF * ci;
+    out[3] = dS_da * dadr;
+    /* n enters through ci (also the trailing cos), co, cnh */
+    double dS_dci = D * dvis_dden * dden_dci * sum_gF * ci + D * vis * sum_gF;
+    double dS_dco = D * dvis_dden * dden_dco * sum_gF * ci;
+    double dS_dcnh = dD_dcnh * vis * sum_gF * ci;
+    double d_ci = dS_dci + sum_gdiff;
+    out[5] = d_ci * wi.x + dS_dco * wo.x + dS_dcnh * h.x;
+    out[6] = d_ci * wi.y + dS_dco * wo.y + dS_dcnh * h.y;
+    out[7] = d_ci * wi.z + dS_dco * wo.z + dS_dcnh * h.z;
+}
+
+void orc_brdf_cos_grad(const double n[3], const double wo[3], const double wi[3], const double albedo[3],
+                       double rough, double metal, int32_t kind, const double g[3], double out[8])
+{
+    brdf_cos_grad(vload(n), vload(wo), vload(wi), albedo, rough, metal, kind, g, out);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * continuation sampling (Sec. 4.2): one-sample MIS mixture of env (light) importance
+ * sampling, GGX visible-normal sampling (Heitz 2018) and cosine sampling of the diffuse lobe
+ * ------------------------------------------------------------------------------------- */
+/* orthonormal basis around n (Duff, Burgess, Christensen, Hery, Kensler, Liani, Villemin 2017);
+ * the branch is taken on n.z >= 0 so that +0 and -0 choose the same basis */
+static void onb(v3 n, v3* t, v3* b, Margin* mg)
+{
+    double sg = (n.z >= 0.0) ? 1.0 : -1.0;
+    double a = -1.0 / (sg + n.z);
+    double bb = n.x * n.y * a;
+    *t = V3(1.0 + sg * n.x * n.x * a, sg * bb, -sg * n.x);
+    *b = V3(bb, sg + n.y * n.y * a, -n.y);
+    if (n.z != 0.0) note(mg, fabs(n.z) / TAU_FRAME, MK_FRAME);
+}
+
+/* Heitz 2018, "Sampling the GGX distribution of visible normals": stretch the view vector,
+ * sample a point on the projected hemisphere (disk warped towards the visible half), unstretch */
+static v3 vndf_local(v3 ve, double a, double u1, double u2)
+{
+    v3 vh = vnorm(V3(a * ve.x, a * ve.y, ve.z));
+    double lensq = vh.x * vh.x + vh.y * vh.y;
+    v3 t1 = lensq > 0.0 ? vscale(V3(-vh.y, vh.x, 0.0), 1.0 / sqrt(lensq)) : V3(1.0, 0.0, 0.0);
+    v3 t2 = vcross(vh, t1);
+    double rr = sqrt(u1), ph = 2.0 * PI * u2;
+    double p1 = rr * cos(ph), p2 = rr * sin(ph);
+    double sblend = 0.5 * (1.0 + vh.z);
+    p2 = (1.0 - sblend) * sqrt(dmax(0.0, 1.0 - p1 * p1)) + sblend * p2;
+    v3 nh = vadd(vadd(vscale(t1, p1), vscale(t2, p2)), vscale(vh, sqrt(dmax(0.0, 1.0 - p1 * p1 - p2 * p2))));
+    return vnorm(V3(a * nh.x, a * nh.y, dmax(0.0, nh.z)));
+}
+
+static v3 vndf_sample_m(v3 n, v3 wo, double a, double u1, double u2, Margin* mg)
+{
+    v3 t, b;
+    onb(n, &t, &b, mg);
+    v3 ve = V3(vdot(wo, t), vdot(wo, b), vdot(wo, n));
+    v3 m = vndf_local(ve, a, u1, u2);
+    v3 wl = vsub(vscale(m, 2.0 * vdot(ve, m)), ve); /* reflect ve about m */
+    return vadd(vadd(vscale(t, wl.x), vscale(b, wl.y)), vscale(n, wl.z));
+}
+
+void orc_vndf_sample(const double n[3], const double wo[3], double alpha, double u1, double u2, double out[3])
+{
+    vstore(out, vndf_sample_m(vload(n), vload(wo), alpha, u1, u2, NULL));
+}
+
+/* pdf of the reflected direction: G1(wo) D(h) / (4 cos_o) */
+static double vndf_pdf_v(v3 n, v3 wo, v3 wi, double a)
+{
+    double co = vdot(n, wo);
+    if (co <= 0.0) return 0.0;
+    v3 hs = vadd(wo, wi);
+    double l = vlen(hs);
+    if (l <= 0.0) return 0.0;
+    v3 h = vscale(hs, 1.0 / l);
+    if (vdot(wo, h) <= 0.0 || vdot(n, h) <= 0.0) return 0.0;
+    return orc_smith_g1(a, co) * orc_ggx_d(a, vdot(n, h)) / (4.0 * co);
+}
+
+double orc_vndf_pdf(const double n[3], const double wo[3], const double wi[3], double alpha)
+{
+    return vndf_pdf_v(vload(n), vload(wo), vload(wi), alpha);
+}
+
+static v3 cosine_sample(v3 n, double u1, double u2, Margin* mg)
+{
+    v3 t, b;
+    onb(n, &t, &b, mg);
+    double rr = sqrt(u1), ph = 2.0 * PI * u2;
+    double z = sqrt(dmax(0.0, 1.0 - u1));
+    return vadd(vadd(vscale(t, rr * cos(ph)), vscale(b, rr * sin(ph))), vscale(n, z));
+}
+
+typedef struct { double c_env, c_s; } Mix;
+
+static Mix mixture(const orc_scene* s, const double alb[3], double m)
+{
+    Mix x;
+    x.c_env = s->env_ok ? 0.25 : 0.0;
+    double f0[3], kd[3];
+    for (int k = 0; k < 3; ++k) { f0[k] = 0.04 * (1.0 - m) + m * alb[k]; kd[k] = (1.0 - m) * alb[k]; }
+    double ys = lum(f0), yd = lum(kd);
+    x.c_s = (ys + yd > 0.0) ? dmin(0.9, dmax(0.1, ys / (ys + yd))) : 0.5;
+    return x;
+}
+
+static double pdf_mix(const orc_scene* s, Mix x, v3 n, v3 wo, v3 wi, double r, Margin* mg)
+{
+    double a = alpha_of(r);
+    double ci = vdot(n, wi);
+    double pe = (x.c_env > 0.0) ? env_pdf_m(s, wi, mg) : 0.0;
+    double pv = vndf_pdf_v(n, wo, wi, a);
+    double pc = dmax(0.0, ci) / PI;
+    return x.c_env * pe + (1.0 - x.c_env) * (x.c_s * pv + (1.0 - x.c_s) * pc);
+}
+
+static double sample_cont_m(const orc_scene* s, v3 n, v3 wo, const double alb[3], double r, double m,
+                            const uint32_t x[4], v3* dir, Margin* mg)
+{
+    Mix mx = mixture(s, alb, m);
+    double u = orc_uniform(x[0]);
+    double t2 = mx.c_env + (1.0 - mx.c_env) * mx.c_s;
+    note(mg, fabs(u - t2) / TAU_LOBE, MK_LOBE);
+    if (u < mx.c_env) {
+        int tex;
+        env_sample_m(s, orc_uniform(x[1]), orc_uniform(x[2]), x[3], dir, &tex, mg);
+    } else if (u < t2) {
+        *dir = vndf_sample_m(n, wo, alpha_of(r), orc_uniform(x[1]), orc_uniform(x[2]), mg);
+    } else {
+        *dir = cosine_sample(n, orc_uniform(x[1]), orc_uniform(x[2]), mg);
+    }
+    return pdf_mix(s, mx, n, wo, *dir, r, mg);
+}
+
+double orc_sample_continuation(const orc_scene* s, const double n[3], const double wo[3],
+                               const double albedo[3], double rough, double metal, int32_t kind,
+                               const uint32_t x[4], double out_dir[3])
+{
+    (void)kind;
+    v3 d;
+    double p = sample_cont_m(s, vload(n), vload(wo), albedo, rough, metal, x, &d, NULL);
+    vstore(out_dir, d);
+    return p;
+}
+
+double orc_pdf_continuation(const orc_scene* s, const double n[3], const double wo[3],
+                            const double albedo[3], double rough, double metal, int32_t kind,
+                            const double wi[3])
+{
+    (void)kind;
+    Mix mx = mixture(s, albedo, metal);
+    return pdf_mix(s, mx, vload(n), vload(wo), vload(wi), rough, NULL);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * weighted reservoir sampling (Appendix A "Spatial-temporal Reuse", Chao 1982): a stream of
+ * candidates, w_sum accumulated, the newcomer kept with probability gamma / w_sum
+ * ------------------------------------------------------------------------------------- */
+typedef struct { double wsum; int sel; } Reservoir;
+
+static int wrs_update(Reservoir* rs, double gamma, double u, int j)
+{
+    rs->wsum += gamma;
+    if (u * rs->wsum < gamma) { rs->sel = j; return 1; }
+    return 0;
+}
+
+int32_t orc_wrs(const double* gamma, const double* u, int32_t m, double* w_sum)
+{
+    Reservoir rs = {0.0, -1};
+    for (int j = 0; j < m; ++j) wrs_update(&rs, gamma[j], u[j], j);
+    if (w_sum) *w_sum = rs.wsum;
+    return rs.sel;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * materials: bilinear texture lookup, texel centres at (i + 0.5) / w, clamp to edge
+ * ------------------------------------------------------------------------------------- */
+typedef struct { int idx[4]; double w[4]; double dw_dx[4], dw_dy[4]; } Taps;
+
+static void taps_at(int w, int h, double su, double sv, Taps* tp)
+{
+    double x = su * w - 0.5, y = sv * h - 0.5;
+    double x0 = floor(x), y0 = floor(y);
+    double fx = x - x0, fy = y - y0;
+    int ix0 = (int)x0, iy0 = (int)y0;
+    int ix1 = ix0 + 1, iy1 = iy0 + 1;
+    ix0 = ix0 < 0 ? 0 : (ix0 > w - 1 ? w - 1 : ix0);
+    ix1 = ix1 < 0 ? 0 : (ix1 > w - 1 ? w - 1 : ix1);
+    iy0 = iy0 < 0 ? 0 : (iy0 > h - 1 ? h - 1 : iy0);
+    iy1 = iy1 < 0 ? 0 : (iy1 > h - 1 ? h - 1 : iy1);
+    tp->idx[0] = iy0 * w + ix0; tp->idx[1] = iy0 * w + ix1;
+    tp->idx[2] = iy1 * w + ix0; tp->idx[3] = iy1 * w + ix1;
+    tp->w[0] = (1 - fx) * (1 - fy); tp->w[1] = fx * (1 - fy);
+    tp->w[2] = (1 - fx) * fy;       tp->w[3] = fx * fy;
+    /* derivatives w.r.t. the texture coordinate (su, sv) */
+    tp->dw_dx[0] = -(1 - fy) * w; tp->dw_dx[1] = (1 - fy) * w; tp->dw_dx[2] = -fy * w; tp->dw_dx[3] = fy * w;
+    tp->dw_dy[0] = -(1 - fx) * h; tp->dw_dy[1] = -fx * h; tp->dw_dy[2] = (1 - fx) * h; tp->dw_dy[3] = fx * h;
+}
+
+typedef struct {
+    int tri;
+    double u, v, t;
+    v3 x, n, N;      /* hit point, shading normal (flipped towards -d), unflipped face normal */
+    double sign;     /* n = sign * N / |N| */
+    v3 e1, e2;
+    double su, sv;   /* texture coordinate */
+    Taps tp;
+    double alb[3], rgh, met;
+} Shade;
+
+static void shade_at(const orc_scene* s, int tri, double u, double v, double t, v3 d, Shade* sh, Margin* mg)
+{
+    v3 a, b, c;
+    tri_verts(s, tri, &a, &b, &c);
+    sh->tri = tri; sh->u = u; sh->v = v; sh->t = t;
+    sh->e1 = vsub(b, a); sh->e2 = vsub(c, a);
+    sh->N = vcross(sh->e1, sh->e2);
+    v3 nh = vnorm(sh->N);
+    double nd = vdot(nh, d);
+    note(mg, fabs(nd) / TAU_FLIP, MK_FLIP);
+    sh->sign = (nd > 0.0) ? -1.0 : 1.0;
+    sh->n = vscale(nh, sh->sign);
+    sh->x = vadd(a, vadd(vscale(sh->e1, u), vscale(sh->e2, v)));
+    const double* uv = s->UV + 6 * tri;
+    double w0 = 1.0 - u - v;
+    sh->su = w0 * uv[0] + u * uv[2] + v * uv[4];
+    sh->sv = w0 * uv[1] + u * uv[3] + v * uv[5];
+    taps_at(s->tw, s->th, sh->su, sh->sv, &sh->tp);
+    sh->alb[0] = sh->alb[1] = sh->alb[2] = sh->rgh = sh->met = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        int i = sh->tp.idx[k];
+        double w = sh->tp.w[k];
+        for (int ch = 0; ch < 3; ++ch) sh->alb[ch] += w * s->alb[3 * i + ch];
+        sh->rgh += w * s->rgh[i];
+        sh->met += w * s->met[i];
+    }
+}
+
+/* ---------------------------------------------------------------------------------------
+ * one path sample (Eq. pbr_render with the split of Eq. incident, RIS of Eq. restir for the
+ * direct part, Eq. mc_indir + Eq. sec_bouce for the indirect part)
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    const orc_scene* s;
+    const orc_view* v;
+    const orc_params* p;
+    double R[9], o[3];
+} Ctx;
+
+typedef struct {
+    double rgb[3];
+    v3 d0;
+    int prim_tri;
+    double pu, pv, pt;
+    int bg_texel;
+    int sel, y_texel;
+    v3 y;
+    double WV;        /* RIS weight times visibility at the primary vertex */
+    int has_cont;
+    v3 wc;
+    double p_ind;
+    double Lind[3];
+} Rec;
+
+static void rng(const Ctx* c, uint32_t pixel, uint32_t sample, uint32_t bounce, uint32_t purpose, uint32_t j, uint32_t out[4])
+{
+    uint32_t ctr[4] = {pixel, sample, ((uint32_t)c->v->view_index << 16) | (bounce << 8) | purpose, j};
+    uint32_t key[2] = {c->p->seed_lo, c->p->seed_hi};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+static void ctx_init(Ctx* c, const orc_scene* s, const orc_view* v, const orc_params* p)
+{
+    c->s = s; c->v = v; c->p = p;
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) c->R[3 * i + j] = v->c2w[4 * i + j];
+        c->o[i] = v->c2w[4 * i + 3];
+    }
+}
+
+/* pinhole camera ray through the jittered pixel position (Sec. 3.2, r(t) = o + t d) */
+static v3 camera_dir(const Ctx* c, int px, int py, int smp)
+{
+    uint32_t x[4];
+    rng(c, (uint32_t)(py * c->v->width + px), (uint32_t)smp, 0, PURPOSE_CAMERA, 0, x);
+    double jx = orc_uniform(x[0]), jy = orc_uniform(x[1]);
+    double dc[3] = {(px + jx - c->v->K[2]) / c->v->K[0], (py + jy - c->v->K[3]) / c->v->K[1], 1.0};
+    v3 d = V3(c->R[0] * dc[0] + c->R[1] * dc[1] + c->R[2] * dc[2],
+              c->R[3] * dc[0] + c->R[4] * dc[1] + c->R[5] * dc[2],
+              c->R[6] * dc[0] + c->R[7] * dc[1] + c->R[8] * dc[2]);
+    return vnorm(d);
+}
+
+static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin* mg, int64_t* cnt)
+{
+    const orc_scene* s = c->s;
+    const int M = c->p->ris_m, B = c->v->bounces, kind = c->p->brdf_kind;
+    const uint32_t pix = (uint32_t)(py * c->v->width + px);
+    memset(rec, 0, sizeof(*rec));
+    rec->prim_tri = -1; rec->sel = -1; rec->y_texel = -1; rec->bg_texel = -1;
+    v3 o = vload(c->o), d = camera_dir(c, px, py, smp);
+    rec->d0 = d;
+    if (cnt) { cnt[0]++; cnt[6]++; }
+    Hit h;
+    bvh_closest(s, o, d, -1, &h, cnt);
+    closest_margins(s, o, d, -1, &h, mg);
+    if (h.tri < 0) {
+        /* primary miss: the environment seen directly */
+        int tx = env_texel_m(s, d, mg);
+        rec->bg_texel = tx;
+        for (int k = 0; k < 3; ++k) rec->rgb[k] = s->env[3 * tx + k];
+        return;
+    }
+    rec->prim_tri = h.tri; rec->pu = h.u; rec->pv = h.v; rec->pt = h.t;
+    double beta[3] = {1, 1, 1}, beta_ind[3] = {1, 1, 1};
+    double L[3] = {0, 0, 0}, Lind[3] = {0, 0, 0};
+    for (int b = 0; b < B; ++b) {
+        Shade sh;
+        shade_at(s, h.tri, h.u, h.v, h.t, d, &sh, mg);
+        v3 wo = vscale(d, -1.0);
+        /* ---- direct light: RIS over M env candidates, streamed through a reservoir ---- */
+        double direct[3] = {0, 0, 0};
+        if (s->env_ok && M > 0) {
+            Reservoir rs = {0.0, -1};
+            v3 ysel = V3(0, 0, 0);
+            int ytex = -1;
+            double fsel[3] = {0, 0, 0}, phat_sel = 0.0;
+            for (int j = 0; j < M; ++j) {
+                uint32_t x[4];
+                rng(c, pix, (uint32_t)smp, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j, x);
+                v3 dir;
+                int tex;
+                double q = env_sample_m(s, orc_uniform(x[0]), orc_uniform(x[1]), x[3], &dir, &tex, mg);
+                double fc[3];
+                brdf_cos(sh.n, wo, dir, sh.alb, sh.rgh, sh.met, kind, fc);
+                double phat = lum(s->env + 3 * tex) * lum(fc); /* p_hat = Y(L_env) Y(f_r) cos */
+                double gamma = phat / q;                      /* gamma_s = p_hat / q_dir */
+                double ua = orc_uniform(x[2]);
+                if (cnt) cnt[5]++;
+                if (wrs_update(&rs, gamma, ua, j)) {
+                    ysel = dir; ytex = tex; phat_sel = phat;
+                    for (int k = 0; k < 3; ++k) fsel[k] = fc[k];
+                }
+                if (gamma > 0.0) note(mg, fabs(ua * rs.wsum - gamma) / rs.wsum / TAU_ACC, MK_ACC);
+            }
+            if (rs.sel >= 0 && rs.wsum > 0.0) {
+                /* Eq. restir with N = 1: f(y) / p_hat(y) * (1/M) sum gamma */
+                double W = rs.wsum / (M * phat_sel);
+                if (cnt) cnt[2]++;
+                int occluded = bvh_any(s, sh.x, ysel, sh.tri, cnt, mg);
+                double V = occluded ? 0.0 : 1.0;
+                for (int k = 0; k < 3; ++k) direct[k] = V * W * s->env[3 * ytex + k] * fsel[k];
+                if (b == 0) { rec->sel = rs.sel; rec->y = ysel; rec->y_texel = ytex; rec->WV = V * W; }
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            L[k] += beta[k] * direct[k];
+            if (b >= 1) Lind[k] += beta_ind[k] * direct[k];
+        }
+        if (b == B - 1) break;
+        /* ---- indirect light: one continuation ray from the MIS mixture ---- */
+        uint32_t x[4];
+        rng(c, pix, (uint32_t)smp, (uint32_t)b, PURPOSE_CONTINUE, 0, x);
+        v3 wc;
+        double pind = sample_cont_m(s, sh.n, wo, sh.alb, sh.rgh, sh.met, x, &wc, mg);
+        double fc[3];
+        brdf_cos(sh.n, wo, wc, sh.alb, sh.rgh, sh.met, kind, fc);
+        if (!(pind > 0.0) || (fc[0] <= 0.0 && fc[1] <= 0.0 && fc[2] <= 0.0)) break;
+        if (b == 0) { rec->has_cont = 1; rec->wc = wc; rec->p_ind = pind; }
+        for (int k = 0; k < 3; ++k) {
+            double f = fc[k] / pind;
+            beta[k] *= f;
+            if (b >= 1) beta_ind[k] *= f;
+        }
+        if (cnt) cnt[1]++;
+        Hit nh;
+        bvh_closest(s, sh.x, wc, sh.tri, &nh, cnt);
+        closest_margins(s, sh.x, wc, sh.tri, &nh, mg);
+        if (nh.tri < 0) break; /* escaped: its env light is already in the direct term */
+        h = nh;
+        d = wc;
+    }
+    for (int k = 0; k < 3; ++k) { rec->rgb[k] = L[k]; rec->Lind[k] = Lind[k]; }
+}
+
+/* ---------------------------------------------------------------------------------------
+ * adjoint of one sample (PRIMARY mode, Sec. 4.2 last sentence and Appendix C limitations)
+ * ------------------------------------------------------------------------------------- */
+enum { GB_ALB = 0, GB_RGH, GB_MET, GB_ENV, GB_VERT, GB_N };
+typedef struct { int32_t buf; int64_t idx; double val; } Entry;
+typedef struct { Entry* e; size_t n, cap; } Sparse;
+
+static void sp_add(Sparse* sp, int buf, int64_t idx, double val)
+{
+    if (val == 0.0) return;
+    if (sp->n == sp->cap) {
+        sp->cap = sp->cap ? 2 * sp->cap : 4096;
+        sp->e = (Entry*)realloc(sp->e, sizeof(Entry) * sp->cap);
+    }
+    sp->e[sp->n].buf = buf; sp->e[sp->n].idx = idx; sp->e[sp->n].val = val;
+    sp->n++;
+}
+
+static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], Sparse* sp)
+{
+    const orc_scene* s = c->s;
+    const int kind = c->p->brdf_kind;
+    if (rec->prim_tri < 0) {
+        for (int k = 0; k < 3; ++k) sp_add(sp, GB_ENV, 3 * (int64_t)rec->bg_texel + k, g[k]);
+        return;
+    }
+    Shade sh;
+    shade_at(s, rec->prim_tri, rec->pu, rec->pv, rec->pt, rec->d0, &sh, NULL);
+    v3 wo = vscale(rec->d0, -1.0);
+    double gm[8] = {0, 0, 0, 0, 0, 0, 0, 0}, tmp[8];
+    /* direct_1 = V W L_env(y) (f_r cos)(y) */
+    if (rec->sel >= 0 && rec->WV != 0.0) {
+        double fc[3], gq[3];
+        brdf_cos(sh.n, wo, rec->y, sh.alb, sh.rgh, sh.met, kind, fc);
+        for (int k = 0; k < 3; ++k) {
+            double le = s->env[3 * rec->y_texel + k];
+            sp_add(sp, GB_ENV, 3 * (int64_t)rec->y_texel + k, g[k] * rec->WV * fc[k]);
+            gq[k] = g[k] * rec->WV * le;
+        }
+        brdf_cos_grad(sh.n, wo, rec->y, sh.alb, sh.rgh, sh.met, kind, gq, tmp);
+        for (int k = 0; k < 8; ++k) gm[k] += tmp[k];
+    }
+    /* beta_1 L_ind = (f_r cos)(wc) / p_ind * L_ind */
+    if (rec->has_cont) {
+        double gq[3];
+        for (int k = 0; k < 3; ++k) gq[k] = g[k] * rec->Lind[k] / rec->p_ind;
+        brdf_cos_grad(sh.n, wo, rec->wc, sh.alb, sh.rgh, sh.met, kind, gq, tmp);
+        for (int k = 0; k < 8; ++k) gm[k] += tmp[k];
+    }
+    /* textures (bilinear scatter) and the texture coordinate */
+    double gsu = 0.0, gsv = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        int i = sh.tp.idx[k];
+        double w = sh.tp.w[k];
+        double dot = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            sp_add(sp, GB_ALB, 3 * (int64_t)i + ch, w * gm[ch]);
+            dot += gm[ch] * s->alb[3 * i + ch];
+        }
+        sp_add(sp, GB_RGH, i, w * gm[3]);
+        sp_add(sp, GB_MET, i, w * gm[4]);
+        dot += gm[3] * s->rgh[i] + gm[4] * s->met[i];
+        gsu += sh.tp.dw_dx[k] * dot;
+        gsv += sh.tp.dw_dy[k] * dot;
+    }
+    /* vertices: (u, v) through the intersection, n through the face normal */
+    const double* uv = s->UV + 6 * sh.tri;
+    double gu = gsu * (uv[2] - uv[0]) + gsv * (uv[3] - uv[1]);
+    double gv = gsu * (uv[4] - uv[0]) + gsv * (uv[5] - uv[1]);
+    v3 md = vscale(rec->d0, -1.0);
+    /* A = [e1 | e2 | -d]; rows of A^-1 are (e2 x -d, -d x e1, e1 x e2) / det */
+    v3 r0 = vcross(sh.e2, md), r1 = vcross(md, sh.e1);
+    double det = vdot(sh.e1, r0);
+    v3 z = vscale(vadd(vscale(r0, gu), vscale(r1, gv)), 1.0 / det); /* A^-T (gu, gv, 0) */
+    double bw[3] = {1.0 - sh.u - sh.v, sh.u, sh.v};
+    v3 gvert[3];
+    for (int k = 0; k < 3; ++k) gvert[k] = vscale(z, -bw[k]);
+    v3 gn = V3(gm[5], gm[6], gm[7]);
+    double Nl = vlen(sh.N);
+    v3 Nh = vscale(sh.N, 1.0 / Nl);
+    v3 gNh = vscale(gn, sh.sign);
+    v3 gN = vscale(vsub(gNh, vscale(Nh, vdot(Nh, gNh))), 1.0 / Nl);
+    v3 ge1 = vcross(sh.e2, gN), ge2 = vcross(gN, sh.e1);
+    gvert[0] = vsub(gvert[0], vadd(ge1, ge2));
+    gvert[1] = vadd(gvert[1], ge1);
+    gvert[2] = vadd(gvert[2], ge2);
+    for (int k = 0; k < 3; ++k) {
+        int vi = s->F[3 * sh.tri + k];
+        sp_add(sp, GB_VERT, 3 * (int64_t)vi + 0, gvert[k].x);
+        sp_add(sp, GB_VERT, 3 * (int64_t)vi + 1, gvert[k].y);
+        sp_add(sp, GB_VERT, 3 * (int64_t)vi + 2, gvert[k].z);
+    }
+}
+
+/* detached evaluation of one sample's primary-vertex terms with the parameters of `ev` */
+static void sample_detached(const Ctx* c, const orc_scene* ev, const Rec* rec, double out[3])
+{
+    const int kind = c->p->brdf_kind;
+    if (rec->prim_tri < 0) {
+        for (int k = 0; k < 3; ++k) out[k] = ev->env[3 * rec->bg_texel + k];
+        return;
+    }
+    v3 o = vload(c->o);
+    double t, u, v;
+    out[0] = out[1] = out[2] = 0.0;
+    if (!tri_solve(ev, rec->prim_tri, o, rec->d0, &t, &u, &v, NULL)) return;
+    Shade sh;
+    shade_at(ev, rec->prim_tri, u, v, t, rec->d0, &sh, NULL);
+    v3 wo = vscale(rec->d0, -1.0);
+    if (rec->sel >= 0 && rec->WV != 0.0) {
+        double fc[3];
+        brdf_cos(sh.n, wo, rec->y, sh.alb, sh.rgh, sh.met, kind, fc);
+        for (int k = 0; k < 3; ++k) out[k] += rec->WV * ev->env[3 * rec->y_texel + k] * fc[k];
+    }
+    if (rec->has_cont) {
+        double fc[3];
+        brdf_cos(sh.n, wo, rec->wc, sh.alb, sh.rgh, sh.met, kind, fc);
+        for (int k = 0; k < 3; ++k) out[k] += fc[k] / rec->p_ind * rec->Lind[k];
+    }
+}
+
+/* ---------------------------------------------------------------------------------------
+ * pixel loops, threaded over contiguous chunks of the pixel list
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    int mode; /* 0 render, 1 backward, 2 detached */
+    Ctx c;
+    const orc_scene* ev;
+    const int32_t* pixels;
+    int32_t i0, i1;
+    double* out_rgb; double* out_margin; int32_t* out_prim;
+    const double* d_rgb;
+    Sparse sp;
+    int64_t cnt[ORC_NCOUNT];
+} Job;
+
+static void* job_run(void* arg)
+{
+    Job* jb = (Job*)arg;
+    const Ctx* c = &jb->c;
+    const int W = c->v->width, spp = c->v->spp;
+    for (int i = jb->i0; i < jb->i1; ++i) {
+        int pix = jb->pixels ? jb->pixels[i] : i;
+        int px = pix % W, py = pix / W;
+        double acc[3] = {0, 0, 0};
+        Margin mg = {INFINITY, 0};
+        Margin* pmg = (jb->mode == 0 && jb->out_margin && c->p->want_margin) ? &mg : NULL;
+        for (int smp = 0; smp < spp; ++smp) {
+            Rec rec;
+            path_sample(c, px, py, smp, &rec, pmg, jb->cnt);
+            if (jb->mode == 0) {
+                for (int k = 0; k < 3; ++k) acc[k] += rec.rgb[k];
+                if (jb->out_prim) jb->out_prim[(size_t)i * spp + smp] = rec.prim_tri;
+            } else if (jb->mode == 1) {
+                double g[3];
+                for (int k = 0; k < 3; ++k) g[k] = jb->d_rgb[3 * (size_t)i + k] / spp;
+                if (g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0) sample_grad(c, &rec, g, &jb->sp);
+            } else {
+                double o3[3];
+                sample_detached(c, jb->ev, &rec, o3);
+                for (int k = 0; k < 3; ++k) acc[k] += o3[k];
+            }
+        }
+        if (jb->mode != 1)
+            for (int k = 0; k < 3; ++k) jb->out_rgb[3 * (size_t)i + k] = acc[k] / spp;
+        if (jb->mode == 0 && jb->out_margin) {
+            jb->out_margin[2 * (size_t)i] = mg.m;
+            jb->out_margin[2 * (size_t)i + 1] = (double)mg.kind;
+        }
+    }
+    return NULL;
+}
+
+static int run_jobs(int mode, const orc_scene* s, const orc_scene* ev, const orc_view* v, const orc_params* p,
+                    const int32_t* pixels, int32_t n, double* out_rgb, double* out_margin, int32_t* out_prim,
+                    const double* d_rgb, const orc_grads* g, int64_t* counts)
+{
+    if (!s || !v || !p || v->width < 1 || v->height < 1 || v->spp < 1 || v->bounces < 1 || p->ris_m < 0) return 1;
+    if (!pixels) n = v->width * v->height;
+    for (int i = 0; pixels && i < n; ++i)
+        if (pixels[i] < 0 || pixels[i] >= v->width * v->height) return 1;
+    int nt = p->threads < 1 ? 1 : p->threads;
+    if (nt > n) nt = n > 0 ? n : 1;
+    Job* jobs = (Job*)calloc((size_t)nt, sizeof(Job));
+    pthread_t* th = (pthread_t*)calloc((size_t)nt, sizeof(pthread_t));
+    for (int t = 0; t < nt; ++t) {
+        Job* jb = &jobs[t];
+        jb->mode = mode;
+        ctx_init(&jb->c, s, v, p);
+        jb->ev = ev;
+        jb->pixels = pixels;
+        jb->i0 = (int32_t)((int64_t)n * t / nt);
+        jb->i1 = (int32_t)((int64_t)n * (t + 1) / nt);
+        jb->out_rgb = out_rgb; jb->out_margin = out_margin; jb->out_prim = out_prim;
+        jb->d_rgb = d_rgb;
+    }
+    if (nt == 1) job_run(&jobs[0]);
+    else {
+        for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, job_run, &jobs[t]);
+        for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+    }
+    for (int t = 0; t < nt; ++t) {
+        if (counts) for (int k = 0; k < ORC_NCOUNT; ++k) counts[k] += jobs[t].cnt[k];
+        if (mode == 1 && g) {
+            double* dst[GB_N] = {g->albedo, g->roughness, g->metallic, g->env, g->verts};
+            double* dab[GB_N] = {g->albedo_abs, g->roughness_abs, g->metallic_abs, g->env_abs, g->verts_abs};
+            for (size_t e = 0; e < jobs[t].sp.n; ++e) {
+                const Entry* en = &jobs[t].sp.e[e];
+                if (dst[en->buf]) dst[en->buf][en->idx] += en->val;
+                if (dab[en->buf]) dab[en->buf][en->idx] += fabs(en->val);
+            }
+        }
+        free(jobs[t].sp.e);
+    }
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+int orc_render(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels, int32_t n_pixels,
+               double* out_rgb, double* out_margin, int32_t* out_prim_tri, int64_t* counts)
+{
+    if (!out_rgb) return 1;
+    return run_jobs(0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, out_prim_tri, NULL, NULL, counts);
+}
+
+int orc_backward(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels, int32_t n_pixels,
+                 const double* d_rgb, const orc_grads* g, int64_t* counts)
+{
+    if (!d_rgb || !g) return 1;
+    return run_jobs(1, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_rgb, g, counts);
+}
+
+int orc_render_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v, const orc_params* p,
+                        const int32_t* pixels, int32_t n_pixels, double* out_rgb)
+{
+    if (!eval || !out_rgb) return 1;
+    return run_jobs(2, frozen, eval, v, p, pixels, n_pixels, out_rgb, NULL, NULL, NULL, NULL, NULL);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * LBVH (Appendix A: "linear BVH (LBVH, Karras 2012)"), restated top-down for comparison.
+ * Morton codes of the triangle centroids in the centroid bounding box (10 bits per axis,
+ * x in the highest position of each triple), key = code << 32 | triangle id, sorted.
+ * The binary radix tree over the sorted keys: a node covering [first, last] splits after
+ * the last key that shares more leading bits with keys[first] than keys[last] does; its
+ * children are numbered by the split position (left = g, right = g + 1), which is the
+ * numbering Karras's bottom-up construction produces.
+ * ------------------------------------------------------------------------------------- */
+static uint32_t spread10(uint32_t v)
+{
+    uint32_t r = 0;
+    for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+static int clz64(uint64_t x) { return x ? __builtin_clzll(x) : 64; }
+
+static int cmp_u64(const void* a, const void* b)
+{
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return (x > y) - (x < y);
+}
+
+typedef struct { const uint64_t* k; int32_t* left; int32_t* right; int32_t* parent; int n; } Lb;
+
+static void lb_node(Lb* L, int first, int last, int idx)
+{
+    int dnode = clz64(L->k[first] ^ L->k[last]);
+    int g = first;
+    for (int i = first; i < last; ++i)
+        if (clz64(L->k[first] ^ L->k[i]) > dnode) g = i;
+    if (g == first) { L->left[idx] = ~g; L->parent[(L->n - 1) + g] = idx; }
+    else { L->left[idx] = g; L->parent[g] = idx; lb_node(L, first, g, g); }
+    if (g + 1 == last) { L->right[idx] = ~(g + 1); L->parent[(L->n - 1) + g + 1] = idx; }
+    else { L->right[idx] = g + 1; L->parent[g + 1] = idx; lb_node(L, g + 1, last, g + 1); }
+}
+
+static void lb_box(int node, int n, const int32_t* left, const int32_t* right, float* lo, float* hi)
+{
+    int ch[2] = {left[node], right[node]};
+    for (int c = 0; c < 2; ++c) if (ch[c] >= 0) lb_box(ch[c], n, left, right, lo, hi);
+    for (int k = 0; k < 3; ++k) {
+        int a = ch[0] >= 0 ? ch[0] : (n - 1) + ~ch[0];
+        int b = ch[1] >= 0 ? ch[1] : (n - 1) + ~ch[1];
+        lo[3 * node + k] = fminf(lo[3 * a + k], lo[3 * b + k]);
+        hi[3 * node + k] = fmaxf(hi[3 * a + k], hi[3 * b + k]);
+    }
+}
+
+int orc_lbvh(const float* verts, const int32_t* tris, int32_t n, uint64_t* keys, int32_t* left, int32_t* right,
+             int32_t* parent, float* lo, float* hi)
+{
+    if (n <= 0) return 0;
+    float* cen = (float*)malloc(sizeof(float) * 3 * (size_t)n);
+    float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const float third = 1.0f / 3.0f;
+    for (int t = 0; t < n; ++t)
+        for (int k = 0; k < 3; ++k) {
+            float a = verts[3 * tris[3 * t] + k], b = verts[3 * tris[3 * t + 1] + k], c = verts[3 * tris[3 * t + 2] + k];
+            float s = a + b;
+            s = s + c;
+            float m = s * third;
+            cen[3 * t + k] = m;
+            if (m < clo[k]) clo[k] = m;
+            if (m > chi[k]) chi[k] = m;
+        }
+    for (int t = 0; t < n; ++t) {
+        uint32_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            float ext = chi[k] - clo[k];
+            float f = 0.0f;
+            if (ext > 0.0f) {
+                float num = cen[3 * t + k] - clo[k];
+                float r = num / ext;
+                f = r * 1024.0f;
+            }
+            float fl = floorf(f);
+            int qi = (int)fl;
+            if (qi < 0) qi = 0;
+            if (qi > 1023) qi = 1023;
+            q[k] = (uint32_t)qi;
+        }
+        uint32_t code = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+        keys[t] = ((uint64_t)code << 32) | (uint32_t)t;
+    }
+    qsort(keys, (size_t)n, sizeof(uint64_t), cmp_u64);
+    for (int i = 0; i < 2 * n - 1; ++i) parent[i] = -1;
+    /* leaf boxes: exact min / max of the three vertices */
+    for (int i = 0; i < n; ++i) {
+        int t = (int)(uint32_t)keys[i];
+        for (int k = 0; k < 3; ++k) {
+            float a = verts[3 * tris[3 * t] + k], b = verts[3 * tris[3 * t + 1] + k], c = verts[3 * tris[3 * t + 2] + k];
+            lo[3 * ((n - 1) + i) + k] = fminf(fminf(a, b), c);
+            hi[3 * ((n - 1) + i) + k] = fmaxf(fmaxf(a, b), c);
+        }
+    }
+    if (n >= 2) {
+        Lb L = {keys, left, right, parent, n};
+        lb_node(&L, 0, n - 1, 0);
+        lb_box(0, n, left, right, lo, hi);
+    }
+    free(cen);
+    return 0;
+}

@@ -1,0 +1,137 @@
+/*
+ * MIRReS stage-2 oracle: plain, slow, FP64 CPU restatement of the forward and adjoint
+ * multi-bounce path tracer with RIS/WRS environment-light sampling.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg may load this library. The product path (the CUDA library) never calls it and shares
+ * no code, header, table or constant generator with it.
+ *
+ * Everything here is restated from the paper's text:
+ *   rendering equation and incident-light split ........ Eq. (pbr_render), Eq. (incident), Sec. 3.2
+ *   direct light MC / RIS estimator ..................... Eq. (pbr_dir), Eq. (restir), Sec. 4.1
+ *   weighted reservoir sampling (streaming RIS) ......... Appendix A, "Spatial-temporal Reuse"
+ *   indirect light, MIS of light and GGX sampling ....... Eq. (pbr_indir), Eq. (mc_indir), Sec. 4.2
+ *   recursive bounces, first three, detached gradients .. Eq. (sec_bouce), Sec. 4.2
+ *   visibility by ray-mesh intersection, LBVH ........... Appendix A, "Visibility estimation"
+ *   vertex offsets refined through the intersection ..... Sec. 3.2 "Mesh refinement", Eq. (loss_pbr)
+ *   luminance operator Y = (r+g+b)/3 .................... Appendix A, "Training details"
+ * Readings of passages the paper leaves open are listed in the repository's design notes.
+ */
+#ifndef MIRRES_ORACLE_H
+#define MIRRES_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    const float* verts;    int32_t n_verts;   /* [V][3] */
+    const int32_t* tris;   int32_t n_tris;    /* [F][3] */
+    const float* tri_uv;                      /* [F][3][2] */
+    const float* albedo; const float* roughness; const float* metallic;
+    int32_t tex_w, tex_h;                     /* [h][w][3], [h][w], [h][w] */
+    const float* env; int32_t env_w, env_h;   /* [h][w][3] lat-long, row 0 = zenith */
+} orc_scene_desc;
+
+typedef struct orc_scene orc_scene;
+
+typedef struct {
+    double K[4];        /* fx, fy, cx, cy */
+    double c2w[12];     /* row-major [R | t], R columns = camera x (right), y (down), z (fwd) */
+    int32_t width, height, spp, bounces;
+    int32_t view_index; /* enters the random counter */
+} orc_view;
+
+typedef struct {
+    int32_t ris_m;       /* RIS candidates per shading point */
+    uint32_t seed_lo, seed_hi;
+    int32_t brdf_kind;   /* 0 = GGX + Lambert (the method); 1 = Lambert only (furnace pin) */
+    int32_t threads;     /* worker threads (>= 1) */
+    int32_t want_margin; /* 1: track decision margins */
+} orc_params;
+
+/* per-pixel gradient destinations; any pointer may be NULL */
+typedef struct {
+    double* albedo; double* roughness; double* metallic; double* env; double* verts;
+    /* absolute-value sums of the same scattered terms (a conditioning measure), may be NULL */
+    double* albedo_abs; double* roughness_abs; double* metallic_abs; double* env_abs; double* verts_abs;
+} orc_grads;
+
+/* counters: [0] primary rays, [1] continuation rays, [2] shadow rays, [3] BVH nodes visited,
+ * [4] triangle tests, [5] RIS candidates, [6] samples, [7] unused */
+#define ORC_NCOUNT 8
+
+orc_scene* orc_scene_new(const orc_scene_desc* d);
+void orc_scene_free(orc_scene* s);
+double orc_scene_tmin(const orc_scene* s);
+
+/* Forward render of listed pixels (pixel = py*width + px; NULL = all pixels in order).
+ * out_rgb [n][3]; out_margin [n][2] (min normalised decision margin over the pixel's samples
+ * and the kind of that decision, may be NULL); out_prim_tri [n][spp] (primary hit triangle or -1, may be NULL). */
+int orc_render(const orc_scene* s, const orc_view* v, const orc_params* p,
+               const int32_t* pixels, int32_t n_pixels,
+               double* out_rgb, double* out_margin, int32_t* out_prim_tri, int64_t* counts);
+
+/* Adjoint (PRIMARY mode: gradients of the primary-vertex terms, indirect light, visibility,
+ * the RIS weight and all sampling decisions detached). d_rgb [n][3] = dL/dI at the listed
+ * pixels. Gradients are accumulated (+=). */
+int orc_backward(const orc_scene* s, const orc_view* v, const orc_params* p,
+                 const int32_t* pixels, int32_t n_pixels, const double* d_rgb,
+                 const orc_grads* g, int64_t* counts);
+
+/* Detached forward: the primary-vertex terms evaluated with the parameters of `eval`, every
+ * detached quantity (sampling decisions, W, V, L_ind, p_ind, hit triangle) taken from
+ * `frozen`. Its derivative w.r.t. `eval` at eval == frozen is what orc_backward returns. */
+int orc_render_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v,
+                        const orc_params* p, const int32_t* pixels, int32_t n_pixels,
+                        double* out_rgb);
+
+/* Ray queries against the oracle's own BVH (mode 0 closest, 1 any) or brute force (2, 3).
+ * rays [n][6] = origin, direction; skip_tri [n] (-1 none); out_tri [n]; out_tuv [n][3];
+ * out_margin [n] (may be NULL). t in (t_min, inf). */
+int orc_trace(const orc_scene* s, const double* rays, const int32_t* skip_tri, int32_t n, int32_t mode,
+              int32_t* out_tri, double* out_tuv, double* out_margin);
+
+/* LBVH (Karras 2012) restated top-down, FP32 Morton codes with a fixed operation order.
+ * keys [F] sorted; left/right [F-1] child codes (>= 0 internal node, < 0 leaf ~pos);
+ * parent [2F-1] (internal nodes first, then leaves); lo/hi [2F-1][3]. */
+int orc_lbvh(const float* verts, const int32_t* tris, int32_t n_tris,
+             uint64_t* keys, int32_t* left, int32_t* right, int32_t* parent, float* lo, float* hi);
+
+/* Environment sampling tables: cond [h][w+1], marg [h+1], prob [h][w]; returns total weight. */
+double orc_env_tables(const orc_scene* s, double* cond, double* marg, double* prob);
+
+/* ---- unit functions, exported for the pins ---- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_uniform(uint32_t x);
+/* f_r(wo, wi) * max(0, n.wi) per channel, GGX + Lambert */
+void orc_brdf_cos(const double n[3], const double wo[3], const double wi[3], const double albedo[3],
+                  double rough, double metal, int32_t kind, double out[3]);
+/* gradient of sum_c g[c] * (f_r cos)[c] w.r.t. albedo[3], rough, metal, n[3] -> out[8] */
+void orc_brdf_cos_grad(const double n[3], const double wo[3], const double wi[3], const double albedo[3],
+                       double rough, double metal, int32_t kind, const double g[3], double out[8]);
+double orc_ggx_d(double alpha, double cos_nh);
+double orc_smith_g1(double alpha, double cos_nv);
+void orc_vndf_sample(const double n[3], const double wo[3], double alpha, double u1, double u2, double out[3]);
+double orc_vndf_pdf(const double n[3], const double wo[3], const double wi[3], double alpha);
+/* continuation sampling: lobe choice + direction; returns pdf of the full mixture */
+double orc_sample_continuation(const orc_scene* s, const double n[3], const double wo[3],
+                               const double albedo[3], double rough, double metal, int32_t kind,
+                               const uint32_t x[4], double out_dir[3]);
+double orc_pdf_continuation(const orc_scene* s, const double n[3], const double wo[3],
+                            const double albedo[3], double rough, double metal, int32_t kind,
+                            const double wi[3]);
+/* env sampling from four random words; returns direction pdf (solid angle), texel index */
+double orc_env_sample(const orc_scene* s, const uint32_t x[4], double out_dir[3], int32_t* out_texel);
+double orc_env_pdf(const orc_scene* s, const double dir[3]);
+int32_t orc_env_texel(const orc_scene* s, const double dir[3]);
+/* streaming WRS over m candidates with weights gamma and accept uniforms u:
+ * returns selected index (-1 none), writes w_sum */
+int32_t orc_wrs(const double* gamma, const double* u, int32_t m, double* w_sum);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
