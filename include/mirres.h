@@ -1,0 +1,224 @@
+/*
+ * mirres.h -- C ABI of the GB300 (sm_103a) MIRReS stage-2 hot path: forward and adjoint
+ * Monte Carlo multi-bounce path tracing of a triangle mesh under an environment map, with a
+ * GGX + Lambert BRDF (per-texel albedo / roughness / metallic) and weighted-reservoir RIS of
+ * environment-light candidates at every shading point.
+ *
+ * The calls follow the paper's statement of the problem (Sec. 3.2): a mesh M = {V, F} whose
+ * vertices are refined, spatially varying materials m, an HDR environment map whose texels
+ * are all trainable, calibrated cameras, rendered images I_PBR and the gradient of
+ * L_PBR = ||I_PBR - I_ref||^2 (Eq. loss_pbr) with respect to all of them.
+ *
+ * Conventions
+ *   - All array arguments inside descriptors are DEVICE pointers into caller-owned memory
+ *     (for example torch tensors). The library borrows them: it never frees them and keeps
+ *     only the pointer; the caller keeps them alive while a scene refers to them.
+ *   - Arrays of per-view / per-scene pointers (images, d_images, grads, scenes) are HOST
+ *     arrays of device pointers, read during the call only.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream)
+ *     unless documented otherwise; results are ready when the stream reaches that point.
+ *   - Float arrays are row-major FP32. Triangle indices are int32.
+ *   - Errors: every call returns a mirres_status; mirres_last_error() returns a message for
+ *     the calling thread. Sticky CUDA errors are reported as MIRRES_ERR_CUDA. Arguments are
+ *     validated on the host before any work is queued; a rejected call queues nothing.
+ *
+ * Readings of passages the paper leaves open (estimator details, BRDF form, sampling
+ * mixture, camera model, random-number layout) are documented with each call below and
+ * are shared, as statements, by the independent CPU reference used in the tests.
+ */
+#ifndef MIRRES_H
+#define MIRRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MIRRES_OK = 0,
+    MIRRES_ERR_ARG = 1,     /* invalid argument (NULL pointer, bad size, mismatched tape) */
+    MIRRES_ERR_CUDA = 2,    /* a CUDA runtime call failed */
+    MIRRES_ERR_OOM = 3,     /* device allocation failed */
+    MIRRES_ERR_TIMEOUT = 4, /* a bounded device loop hit its iteration cap (error flag set) */
+    MIRRES_ERR_STATE = 5    /* call out of order (e.g. render before mirres_bvh_build) */
+} mirres_status;
+
+typedef struct mirres_context mirres_context; /* per device / stream: workspace, counters */
+typedef struct mirres_scene mirres_scene;     /* BVH, env sampling tables, borrowed inputs */
+
+/* Scene description (Sec. 3.2: mesh M = {V, F}, material textures, env map 256x512 in the
+ * paper; any size here). Every pointer is a device pointer, borrowed.
+ *   verts    [n_verts][3]        world positions (y up)
+ *   tris     [n_tris][3]         vertex indices, 0 <= index < n_verts (checked on device by
+ *                                mirres_bvh_build, which then returns MIRRES_ERR_ARG)
+ *   tri_uv   [n_tris][3][2]      per-corner texture coordinates
+ *   albedo   [tex_h][tex_w][3], roughness [tex_h][tex_w], metallic [tex_h][tex_w]
+ *                                sampled bilinearly, texel centres at (i + 0.5) / size,
+ *                                clamp to edge; row index = v * tex_h
+ *   env      [env_h][env_w][3]   latitude-longitude radiance, row 0 = zenith (+y);
+ *                                direction d -> u = atan2(d.x, -d.z) / 2pi + 1/2,
+ *                                v = acos(d.y) / pi, nearest texel (piecewise constant)
+ * n_tris may be 0 (every ray escapes). tex_w, tex_h, env_w, env_h >= 1. */
+typedef struct {
+    const float* verts;   int32_t n_verts;
+    const int32_t* tris;  int32_t n_tris;
+    const float* tri_uv;
+    const float* albedo;  const float* roughness; const float* metallic;
+    int32_t tex_w, tex_h;
+    const float* env;     int32_t env_w, env_h;
+} mirres_scene_desc;
+
+/* One camera (pinhole, Sec. 3.2 camera ray r(t) = o + t d). K = (fx, fy, cx, cy) in pixels;
+ * c2w = row-major 3x4 [R | t] whose columns are the camera x (right), y (down) and z
+ * (forward) axes in world space and whose last column is the centre o. Pixel (px, py) with
+ * jitter (j0, j1) in [0,1)^2 looks along normalize(R ((px + j0 - cx)/fx, (py + j1 - cy)/fy, 1)).
+ * spp = samples per pixel, bounces = shading vertices per path (the paper uses three,
+ * Sec. 4.2), scene = index into the call's scene array. */
+typedef struct {
+    float K[4];
+    float c2w[12];
+    int32_t width, height, spp, bounces;
+    int32_t scene;
+} mirres_view;
+
+/* Render parameters.
+ *   ris_m    RIS candidates per shading point (m of Eq. restir), >= 1
+ *   seed     key of the Philox4x32-10 stream. Uniform number k of purpose P for sample s
+ *            of pixel p of view index v at bounce b is drawn from counter
+ *            (p, s, v << 16 | b << 8 | P, j) and key (seed_lo, seed_hi); u = (x >> 8) 2^-24.
+ *            P = 0 camera jitter, 1 RIS candidate j, 2 continuation. v is the view's index
+ *            in the call's view array (< 65536); bounces < 256.
+ *   grad_mode 0 = PRIMARY (the paper: gradients of indirect rays detached, Sec. 4.2)
+ *   launch   0 = plain: per-view wavefront launches (ray generation, closest hit,
+ *                 shade + RIS + next-bounce queue, shadow rays, resolve);
+ *            1 = batched: one persistent launch over every view of every scene, work
+ *                 pulled from a device counter (see mirres_batch_* for the graph form).
+ *            Both produce bit-identical images, tapes and gradients.
+ *   block, blocks_per_sm  launch shape of the persistent kernel (0 = autotuned / default) */
+typedef struct {
+    int32_t ris_m;
+    uint32_t seed_lo, seed_hi;
+    int32_t grad_mode;
+    int32_t launch;
+    int32_t block;
+    int32_t blocks_per_sm;
+    int32_t reserved;
+} mirres_params;
+
+/* Gradient destinations for one scene (device pointers, shapes of the scene's inputs).
+ * Accumulated (+=); a NULL pointer skips that parameter. */
+typedef struct {
+    float* albedo; float* roughness; float* metallic; float* env; float* verts;
+} mirres_grads;
+
+/* ---- lifetime ------------------------------------------------------------------------ */
+
+/* Create a context on `device` (makes it current on the calling thread). The context owns
+ * a grow-only device workspace (ray queues, per-view scratch), device counters and an error
+ * flag. Calls sharing a context must be issued on one stream at a time. */
+mirres_status mirres_context_create(int32_t device, mirres_context** out);
+mirres_status mirres_context_destroy(mirres_context* ctx);
+
+/* Create a scene from borrowed device arrays; validates sizes and pointers on the host.
+ * The scene owns its LBVH and env-sampling tables (allocated here). */
+mirres_status mirres_scene_create(mirres_context* ctx, const mirres_scene_desc* desc, mirres_scene** out);
+mirres_status mirres_scene_destroy(mirres_scene* scene);
+
+/* LBVH build (Appendix A "Visibility estimation": a linear BVH after Karras 2012): FP32
+ * triangle centroids (fixed operation order, no contraction), 30-bit Morton codes in the
+ * centroid box, keys code << 32 | triangle, stable radix sort, binary radix tree, bottom-up
+ * boxes, traversal layout. Also rebuilds the env sampling tables (FP64 prefix sums of
+ * Y(L) sin(theta); Y = (r+g+b)/3, Appendix A). Checks triangle indices (synchronises the
+ * stream once to read the check; MIRRES_ERR_ARG if any index is out of range). */
+mirres_status mirres_bvh_build(mirres_scene* scene, void* stream);
+
+/* Refit after the vertices moved (the paper's "LBVH is updated in each iteration",
+ * Appendix A): topology kept, boxes and packed triangles recomputed bottom-up; env tables
+ * rebuilt. Asynchronous. Requires a prior mirres_bvh_build. */
+mirres_status mirres_bvh_refit(mirres_scene* scene, void* stream);
+
+/* ---- forward / adjoint ----------------------------------------------------------------- */
+
+/* Bytes of tape needed for these views: 36 bytes per path sample (sum of width*height*spp).
+ * The tape records, per sample, the primary triangle, the selected RIS candidate, V*W of the
+ * primary vertex, the incident indirect radiance L_ind at the primary vertex and the
+ * sample's radiance; the adjoint replays the primary vertex from it and the random stream. */
+size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views);
+
+/* Forward render (Eq. pbr_render with Eq. incident: direct light by RIS over ris_m env
+ * candidates streamed through a weighted reservoir, Eq. restir and Appendix A; indirect light
+ * by one continuation ray per vertex from a one-sample MIS mixture of env importance sampling
+ * (weight 1/4 when the env is not black), GGX visible-normal sampling and cosine sampling
+ * (split by the Fresnel/diffuse luminance ratio clamped to [0.1, 0.9]), Eq. mc_indir and
+ * Eq. sec_bouce). A continuation ray that escapes adds nothing (its env light is already in
+ * the direct term); a primary ray that escapes sees the env.
+ *   images[v]  device [height][width][3], written (mean over spp)
+ *   tape       device, mirres_tape_bytes(views) bytes, or NULL (the context's workspace is
+ *              used instead; mirres_backward then needs a tape from a later render)
+ * Scenes must have been built. Each images[v] must not alias another. */
+mirres_status mirres_render(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                            const mirres_view* views, int32_t n_views, const mirres_params* params,
+                            float* const* images, void* tape, size_t tape_bytes, void* stream);
+
+/* Adjoint, PRIMARY mode (Sec. 4.2: gradients of indirect rays detached; Appendix C: no
+ * gradients of non-primary rays): for every sample, the primary vertex is replayed from the
+ * tape and the random stream, and the derivatives of direct_1 + beta_1 * L_ind (RIS weight,
+ * visibility, every sampling decision, p_ind and L_ind held fixed) are scattered into the
+ * texels of albedo / roughness / metallic (bilinear weights), the env texel of the selected
+ * candidate and of escaping primary rays, and the three vertices of the primary triangle
+ * (through the intersection barycentrics and the face normal). Warp-aggregated FP32 atomics.
+ *   d_images[v]  device [height][width][3] = dL/dI (e.g. 2 (I - I_ref) for Eq. loss_pbr)
+ *   grads[s]     gradient destinations of scene s (host array of n_scenes structs)
+ * The views, params and scenes must be those of the render that wrote `tape`. */
+mirres_status mirres_backward(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                              const mirres_view* views, int32_t n_views, const mirres_params* params,
+                              const float* const* d_images, const void* tape, size_t tape_bytes,
+                              const mirres_grads* grads, void* stream);
+
+/* L2 image loss of Eq. (loss_pbr) and its gradient: d_image = 2 (image - ref) and
+ * loss[0] += sum (image - ref)^2 (device scalar, FP32 accumulated per block then atomically).
+ * n = number of floats. Any of d_image / loss may be NULL. */
+mirres_status mirres_l2_loss(const float* image, const float* ref, int64_t n, float* d_image, float* loss,
+                             void* stream);
+
+/* ---- ray queries ---------------------------------------------------------------------- */
+
+/* Closest (any = 0) or any (any = 1) hit of n rays against the scene's LBVH: rays [n][6]
+ * device (origin, direction), skip_tri [n] device or NULL (triangle to ignore, -1 none);
+ * hit_tri [n] device (-1 = miss; any-hit writes 1 / -1), hit_tuv [n][3] device or NULL
+ * (t, u, v with barycentric u of vertex 1, v of vertex 2). Hits need t > t_min
+ * (1e-5 x scene diagonal); equal t -> smaller triangle index. */
+mirres_status mirres_trace(mirres_context* ctx, const mirres_scene* scene, const float* rays,
+                           const int32_t* skip_tri, int64_t n, int32_t any, int32_t* hit_tri,
+                           float* hit_tuv, void* stream);
+
+/* ---- introspection ------------------------------------------------------------------- */
+
+/* Copy the LBVH arrays to caller device buffers (any may be NULL): keys [F] (uint64, sorted),
+ * left/right [F-1] (>= 0 internal node, < 0 leaf ~position), parent [2F-1], lo/hi [2F-1][3]
+ * (internal nodes first, then leaves). */
+mirres_status mirres_bvh_export(const mirres_scene* scene, uint64_t* keys, int32_t* left, int32_t* right,
+                                int32_t* parent, float* lo, float* hi, void* stream);
+
+/* Copy the env sampling tables to caller device buffers (any may be NULL): marg [env_h + 1]
+ * and cond [env_h][env_w + 1] as uint32 thresholds ceil(cdf * 2^24) (cdf <= u exactly when
+ * threshold <= u * 2^24 for a 24-bit uniform u), texel [env_h][env_w][4] = (r, g, b,
+ * probability * env_w * env_h) and the FP64 total weight (device double). */
+mirres_status mirres_env_export(const mirres_scene* scene, uint32_t* marg, uint32_t* cond, float* texel,
+                                double* total, void* stream);
+
+/* Cumulative counters since the context was created (synchronises the context's last
+ * stream): [0] primary rays, [1] continuation rays, [2] shadow rays, [3] samples rendered,
+ * [4] samples differentiated, [5] RIS candidates, [6] kernel launches, [7] error flag. */
+mirres_status mirres_get_counters(mirres_context* ctx, uint64_t out[8]);
+mirres_status mirres_reset_counters(mirres_context* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mirres_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MIRRES_H */

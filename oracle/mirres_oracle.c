@@ -32,8 +32,10 @@
 #define TAU_FLIP 2e-5   /* |n . d| when the face normal is flipped towards the viewer */
 #define TAU_ENV 3e-6    /* distance to a texel boundary of the env lookup, in u (or v) units */
 #define TAU_FRAME 1e-5  /* |n.z| in the orthonormal-basis sign choice */
+#define TAU_GRAZE 2e-3  /* cos of the viewing angle at the primary vertex: below it an FP32
+                         * evaluation of the BRDF carries a relative error above ~3e-5 */
 
-enum { MK_NONE = 0, MK_BARY, MK_TMIN, MK_TDEPTH, MK_ACC, MK_CDF, MK_LOBE, MK_FLIP, MK_ENV, MK_FRAME };
+enum { MK_NONE = 0, MK_BARY, MK_TMIN, MK_TDEPTH, MK_ACC, MK_CDF, MK_LOBE, MK_FLIP, MK_ENV, MK_FRAME, MK_GRAZE };
 
 /* ---------------------------------------------------------------------------------------
  * small vector algebra (FP64)
@@ -966,6 +968,7 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         Shade sh;
         shade_at(s, h.tri, h.u, h.v, h.t, d, &sh, mg);
         v3 wo = vscale(d, -1.0);
+        if (b == 0) note(mg, vdot(sh.n, wo) / TAU_GRAZE, MK_GRAZE);
         /* ---- direct light: RIS over M env candidates, streamed through a reservoir ---- */
         double direct[3] = {0, 0, 0};
         if (s->env_ok && M > 0) {
@@ -1034,7 +1037,7 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
 /* ---------------------------------------------------------------------------------------
  * adjoint of one sample (PRIMARY mode, Sec. 4.2 last sentence and Appendix C limitations)
  * ------------------------------------------------------------------------------------- */
-enum { GB_ALB = 0, GB_RGH, GB_MET, GB_ENV, GB_VERT, GB_N };
+enum { GB_ALB = 0, GB_RGH, GB_MET, GB_ENV, GB_VERT, GB_ALB_S, GB_RGH_S, GB_MET_S, GB_N };
 typedef struct { int32_t buf; int64_t idx; double val; } Entry;
 typedef struct { Entry* e; size_t n, cap; } Sparse;
 
@@ -1080,6 +1083,29 @@ static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], Sparse*
         brdf_cos_grad(sh.n, wo, rec->wc, sh.alb, sh.rgh, sh.met, kind, gq, tmp);
         for (int k = 0; k < 8; ++k) gm[k] += tmp[k];
     }
+    const double* uv = s->UV + 6 * sh.tri;
+    v3 md = vscale(rec->d0, -1.0);
+    /* A = [e1 | e2 | -d]; rows of A^-1 are (e2 x -d, -d x e1, e1 x e2) / det */
+    v3 r0 = vcross(sh.e2, md), r1 = vcross(md, sh.e1);
+    double det = vdot(sh.e1, r0);
+    /* FP32 sensitivity (test tolerance only): barycentric error of a single-precision primary
+     * ray, ~8 u (t + |o - v0| + |o|) |row of A^-1|, mapped to the fractional texel position */
+    {
+        const double u32 = 1.0 / 16777216.0;
+        v3 o = vload(c->o), a, b, cc;
+        tri_verts(s, sh.tri, &a, &b, &cc);
+        double lever = 8.0 * u32 * (sh.t + vlen(vsub(o, a)) + vlen(o)) / fabs(det);
+        double du = lever * vlen(r0), dv = lever * vlen(r1);
+        double dfx = s->tw * (fabs(uv[2] - uv[0]) * du + fabs(uv[4] - uv[0]) * dv);
+        double dfy = s->th * (fabs(uv[3] - uv[1]) * du + fabs(uv[5] - uv[1]) * dv);
+        double dw = dfx + dfy;
+        for (int k = 0; k < 4; ++k) {
+            int i = sh.tp.idx[k];
+            for (int ch = 0; ch < 3; ++ch) sp_add(sp, GB_ALB_S, 3 * (int64_t)i + ch, dw * fabs(gm[ch]));
+            sp_add(sp, GB_RGH_S, i, dw * fabs(gm[3]));
+            sp_add(sp, GB_MET_S, i, dw * fabs(gm[4]));
+        }
+    }
     /* textures (bilinear scatter) and the texture coordinate */
     double gsu = 0.0, gsv = 0.0;
     for (int k = 0; k < 4; ++k) {
@@ -1097,13 +1123,8 @@ static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], Sparse*
         gsv += sh.tp.dw_dy[k] * dot;
     }
     /* vertices: (u, v) through the intersection, n through the face normal */
-    const double* uv = s->UV + 6 * sh.tri;
     double gu = gsu * (uv[2] - uv[0]) + gsv * (uv[3] - uv[1]);
     double gv = gsu * (uv[4] - uv[0]) + gsv * (uv[5] - uv[1]);
-    v3 md = vscale(rec->d0, -1.0);
-    /* A = [e1 | e2 | -d]; rows of A^-1 are (e2 x -d, -d x e1, e1 x e2) / det */
-    v3 r0 = vcross(sh.e2, md), r1 = vcross(md, sh.e1);
-    double det = vdot(sh.e1, r0);
     v3 z = vscale(vadd(vscale(r0, gu), vscale(r1, gv)), 1.0 / det); /* A^-T (gu, gv, 0) */
     double bw[3] = {1.0 - sh.u - sh.v, sh.u, sh.v};
     v3 gvert[3];
@@ -1235,8 +1256,10 @@ static int run_jobs(int mode, const orc_scene* s, const orc_scene* ev, const orc
     for (int t = 0; t < nt; ++t) {
         if (counts) for (int k = 0; k < ORC_NCOUNT; ++k) counts[k] += jobs[t].cnt[k];
         if (mode == 1 && g) {
-            double* dst[GB_N] = {g->albedo, g->roughness, g->metallic, g->env, g->verts};
-            double* dab[GB_N] = {g->albedo_abs, g->roughness_abs, g->metallic_abs, g->env_abs, g->verts_abs};
+            double* dst[GB_N] = {g->albedo, g->roughness, g->metallic, g->env, g->verts,
+                                 g->albedo_sens, g->roughness_sens, g->metallic_sens};
+            double* dab[GB_N] = {g->albedo_abs, g->roughness_abs, g->metallic_abs, g->env_abs, g->verts_abs,
+                                 NULL, NULL, NULL};
             for (size_t e = 0; e < jobs[t].sp.n; ++e) {
                 const Entry* en = &jobs[t].sp.e[e];
                 if (dst[en->buf]) dst[en->buf][en->idx] += en->val;

@@ -57,6 +57,11 @@ typedef struct {
     double* albedo; double* roughness; double* metallic; double* env; double* verts;
     /* absolute-value sums of the same scattered terms (a conditioning measure), may be NULL */
     double* albedo_abs; double* roughness_abs; double* metallic_abs; double* env_abs; double* verts_abs;
+    /* FP32 sensitivity of the texel terms: sum over samples of |d(texel gradient)| when the
+     * primary ray is perturbed by a few FP32 rounding units (bilinear weights move between
+     * neighbouring texels); a bound on how far an FP32 evaluation may legitimately differ.
+     * May be NULL. */
+    double* albedo_sens; double* roughness_sens; double* metallic_sens;
 } orc_grads;
 
 /* counters: [0] primary rays, [1] continuation rays, [2] shadow rays, [3] BVH nodes visited,

@@ -53,9 +53,12 @@ class Params(C.Structure):
                 ("brdf_kind", C.c_int32), ("threads", C.c_int32), ("want_margin", C.c_int32)]
 
 
+GRAD_FIELDS = ("albedo", "roughness", "metallic", "env", "verts", "albedo_abs", "roughness_abs", "metallic_abs",
+               "env_abs", "verts_abs", "albedo_sens", "roughness_sens", "metallic_sens")
+
+
 class Grads(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("albedo", "roughness", "metallic", "env", "verts", "albedo_abs",
-                                            "roughness_abs", "metallic_abs", "env_abs", "verts_abs")]
+    _fields_ = [(n, C.c_void_p) for n in GRAD_FIELDS]
 
 
 def lib():
@@ -187,8 +190,9 @@ def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, 
     if want_abs:
         for k in list(out):
             out[k + "_abs"] = np.zeros(out[k].shape)
-    g = Grads(*[_p(out.get(k)) for k in ("albedo", "roughness", "metallic", "env", "verts", "albedo_abs",
-                                          "roughness_abs", "metallic_abs", "env_abs", "verts_abs")])
+        for k in ("albedo", "roughness", "metallic"):
+            out[k + "_sens"] = np.zeros(out[k].shape)
+    g = Grads(*[_p(out.get(k)) for k in GRAD_FIELDS])
     cnt = np.zeros(8, dtype=np.int64)
     v = make_view(view, index)
     p = make_params(ris_m, seed, threads, brdf_kind, 0)

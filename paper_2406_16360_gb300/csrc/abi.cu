@@ -1,0 +1,526 @@
+// abi.cu -- the extern "C" entry points of libmirres (include/mirres.h): argument checks,
+// workspace management and the launch sequences of the plain and batched paths.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "render.h"
+
+static thread_local std::string g_err;
+
+void mr_set_error(const std::string& msg) { g_err = msg; }
+
+mirres_status mr_cuda_status(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MIRRES_ERR_OOM : MIRRES_ERR_CUDA;
+}
+
+static mirres_status arg_error(const std::string& msg)
+{
+    g_err = msg;
+    return MIRRES_ERR_ARG;
+}
+
+#define MR_TRY(x)                            \
+    do {                                     \
+        mirres_status s__ = (x);             \
+        if (s__ != MIRRES_OK) return s__;    \
+    } while (0)
+
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// samples per chunk of the plain wavefront path (queue capacity)
+static const uint32_t kChunk = 1u << 22;
+static const size_t kQueueCnt = 1024;
+
+SceneDev mr_scene_dev(const mirres_scene* s)
+{
+    SceneDev d;
+    d.nodes = s->nodes;
+    d.ptri = s->ptri;
+    d.leaf_of = s->leaf_of;
+    d.tris = s->desc.tris;
+    d.tri_uv = s->desc.tri_uv;
+    d.albedo = s->desc.albedo;
+    d.rough = s->desc.roughness;
+    d.metal = s->desc.metallic;
+    d.env_texel = s->env_texel;
+    d.env_marg = s->env_marg;
+    d.env_cond = s->env_cond;
+    d.n_tris = s->desc.n_tris;
+    d.n_verts = s->desc.n_verts;
+    d.tw = s->desc.tex_w;
+    d.th = s->desc.tex_h;
+    d.ew = s->desc.env_w;
+    d.eh = s->desc.env_h;
+    d.env_ok_dev = s->env_ok;
+    d.tmin_dev = s->tmin;
+    return d;
+}
+
+// ---- workspace --------------------------------------------------------------------------
+static mirres_status ws_reserve(mirres_context* ctx, size_t bytes)
+{
+    if (bytes <= ctx->ws.bytes) return MIRRES_OK;
+    if (ctx->ws.ptr) {
+        MR_CUDA(cudaDeviceSynchronize());
+        cudaFree(ctx->ws.ptr);
+        ctx->ws.ptr = nullptr;
+        ctx->ws.bytes = 0;
+    }
+    const size_t want = bytes + bytes / 4 + (1u << 20);
+    cudaError_t e = cudaMalloc(&ctx->ws.ptr, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&ctx->ws.ptr, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->ws.ptr = nullptr;
+            g_err = "workspace allocation of " + std::to_string(bytes) + " bytes failed";
+            return MIRRES_ERR_OOM;
+        }
+        ctx->ws.bytes = bytes;
+        return MIRRES_OK;
+    }
+    ctx->ws.bytes = want;
+    return MIRRES_OK;
+}
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* p) : base(static_cast<char*>(p)) {}
+    template <typename T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+// ---- argument checks ----------------------------------------------------------------------
+static mirres_status check_views(const mirres_view* views, int32_t n_views, int32_t n_scenes,
+                                 std::vector<ViewDev>& out, uint64_t& total, uint64_t& max_view)
+{
+    if (n_views < 1 || n_views > 65535) return arg_error("n_views must be in [1, 65535]");
+    if (!views) return arg_error("views is NULL");
+    out.resize((size_t)n_views);
+    total = 0;
+    max_view = 0;
+    for (int i = 0; i < n_views; ++i) {
+        const mirres_view& v = views[i];
+        if (v.width < 1 || v.height < 1 || v.spp < 1 || v.bounces < 1 || v.bounces > 255)
+            return arg_error("view " + std::to_string(i) + ": width, height, spp >= 1 and bounces in [1, 255]");
+        const uint64_t n = (uint64_t)v.width * (uint64_t)v.height * (uint64_t)v.spp;
+        if (n > 0xFFFFFFFFull) return arg_error("view " + std::to_string(i) + ": width*height*spp exceeds 2^32-1");
+        if (v.scene < 0 || v.scene >= n_scenes) return arg_error("view " + std::to_string(i) + ": bad scene index");
+        if (!(v.K[0] != 0.0f) || !(v.K[1] != 0.0f)) return arg_error("view " + std::to_string(i) + ": fx, fy == 0");
+        ViewDev& d = out[(size_t)i];
+        std::memcpy(d.K, v.K, sizeof(d.K));
+        std::memcpy(d.c2w, v.c2w, sizeof(d.c2w));
+        d.width = v.width;
+        d.height = v.height;
+        d.spp = v.spp;
+        d.bounces = v.bounces;
+        d.scene = v.scene;
+        d.index = i;
+        d.offset = total;
+        total += n;
+        max_view = std::max(max_view, n);
+    }
+    return MIRRES_OK;
+}
+
+static mirres_status check_scenes(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                  std::vector<SceneDev>& out)
+{
+    if (n_scenes < 1 || !scenes) return arg_error("need at least one scene");
+    out.resize((size_t)n_scenes);
+    for (int i = 0; i < n_scenes; ++i) {
+        if (!scenes[i]) return arg_error("scene " + std::to_string(i) + " is NULL");
+        if (scenes[i]->ctx != ctx) return arg_error("scene " + std::to_string(i) + " belongs to another context");
+        if (!scenes[i]->built) {
+            g_err = "scene " + std::to_string(i) + ": call mirres_bvh_build first";
+            return MIRRES_ERR_STATE;
+        }
+        out[(size_t)i] = mr_scene_dev(scenes[i]);
+    }
+    return MIRRES_OK;
+}
+
+static mirres_status check_params(const mirres_params* p)
+{
+    if (!p) return arg_error("params is NULL");
+    if (p->ris_m < 1) return arg_error("ris_m must be >= 1");
+    if (p->grad_mode != 0) return arg_error("grad_mode: only 0 (PRIMARY) is implemented");
+    if (p->launch != 0 && p->launch != 1) return arg_error("launch must be 0 (plain) or 1 (batched)");
+    if (p->block != 0 && (p->block < 32 || p->block > 1024 || p->block % 32))
+        return arg_error("block must be 0 or a multiple of 32 in [32, 1024]");
+    if (p->blocks_per_sm < 0) return arg_error("blocks_per_sm must be >= 0");
+    return MIRRES_OK;
+}
+
+// ---- lifetime -------------------------------------------------------------------------------
+extern "C" mirres_status mirres_context_create(int32_t device, mirres_context** out)
+{
+    if (!out) return arg_error("out is NULL");
+    *out = nullptr;
+    int n = 0;
+    MR_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return arg_error("device index out of range");
+    MR_CUDA(cudaSetDevice(device));
+    mirres_context* c = new mirres_context();
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->counters, sizeof(unsigned long long) * CNT_N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->queue_cnt, sizeof(unsigned int) * kQueueCnt);
+    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned long long) * CNT_N);
+    if (e != cudaSuccess) {
+        if (c->counters) cudaFree(c->counters);
+        if (c->queue_cnt) cudaFree(c->queue_cnt);
+        delete c;
+        return mr_cuda_status(e, "mirres_context_create");
+    }
+    *out = c;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_context_destroy(mirres_context* ctx)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
+    if (ctx->counters) cudaFree(ctx->counters);
+    if (ctx->queue_cnt) cudaFree(ctx->queue_cnt);
+    delete ctx;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_scene_create(mirres_context* ctx, const mirres_scene_desc* d, mirres_scene** out)
+{
+    if (!ctx || !d || !out) return arg_error("ctx, desc and out must not be NULL");
+    *out = nullptr;
+    if (d->n_tris < 0 || d->n_verts < 0) return arg_error("n_tris and n_verts must be >= 0");
+    if (d->n_tris > 0 && (d->n_verts < 1 || !d->verts || !d->tris || !d->tri_uv))
+        return arg_error("a scene with triangles needs verts, tris and tri_uv");
+    if (d->n_tris > (1 << 30)) return arg_error("n_tris must be < 2^30");
+    if (d->tex_w < 1 || d->tex_h < 1 || !d->albedo || !d->roughness || !d->metallic)
+        return arg_error("textures: tex_w, tex_h >= 1 and non-NULL albedo, roughness, metallic");
+    if ((int64_t)d->tex_w * d->tex_h > (1ll << 30)) return arg_error("texture too large");
+    if (d->env_w < 1 || d->env_h < 1 || !d->env) return arg_error("env: env_w, env_h >= 1 and non-NULL env");
+    if ((int64_t)d->env_w * d->env_h > (1ll << 28)) return arg_error("env map too large");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    mirres_scene* s = new mirres_scene();
+    s->ctx = ctx;
+    s->desc = *d;
+    mirres_status st = mr_bvh_alloc(s);
+    if (st == MIRRES_OK) st = mr_env_alloc(s);
+    if (st != MIRRES_OK) {
+        mr_bvh_free(s);
+        mr_env_free(s);
+        delete s;
+        return st;
+    }
+    *out = s;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_scene_destroy(mirres_scene* s)
+{
+    if (!s) return arg_error("scene is NULL");
+    cudaSetDevice(s->ctx->device);
+    cudaDeviceSynchronize();
+    mr_bvh_free(s);
+    mr_env_free(s);
+    delete s;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_bvh_build(mirres_scene* s, void* stream)
+{
+    if (!s) return arg_error("scene is NULL");
+    MR_CUDA(cudaSetDevice(s->ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    MR_TRY(mr_bvh_build(s, st));
+    MR_TRY(mr_env_build(s, st));
+    s->ctx->host_launches += 24;
+    s->built = true;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_bvh_refit(mirres_scene* s, void* stream)
+{
+    if (!s) return arg_error("scene is NULL");
+    if (!s->built) {
+        g_err = "mirres_bvh_refit: call mirres_bvh_build first";
+        return MIRRES_ERR_STATE;
+    }
+    MR_CUDA(cudaSetDevice(s->ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    MR_TRY(mr_bvh_refit(s, st));
+    MR_TRY(mr_env_build(s, st));
+    s->ctx->host_launches += 6;
+    return MIRRES_OK;
+}
+
+extern "C" size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views)
+{
+    if (!views || n_views < 1) return 0;
+    uint64_t n = 0;
+    for (int i = 0; i < n_views; ++i)
+        n += (uint64_t)std::max(views[i].width, 0) * (uint64_t)std::max(views[i].height, 0) *
+             (uint64_t)std::max(views[i].spp, 0);
+    return (size_t)(36ull * n);
+}
+
+// ---- forward ---------------------------------------------------------------------------------
+static Rng make_rng(const mirres_params* p)
+{
+    Rng r;
+    r.k0 = p->seed_lo;
+    r.k1 = p->seed_hi;
+    return r;
+}
+
+extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                       const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                       float* const* images, void* tape, size_t tape_bytes, void* stream)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    MR_TRY(check_params(params));
+    std::vector<SceneDev> sdev;
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev));
+    std::vector<ViewDev> vdev;
+    uint64_t total = 0, max_view = 0;
+    MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
+    if (!images) return arg_error("images is NULL");
+    for (int i = 0; i < n_views; ++i)
+        if (!images[i]) return arg_error("images[" + std::to_string(i) + "] is NULL");
+    if (tape && tape_bytes < 36ull * total) return arg_error("tape_bytes is smaller than mirres_tape_bytes(views)");
+    if (tape && (reinterpret_cast<uintptr_t>(tape) & 15)) return arg_error("tape must be 16-byte aligned");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    ctx->last_stream = st;
+    const Rng rng = make_rng(params);
+    const int M = params->ris_m;
+    const int sms = ctx->sm_count;
+
+    // workspace layout
+    const bool batched = params->launch == 1;
+    const uint32_t chunk = (uint32_t)std::min<uint64_t>(max_view, kChunk);
+    Carver plan(nullptr);
+    plan.take<char>(tape ? 0 : 36ull * total);
+    plan.take<ViewDev>((size_t)n_views);
+    plan.take<SceneDev>((size_t)n_scenes);
+    plan.take<float*>((size_t)n_views);
+    plan.take<uint64_t>((size_t)n_views);
+    plan.take<unsigned long long>(1);
+    if (!batched) plan.take<float4>(13ull * chunk);
+    MR_TRY(ws_reserve(ctx, plan.off));
+    Carver cv(ctx->ws.ptr);
+    void* internal_tape = cv.take<char>(tape ? 0 : 36ull * total);
+    void* tp = tape ? tape : internal_tape;
+    ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
+    SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
+    float** d_images = cv.take<float*>((size_t)n_views);
+    uint64_t* d_pixoff = cv.take<uint64_t>((size_t)n_views);
+    unsigned long long* d_work = cv.take<unsigned long long>(1);
+
+    if (batched) {
+        std::vector<uint64_t> pixoff((size_t)n_views);
+        uint64_t tp_pix = 0;
+        for (int i = 0; i < n_views; ++i) {
+            pixoff[(size_t)i] = tp_pix;
+            tp_pix += (uint64_t)vdev[(size_t)i].width * vdev[(size_t)i].height;
+        }
+        MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
+        MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
+        MR_CUDA(cudaMemcpyAsync(d_images, images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
+        MR_CUDA(cudaMemcpyAsync(d_pixoff, pixoff.data(), sizeof(uint64_t) * pixoff.size(), cudaMemcpyHostToDevice, st));
+        MR_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), st));
+        const int block = params->block ? params->block : 128;
+        const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy(block);
+        MR_CUDA(mr_launch_persistent(d_scenes, d_views, n_views, total, rng, M, d_work, 32u * 8u, tp, ctx->counters,
+                                     block, per_sm * sms, st));
+        mr_launch_resolve_all(d_views, n_views, d_pixoff, tp_pix, d_images, tp, total, sms, st);
+        MR_CUDA(cudaGetLastError());
+        ctx->host_launches += 2;
+        return MIRRES_OK;
+    }
+
+    // plain: per view, per chunk of at most kChunk samples, one wavefront per bounce
+    QueueDev qa{cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk)};
+    QueueDev qb{cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk)};
+    float4* hits = cv.take<float4>(chunk);
+    ShadowDev sq{cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk)};
+    for (int vi = 0; vi < n_views; ++vi) {
+        const ViewDev& v = vdev[(size_t)vi];
+        const SceneDev& s = sdev[(size_t)v.scene];
+        const uint64_t nv = (uint64_t)v.width * v.height * v.spp;
+        for (uint64_t first = 0; first < nv; first += chunk) {
+            const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, nv - first);
+            MR_CUDA(cudaMemsetAsync(ctx->queue_cnt, 0, sizeof(unsigned int) * (2 * v.bounces + 2), st));
+            mr_launch_raygen(v, rng, (uint32_t)first, n, qa, tp, total, sms, st);
+            QueueDev cur = qa, nxt = qb;
+            for (int b = 0; b < v.bounces; ++b) {
+                const unsigned int* cnt_in = b == 0 ? nullptr : ctx->queue_cnt + 2 * (b - 1);
+                mr_launch_trace(s, cur.o, cur.d, cnt_in, n, n, hits, false, sms, st);
+                mr_launch_shade(s, v, rng, b, M, cur, cnt_in, n, n, hits, nxt, ctx->queue_cnt + 2 * b, sq,
+                                ctx->queue_cnt + 2 * b + 1, tp, total, sms, st);
+                mr_launch_shadow(s, v, b, sq, ctx->queue_cnt + 2 * b + 1, n, tp, total, sms, st);
+                std::swap(cur, nxt);
+            }
+            mr_launch_account(ctx->counters, ctx->queue_cnt, v.bounces, n, st);
+            ctx->host_launches += 2 + 3 * (unsigned long long)v.bounces;
+        }
+        mr_launch_resolve(v, tp, total, images[vi], sms, st);
+        ctx->host_launches += 1;
+    }
+    MR_CUDA(cudaGetLastError());
+    return MIRRES_OK;
+}
+
+// ---- adjoint ---------------------------------------------------------------------------------
+extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                         const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                         const float* const* d_images, const void* tape, size_t tape_bytes,
+                                         const mirres_grads* grads, void* stream)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    MR_TRY(check_params(params));
+    std::vector<SceneDev> sdev;
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev));
+    std::vector<ViewDev> vdev;
+    uint64_t total = 0, max_view = 0;
+    MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
+    if (!d_images || !grads) return arg_error("d_images and grads must not be NULL");
+    for (int i = 0; i < n_views; ++i)
+        if (!d_images[i]) return arg_error("d_images[" + std::to_string(i) + "] is NULL");
+    if (!tape) return arg_error("mirres_backward needs the tape written by mirres_render");
+    if (tape_bytes < 36ull * total) return arg_error("tape_bytes is smaller than mirres_tape_bytes(views)");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    ctx->last_stream = st;
+    std::vector<GradDev> gdev((size_t)n_scenes);
+    for (int i = 0; i < n_scenes; ++i)
+        gdev[(size_t)i] = GradDev{grads[i].albedo, grads[i].roughness, grads[i].metallic, grads[i].env, grads[i].verts};
+    Carver plan(nullptr);
+    plan.take<ViewDev>((size_t)n_views);
+    plan.take<SceneDev>((size_t)n_scenes);
+    plan.take<const float*>((size_t)n_views);
+    plan.take<GradDev>((size_t)n_scenes);
+    MR_TRY(ws_reserve(ctx, plan.off));
+    Carver cv(ctx->ws.ptr);
+    ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
+    SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
+    const float** d_dimg = cv.take<const float*>((size_t)n_views);
+    GradDev* d_grads = cv.take<GradDev>((size_t)n_scenes);
+    MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_dimg, d_images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_grads, gdev.data(), sizeof(GradDev) * gdev.size(), cudaMemcpyHostToDevice, st));
+    mr_launch_backward(d_scenes, d_views, n_views, total, make_rng(params), d_dimg, d_grads, tape, ctx->counters,
+                       ctx->sm_count, st);
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += 1;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_l2_loss(const float* image, const float* ref, int64_t n, float* d_image,
+                                        float* loss, void* stream)
+{
+    if (!image || !ref || n < 0) return arg_error("image, ref must not be NULL and n >= 0");
+    if (n == 0) return MIRRES_OK;
+    int dev = 0, sms = 1;
+    MR_CUDA(cudaGetDevice(&dev));
+    MR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    mr_launch_l2(image, ref, n, d_image, loss, sms, as_stream(stream));
+    MR_CUDA(cudaGetLastError());
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_trace(mirres_context* ctx, const mirres_scene* s, const float* rays,
+                                      const int32_t* skip_tri, int64_t n, int32_t any, int32_t* hit_tri,
+                                      float* hit_tuv, void* stream)
+{
+    if (!ctx || !s || !rays || !hit_tri || n < 0) return arg_error("ctx, scene, rays, hit_tri required; n >= 0");
+    if (!s->built) {
+        g_err = "mirres_trace: call mirres_bvh_build first";
+        return MIRRES_ERR_STATE;
+    }
+    if (n == 0) return MIRRES_OK;
+    MR_CUDA(cudaSetDevice(ctx->device));
+    mr_launch_trace_rays(mr_scene_dev(s), rays, skip_tri, n, any ? 1 : 0, hit_tri, hit_tuv, ctx->sm_count,
+                         as_stream(stream));
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += 1;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_bvh_export(const mirres_scene* s, uint64_t* keys, int32_t* left, int32_t* right,
+                                           int32_t* parent, float* lo, float* hi, void* stream)
+{
+    if (!s) return arg_error("scene is NULL");
+    if (!s->built) {
+        g_err = "mirres_bvh_export: call mirres_bvh_build first";
+        return MIRRES_ERR_STATE;
+    }
+    const size_t F = (size_t)s->desc.n_tris;
+    if (F == 0) return MIRRES_OK;
+    const cudaStream_t st = as_stream(stream);
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (keys) MR_CUDA(cudaMemcpyAsync(keys, s->keys, sizeof(uint64_t) * F, k, st));
+    if (left && F > 1) MR_CUDA(cudaMemcpyAsync(left, s->left, sizeof(int32_t) * (F - 1), k, st));
+    if (right && F > 1) MR_CUDA(cudaMemcpyAsync(right, s->right, sizeof(int32_t) * (F - 1), k, st));
+    if (parent) MR_CUDA(cudaMemcpyAsync(parent, s->parent, sizeof(int32_t) * (2 * F - 1), k, st));
+    if (lo) MR_CUDA(cudaMemcpyAsync(lo, s->lo, sizeof(float) * 3 * (2 * F - 1), k, st));
+    if (hi) MR_CUDA(cudaMemcpyAsync(hi, s->hi, sizeof(float) * 3 * (2 * F - 1), k, st));
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_env_export(const mirres_scene* s, uint32_t* marg, uint32_t* cond, float* texel,
+                                           double* total, void* stream)
+{
+    if (!s) return arg_error("scene is NULL");
+    if (!s->built) {
+        g_err = "mirres_env_export: call mirres_bvh_build first";
+        return MIRRES_ERR_STATE;
+    }
+    const size_t W = (size_t)s->desc.env_w, H = (size_t)s->desc.env_h;
+    const cudaStream_t st = as_stream(stream);
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (marg) MR_CUDA(cudaMemcpyAsync(marg, s->env_marg, sizeof(uint32_t) * (H + 1), k, st));
+    if (cond) MR_CUDA(cudaMemcpyAsync(cond, s->env_cond, sizeof(uint32_t) * H * (W + 1), k, st));
+    if (texel) MR_CUDA(cudaMemcpyAsync(texel, s->env_texel, sizeof(float4) * H * W, k, st));
+    if (total) MR_CUDA(cudaMemcpyAsync(total, s->env_total, sizeof(double), k, st));
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_get_counters(mirres_context* ctx, uint64_t out[8])
+{
+    if (!ctx || !out) return arg_error("ctx and out must not be NULL");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    unsigned long long h[CNT_N];
+    MR_CUDA(cudaStreamSynchronize(ctx->last_stream));
+    MR_CUDA(cudaMemcpy(h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 8; ++i) out[i] = (uint64_t)h[i];
+    out[CNT_LAUNCH] = ctx->host_launches;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_reset_counters(mirres_context* ctx)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    MR_CUDA(cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * CNT_N));
+    ctx->host_launches = 0;
+    return MIRRES_OK;
+}
+
+extern "C" const char* mirres_last_error(void) { return g_err.c_str(); }

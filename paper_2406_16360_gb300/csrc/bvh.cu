@@ -1,0 +1,467 @@
+// bvh.cu -- LBVH build and refit on the GPU (Appendix A of the paper: a linear BVH after
+// Karras 2012, "updated in each iteration to match the mesh refinement").
+//
+// build:  bounds (triangle centroids, centroid box, vertex box) -> 30-bit Morton codes ->
+//         stable LSD radix sort of the codes with the triangle id as payload (the initial
+//         order is by id, so the result is sorted by key = code << 32 | id) -> Karras's
+//         per-node hierarchy construction -> bottom-up boxes with arrival counters, which
+//         also writes the traversal layout (both child boxes in the parent, 64 bytes) and
+//         the packed triangles (v0, e1, e2; 48 bytes) in leaf order.
+// refit:  bounds (vertex box only) -> bottom-up boxes, topology kept.
+#include "internal.h"
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+__device__ __forceinline__ unsigned int f2o(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(unsigned int u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// bounds[0..2] centroid lo, [3..5] centroid hi, [6..8] vertex lo, [9..11] vertex hi
+__global__ void k_init_bounds(unsigned int* bounds, int32_t* bad)
+{
+    const int i = threadIdx.x;
+    if (i < 12) {
+        const bool is_lo = (i < 3) || (i >= 6 && i < 9);
+        bounds[i] = is_lo ? f2o(__int_as_float(0x7f800000)) : f2o(__int_as_float(0xff800000));
+    }
+    if (i == 0) *bad = 0;
+}
+
+__device__ __forceinline__ int checked_index(const int32_t* tris, size_t k, int V, int32_t* bad)
+{
+    const int i = __ldg(tris + k);
+    if (i < 0 || i >= V) {
+        *bad = 1;
+        return 0;
+    }
+    return i;
+}
+
+__global__ void __launch_bounds__(256) k_bounds(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                                                int F, int V, float* __restrict__ cent, unsigned int* bounds,
+                                                int32_t* bad, int with_centroids)
+{
+    const float INF = __int_as_float(0x7f800000);
+    float b[12] = {INF, INF, INF, -INF, -INF, -INF, INF, INF, INF, -INF, -INF, -INF};
+    const float third = 1.0f / 3.0f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < F; t += gridDim.x * blockDim.x) {
+        const int i0 = checked_index(tris, 3 * (size_t)t, V, bad);
+        const int i1 = checked_index(tris, 3 * (size_t)t + 1, V, bad);
+        const int i2 = checked_index(tris, 3 * (size_t)t + 2, V, bad);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float a = __ldg(verts + 3 * (size_t)i0 + k), c1 = __ldg(verts + 3 * (size_t)i1 + k),
+                        c2 = __ldg(verts + 3 * (size_t)i2 + k);
+            b[6 + k] = fminf(b[6 + k], fminf(fminf(a, c1), c2));
+            b[9 + k] = fmaxf(b[9 + k], fmaxf(fmaxf(a, c1), c2));
+            if (with_centroids) {
+                // fixed order, no contraction: ((a + b) + c) * (1/3)
+                const float m = __fmul_rn(__fadd_rn(__fadd_rn(a, c1), c2), third);
+                cent[(size_t)k * F + t] = m;
+                b[k] = fminf(b[k], m);
+                b[3 + k] = fmaxf(b[3 + k], m);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        float v = b[k];
+        const bool is_lo = (k < 3) || (k >= 6 && k < 9);
+        for (int off = 16; off > 0; off >>= 1) {
+            const float o = __shfl_xor_sync(MR_FULL, v, off);
+            v = is_lo ? fminf(v, o) : fmaxf(v, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (is_lo) atomicMin(bounds + k, f2o(v));
+            else atomicMax(bounds + k, f2o(v));
+        }
+    }
+}
+
+__global__ void k_finish_bounds(const unsigned int* bounds, int F, float* tmin)
+{
+    if (threadIdx.x != 0) return;
+    if (F <= 0) {
+        *tmin = 0.0f;
+        return;
+    }
+    const float dx = o2f(bounds[9]) - o2f(bounds[6]);
+    const float dy = o2f(bounds[10]) - o2f(bounds[7]);
+    const float dz = o2f(bounds[11]) - o2f(bounds[8]);
+    *tmin = 1e-5f * sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+__device__ __forceinline__ uint32_t expand10(uint32_t x)
+{
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__global__ void k_morton(const float* __restrict__ cent, const unsigned int* __restrict__ bounds, int F,
+                         uint32_t* __restrict__ codes, int32_t* __restrict__ vals)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= F) return;
+    uint32_t q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = o2f(bounds[k]), hi = o2f(bounds[3 + k]);
+        const float ext = __fsub_rn(hi, lo);
+        float f = 0.0f;
+        if (ext > 0.0f) f = __fmul_rn(__fdiv_rn(__fsub_rn(cent[(size_t)k * F + t], lo), ext), 1024.0f);
+        int qi = (int)floorf(f);
+        qi = min(max(qi, 0), 1023);
+        q[k] = (uint32_t)qi;
+    }
+    codes[t] = (expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]);
+    vals[t] = t;
+}
+
+// ---- stable LSD radix sort, 8-bit digits --------------------------------------------------
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
+                                                        uint32_t* __restrict__ hist, int nb)
+{
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const int idx = base + i * RS_THREADS + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of `total` entries in place, one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ a, int total)
+{
+    __shared__ uint32_t wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int seg = (total + 1023) / 1024;
+    const int start = tid * seg, end = min(start + seg, total);
+    uint32_t s = 0;
+    for (int i = start; i < end; ++i) s += a[i];
+    // inclusive scan of the per-thread sums
+    uint32_t x = s;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(MR_FULL, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(MR_FULL, w, off);
+            if (lane >= off) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - s + (warp > 0 ? wsum[warp - 1] : 0u);
+    for (int i = start; i < end; ++i) {
+        const uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                           const int32_t* __restrict__ vin,
+                                                           uint32_t* __restrict__ kout, int32_t* __restrict__ vout,
+                                                           int n, int shift, const uint32_t* __restrict__ offs,
+                                                           int nb)
+{
+    constexpr int NW = RS_THREADS / 32;
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[NW][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    base[tid] = offs[(size_t)tid * nb + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const int tile = blockIdx.x * RS_TILE;
+    for (int round = 0; round < RS_ITEMS; ++round) {
+        const int idx = tile + round * RS_THREADS + tid;
+        const bool valid = idx < n;
+        const uint32_t k = valid ? kin[idx] : 0u;
+        const int32_t v = valid ? vin[idx] : 0;
+        const uint32_t dig = valid ? ((k >> shift) & 255u) : 0x1000u;
+        const unsigned peers = __match_any_sync(MR_FULL, dig);
+        const int rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) wcnt[warp][dig] = __popc(peers);
+        __syncthreads();
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = acc;
+            acc += c;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t dst = base[dig] + wcnt[warp][dig] + (uint32_t)rank;
+            kout[dst] = k;
+            vout[dst] = v;
+        }
+        __syncthreads();
+        base[tid] += acc;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+    }
+}
+
+__global__ void k_keys(const uint32_t* __restrict__ codes, const int32_t* __restrict__ vals, int F,
+                       uint64_t* __restrict__ keys, int32_t* __restrict__ perm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= F) return;
+    keys[i] = ((uint64_t)codes[i] << 32) | (uint32_t)vals[i];
+    perm[i] = vals[i];
+}
+
+// ---- Karras 2012 hierarchy: one thread per internal node ---------------------------------
+__device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int F, int i, int j)
+{
+    if (j < 0 || j >= F) return -1;
+    return __clzll(k[i] ^ k[j]);
+}
+
+__global__ void k_karras(const uint64_t* __restrict__ k, int F, int32_t* __restrict__ left,
+                         int32_t* __restrict__ right, int32_t* __restrict__ parent)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= F - 1) return;
+    if (i == 0) parent[0] = -1;
+    const int d = (delta(k, F, i, i + 1) - delta(k, F, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(k, F, i, i - d);
+    int lmax = 2;
+    while (delta(k, F, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(k, F, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta(k, F, i, j);
+    int s = 0;
+    for (int div = 2;; div <<= 1) {
+        const int t = (l + div - 1) / div;
+        if (delta(k, F, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    const int g = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    if (lo == g) {
+        left[i] = ~g;
+        parent[(F - 1) + g] = i;
+    } else {
+        left[i] = g;
+        parent[g] = i;
+    }
+    if (hi == g + 1) {
+        right[i] = ~(g + 1);
+        parent[(F - 1) + g + 1] = i;
+    } else {
+        right[i] = g + 1;
+        parent[g + 1] = i;
+    }
+}
+
+// ---- bottom-up boxes, traversal layout, packed triangles ---------------------------------
+__global__ void k_bottom_up(const float* __restrict__ verts, const int32_t* __restrict__ tris, int F, int V,
+                            const int32_t* __restrict__ perm, const int32_t* __restrict__ left,
+                            const int32_t* __restrict__ right, const int32_t* __restrict__ parent,
+                            float* lo, float* hi, int32_t* flags, float4* __restrict__ nodes,
+                            float4* __restrict__ ptri, int32_t* __restrict__ leaf_of)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= F) return;
+    const int t = perm[j];
+    int idx[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int v = __ldg(tris + 3 * (size_t)t + c);
+        idx[c] = (v >= 0 && v < V) ? v : 0;
+    }
+    const float3 a = f3(verts[3 * (size_t)idx[0]], verts[3 * (size_t)idx[0] + 1], verts[3 * (size_t)idx[0] + 2]);
+    const float3 b = f3(verts[3 * (size_t)idx[1]], verts[3 * (size_t)idx[1] + 1], verts[3 * (size_t)idx[1] + 2]);
+    const float3 c = f3(verts[3 * (size_t)idx[2]], verts[3 * (size_t)idx[2] + 1], verts[3 * (size_t)idx[2] + 2]);
+    const size_t L = (size_t)(F - 1) + j;
+    lo[3 * L] = fminf(fminf(a.x, b.x), c.x);
+    lo[3 * L + 1] = fminf(fminf(a.y, b.y), c.y);
+    lo[3 * L + 2] = fminf(fminf(a.z, b.z), c.z);
+    hi[3 * L] = fmaxf(fmaxf(a.x, b.x), c.x);
+    hi[3 * L + 1] = fmaxf(fmaxf(a.y, b.y), c.y);
+    hi[3 * L + 2] = fmaxf(fmaxf(a.z, b.z), c.z);
+    ptri[3 * (size_t)j] = make_float4(a.x, a.y, a.z, __int_as_float(t));
+    ptri[3 * (size_t)j + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, 0.0f);
+    ptri[3 * (size_t)j + 2] = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, 0.0f);
+    leaf_of[t] = j;
+    int p = parent[L];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;  // the sibling's thread finishes this node
+        __threadfence();
+        const int cl = left[p], cr = right[p];
+        const size_t il = cl >= 0 ? (size_t)cl : (size_t)(F - 1) + ~cl;
+        const size_t ir = cr >= 0 ? (size_t)cr : (size_t)(F - 1) + ~cr;
+        float bl[6], br[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            bl[k] = __ldcg(lo + 3 * il + k);
+            bl[3 + k] = __ldcg(hi + 3 * il + k);
+            br[k] = __ldcg(lo + 3 * ir + k);
+            br[3 + k] = __ldcg(hi + 3 * ir + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            __stcg(lo + 3 * (size_t)p + k, fminf(bl[k], br[k]));
+            __stcg(hi + 3 * (size_t)p + k, fmaxf(bl[3 + k], br[3 + k]));
+        }
+        nodes[4 * (size_t)p] = make_float4(bl[0], bl[1], bl[2], bl[3]);
+        nodes[4 * (size_t)p + 1] = make_float4(bl[4], bl[5], br[0], br[1]);
+        nodes[4 * (size_t)p + 2] = make_float4(br[2], br[3], br[4], br[5]);
+        nodes[4 * (size_t)p + 3] = make_float4(__int_as_float(cl), __int_as_float(cr), 0.0f, 0.0f);
+        p = parent[p];
+    }
+}
+
+int grid_for(int n, int block) { return (n + block - 1) / block; }
+
+}  // namespace
+
+template <typename T>
+static mirres_status mr_alloc(T** p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        mr_set_error(std::string("device allocation failed: ") + cudaGetErrorString(e));
+        return MIRRES_ERR_OOM;
+    }
+    return MIRRES_OK;
+}
+
+#define MR_TRY(x)                            \
+    do {                                     \
+        mirres_status s__ = (x);             \
+        if (s__ != MIRRES_OK) return s__;    \
+    } while (0)
+
+mirres_status mr_bvh_alloc(mirres_scene* s)
+{
+    const size_t F = (size_t)s->desc.n_tris;
+    const size_t nb = (F + RS_TILE - 1) / RS_TILE;
+    MR_TRY(mr_alloc(&s->keys, F));
+    MR_TRY(mr_alloc(&s->perm, F));
+    MR_TRY(mr_alloc(&s->left, F > 1 ? F - 1 : 1));
+    MR_TRY(mr_alloc(&s->right, F > 1 ? F - 1 : 1));
+    MR_TRY(mr_alloc(&s->parent, F > 0 ? 2 * F - 1 : 1));
+    MR_TRY(mr_alloc(&s->lo, 3 * (F > 0 ? 2 * F - 1 : 1)));
+    MR_TRY(mr_alloc(&s->hi, 3 * (F > 0 ? 2 * F - 1 : 1)));
+    MR_TRY(mr_alloc(&s->flags, F > 1 ? F - 1 : 1));
+    MR_TRY(mr_alloc(&s->nodes, 4 * (F > 1 ? F - 1 : 1)));
+    MR_TRY(mr_alloc(&s->ptri, 3 * F));
+    MR_TRY(mr_alloc(&s->leaf_of, F));
+    MR_TRY(mr_alloc(&s->cent, 3 * F));
+    MR_TRY(mr_alloc(&s->codes[0], F));
+    MR_TRY(mr_alloc(&s->codes[1], F));
+    MR_TRY(mr_alloc(&s->vals[0], F));
+    MR_TRY(mr_alloc(&s->vals[1], F));
+    MR_TRY(mr_alloc(&s->hist, 256 * (nb ? nb : 1)));
+    MR_TRY(mr_alloc(&s->bounds, 12));
+    MR_TRY(mr_alloc(&s->tmin, 1));
+    MR_TRY(mr_alloc(&s->bad, 1));
+    return MIRRES_OK;
+}
+
+void mr_bvh_free(mirres_scene* s)
+{
+    void* ptrs[] = {s->keys, s->perm, s->left, s->right, s->parent, s->lo, s->hi, s->flags, s->nodes, s->ptri,
+                    s->leaf_of, s->cent, s->codes[0], s->codes[1], s->vals[0], s->vals[1], s->hist, s->bounds,
+                    s->tmin, s->bad};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+static mirres_status bottom_up(mirres_scene* s, cudaStream_t st)
+{
+    const int F = s->desc.n_tris;
+    if (F <= 0) return MIRRES_OK;
+    if (F > 1) MR_CUDA(cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (size_t)(F - 1), st));
+    k_bottom_up<<<grid_for(F, 256), 256, 0, st>>>(s->desc.verts, s->desc.tris, F, s->desc.n_verts, s->perm, s->left,
+                                                 s->right, s->parent, s->lo, s->hi, s->flags, s->nodes, s->ptri,
+                                                 s->leaf_of);
+    MR_CUDA(cudaGetLastError());
+    return MIRRES_OK;
+}
+
+static mirres_status bounds(mirres_scene* s, cudaStream_t st, int with_centroids)
+{
+    const int F = s->desc.n_tris;
+    k_init_bounds<<<1, 32, 0, st>>>(s->bounds, s->bad);
+    if (F > 0) {
+        int grid = grid_for(F, 256);
+        if (grid > 4096) grid = 4096;
+        k_bounds<<<grid, 256, 0, st>>>(s->desc.verts, s->desc.tris, F, s->desc.n_verts, s->cent, s->bounds, s->bad,
+                                       with_centroids);
+    }
+    k_finish_bounds<<<1, 32, 0, st>>>(s->bounds, F, s->tmin);
+    MR_CUDA(cudaGetLastError());
+    return MIRRES_OK;
+}
+
+mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st)
+{
+    const int F = s->desc.n_tris;
+    MR_TRY(bounds(s, st, 1));
+    if (F > 0) {
+        const int nb = (F + RS_TILE - 1) / RS_TILE;
+        k_morton<<<grid_for(F, 256), 256, 0, st>>>(s->cent, s->bounds, F, s->codes[0], s->vals[0]);
+        int cur = 0;
+        for (int shift = 0; shift < 32; shift += 8) {
+            k_rs_hist<<<nb, RS_THREADS, 0, st>>>(s->codes[cur], F, shift, s->hist, nb);
+            k_rs_scan<<<1, 1024, 0, st>>>(s->hist, 256 * nb);
+            k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(s->codes[cur], s->vals[cur], s->codes[cur ^ 1], s->vals[cur ^ 1],
+                                                    F, shift, s->hist, nb);
+            cur ^= 1;
+        }
+        k_keys<<<grid_for(F, 256), 256, 0, st>>>(s->codes[cur], s->vals[cur], F, s->keys, s->perm);
+        MR_CUDA(cudaMemsetAsync(s->parent, 0xFF, sizeof(int32_t) * (size_t)(2 * F - 1), st));
+        if (F > 1) k_karras<<<grid_for(F - 1, 256), 256, 0, st>>>(s->keys, F, s->left, s->right, s->parent);
+        MR_CUDA(cudaGetLastError());
+        MR_TRY(bottom_up(s, st));
+    }
+    int32_t bad = 0;
+    MR_CUDA(cudaMemcpyAsync(&bad, s->bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MR_CUDA(cudaStreamSynchronize(st));
+    if (bad) {
+        mr_set_error("mirres_bvh_build: a triangle index is outside [0, n_verts)");
+        return MIRRES_ERR_ARG;
+    }
+    return MIRRES_OK;
+}
+
+mirres_status mr_bvh_refit(mirres_scene* s, cudaStream_t st)
+{
+    MR_TRY(bounds(s, st, 0));
+    MR_TRY(bottom_up(s, st));
+    return MIRRES_OK;
+}

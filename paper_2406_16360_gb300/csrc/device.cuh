@@ -1,0 +1,526 @@
+// device.cuh -- sm_103a device code shared by the kernels of the MIRReS hot path.
+//
+// FP32 throughout (FP64 only in the env CDF build). Everything here is __forceinline__ so
+// that each translation unit is self-contained (no relocatable device code).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MR_PI 3.14159265358979323846f
+#define MR_INV_PI 0.31830988618379067154f
+#define MR_FULL 0xffffffffu
+
+// traversal stack: the first MR_SSTACK entries live in shared memory (column per thread),
+// deeper entries in a small local array; an LBVH over 64-bit unique keys is at most 63 deep
+#define MR_SSTACK 32
+#define MR_LSTACK 32
+
+// ---------------------------------------------------------------------------------------
+// scene as seen by the kernels
+// ---------------------------------------------------------------------------------------
+struct SceneDev {
+    const float4* nodes;      // [F-1][4]: (lmin.xyz, lmax.x) (lmax.yz, rmin.xy) (rmin.z, rmax.xyz) (l, r, -, -)
+    const float4* ptri;       // [F][3] by leaf position: (v0, tri) (e1, 0) (e2, 0)
+    const int32_t* leaf_of;   // [F] triangle -> leaf position
+    const int32_t* tris;      // [F][3] caller's vertex indices
+    const float* tri_uv;      // [F][3][2]
+    const float* albedo;      // [th][tw][3]
+    const float* rough;       // [th][tw]
+    const float* metal;       // [th][tw]
+    const float4* env_texel;  // [eh][ew]: (r, g, b, prob * ew * eh)
+    const uint32_t* env_marg; // [eh + 1] thresholds ceil(cdf * 2^24)
+    const uint32_t* env_cond; // [eh][ew + 1]
+    int32_t n_tris, n_verts, tw, th, ew, eh;
+    const int32_t* env_ok_dev; // device-written: total env weight > 0
+    const float* tmin_dev;     // device-written: 1e-5 x scene diagonal
+};
+
+struct ViewDev {
+    float K[4];
+    float c2w[12];
+    int32_t width, height, spp, bounces;
+    int32_t scene;
+    int32_t index;            // the view's index in the call (enters the random counter)
+    uint64_t offset;          // first global sample index of this view
+};
+
+// ---------------------------------------------------------------------------------------
+// small vector algebra
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 add(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 sub(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 mul(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 hmul(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b)
+{
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize(float3 a) { return mul(a, 1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ float lum(float3 c) { return (c.x + c.y + c.z) * (1.0f / 3.0f); }
+__device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+// explicitly rounded operations at the boundaries between stages, so that a product formed
+// in one kernel and summed in another rounds exactly like the fused persistent kernel
+__device__ __forceinline__ float3 hmul_rn(float3 a, float3 b)
+{
+    return f3(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y), __fmul_rn(a.z, b.z));
+}
+__device__ __forceinline__ float3 add_rn(float3 a, float3 b)
+{
+    return f3(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z));
+}
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator (Salmon et al., SC'11)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2 };
+
+struct Rng {
+    uint32_t k0, k1;
+    __device__ __forceinline__ uint4 draw(uint32_t pixel, uint32_t sample, uint32_t view, uint32_t bounce,
+                                          uint32_t purpose, uint32_t j) const
+    {
+        return philox(make_uint4(pixel, sample, (view << 16) | (bounce << 8) | purpose, j), k0, k1);
+    }
+};
+
+// 24-bit uniform in [0, 1), exact in FP32
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-8f; }
+__device__ __forceinline__ float sub_hi(uint32_t x) { return ((float)(x >> 16) + 0.5f) * 1.52587890625e-5f; }
+__device__ __forceinline__ float sub_lo(uint32_t x) { return ((float)(x & 0xFFFFu) + 0.5f) * 1.52587890625e-5f; }
+
+// ---------------------------------------------------------------------------------------
+// environment map: lookup and inverse-CDF sampling over uint32 thresholds
+// ---------------------------------------------------------------------------------------
+// largest i in [0, n-1] with a[i] <= k (a[0] == 0 <= k)
+__device__ __forceinline__ int search_le(const uint32_t* __restrict__ a, int n, uint32_t k)
+{
+    int lo = 0, len = n;
+    while (len > 1) {
+        const int half = len >> 1;
+        const int mid = lo + half;
+        if (__ldg(a + mid) <= k) lo = mid;
+        len -= half;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int env_texel_of(const SceneDev& s, float3 d)
+{
+    const float u = atan2f(d.x, -d.z) * (0.5f * MR_INV_PI) + 0.5f;
+    const float v = acosf(fminf(1.0f, fmaxf(-1.0f, d.y))) * MR_INV_PI;
+    int c = (int)floorf(u * (float)s.ew), r = (int)floorf(v * (float)s.eh);
+    c = min(max(c, 0), s.ew - 1);
+    r = min(max(r, 0), s.eh - 1);
+    return r * s.ew + c;
+}
+
+__device__ __forceinline__ float env_pdf_dir(const SceneDev& s, float3 d, int texel)
+{
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - d.y * d.y));
+    if (!(st > 0.0f)) return 0.0f;
+    return __ldg(&s.env_texel[texel].w) / (2.0f * MR_PI * MR_PI * st);
+}
+
+// sample a direction with probability proportional to Y(L) sin(theta_row); returns pdf
+__device__ __forceinline__ float env_sample(const SceneDev& s, uint32_t xrow, uint32_t xcol, uint32_t sub,
+                                            float3& dir, int& texel)
+{
+    const int r = search_le(s.env_marg, s.eh, xrow >> 8);
+    const int c = search_le(s.env_cond + (size_t)r * (s.ew + 1), s.ew, xcol >> 8);
+    const float uu = ((float)c + sub_hi(sub)) / (float)s.ew;
+    const float vv = ((float)r + sub_lo(sub)) / (float)s.eh;
+    float sp, cp, st, ct;
+    sincospif(2.0f * uu - 1.0f, &sp, &cp);
+    sincospif(vv, &st, &ct);
+    dir = f3(st * sp, ct, -st * cp);
+    texel = r * s.ew + c;
+    return __ldg(&s.env_texel[texel].w) / (2.0f * MR_PI * MR_PI * st);
+}
+
+// ---------------------------------------------------------------------------------------
+// BRDF: Lambert (1-m) a / pi + GGX D * height-correlated Smith G2 * Schlick F / (4 ci co)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float alpha_of(float r) { return fmaxf(r * r, 1e-3f); }
+__device__ __forceinline__ float smith_a(float a2, float c) { return sqrtf(a2 + (1.0f - a2) * c * c); }
+
+// GGX denominator k = cos^2 (a^2 - 1) + 1 written as |n x h|^2 + a^2 cos^2: near the specular
+// peak 1 - cos^2 cancels catastrophically in FP32, the cross product does not
+__device__ __forceinline__ float ggx_k(float3 n, float3 h, float cnh, float a2)
+{
+    const float3 c = cross(n, h);
+    return dot(c, c) + a2 * cnh * cnh;
+}
+
+struct Material {
+    float3 alb;
+    float rough, metal;
+};
+
+// f_r(wo, wi) * max(0, n.wi), zero outside both upper hemispheres
+__device__ __forceinline__ float3 brdf_cos(float3 n, float3 wo, float3 wi, const Material& m)
+{
+    const float co = dot(n, wo), ci = dot(n, wi);
+    if (co <= 0.0f || ci <= 0.0f) return f3(0.f, 0.f, 0.f);
+    const float a = alpha_of(m.rough), a2 = a * a;
+    const float3 h = normalize(add(wo, wi));
+    const float cnh = dot(n, h), coh = dot(wo, h);
+    const float k = ggx_k(n, h, cnh, a2);
+    const float D = a2 / (MR_PI * k * k);
+    const float vis = 0.5f / (ci * smith_a(a2, co) + co * smith_a(a2, ci));
+    const float om = 1.0f - coh;
+    const float w5 = (om * om) * (om * om) * om;
+    const float dv = D * vis;
+    float3 out;
+    {
+        const float kd = (1.0f - m.metal) * m.alb.x, f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.x;
+        out.x = (kd * MR_INV_PI + dv * (f0 + (1.0f - f0) * w5)) * ci;
+    }
+    {
+        const float kd = (1.0f - m.metal) * m.alb.y, f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.y;
+        out.y = (kd * MR_INV_PI + dv * (f0 + (1.0f - f0) * w5)) * ci;
+    }
+    {
+        const float kd = (1.0f - m.metal) * m.alb.z, f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.z;
+        out.z = (kd * MR_INV_PI + dv * (f0 + (1.0f - f0) * w5)) * ci;
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------------------
+// continuation sampling: one-sample mixture of env, GGX visible normals (Heitz 2018), cosine
+// ---------------------------------------------------------------------------------------
+// orthonormal basis (Duff et al. 2017), branch on n.z >= 0 so that +0 and -0 agree
+__device__ __forceinline__ void onb(float3 n, float3& t, float3& b)
+{
+    const float sg = (n.z >= 0.0f) ? 1.0f : -1.0f;
+    const float a = -1.0f / (sg + n.z);
+    const float bb = n.x * n.y * a;
+    t = f3(1.0f + sg * n.x * n.x * a, sg * bb, -sg * n.x);
+    b = f3(bb, sg + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float3 vndf_local(float3 ve, float a, float u1, float u2)
+{
+    const float3 vh = normalize(f3(a * ve.x, a * ve.y, ve.z));
+    const float lensq = vh.x * vh.x + vh.y * vh.y;
+    const float3 t1 = lensq > 0.0f ? mul(f3(-vh.y, vh.x, 0.0f), rsqrtf(lensq)) : f3(1.0f, 0.0f, 0.0f);
+    const float3 t2 = cross(vh, t1);
+    const float r = sqrtf(u1);
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    const float p1 = r * cp;
+    float p2 = r * sp;
+    const float s = 0.5f * (1.0f + vh.z);
+    p2 = (1.0f - s) * sqrtf(fmaxf(0.0f, 1.0f - p1 * p1)) + s * p2;
+    const float3 nh = add(add(mul(t1, p1), mul(t2, p2)), mul(vh, sqrtf(fmaxf(0.0f, 1.0f - p1 * p1 - p2 * p2))));
+    return normalize(f3(a * nh.x, a * nh.y, fmaxf(0.0f, nh.z)));
+}
+
+__device__ __forceinline__ float vndf_pdf(float3 n, float3 wo, float3 wi, float a)
+{
+    const float co = dot(n, wo);
+    if (co <= 0.0f) return 0.0f;
+    const float3 hs = add(wo, wi);
+    const float l2 = dot(hs, hs);
+    if (!(l2 > 0.0f)) return 0.0f;
+    const float3 h = mul(hs, rsqrtf(l2));
+    const float cnh = dot(n, h);
+    if (dot(wo, h) <= 0.0f || cnh <= 0.0f) return 0.0f;
+    const float a2 = a * a;
+    const float k = ggx_k(n, h, cnh, a2);
+    const float D = a2 / (MR_PI * k * k);
+    const float g1 = 2.0f * co / (co + smith_a(a2, co));
+    return g1 * D / (4.0f * co);
+}
+
+struct Mix {
+    float c_env, c_s;
+};
+
+__device__ __forceinline__ Mix mixture(int env_ok, const Material& m)
+{
+    Mix x;
+    x.c_env = env_ok ? 0.25f : 0.0f;
+    const float3 f0 = f3(0.04f * (1.0f - m.metal) + m.metal * m.alb.x, 0.04f * (1.0f - m.metal) + m.metal * m.alb.y,
+                         0.04f * (1.0f - m.metal) + m.metal * m.alb.z);
+    const float3 kd = mul(m.alb, 1.0f - m.metal);
+    const float ys = lum(f0), yd = lum(kd);
+    x.c_s = (ys + yd > 0.0f) ? fminf(0.9f, fmaxf(0.1f, ys / (ys + yd))) : 0.5f;
+    return x;
+}
+
+__device__ __forceinline__ float pdf_mix(const SceneDev& s, int env_ok, Mix x, float3 n, float3 wo, float3 wi,
+                                         float rough)
+{
+    const float a = alpha_of(rough);
+    const float pe = (x.c_env > 0.0f) ? env_pdf_dir(s, wi, env_texel_of(s, wi)) : 0.0f;
+    const float pv = vndf_pdf(n, wo, wi, a);
+    const float pc = fmaxf(0.0f, dot(n, wi)) * MR_INV_PI;
+    return x.c_env * pe + (1.0f - x.c_env) * (x.c_s * pv + (1.0f - x.c_s) * pc);
+}
+
+// returns the mixture pdf of the sampled direction
+__device__ __forceinline__ float sample_continuation(const SceneDev& s, int env_ok, float3 n, float3 wo,
+                                                     const Material& m, uint4 x, float3& dir)
+{
+    const Mix mx = mixture(env_ok, m);
+    const float u = u24(x.x);
+    const float t2 = mx.c_env + (1.0f - mx.c_env) * mx.c_s;
+    if (u < mx.c_env) {
+        int tex;
+        env_sample(s, x.y, x.z, x.w, dir, tex);
+    } else {
+        float3 t, b;
+        onb(n, t, b);
+        const float u1 = u24(x.y), u2 = u24(x.z);
+        float3 wl;
+        if (u < t2) {
+            const float3 ve = f3(dot(wo, t), dot(wo, b), dot(wo, n));
+            const float3 mh = vndf_local(ve, alpha_of(m.rough), u1, u2);
+            wl = sub(mul(mh, 2.0f * dot(ve, mh)), ve);
+        } else {
+            const float r = sqrtf(u1);
+            float sp, cp;
+            sincospif(2.0f * u2, &sp, &cp);
+            wl = f3(r * cp, r * sp, sqrtf(fmaxf(0.0f, 1.0f - u1)));
+        }
+        dir = add(add(mul(t, wl.x), mul(b, wl.y)), mul(n, wl.z));
+    }
+    return pdf_mix(s, env_ok, mx, n, wo, dir, m.rough);
+}
+
+// ---------------------------------------------------------------------------------------
+// ray / triangle (Moller-Trumbore, FP32) and LBVH traversal
+// ---------------------------------------------------------------------------------------
+struct Hit {
+    float t, u, v;
+    int tri;
+};
+
+// plane intersection; returns false only when the ray is parallel (det == 0)
+__device__ __forceinline__ bool tri_solve(float3 o, float3 d, float3 v0, float3 e1, float3 e2, float& t, float& u,
+                                          float& v)
+{
+    const float3 p = cross(d, e2);
+    const float det = dot(e1, p);
+    if (det == 0.0f) return false;
+    const float inv = 1.0f / det;
+    const float3 sv = sub(o, v0);
+    u = dot(sv, p) * inv;
+    const float3 q = cross(sv, e1);
+    v = dot(d, q) * inv;
+    t = dot(e2, q) * inv;
+    return true;
+}
+
+__device__ __forceinline__ void load_tri(const SceneDev& s, int leaf, float3& v0, float3& e1, float3& e2, int& tri)
+{
+    const float4 a = __ldg(s.ptri + 3 * (size_t)leaf);
+    const float4 b = __ldg(s.ptri + 3 * (size_t)leaf + 1);
+    const float4 c = __ldg(s.ptri + 3 * (size_t)leaf + 2);
+    v0 = xyz(a);
+    tri = __float_as_int(a.w);
+    e1 = xyz(b);
+    e2 = xyz(c);
+}
+
+// test one leaf; closest: keep smallest t, ties -> smaller id. Returns hit (any mode).
+__device__ __forceinline__ bool test_leaf(const SceneDev& s, int leaf, float3 o, float3 d, int skip, float tmin,
+                                          Hit& best)
+{
+    float3 v0, e1, e2;
+    int tri;
+    load_tri(s, leaf, v0, e1, e2, tri);
+    if (tri == skip) return false;
+    float t, u, v;
+    if (!tri_solve(o, d, v0, e1, e2, t, u, v)) return false;
+    if (!(u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t > tmin)) return false;
+    if (t < best.t || (t == best.t && tri < best.tri)) {
+        best.t = t;
+        best.u = u;
+        best.v = v;
+        best.tri = tri;
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float safe_inv(float x)
+{
+    return 1.0f / (fabsf(x) > 1e-30f ? x : copysignf(1e-30f, x));
+}
+
+// slab test of one box; returns the entry distance, or NaN on a miss (NaN <= t is false)
+__device__ __forceinline__ float slab(float3 lo, float3 hi, float3 o, float3 inv, float tmin, float tmax)
+{
+    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
+    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
+    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    // a few ulp of slack so that rounding never culls a box the ray touches
+    return (tn <= tf * 1.0000005f + 1e-30f) ? tn : __int_as_float(0x7fffffff);
+}
+
+// Closest (any = false) or any hit with t in (tmin, tmax). `sstk` = this thread's shared
+// stack column (stride `sstride`). Returns the number of nodes visited (for counters), or
+// -1 if the iteration cap was reached (a malformed tree; the ray reports a miss).
+template <bool ANY>
+__device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, int skip, float tmin, float tmax,
+                                        Hit& best, uint32_t* sstk, int sstride)
+{
+    best.t = tmax;
+    best.tri = -1;
+    best.u = best.v = 0.0f;
+    const int F = s.n_tris;
+    if (F <= 0) return 0;
+    if (F == 1) {
+        test_leaf(s, 0, o, d, skip, tmin, best);
+        return 1;
+    }
+    const float3 inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    uint32_t lstk[MR_LSTACK];
+    int sp = 0;
+    int node = 0;
+    int visited = 0;
+    const int cap = 4 * F + 64;
+    while (true) {
+        if (++visited > cap) {
+            best.tri = -1;
+            return -1;
+        }
+        const float4 n0 = __ldg(s.nodes + 4 * (size_t)node);
+        const float4 n1 = __ldg(s.nodes + 4 * (size_t)node + 1);
+        const float4 n2 = __ldg(s.nodes + 4 * (size_t)node + 2);
+        const int2 ch = *reinterpret_cast<const int2*>(&s.nodes[4 * (size_t)node + 3]);
+        const float tl = slab(f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), o, inv, tmin, best.t);
+        const float tr = slab(f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), o, inv, tmin, best.t);
+        bool gl = tl <= best.t, gr = tr <= best.t;
+        // leaves are tested on the spot
+        if (gl && ch.x < 0) {
+            if (test_leaf(s, ~ch.x, o, d, skip, tmin, best) && ANY) return visited;
+            gl = false;
+        }
+        if (gr && ch.y < 0) {
+            if (test_leaf(s, ~ch.y, o, d, skip, tmin, best) && ANY) return visited;
+            gr = false;
+        }
+        if (gl && gr) {
+            const bool lfirst = tl <= tr;
+            const int nearc = lfirst ? ch.x : ch.y, farc = lfirst ? ch.y : ch.x;
+            if (sp < MR_SSTACK) sstk[sp * sstride] = (uint32_t)farc;
+            else lstk[min(sp - MR_SSTACK, MR_LSTACK - 1)] = (uint32_t)farc;
+            ++sp;
+            node = nearc;
+        } else if (gl) {
+            node = ch.x;
+        } else if (gr) {
+            node = ch.y;
+        } else {
+            if (sp == 0) break;
+            --sp;
+            node = (int)(sp < MR_SSTACK ? sstk[sp * sstride] : lstk[min(sp - MR_SSTACK, MR_LSTACK - 1)]);
+        }
+    }
+    return visited;
+}
+
+// ---------------------------------------------------------------------------------------
+// shading point
+// ---------------------------------------------------------------------------------------
+struct Taps {
+    int idx[4];
+    float w[4];
+    float fx, fy;
+};
+
+__device__ __forceinline__ void taps_at(int w, int h, float su, float sv, Taps& tp)
+{
+    const float x = su * (float)w - 0.5f, y = sv * (float)h - 0.5f;
+    const float x0 = floorf(x), y0 = floorf(y);
+    tp.fx = x - x0;
+    tp.fy = y - y0;
+    int ix0 = (int)x0, iy0 = (int)y0;
+    int ix1 = ix0 + 1, iy1 = iy0 + 1;
+    ix0 = min(max(ix0, 0), w - 1);
+    ix1 = min(max(ix1, 0), w - 1);
+    iy0 = min(max(iy0, 0), h - 1);
+    iy1 = min(max(iy1, 0), h - 1);
+    tp.idx[0] = iy0 * w + ix0;
+    tp.idx[1] = iy0 * w + ix1;
+    tp.idx[2] = iy1 * w + ix0;
+    tp.idx[3] = iy1 * w + ix1;
+    tp.w[0] = (1.0f - tp.fx) * (1.0f - tp.fy);
+    tp.w[1] = tp.fx * (1.0f - tp.fy);
+    tp.w[2] = (1.0f - tp.fx) * tp.fy;
+    tp.w[3] = tp.fx * tp.fy;
+}
+
+struct Shade {
+    float3 x, n, N, e1, e2;
+    float sign;
+    float su, sv;
+    Taps tp;
+    Material m;
+};
+
+__device__ __forceinline__ void shade_at(const SceneDev& s, int tri, float u, float v, float3 d, Shade& sh)
+{
+    float3 v0;
+    int tri_chk;
+    load_tri(s, __ldg(s.leaf_of + tri), v0, sh.e1, sh.e2, tri_chk);
+    sh.N = cross(sh.e1, sh.e2);
+    const float3 nh = normalize(sh.N);
+    sh.sign = (dot(nh, d) > 0.0f) ? -1.0f : 1.0f;
+    sh.n = mul(nh, sh.sign);
+    sh.x = add(v0, add(mul(sh.e1, u), mul(sh.e2, v)));
+    const float* uv = s.tri_uv + 6 * (size_t)tri;
+    const float w0 = 1.0f - u - v;
+    sh.su = w0 * __ldg(uv + 0) + u * __ldg(uv + 2) + v * __ldg(uv + 4);
+    sh.sv = w0 * __ldg(uv + 1) + u * __ldg(uv + 3) + v * __ldg(uv + 5);
+    taps_at(s.tw, s.th, sh.su, sh.sv, sh.tp);
+    float3 a = f3(0.f, 0.f, 0.f);
+    float r = 0.0f, m = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = sh.tp.idx[k];
+        const float w = sh.tp.w[k];
+        a.x += w * __ldg(s.albedo + 3 * (size_t)i);
+        a.y += w * __ldg(s.albedo + 3 * (size_t)i + 1);
+        a.z += w * __ldg(s.albedo + 3 * (size_t)i + 2);
+        r += w * __ldg(s.rough + i);
+        m += w * __ldg(s.metal + i);
+    }
+    sh.m.alb = a;
+    sh.m.rough = r;
+    sh.m.metal = m;
+}
+
+// camera ray direction for pixel (px, py) with jitter from the random stream
+__device__ __forceinline__ float3 camera_dir(const ViewDev& v, int px, int py, float j0, float j1)
+{
+    const float dcx = ((float)px + j0 - v.K[2]) / v.K[0];
+    const float dcy = ((float)py + j1 - v.K[3]) / v.K[1];
+    const float3 d = f3(v.c2w[0] * dcx + v.c2w[1] * dcy + v.c2w[2], v.c2w[4] * dcx + v.c2w[5] * dcy + v.c2w[6],
+                        v.c2w[8] * dcx + v.c2w[9] * dcy + v.c2w[10]);
+    return normalize(d);
+}
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }

@@ -1,0 +1,111 @@
+// env.cu -- environment-map importance-sampling tables (the paper's proposal
+// q_dir ~ L_env, "directly sampled from our environment map", Sec. 4.1).
+//
+// Texel weight w = Y(L) sin(theta_row), Y = (r + g + b) / 3 (Appendix A). Per-row conditional
+// CDFs and the marginal CDF over rows are FP64 prefix sums (one thread per row, sequential
+// over the row, so every sum has a fixed order), converted to uint32 thresholds
+// ceil(cdf * 2^24): for a 24-bit uniform u = k 2^-24, cdf <= u exactly when threshold <= k,
+// so the search needs no FP64 arithmetic. The texel table packs (r, g, b, P * W * H).
+#include "internal.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t threshold(double cdf)
+{
+    const double x = ceil(cdf * 16777216.0);
+    return x <= 0.0 ? 0u : (x >= 16777216.0 ? 16777216u : (uint32_t)x);
+}
+
+__global__ void k_env_rows(const float* __restrict__ env, int W, int H, double* __restrict__ w,
+                           double* __restrict__ rowsum, uint32_t* __restrict__ cond)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H) return;
+    const double st = sin(3.14159265358979323846 * ((double)r + 0.5) / (double)H);
+    double acc = 0.0;
+    for (int c = 0; c < W; ++c) {
+        const float* p = env + 3 * ((size_t)r * W + c);
+        const double y = (((double)p[0] + (double)p[1]) + (double)p[2]) / 3.0 * st;
+        w[(size_t)r * W + c] = y;
+        acc += y;
+    }
+    rowsum[r] = acc;
+    uint32_t* cr = cond + (size_t)r * (W + 1);
+    double run = 0.0;
+    for (int c = 0; c <= W; ++c) {
+        double v;
+        if (acc > 0.0) v = (c == W) ? 1.0 : run / acc;
+        else v = (double)c / (double)W;
+        cr[c] = threshold(v);
+        if (c < W) run += w[(size_t)r * W + c];
+    }
+}
+
+__global__ void k_env_marg(const double* __restrict__ rowsum, int H, double* total_out, int32_t* ok_out,
+                           uint32_t* __restrict__ marg)
+{
+    if (threadIdx.x != 0) return;
+    double total = 0.0;
+    for (int r = 0; r < H; ++r) total += rowsum[r];
+    const int ok = total > 0.0;
+    double run = 0.0;
+    for (int r = 0; r <= H; ++r) {
+        double v;
+        if (ok) v = (r == H) ? 1.0 : run / total;
+        else v = (double)r / (double)H;
+        marg[r] = threshold(v);
+        if (r < H) run += rowsum[r];
+    }
+    *total_out = total;
+    *ok_out = ok;
+}
+
+__global__ void k_env_texels(const float* __restrict__ env, const double* __restrict__ w, int W, int H,
+                             const double* __restrict__ total, float4* __restrict__ texel)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)W * H) return;
+    const double tot = *total;
+    const float p = tot > 0.0 ? (float)(w[i] / tot * ((double)W * (double)H)) : 0.0f;
+    texel[i] = make_float4(env[3 * i], env[3 * i + 1], env[3 * i + 2], p);
+}
+
+}  // namespace
+
+mirres_status mr_env_alloc(mirres_scene* s)
+{
+    const size_t W = (size_t)s->desc.env_w, H = (size_t)s->desc.env_h;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc((void**)&s->env_w, sizeof(double) * W * H);
+    e = e ? e : cudaMalloc((void**)&s->env_rowsum, sizeof(double) * H);
+    e = e ? e : cudaMalloc((void**)&s->env_total, sizeof(double));
+    e = e ? e : cudaMalloc((void**)&s->env_ok, sizeof(int32_t));
+    e = e ? e : cudaMalloc((void**)&s->env_marg, sizeof(uint32_t) * (H + 1));
+    e = e ? e : cudaMalloc((void**)&s->env_cond, sizeof(uint32_t) * H * (W + 1));
+    e = e ? e : cudaMalloc((void**)&s->env_texel, sizeof(float4) * W * H);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mr_set_error(std::string("env table allocation failed: ") + cudaGetErrorString(e));
+        return MIRRES_ERR_OOM;
+    }
+    return MIRRES_OK;
+}
+
+void mr_env_free(mirres_scene* s)
+{
+    void* ptrs[] = {s->env_w, s->env_rowsum, s->env_total, s->env_ok, s->env_marg, s->env_cond, s->env_texel};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+mirres_status mr_env_build(mirres_scene* s, cudaStream_t st)
+{
+    const int W = s->desc.env_w, H = s->desc.env_h;
+    k_env_rows<<<(H + 63) / 64, 64, 0, st>>>(s->desc.env, W, H, s->env_w, s->env_rowsum, s->env_cond);
+    k_env_marg<<<1, 32, 0, st>>>(s->env_rowsum, H, s->env_total, s->env_ok, s->env_marg);
+    const size_t n = (size_t)W * H;
+    k_env_texels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->desc.env, s->env_w, W, H, s->env_total,
+                                                             s->env_texel);
+    MR_CUDA(cudaGetLastError());
+    return MIRRES_OK;
+}

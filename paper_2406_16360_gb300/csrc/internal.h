@@ -1,0 +1,83 @@
+// internal.h -- host-side declarations shared by the translation units of libmirres.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mirres.h"
+#include "device.cuh"
+
+// error handling: a thread-local message behind mirres_last_error()
+void mr_set_error(const std::string& msg);
+mirres_status mr_cuda_status(cudaError_t e, const char* what);
+#define MR_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e__ = (call);                                                      \
+        if (e__ != cudaSuccess) return mr_cuda_status(e__, #call);                     \
+    } while (0)
+
+// device workspace owned by a context (grow-only)
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+enum { CNT_PRIMARY = 0, CNT_CONT, CNT_SHADOW, CNT_SAMPLES, CNT_DIFF, CNT_CAND, CNT_LAUNCH, CNT_ERROR, CNT_N };
+
+struct mirres_context {
+    int device = 0;
+    int sm_count = 0;
+    Workspace ws;
+    unsigned long long* counters = nullptr;  // device [CNT_N]
+    unsigned int* queue_cnt = nullptr;       // device scratch counters [64]
+    cudaStream_t last_stream = nullptr;
+    unsigned long long host_launches = 0;
+};
+
+struct mirres_scene {
+    mirres_context* ctx = nullptr;
+    mirres_scene_desc desc{};
+    bool built = false;
+    // LBVH
+    uint64_t* keys = nullptr;        // [F]
+    int32_t* perm = nullptr;         // [F] leaf position -> triangle
+    int32_t* left = nullptr;         // [F-1]
+    int32_t* right = nullptr;        // [F-1]
+    int32_t* parent = nullptr;       // [2F-1]
+    float* lo = nullptr;             // [2F-1][3]
+    float* hi = nullptr;             // [2F-1][3]
+    int32_t* flags = nullptr;        // [F-1] bottom-up arrival counters
+    float4* nodes = nullptr;         // [F-1][4]
+    float4* ptri = nullptr;          // [F][3]
+    int32_t* leaf_of = nullptr;      // [F]
+    float* cent = nullptr;           // [3][F] centroids (build scratch)
+    uint32_t* codes[2] = {nullptr, nullptr};
+    int32_t* vals[2] = {nullptr, nullptr};
+    uint32_t* hist = nullptr;        // radix histograms
+    unsigned int* bounds = nullptr;  // [12] ordered-uint bounds: centroid lo/hi, vertex lo/hi
+    float* tmin = nullptr;           // [1]
+    int32_t* bad = nullptr;          // [1] invalid index flag
+    // env tables
+    double* env_w = nullptr;         // [eh][ew]
+    double* env_rowsum = nullptr;    // [eh]
+    double* env_total = nullptr;     // [1]
+    int32_t* env_ok = nullptr;       // [1]
+    uint32_t* env_marg = nullptr;    // [eh+1]
+    uint32_t* env_cond = nullptr;    // [eh][ew+1]
+    float4* env_texel = nullptr;     // [eh][ew]
+};
+
+SceneDev mr_scene_dev(const mirres_scene* s);
+
+// bvh.cu
+mirres_status mr_bvh_alloc(mirres_scene* s);
+void mr_bvh_free(mirres_scene* s);
+mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st);
+mirres_status mr_bvh_refit(mirres_scene* s, cudaStream_t st);
+// env.cu
+mirres_status mr_env_alloc(mirres_scene* s);
+void mr_env_free(mirres_scene* s);
+mirres_status mr_env_build(mirres_scene* s, cudaStream_t st);

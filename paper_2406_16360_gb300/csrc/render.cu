@@ -1,0 +1,900 @@
+// render.cu -- forward path tracing (wavefront and persistent), adjoint replay, L2 loss.
+//
+// One path sample = one pixel sample of one view. Per sample the tape holds nine 32-bit
+// words (SoA, N = samples of the call): primary triangle, selected RIS candidate at the
+// primary vertex, V*W at the primary vertex, L_ind (3) at the primary vertex, radiance (3).
+// The image is the mean of the sample radiances over spp, summed in sample order.
+#include "render.h"
+
+namespace {
+
+struct TapeDev {
+    int32_t* tri;
+    int32_t* cand;
+    float* wv;
+    float* lind[3];
+    float* rad[3];
+};
+
+__device__ __forceinline__ TapeDev tape_of(void* base, uint64_t n)
+{
+    TapeDev t;
+    uint32_t* w = reinterpret_cast<uint32_t*>(base);
+    t.tri = reinterpret_cast<int32_t*>(w);
+    t.cand = reinterpret_cast<int32_t*>(w + n);
+    t.wv = reinterpret_cast<float*>(w + 2 * n);
+    for (int k = 0; k < 3; ++k) t.lind[k] = reinterpret_cast<float*>(w + (3 + k) * n);
+    for (int k = 0; k < 3; ++k) t.rad[k] = reinterpret_cast<float*>(w + (6 + k) * n);
+    return t;
+}
+
+// ---------------------------------------------------------------------------------------
+// one shading vertex: RIS over M env candidates (Eq. restir, streamed through a weighted
+// reservoir), the shadow ray that tests the selected candidate, and the continuation ray
+// drawn from the MIS mixture (Eq. mc_indir). Shared by the wavefront and persistent kernels.
+// ---------------------------------------------------------------------------------------
+struct VertexOut {
+    bool shadow;
+    float3 sh_o, sh_d;
+    float3 add_rad, add_lind;
+    bool cont;
+    float3 c_d, c_beta, c_bind;
+    float3 x;
+    int cand;
+    float W;
+};
+
+__device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, const Rng& rng, uint32_t pixel,
+                                             uint32_t smp, uint32_t view, int b, int B, int M, const Hit& h,
+                                             float3 d, float3 beta, float3 bind, VertexOut& out)
+{
+    Shade sh;
+    shade_at(s, h.tri, h.u, h.v, d, sh);
+    const float3 wo = f3(-d.x, -d.y, -d.z);
+    out.x = sh.x;
+    out.shadow = false;
+    out.cont = false;
+    out.cand = -1;
+    out.W = 0.0f;
+    if (env_ok && M > 0) {
+        float wsum = 0.0f, phat_sel = 0.0f;
+        int sel = -1, ytex = 0;
+        float3 ysel = f3(0.f, 0.f, 0.f), fsel = f3(0.f, 0.f, 0.f);
+        for (int j = 0; j < M; ++j) {
+            const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j);
+            float3 dir;
+            int tex;
+            const float q = env_sample(s, x.x, x.y, x.w, dir, tex);
+            const float3 fc = brdf_cos(sh.n, wo, dir, sh.m);
+            const float4 L = __ldg(s.env_texel + tex);
+            const float phat = lum(xyz(L)) * lum(fc);  // p_hat = Y(L_env) Y(f_r) cos
+            const float gamma = phat / q;              // gamma = p_hat / q_dir
+            wsum += gamma;
+            if (u24(x.z) * wsum < gamma) {
+                sel = j;
+                ytex = tex;
+                ysel = dir;
+                fsel = fc;
+                phat_sel = phat;
+            }
+        }
+        if (sel >= 0 && wsum > 0.0f) {
+            const float W = wsum / ((float)M * phat_sel);
+            const float4 L = __ldg(s.env_texel + ytex);
+            const float3 contrib = mul(hmul(xyz(L), fsel), W);
+            out.add_rad = hmul_rn(beta, contrib);
+            out.add_lind = (b >= 1) ? hmul_rn(bind, contrib) : f3(0.f, 0.f, 0.f);
+            out.shadow = true;
+            out.sh_o = sh.x;
+            out.sh_d = ysel;
+            if (b == 0) {
+                out.cand = sel;
+                out.W = W;
+            }
+        }
+    }
+    if (b < B - 1) {
+        const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CONTINUE, 0u);
+        float3 wc;
+        const float pind = sample_continuation(s, env_ok, sh.n, wo, sh.m, x, wc);
+        const float3 fc = brdf_cos(sh.n, wo, wc, sh.m);
+        if (pind > 0.0f && (fc.x > 0.0f || fc.y > 0.0f || fc.z > 0.0f)) {
+            const float3 f = f3(fc.x / pind, fc.y / pind, fc.z / pind);
+            out.cont = true;
+            out.c_d = wc;
+            out.c_beta = hmul_rn(beta, f);
+            out.c_bind = (b >= 1) ? hmul_rn(bind, f) : bind;
+        }
+    }
+}
+
+__device__ __forceinline__ const ViewDev& view_of(const ViewDev* views, int n, uint64_t g, int& vi)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].offset <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    vi = lo;
+    return views[lo];
+}
+
+// ---------------------------------------------------------------------------------------
+// wavefront (plain) kernels: one view chunk at a time
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_raygen(ViewDev v, Rng rng, uint32_t first, uint32_t n, QueueDev q,
+                                                void* tape, uint64_t ntot)
+{
+    const TapeDev tp = tape_of(tape, ntot);
+    const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t sid = first + i;
+        const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
+        const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+        const uint4 x = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_CAMERA, 0u);
+        const float3 d = camera_dir(v, px, py, u24(x.x), u24(x.y));
+        q.o[i] = make_float4(o.x, o.y, o.z, __int_as_float(-1));
+        q.d[i] = make_float4(d.x, d.y, d.z, __uint_as_float(sid));
+        q.b[i] = make_float4(1.f, 1.f, 1.f, 0.f);
+        q.bi[i] = make_float4(1.f, 1.f, 1.f, 0.f);
+        const uint64_t g = v.offset + sid;
+        tp.tri[g] = -1;
+        tp.cand[g] = -1;
+        tp.wv[g] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            tp.lind[k][g] = 0.0f;
+            tp.rad[k][g] = 0.0f;
+        }
+    }
+}
+
+template <bool ANY>
+__global__ void __launch_bounds__(256) k_trace(SceneDev s, const float4* __restrict__ qo,
+                                               const float4* __restrict__ qd, const unsigned int* count,
+                                               unsigned int count_fixed, float4* __restrict__ hits)
+{
+    extern __shared__ uint32_t sstk[];
+    const unsigned int n = count ? *count : count_fixed;
+    const float tmin = *s.tmin_dev;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = qo[i], b = qd[i];
+        Hit h;
+        traverse<ANY>(s, xyz(a), xyz(b), __float_as_int(a.w), tmin, __int_as_float(0x7f800000), h,
+                      sstk + threadIdx.x, blockDim.x);
+        hits[i] = make_float4(h.t, h.u, h.v, __int_as_float(h.tri));
+    }
+}
+
+// warp-aggregated append: returns the slot of this lane (valid only if want)
+__device__ __forceinline__ unsigned int warp_append(bool want, unsigned int* counter)
+{
+    const unsigned m = __ballot_sync(MR_FULL, want);
+    if (!m) return 0u;
+    const int leader = __ffs(m) - 1;
+    unsigned int base = 0;
+    if (lane_id() == leader) base = atomicAdd(counter, (unsigned)__popc(m));
+    base = __shfl_sync(MR_FULL, base, leader);
+    return base + __popc(m & lanemask_lt());
+}
+
+__global__ void __launch_bounds__(256) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev qin,
+                                               const unsigned int* count_in, unsigned int count_fixed,
+                                               const float4* __restrict__ hits, QueueDev qout,
+                                               unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
+                                               void* tape, uint64_t ntot)
+{
+    const TapeDev tp = tape_of(tape, ntot);
+    const unsigned int n = count_in ? *count_in : count_fixed;
+    const int env_ok = *s.env_ok_dev;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    const unsigned int rounds = (n + stride - 1) / stride;
+    for (unsigned int r = 0; r < rounds; ++r) {
+        const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const bool live = i < n;
+        VertexOut out;
+        out.shadow = false;
+        out.cont = false;
+        uint32_t sid = 0;
+        float4 qb = make_float4(0.f, 0.f, 0.f, 0.f), qbi = qb;
+        float3 d = f3(0.f, 0.f, 1.f);
+        int tri = -1;
+        if (live) {
+            const float4 hd = hits[i];
+            const float4 qd = qin.d[i];
+            d = xyz(qd);
+            sid = __float_as_uint(qd.w);
+            const uint64_t g = v.offset + sid;
+            tri = __float_as_int(hd.w);
+            if (tri < 0) {
+                if (b == 0) {  // a primary ray that escapes sees the environment
+                    const float4 L = __ldg(s.env_texel + env_texel_of(s, d));
+                    tp.rad[0][g] = L.x;
+                    tp.rad[1][g] = L.y;
+                    tp.rad[2][g] = L.z;
+                }
+            } else {
+                qb = qin.b[i];
+                qbi = qin.bi[i];
+                const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
+                Hit h;
+                h.t = hd.x;
+                h.u = hd.y;
+                h.v = hd.z;
+                h.tri = tri;
+                shade_vertex(s, env_ok, rng, pixel, smp, (uint32_t)v.index, b, v.bounces, M, h, d, xyz(qb),
+                             xyz(qbi), out);
+                if (b == 0) {
+                    tp.tri[g] = tri;
+                    tp.cand[g] = out.cand;
+                    tp.wv[g] = out.W;
+                }
+            }
+        }
+        const unsigned int ss = warp_append(out.shadow, count_sh);
+        if (out.shadow) {
+            sq.o[ss] = make_float4(out.sh_o.x, out.sh_o.y, out.sh_o.z, __int_as_float(tri));
+            sq.d[ss] = make_float4(out.sh_d.x, out.sh_d.y, out.sh_d.z, __uint_as_float(sid));
+            sq.add[ss] = make_float4(out.add_rad.x, out.add_rad.y, out.add_rad.z, 0.f);
+            sq.addi[ss] = make_float4(out.add_lind.x, out.add_lind.y, out.add_lind.z, 0.f);
+        }
+        const unsigned int cs = warp_append(out.cont, count_out);
+        if (out.cont) {
+            qout.o[cs] = make_float4(out.x.x, out.x.y, out.x.z, __int_as_float(tri));
+            qout.d[cs] = make_float4(out.c_d.x, out.c_d.y, out.c_d.z, __uint_as_float(sid));
+            qout.b[cs] = make_float4(out.c_beta.x, out.c_beta.y, out.c_beta.z, 0.f);
+            qout.bi[cs] = make_float4(out.c_bind.x, out.c_bind.y, out.c_bind.z, 0.f);
+        }
+    }
+}
+
+// shadow rays: any hit; unoccluded rays add their contribution to the sample
+__global__ void __launch_bounds__(256) k_shadow(SceneDev s, ViewDev v, int b, ShadowDev sq,
+                                                const unsigned int* count, void* tape, uint64_t ntot)
+{
+    extern __shared__ uint32_t sstk[];
+    const TapeDev tp = tape_of(tape, ntot);
+    const unsigned int n = *count;
+    const float tmin = *s.tmin_dev;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = sq.o[i], dd = sq.d[i];
+        Hit h;
+        traverse<true>(s, xyz(a), xyz(dd), __float_as_int(a.w), tmin, __int_as_float(0x7f800000), h,
+                       sstk + threadIdx.x, blockDim.x);
+        const uint64_t g = v.offset + __float_as_uint(dd.w);
+        if (h.tri < 0) {
+            const float4 ad = sq.add[i], ai = sq.addi[i];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float av = k == 0 ? ad.x : (k == 1 ? ad.y : ad.z);
+                const float ai_ = k == 0 ? ai.x : (k == 1 ? ai.y : ai.z);
+                tp.rad[k][g] = __fadd_rn(tp.rad[k][g], av);
+                if (b >= 1) tp.lind[k][g] = __fadd_rn(tp.lind[k][g], ai_);
+            }
+        } else if (b == 0) {
+            tp.wv[g] = 0.0f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_resolve(ViewDev v, const void* tape, uint64_t ntot, float* __restrict__ img)
+{
+    const TapeDev tp = tape_of(const_cast<void*>(tape), ntot);
+    const uint32_t npix = (uint32_t)v.width * (uint32_t)v.height;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        const uint64_t g0 = v.offset + (uint64_t)p * (uint32_t)v.spp;
+        float acc[3] = {0.f, 0.f, 0.f};
+        for (int smp = 0; smp < v.spp; ++smp)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[k] = __fadd_rn(acc[k], tp.rad[k][g0 + smp]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) img[3 * (size_t)p + k] = acc[k] / (float)v.spp;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// persistent batched kernel: every view of every scene in one launch. Each warp pulls
+// chunks of consecutive samples from a device counter; a lane whose path ends takes the
+// next sample from the warp's chunk (ballot + popc), so lanes stay busy across views.
+// ---------------------------------------------------------------------------------------
+__global__ void k_persistent(const SceneDev* __restrict__ scenes, const ViewDev* __restrict__ views, int n_views,
+                             uint64_t total, Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
+                             unsigned long long* counters)
+{
+    extern __shared__ uint32_t sstk[];
+    const TapeDev tp = tape_of(tape, total);
+    const int lane = lane_id();
+    uint32_t* mystk = sstk + threadIdx.x;
+    const int sstride = blockDim.x;
+
+    bool active = false;
+    uint64_t g = 0;
+    int vi = 0, b = 0, B = 1, origin = -1, tri0 = -1, cand0 = -1, env_ok = 0;
+    uint32_t pixel = 0, smp = 0, vidx = 0;
+    float3 o = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f), beta = f3(1.f, 1.f, 1.f), bind = beta;
+    float3 rad = f3(0.f, 0.f, 0.f), lind = rad;
+    float wv0 = 0.0f, tmin = 0.0f;
+    const SceneDev* sp = scenes;
+
+    uint64_t pool = 0, pool_end = 0;
+    bool exhausted = false;
+    unsigned long long n_cont = 0, n_shadow = 0, n_cand = 0, n_prim = 0;
+
+    while (true) {
+        unsigned idle = __ballot_sync(MR_FULL, !active);
+        if (idle && pool == pool_end && !exhausted) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(work, (unsigned long long)chunk);
+            base = __shfl_sync(MR_FULL, base, 0);
+            if (base >= total) exhausted = true;
+            else {
+                pool = base;
+                pool_end = (base + chunk < total) ? base + chunk : total;
+            }
+        }
+        if (idle && pool < pool_end) {
+            const uint64_t avail = pool_end - pool;
+            const unsigned rank = __popc(idle & lanemask_lt());
+            if (!active && rank < avail) {
+                g = pool + rank;
+                const ViewDev& v = view_of(views, n_views, g, vi);
+                sp = scenes + v.scene;
+                const uint32_t sid = (uint32_t)(g - v.offset);
+                pixel = sid / (uint32_t)v.spp;
+                smp = sid % (uint32_t)v.spp;
+                vidx = (uint32_t)v.index;
+                B = v.bounces;
+                const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+                const uint4 x = rng.draw(pixel, smp, vidx, 0u, PURPOSE_CAMERA, 0u);
+                o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+                d = camera_dir(v, px, py, u24(x.x), u24(x.y));
+                beta = bind = f3(1.f, 1.f, 1.f);
+                rad = lind = f3(0.f, 0.f, 0.f);
+                b = 0;
+                origin = -1;
+                tri0 = -1;
+                cand0 = -1;
+                wv0 = 0.0f;
+                env_ok = *sp->env_ok_dev;
+                tmin = *sp->tmin_dev;
+                active = true;
+                ++n_prim;
+            }
+            pool += ((uint64_t)__popc(idle) < avail) ? (uint64_t)__popc(idle) : avail;
+        }
+        if (!__any_sync(MR_FULL, active)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (active) {
+            const SceneDev s = *sp;
+            Hit h;
+            traverse<false>(s, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk, sstride);
+            bool done = false;
+            if (h.tri < 0) {
+                if (b == 0) {
+                    const float4 L = __ldg(s.env_texel + env_texel_of(s, d));
+                    rad = f3(L.x, L.y, L.z);
+                }
+                done = true;
+            } else {
+                if (b == 0) tri0 = h.tri;
+                VertexOut out;
+                shade_vertex(s, env_ok, rng, pixel, smp, vidx, b, B, M, h, d, beta, bind, out);
+                n_cand += (env_ok && M > 0) ? (unsigned long long)M : 0ull;
+                if (b == 0) {
+                    cand0 = out.cand;
+                    wv0 = out.W;
+                }
+                if (out.shadow) {
+                    ++n_shadow;
+                    Hit hs;
+                    traverse<true>(s, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk,
+                                   sstride);
+                    if (hs.tri < 0) {
+                        rad = add_rn(rad, out.add_rad);
+                        if (b >= 1) lind = add_rn(lind, out.add_lind);
+                    } else if (b == 0) {
+                        wv0 = 0.0f;
+                    }
+                }
+                if (out.cont) {
+                    ++n_cont;
+                    o = out.x;
+                    d = out.c_d;
+                    beta = out.c_beta;
+                    bind = out.c_bind;
+                    origin = h.tri;
+                    ++b;
+                } else {
+                    done = true;
+                }
+            }
+            if (done) {
+                tp.tri[g] = tri0;
+                tp.cand[g] = cand0;
+                tp.wv[g] = wv0;
+                tp.lind[0][g] = lind.x;
+                tp.lind[1][g] = lind.y;
+                tp.lind[2][g] = lind.z;
+                tp.rad[0][g] = rad.x;
+                tp.rad[1][g] = rad.y;
+                tp.rad[2][g] = rad.z;
+                active = false;
+            }
+        }
+    }
+    // per-warp counter flush
+    for (int off = 16; off > 0; off >>= 1) {
+        n_prim += __shfl_xor_sync(MR_FULL, n_prim, off);
+        n_cont += __shfl_xor_sync(MR_FULL, n_cont, off);
+        n_shadow += __shfl_xor_sync(MR_FULL, n_shadow, off);
+        n_cand += __shfl_xor_sync(MR_FULL, n_cand, off);
+    }
+    if (lane == 0) {
+        atomicAdd(counters + 0, n_prim);
+        atomicAdd(counters + 1, n_cont);
+        atomicAdd(counters + 2, n_shadow);
+        atomicAdd(counters + 5, n_cand);
+    }
+}
+
+// resolve every view of a batch in one launch: one thread per pixel over all views
+__global__ void __launch_bounds__(256) k_resolve_all(const ViewDev* __restrict__ views, int n_views,
+                                                     const uint64_t* __restrict__ pix_off, uint64_t total_pix,
+                                                     float* const* __restrict__ images, const void* tape,
+                                                     uint64_t ntot)
+{
+    const TapeDev tp = tape_of(const_cast<void*>(tape), ntot);
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total_pix;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_views - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pix_off[mid] <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        const ViewDev& v = views[lo];
+        const uint64_t p = q - pix_off[lo];
+        const uint64_t g0 = v.offset + p * (uint32_t)v.spp;
+        float acc[3] = {0.f, 0.f, 0.f};
+        for (int smp = 0; smp < v.spp; ++smp)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[k] = __fadd_rn(acc[k], tp.rad[k][g0 + smp]);
+        float* img = images[lo];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) img[3 * p + k] = acc[k] / (float)v.spp;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint (PRIMARY mode): replay of the primary vertex from the tape and the random stream
+// ---------------------------------------------------------------------------------------
+// reverse-mode derivative of Q = f_r(wo, wi) max(0, n.wi) (per channel) for the upstream
+// gradient gq: gm = (d/d albedo[3], d/d roughness, d/d metallic, d/d n[3])
+__device__ __forceinline__ void brdf_cos_adjoint(float3 n, float3 wo, float3 wi, const Material& m, float3 gq,
+                                                 float gm[8])
+{
+    const float co = dot(n, wo), ci = dot(n, wi);
+    if (co <= 0.0f || ci <= 0.0f) return;
+    const float r = m.rough;
+    const float a = alpha_of(r), a2 = a * a;
+    const float3 h = normalize(add(wo, wi));
+    const float cnh = dot(n, h), coh = dot(wo, h);
+    const float k = ggx_k(n, h, cnh, a2);  // d k / d cnh = 2 cnh (a^2 - 1)
+    const float D = a2 / (MR_PI * k * k);
+    const float Ao = smith_a(a2, co), Ai = smith_a(a2, ci);
+    const float den = ci * Ao + co * Ai;
+    const float vis = 0.5f / den;
+    const float om = 1.0f - coh;
+    const float w5 = (om * om) * (om * om) * om;
+    const float alb[3] = {m.alb.x, m.alb.y, m.alb.z};
+    const float g[3] = {gq.x, gq.y, gq.z};
+    float S = 0.0f, g_ci = 0.0f, g_m = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float kd = (1.0f - m.metal) * alb[c];
+        const float f0 = 0.04f * (1.0f - m.metal) + m.metal * alb[c];
+        const float F = f0 * (1.0f - w5) + w5;
+        const float gF = g[c] * D * vis * ci;
+        const float gkd = g[c] * ci * MR_INV_PI;
+        gm[c] += gkd * (1.0f - m.metal) + gF * (1.0f - w5) * m.metal;
+        g_m += -gkd * alb[c] + gF * (1.0f - w5) * (alb[c] - 0.04f);
+        S += g[c] * F;
+        g_ci += g[c] * (kd * MR_INV_PI + D * vis * F);  // the trailing cosine
+    }
+    const float gDV = S * ci;
+    const float gD = gDV * vis, gvis = gDV * D;
+    const float gden = gvis * (-0.5f / (den * den));
+    const float k3 = MR_PI * k * k * k;
+    float g_a = gD * (2.0f * a / (MR_PI * k * k) - 4.0f * a * a2 * cnh * cnh / k3);
+    const float g_cnh = gD * (-4.0f * a2 * cnh * (a2 - 1.0f) / k3);
+    g_ci += gden * (Ao + co * (1.0f - a2) * ci / Ai);
+    const float g_co = gden * (Ai + ci * (1.0f - a2) * co / Ao);
+    g_a += gden * (ci * a * (1.0f - co * co) / Ao + co * a * (1.0f - ci * ci) / Ai);
+    gm[3] += (r * r > 1e-3f) ? g_a * 2.0f * r : 0.0f;
+    gm[4] += g_m;
+    gm[5] += g_ci * wi.x + g_co * wo.x + g_cnh * h.x;
+    gm[6] += g_ci * wi.y + g_co * wo.y + g_cnh * h.y;
+    gm[7] += g_ci * wi.z + g_co * wo.z + g_cnh * h.z;
+}
+
+// Warp-aggregated scatter: lanes with the same key (>= 0) sum their NV values with a
+// butterfly and one lane issues the atomics; singletons add directly. All 32 lanes call.
+template <int NV, typename Emit>
+__device__ __forceinline__ void scatter_agg(int key, const float (&v)[NV], const Emit& emit)
+{
+    const int lane = lane_id();
+    const unsigned peers = __match_any_sync(MR_FULL, key);
+    const bool valid = key >= 0;
+    const bool single = __popc(peers) == 1;
+    if (valid && single) emit(key, v);
+    unsigned multi = __ballot_sync(MR_FULL, valid && !single && (__ffs(peers) - 1) == lane);
+    while (multi) {
+        const int l = __ffs(multi) - 1;
+        multi &= multi - 1;
+        const int kk = __shfl_sync(MR_FULL, key, l);
+        const bool mine = key == kk;
+        float s[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            float x = mine ? v[c] : 0.0f;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(MR_FULL, x, off);
+            s[c] = x;
+        }
+        if (lane == l) emit(kk, s);
+    }
+}
+
+struct EmitEnv {
+    float* g;
+    __device__ void operator()(int key, const float (&v)[3]) const
+    {
+        if (!g) return;
+        atomicAdd(g + 3 * (size_t)key, v[0]);
+        atomicAdd(g + 3 * (size_t)key + 1, v[1]);
+        atomicAdd(g + 3 * (size_t)key + 2, v[2]);
+    }
+};
+struct EmitTex {
+    float* ga;
+    float* gr;
+    float* gm;
+    __device__ void operator()(int key, const float (&v)[5]) const
+    {
+        if (ga) {
+            atomicAdd(ga + 3 * (size_t)key, v[0]);
+            atomicAdd(ga + 3 * (size_t)key + 1, v[1]);
+            atomicAdd(ga + 3 * (size_t)key + 2, v[2]);
+        }
+        if (gr) atomicAdd(gr + key, v[3]);
+        if (gm) atomicAdd(gm + key, v[4]);
+    }
+};
+struct EmitVert {
+    float* g;
+    __device__ void operator()(int key, const float (&v)[3]) const
+    {
+        if (!g) return;
+        atomicAdd(g + 3 * (size_t)key, v[0]);
+        atomicAdd(g + 3 * (size_t)key + 1, v[1]);
+        atomicAdd(g + 3 * (size_t)key + 2, v[2]);
+    }
+};
+
+__global__ void __launch_bounds__(256) k_backward(const SceneDev* __restrict__ scenes,
+                                                  const ViewDev* __restrict__ views, int n_views, uint64_t total,
+                                                  Rng rng, const float* const* __restrict__ d_images,
+                                                  const GradDev* __restrict__ grads, const void* tape,
+                                                  unsigned long long* counters)
+{
+    const TapeDev tp = tape_of(const_cast<void*>(tape), total);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t rounds = (total + stride - 1) / stride;
+    unsigned long long n_diff = 0;
+    for (uint64_t r = 0; r < rounds; ++r) {
+        const uint64_t g = r * stride + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+        const bool live = g < total;
+        int env_key = -1, tex_key[4] = {-1, -1, -1, -1}, vert_key[3] = {-1, -1, -1};
+        float env_v[3] = {0.f, 0.f, 0.f};
+        float tex_v[4][5];
+        float vert_v[3][3];
+        int scene_id = 0;
+        if (live) {
+            int vi;
+            const ViewDev& v = view_of(views, n_views, g, vi);
+            scene_id = v.scene;
+            const SceneDev s = scenes[v.scene];
+            const uint32_t sid = (uint32_t)(g - v.offset);
+            const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
+            const float* dimg = d_images[vi];
+            const float inv_spp = 1.0f / (float)v.spp;
+            const float3 gI = f3(dimg[3 * (size_t)pixel] * inv_spp, dimg[3 * (size_t)pixel + 1] * inv_spp,
+                                 dimg[3 * (size_t)pixel + 2] * inv_spp);
+            if (gI.x != 0.0f || gI.y != 0.0f || gI.z != 0.0f) {
+                ++n_diff;
+                const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+                const uint4 xc = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_CAMERA, 0u);
+                const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+                const float3 d = camera_dir(v, px, py, u24(xc.x), u24(xc.y));
+                const int tri = tp.tri[g];
+                if (tri < 0) {
+                    env_key = env_texel_of(s, d);
+                    env_v[0] = gI.x;
+                    env_v[1] = gI.y;
+                    env_v[2] = gI.z;
+                } else {
+                    float3 v0, e1, e2;
+                    int tchk;
+                    load_tri(s, __ldg(s.leaf_of + tri), v0, e1, e2, tchk);
+                    float t, u, vv;
+                    tri_solve(o, d, v0, e1, e2, t, u, vv);
+                    Shade sh;
+                    shade_at(s, tri, u, vv, d, sh);
+                    const float3 wo = f3(-d.x, -d.y, -d.z);
+                    const int env_ok = *s.env_ok_dev;
+                    float gm[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    const int cand = tp.cand[g];
+                    const float wv = tp.wv[g];
+                    if (cand >= 0 && wv != 0.0f) {
+                        const uint4 x = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_CANDIDATE, (uint32_t)cand);
+                        float3 y;
+                        int ytex;
+                        env_sample(s, x.x, x.y, x.w, y, ytex);
+                        const float3 fc = brdf_cos(sh.n, wo, y, sh.m);
+                        const float4 L = __ldg(s.env_texel + ytex);
+                        env_key = ytex;
+                        env_v[0] = gI.x * wv * fc.x;
+                        env_v[1] = gI.y * wv * fc.y;
+                        env_v[2] = gI.z * wv * fc.z;
+                        brdf_cos_adjoint(sh.n, wo, y, sh.m, f3(gI.x * wv * L.x, gI.y * wv * L.y, gI.z * wv * L.z), gm);
+                    }
+                    const float3 li = f3(tp.lind[0][g], tp.lind[1][g], tp.lind[2][g]);
+                    if (v.bounces > 1 && (li.x != 0.0f || li.y != 0.0f || li.z != 0.0f)) {
+                        const uint4 x = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_CONTINUE, 0u);
+                        float3 wc;
+                        const float pind = sample_continuation(s, env_ok, sh.n, wo, sh.m, x, wc);
+                        if (pind > 0.0f)
+                            brdf_cos_adjoint(sh.n, wo, wc, sh.m,
+                                             f3(gI.x * li.x / pind, gI.y * li.y / pind, gI.z * li.z / pind), gm);
+                    }
+                    // textures (bilinear) and the texture coordinate
+                    const Taps& tpz = sh.tp;
+                    float dt[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ti = tpz.idx[q];
+                        const float w = tpz.w[q];
+                        tex_key[q] = ti;
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) tex_v[q][c] = w * gm[c];
+                        dt[q] = gm[0] * __ldg(s.albedo + 3 * (size_t)ti) + gm[1] * __ldg(s.albedo + 3 * (size_t)ti + 1) +
+                                gm[2] * __ldg(s.albedo + 3 * (size_t)ti + 2) + gm[3] * __ldg(s.rough + ti) +
+                                gm[4] * __ldg(s.metal + ti);
+                    }
+                    // derivative of the bilinear lookup along the texture coordinate, as texel
+                    // differences (exactly zero across clamped or equal texels)
+                    const float gsu = (float)s.tw * ((1.0f - tpz.fy) * (dt[1] - dt[0]) + tpz.fy * (dt[3] - dt[2]));
+                    const float gsv = (float)s.th * ((1.0f - tpz.fx) * (dt[2] - dt[0]) + tpz.fx * (dt[3] - dt[1]));
+                    const float* uv = s.tri_uv + 6 * (size_t)tri;
+                    const float gu = gsu * (__ldg(uv + 2) - __ldg(uv + 0)) + gsv * (__ldg(uv + 3) - __ldg(uv + 1));
+                    const float gv = gsu * (__ldg(uv + 4) - __ldg(uv + 0)) + gsv * (__ldg(uv + 5) - __ldg(uv + 1));
+                    // (u, v) through the intersection: A = [e1 | e2 | -d], z = A^-T (gu, gv, 0)
+                    const float3 md = f3(-d.x, -d.y, -d.z);
+                    const float3 r0 = cross(e2, md), r1 = cross(md, e1);
+                    const float det = dot(e1, r0);
+                    const float3 z = mul(add(mul(r0, gu), mul(r1, gv)), 1.0f / det);
+                    const float bw[3] = {1.0f - u - vv, u, vv};
+                    float3 gvx[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) gvx[c] = mul(z, -bw[c]);
+                    // n = sign * N / |N|, N = e1 x e2
+                    const float Nl = sqrtf(dot(sh.N, sh.N));
+                    const float3 Nh = mul(sh.N, 1.0f / Nl);
+                    const float3 gNh = mul(f3(gm[5], gm[6], gm[7]), sh.sign);
+                    const float3 gN = mul(sub(gNh, mul(Nh, dot(Nh, gNh))), 1.0f / Nl);
+                    const float3 ge1 = cross(e2, gN), ge2 = cross(gN, e1);
+                    gvx[0] = sub(gvx[0], add(ge1, ge2));
+                    gvx[1] = add(gvx[1], ge1);
+                    gvx[2] = add(gvx[2], ge2);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int vid = __ldg(s.tris + 3 * (size_t)tri + c);
+                        vert_key[c] = (vid >= 0 && vid < s.n_verts) ? vid : -1;
+                        vert_v[c][0] = gvx[c].x;
+                        vert_v[c][1] = gvx[c].y;
+                        vert_v[c][2] = gvx[c].z;
+                    }
+                }
+            }
+        }
+        // scatters are keyed per scene; lanes of other scenes never share a key group
+        // because the key is combined with the scene id in the match
+        const GradDev gd = grads[scene_id];
+        const unsigned same_scene = __match_any_sync(MR_FULL, scene_id);
+        if (same_scene == MR_FULL) {
+            scatter_agg<3>(env_key, env_v, EmitEnv{gd.env});
+#pragma unroll
+            for (int q = 0; q < 4; ++q) scatter_agg<5>(tex_key[q], tex_v[q], EmitTex{gd.albedo, gd.rough, gd.metal});
+#pragma unroll
+            for (int c = 0; c < 3; ++c) scatter_agg<3>(vert_key[c], vert_v[c], EmitVert{gd.verts});
+        } else {
+            if (env_key >= 0) EmitEnv{gd.env}(env_key, env_v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (tex_key[q] >= 0) EmitTex{gd.albedo, gd.rough, gd.metal}(tex_key[q], tex_v[q]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (vert_key[c] >= 0) EmitVert{gd.verts}(vert_key[c], vert_v[c]);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) n_diff += __shfl_xor_sync(MR_FULL, n_diff, off);
+    if (lane_id() == 0 && n_diff) atomicAdd(counters + 4, n_diff);
+}
+
+// ---------------------------------------------------------------------------------------
+// L2 loss of Eq. (loss_pbr) and its image gradient
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_l2(const float* __restrict__ img, const float* __restrict__ ref, int64_t n,
+                                            float* __restrict__ dimg, float* loss)
+{
+    float acc = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = img[i] - ref[i];
+        if (dimg) dimg[i] = 2.0f * e;
+        acc += e * e;
+    }
+    if (!loss) return;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(MR_FULL, acc, off);
+    __shared__ float ws[8];
+    if (lane_id() == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+        atomicAdd(loss, s);
+    }
+}
+
+// add one chunk's queue counts to the cumulative counters: qcnt[2b] continuation rays
+// emitted at bounce b, qcnt[2b+1] shadow rays of bounce b
+__global__ void k_account(unsigned long long* counters, const unsigned int* __restrict__ qcnt, int bounces,
+                          uint64_t primary)
+{
+    if (threadIdx.x != 0) return;
+    unsigned long long cont = 0, shadow = 0;
+    for (int b = 0; b < bounces; ++b) {
+        cont += qcnt[2 * b];
+        shadow += qcnt[2 * b + 1];
+    }
+    counters[0] += primary;
+    counters[1] += cont;
+    counters[2] += shadow;
+}
+
+// ray queries for mirres_trace
+__global__ void __launch_bounds__(256) k_trace_rays(SceneDev s, const float* __restrict__ rays,
+                                                    const int32_t* __restrict__ skip, int64_t n, int any,
+                                                    int32_t* __restrict__ hit_tri, float* __restrict__ hit_tuv)
+{
+    extern __shared__ uint32_t sstk[];
+    const float tmin = *s.tmin_dev;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float3 o = f3(rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]);
+        const float3 d = f3(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5]);
+        const int sk = skip ? skip[i] : -1;
+        Hit h;
+        if (any) traverse<true>(s, o, d, sk, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x);
+        else traverse<false>(s, o, d, sk, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x);
+        hit_tri[i] = any ? (h.tri >= 0 ? 1 : -1) : h.tri;
+        if (hit_tuv && !any) {
+            hit_tuv[3 * i] = h.tri >= 0 ? h.t : 0.0f;
+            hit_tuv[3 * i + 1] = h.u;
+            hit_tuv[3 * i + 2] = h.v;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------------------
+static unsigned grid_cap(uint64_t n, int block, int cap)
+{
+    const uint64_t g = (n + block - 1) / block;
+    return (unsigned)(g < 1 ? 1 : (g > (uint64_t)cap ? (uint64_t)cap : g));
+}
+
+static size_t stack_bytes(int block) { return sizeof(uint32_t) * MR_SSTACK * (size_t)block; }
+
+void mr_launch_raygen(const ViewDev& v, Rng rng, uint32_t first, uint32_t n, const QueueDev& q, void* tape,
+                      uint64_t ntot, int sms, cudaStream_t st)
+{
+    k_raygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(v, rng, first, n, q, tape, ntot);
+}
+
+void mr_launch_trace(const SceneDev& s, const float4* qo, const float4* qd, const unsigned int* count,
+                     unsigned int count_fixed, uint64_t upper, float4* hits, bool any, int sms, cudaStream_t st)
+{
+    const unsigned grid = grid_cap(upper, 256, sms * 8);
+    if (any) k_trace<true><<<grid, 256, stack_bytes(256), st>>>(s, qo, qd, count, count_fixed, hits);
+    else k_trace<false><<<grid, 256, stack_bytes(256), st>>>(s, qo, qd, count, count_fixed, hits);
+}
+
+void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& qin,
+                     const unsigned int* count_in, unsigned int count_fixed, uint64_t upper, const float4* hits,
+                     const QueueDev& qout, unsigned int* count_out, const ShadowDev& sq, unsigned int* count_sh,
+                     void* tape, uint64_t ntot, int sms, cudaStream_t st)
+{
+    k_shade<<<grid_cap(upper, 256, sms * 8), 256, 0, st>>>(s, v, rng, b, M, qin, count_in, count_fixed, hits, qout,
+                                                          count_out, sq, count_sh, tape, ntot);
+}
+
+void mr_launch_shadow(const SceneDev& s, const ViewDev& v, int b, const ShadowDev& sq, const unsigned int* count,
+                      uint64_t upper, void* tape, uint64_t ntot, int sms, cudaStream_t st)
+{
+    k_shadow<<<grid_cap(upper, 256, sms * 8), 256, stack_bytes(256), st>>>(s, v, b, sq, count, tape, ntot);
+}
+
+void mr_launch_resolve(const ViewDev& v, const void* tape, uint64_t ntot, float* img, int sms, cudaStream_t st)
+{
+    k_resolve<<<grid_cap((uint64_t)v.width * v.height, 256, sms * 8), 256, 0, st>>>(v, tape, ntot, img);
+}
+
+cudaError_t mr_launch_persistent(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
+                                 int M, unsigned long long* work, uint32_t chunk, void* tape,
+                                 unsigned long long* counters, int block, int blocks, cudaStream_t st)
+{
+    const size_t smem = stack_bytes(block);
+    cudaError_t e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_persistent<<<blocks, block, smem, st>>>(scenes, views, n_views, total, rng, M, work, chunk, tape, counters);
+    return cudaGetLastError();
+}
+
+int mr_persistent_occupancy(int block)
+{
+    int n = 0;
+    cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stack_bytes(block));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent, block, stack_bytes(block)) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n < 1 ? 1 : n;
+}
+
+void mr_launch_resolve_all(const ViewDev* views, int n_views, const uint64_t* pix_off, uint64_t total_pix,
+                           float* const* images, const void* tape, uint64_t ntot, int sms, cudaStream_t st)
+{
+    k_resolve_all<<<grid_cap(total_pix, 256, sms * 8), 256, 0, st>>>(views, n_views, pix_off, total_pix, images, tape,
+                                                                     ntot);
+}
+
+void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
+                        const float* const* d_images, const GradDev* grads, const void* tape,
+                        unsigned long long* counters, int sms, cudaStream_t st)
+{
+    k_backward<<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng, d_images, grads,
+                                                             tape, counters);
+}
+
+void mr_launch_account(unsigned long long* counters, const unsigned int* qcnt, int bounces, uint64_t primary,
+                       cudaStream_t st)
+{
+    k_account<<<1, 32, 0, st>>>(counters, qcnt, bounces, primary);
+}
+
+void mr_launch_l2(const float* img, const float* ref, int64_t n, float* dimg, float* loss, int sms, cudaStream_t st)
+{
+    k_l2<<<grid_cap((uint64_t)n, 256, sms * 8), 256, 0, st>>>(img, ref, n, dimg, loss);
+}
+
+void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* skip, int64_t n, int any,
+                          int32_t* hit_tri, float* hit_tuv, int sms, cudaStream_t st)
+{
+    k_trace_rays<<<grid_cap((uint64_t)n, 256, sms * 8), 256, stack_bytes(256), st>>>(s, rays, skip, n, any, hit_tri,
+                                                                                     hit_tuv);
+}

@@ -1,0 +1,54 @@
+// render.h -- structures and launchers of the forward / adjoint kernels (host side).
+#pragma once
+
+#include "internal.h"
+
+// ray queue (SoA of float4): (o, origin triangle), (d, sample id), throughput, indirect throughput
+struct QueueDev {
+    float4* o;
+    float4* d;
+    float4* b;
+    float4* bi;
+};
+
+// shadow-ray queue: (o, origin triangle), (d, sample id), radiance to add, L_ind to add
+struct ShadowDev {
+    float4* o;
+    float4* d;
+    float4* add;
+    float4* addi;
+};
+
+struct GradDev {
+    float* albedo;
+    float* rough;
+    float* metal;
+    float* env;
+    float* verts;
+};
+
+void mr_launch_raygen(const ViewDev& v, Rng rng, uint32_t first, uint32_t n, const QueueDev& q, void* tape,
+                      uint64_t ntot, int sms, cudaStream_t st);
+void mr_launch_trace(const SceneDev& s, const float4* qo, const float4* qd, const unsigned int* count,
+                     unsigned int count_fixed, uint64_t upper, float4* hits, bool any, int sms, cudaStream_t st);
+void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& qin,
+                     const unsigned int* count_in, unsigned int count_fixed, uint64_t upper, const float4* hits,
+                     const QueueDev& qout, unsigned int* count_out, const ShadowDev& sq, unsigned int* count_sh,
+                     void* tape, uint64_t ntot, int sms, cudaStream_t st);
+void mr_launch_shadow(const SceneDev& s, const ViewDev& v, int b, const ShadowDev& sq, const unsigned int* count,
+                      uint64_t upper, void* tape, uint64_t ntot, int sms, cudaStream_t st);
+void mr_launch_resolve(const ViewDev& v, const void* tape, uint64_t ntot, float* img, int sms, cudaStream_t st);
+void mr_launch_account(unsigned long long* counters, const unsigned int* qcnt, int bounces, uint64_t primary,
+                       cudaStream_t st);
+cudaError_t mr_launch_persistent(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
+                                 int M, unsigned long long* work, uint32_t chunk, void* tape,
+                                 unsigned long long* counters, int block, int blocks, cudaStream_t st);
+int mr_persistent_occupancy(int block);
+void mr_launch_resolve_all(const ViewDev* views, int n_views, const uint64_t* pix_off, uint64_t total_pix,
+                           float* const* images, const void* tape, uint64_t ntot, int sms, cudaStream_t st);
+void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
+                        const float* const* d_images, const GradDev* grads, const void* tape,
+                        unsigned long long* counters, int sms, cudaStream_t st);
+void mr_launch_l2(const float* img, const float* ref, int64_t n, float* dimg, float* loss, int sms, cudaStream_t st);
+void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* skip, int64_t n, int any,
+                          int32_t* hit_tri, float* hit_tuv, int sms, cudaStream_t st);

@@ -1,0 +1,260 @@
+"""Thin Python binding of libmirres (include/mirres.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no arithmetic of the
+method: tensors are passed as device pointers, views / params as the C structs. Streams
+default to PyTorch's current stream. Importing this module never falls back to anything: if
+the shared library is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+__all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_view", "make_params",
+           "mirres_context_create", "mirres_context_destroy", "mirres_scene_create", "mirres_scene_destroy",
+           "mirres_bvh_build", "mirres_bvh_refit", "mirres_tape_bytes", "mirres_render", "mirres_backward",
+           "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
+           "mirres_reset_counters", "mirres_last_error", "library_path"]
+
+STATUS = {0: "MIRRES_OK", 1: "MIRRES_ERR_ARG", 2: "MIRRES_ERR_CUDA", 3: "MIRRES_ERR_OOM", 4: "MIRRES_ERR_TIMEOUT",
+          5: "MIRRES_ERR_STATE"}
+
+
+class MirresError(RuntimeError):
+    def __init__(self, call, status, message):
+        super().__init__(f"{call} -> {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("verts", C.c_void_p), ("n_verts", C.c_int32), ("tris", C.c_void_p), ("n_tris", C.c_int32),
+                ("tri_uv", C.c_void_p), ("albedo", C.c_void_p), ("roughness", C.c_void_p),
+                ("metallic", C.c_void_p), ("tex_w", C.c_int32), ("tex_h", C.c_int32), ("env", C.c_void_p),
+                ("env_w", C.c_int32), ("env_h", C.c_int32)]
+
+
+class View(C.Structure):
+    _fields_ = [("K", C.c_float * 4), ("c2w", C.c_float * 12), ("width", C.c_int32), ("height", C.c_int32),
+                ("spp", C.c_int32), ("bounces", C.c_int32), ("scene", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("ris_m", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("grad_mode", C.c_int32),
+                ("launch", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class Grads(C.Structure):
+    _fields_ = [("albedo", C.c_void_p), ("roughness", C.c_void_p), ("metallic", C.c_void_p), ("env", C.c_void_p),
+                ("verts", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libmirres.so is not built (run __graft_entry__.build()); there is no fallback")
+            L = C.CDLL(_build.LIB)
+            vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+            st = C.c_int
+            sig = {
+                "mirres_context_create": (st, [i32, C.POINTER(vp)]),
+                "mirres_context_destroy": (st, [vp]),
+                "mirres_scene_create": (st, [vp, C.POINTER(SceneDesc), C.POINTER(vp)]),
+                "mirres_scene_destroy": (st, [vp]),
+                "mirres_bvh_build": (st, [vp, vp]),
+                "mirres_bvh_refit": (st, [vp, vp]),
+                "mirres_tape_bytes": (sz, [C.POINTER(View), i32]),
+                "mirres_render": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
+                                       C.POINTER(vp), vp, sz, vp]),
+                "mirres_backward": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
+                                         C.POINTER(vp), vp, sz, C.POINTER(Grads), vp]),
+                "mirres_l2_loss": (st, [vp, vp, i64, vp, vp, vp]),
+                "mirres_trace": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
+                "mirres_bvh_export": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
+                "mirres_env_export": (st, [vp, vp, vp, vp, vp, vp]),
+                "mirres_get_counters": (st, [vp, C.POINTER(C.c_uint64)]),
+                "mirres_reset_counters": (st, [vp]),
+                "mirres_last_error": (C.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def mirres_last_error() -> str:
+    return lib().mirres_last_error().decode()
+
+
+def _check(call, status):
+    if status != 0:
+        raise MirresError(call, status, mirres_last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _check("mirres_context_destroy", lib().mirres_context_destroy(self.handle))
+            self.handle = None
+
+
+class Scene:
+    """A scene handle plus references to the borrowed tensors (kept alive here)."""
+
+    def __init__(self, ctx, handle, tensors):
+        self.ctx = ctx
+        self.handle = handle
+        self.tensors = tensors
+
+    def close(self):
+        if self.handle:
+            _check("mirres_scene_destroy", lib().mirres_scene_destroy(self.handle))
+            self.handle = None
+
+
+def make_view(K, c2w, width, height, spp, bounces, scene=0) -> View:
+    return View((C.c_float * 4)(*[float(x) for x in K]), (C.c_float * 12)(*[float(x) for x in c2w]), int(width),
+                int(height), int(spp), int(bounces), int(scene))
+
+
+def make_params(ris_m, seed=0, launch=0, block=0, blocks_per_sm=0, grad_mode=0) -> Params:
+    return Params(int(ris_m), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(grad_mode), int(launch), int(block),
+                  int(blocks_per_sm), 0)
+
+
+def _views(views):
+    arr = (View * len(views))()
+    for i, v in enumerate(views):
+        arr[i] = v if isinstance(v, View) else make_view(v.K, v.c2w, v.width, v.height, v.spp, v.bounces,
+                                                         getattr(v, "scene", 0))
+    return arr
+
+
+def mirres_context_create(device: int = 0) -> Context:
+    h = C.c_void_p()
+    _check("mirres_context_create", lib().mirres_context_create(int(device), C.byref(h)))
+    return Context(h, device)
+
+
+def mirres_context_destroy(ctx: Context):
+    ctx.close()
+
+
+def mirres_scene_create(ctx: Context, verts, tris, tri_uv, albedo, roughness, metallic, env) -> Scene:
+    ts = dict(verts=verts, tris=tris, tri_uv=tri_uv, albedo=albedo, roughness=roughness, metallic=metallic, env=env)
+    for k, t in ts.items():
+        want = torch.int32 if k == "tris" else torch.float32
+        if t.dtype != want:
+            raise ValueError(f"{k} must be {want}")
+    d = SceneDesc(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(tri_uv), _ptr(albedo),
+                  _ptr(roughness), _ptr(metallic), albedo.shape[1], albedo.shape[0], _ptr(env), env.shape[1],
+                  env.shape[0])
+    h = C.c_void_p()
+    _check("mirres_scene_create", lib().mirres_scene_create(ctx.handle, C.byref(d), C.byref(h)))
+    return Scene(ctx, h, ts)
+
+
+def mirres_scene_destroy(scene: Scene):
+    scene.close()
+
+
+def mirres_bvh_build(scene: Scene, stream=None):
+    _check("mirres_bvh_build", lib().mirres_bvh_build(scene.handle, _stream(stream)))
+
+
+def mirres_bvh_refit(scene: Scene, stream=None):
+    _check("mirres_bvh_refit", lib().mirres_bvh_refit(scene.handle, _stream(stream)))
+
+
+def mirres_tape_bytes(views) -> int:
+    vs = _views(views)
+    return int(lib().mirres_tape_bytes(vs, len(vs)))
+
+
+def mirres_render(ctx: Context, scenes, views, params: Params, images, tape=None, stream=None):
+    vs = _views(views)
+    sc = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    im = (C.c_void_p * len(images))(*[_ptr(t).value for t in images])
+    nbytes = 0 if tape is None else tape.numel() * tape.element_size()
+    _check("mirres_render", lib().mirres_render(ctx.handle, sc, len(scenes), vs, len(vs), C.byref(params), im,
+                                                _ptr(tape), nbytes, _stream(stream)))
+
+
+def mirres_backward(ctx: Context, scenes, views, params: Params, d_images, tape, grads, stream=None):
+    """grads: list (one per scene) of dicts with optional albedo/roughness/metallic/env/verts tensors."""
+    vs = _views(views)
+    sc = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    di = (C.c_void_p * len(d_images))(*[_ptr(t).value for t in d_images])
+    ga = (Grads * len(scenes))()
+    for i, g in enumerate(grads):
+        ga[i] = Grads(*[_ptr(g.get(k)) for k in ("albedo", "roughness", "metallic", "env", "verts")])
+    nbytes = tape.numel() * tape.element_size()
+    _check("mirres_backward", lib().mirres_backward(ctx.handle, sc, len(scenes), vs, len(vs), C.byref(params), di,
+                                                    _ptr(tape), nbytes, ga, _stream(stream)))
+
+
+def mirres_l2_loss(image, ref, d_image=None, loss=None, stream=None):
+    _check("mirres_l2_loss", lib().mirres_l2_loss(_ptr(image), _ptr(ref), image.numel(), _ptr(d_image), _ptr(loss),
+                                                  _stream(stream)))
+
+
+def mirres_trace(ctx: Context, scene: Scene, rays, hit_tri, hit_tuv=None, skip=None, any_hit=False, stream=None):
+    _check("mirres_trace", lib().mirres_trace(ctx.handle, scene.handle, _ptr(rays), _ptr(skip), rays.shape[0],
+                                              1 if any_hit else 0, _ptr(hit_tri), _ptr(hit_tuv), _stream(stream)))
+
+
+def mirres_bvh_export(scene: Scene, keys=None, left=None, right=None, parent=None, lo=None, hi=None, stream=None):
+    _check("mirres_bvh_export", lib().mirres_bvh_export(scene.handle, _ptr(keys), _ptr(left), _ptr(right),
+                                                        _ptr(parent), _ptr(lo), _ptr(hi), _stream(stream)))
+
+
+def mirres_env_export(scene: Scene, marg=None, cond=None, texel=None, total=None, stream=None):
+    _check("mirres_env_export", lib().mirres_env_export(scene.handle, _ptr(marg), _ptr(cond), _ptr(texel),
+                                                        _ptr(total), _stream(stream)))
+
+
+def mirres_get_counters(ctx: Context):
+    out = (C.c_uint64 * 8)()
+    _check("mirres_get_counters", lib().mirres_get_counters(ctx.handle, out))
+    return [int(x) for x in out]
+
+
+def mirres_reset_counters(ctx: Context):
+    _check("mirres_reset_counters", lib().mirres_reset_counters(ctx.handle))

@@ -1,0 +1,122 @@
+"""PyTorch-facing helpers over the C ABI: device-resident scenes and an autograd Function.
+
+PyTorch supplies device memory and streams only; every step of the path runs in libmirres.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import mirres as M
+
+
+def _dev(a, dtype, device):
+    return torch.as_tensor(a).to(device=device, dtype=dtype).contiguous()
+
+
+class DeviceScene:
+    """Scene inputs as CUDA tensors plus the library scene handle (LBVH and env tables built)."""
+
+    def __init__(self, ctx: M.Context, scene, device="cuda"):
+        self.device = torch.device(device)
+        self.verts = _dev(scene.verts, torch.float32, self.device)
+        self.tris = _dev(scene.tris, torch.int32, self.device)
+        self.tri_uv = _dev(scene.tri_uv, torch.float32, self.device)
+        self.albedo = _dev(scene.albedo, torch.float32, self.device)
+        self.roughness = _dev(scene.roughness, torch.float32, self.device)
+        self.metallic = _dev(scene.metallic, torch.float32, self.device)
+        self.env = _dev(scene.env, torch.float32, self.device)
+        self.handle = M.mirres_scene_create(ctx, self.verts, self.tris, self.tri_uv, self.albedo, self.roughness,
+                                            self.metallic, self.env)
+        M.mirres_bvh_build(self.handle)
+        self._versions = self._param_versions()
+
+    def _param_versions(self):
+        return (self.verts._version, self.env._version)
+
+    def refresh(self):
+        """Refit the LBVH and rebuild the env tables if vertices or env changed in place."""
+        v = self._param_versions()
+        if v != self._versions:
+            M.mirres_bvh_refit(self.handle)
+            self._versions = v
+
+    def params(self):
+        return dict(albedo=self.albedo, roughness=self.roughness, metallic=self.metallic, env=self.env,
+                    verts=self.verts)
+
+    def close(self):
+        self.handle.close()
+
+
+class GpuWorkload:
+    """A synthetic workload resident on one GPU."""
+
+    def __init__(self, workload, device=0, ctx=None):
+        self.workload = workload
+        self.ctx = ctx or M.mirres_context_create(device)
+        self.device = torch.device("cuda", device)
+        self.scenes = [DeviceScene(self.ctx, s, self.device) for s in workload.scenes]
+        self.views = list(workload.views)
+        self.samples = workload.samples
+
+    def new_images(self):
+        return [torch.empty((v.height, v.width, 3), device=self.device, dtype=torch.float32) for v in self.views]
+
+    def new_tape(self):
+        n = M.mirres_tape_bytes(self.views)
+        return torch.empty(n // 4, device=self.device, dtype=torch.int32)
+
+    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0):
+        s = self.workload.seed if seed is None else seed
+        return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm)
+
+    def render(self, launch=0, images=None, tape=None, seed=None, block=0, blocks_per_sm=0, stream=None):
+        images = images if images is not None else self.new_images()
+        tape = tape if tape is not None else self.new_tape()
+        M.mirres_render(self.ctx, [s.handle for s in self.scenes], self.views,
+                        self.params(launch, seed, block, blocks_per_sm), images, tape, stream)
+        return images, tape
+
+    def zero_grads(self):
+        out = []
+        for s in self.scenes:
+            out.append({k: torch.zeros_like(t) for k, t in s.params().items()})
+        return out
+
+    def backward(self, d_images, tape, grads=None, launch=0, seed=None, stream=None):
+        grads = grads if grads is not None else self.zero_grads()
+        M.mirres_backward(self.ctx, [s.handle for s in self.scenes], self.views, self.params(launch, seed),
+                          d_images, tape, grads, stream)
+        return grads
+
+    def close(self):
+        for s in self.scenes:
+            s.close()
+        self.ctx.close()
+
+
+class MirresRender(torch.autograd.Function):
+    """images = MirresRender.apply(gw, launch, seed, albedo, roughness, metallic, env, verts)
+
+    The parameter tensors must be the ones the GpuWorkload's single scene borrows (updated in
+    place by the optimiser). Backward is the PRIMARY-mode adjoint of the paper (indirect rays
+    detached), replayed from the tape the forward wrote.
+    """
+
+    @staticmethod
+    def forward(ctx, gw, launch, seed, albedo, roughness, metallic, env, verts):
+        scene = gw.scenes[0]
+        for name, t in dict(albedo=albedo, roughness=roughness, metallic=metallic, env=env, verts=verts).items():
+            if t.data_ptr() != getattr(scene, name).data_ptr():
+                raise ValueError(f"{name} is not the tensor the scene borrows")
+        scene.refresh()
+        images, tape = gw.render(launch=launch, seed=seed)
+        ctx.gw, ctx.launch, ctx.seed, ctx.tape = gw, launch, seed, tape
+        return torch.stack(images) if len(images) > 1 else images[0].unsqueeze(0)
+
+    @staticmethod
+    def backward(ctx, grad_images):
+        gw = ctx.gw
+        d = [grad_images[i].contiguous() for i in range(grad_images.shape[0])]
+        g = gw.backward(d, ctx.tape, launch=ctx.launch, seed=ctx.seed)[0]
+        return None, None, None, g["albedo"], g["roughness"], g["metallic"], g["env"], g["verts"]
