@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the MIRReS stage-2 hot path on one GB300 (or N independent replicas).
+
+One step = one pass of the whole path over the workload: LBVH build (Morton codes, radix
+sort, hierarchy, boxes) and env sampling tables, the forward render of every view, the L2
+image loss against reference images and the adjoint (PRIMARY mode) into the gradients of
+textures, env map and vertices. Metric: forward+backward path samples per second (one path
+sample = one pixel sample of one view), for the batched persistent launch (the headline
+value) and for the plain per-view wavefront launch; Mrays/s alongside.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config3|config5|config2]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores, bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd path-samples/s (batched persistent launch; plain per-view launch and Mrays/s alongside)"
+UNIT = "path-samples/s"
+
+
+def make_workload(name, views=None):
+    from paper_2406_16360_gb300 import synth
+    if name == "config3":
+        return synth.config3() if views is None else synth.config3(n_views=views)
+    if name == "config2":
+        return synth.config2()
+    if name == "config5":
+        return synth.config5() if views is None else synth.config5(n_scenes=views)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(w, name):
+    sc = w.scenes[0]
+    v = w.views[0]
+    cfg = {"workload": w.name, "views": len(w.views), "scenes": len(w.scenes),
+           "triangles": int(sum(s.n_tris for s in w.scenes)), "ris_m": w.ris_m,
+           "samples_per_step": int(w.samples)}
+    if name != "config5":
+        cfg.update({"resolution": f"{v.width}x{v.height}", "spp": v.spp, "bounces": v.bounces,
+                    "texture": f"{sc.albedo.shape[1]}x{sc.albedo.shape[0]}",
+                    "env": f"{sc.env.shape[1]}x{sc.env.shape[0]}"})
+    return cfg
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------------------
+def oracle_sample(w, target_seconds, threads):
+    """fwd+bwd of the oracle on a bounded set of pixels of view 0 (all spp, all bounces)."""
+    import numpy as np
+    from oracle import oracle as O
+    v = w.views[0]
+    osc = O.OracleScene(w.scenes[v.scene])
+    rng = np.random.Generator(np.random.PCG64(77))
+    n_all = v.width * v.height
+
+    def run(npix):
+        pix = np.sort(rng.choice(n_all, size=npix, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        r = O.render(osc, v, 0, w.ris_m, seed=w.seed, pixels=pix, threads=threads, margins=False)
+        g = O.backward(osc, v, 0, w.ris_m, np.ones((npix, 3)), seed=w.seed, pixels=pix, threads=threads,
+                       want_abs=False)
+        dt = time.perf_counter() - t0
+        return dt, r["counts"], npix * v.spp
+
+    dt, _, _ = run(max(threads * 2, 32))
+    per_px = dt / max(threads * 2, 32)
+    npix = int(min(n_all, max(threads * 4, target_seconds / max(per_px, 1e-9))))
+    return osc, run, npix
+
+
+def cpu_baseline(w, seconds=15.0):
+    threads = os.cpu_count() or 1
+    osc, run, npix = oracle_sample(w, seconds, threads)
+    dt, counts, samples = run(npix)
+    v = w.views[0]
+    return {"value": samples / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"fwd+bwd of {npix} random pixels of view 0 ({v.width}x{v.height}, {v.spp} spp, "
+                      f"{v.bounces} bounces, M={w.ris_m}), {samples} path samples in {dt:.1f} s"}, counts, samples
+
+
+def run_reference(args):
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    w = make_workload(args.workload, args.views)
+    threads = os.cpu_count() or 1
+    osc, run, npix = oracle_sample(w, args.ref_seconds, threads)
+    for _ in range(args.warmup):
+        run(npix)
+    tot_t, tot_s = 0.0, 0
+    for _ in range(args.steps):
+        dt, _, s = run(npix)
+        tot_t += dt
+        tot_s += s
+    value = tot_s / tot_t
+    v = w.views[0]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, args.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step: fwd+bwd of {npix} random pixels of view 0 "
+                                       f"({v.width}x{v.height}, {v.spp} spp)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="config3", choices=["config3", "config5", "config2"])
+    ap.add_argument("--views", type=int, default=None, help="override the view / scene count (smaller runs)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-launch arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mine":
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_16360_gb300 import mirres as M
+    from paper_2406_16360_gb300.renderer import GpuWorkload
+
+    w = make_workload(args.workload, args.views)
+    gw = GpuWorkload(w, local)
+    samples = w.samples
+    stream = torch.cuda.current_stream()
+    scenes = [s.handle for s in gw.scenes]
+    images = gw.new_images()
+    tape = gw.new_tape()
+    grads = gw.zero_grads()
+    # reference images: the same scene rendered with another seed
+    refs, _ = gw.render(launch=1, seed=w.seed + 1, tape=tape)
+    refs = [r.clone() for r in refs]
+    d_images = [torch.empty_like(r) for r in refs]
+    loss = torch.zeros(1, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(launch, ev_render=None):
+        for s in gw.scenes:
+            M.mirres_bvh_build(s.handle)
+        if ev_render is not None:
+            ev_render[0].record()
+        M.mirres_render(gw.ctx, scenes, gw.views, gw.params(launch, block=args.block,
+                                                            blocks_per_sm=args.blocks_per_sm), images, tape)
+        if ev_render is not None:
+            ev_render[1].record()
+        for img, ref, d in zip(images, refs, d_images):
+            M.mirres_l2_loss(img, ref, d, loss)
+        M.mirres_backward(gw.ctx, scenes, gw.views, gw.params(launch), d_images, tape, grads)
+
+    def zero():
+        for g in grads:
+            for t in g.values():
+                t.zero_()
+        loss.zero_()
+
+    def timed(launch, steps, warmup):
+        for _ in range(warmup):
+            zero()
+            step(launch)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        c0 = M.mirres_get_counters(gw.ctx)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))  # evict L2 between timed steps (outside the timed window)
+            zero()
+            evs[i][0].record()
+            step(launch, evr[i])
+            evs[i][1].record()
+        torch.cuda.synchronize()
+        barrier()
+        c1 = M.mirres_get_counters(gw.ctx)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        ms_render = sum(a.elapsed_time(b) for a, b in evr)
+        rays = (c1[0] - c0[0]) + (c1[1] - c0[1]) + (c1[2] - c0[2])
+        launches = c1[6] - c0[6]
+        return ms, ms_render, rays, launches, [c1[k] - c0[k] for k in range(8)]
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_b, msr_b, rays_b, launches_b, cnt_b = timed(1, args.steps, args.warmup)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms_b], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_b = float(t.item())
+    plain = None
+    if not args.no_plain:
+        ms_p, msr_p, rays_p, launches_p, _ = timed(0, args.steps, args.warmup)
+        if world > 1:
+            t = torch.tensor([ms_p], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_p = float(t.item())
+        plain = {"value": world * samples * args.steps / (ms_p / 1e3), "ms_per_step": ms_p / args.steps,
+                 "mrays_per_s": world * rays_p / (ms_p / 1e3) / 1e6, "render_ms_per_step": msr_p / args.steps,
+                 "gpu_launches": launches_p}
+
+    # end to end: host parameters and reference images in pinned memory, copies in the timed region
+    host_params = [{k: t.detach().cpu().pin_memory() for k, t in s.params().items()} for s in gw.scenes]
+    host_refs = [r.cpu().pin_memory() for r in refs]
+    host_grads = [{k: torch.empty(t.shape, dtype=t.dtype).pin_memory() for k, t in g.items()} for g in grads]
+    host_loss = torch.empty(1).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for hp in host_params for t in hp.values()) + \
+        sum(t.numel() * t.element_size() for t in host_refs)
+    d2h = sum(t.numel() * t.element_size() for hg in host_grads for t in hg.values()) + 4
+
+    def e2e_step():
+        for s, hp in zip(gw.scenes, host_params):
+            for k, t in s.params().items():
+                t.copy_(hp[k], non_blocking=True)
+        for r, hr in zip(refs, host_refs):
+            r.copy_(hr, non_blocking=True)
+        zero()
+        step(1)
+        for g, hg in zip(grads, host_grads):
+            for k in g:
+                hg[k].copy_(g[k], non_blocking=True)
+        host_loss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(1):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    value = world * samples * args.steps / (ms_b / 1e3)
+    mrays = world * rays_b / (ms_b / 1e3) / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}",
+                           l2="flushed between timed steps (512 MiB write) and each step writes > 40 GB"),
+            "mrays_per_s": mrays, "render_ms_per_step": msr_b / args.steps,
+            "batched": {"value": value, "ms_per_step": ms_b / args.steps, "mrays_per_s": mrays},
+            "plain": plain,
+            "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
+            "counters_per_step": {"primary_rays": cnt_b[0] // args.steps, "continuation_rays": cnt_b[1] // args.steps,
+                                  "shadow_rays": cnt_b[2] // args.steps, "ris_candidates": cnt_b[5] // args.steps,
+                                  "samples_differentiated": cnt_b[4] // args.steps},
+            "gpu_launches": launches_b,
+            "clocks": clk,
+            "e2e": {"value": world * samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+
+    # roofline of the dominant kernel (the persistent forward): FP32 ALU bound, algorithmic FLOPs
+    # per path sample from the oracle's instrumented traversal and candidate counts
+    if rank == 0 and not args.no_cpu:
+        cb, counts, osamples = cpu_baseline(w)
+        line["cpu_baseline"] = cb
+        sc0 = w.scenes[0]
+        env_bits = math.log2(sc0.env.shape[0] * sc0.env.shape[1])
+        flops_per_sample = (counts[3] * 12 + counts[4] * 27 + counts[5] * (60 + 2 * env_bits)) / max(counts[6], 1)
+        render_s = msr_b / args.steps / 1e3
+        achieved = flops_per_sample * samples / render_s / 1e12
+        peak = 152 * 128 * 2 * 2.070e9 / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "kernel": "k_persistent (forward, batched)",
+                            "flops_per_sample": flops_per_sample,
+                            "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock), non-tensor"}
+    if rank == 0:
+        print(json.dumps(line))
+    gw.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
