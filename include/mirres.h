@@ -162,6 +162,34 @@ mirres_status mirres_render(mirres_context* ctx, mirres_scene* const* scenes, in
                             const mirres_view* views, int32_t n_views, const mirres_params* params,
                             float* const* images, void* tape, size_t tape_bytes, void* stream);
 
+/* ---- forward without device allocation ------------------------------------------------ */
+
+#define MIRRES_NOALLOC_SCRATCH_BYTES (512u * 1024u) /* static scratch per GPU, held until exit */
+#define MIRRES_NOALLOC_MAX_VIEWS 4096
+#define MIRRES_NOALLOC_MAX_SCENES 256
+
+/* The paper has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory while they render: for example a process whose device memory is entirely
+ * reserved by another allocator (a framework's caching allocator), or a latency-critical
+ * serving loop that must not pay the device-wide synchronisation cudaMalloc / cudaFree can
+ * bring. It runs the batched persistent forward of mirres_render (launch = 1; the launch
+ * field is ignored) with the same results, but keeps its scratch -- the per-call view,
+ * scene and image tables and the work counter -- in one static device array of
+ * MIRRES_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process
+ * exits. It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - The tape is required (caller-owned, mirres_tape_bytes(views) bytes, 16-byte aligned).
+ *   - n_views > MIRRES_NOALLOC_MAX_VIEWS or n_scenes > MIRRES_NOALLOC_MAX_SCENES is rejected
+ *     with MIRRES_ERR_ARG and a message naming the limit; all scenes share one context.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture begins.
+ *   - Every call shares the one array, which keeps the last call's contents; the call resets
+ *     what must start at zero (the work counter). Calls whose work overlaps on the GPU (on
+ *     different streams, or from several host threads without ordering) race on the array:
+ *     serialise them. */
+mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int32_t n_scenes, const mirres_view* views,
+                                    int32_t n_views, const mirres_params* params, float* const* images,
+                                    void* tape, size_t tape_bytes, void* stream);
+
 /* Adjoint, PRIMARY mode (Sec. 4.2: gradients of indirect rays detached; Appendix C: no
  * gradients of non-primary rays): for every sample, the primary vertex is replayed from the
  * tape and the random stream, and the derivatives of direct_1 + beta_1 * L_ind (RIS weight,

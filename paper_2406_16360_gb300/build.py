@@ -1,6 +1,6 @@
 """Build libmirres.so in-tree with nvcc for sm_103a (GB300).
 
-Four translation units are compiled in parallel and linked into one shared library with the
+The translation units are compiled in parallel and linked into one shared library with the
 CUDA runtime linked dynamically (the process shares one runtime with PyTorch).
 """
 from __future__ import annotations
@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmirres.so")
-UNITS = ["abi.cu", "bvh.cu", "env.cu", "render.cu"]
+UNITS = ["abi.cu", "bvh.cu", "env.cu", "render.cu", "noalloc.cu"]
 HEADERS = ["device.cuh", "internal.h", "render.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

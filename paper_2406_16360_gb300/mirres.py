@@ -17,9 +17,15 @@ from . import build as _build
 
 __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_view", "make_params",
            "mirres_context_create", "mirres_context_destroy", "mirres_scene_create", "mirres_scene_destroy",
-           "mirres_bvh_build", "mirres_bvh_refit", "mirres_tape_bytes", "mirres_render", "mirres_backward",
+           "mirres_bvh_build", "mirres_bvh_refit", "mirres_tape_bytes", "mirres_render", "mirres_render_noalloc",
+           "mirres_backward",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
+
+# limits of mirres_render_noalloc (include/mirres.h)
+MIRRES_NOALLOC_SCRATCH_BYTES = 512 * 1024
+MIRRES_NOALLOC_MAX_VIEWS = 4096
+MIRRES_NOALLOC_MAX_SCENES = 256
 
 STATUS = {0: "MIRRES_OK", 1: "MIRRES_ERR_ARG", 2: "MIRRES_ERR_CUDA", 3: "MIRRES_ERR_OOM", 4: "MIRRES_ERR_TIMEOUT",
           5: "MIRRES_ERR_STATE"}
@@ -81,6 +87,8 @@ def lib():
                 "mirres_tape_bytes": (sz, [C.POINTER(View), i32]),
                 "mirres_render": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
                                        C.POINTER(vp), vp, sz, vp]),
+                "mirres_render_noalloc": (st, [C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
+                                               C.POINTER(vp), vp, sz, vp]),
                 "mirres_backward": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
                                          C.POINTER(vp), vp, sz, C.POINTER(Grads), vp]),
                 "mirres_l2_loss": (st, [vp, vp, i64, vp, vp, vp]),
@@ -215,6 +223,15 @@ def mirres_render(ctx: Context, scenes, views, params: Params, images, tape=None
     nbytes = 0 if tape is None else tape.numel() * tape.element_size()
     _check("mirres_render", lib().mirres_render(ctx.handle, sc, len(scenes), vs, len(vs), C.byref(params), im,
                                                 _ptr(tape), nbytes, _stream(stream)))
+
+
+def mirres_render_noalloc(scenes, views, params: Params, images, tape, stream=None):
+    vs = _views(views)
+    sc = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    im = (C.c_void_p * len(images))(*[_ptr(t).value for t in images])
+    nbytes = 0 if tape is None else tape.numel() * tape.element_size()
+    _check("mirres_render_noalloc", lib().mirres_render_noalloc(sc, len(scenes), vs, len(vs), C.byref(params), im,
+                                                                _ptr(tape), nbytes, _stream(stream)))
 
 
 def mirres_backward(ctx: Context, scenes, views, params: Params, d_images, tape, grads, stream=None):
