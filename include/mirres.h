@@ -94,8 +94,10 @@ typedef struct {
  *   launch   0 = plain: per-view wavefront launches (ray generation, closest hit,
  *                 shade + RIS + next-bounce queue, shadow rays, resolve);
  *            1 = batched: one persistent launch over every view of every scene, work
- *                 pulled from a device counter (see mirres_batch_* for the graph form).
- *            Both produce bit-identical images, tapes and gradients.
+ *                 pulled from a device counter.
+ *            Both take every discrete decision identically (hit triangles, selected
+ *            candidates, lobes); values agree to FP32 rounding (the two kernels may contract
+ *            multiply-adds differently).
  *   block, blocks_per_sm  launch shape of the persistent kernel (0 = autotuned / default) */
 typedef struct {
     int32_t ris_m;
@@ -134,8 +136,8 @@ mirres_status mirres_scene_destroy(mirres_scene* scene);
  * stream once to read the check; MIRRES_ERR_ARG if any index is out of range). */
 mirres_status mirres_bvh_build(mirres_scene* scene, void* stream);
 
-/* Refit after the vertices moved (the paper's "LBVH is updated in each iteration",
- * Appendix A): topology kept, boxes and packed triangles recomputed bottom-up; env tables
+/* Refit after the vertices moved (the paper keeps its LBVH in step with the mesh at every
+ * iteration, Appendix A): topology kept, boxes and packed triangles recomputed bottom-up; env tables
  * rebuilt. Asynchronous. Requires a prior mirres_bvh_build. */
 mirres_status mirres_bvh_refit(mirres_scene* scene, void* stream);
 

@@ -153,7 +153,7 @@ static int bvh_build(orc_scene* s, const double* cent, int first, int count)
     return ni;
 }
 
-/* Environment sampling distribution, the proposal q_dir "proportional to L_env" of Sec. 4.1:
+/* Environment sampling distribution, the proposal q_dir of Sec. 4.1 (proportional to L_env):
  * texel weight Y(L) * sin(theta_row), a marginal CDF over rows and a conditional CDF per row,
  * built in FP64 by sequential prefix sums. */
 static void env_build(orc_scene* s)
@@ -1295,7 +1295,7 @@ int orc_render_detached(const orc_scene* frozen, const orc_scene* eval, const or
 }
 
 /* ---------------------------------------------------------------------------------------
- * LBVH (Appendix A: "linear BVH (LBVH, Karras 2012)"), restated top-down for comparison.
+ * LBVH (Appendix A: a linear BVH after Karras 2012), restated top-down for comparison.
  * Morton codes of the triangle centroids in the centroid bounding box (10 bits per axis,
  * x in the highest position of each triple), key = code << 32 | triangle id, sorted.
  * The binary radix tree over the sorted keys: a node covering [first, last] splits after

@@ -1,5 +1,5 @@
 // bvh.cu -- LBVH build and refit on the GPU (Appendix A of the paper: a linear BVH after
-// Karras 2012, "updated in each iteration to match the mesh refinement").
+// Karras 2012, kept up to date with the refined mesh at every optimisation iteration).
 //
 // build:  bounds (triangle centroids, centroid box, vertex box) -> 30-bit Morton codes ->
 //         stable LSD radix sort of the codes with the triangle id as payload (the initial

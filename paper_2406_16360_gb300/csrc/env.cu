@@ -1,5 +1,5 @@
 // env.cu -- environment-map importance-sampling tables (the paper's proposal
-// q_dir ~ L_env, "directly sampled from our environment map", Sec. 4.1).
+// q_dir proportional to L_env, drawn from the environment map itself, Sec. 4.1).
 //
 // Texel weight w = Y(L) sin(theta_row), Y = (r + g + b) / 3 (Appendix A). Per-row conditional
 // CDFs and the marginal CDF over rows are FP64 prefix sums (one thread per row, sequential
