@@ -50,6 +50,11 @@ SceneDev mr_scene_dev(const mirres_scene* s)
     d.env_texel = s->env_texel;
     d.env_marg = s->env_marg;
     d.env_cond = s->env_cond;
+    d.env_gmarg = s->env_gmarg;
+    d.env_gcond = s->env_gcond;
+    d.gm_shift = s->gm_shift;
+    d.gc_shift = s->gc_shift;
+    d.gc = s->gc;
     d.n_tris = s->desc.n_tris;
     d.n_verts = s->desc.n_verts;
     d.tw = s->desc.tex_w;
@@ -321,7 +326,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     plan.take<float*>((size_t)n_views);
     plan.take<uint64_t>((size_t)n_views);
     plan.take<unsigned long long>(1);
-    if (!batched) plan.take<float4>(13ull * chunk);
+    if (!batched) plan.take<float4>(16ull * chunk);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
     void* internal_tape = cv.take<char>(tape ? 0 : 36ull * total);
@@ -357,7 +362,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     // plain: per view, per chunk of at most kChunk samples, one wavefront per bounce
     QueueDev qa{cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk)};
     QueueDev qb{cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk)};
-    float4* hits = cv.take<float4>(chunk);
+    QueueDev hq{cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk)};
     ShadowDev sq{cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk), cv.take<float4>(chunk)};
     for (int vi = 0; vi < n_views; ++vi) {
         const ViewDev& v = vdev[(size_t)vi];
@@ -365,18 +370,20 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
         const uint64_t nv = (uint64_t)v.width * v.height * v.spp;
         for (uint64_t first = 0; first < nv; first += chunk) {
             const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, nv - first);
-            MR_CUDA(cudaMemsetAsync(ctx->queue_cnt, 0, sizeof(unsigned int) * (2 * v.bounces + 2), st));
+            unsigned int* qc = ctx->queue_cnt;
+            MR_CUDA(cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (3 * v.bounces + 3), st));
             mr_launch_raygen(v, rng, (uint32_t)first, n, qa, tp, total, sms, st);
             QueueDev cur = qa, nxt = qb;
             for (int b = 0; b < v.bounces; ++b) {
-                const unsigned int* cnt_in = b == 0 ? nullptr : ctx->queue_cnt + 2 * (b - 1);
-                mr_launch_trace(s, cur.o, cur.d, cnt_in, n, n, hits, false, sms, st);
-                mr_launch_shade(s, v, rng, b, M, cur, cnt_in, n, n, hits, nxt, ctx->queue_cnt + 2 * b, sq,
-                                ctx->queue_cnt + 2 * b + 1, tp, total, sms, st);
-                mr_launch_shadow(s, v, b, sq, ctx->queue_cnt + 2 * b + 1, n, tp, total, sms, st);
+                // ray queue of bounce b: the raygen output, then the continuations of bounce b-1
+                const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
+                mr_launch_closest(s, v, b, cur, cnt_in, n, n, hq, qc + 3 * b, tp, total, sms, st);
+                mr_launch_shade(s, v, rng, b, M, hq, qc + 3 * b, n, nxt, qc + 3 * b + 1, sq, qc + 3 * b + 2, tp,
+                                total, sms, st);
+                mr_launch_shadow(s, v, b, sq, qc + 3 * b + 2, n, tp, total, sms, st);
                 std::swap(cur, nxt);
             }
-            mr_launch_account(ctx->counters, ctx->queue_cnt, v.bounces, n, st);
+            mr_launch_account(ctx->counters, qc, v.bounces, n, st);
             ctx->host_launches += 2 + 3 * (unsigned long long)v.bounces;
         }
         mr_launch_resolve(v, tp, total, images[vi], sms, st);

@@ -31,6 +31,9 @@ struct SceneDev {
     const float4* env_texel;  // [eh][ew]: (r, g, b, prob * ew * eh)
     const uint32_t* env_marg; // [eh + 1] thresholds ceil(cdf * 2^24)
     const uint32_t* env_cond; // [eh][ew + 1]
+    const uint32_t* env_gmarg; // [gm + 1] guide: answer of the marginal search at bucket starts
+    const uint32_t* env_gcond; // [eh][gc + 1] guide of every row's conditional search
+    int32_t gm_shift, gc_shift, gc;
     int32_t n_tris, n_verts, tw, th, ew, eh;
     const int32_t* env_ok_dev; // device-written: total env weight > 0
     const float* tmin_dev;     // device-written: 1e-5 x scene diagonal
@@ -137,12 +140,30 @@ __device__ __forceinline__ float env_pdf_dir(const SceneDev& s, float3 d, int te
     return __ldg(&s.env_texel[texel].w) / (2.0f * MR_PI * MR_PI * st);
 }
 
-// sample a direction with probability proportional to Y(L) sin(theta_row); returns pdf
+// largest i in [lo, hi] with a[i] <= k, given a[lo] <= k
+__device__ __forceinline__ int search_range(const uint32_t* __restrict__ a, int lo, int hi, uint32_t k)
+{
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(a + mid) <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// sample a direction with probability proportional to Y(L) sin(theta_row); returns pdf.
+// The inverse-CDF searches start from guide tables (cut-point method): the answer at the
+// start of the uniform's bucket and at the next bucket bound the answer, so the search is
+// the same function of the uniform as a full binary search, over a range of ~1-2 entries.
 __device__ __forceinline__ float env_sample(const SceneDev& s, uint32_t xrow, uint32_t xcol, uint32_t sub,
                                             float3& dir, int& texel)
 {
-    const int r = search_le(s.env_marg, s.eh, xrow >> 8);
-    const int c = search_le(s.env_cond + (size_t)r * (s.ew + 1), s.ew, xcol >> 8);
+    const uint32_t kr = xrow >> 8, kc = xcol >> 8;
+    const uint32_t bm = kr >> s.gm_shift;
+    const int r = search_range(s.env_marg, (int)__ldg(s.env_gmarg + bm), (int)__ldg(s.env_gmarg + bm + 1), kr);
+    const uint32_t* grow = s.env_gcond + (size_t)r * (s.gc + 1);
+    const uint32_t bc = kc >> s.gc_shift;
+    const int c = search_range(s.env_cond + (size_t)r * (s.ew + 1), (int)__ldg(grow + bc), (int)__ldg(grow + bc + 1), kc);
     const float uu = ((float)c + sub_hi(sub)) / (float)s.ew;
     const float vv = ((float)r + sub_lo(sub)) / (float)s.eh;
     float sp, cp, st, ct;

@@ -70,12 +70,48 @@ __global__ void k_env_texels(const float* __restrict__ env, const double* __rest
     texel[i] = make_float4(env[3 * i], env[3 * i + 1], env[3 * i + 2], p);
 }
 
+// largest i in [0, n-1] with a[i] <= k
+__device__ __forceinline__ uint32_t search_all(const uint32_t* a, int n, uint32_t k)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return (uint32_t)lo;
+}
+
+// guide tables: for bucket b of the 24-bit uniform, the search answer at u = b << shift;
+// entry g (one past the last bucket) is n - 1
+__global__ void k_env_guide(const uint32_t* __restrict__ cdf, int rows, int stride, int n, int g, int shift,
+                            uint32_t* __restrict__ guide)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)rows * (g + 1)) return;
+    const int row = (int)(i / (size_t)(g + 1)), b = (int)(i % (size_t)(g + 1));
+    const uint32_t* a = cdf + (size_t)row * stride;
+    guide[i] = (b == g) ? (uint32_t)(n - 1) : search_all(a, n, (uint32_t)b << shift);
+}
+
 }  // namespace
+
+static void guide_shape(int n, int& g, int& shift)
+{
+    int lg = 0;
+    while ((1 << lg) < n && lg < 24) ++lg;
+    g = 1 << lg;
+    shift = 24 - lg;
+}
 
 mirres_status mr_env_alloc(mirres_scene* s)
 {
     const size_t W = (size_t)s->desc.env_w, H = (size_t)s->desc.env_h;
+    guide_shape((int)H, s->gm, s->gm_shift);
+    guide_shape((int)W, s->gc, s->gc_shift);
     cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc((void**)&s->env_gmarg, sizeof(uint32_t) * (size_t)(s->gm + 1));
+    e = e ? e : cudaMalloc((void**)&s->env_gcond, sizeof(uint32_t) * H * (size_t)(s->gc + 1));
     e = e ? e : cudaMalloc((void**)&s->env_w, sizeof(double) * W * H);
     e = e ? e : cudaMalloc((void**)&s->env_rowsum, sizeof(double) * H);
     e = e ? e : cudaMalloc((void**)&s->env_total, sizeof(double));
@@ -93,7 +129,8 @@ mirres_status mr_env_alloc(mirres_scene* s)
 
 void mr_env_free(mirres_scene* s)
 {
-    void* ptrs[] = {s->env_w, s->env_rowsum, s->env_total, s->env_ok, s->env_marg, s->env_cond, s->env_texel};
+    void* ptrs[] = {s->env_w,    s->env_rowsum, s->env_total, s->env_ok,   s->env_marg,
+                    s->env_cond, s->env_texel,  s->env_gmarg, s->env_gcond};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -106,6 +143,11 @@ mirres_status mr_env_build(mirres_scene* s, cudaStream_t st)
     const size_t n = (size_t)W * H;
     k_env_texels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->desc.env, s->env_w, W, H, s->env_total,
                                                              s->env_texel);
+    k_env_guide<<<(unsigned)((s->gm + 1 + 255) / 256), 256, 0, st>>>(s->env_marg, 1, H + 1, H, s->gm, s->gm_shift,
+                                                                     s->env_gmarg);
+    const size_t ng = (size_t)H * (s->gc + 1);
+    k_env_guide<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(s->env_cond, H, W + 1, W, s->gc, s->gc_shift,
+                                                              s->env_gcond);
     MR_CUDA(cudaGetLastError());
     return MIRRES_OK;
 }

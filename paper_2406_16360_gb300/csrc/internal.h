@@ -68,6 +68,9 @@ struct mirres_scene {
     uint32_t* env_marg = nullptr;    // [eh+1]
     uint32_t* env_cond = nullptr;    // [eh][ew+1]
     float4* env_texel = nullptr;     // [eh][ew]
+    uint32_t* env_gmarg = nullptr;   // [gm+1]
+    uint32_t* env_gcond = nullptr;   // [eh][gc+1]
+    int gm_shift = 0, gc_shift = 0, gm = 1, gc = 1;
 };
 
 SceneDev mr_scene_dev(const mirres_scene* s);

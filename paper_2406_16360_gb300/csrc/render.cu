@@ -150,22 +150,6 @@ __global__ void __launch_bounds__(256) k_raygen(ViewDev v, Rng rng, uint32_t fir
     }
 }
 
-template <bool ANY>
-__global__ void __launch_bounds__(256) k_trace(SceneDev s, const float4* __restrict__ qo,
-                                               const float4* __restrict__ qd, const unsigned int* count,
-                                               unsigned int count_fixed, float4* __restrict__ hits)
-{
-    extern __shared__ uint32_t sstk[];
-    const unsigned int n = count ? *count : count_fixed;
-    const float tmin = *s.tmin_dev;
-    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float4 a = qo[i], b = qd[i];
-        Hit h;
-        traverse<ANY>(s, xyz(a), xyz(b), __float_as_int(a.w), tmin, __int_as_float(0x7f800000), h,
-                      sstk + threadIdx.x, blockDim.x);
-        hits[i] = make_float4(h.t, h.u, h.v, __int_as_float(h.tri));
-    }
-}
 
 // warp-aggregated append: returns the slot of this lane (valid only if want)
 __device__ __forceinline__ unsigned int warp_append(bool want, unsigned int* counter)
@@ -179,57 +163,85 @@ __device__ __forceinline__ unsigned int warp_append(bool want, unsigned int* cou
     return base + __popc(m & lanemask_lt());
 }
 
-__global__ void __launch_bounds__(256) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev qin,
-                                               const unsigned int* count_in, unsigned int count_fixed,
-                                               const float4* __restrict__ hits, QueueDev qout,
+// closest hit of every queued ray. A primary ray that escapes writes the environment into
+// its sample; an escaping continuation ray ends its path. Hits are compacted (warp ballot)
+// into the shade queue, so that shading runs on full warps of hits.
+__global__ void __launch_bounds__(256) k_closest(SceneDev s, ViewDev v, int b, QueueDev q, const unsigned int* count,
+                                                 unsigned int count_fixed, QueueDev hq, unsigned int* count_hit,
+                                                 void* tape, uint64_t ntot)
+{
+    extern __shared__ uint32_t sstk[];
+    const TapeDev tp = tape_of(tape, ntot);
+    const unsigned int n = count ? *count : count_fixed;
+    const float tmin = *s.tmin_dev;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    const unsigned int rounds = (n + stride - 1) / stride;
+    for (unsigned int r = 0; r < rounds; ++r) {
+        const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        Hit h;
+        h.tri = -1;
+        float4 qd = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n) {
+            const float4 a = q.o[i];
+            qd = q.d[i];
+            traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), tmin, __int_as_float(0x7f800000), h,
+                            sstk + threadIdx.x, blockDim.x);
+            if (h.tri < 0 && b == 0) {
+                const uint64_t g = v.offset + __float_as_uint(qd.w);
+                const float4 L = __ldg(s.env_texel + env_texel_of(s, xyz(qd)));
+                tp.rad[0][g] = L.x;
+                tp.rad[1][g] = L.y;
+                tp.rad[2][g] = L.z;
+            }
+        }
+        const bool hit = h.tri >= 0;
+        const unsigned int slot = warp_append(hit, count_hit);
+        if (hit) {
+            hq.o[slot] = make_float4(h.t, h.u, h.v, __int_as_float(h.tri));
+            hq.d[slot] = qd;
+            hq.b[slot] = q.b[i];
+            hq.bi[slot] = q.bi[i];
+        }
+    }
+}
+
+// shade every compacted hit: RIS + shadow ray + continuation (next-bounce queue)
+__global__ void __launch_bounds__(256) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev hq,
+                                               const unsigned int* count_hit, QueueDev qout,
                                                unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
                                                void* tape, uint64_t ntot)
 {
     const TapeDev tp = tape_of(tape, ntot);
-    const unsigned int n = count_in ? *count_in : count_fixed;
+    const unsigned int n = *count_hit;
     const int env_ok = *s.env_ok_dev;
     const unsigned int stride = gridDim.x * blockDim.x;
     const unsigned int rounds = (n + stride - 1) / stride;
     for (unsigned int r = 0; r < rounds; ++r) {
         const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
-        const bool live = i < n;
         VertexOut out;
         out.shadow = false;
         out.cont = false;
         uint32_t sid = 0;
-        float4 qb = make_float4(0.f, 0.f, 0.f, 0.f), qbi = qb;
-        float3 d = f3(0.f, 0.f, 1.f);
         int tri = -1;
-        if (live) {
-            const float4 hd = hits[i];
-            const float4 qd = qin.d[i];
-            d = xyz(qd);
+        if (i < n) {
+            const float4 hd = hq.o[i];
+            const float4 qd = hq.d[i];
+            const float3 d = xyz(qd);
             sid = __float_as_uint(qd.w);
             const uint64_t g = v.offset + sid;
             tri = __float_as_int(hd.w);
-            if (tri < 0) {
-                if (b == 0) {  // a primary ray that escapes sees the environment
-                    const float4 L = __ldg(s.env_texel + env_texel_of(s, d));
-                    tp.rad[0][g] = L.x;
-                    tp.rad[1][g] = L.y;
-                    tp.rad[2][g] = L.z;
-                }
-            } else {
-                qb = qin.b[i];
-                qbi = qin.bi[i];
-                const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
-                Hit h;
-                h.t = hd.x;
-                h.u = hd.y;
-                h.v = hd.z;
-                h.tri = tri;
-                shade_vertex(s, env_ok, rng, pixel, smp, (uint32_t)v.index, b, v.bounces, M, h, d, xyz(qb),
-                             xyz(qbi), out);
-                if (b == 0) {
-                    tp.tri[g] = tri;
-                    tp.cand[g] = out.cand;
-                    tp.wv[g] = out.W;
-                }
+            const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
+            Hit h;
+            h.t = hd.x;
+            h.u = hd.y;
+            h.v = hd.z;
+            h.tri = tri;
+            shade_vertex(s, env_ok, rng, pixel, smp, (uint32_t)v.index, b, v.bounces, M, h, d, xyz(hq.b[i]),
+                         xyz(hq.bi[i]), out);
+            if (b == 0) {
+                tp.tri[g] = tri;
+                tp.cand[g] = out.cand;
+                tp.wv[g] = out.W;
             }
         }
         const unsigned int ss = warp_append(out.shadow, count_sh);
@@ -294,9 +306,11 @@ __global__ void __launch_bounds__(256) k_resolve(ViewDev v, const void* tape, ui
 }
 
 // ---------------------------------------------------------------------------------------
-// persistent batched kernel: every view of every scene in one launch. Each warp pulls
-// chunks of consecutive samples from a device counter; a lane whose path ends takes the
-// next sample from the warp's chunk (ballot + popc), so lanes stay busy across views.
+// persistent batched kernel: every view of every scene in one launch. Each warp pulls chunks
+// of consecutive samples from a device counter. An iteration first refills and traces until
+// every lane holds a ray that hit something (lanes whose ray escaped finish their sample and
+// take the next one), so that the expensive part -- shading with RIS over M candidates --
+// runs on full warps; then the shadow rays of those vertices are traced.
 // ---------------------------------------------------------------------------------------
 __global__ void k_persistent(const SceneDev* __restrict__ scenes, const ViewDev* __restrict__ views, int n_views,
                              uint64_t total, Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
@@ -308,110 +322,134 @@ __global__ void k_persistent(const SceneDev* __restrict__ scenes, const ViewDev*
     uint32_t* mystk = sstk + threadIdx.x;
     const int sstride = blockDim.x;
 
-    bool active = false;
+    bool has_path = false, has_hit = false;
     uint64_t g = 0;
-    int vi = 0, b = 0, B = 1, origin = -1, tri0 = -1, cand0 = -1, env_ok = 0;
+    int b = 0, B = 1, origin = -1, tri0 = -1, cand0 = -1, env_ok = 0;
     uint32_t pixel = 0, smp = 0, vidx = 0;
     float3 o = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f), beta = f3(1.f, 1.f, 1.f), bind = beta;
     float3 rad = f3(0.f, 0.f, 0.f), lind = rad;
     float wv0 = 0.0f, tmin = 0.0f;
     const SceneDev* sp = scenes;
+    Hit h;
+    h.tri = -1;
 
     uint64_t pool = 0, pool_end = 0;
     bool exhausted = false;
     unsigned long long n_cont = 0, n_shadow = 0, n_cand = 0, n_prim = 0;
 
     while (true) {
-        unsigned idle = __ballot_sync(MR_FULL, !active);
-        if (idle && pool == pool_end && !exhausted) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(work, (unsigned long long)chunk);
-            base = __shfl_sync(MR_FULL, base, 0);
-            if (base >= total) exhausted = true;
-            else {
-                pool = base;
-                pool_end = (base + chunk < total) ? base + chunk : total;
+        // ---- refill and trace until the warp is full of hits (bounded number of passes) ----
+        for (int pass = 0; pass < 8; ++pass) {
+            const unsigned idle = __ballot_sync(MR_FULL, !has_path);
+            if (idle && pool == pool_end && !exhausted) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(work, (unsigned long long)chunk);
+                base = __shfl_sync(MR_FULL, base, 0);
+                if (base >= total) exhausted = true;
+                else {
+                    pool = base;
+                    pool_end = (base + chunk < total) ? base + chunk : total;
+                }
             }
-        }
-        if (idle && pool < pool_end) {
-            const uint64_t avail = pool_end - pool;
-            const unsigned rank = __popc(idle & lanemask_lt());
-            if (!active && rank < avail) {
-                g = pool + rank;
-                const ViewDev& v = view_of(views, n_views, g, vi);
-                sp = scenes + v.scene;
-                const uint32_t sid = (uint32_t)(g - v.offset);
-                pixel = sid / (uint32_t)v.spp;
-                smp = sid % (uint32_t)v.spp;
-                vidx = (uint32_t)v.index;
-                B = v.bounces;
-                const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
-                const uint4 x = rng.draw(pixel, smp, vidx, 0u, PURPOSE_CAMERA, 0u);
-                o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
-                d = camera_dir(v, px, py, u24(x.x), u24(x.y));
-                beta = bind = f3(1.f, 1.f, 1.f);
-                rad = lind = f3(0.f, 0.f, 0.f);
-                b = 0;
-                origin = -1;
-                tri0 = -1;
-                cand0 = -1;
-                wv0 = 0.0f;
-                env_ok = *sp->env_ok_dev;
-                tmin = *sp->tmin_dev;
-                active = true;
-                ++n_prim;
+            if (idle && pool < pool_end) {
+                const uint64_t avail = pool_end - pool;
+                const unsigned rank = __popc(idle & lanemask_lt());
+                if (!has_path && rank < avail) {
+                    g = pool + rank;
+                    int vi;
+                    const ViewDev& v = view_of(views, n_views, g, vi);
+                    sp = scenes + v.scene;
+                    const uint32_t sid = (uint32_t)(g - v.offset);
+                    pixel = sid / (uint32_t)v.spp;
+                    smp = sid % (uint32_t)v.spp;
+                    vidx = (uint32_t)v.index;
+                    B = v.bounces;
+                    const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+                    const uint4 x = rng.draw(pixel, smp, vidx, 0u, PURPOSE_CAMERA, 0u);
+                    o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+                    d = camera_dir(v, px, py, u24(x.x), u24(x.y));
+                    beta = bind = f3(1.f, 1.f, 1.f);
+                    rad = lind = f3(0.f, 0.f, 0.f);
+                    b = 0;
+                    origin = -1;
+                    tri0 = -1;
+                    cand0 = -1;
+                    wv0 = 0.0f;
+                    env_ok = *sp->env_ok_dev;
+                    tmin = *sp->tmin_dev;
+                    has_path = true;
+                    has_hit = false;
+                    ++n_prim;
+                }
+                const uint64_t took = ((uint64_t)__popc(idle) < avail) ? (uint64_t)__popc(idle) : avail;
+                pool += took;
             }
-            pool += ((uint64_t)__popc(idle) < avail) ? (uint64_t)__popc(idle) : avail;
+            const bool need = has_path && !has_hit;
+            if (!__any_sync(MR_FULL, need)) break;
+            if (need) {
+                traverse<false>(*sp, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk, sstride);
+                if (h.tri >= 0) {
+                    has_hit = true;
+                } else {
+                    // escaped: a primary ray sees the env; a continuation ray ends the path
+                    if (b == 0) {
+                        const float4 L = __ldg(sp->env_texel + env_texel_of(*sp, d));
+                        rad = f3(L.x, L.y, L.z);
+                    }
+                    tp.tri[g] = tri0;
+                    tp.cand[g] = cand0;
+                    tp.wv[g] = wv0;
+                    tp.lind[0][g] = lind.x;
+                    tp.lind[1][g] = lind.y;
+                    tp.lind[2][g] = lind.z;
+                    tp.rad[0][g] = rad.x;
+                    tp.rad[1][g] = rad.y;
+                    tp.rad[2][g] = rad.z;
+                    has_path = false;
+                }
+            }
+            if (__all_sync(MR_FULL, has_hit || (!has_path && exhausted && pool == pool_end))) break;
         }
-        if (!__any_sync(MR_FULL, active)) {
-            if (exhausted) break;
+        if (!__any_sync(MR_FULL, has_hit)) {
+            if (exhausted && pool == pool_end && !__any_sync(MR_FULL, has_path)) break;
             continue;
         }
-        if (active) {
-            const SceneDev s = *sp;
-            Hit h;
-            traverse<false>(s, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk, sstride);
-            bool done = false;
-            if (h.tri < 0) {
-                if (b == 0) {
-                    const float4 L = __ldg(s.env_texel + env_texel_of(s, d));
-                    rad = f3(L.x, L.y, L.z);
-                }
-                done = true;
-            } else {
-                if (b == 0) tri0 = h.tri;
-                VertexOut out;
-                shade_vertex(s, env_ok, rng, pixel, smp, vidx, b, B, M, h, d, beta, bind, out);
-                n_cand += (env_ok && M > 0) ? (unsigned long long)M : 0ull;
-                if (b == 0) {
-                    cand0 = out.cand;
-                    wv0 = out.W;
-                }
-                if (out.shadow) {
-                    ++n_shadow;
-                    Hit hs;
-                    traverse<true>(s, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk,
-                                   sstride);
-                    if (hs.tri < 0) {
-                        rad = add_rn(rad, out.add_rad);
-                        if (b >= 1) lind = add_rn(lind, out.add_lind);
-                    } else if (b == 0) {
-                        wv0 = 0.0f;
-                    }
-                }
-                if (out.cont) {
-                    ++n_cont;
-                    o = out.x;
-                    d = out.c_d;
-                    beta = out.c_beta;
-                    bind = out.c_bind;
-                    origin = h.tri;
-                    ++b;
-                } else {
-                    done = true;
-                }
+        // ---- shade the hits: RIS, shadow ray, continuation ----
+        VertexOut out;
+        out.shadow = false;
+        out.cont = false;
+        if (has_hit) {
+            const SceneDev& s = *sp;
+            if (b == 0) tri0 = h.tri;
+            shade_vertex(s, env_ok, rng, pixel, smp, vidx, b, B, M, h, d, beta, bind, out);
+            n_cand += (env_ok && M > 0) ? (unsigned long long)M : 0ull;
+            if (b == 0) {
+                cand0 = out.cand;
+                wv0 = out.W;
             }
-            if (done) {
+        }
+        if (out.shadow) {
+            ++n_shadow;
+            Hit hs;
+            traverse<true>(*sp, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk, sstride);
+            if (hs.tri < 0) {
+                rad = add_rn(rad, out.add_rad);
+                if (b >= 1) lind = add_rn(lind, out.add_lind);
+            } else if (b == 0) {
+                wv0 = 0.0f;
+            }
+        }
+        if (has_hit) {
+            has_hit = false;
+            if (out.cont) {
+                ++n_cont;
+                o = out.x;
+                d = out.c_d;
+                beta = out.c_beta;
+                bind = out.c_bind;
+                origin = h.tri;
+                ++b;
+            } else {
                 tp.tri[g] = tri0;
                 tp.cand[g] = cand0;
                 tp.wv[g] = wv0;
@@ -421,7 +459,7 @@ __global__ void k_persistent(const SceneDev* __restrict__ scenes, const ViewDev*
                 tp.rad[0][g] = rad.x;
                 tp.rad[1][g] = rad.y;
                 tp.rad[2][g] = rad.z;
-                active = false;
+                has_path = false;
             }
         }
     }
@@ -758,16 +796,16 @@ __global__ void __launch_bounds__(256) k_l2(const float* __restrict__ img, const
     }
 }
 
-// add one chunk's queue counts to the cumulative counters: qcnt[2b] continuation rays
-// emitted at bounce b, qcnt[2b+1] shadow rays of bounce b
+// add one chunk's queue counts to the cumulative counters: per bounce b, qcnt[3b] hits,
+// qcnt[3b+1] continuation rays emitted, qcnt[3b+2] shadow rays
 __global__ void k_account(unsigned long long* counters, const unsigned int* __restrict__ qcnt, int bounces,
                           uint64_t primary)
 {
     if (threadIdx.x != 0) return;
     unsigned long long cont = 0, shadow = 0;
     for (int b = 0; b < bounces; ++b) {
-        cont += qcnt[2 * b];
-        shadow += qcnt[2 * b + 1];
+        cont += qcnt[3 * b + 1];
+        shadow += qcnt[3 * b + 2];
     }
     counters[0] += primary;
     counters[1] += cont;
@@ -816,21 +854,20 @@ void mr_launch_raygen(const ViewDev& v, Rng rng, uint32_t first, uint32_t n, con
     k_raygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(v, rng, first, n, q, tape, ntot);
 }
 
-void mr_launch_trace(const SceneDev& s, const float4* qo, const float4* qd, const unsigned int* count,
-                     unsigned int count_fixed, uint64_t upper, float4* hits, bool any, int sms, cudaStream_t st)
+void mr_launch_closest(const SceneDev& s, const ViewDev& v, int b, const QueueDev& q, const unsigned int* count,
+                       unsigned int count_fixed, uint64_t upper, const QueueDev& hq, unsigned int* count_hit,
+                       void* tape, uint64_t ntot, int sms, cudaStream_t st)
 {
-    const unsigned grid = grid_cap(upper, 256, sms * 8);
-    if (any) k_trace<true><<<grid, 256, stack_bytes(256), st>>>(s, qo, qd, count, count_fixed, hits);
-    else k_trace<false><<<grid, 256, stack_bytes(256), st>>>(s, qo, qd, count, count_fixed, hits);
+    k_closest<<<grid_cap(upper, 256, sms * 8), 256, stack_bytes(256), st>>>(s, v, b, q, count, count_fixed, hq,
+                                                                           count_hit, tape, ntot);
 }
 
-void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& qin,
-                     const unsigned int* count_in, unsigned int count_fixed, uint64_t upper, const float4* hits,
-                     const QueueDev& qout, unsigned int* count_out, const ShadowDev& sq, unsigned int* count_sh,
-                     void* tape, uint64_t ntot, int sms, cudaStream_t st)
+void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& hq,
+                     const unsigned int* count_hit, uint64_t upper, const QueueDev& qout, unsigned int* count_out,
+                     const ShadowDev& sq, unsigned int* count_sh, void* tape, uint64_t ntot, int sms, cudaStream_t st)
 {
-    k_shade<<<grid_cap(upper, 256, sms * 8), 256, 0, st>>>(s, v, rng, b, M, qin, count_in, count_fixed, hits, qout,
-                                                          count_out, sq, count_sh, tape, ntot);
+    k_shade<<<grid_cap(upper, 256, sms * 8), 256, 0, st>>>(s, v, rng, b, M, hq, count_hit, qout, count_out, sq,
+                                                          count_sh, tape, ntot);
 }
 
 void mr_launch_shadow(const SceneDev& s, const ViewDev& v, int b, const ShadowDev& sq, const unsigned int* count,

@@ -29,12 +29,12 @@ struct GradDev {
 
 void mr_launch_raygen(const ViewDev& v, Rng rng, uint32_t first, uint32_t n, const QueueDev& q, void* tape,
                       uint64_t ntot, int sms, cudaStream_t st);
-void mr_launch_trace(const SceneDev& s, const float4* qo, const float4* qd, const unsigned int* count,
-                     unsigned int count_fixed, uint64_t upper, float4* hits, bool any, int sms, cudaStream_t st);
-void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& qin,
-                     const unsigned int* count_in, unsigned int count_fixed, uint64_t upper, const float4* hits,
-                     const QueueDev& qout, unsigned int* count_out, const ShadowDev& sq, unsigned int* count_sh,
-                     void* tape, uint64_t ntot, int sms, cudaStream_t st);
+void mr_launch_closest(const SceneDev& s, const ViewDev& v, int b, const QueueDev& q, const unsigned int* count,
+                       unsigned int count_fixed, uint64_t upper, const QueueDev& hq, unsigned int* count_hit,
+                       void* tape, uint64_t ntot, int sms, cudaStream_t st);
+void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& hq,
+                     const unsigned int* count_hit, uint64_t upper, const QueueDev& qout, unsigned int* count_out,
+                     const ShadowDev& sq, unsigned int* count_sh, void* tape, uint64_t ntot, int sms, cudaStream_t st);
 void mr_launch_shadow(const SceneDev& s, const ViewDev& v, int b, const ShadowDev& sq, const unsigned int* count,
                       uint64_t upper, void* tape, uint64_t ntot, int sms, cudaStream_t st);
 void mr_launch_resolve(const ViewDev& v, const void* tape, uint64_t ntot, float* img, int sms, cudaStream_t st);
