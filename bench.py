@@ -5,8 +5,9 @@ One step = one pass of the whole path over the workload: LBVH build (Morton code
 sort, hierarchy, boxes) and env sampling tables, the forward render of every view, the L2
 image loss against reference images and the adjoint (PRIMARY mode) into the gradients of
 textures, env map and vertices. Metric: forward+backward path samples per second (one path
-sample = one pixel sample of one view), for the batched persistent launch (the headline
-value) and for the plain per-view wavefront launch; Mrays/s alongside.
+sample = one pixel sample of one view), for the batched launch (every view in one
+graph-captured wavefront: the headline value), the plain per-view wavefront launch and the
+single persistent kernel; Mrays/s alongside.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config3|config5|config2]
   python bench.py --impl reference ...   (the CPU oracle on the host cores, bounded sample)
@@ -25,7 +26,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "fwd+bwd path-samples/s (batched persistent launch; plain per-view launch and Mrays/s alongside)"
+METRIC = "fwd+bwd path-samples/s (batched launch; plain per-view launch and Mrays/s alongside)"
 UNIT = "path-samples/s"
 
 
@@ -132,8 +133,9 @@ def oracle_sample(w, target_seconds, threads):
         dt = time.perf_counter() - t0
         return dt, r["counts"], npix * v.spp
 
-    dt, _, _ = run(max(threads * 2, 32))
-    per_px = dt / max(threads * 2, 32)
+    probe = min(n_all, threads * 32)
+    dt, _, _ = run(probe)
+    per_px = dt / probe
     npix = int(min(n_all, max(threads * 4, target_seconds / max(per_px, 1e-9))))
     return osc, run, npix
 
@@ -225,6 +227,11 @@ def main():
     images = gw.new_images()
     tape = gw.new_tape()
     grads = gw.zero_grads()
+    tuned = None
+    if not args.block:
+        t0 = time.perf_counter()
+        tuned = gw.autotune(tape=tape, budget=min(samples, 32_000_000))
+        tuned["tuning_s"] = time.perf_counter() - t0
     # reference images: the same scene rendered with another seed
     refs, _ = gw.render(launch=1, seed=w.seed + 1, tape=tape)
     refs = [r.clone() for r in refs]
@@ -241,8 +248,9 @@ def main():
             M.mirres_bvh_build(s.handle)
         if ev_render is not None:
             ev_render[0].record()
-        M.mirres_render(gw.ctx, scenes, gw.views, gw.params(launch, block=args.block,
-                                                            blocks_per_sm=args.blocks_per_sm), images, tape)
+        # the batched wavefront records stage events (graph event nodes) for the roofline
+        M.mirres_render(gw.ctx, scenes, gw.views, gw.params(launch, block=args.block, blocks_per_sm=args.blocks_per_sm,
+                                                            flags=1 if launch == 1 else 0), images, tape)
         if ev_render is not None:
             ev_render[1].record()
         for img, ref, d in zip(images, refs, d_images):
@@ -280,24 +288,29 @@ def main():
         launches = c1[6] - c0[6]
         return ms, ms_render, rays, launches, [c1[k] - c0[k] for k in range(8)]
 
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
     clocks = ClockSampler(local)
     clocks.start()
     ms_b, msr_b, rays_b, launches_b, cnt_b = timed(1, args.steps, args.warmup)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms_b], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_b = float(t.item())
-    plain = None
-    if not args.no_plain:
-        ms_p, msr_p, rays_p, launches_p, _ = timed(0, args.steps, args.warmup)
-        if world > 1:
-            t = torch.tensor([ms_p], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_p = float(t.item())
-        plain = {"value": world * samples * args.steps / (ms_p / 1e3), "ms_per_step": ms_p / args.steps,
-                 "mrays_per_s": world * rays_p / (ms_p / 1e3) / 1e6, "render_ms_per_step": msr_p / args.steps,
-                 "gpu_launches": launches_p}
+    stages = M.mirres_stage_times(gw.ctx)  # stage times of the last timed batched render
+    ms_b = max_over_ranks(ms_b)
+
+    def arm(launch):
+        ms, msr, rays, launches, _ = timed(launch, args.steps, args.warmup)
+        ms = max_over_ranks(ms)
+        return {"value": world * samples * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                "mrays_per_s": world * rays / (ms / 1e3) / 1e6, "render_ms_per_step": msr / args.steps,
+                "gpu_launches": launches}
+
+    plain = None if args.no_plain else arm(0)
+    persistent = None if args.no_plain else dict(arm(2), launch_shape=tuned)
 
     # end to end: host parameters and reference images in pinned memory, copies in the timed region
     host_params = [{k: t.detach().cpu().pin_memory() for k, t in s.params().items()} for s in gw.scenes]
@@ -345,8 +358,12 @@ def main():
             "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}",
                            l2="flushed between timed steps (512 MiB write) and each step writes > 40 GB"),
             "mrays_per_s": mrays, "render_ms_per_step": msr_b / args.steps,
-            "batched": {"value": value, "ms_per_step": ms_b / args.steps, "mrays_per_s": mrays},
+            "batched": {"value": value, "ms_per_step": ms_b / args.steps, "mrays_per_s": mrays,
+                        "launch": "batched wavefront, one CUDA graph per forward",
+                        "stage_ms_per_render": {k: v[0] for k, v in stages.items()},
+                        "stage_launches_per_render": {k: v[1] for k, v in stages.items()}},
             "plain": plain,
+            "persistent": persistent,
             "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
             "counters_per_step": {"primary_rays": cnt_b[0] // args.steps, "continuation_rays": cnt_b[1] // args.steps,
                                   "shadow_rays": cnt_b[2] // args.steps, "ris_candidates": cnt_b[5] // args.steps,
@@ -356,22 +373,24 @@ def main():
             "e2e": {"value": world * samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
 
-    # roofline of the dominant kernel (the persistent forward): FP32 ALU bound, algorithmic FLOPs
-    # per path sample from the oracle's instrumented traversal and candidate counts
+    # roofline of the dominant kernel, the shading stage (k_wshade): FP32 ALU bound; algorithmic
+    # FLOPs = RIS candidates x (60 BRDF FLOPs + 2 log2(env texels) search steps) per candidate,
+    # candidates counted by the library, time from the stage events captured in the graph
+    env_texels = sum(s.env.shape[0] * s.env.shape[1] for s in w.scenes) / len(w.scenes)
+    per_cand = 60 + 2 * math.log2(env_texels)
+    cand_per_render = cnt_b[5] / args.steps
+    shade_ms, shade_launches = stages["shade"]
+    achieved = cand_per_render * per_cand / (shade_ms / 1e3) / 1e12
+    peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None, "kernel": "k_wshade (shade + RIS stage)",
+                        "kernel_ms_per_launch": shade_ms / max(shade_launches, 1),
+                        "kernel_share_of_render": shade_ms / max(sum(v[0] for v in stages.values()), 1e-9),
+                        "flops_per_candidate": per_cand, "candidates_per_render": cand_per_render,
+                        "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock), non-tensor"}
     if rank == 0 and not args.no_cpu:
         cb, counts, osamples = cpu_baseline(w)
         line["cpu_baseline"] = cb
-        sc0 = w.scenes[0]
-        env_bits = math.log2(sc0.env.shape[0] * sc0.env.shape[1])
-        flops_per_sample = (counts[3] * 12 + counts[4] * 27 + counts[5] * (60 + 2 * env_bits)) / max(counts[6], 1)
-        render_s = msr_b / args.steps / 1e3
-        achieved = flops_per_sample * samples / render_s / 1e12
-        peak = 152 * 128 * 2 * 2.070e9 / 1e12
-        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": None,
-                            "kernel": "k_persistent (forward, batched)",
-                            "flops_per_sample": flops_per_sample,
-                            "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock), non-tensor"}
     if rank == 0:
         print(json.dumps(line))
     gw.close()

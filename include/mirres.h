@@ -91,14 +91,19 @@ typedef struct {
  *            P = 0 camera jitter, 1 RIS candidate j, 2 continuation. v is the view's index
  *            in the call's view array (< 65536); bounces < 256.
  *   grad_mode 0 = PRIMARY (the paper: gradients of indirect rays detached, Sec. 4.2)
- *   launch   0 = plain: per-view wavefront launches (ray generation, closest hit,
- *                 shade + RIS + next-bounce queue, shadow rays, resolve);
- *            1 = batched: one persistent launch over every view of every scene, work
- *                 pulled from a device counter.
- *            Both take every discrete decision identically (hit triangles, selected
- *            candidates, lobes); values agree to FP32 rounding (the two kernels may contract
+ *   launch   0 = plain: per-view wavefront launches (ray generation, closest hit with hit
+ *                 compaction, shade + RIS + next-bounce queue, shadow rays, resolve);
+ *            1 = batched wavefront: every view of every scene flattened into waves of up to
+ *                 2^24 samples; the whole forward is one CUDA graph, captured on first use and
+ *                 replayed while the shape, tape, seed and workspace stay the same;
+ *            2 = persistent kernel: one launch over every view of every scene, each warp
+ *                 pulling samples from a device counter and refilling lanes by ballot.
+ *            All take every discrete decision identically (hit triangles, selected
+ *            candidates, lobes); values agree to FP32 rounding (the kernels may contract
  *            multiply-adds differently).
- *   block, blocks_per_sm  launch shape of the persistent kernel (0 = autotuned / default) */
+ *   block, blocks_per_sm  launch shape of the persistent kernel (0 = autotuned / default)
+ *   flags    bit 0: record CUDA events around every stage kernel of the batched wavefront
+ *            (read back with mirres_stage_times) */
 typedef struct {
     int32_t ris_m;
     uint32_t seed_lo, seed_hi;
@@ -106,7 +111,7 @@ typedef struct {
     int32_t launch;
     int32_t block;
     int32_t blocks_per_sm;
-    int32_t reserved;
+    int32_t flags;
 } mirres_params;
 
 /* Gradient destinations for one scene (device pointers, shapes of the scene's inputs).
@@ -164,6 +169,26 @@ mirres_status mirres_render(mirres_context* ctx, mirres_scene* const* scenes, in
                             const mirres_view* views, int32_t n_views, const mirres_params* params,
                             float* const* images, void* tape, size_t tape_bytes, void* stream);
 
+/* Autotuner of the batched launch (no counterpart in the paper; a launch-shape search):
+ * times each compiled persistent-kernel variant (block size x resident blocks per SM, which
+ * sets its register cap) and each per-warp work chunk (64, 256, 1024 samples) on the first
+ * budget_samples samples of this batch (0 = all), keeps the fastest in the context (used by
+ * later batched renders whose params.block is 0) and reports it. Synchronises `stream`.
+ * The tape must be the full tape of these views (its first samples are overwritten). */
+mirres_status mirres_autotune(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                              const mirres_view* views, int32_t n_views, const mirres_params* params,
+                              void* tape, size_t tape_bytes, uint64_t budget_samples, int32_t* out_block,
+                              int32_t* out_blocks_per_sm, int32_t* out_chunk, float* out_ms, void* stream);
+
+/* Set the batched launch shape of the context directly (e.g. from a cache of autotuner
+ * results): block 0 restores the default. */
+mirres_status mirres_set_launch(mirres_context* ctx, int32_t block, int32_t blocks_per_sm, int32_t chunk);
+
+/* Summed device time (ms) and launch count of each stage of the last batched-wavefront
+ * render that was issued with params.flags bit 0: out_ms[0..3] = closest hit, shade (RIS),
+ * shadow rays, ray generation; out_launches likewise. Synchronises on those events. */
+mirres_status mirres_stage_times(mirres_context* ctx, double out_ms[4], int32_t out_launches[4]);
+
 /* ---- forward without device allocation ------------------------------------------------ */
 
 #define MIRRES_NOALLOC_SCRATCH_BYTES (512u * 1024u) /* static scratch per GPU, held until exit */
@@ -174,7 +199,7 @@ mirres_status mirres_render(mirres_context* ctx, mirres_scene* const* scenes, in
  * device memory while they render: for example a process whose device memory is entirely
  * reserved by another allocator (a framework's caching allocator), or a latency-critical
  * serving loop that must not pay the device-wide synchronisation cudaMalloc / cudaFree can
- * bring. It runs the batched persistent forward of mirres_render (launch = 1; the launch
+ * bring. It runs the persistent-kernel forward of mirres_render (launch = 2; the launch
  * field is ignored) with the same results, but keeps its scratch -- the per-call view,
  * scene and image tables and the work counter -- in one static device array of
  * MIRRES_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process

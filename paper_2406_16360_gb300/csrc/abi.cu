@@ -163,7 +163,8 @@ static mirres_status check_params(const mirres_params* p)
     if (!p) return arg_error("params is NULL");
     if (p->ris_m < 1) return arg_error("ris_m must be >= 1");
     if (p->grad_mode != 0) return arg_error("grad_mode: only 0 (PRIMARY) is implemented");
-    if (p->launch != 0 && p->launch != 1) return arg_error("launch must be 0 (plain) or 1 (batched)");
+    if (p->launch < 0 || p->launch > 2)
+        return arg_error("launch must be 0 (plain), 1 (batched wavefront) or 2 (persistent kernel)");
     if (p->block != 0 && (p->block < 32 || p->block > 1024 || p->block % 32))
         return arg_error("block must be 0 or a multiple of 32 in [32, 1024]");
     if (p->blocks_per_sm < 0) return arg_error("blocks_per_sm must be >= 0");
@@ -200,6 +201,11 @@ extern "C" mirres_status mirres_context_destroy(mirres_context* ctx)
     if (!ctx) return arg_error("ctx is NULL");
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    for (int i = 0; i < ctx->n_stage_events; ++i) cudaEventDestroy(ctx->stage_events[i]);
+    delete[] ctx->stage_events;
+    delete[] ctx->stage_kind;
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->queue_cnt) cudaFree(ctx->queue_cnt);
@@ -293,6 +299,127 @@ static Rng make_rng(const mirres_params* p)
     return r;
 }
 
+// samples per wave of the batched wavefront
+static const uint64_t kWave = 1ull << 24;
+
+struct GraphKey {
+    uint64_t total, total_pix, wave;
+    int32_t n_views, n_scenes, max_b, M, sms, flags;
+    uint32_t k0, k1;
+    const void* tape;
+    const void* ws;
+    size_t ws_bytes;
+};
+
+// Batched wavefront: tables uploaded to the workspace, then the whole forward replayed from a
+// CUDA graph captured on the context's capture stream (re-captured when the shape, the tape,
+// the seed or the workspace changes).
+static mirres_status stage_events(mirres_context* ctx, int pairs)
+{
+    if (ctx->n_stage_events >= 2 * pairs) return MIRRES_OK;
+    for (int i = 0; i < ctx->n_stage_events; ++i) cudaEventDestroy(ctx->stage_events[i]);
+    delete[] ctx->stage_events;
+    delete[] ctx->stage_kind;
+    ctx->stage_events = new cudaEvent_t[(size_t)2 * pairs];
+    ctx->stage_kind = new int[(size_t)pairs];
+    ctx->n_stage_events = 0;
+    for (int i = 0; i < 2 * pairs; ++i) {
+        MR_CUDA(cudaEventCreate(&ctx->stage_events[i]));
+        ctx->n_stage_events = i + 1;
+    }
+    return MIRRES_OK;
+}
+
+static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev>& sdev,
+                                 const std::vector<ViewDev>& vdev, uint64_t total, float* const* images, void* tape,
+                                 int M, Rng rng, int flags, cudaStream_t st)
+{
+    const int n_views = (int)vdev.size(), n_scenes = (int)sdev.size();
+    int max_b = 1;
+    uint64_t total_pix = 0;
+    std::vector<uint64_t> pixoff((size_t)n_views);
+    for (int i = 0; i < n_views; ++i) {
+        max_b = std::max(max_b, vdev[(size_t)i].bounces);
+        pixoff[(size_t)i] = total_pix;
+        total_pix += (uint64_t)vdev[(size_t)i].width * vdev[(size_t)i].height;
+    }
+    const uint64_t wave = std::min<uint64_t>(total, kWave);
+    Carver plan(nullptr);
+    plan.take<char>(tape ? 0 : 36ull * total);
+    plan.take<ViewDev>((size_t)n_views);
+    plan.take<SceneDev>((size_t)n_scenes);
+    plan.take<float*>((size_t)n_views);
+    plan.take<uint64_t>((size_t)n_views);
+    plan.take<unsigned int>(3 * (size_t)max_b + 3);
+    plan.take<float4>(16ull * wave);
+    MR_TRY(ws_reserve(ctx, plan.off));
+    Carver cv(ctx->ws.ptr);
+    void* internal_tape = cv.take<char>(tape ? 0 : 36ull * total);
+    void* tp = tape ? tape : internal_tape;
+    ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
+    SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
+    float** d_images = cv.take<float*>((size_t)n_views);
+    uint64_t* d_pixoff = cv.take<uint64_t>((size_t)n_views);
+    unsigned int* qc = cv.take<unsigned int>(3 * (size_t)max_b + 3);
+    QueueDev qa{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+    QueueDev qb{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+    QueueDev hq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+    ShadowDev sq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+    MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_images, images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_pixoff, pixoff.data(), sizeof(uint64_t) * pixoff.size(), cudaMemcpyHostToDevice, st));
+
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.total = total;
+    key.total_pix = total_pix;
+    key.wave = wave;
+    key.n_views = n_views;
+    key.n_scenes = n_scenes;
+    key.max_b = max_b;
+    key.M = M;
+    key.sms = ctx->sm_count;
+    key.flags = flags & 1;
+    key.k0 = rng.k0;
+    key.k1 = rng.k1;
+    key.tape = tp;
+    key.ws = ctx->ws.ptr;
+    key.ws_bytes = ctx->ws.bytes;
+    static_assert(sizeof(GraphKey) <= sizeof(ctx->graph_key), "graph key too large");
+    if (!ctx->graph || std::memcmp(ctx->graph_key, &key, sizeof(key)) != 0) {
+        if (ctx->graph) {
+            cudaGraphExecDestroy(ctx->graph);
+            ctx->graph = nullptr;
+        }
+        if (!ctx->capture_stream) MR_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        const int pairs = mr_wave_stage_pairs(total, wave, max_b);
+        if (flags & 1) MR_TRY(stage_events(ctx, pairs));
+        MR_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave, qa, qb, hq, sq, qc, tp, ctx->counters,
+                       d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
+                       (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr);
+        ctx->stage_pairs = (flags & 1) ? pairs : 0;
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
+        if (ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return mr_cuda_status(ec, "mirres_render: graph capture");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            ctx->graph = nullptr;
+            return mr_cuda_status(ei, "mirres_render: graph instantiation");
+        }
+        std::memcpy(ctx->graph_key, &key, sizeof(key));
+        ctx->graph_launches = (unsigned long long)mr_wave_launches(total, wave, max_b);
+    }
+    MR_CUDA(cudaGraphLaunch(ctx->graph, st));
+    ctx->host_launches += ctx->graph_launches;
+    return MIRRES_OK;
+}
+
 extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
                                        const mirres_view* views, int32_t n_views, const mirres_params* params,
                                        float* const* images, void* tape, size_t tape_bytes, void* stream)
@@ -316,8 +443,10 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     const int M = params->ris_m;
     const int sms = ctx->sm_count;
 
+    if (params->launch == 1) return render_wave(ctx, sdev, vdev, total, images, tape, M, rng, params->flags, st);
+
     // workspace layout
-    const bool batched = params->launch == 1;
+    const bool batched = params->launch == 2;
     const uint32_t chunk = (uint32_t)std::min<uint64_t>(max_view, kChunk);
     Carver plan(nullptr);
     plan.take<char>(tape ? 0 : 36ull * total);
@@ -349,10 +478,15 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
         MR_CUDA(cudaMemcpyAsync(d_images, images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
         MR_CUDA(cudaMemcpyAsync(d_pixoff, pixoff.data(), sizeof(uint64_t) * pixoff.size(), cudaMemcpyHostToDevice, st));
         MR_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), st));
-        const int block = params->block ? params->block : 128;
-        const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy(block);
-        MR_CUDA(mr_launch_persistent(d_scenes, d_views, n_views, total, rng, M, d_work, 32u * 8u, tp, ctx->counters,
-                                     block, per_sm * sms, st));
+        int var = mr_persistent_pick(params->block, params->blocks_per_sm);
+        unsigned int chunk_w = 256;
+        if (params->block == 0 && ctx->tuned_variant >= 0) {
+            var = ctx->tuned_variant;
+            chunk_w = ctx->tuned_chunk;
+        }
+        const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy_v(var);
+        MR_CUDA(mr_launch_persistent_v(var, d_scenes, d_views, n_views, total, rng, M, d_work, chunk_w, tp,
+                                       ctx->counters, per_sm * sms, st));
         mr_launch_resolve_all(d_views, n_views, d_pixoff, tp_pix, d_images, tp, total, sms, st);
         MR_CUDA(cudaGetLastError());
         ctx->host_launches += 2;
@@ -379,7 +513,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
                 const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
                 mr_launch_closest(s, v, b, cur, cnt_in, n, n, hq, qc + 3 * b, tp, total, sms, st);
                 mr_launch_shade(s, v, rng, b, M, hq, qc + 3 * b, n, nxt, qc + 3 * b + 1, sq, qc + 3 * b + 2, tp,
-                                total, sms, st);
+                                total, ctx->counters, sms, st);
                 mr_launch_shadow(s, v, b, sq, qc + 3 * b + 2, n, tp, total, sms, st);
                 std::swap(cur, nxt);
             }
@@ -390,6 +524,121 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
         ctx->host_launches += 1;
     }
     MR_CUDA(cudaGetLastError());
+    return MIRRES_OK;
+}
+
+// ---- autotuning of the persistent launch -----------------------------------------------------
+extern "C" mirres_status mirres_autotune(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                         const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                         void* tape, size_t tape_bytes, uint64_t budget_samples,
+                                         int32_t* out_block, int32_t* out_blocks_per_sm, int32_t* out_chunk,
+                                         float* out_ms, void* stream)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    MR_TRY(check_params(params));
+    std::vector<SceneDev> sdev;
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev));
+    std::vector<ViewDev> vdev;
+    uint64_t total = 0, max_view = 0;
+    MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
+    if (!tape || tape_bytes < 36ull * total) return arg_error("mirres_autotune needs the full tape of these views");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    const uint64_t n = std::max<uint64_t>(1, std::min<uint64_t>(budget_samples ? budget_samples : total, total));
+    Carver plan(nullptr);
+    plan.take<ViewDev>((size_t)n_views);
+    plan.take<SceneDev>((size_t)n_scenes);
+    plan.take<unsigned long long>(1);
+    MR_TRY(ws_reserve(ctx, plan.off));
+    Carver cv(ctx->ws.ptr);
+    ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
+    SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
+    unsigned long long* d_work = cv.take<unsigned long long>(1);
+    MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0, e1;
+    MR_CUDA(cudaEventCreate(&e0));
+    MR_CUDA(cudaEventCreate(&e1));
+    const unsigned int chunks[] = {64u, 256u, 1024u};
+    float best = 1e30f;
+    int best_v = mr_persistent_pick(0, 0);
+    unsigned int best_c = 256u;
+    const Rng rng = make_rng(params);
+    mirres_status status = MIRRES_OK;
+    for (int v = 0; v < mr_persistent_variants() && status == MIRRES_OK; ++v) {
+        const int blocks = mr_persistent_occupancy_v(v) * ctx->sm_count;
+        for (unsigned int c : chunks) {
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run warms caches and clocks
+                cudaError_t e = cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), st);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess)
+                    e = mr_launch_persistent_v(v, d_scenes, d_views, n_views, n, rng, params->ris_m, d_work, c, tape,
+                                               ctx->counters, blocks, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    status = mr_cuda_status(e, "mirres_autotune");
+                    break;
+                }
+            }
+            if (status != MIRRES_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+                best_c = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != MIRRES_OK) return status;
+    ctx->tuned_variant = best_v;
+    ctx->tuned_chunk = best_c;
+    int blk, minb;
+    mr_persistent_variant_shape(best_v, &blk, &minb);
+    if (out_block) *out_block = blk;
+    if (out_blocks_per_sm) *out_blocks_per_sm = minb;
+    if (out_chunk) *out_chunk = (int32_t)best_c;
+    if (out_ms) *out_ms = best;
+    ctx->host_launches += (unsigned long long)mr_persistent_variants() * 6;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_set_launch(mirres_context* ctx, int32_t block, int32_t blocks_per_sm, int32_t chunk)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    if (block == 0) {
+        ctx->tuned_variant = -1;
+        ctx->tuned_chunk = 256;
+        return MIRRES_OK;
+    }
+    if (chunk < 1) return arg_error("chunk must be >= 1");
+    ctx->tuned_variant = mr_persistent_pick(block, blocks_per_sm);
+    ctx->tuned_chunk = (unsigned int)chunk;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_stage_times(mirres_context* ctx, double out_ms[4], int32_t out_launches[4])
+{
+    if (!ctx || !out_ms) return arg_error("ctx and out_ms must not be NULL");
+    for (int k = 0; k < 4; ++k) {
+        out_ms[k] = 0.0;
+        if (out_launches) out_launches[k] = 0;
+    }
+    if (ctx->stage_pairs == 0) {
+        g_err = "mirres_stage_times: no batched render with params.flags bit 0 was captured";
+        return MIRRES_ERR_STATE;
+    }
+    MR_CUDA(cudaSetDevice(ctx->device));
+    for (int p = 0; p < ctx->stage_pairs; ++p) {
+        MR_CUDA(cudaEventSynchronize(ctx->stage_events[2 * p + 1]));
+        float ms = 0.0f;
+        MR_CUDA(cudaEventElapsedTime(&ms, ctx->stage_events[2 * p], ctx->stage_events[2 * p + 1]));
+        out_ms[ctx->stage_kind[p]] += ms;
+        if (out_launches) out_launches[ctx->stage_kind[p]] += 1;
+    }
     return MIRRES_OK;
 }
 

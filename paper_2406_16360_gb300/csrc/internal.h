@@ -35,6 +35,17 @@ struct mirres_context {
     unsigned int* queue_cnt = nullptr;       // device scratch counters [64]
     cudaStream_t last_stream = nullptr;
     unsigned long long host_launches = 0;
+    int tuned_variant = -1;     // persistent-kernel launch shape chosen by mirres_autotune
+    unsigned int tuned_chunk = 256;
+    // batched wavefront: the captured forward and the arguments it was captured for
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    unsigned char graph_key[128] = {};
+    unsigned long long graph_launches = 0;  // kernel launches inside the graph
+    cudaEvent_t* stage_events = nullptr;     // [n_stage_events]: (start, end) pairs per stage launch
+    int n_stage_events = 0;
+    int stage_pairs = 0;                     // pairs recorded by the current graph
+    int* stage_kind = nullptr;               // [n_stage_events / 2]: 0 closest, 1 shade, 2 shadow, 3 raygen
 };
 
 struct mirres_scene {

@@ -1,0 +1,135 @@
+// path.cuh -- per-path device code shared by the plain wavefront, the batched wavefront and
+// the persistent kernels: the tape layout, one shading vertex (RIS + shadow ray + continuation)
+// and warp-aggregated queue appends.
+#pragma once
+
+#include "device.cuh"
+
+namespace {
+
+struct TapeDev {
+    int32_t* tri;
+    int32_t* cand;
+    float* wv;
+    float* lind[3];
+    float* rad[3];
+};
+
+__device__ __forceinline__ TapeDev tape_of(void* base, uint64_t n)
+{
+    TapeDev t;
+    uint32_t* w = reinterpret_cast<uint32_t*>(base);
+    t.tri = reinterpret_cast<int32_t*>(w);
+    t.cand = reinterpret_cast<int32_t*>(w + n);
+    t.wv = reinterpret_cast<float*>(w + 2 * n);
+    for (int k = 0; k < 3; ++k) t.lind[k] = reinterpret_cast<float*>(w + (3 + k) * n);
+    for (int k = 0; k < 3; ++k) t.rad[k] = reinterpret_cast<float*>(w + (6 + k) * n);
+    return t;
+}
+
+// ---------------------------------------------------------------------------------------
+// one shading vertex: RIS over M env candidates (Eq. restir, streamed through a weighted
+// reservoir), the shadow ray that tests the selected candidate, and the continuation ray
+// drawn from the MIS mixture (Eq. mc_indir). Shared by the wavefront and persistent kernels.
+// ---------------------------------------------------------------------------------------
+struct VertexOut {
+    bool shadow;
+    float3 sh_o, sh_d;
+    float3 add_rad, add_lind;
+    bool cont;
+    float3 c_d, c_beta, c_bind;
+    float3 x;
+    int cand;
+    float W;
+};
+
+__device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, const Rng& rng, uint32_t pixel,
+                                             uint32_t smp, uint32_t view, int b, int B, int M, const Hit& h,
+                                             float3 d, float3 beta, float3 bind, VertexOut& out)
+{
+    Shade sh;
+    shade_at(s, h.tri, h.u, h.v, d, sh);
+    const float3 wo = f3(-d.x, -d.y, -d.z);
+    out.x = sh.x;
+    out.shadow = false;
+    out.cont = false;
+    out.cand = -1;
+    out.W = 0.0f;
+    if (env_ok && M > 0) {
+        float wsum = 0.0f, phat_sel = 0.0f;
+        int sel = -1, ytex = 0;
+        float3 ysel = f3(0.f, 0.f, 0.f), fsel = f3(0.f, 0.f, 0.f);
+        for (int j = 0; j < M; ++j) {
+            const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j);
+            float3 dir;
+            int tex;
+            const float q = env_sample(s, x.x, x.y, x.w, dir, tex);
+            const float3 fc = brdf_cos(sh.n, wo, dir, sh.m);
+            const float4 L = __ldg(s.env_texel + tex);
+            const float phat = lum(xyz(L)) * lum(fc);  // p_hat = Y(L_env) Y(f_r) cos
+            const float gamma = phat / q;              // gamma = p_hat / q_dir
+            wsum += gamma;
+            if (u24(x.z) * wsum < gamma) {
+                sel = j;
+                ytex = tex;
+                ysel = dir;
+                fsel = fc;
+                phat_sel = phat;
+            }
+        }
+        if (sel >= 0 && wsum > 0.0f) {
+            const float W = wsum / ((float)M * phat_sel);
+            const float4 L = __ldg(s.env_texel + ytex);
+            const float3 contrib = mul(hmul(xyz(L), fsel), W);
+            out.add_rad = hmul_rn(beta, contrib);
+            out.add_lind = (b >= 1) ? hmul_rn(bind, contrib) : f3(0.f, 0.f, 0.f);
+            out.shadow = true;
+            out.sh_o = sh.x;
+            out.sh_d = ysel;
+            if (b == 0) {
+                out.cand = sel;
+                out.W = W;
+            }
+        }
+    }
+    if (b < B - 1) {
+        const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CONTINUE, 0u);
+        float3 wc;
+        const float pind = sample_continuation(s, env_ok, sh.n, wo, sh.m, x, wc);
+        const float3 fc = brdf_cos(sh.n, wo, wc, sh.m);
+        if (pind > 0.0f && (fc.x > 0.0f || fc.y > 0.0f || fc.z > 0.0f)) {
+            const float3 f = f3(fc.x / pind, fc.y / pind, fc.z / pind);
+            out.cont = true;
+            out.c_d = wc;
+            out.c_beta = hmul_rn(beta, f);
+            out.c_bind = (b >= 1) ? hmul_rn(bind, f) : bind;
+        }
+    }
+}
+
+__device__ __forceinline__ const ViewDev& view_of(const ViewDev* views, int n, uint64_t g, int& vi)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].offset <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    vi = lo;
+    return views[lo];
+}
+
+
+// warp-aggregated append: returns the slot of this lane (valid only if want)
+__device__ __forceinline__ unsigned int warp_append(bool want, unsigned int* counter)
+{
+    const unsigned m = __ballot_sync(MR_FULL, want);
+    if (!m) return 0u;
+    const int leader = __ffs(m) - 1;
+    unsigned int base = 0;
+    if (lane_id() == leader) base = atomicAdd(counter, (unsigned)__popc(m));
+    base = __shfl_sync(MR_FULL, base, leader);
+    return base + __popc(m & lanemask_lt());
+}
+
+}  // namespace

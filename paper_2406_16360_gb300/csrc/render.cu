@@ -5,120 +5,9 @@
 // primary vertex, V*W at the primary vertex, L_ind (3) at the primary vertex, radiance (3).
 // The image is the mean of the sample radiances over spp, summed in sample order.
 #include "render.h"
+#include "path.cuh"
 
 namespace {
-
-struct TapeDev {
-    int32_t* tri;
-    int32_t* cand;
-    float* wv;
-    float* lind[3];
-    float* rad[3];
-};
-
-__device__ __forceinline__ TapeDev tape_of(void* base, uint64_t n)
-{
-    TapeDev t;
-    uint32_t* w = reinterpret_cast<uint32_t*>(base);
-    t.tri = reinterpret_cast<int32_t*>(w);
-    t.cand = reinterpret_cast<int32_t*>(w + n);
-    t.wv = reinterpret_cast<float*>(w + 2 * n);
-    for (int k = 0; k < 3; ++k) t.lind[k] = reinterpret_cast<float*>(w + (3 + k) * n);
-    for (int k = 0; k < 3; ++k) t.rad[k] = reinterpret_cast<float*>(w + (6 + k) * n);
-    return t;
-}
-
-// ---------------------------------------------------------------------------------------
-// one shading vertex: RIS over M env candidates (Eq. restir, streamed through a weighted
-// reservoir), the shadow ray that tests the selected candidate, and the continuation ray
-// drawn from the MIS mixture (Eq. mc_indir). Shared by the wavefront and persistent kernels.
-// ---------------------------------------------------------------------------------------
-struct VertexOut {
-    bool shadow;
-    float3 sh_o, sh_d;
-    float3 add_rad, add_lind;
-    bool cont;
-    float3 c_d, c_beta, c_bind;
-    float3 x;
-    int cand;
-    float W;
-};
-
-__device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, const Rng& rng, uint32_t pixel,
-                                             uint32_t smp, uint32_t view, int b, int B, int M, const Hit& h,
-                                             float3 d, float3 beta, float3 bind, VertexOut& out)
-{
-    Shade sh;
-    shade_at(s, h.tri, h.u, h.v, d, sh);
-    const float3 wo = f3(-d.x, -d.y, -d.z);
-    out.x = sh.x;
-    out.shadow = false;
-    out.cont = false;
-    out.cand = -1;
-    out.W = 0.0f;
-    if (env_ok && M > 0) {
-        float wsum = 0.0f, phat_sel = 0.0f;
-        int sel = -1, ytex = 0;
-        float3 ysel = f3(0.f, 0.f, 0.f), fsel = f3(0.f, 0.f, 0.f);
-        for (int j = 0; j < M; ++j) {
-            const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j);
-            float3 dir;
-            int tex;
-            const float q = env_sample(s, x.x, x.y, x.w, dir, tex);
-            const float3 fc = brdf_cos(sh.n, wo, dir, sh.m);
-            const float4 L = __ldg(s.env_texel + tex);
-            const float phat = lum(xyz(L)) * lum(fc);  // p_hat = Y(L_env) Y(f_r) cos
-            const float gamma = phat / q;              // gamma = p_hat / q_dir
-            wsum += gamma;
-            if (u24(x.z) * wsum < gamma) {
-                sel = j;
-                ytex = tex;
-                ysel = dir;
-                fsel = fc;
-                phat_sel = phat;
-            }
-        }
-        if (sel >= 0 && wsum > 0.0f) {
-            const float W = wsum / ((float)M * phat_sel);
-            const float4 L = __ldg(s.env_texel + ytex);
-            const float3 contrib = mul(hmul(xyz(L), fsel), W);
-            out.add_rad = hmul_rn(beta, contrib);
-            out.add_lind = (b >= 1) ? hmul_rn(bind, contrib) : f3(0.f, 0.f, 0.f);
-            out.shadow = true;
-            out.sh_o = sh.x;
-            out.sh_d = ysel;
-            if (b == 0) {
-                out.cand = sel;
-                out.W = W;
-            }
-        }
-    }
-    if (b < B - 1) {
-        const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CONTINUE, 0u);
-        float3 wc;
-        const float pind = sample_continuation(s, env_ok, sh.n, wo, sh.m, x, wc);
-        const float3 fc = brdf_cos(sh.n, wo, wc, sh.m);
-        if (pind > 0.0f && (fc.x > 0.0f || fc.y > 0.0f || fc.z > 0.0f)) {
-            const float3 f = f3(fc.x / pind, fc.y / pind, fc.z / pind);
-            out.cont = true;
-            out.c_d = wc;
-            out.c_beta = hmul_rn(beta, f);
-            out.c_bind = (b >= 1) ? hmul_rn(bind, f) : bind;
-        }
-    }
-}
-
-__device__ __forceinline__ const ViewDev& view_of(const ViewDev* views, int n, uint64_t g, int& vi)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (views[mid].offset <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    vi = lo;
-    return views[lo];
-}
 
 // ---------------------------------------------------------------------------------------
 // wavefront (plain) kernels: one view chunk at a time
@@ -151,17 +40,6 @@ __global__ void __launch_bounds__(256) k_raygen(ViewDev v, Rng rng, uint32_t fir
 }
 
 
-// warp-aggregated append: returns the slot of this lane (valid only if want)
-__device__ __forceinline__ unsigned int warp_append(bool want, unsigned int* counter)
-{
-    const unsigned m = __ballot_sync(MR_FULL, want);
-    if (!m) return 0u;
-    const int leader = __ffs(m) - 1;
-    unsigned int base = 0;
-    if (lane_id() == leader) base = atomicAdd(counter, (unsigned)__popc(m));
-    base = __shfl_sync(MR_FULL, base, leader);
-    return base + __popc(m & lanemask_lt());
-}
 
 // closest hit of every queued ray. A primary ray that escapes writes the environment into
 // its sample; an escaping continuation ray ends its path. Hits are compacted (warp ballot)
@@ -209,10 +87,11 @@ __global__ void __launch_bounds__(256) k_closest(SceneDev s, ViewDev v, int b, Q
 __global__ void __launch_bounds__(256) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev hq,
                                                const unsigned int* count_hit, QueueDev qout,
                                                unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
-                                               void* tape, uint64_t ntot)
+                                               void* tape, uint64_t ntot, unsigned long long* counters)
 {
     const TapeDev tp = tape_of(tape, ntot);
     const unsigned int n = *count_hit;
+    unsigned long long n_cand = 0;
     const int env_ok = *s.env_ok_dev;
     const unsigned int stride = gridDim.x * blockDim.x;
     const unsigned int rounds = (n + stride - 1) / stride;
@@ -238,6 +117,7 @@ __global__ void __launch_bounds__(256) k_shade(SceneDev s, ViewDev v, Rng rng, i
             h.tri = tri;
             shade_vertex(s, env_ok, rng, pixel, smp, (uint32_t)v.index, b, v.bounces, M, h, d, xyz(hq.b[i]),
                          xyz(hq.bi[i]), out);
+            if (env_ok) n_cand += (unsigned long long)M;
             if (b == 0) {
                 tp.tri[g] = tri;
                 tp.cand[g] = out.cand;
@@ -259,6 +139,8 @@ __global__ void __launch_bounds__(256) k_shade(SceneDev s, ViewDev v, Rng rng, i
             qout.bi[cs] = make_float4(out.c_bind.x, out.c_bind.y, out.c_bind.z, 0.f);
         }
     }
+    for (int off = 16; off > 0; off >>= 1) n_cand += __shfl_xor_sync(MR_FULL, n_cand, off);
+    if (lane_id() == 0 && n_cand) atomicAdd(counters + 5, n_cand);
 }
 
 // shadow rays: any hit; unoccluded rays add their contribution to the sample
@@ -312,9 +194,10 @@ __global__ void __launch_bounds__(256) k_resolve(ViewDev v, const void* tape, ui
 // take the next one), so that the expensive part -- shading with RIS over M candidates --
 // runs on full warps; then the shadow rays of those vertices are traced.
 // ---------------------------------------------------------------------------------------
-__global__ void k_persistent(const SceneDev* __restrict__ scenes, const ViewDev* __restrict__ views, int n_views,
-                             uint64_t total, Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
-                             unsigned long long* counters)
+__device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ scenes,
+                                                const ViewDev* __restrict__ views, int n_views, uint64_t total,
+                                                Rng rng, int M, unsigned long long* work, uint32_t chunk,
+                                                void* tape, unsigned long long* counters)
 {
     extern __shared__ uint32_t sstk[];
     const TapeDev tp = tape_of(tape, total);
@@ -476,6 +359,16 @@ __global__ void k_persistent(const SceneDev* __restrict__ scenes, const ViewDev*
         atomicAdd(counters + 2, n_shadow);
         atomicAdd(counters + 5, n_cand);
     }
+}
+
+// launch-shape variants: the register cap of each (block size, resident blocks per SM)
+// pair is set by __launch_bounds__; the autotuner times them on the workload
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
+    k_persistent(const SceneDev* __restrict__ scenes, const ViewDev* __restrict__ views, int n_views, uint64_t total,
+                 Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape, unsigned long long* counters)
+{
+    persistent_body(scenes, views, n_views, total, rng, M, work, chunk, tape, counters);
 }
 
 // resolve every view of a batch in one launch: one thread per pixel over all views
@@ -864,10 +757,11 @@ void mr_launch_closest(const SceneDev& s, const ViewDev& v, int b, const QueueDe
 
 void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& hq,
                      const unsigned int* count_hit, uint64_t upper, const QueueDev& qout, unsigned int* count_out,
-                     const ShadowDev& sq, unsigned int* count_sh, void* tape, uint64_t ntot, int sms, cudaStream_t st)
+                     const ShadowDev& sq, unsigned int* count_sh, void* tape, uint64_t ntot,
+                     unsigned long long* counters, int sms, cudaStream_t st)
 {
     k_shade<<<grid_cap(upper, 256, sms * 8), 256, 0, st>>>(s, v, rng, b, M, hq, count_hit, qout, count_out, sq,
-                                                          count_sh, tape, ntot);
+                                                          count_sh, tape, ntot, counters);
 }
 
 void mr_launch_shadow(const SceneDev& s, const ViewDev& v, int b, const ShadowDev& sq, const unsigned int* count,
@@ -881,27 +775,82 @@ void mr_launch_resolve(const ViewDev& v, const void* tape, uint64_t ntot, float*
     k_resolve<<<grid_cap((uint64_t)v.width * v.height, 256, sms * 8), 256, 0, st>>>(v, tape, ntot, img);
 }
 
-cudaError_t mr_launch_persistent(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
-                                 int M, unsigned long long* work, uint32_t chunk, void* tape,
-                                 unsigned long long* counters, int block, int blocks, cudaStream_t st)
+typedef void (*PersistentFn)(const SceneDev*, const ViewDev*, int, uint64_t, Rng, int, unsigned long long*, uint32_t,
+                             void*, unsigned long long*);
+
+struct PersistentVariant {
+    int block, minb;
+    PersistentFn fn;
+};
+
+static const PersistentVariant kVariants[] = {
+    {128, 2, k_persistent<128, 2>}, {128, 3, k_persistent<128, 3>}, {128, 4, k_persistent<128, 4>},
+    {128, 5, k_persistent<128, 5>}, {128, 6, k_persistent<128, 6>}, {256, 2, k_persistent<256, 2>},
+    {256, 3, k_persistent<256, 3>}, {64, 8, k_persistent<64, 8>},
+};
+
+int mr_persistent_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
+
+void mr_persistent_variant_shape(int v, int* block, int* minb)
 {
-    const size_t smem = stack_bytes(block);
-    cudaError_t e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_persistent<<<blocks, block, smem, st>>>(scenes, views, n_views, total, rng, M, work, chunk, tape, counters);
-    return cudaGetLastError();
+    *block = kVariants[v].block;
+    *minb = kVariants[v].minb;
 }
 
-int mr_persistent_occupancy(int block)
+// variant for a requested (block, blocks per SM): the same block size with the nearest
+// register cap; block 0 (or no variant of that size) = the default (128, 3)
+int mr_persistent_pick(int block, int per_sm)
 {
+    const int dflt = 1;
+    if (block == 0) return dflt;
+    const int want = per_sm ? per_sm : 3;
+    int best = -1, bestd = 1 << 30;
+    for (int i = 0; i < mr_persistent_variants(); ++i) {
+        if (kVariants[i].block != block) continue;
+        const int d = abs(kVariants[i].minb - want);
+        if (d < bestd) {
+            bestd = d;
+            best = i;
+        }
+    }
+    return best < 0 ? dflt : best;
+}
+
+int mr_persistent_occupancy_v(int v)
+{
+    const PersistentVariant& pv = kVariants[v];
+    const size_t smem = stack_bytes(pv.block);
+    cudaFuncSetAttribute(pv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
-    cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stack_bytes(block));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent, block, stack_bytes(block)) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pv.fn, pv.block, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     return n < 1 ? 1 : n;
 }
+
+cudaError_t mr_launch_persistent_v(int v, const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total,
+                                   Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
+                                   unsigned long long* counters, int blocks, cudaStream_t st)
+{
+    const PersistentVariant& pv = kVariants[v];
+    const size_t smem = stack_bytes(pv.block);
+    cudaError_t e = cudaFuncSetAttribute(pv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    pv.fn<<<blocks, pv.block, smem, st>>>(scenes, views, n_views, total, rng, M, work, chunk, tape, counters);
+    return cudaGetLastError();
+}
+
+// the launch used before variants existed: (block, blocks per SM) mapped to a variant
+cudaError_t mr_launch_persistent(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
+                                 int M, unsigned long long* work, uint32_t chunk, void* tape,
+                                 unsigned long long* counters, int block, int blocks, cudaStream_t st)
+{
+    const int v = mr_persistent_pick(block, 0);
+    return mr_launch_persistent_v(v, scenes, views, n_views, total, rng, M, work, chunk, tape, counters, blocks, st);
+}
+
+int mr_persistent_occupancy(int block) { return mr_persistent_occupancy_v(mr_persistent_pick(block, 0)); }
 
 void mr_launch_resolve_all(const ViewDev* views, int n_views, const uint64_t* pix_off, uint64_t total_pix,
                            float* const* images, const void* tape, uint64_t ntot, int sms, cudaStream_t st)

@@ -34,7 +34,8 @@ void mr_launch_closest(const SceneDev& s, const ViewDev& v, int b, const QueueDe
                        void* tape, uint64_t ntot, int sms, cudaStream_t st);
 void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& hq,
                      const unsigned int* count_hit, uint64_t upper, const QueueDev& qout, unsigned int* count_out,
-                     const ShadowDev& sq, unsigned int* count_sh, void* tape, uint64_t ntot, int sms, cudaStream_t st);
+                     const ShadowDev& sq, unsigned int* count_sh, void* tape, uint64_t ntot,
+                     unsigned long long* counters, int sms, cudaStream_t st);
 void mr_launch_shadow(const SceneDev& s, const ViewDev& v, int b, const ShadowDev& sq, const unsigned int* count,
                       uint64_t upper, void* tape, uint64_t ntot, int sms, cudaStream_t st);
 void mr_launch_resolve(const ViewDev& v, const void* tape, uint64_t ntot, float* img, int sms, cudaStream_t st);
@@ -44,6 +45,13 @@ cudaError_t mr_launch_persistent(const SceneDev* scenes, const ViewDev* views, i
                                  int M, unsigned long long* work, uint32_t chunk, void* tape,
                                  unsigned long long* counters, int block, int blocks, cudaStream_t st);
 int mr_persistent_occupancy(int block);
+int mr_persistent_variants();
+void mr_persistent_variant_shape(int v, int* block, int* minb);
+int mr_persistent_pick(int block, int per_sm);
+int mr_persistent_occupancy_v(int v);
+cudaError_t mr_launch_persistent_v(int v, const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total,
+                                   Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
+                                   unsigned long long* counters, int blocks, cudaStream_t st);
 void mr_launch_resolve_all(const ViewDev* views, int n_views, const uint64_t* pix_off, uint64_t total_pix,
                            float* const* images, const void* tape, uint64_t ntot, int sms, cudaStream_t st);
 void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
@@ -52,3 +60,12 @@ void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_view
 void mr_launch_l2(const float* img, const float* ref, int64_t n, float* dimg, float* loss, int sms, cudaStream_t st);
 void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* skip, int64_t n, int any,
                           int32_t* hit_tri, float* hit_tuv, int sms, cudaStream_t st);
+
+// wave.cu: the batched wavefront forward (recorded on a stream, captured as a graph)
+void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,
+                    Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,
+                    const ShadowDev& sq, unsigned int* qc, void* tape, unsigned long long* counters,
+                    const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaStream_t st,
+                    cudaEvent_t* ev, int* kind);
+int mr_wave_launches(uint64_t total, uint64_t wave, int max_bounces);
+int mr_wave_stage_pairs(uint64_t total, uint64_t wave, int max_bounces);

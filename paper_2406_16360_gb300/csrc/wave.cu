@@ -1,0 +1,240 @@
+// wave.cu -- batched wavefront: every view of every scene flattened into one sample space and
+// processed in large waves (ray generation, then per bounce: closest hit with hit compaction,
+// shading with RIS, shadow rays). Stage kernels are grid-stride loops over device-side queue
+// counts, so the whole forward is one fixed launch sequence that is captured once as a CUDA
+// graph and replayed. Each queued path carries its view index (in the w component of its
+// throughput), through which it finds its camera, spp, bounce count and scene.
+#include "path.cuh"
+#include "render.h"
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ views, int n_views, Rng rng,
+                                                 uint64_t first, uint32_t n, QueueDev q, void* tape, uint64_t ntot)
+{
+    const TapeDev tp = tape_of(tape, ntot);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t g = first + i;
+        int vi;
+        const ViewDev& v = view_of(views, n_views, g, vi);
+        const uint32_t sid = (uint32_t)(g - v.offset);
+        const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
+        const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+        const uint4 x = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_CAMERA, 0u);
+        const float3 d = camera_dir(v, px, py, u24(x.x), u24(x.y));
+        q.o[i] = make_float4(v.c2w[3], v.c2w[7], v.c2w[11], __int_as_float(-1));
+        q.d[i] = make_float4(d.x, d.y, d.z, __uint_as_float(sid));
+        q.b[i] = make_float4(1.f, 1.f, 1.f, __int_as_float(vi));
+        q.bi[i] = make_float4(1.f, 1.f, 1.f, 0.f);
+        tp.tri[g] = -1;
+        tp.cand[g] = -1;
+        tp.wv[g] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            tp.lind[k][g] = 0.0f;
+            tp.rad[k][g] = 0.0f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_wclosest(const SceneDev* __restrict__ scenes,
+                                                  const ViewDev* __restrict__ views, int b, QueueDev q,
+                                                  const unsigned int* count, unsigned int count_fixed, QueueDev hq,
+                                                  unsigned int* count_hit, void* tape, uint64_t ntot)
+{
+    extern __shared__ uint32_t sstk[];
+    const TapeDev tp = tape_of(tape, ntot);
+    const unsigned int n = count ? *count : count_fixed;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    const unsigned int rounds = (n + stride - 1) / stride;
+    for (unsigned int r = 0; r < rounds; ++r) {
+        const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        Hit h;
+        h.tri = -1;
+        float4 qd = make_float4(0.f, 0.f, 0.f, 0.f), qb = qd;
+        if (i < n) {
+            const float4 a = q.o[i];
+            qd = q.d[i];
+            qb = q.b[i];
+            const ViewDev& v = views[__float_as_int(qb.w)];
+            const SceneDev& s = scenes[v.scene];
+            traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), *s.tmin_dev, __int_as_float(0x7f800000), h,
+                            sstk + threadIdx.x, blockDim.x);
+            if (h.tri < 0 && b == 0) {
+                const uint64_t g = v.offset + __float_as_uint(qd.w);
+                const float4 L = __ldg(s.env_texel + env_texel_of(s, xyz(qd)));
+                tp.rad[0][g] = L.x;
+                tp.rad[1][g] = L.y;
+                tp.rad[2][g] = L.z;
+            }
+        }
+        const bool hit = h.tri >= 0;
+        const unsigned int slot = warp_append(hit, count_hit);
+        if (hit) {
+            hq.o[slot] = make_float4(h.t, h.u, h.v, __int_as_float(h.tri));
+            hq.d[slot] = qd;
+            hq.b[slot] = qb;
+            hq.bi[slot] = q.bi[i];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_wshade(const SceneDev* __restrict__ scenes,
+                                                const ViewDev* __restrict__ views, Rng rng, int b, int M,
+                                                QueueDev hq, const unsigned int* count_hit, QueueDev qout,
+                                                unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
+                                                void* tape, uint64_t ntot, unsigned long long* counters)
+{
+    const TapeDev tp = tape_of(tape, ntot);
+    const unsigned int n = *count_hit;
+    unsigned long long n_cand = 0;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    const unsigned int rounds = (n + stride - 1) / stride;
+    for (unsigned int r = 0; r < rounds; ++r) {
+        const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        VertexOut out;
+        out.shadow = false;
+        out.cont = false;
+        uint32_t sid = 0;
+        int tri = -1, vi = 0;
+        if (i < n) {
+            const float4 hd = hq.o[i];
+            const float4 qd = hq.d[i];
+            const float4 qb = hq.b[i];
+            vi = __float_as_int(qb.w);
+            const ViewDev& v = views[vi];
+            const SceneDev& s = scenes[v.scene];
+            sid = __float_as_uint(qd.w);
+            const uint64_t g = v.offset + sid;
+            tri = __float_as_int(hd.w);
+            const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
+            Hit h;
+            h.t = hd.x;
+            h.u = hd.y;
+            h.v = hd.z;
+            h.tri = tri;
+            const int env_ok = *s.env_ok_dev;
+            shade_vertex(s, env_ok, rng, pixel, smp, (uint32_t)v.index, b, v.bounces, M, h, xyz(qd), xyz(qb),
+                         xyz(hq.bi[i]), out);
+            if (env_ok) n_cand += (unsigned long long)M;
+            if (b == 0) {
+                tp.tri[g] = tri;
+                tp.cand[g] = out.cand;
+                tp.wv[g] = out.W;
+            }
+        }
+        const unsigned int ss = warp_append(out.shadow, count_sh);
+        if (out.shadow) {
+            sq.o[ss] = make_float4(out.sh_o.x, out.sh_o.y, out.sh_o.z, __int_as_float(tri));
+            sq.d[ss] = make_float4(out.sh_d.x, out.sh_d.y, out.sh_d.z, __uint_as_float(sid));
+            sq.add[ss] = make_float4(out.add_rad.x, out.add_rad.y, out.add_rad.z, __int_as_float(vi));
+            sq.addi[ss] = make_float4(out.add_lind.x, out.add_lind.y, out.add_lind.z, 0.f);
+        }
+        const unsigned int cs = warp_append(out.cont, count_out);
+        if (out.cont) {
+            qout.o[cs] = make_float4(out.x.x, out.x.y, out.x.z, __int_as_float(tri));
+            qout.d[cs] = make_float4(out.c_d.x, out.c_d.y, out.c_d.z, __uint_as_float(sid));
+            qout.b[cs] = make_float4(out.c_beta.x, out.c_beta.y, out.c_beta.z, __int_as_float(vi));
+            qout.bi[cs] = make_float4(out.c_bind.x, out.c_bind.y, out.c_bind.z, 0.f);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) n_cand += __shfl_xor_sync(MR_FULL, n_cand, off);
+    if (lane_id() == 0 && n_cand) atomicAdd(counters + 5, n_cand);
+}
+
+__global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ scenes,
+                                                 const ViewDev* __restrict__ views, int b, ShadowDev sq,
+                                                 const unsigned int* count, void* tape, uint64_t ntot)
+{
+    extern __shared__ uint32_t sstk[];
+    const TapeDev tp = tape_of(tape, ntot);
+    const unsigned int n = *count;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = sq.o[i], dd = sq.d[i], ad = sq.add[i];
+        const ViewDev& v = views[__float_as_int(ad.w)];
+        const SceneDev& s = scenes[v.scene];
+        Hit h;
+        traverse<true>(s, xyz(a), xyz(dd), __float_as_int(a.w), *s.tmin_dev, __int_as_float(0x7f800000), h,
+                       sstk + threadIdx.x, blockDim.x);
+        const uint64_t g = v.offset + __float_as_uint(dd.w);
+        if (h.tri < 0) {
+            const float4 ai = sq.addi[i];
+            tp.rad[0][g] = __fadd_rn(tp.rad[0][g], ad.x);
+            tp.rad[1][g] = __fadd_rn(tp.rad[1][g], ad.y);
+            tp.rad[2][g] = __fadd_rn(tp.rad[2][g], ad.z);
+            if (b >= 1) {
+                tp.lind[0][g] = __fadd_rn(tp.lind[0][g], ai.x);
+                tp.lind[1][g] = __fadd_rn(tp.lind[1][g], ai.y);
+                tp.lind[2][g] = __fadd_rn(tp.lind[2][g], ai.z);
+            }
+        } else if (b == 0) {
+            tp.wv[g] = 0.0f;
+        }
+    }
+}
+
+unsigned grid_cap(uint64_t n, int block, int cap)
+{
+    const uint64_t g = (n + block - 1) / block;
+    return (unsigned)(g < 1 ? 1 : (g > (uint64_t)cap ? (uint64_t)cap : g));
+}
+
+}  // namespace
+
+// Record the whole batched forward on `st` (capturable: kernels, memsets, event records).
+// With `ev` non-null, an event pair is recorded around every stage launch: ev[2k], ev[2k+1]
+// for pair k, whose stage kind (0 closest, 1 shade, 2 shadow, 3 raygen) goes to kind[k].
+void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,
+                    Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,
+                    const ShadowDev& sq, unsigned int* qc, void* tape, unsigned long long* counters,
+                    const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaStream_t st,
+                    cudaEvent_t* ev, int* kind)
+{
+    const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
+    int pair = 0;
+    auto mark = [&](int k, bool start) {
+        if (!ev) return;
+        if (start) kind[pair] = k;
+        cudaEventRecordWithFlags(ev[2 * pair + (start ? 0 : 1)], st, cudaEventRecordExternal);
+        if (!start) ++pair;
+    };
+    for (uint64_t first = 0; first < total; first += wave) {
+        const uint32_t n = (uint32_t)(total - first < wave ? total - first : wave);
+        cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (3 * max_bounces + 3), st);
+        mark(3, true);
+        k_wraygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(views, n_views, rng, first, n, qa, tape, total);
+        mark(3, false);
+        QueueDev cur = qa, nxt = qb;
+        for (int b = 0; b < max_bounces; ++b) {
+            const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
+            mark(0, true);
+            k_wclosest<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(scenes, views, b, cur, cnt_in, n, hq,
+                                                                     qc + 3 * b, tape, total);
+            mark(0, false);
+            mark(1, true);
+            k_wshade<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, b, M, hq, qc + 3 * b, nxt,
+                                                                qc + 3 * b + 1, sq, qc + 3 * b + 2, tape, total, counters);
+            mark(1, false);
+            mark(2, true);
+            k_wshadow<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(scenes, views, b, sq, qc + 3 * b + 2, tape, total);
+            mark(2, false);
+            QueueDev t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        mr_launch_account(counters, qc, max_bounces, n, st);
+    }
+    mr_launch_resolve_all(views, n_views, pix_off, total_pix, images, tape, total, sms, st);
+}
+
+int mr_wave_stage_pairs(uint64_t total, uint64_t wave, int max_bounces)
+{
+    const uint64_t waves = (total + wave - 1) / wave;
+    return (int)(waves * (1 + 3 * (uint64_t)max_bounces));
+}
+
+int mr_wave_launches(uint64_t total, uint64_t wave, int max_bounces)
+{
+    const uint64_t waves = (total + wave - 1) / wave;
+    return (int)(waves * (2 + 3 * (uint64_t)max_bounces) + 1);
+}

@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_view", "make_params",
            "mirres_context_create", "mirres_context_destroy", "mirres_scene_create", "mirres_scene_destroy",
            "mirres_bvh_build", "mirres_bvh_refit", "mirres_tape_bytes", "mirres_render", "mirres_render_noalloc",
-           "mirres_backward",
+           "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
 
@@ -52,7 +52,7 @@ class View(C.Structure):
 class Params(C.Structure):
     _fields_ = [("ris_m", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("grad_mode", C.c_int32),
                 ("launch", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flags", C.c_int32)]
 
 
 class Grads(C.Structure):
@@ -87,6 +87,11 @@ def lib():
                 "mirres_tape_bytes": (sz, [C.POINTER(View), i32]),
                 "mirres_render": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
                                        C.POINTER(vp), vp, sz, vp]),
+                "mirres_autotune": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params), vp, sz,
+                                         C.c_uint64, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                         C.POINTER(C.c_float), vp]),
+                "mirres_set_launch": (st, [vp, i32, i32, i32]),
+                "mirres_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(i32)]),
                 "mirres_render_noalloc": (st, [C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
                                                C.POINTER(vp), vp, sz, vp]),
                 "mirres_backward": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
@@ -162,9 +167,9 @@ def make_view(K, c2w, width, height, spp, bounces, scene=0) -> View:
                 int(height), int(spp), int(bounces), int(scene))
 
 
-def make_params(ris_m, seed=0, launch=0, block=0, blocks_per_sm=0, grad_mode=0) -> Params:
+def make_params(ris_m, seed=0, launch=0, block=0, blocks_per_sm=0, grad_mode=0, flags=0) -> Params:
     return Params(int(ris_m), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(grad_mode), int(launch), int(block),
-                  int(blocks_per_sm), 0)
+                  int(blocks_per_sm), int(flags))
 
 
 def _views(views):
@@ -223,6 +228,31 @@ def mirres_render(ctx: Context, scenes, views, params: Params, images, tape=None
     nbytes = 0 if tape is None else tape.numel() * tape.element_size()
     _check("mirres_render", lib().mirres_render(ctx.handle, sc, len(scenes), vs, len(vs), C.byref(params), im,
                                                 _ptr(tape), nbytes, _stream(stream)))
+
+
+def mirres_autotune(ctx: Context, scenes, views, params: Params, tape, budget_samples=0, stream=None):
+    """Returns dict(block, blocks_per_sm, chunk, ms) of the fastest persistent launch."""
+    vs = _views(views)
+    sc = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    b, m, c, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float()
+    nbytes = tape.numel() * tape.element_size()
+    _check("mirres_autotune", lib().mirres_autotune(ctx.handle, sc, len(scenes), vs, len(vs), C.byref(params),
+                                                    _ptr(tape), nbytes, int(budget_samples), C.byref(b), C.byref(m),
+                                                    C.byref(c), C.byref(ms), _stream(stream)))
+    return dict(block=b.value, blocks_per_sm=m.value, chunk=c.value, ms=ms.value)
+
+
+def mirres_set_launch(ctx: Context, block, blocks_per_sm, chunk):
+    _check("mirres_set_launch", lib().mirres_set_launch(ctx.handle, int(block), int(blocks_per_sm), int(chunk)))
+
+
+def mirres_stage_times(ctx: Context):
+    """(ms, launches) per stage of the last event-recording batched render: closest, shade, shadow, raygen."""
+    ms = (C.c_double * 4)()
+    n = (C.c_int32 * 4)()
+    _check("mirres_stage_times", lib().mirres_stage_times(ctx.handle, ms, n))
+    names = ("closest", "shade", "shadow", "raygen")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(names)}
 
 
 def mirres_render_noalloc(scenes, views, params: Params, images, tape, stream=None):

@@ -4,6 +4,9 @@ PyTorch supplies device memory and streams only; every step of the path runs in 
 """
 from __future__ import annotations
 
+import json
+import os
+
 import torch
 
 from . import mirres as M
@@ -66,16 +69,47 @@ class GpuWorkload:
         n = M.mirres_tape_bytes(self.views)
         return torch.empty(n // 4, device=self.device, dtype=torch.int32)
 
-    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0):
+    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0, flags=0):
         s = self.workload.seed if seed is None else seed
-        return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm)
+        return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm, flags=flags)
 
-    def render(self, launch=0, images=None, tape=None, seed=None, block=0, blocks_per_sm=0, stream=None):
+    def render(self, launch=0, images=None, tape=None, seed=None, block=0, blocks_per_sm=0, flags=0, stream=None):
         images = images if images is not None else self.new_images()
         tape = tape if tape is not None else self.new_tape()
         M.mirres_render(self.ctx, [s.handle for s in self.scenes], self.views,
-                        self.params(launch, seed, block, blocks_per_sm), images, tape, stream)
+                        self.params(launch, seed, block, blocks_per_sm, flags), images, tape, stream)
         return images, tape
+
+    def tune_key(self):
+        v = self.views
+        return "|".join([torch.cuda.get_device_name(self.device), self.workload.name, f"{len(v)} views",
+                         f"{len(self.scenes)} scenes", f"{self.samples} samples", f"M={self.workload.ris_m}"])
+
+    def autotune(self, tape=None, budget=32_000_000, cache=None):
+        """Pick the batched launch shape: from the JSON cache if this (GPU, workload shape) was
+        tuned before, else by timing every compiled variant (mirres_autotune) and caching it."""
+        path = cache or os.environ.get("MIRRES_TUNE_CACHE") or os.path.join(
+            os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json")
+        key = self.tune_key()
+        data = {}
+        if os.path.exists(path):
+            try:
+                data = json.load(open(path))
+            except (OSError, ValueError):
+                data = {}
+        if key in data:
+            e = data[key]
+            M.mirres_set_launch(self.ctx, e["block"], e["blocks_per_sm"], e["chunk"])
+            return dict(e, cached=True)
+        tape = tape if tape is not None else self.new_tape()
+        res = M.mirres_autotune(self.ctx, [s.handle for s in self.scenes], self.views, self.params(1), tape, budget)
+        data[key] = res
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1)
+        os.replace(tmp, path)
+        return dict(res, cached=False)
 
     def zero_grads(self):
         out = []

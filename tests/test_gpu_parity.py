@@ -213,17 +213,18 @@ def test_config1_forward_plain_and_batched_identical(M, ctx):
     w = synth.config1()
     gw = _gw(ctx, w)
     imgs0, tape0, st = _check_forward(gw, w, 0)
-    imgs1, tape1 = gw.render(launch=1)
-    torch.cuda.synchronize()
-    # the two launch paths take every discrete decision identically (hit triangle, selected
-    # candidate); their values differ only by FP32 contraction choices of the two kernels
+    # the launch paths take every discrete decision identically (hit triangle, selected
+    # candidate); their values differ only by FP32 contraction choices of the kernels
     N = w.samples
     a = tape0.cpu().numpy().view(np.uint32).reshape(9, N)
-    b = tape1.cpu().numpy().view(np.uint32).reshape(9, N)
-    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
-    fa, fb = a[2:].view(np.float32), b[2:].view(np.float32)
-    assert np.all(np.abs(fa - fb) <= 2e-6 * np.maximum(np.abs(fa), 1e-30))
-    torch.testing.assert_close(imgs0[0], imgs1[0], rtol=2e-6, atol=0)
+    for launch in (1, 2):
+        imgs1, tape1 = gw.render(launch=launch)
+        torch.cuda.synchronize()
+        b = tape1.cpu().numpy().view(np.uint32).reshape(9, N)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        fa, fb = a[2:].view(np.float32), b[2:].view(np.float32)
+        assert np.all(np.abs(fa - fb) <= 2e-6 * np.maximum(np.abs(fa), 1e-30))
+        torch.testing.assert_close(imgs0[0], imgs1[0], rtol=2e-6, atol=0)
     print("config1 forward:", {k: st[0][k] for k in ("n", "flagged", "max_err_unflagged", "median_err")})
 
 
