@@ -243,7 +243,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def step(launch, ev_render=None):
+    def step(launch, ev_render=None, ev_bwd=None):
         for s in gw.scenes:
             M.mirres_bvh_build(s.handle)
         if ev_render is not None:
@@ -255,7 +255,11 @@ def main():
             ev_render[1].record()
         for img, ref, d in zip(images, refs, d_images):
             M.mirres_l2_loss(img, ref, d, loss)
+        if ev_bwd is not None:
+            ev_bwd[0].record()
         M.mirres_backward(gw.ctx, scenes, gw.views, gw.params(launch), d_images, tape, grads)
+        if ev_bwd is not None:
+            ev_bwd[1].record()
 
     def zero():
         for g in grads:
@@ -273,17 +277,19 @@ def main():
         c0 = M.mirres_get_counters(gw.ctx)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for i in range(steps):
             flush.fill_(float(i))  # evict L2 between timed steps (outside the timed window)
             zero()
             evs[i][0].record()
-            step(launch, evr[i])
+            step(launch, evr[i], evg[i])
             evs[i][1].record()
         torch.cuda.synchronize()
         barrier()
         c1 = M.mirres_get_counters(gw.ctx)
         ms = sum(a.elapsed_time(b) for a, b in evs)
         ms_render = sum(a.elapsed_time(b) for a, b in evr)
+        timed.backward_ms = sum(a.elapsed_time(b) for a, b in evg) / steps
         rays = (c1[0] - c0[0]) + (c1[1] - c0[1]) + (c1[2] - c0[2])
         launches = c1[6] - c0[6]
         return ms, ms_render, rays, launches, [c1[k] - c0[k] for k in range(8)]
@@ -299,6 +305,7 @@ def main():
     clocks.start()
     ms_b, msr_b, rays_b, launches_b, cnt_b = timed(1, args.steps, args.warmup)
     clk = clocks.stop()
+    backward_ms = timed.backward_ms
     stages = M.mirres_stage_times(gw.ctx)  # stage times of the last timed batched render
     ms_b = max_over_ranks(ms_b)
 
@@ -357,7 +364,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}",
                            l2="flushed between timed steps (512 MiB write) and each step writes > 40 GB"),
-            "mrays_per_s": mrays, "render_ms_per_step": msr_b / args.steps,
+            "mrays_per_s": mrays, "render_ms_per_step": msr_b / args.steps, "backward_ms_per_step": backward_ms,
             "batched": {"value": value, "ms_per_step": ms_b / args.steps, "mrays_per_s": mrays,
                         "launch": "batched wavefront, one CUDA graph per forward",
                         "stage_ms_per_render": {k: v[0] for k, v in stages.items()},

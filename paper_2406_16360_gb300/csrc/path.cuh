@@ -56,30 +56,57 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
     out.cand = -1;
     out.W = 0.0f;
     if (env_ok && M > 0) {
+        // per-vertex parts of the BRDF: the candidates need only the luminance of f_r cos
+        // (p_hat = Y(L_env) Y(f_r) cos); the selected one's RGB is rebuilt after the loop
+        const float co = dot(sh.n, wo);
+        const float a = alpha_of(sh.m.rough), a2 = a * a;
+        const float Ao = smith_a(a2, co);
+        const float3 kd = mul(sh.m.alb, 1.0f - sh.m.metal);
+        const float3 f0 = f3(0.04f * (1.0f - sh.m.metal) + sh.m.metal * sh.m.alb.x,
+                             0.04f * (1.0f - sh.m.metal) + sh.m.metal * sh.m.alb.y,
+                             0.04f * (1.0f - sh.m.metal) + sh.m.metal * sh.m.alb.z);
+        const float ykd = lum(kd) * MR_INV_PI, yf0 = lum(f0);
         float wsum = 0.0f, phat_sel = 0.0f;
+        float dv_sel = 0.0f, w5_sel = 0.0f, ci_sel = 0.0f;
         int sel = -1, ytex = 0;
-        float3 ysel = f3(0.f, 0.f, 0.f), fsel = f3(0.f, 0.f, 0.f);
+        float3 ysel = f3(0.f, 0.f, 0.f);
+#pragma unroll 2
         for (int j = 0; j < M; ++j) {
             const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j);
             float3 dir;
             int tex;
             const float q = env_sample(s, x.x, x.y, x.w, dir, tex);
-            const float3 fc = brdf_cos(sh.n, wo, dir, sh.m);
-            const float4 L = __ldg(s.env_texel + tex);
-            const float phat = lum(xyz(L)) * lum(fc);  // p_hat = Y(L_env) Y(f_r) cos
-            const float gamma = phat / q;              // gamma = p_hat / q_dir
+            const float ci = dot(sh.n, dir);
+            float phat = 0.0f, dv = 0.0f, w5 = 0.0f;
+            if (co > 0.0f && ci > 0.0f) {
+                const float3 h = normalize(add(wo, dir));
+                const float cnh = dot(sh.n, h), coh = dot(wo, h);
+                const float k = ggx_k(sh.n, h, cnh, a2);
+                const float D = a2 / (MR_PI * k * k);
+                dv = D * (0.5f / (ci * Ao + co * smith_a(a2, ci)));
+                const float om = 1.0f - coh;
+                w5 = (om * om) * (om * om) * om;
+                const float yfc = (ykd + dv * (yf0 * (1.0f - w5) + w5)) * ci;
+                phat = lum(xyz(__ldg(s.env_texel + tex))) * yfc;  // p_hat = Y(L_env) Y(f_r) cos
+            }
+            const float gamma = phat / q;  // gamma = p_hat / q_dir
             wsum += gamma;
             if (u24(x.z) * wsum < gamma) {
                 sel = j;
                 ytex = tex;
                 ysel = dir;
-                fsel = fc;
                 phat_sel = phat;
+                dv_sel = dv;
+                w5_sel = w5;
+                ci_sel = ci;
             }
         }
         if (sel >= 0 && wsum > 0.0f) {
             const float W = wsum / ((float)M * phat_sel);
             const float4 L = __ldg(s.env_texel + ytex);
+            const float3 fsel = f3((kd.x * MR_INV_PI + dv_sel * (f0.x * (1.0f - w5_sel) + w5_sel)) * ci_sel,
+                                   (kd.y * MR_INV_PI + dv_sel * (f0.y * (1.0f - w5_sel) + w5_sel)) * ci_sel,
+                                   (kd.z * MR_INV_PI + dv_sel * (f0.z * (1.0f - w5_sel) + w5_sel)) * ci_sel);
             const float3 contrib = mul(hmul(xyz(L), fsel), W);
             out.add_rad = hmul_rn(beta, contrib);
             out.add_lind = (b >= 1) ? hmul_rn(bind, contrib) : f3(0.f, 0.f, 0.f);

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_closest(SceneDev s, ViewDev v, int b, Q
 }
 
 // shade every compacted hit: RIS + shadow ray + continuation (next-bounce queue)
-__global__ void __launch_bounds__(256) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev hq,
+__global__ void __launch_bounds__(256, 4) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev hq,
                                                const unsigned int* count_hit, QueueDev qout,
                                                unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
                                                void* tape, uint64_t ntot, unsigned long long* counters)
@@ -515,7 +515,7 @@ struct EmitVert {
     }
 };
 
-__global__ void __launch_bounds__(256) k_backward(const SceneDev* __restrict__ scenes,
+__global__ void __launch_bounds__(256, 4) k_backward(const SceneDev* __restrict__ scenes,
                                                   const ViewDev* __restrict__ views, int n_views, uint64_t total,
                                                   Rng rng, const float* const* __restrict__ d_images,
                                                   const GradDev* __restrict__ grads, const void* tape,
