@@ -179,6 +179,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def reduce_max(x, device):
+    """max of a per-rank number over all ranks (the slowest replica sets the time)"""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([float(x)], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
 # ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
@@ -295,11 +306,7 @@ def main():
         return ms, ms_render, rays, launches, [c1[k] - c0[k] for k in range(8)]
 
     def max_over_ranks(x):
-        if world > 1:
-            t = torch.tensor([x], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        return reduce_max(x, dev)
 
     clocks = ClockSampler(local)
     clocks.start()

@@ -1,0 +1,332 @@
+"""GPU parity on edge cases, multi-scene batches, the full-size config-3 workload (sampled
+pixels, in the launch mode the benchmark times), finite differences, and the config-4
+optimisation loop -- all through the C ABI, all against the FP64 oracle."""
+import copy
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2406_16360_gb300 import synth
+from tests.parity import compare_grads, compare_pixels
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_16360_gb300 import mirres
+    return mirres
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.mirres_context_create(0)
+    yield c
+    c.close()
+
+
+def _gw(ctx, w):
+    from paper_2406_16360_gb300.renderer import GpuWorkload
+    return GpuWorkload(w, 0, ctx=ctx)
+
+
+def _forward_parity(gw, w, launch, pixels=None, max_flag_frac=0.08):
+    images, tape = gw.render(launch=launch)
+    torch.cuda.synchronize()
+    for vi, v in enumerate(w.views):
+        osc = O.OracleScene(w.scenes[v.scene])
+        r = O.render(osc, v, vi, w.ris_m, seed=w.seed, pixels=pixels)
+        got = images[vi].cpu().numpy().reshape(-1, 3)
+        if pixels is not None:
+            got = got[pixels]
+        st = compare_pixels(got, r["rgb"], r["margin"])
+        assert st["failures"] == 0, (vi, st["failures"], st["max_err_unflagged"])
+        assert st["flagged"] <= max_flag_frac * st["n"] + 1, (vi, st["flagged"], st["n"])
+    return images, tape
+
+
+def _grad_parity(gw, w, tape, pixels_per_view=None, seed=7):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d_imgs, plist = [], []
+    for vi, v in enumerate(w.views):
+        osc = O.OracleScene(w.scenes[v.scene])
+        npx = v.width * v.height
+        pix = None if pixels_per_view is None else np.sort(rng.choice(npx, size=min(npx, pixels_per_view),
+                                                                      replace=False)).astype(np.int32)
+        r = O.render(osc, v, vi, w.ris_m, seed=w.seed, pixels=pix)
+        g = rng.normal(size=(npx if pix is None else len(pix), 3))
+        g[r["margin"] < 1.0] = 0.0
+        full = np.zeros((npx, 3))
+        if pix is None:
+            full[:] = g
+        else:
+            full[pix] = g
+        d_imgs.append(torch.as_tensor(full.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda"))
+        plist.append((pix, full if pix is None else full[pix]))
+    grads = gw.backward(d_imgs, tape)
+    torch.cuda.synchronize()
+    for si, sc in enumerate(w.scenes):
+        osc = O.OracleScene(sc)
+        acc = None
+        for vi, v in enumerate(w.views):
+            if v.scene != si:
+                continue
+            pix, g = plist[vi]
+            gi = O.backward(osc, v, vi, w.ris_m, d_imgs[vi].double().cpu().numpy().reshape(-1, 3)[pix]
+                            if pix is not None else d_imgs[vi].double().cpu().numpy().reshape(-1, 3),
+                            seed=w.seed, pixels=pix)
+            if acc is None:
+                acc = gi
+            else:
+                for k in gi:
+                    if k != "counts":
+                        acc[k] = acc[k] + gi[k]
+        if acc is None:
+            continue
+        for k in ("albedo", "roughness", "metallic", "env", "verts"):
+            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"))
+            assert st["failures"] == 0, (si, k, st["failures"], st["detail"])
+
+
+# ---------------------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------------------
+def _edge_workloads():
+    out = {}
+    # no triangles at all: every ray escapes, the image is the environment
+    sc = synth.tiny_scene()
+    empty = synth._scene(np.zeros((1, 3)), np.zeros((0, 3), np.int32), np.zeros((0, 3, 2)), sc.albedo,
+                         sc.roughness, sc.metallic, sc.env)
+    K, c2w = synth.look_at((0.0, 1.5, 4.0), (0.0, 1.0, 0.0), 13, 7)
+    out["empty_scene"] = synth.Workload("empty", [empty], [synth.View(K, c2w, 13, 7, 3, 2)], ris_m=4)
+    # a single triangle (LBVH without internal nodes)
+    one = synth._scene(np.array([[-1, 0, -1], [1, 0, -1], [0, 2, -1.2]]), np.array([[0, 1, 2]]),
+                       np.array([[[0, 0], [1, 0], [0.5, 1]]]), np.full((2, 2, 3), 0.6), np.full((2, 2), 0.4),
+                       np.full((2, 2), 0.2), sc.env)
+    K, c2w = synth.look_at((0.0, 0.8, 2.5), (0.0, 0.8, -1.0), 17, 11)
+    out["single_triangle"] = synth.Workload("one", [one], [synth.View(K, c2w, 17, 11, 5, 3)], ris_m=3)
+    # black environment: no RIS candidate has weight, the image is black
+    black = copy.deepcopy(sc)
+    black.env[:] = 0.0
+    K, c2w = synth.look_at((0.0, 1.5, 4.0), (0.0, 1.0, 0.0), 9, 9)
+    out["black_env"] = synth.Workload("black", [black], [synth.View(K, c2w, 9, 9, 2, 3)], ris_m=8)
+    # one bounce, one candidate, one sample, a 1x1 image and a ragged 31x3 image
+    K, c2w = synth.look_at((0.0, 1.5, 4.0), (0.0, 1.0, 0.0), 1, 1)
+    K2, c2w2 = synth.look_at((0.3, 1.2, 3.5), (0.0, 0.9, 0.0), 31, 3)
+    out["tiny_views"] = synth.Workload("tiny", [sc], [synth.View(K, c2w, 1, 1, 1, 1),
+                                                      synth.View(K2, c2w2, 31, 3, 7, 2)], ris_m=1, seed=5)
+    return out
+
+
+@pytest.mark.parametrize("name", list(_edge_workloads().keys()))
+@pytest.mark.parametrize("launch", [0, 1, 2])
+def test_edge_cases_forward(M, ctx, name, launch):
+    w = _edge_workloads()[name]
+    gw = _gw(ctx, w)
+    images, tape = _forward_parity(gw, w, launch, max_flag_frac=0.2)
+    if name == "black_env":
+        assert float(images[0].abs().max()) == 0.0
+    if name == "empty_scene":
+        t = tape.cpu().numpy().view(np.int32).reshape(9, -1)
+        assert np.all(t[0] == -1)
+    for s in gw.scenes:
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["single_triangle", "tiny_views"])
+def test_edge_cases_backward(M, ctx, name):
+    w = _edge_workloads()[name]
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1)
+    _grad_parity(gw, w, tape)
+    for s in gw.scenes:
+        s.close()
+
+
+def test_multi_scene_batch_mixed_bounces(M, ctx):
+    """several scenes of different sizes and views of different resolution / spp / bounces in
+    one call: the batched and persistent launches against the oracle and the plain launch"""
+    w = synth.config5(seed=3, n_scenes=4, max_tris=6000, res_choices=(16, 24, 40), spp_choices=(2, 3, 5), tex=16)
+    for s in w.scenes:
+        s.env[:] = np.minimum(s.env, 50.0)  # keep the per-pixel check well conditioned
+    gw = _gw(ctx, w)
+    img0, tape0 = gw.render(launch=0)
+    for launch in (1, 2):
+        img, tape = _forward_parity(gw, w, launch, max_flag_frac=0.15)
+        n = w.samples
+        a = tape0.cpu().numpy().view(np.uint32).reshape(9, n)
+        b = tape.cpu().numpy().view(np.uint32).reshape(9, n)
+        assert np.array_equal(a[:2], b[:2])
+    _grad_parity(gw, w, tape0)
+    for s in gw.scenes:
+        s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# full-size config 3, sampled pixels, the benchmark's launch (batched)
+# ---------------------------------------------------------------------------------------
+def test_config3_full_size_sampled(M, ctx):
+    w = synth.config3(n_views=100)
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1)
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(11))
+    views = [0, 37, 99]
+    for vi in views:
+        v = w.views[vi]
+        pix = np.sort(rng.choice(v.width * v.height, size=96, replace=False)).astype(np.int32)
+        osc = O.OracleScene(w.scenes[0]) if vi == views[0] else osc
+        r = O.render(osc, v, vi, w.ris_m, seed=w.seed, pixels=pix)
+        st = compare_pixels(images[vi].cpu().numpy().reshape(-1, 3)[pix], r["rgb"], r["margin"])
+        assert st["failures"] == 0, (vi, st["max_err_unflagged"])
+        assert st["flagged"] <= 0.5 * len(pix)
+    # adjoint of a few pixels of view 37 at full size
+    v = w.views[37]
+    pix = np.sort(rng.choice(v.width * v.height, size=48, replace=False)).astype(np.int32)
+    r = O.render(osc, v, 37, w.ris_m, seed=w.seed, pixels=pix)
+    g = rng.normal(size=(len(pix), 3))
+    g[r["margin"] < 1.0] = 0.0
+    d = [torch.zeros((vv.height, vv.width, 3), device="cuda") for vv in w.views]
+    d[37].view(-1, 3)[torch.as_tensor(pix.astype(np.int64), device="cuda")] = torch.as_tensor(
+        g, dtype=torch.float32, device="cuda")
+    grads = gw.backward(d, tape)
+    torch.cuda.synchronize()
+    og = O.backward(osc, v, 37, w.ris_m, d[37].double().cpu().numpy().reshape(-1, 3)[pix], seed=w.seed, pixels=pix)
+    for k in ("albedo", "roughness", "metallic", "env", "verts"):
+        st = compare_grads(grads[0][k].cpu().numpy(), og[k], og[k + "_abs"], og.get(k + "_sens"))
+        assert st["failures"] == 0, (k, st["detail"])
+    for s in gw.scenes:
+        s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# gradients against central finite differences (config 2 scene, 64 random texels)
+# ---------------------------------------------------------------------------------------
+def test_config2_gradients_vs_finite_differences(M, ctx):
+    w = synth.config2(res=48, n_views=1, tex=512, spp=8)
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1)
+    v = w.views[0]
+    osc = O.OracleScene(w.scenes[0])
+    r = O.render(osc, v, 0, w.ris_m, seed=w.seed)
+    rng = np.random.Generator(np.random.PCG64(17))
+    g = rng.normal(size=(v.width * v.height, 3))
+    g[r["margin"] < 1.0] = 0.0
+    d = [torch.as_tensor(g.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda")]
+    grads = gw.backward(d, tape)
+    torch.cuda.synchronize()
+    ga = grads[0]["albedo"].cpu().numpy().reshape(-1)
+    oa = O.backward(osc, v, 0, w.ris_m, d[0].double().cpu().numpy().reshape(-1, 3), seed=w.seed)
+    touched = np.flatnonzero(np.abs(oa["albedo"].reshape(-1)) > 1e-3 * np.abs(oa["albedo"]).max())
+    pick = rng.choice(touched, size=min(64, len(touched)), replace=False)
+    sc0 = w.scenes[0]
+    gf = d[0].double().cpu().numpy().reshape(-1, 3)
+    checked = 0
+    for idx in pick:
+        h = 2e-3
+        vals = []
+        for sgn in (+1, -1):
+            sc1 = copy.deepcopy(sc0)
+            flat = sc1.albedo.reshape(-1)
+            flat[idx] = np.float32(flat[idx] + sgn * h)
+            dh = float(flat[idx]) - float(sc0.albedo.reshape(-1)[idx])
+            rgb = O.render_detached(osc, O.OracleScene(sc1), v, 0, w.ris_m, seed=w.seed)
+            vals.append(((gf * rgb).sum(), dh))
+        fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+        sens = oa["albedo_sens"].reshape(-1)[idx]
+        assert abs(ga[idx] - fd) <= 1e-3 * abs(fd) + 2.0 * sens + 1e-6 * np.abs(oa["albedo"]).max(), (
+            idx, ga[idx], fd, sens)
+        checked += 1
+    assert checked == len(pick)
+    for s in gw.scenes:
+        s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# config 4: optimisation loop through the autograd Function vs the same loop driven by
+# the oracle's gradients
+# ---------------------------------------------------------------------------------------
+def test_config4_loop_tracks_oracle_gradients(M, ctx):
+    from paper_2406_16360_gb300.renderer import GpuWorkload, MirresRender
+    res, steps = 24, 16
+    target_w = synth.config2(res=res, n_views=2, tex=16, spp=4, bounces=2)
+    gt = target_w.scenes[0]
+    tgw = GpuWorkload(target_w, 0, ctx=ctx)
+    targets, _ = tgw.render(launch=1, seed=99)
+    targets = torch.stack([t.clone() for t in targets])
+    init = copy.deepcopy(gt)
+    init.albedo[:] = 0.5
+    init.roughness[:] = 0.5
+    init.env[:] = 1.0
+    losses = {}
+    for mode in ("gpu", "oracle"):
+        w = synth.Workload(target_w.name, [copy.deepcopy(init)], target_w.views, target_w.ris_m, seed=1)
+        gw = GpuWorkload(w, 0, ctx=ctx)
+        ds = gw.scenes[0]
+        params = [ds.albedo, ds.env]
+        for p in params:
+            p.requires_grad_(True)
+        opt = torch.optim.Adam(params, lr=5e-2)
+        curve = []
+        for it in range(steps):
+            opt.zero_grad()
+            if mode == "gpu":
+                img = MirresRender.apply(gw, 1, 1 + it, ds.albedo, ds.roughness, ds.metallic, ds.env, ds.verts)
+                loss = ((img - targets) ** 2).sum()
+                loss.backward()
+            else:
+                with torch.no_grad():
+                    sc = synth.Workload(w.name, [synth._scene(gt.verts, gt.tris, gt.tri_uv, ds.albedo.cpu().numpy(),
+                                                              ds.roughness.cpu().numpy(), ds.metallic.cpu().numpy(),
+                                                              ds.env.cpu().numpy())], w.views, w.ris_m, seed=1 + it)
+                    osc = O.OracleScene(sc.scenes[0])
+                    tot = 0.0
+                    ga = np.zeros(ds.albedo.shape)
+                    ge = np.zeros(ds.env.shape)
+                    for vi, v in enumerate(w.views):
+                        rr = O.render(osc, v, vi, w.ris_m, seed=1 + it, margins=False)["rgb"]
+                        diff = rr - targets[vi].double().cpu().numpy().reshape(-1, 3)
+                        tot += float((diff ** 2).sum())
+                        gg = O.backward(osc, v, vi, w.ris_m, 2 * diff, seed=1 + it, want_abs=False)
+                        ga += gg["albedo"]
+                        ge += gg["env"]
+                    loss = torch.tensor(tot)
+                    ds.albedo.grad = torch.as_tensor(ga, dtype=torch.float32, device="cuda")
+                    ds.env.grad = torch.as_tensor(ge, dtype=torch.float32, device="cuda")
+            curve.append(float(loss))
+            opt.step()
+        losses[mode] = curve
+        for p in params:
+            p.requires_grad_(False)
+        gw.scenes[0].close()
+    a, b = np.array(losses["gpu"]), np.array(losses["oracle"])
+    assert a[-1] < 0.95 * a[0], a
+    # same seeds, same gradients up to FP32: the two loops follow the same curve
+    np.testing.assert_allclose(a, b, rtol=1e-2)
+    for s in tgw.scenes:
+        s.close()
+
+
+def test_autotune_and_set_launch(M, ctx):
+    w = synth.config2(res=32, n_views=2, tex=16, spp=4)
+    gw = _gw(ctx, w)
+    tape = gw.new_tape()
+    res = M.mirres_autotune(ctx, [s.handle for s in gw.scenes], gw.views, gw.params(2), tape, 0)
+    assert res["block"] in (64, 128, 256) and res["blocks_per_sm"] >= 1 and res["chunk"] in (64, 256, 1024)
+    assert res["ms"] > 0
+    ref, reft = gw.render(launch=0)
+    for blk, per in ((128, 3), (256, 2), (64, 8)):
+        M.mirres_set_launch(ctx, blk, per, 64)
+        img, t = gw.render(launch=2)
+        torch.cuda.synchronize()
+        n = w.samples
+        assert np.array_equal(t.cpu().numpy().view(np.uint32).reshape(9, n)[:2],
+                              reft.cpu().numpy().view(np.uint32).reshape(9, n)[:2])
+    M.mirres_set_launch(ctx, 0, 0, 0)
+    for s in gw.scenes:
+        s.close()
