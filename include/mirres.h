@@ -148,10 +148,17 @@ mirres_status mirres_bvh_refit(mirres_scene* scene, void* stream);
 
 /* ---- forward / adjoint ----------------------------------------------------------------- */
 
-/* Bytes of tape needed for these views: 36 bytes per path sample (sum of width*height*spp).
- * The tape records, per sample, the primary triangle, the selected RIS candidate, V*W of the
- * primary vertex, the incident indirect radiance L_ind at the primary vertex and the
- * sample's radiance; the adjoint replays the primary vertex from it and the random stream. */
+/* Tape bytes per path sample: 17 32-bit words, stored as 17 arrays over the samples. */
+#define MIRRES_TAPE_BYTES_PER_SAMPLE 68
+
+/* Bytes of tape needed for these views: MIRRES_TAPE_BYTES_PER_SAMPLE per path sample (sum of
+ * width*height*spp). The tape records, per sample (word: content): 0 primary triangle (-1 if
+ * the primary ray escaped), 1 index of the selected RIS candidate at the primary vertex (-1 if
+ * none), 2 V*W of that candidate, 3-5 the incident indirect radiance L_ind at the primary
+ * vertex, 6-8 the sample's radiance, 9 the env texel of the selected candidate, 10-12 its
+ * direction, 13-15 the continuation direction at the primary vertex, 16 its mixture pdf
+ * p_ind. Words 9-16 are meaningful only where word 1 >= 0, resp. L_ind != 0. The adjoint
+ * replays the primary vertex from it and the camera's random numbers; no sample is re-drawn. */
 size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views);
 
 /* Forward render (Eq. pbr_render with Eq. incident: direct light by RIS over ris_m env
@@ -219,7 +226,7 @@ mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int32_t n_scene
 
 /* Adjoint, PRIMARY mode (Sec. 4.2: gradients of indirect rays detached; Appendix C: no
  * gradients of non-primary rays): for every sample, the primary vertex is replayed from the
- * tape and the random stream, and the derivatives of direct_1 + beta_1 * L_ind (RIS weight,
+ * tape and the camera's random numbers, and the derivatives of direct_1 + beta_1 * L_ind (RIS weight,
  * visibility, every sampling decision, p_ind and L_ind held fixed) are scattered into the
  * texels of albedo / roughness / metallic (bilinear weights), the env texel of the selected
  * candidate and of escaping primary rays, and the three vertices of the primary triangle

@@ -31,8 +31,18 @@ def _inputs():
     return files
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def extra_flags() -> list:
+    """MIRRES_NVCC_FLAGS: extra nvcc flags, e.g. the launch knobs -DMR_SHADE_MINB=3."""
+    return os.environ.get("MIRRES_NVCC_FLAGS", "").split()
+
+
 def stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    if not os.path.exists(STAMP) or open(STAMP).read() != " ".join(extra_flags()):
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in _inputs())
@@ -43,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
-                    "-I", CSRC, "-I", INCLUDE]
+                    "-I", CSRC, "-I", INCLUDE] + extra_flags()
     procs, objs = [], []
     for u in UNITS:
         obj = os.path.join(BUILD, u.replace(".cu", ".o"))
@@ -66,6 +76,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".tmp%d" % os.getpid()
     subprocess.run([nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs, check=True)
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(extra_flags()))
     if verbose:
         for u in UNITS:
             sys.stdout.write(open(os.path.join(BUILD, u.replace(".cu", ".log"))).read())

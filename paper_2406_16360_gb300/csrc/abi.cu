@@ -52,6 +52,9 @@ SceneDev mr_scene_dev(const mirres_scene* s)
     d.env_cond = s->env_cond;
     d.env_gmarg = s->env_gmarg;
     d.env_gcond = s->env_gcond;
+    d.env_row = s->env_row;
+    d.env_col = s->env_col;
+    d.env_fine = (s->desc.env_w >= 64 && s->desc.env_h >= 32) ? 1 : 0;
     d.gm_shift = s->gm_shift;
     d.gc_shift = s->gc_shift;
     d.gc = s->gc;
@@ -287,7 +290,7 @@ extern "C" size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views)
     for (int i = 0; i < n_views; ++i)
         n += (uint64_t)std::max(views[i].width, 0) * (uint64_t)std::max(views[i].height, 0) *
              (uint64_t)std::max(views[i].spp, 0);
-    return (size_t)(36ull * n);
+    return (size_t)((uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * n);
 }
 
 // ---- forward ---------------------------------------------------------------------------------
@@ -345,7 +348,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     }
     const uint64_t wave = std::min<uint64_t>(total, kWave);
     Carver plan(nullptr);
-    plan.take<char>(tape ? 0 : 36ull * total);
+    plan.take<char>(tape ? 0 : (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total);
     plan.take<ViewDev>((size_t)n_views);
     plan.take<SceneDev>((size_t)n_scenes);
     plan.take<float*>((size_t)n_views);
@@ -354,7 +357,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     plan.take<float4>(16ull * wave);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
-    void* internal_tape = cv.take<char>(tape ? 0 : 36ull * total);
+    void* internal_tape = cv.take<char>(tape ? 0 : (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total);
     void* tp = tape ? tape : internal_tape;
     ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
     SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
@@ -434,7 +437,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     if (!images) return arg_error("images is NULL");
     for (int i = 0; i < n_views; ++i)
         if (!images[i]) return arg_error("images[" + std::to_string(i) + "] is NULL");
-    if (tape && tape_bytes < 36ull * total) return arg_error("tape_bytes is smaller than mirres_tape_bytes(views)");
+    if (tape && tape_bytes < (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total) return arg_error("tape_bytes is smaller than mirres_tape_bytes(views)");
     if (tape && (reinterpret_cast<uintptr_t>(tape) & 15)) return arg_error("tape must be 16-byte aligned");
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
@@ -449,7 +452,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     const bool batched = params->launch == 2;
     const uint32_t chunk = (uint32_t)std::min<uint64_t>(max_view, kChunk);
     Carver plan(nullptr);
-    plan.take<char>(tape ? 0 : 36ull * total);
+    plan.take<char>(tape ? 0 : (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total);
     plan.take<ViewDev>((size_t)n_views);
     plan.take<SceneDev>((size_t)n_scenes);
     plan.take<float*>((size_t)n_views);
@@ -458,7 +461,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     if (!batched) plan.take<float4>(16ull * chunk);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
-    void* internal_tape = cv.take<char>(tape ? 0 : 36ull * total);
+    void* internal_tape = cv.take<char>(tape ? 0 : (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total);
     void* tp = tape ? tape : internal_tape;
     ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
     SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
@@ -541,7 +544,7 @@ extern "C" mirres_status mirres_autotune(mirres_context* ctx, mirres_scene* cons
     std::vector<ViewDev> vdev;
     uint64_t total = 0, max_view = 0;
     MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
-    if (!tape || tape_bytes < 36ull * total) return arg_error("mirres_autotune needs the full tape of these views");
+    if (!tape || tape_bytes < (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total) return arg_error("mirres_autotune needs the full tape of these views");
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
     const uint64_t n = std::max<uint64_t>(1, std::min<uint64_t>(budget_samples ? budget_samples : total, total));
@@ -659,7 +662,7 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
     for (int i = 0; i < n_views; ++i)
         if (!d_images[i]) return arg_error("d_images[" + std::to_string(i) + "] is NULL");
     if (!tape) return arg_error("mirres_backward needs the tape written by mirres_render");
-    if (tape_bytes < 36ull * total) return arg_error("tape_bytes is smaller than mirres_tape_bytes(views)");
+    if (tape_bytes < (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total) return arg_error("tape_bytes is smaller than mirres_tape_bytes(views)");
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
     ctx->last_stream = st;

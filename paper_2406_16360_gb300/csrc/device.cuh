@@ -11,6 +11,18 @@
 #define MR_INV_PI 0.31830988618379067154f
 #define MR_FULL 0xffffffffu
 
+// launch tuning knobs (overridable with -D at build time): minimum resident blocks of 256
+// threads per SM for the shading and adjoint kernels, and the RIS candidate loop's unroll
+#ifndef MR_SHADE_MINB
+#define MR_SHADE_MINB 4
+#endif
+#ifndef MR_BWD_MINB
+#define MR_BWD_MINB 4
+#endif
+#ifndef MR_CAND_UNROLL
+#define MR_CAND_UNROLL 1
+#endif
+
 // traversal stack: the first MR_SSTACK entries live in shared memory (column per thread),
 // deeper entries in a small local array; an LBVH over 64-bit unique keys is at most 63 deep
 #define MR_SSTACK 32
@@ -33,6 +45,9 @@ struct SceneDev {
     const uint32_t* env_cond; // [eh][ew + 1]
     const uint32_t* env_gmarg; // [gm + 1] guide: answer of the marginal search at bucket starts
     const uint32_t* env_gcond; // [eh][gc + 1] guide of every row's conditional search
+    const float4* env_row;    // [eh]: (cos th_r, sin th_r, 2 pi^2 total / (ew eh sin th_r), 0) at row centres
+    const float2* env_col;    // [ew]: (cos psi_c, sin psi_c), psi = 2 pi u - pi at column centres
+    int32_t env_fine;         // 1 when a texel spans at most pi/32 in both angles (tables used)
     int32_t gm_shift, gc_shift, gc;
     int32_t n_tris, n_verts, tw, th, ew, eh;
     const int32_t* env_ok_dev; // device-written: total env weight > 0
@@ -151,27 +166,81 @@ __device__ __forceinline__ int search_range(const uint32_t* __restrict__ a, int 
     return lo;
 }
 
-// sample a direction with probability proportional to Y(L) sin(theta_row); returns pdf.
-// The inverse-CDF searches start from guide tables (cut-point method): the answer at the
-// start of the uniform's bucket and at the next bucket bound the answer, so the search is
-// the same function of the uniform as a full binary search, over a range of ~1-2 entries.
-__device__ __forceinline__ float env_sample(const SceneDev& s, uint32_t xrow, uint32_t xcol, uint32_t sub,
-                                            float3& dir, int& texel)
+// sin and cos of a small angle by their Taylor series; for |x| <= pi/64 the truncation error
+// is below 2e-13, far under FP32 rounding
+__device__ __forceinline__ void sincos_small(float x, float& sn, float& cs)
+{
+    const float x2 = x * x;
+    sn = x * (1.0f - x2 * (1.0f / 6.0f) * (1.0f - x2 * (1.0f / 20.0f)));
+    cs = 1.0f - x2 * 0.5f * (1.0f - x2 * (1.0f / 12.0f) * (1.0f - x2 * (1.0f / 30.0f)));
+}
+
+// direction of the sub-texel position (c + s_hi, r + s_lo) of texel (r, c) of the y-up
+// lat-long map: theta = pi v, psi = 2 pi u - pi, dir = (sin theta sin psi, cos theta,
+// -sin theta cos psi). On fine maps each angle is its texel centre (tabulated) plus an offset
+// of at most half a texel, combined by the angle-sum formulas; coarse maps use sincospi.
+// Returns sin theta; rowv = the row's table entry.
+__device__ __forceinline__ float env_dir(const SceneDev& s, int r, int c, uint32_t sub, float3& dir, float4& rowv)
+{
+    rowv = __ldg(s.env_row + r);
+    float st, ct, sp, cp;
+    if (s.env_fine) {
+        const float2 cv = __ldg(s.env_col + c);
+        float sdt, cdt, sdp, cdp;
+        sincos_small((sub_lo(sub) - 0.5f) * (MR_PI / (float)s.eh), sdt, cdt);
+        sincos_small((sub_hi(sub) - 0.5f) * ((2.0f * MR_PI) / (float)s.ew), sdp, cdp);
+        st = rowv.y * cdt + rowv.x * sdt;
+        ct = rowv.x * cdt - rowv.y * sdt;
+        sp = cv.y * cdp + cv.x * sdp;
+        cp = cv.x * cdp - cv.y * sdp;
+    } else {
+        const float uu = ((float)c + sub_hi(sub)) / (float)s.ew;
+        const float vv = ((float)r + sub_lo(sub)) / (float)s.eh;
+        sincospif(2.0f * uu - 1.0f, &sp, &cp);
+        sincospif(vv, &st, &ct);
+    }
+    dir = f3(st * sp, ct, -st * cp);
+    return st;
+}
+
+// inverse-CDF texel draw: row from the marginal, column from the row's conditional. The
+// searches start from guide tables (cut-point method): the answer at the start of the
+// uniform's bucket and at the next bucket bound the answer, so the search is the same
+// function of the uniform as a full binary search, over a range of ~1-2 entries.
+__device__ __forceinline__ void env_texel_draw(const SceneDev& s, uint32_t xrow, uint32_t xcol, int& r, int& c)
 {
     const uint32_t kr = xrow >> 8, kc = xcol >> 8;
     const uint32_t bm = kr >> s.gm_shift;
-    const int r = search_range(s.env_marg, (int)__ldg(s.env_gmarg + bm), (int)__ldg(s.env_gmarg + bm + 1), kr);
+    r = search_range(s.env_marg, (int)__ldg(s.env_gmarg + bm), (int)__ldg(s.env_gmarg + bm + 1), kr);
     const uint32_t* grow = s.env_gcond + (size_t)r * (s.gc + 1);
     const uint32_t bc = kc >> s.gc_shift;
-    const int c = search_range(s.env_cond + (size_t)r * (s.ew + 1), (int)__ldg(grow + bc), (int)__ldg(grow + bc + 1), kc);
-    const float uu = ((float)c + sub_hi(sub)) / (float)s.ew;
-    const float vv = ((float)r + sub_lo(sub)) / (float)s.eh;
-    float sp, cp, st, ct;
-    sincospif(2.0f * uu - 1.0f, &sp, &cp);
-    sincospif(vv, &st, &ct);
-    dir = f3(st * sp, ct, -st * cp);
+    c = search_range(s.env_cond + (size_t)r * (s.ew + 1), (int)__ldg(grow + bc), (int)__ldg(grow + bc + 1), kc);
+}
+
+// sample a direction with probability proportional to Y(L) sin(theta_row); returns pdf.
+__device__ __forceinline__ float env_sample(const SceneDev& s, uint32_t xrow, uint32_t xcol, uint32_t sub,
+                                            float3& dir, int& texel)
+{
+    int r, c;
+    env_texel_draw(s, xrow, xcol, r, c);
+    float4 rowv;
+    const float st = env_dir(s, r, c, sub, dir, rowv);
     texel = r * s.ew + c;
     return __ldg(&s.env_texel[texel].w) / (2.0f * MR_PI * MR_PI * st);
+}
+
+// a RIS candidate: direction and texel as env_sample, and instead of its pdf the factor
+// Y(L_env) sin(theta) / q = (sin theta) 2 pi^2 total / (W H sin theta_row), so that the
+// resampling weight p_hat / q = Y(f_r cos) times this factor (no texel fetch, no division)
+__device__ __forceinline__ float env_candidate(const SceneDev& s, uint32_t xrow, uint32_t xcol, uint32_t sub,
+                                               float3& dir, int& texel)
+{
+    int r, c;
+    env_texel_draw(s, xrow, xcol, r, c);
+    float4 rowv;
+    const float st = env_dir(s, r, c, sub, dir, rowv);
+    texel = r * s.ew + c;
+    return st * rowv.z;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -70,6 +70,28 @@ __global__ void k_env_texels(const float* __restrict__ env, const double* __rest
     texel[i] = make_float4(env[3 * i], env[3 * i + 1], env[3 * i + 2], p);
 }
 
+// angle tables for drawing directions inside a texel without a full-range sin/cos: the row
+// centre theta_r = pi (r + 1/2) / H and the column centre psi_c = 2 pi (c + 1/2) / W - pi, plus
+// the per-row RIS weight factor. With q = P W H / (2 pi^2 sin theta) and P = Y(L) sin theta_r /
+// total, the candidate weight p_hat / q = Y(f_r cos) sin theta 2 pi^2 total / (W H sin theta_r):
+// Y(L) cancels, so a candidate needs no texel fetch.
+__global__ void k_env_angles(int W, int H, const double* __restrict__ total, float4* __restrict__ row,
+                             float2* __restrict__ col)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double pi = 3.14159265358979323846;
+    if (i < H) {
+        const double th = pi * ((double)i + 0.5) / (double)H;
+        const double st = sin(th), tot = *total;
+        const double g = tot > 0.0 ? 2.0 * pi * pi * tot / ((double)W * (double)H * st) : 0.0;
+        row[i] = make_float4((float)cos(th), (float)st, (float)g, 0.0f);
+    }
+    if (i < W) {
+        const double ps = 2.0 * pi * ((double)i + 0.5) / (double)W - pi;
+        col[i] = make_float2((float)cos(ps), (float)sin(ps));
+    }
+}
+
 // largest i in [0, n-1] with a[i] <= k
 __device__ __forceinline__ uint32_t search_all(const uint32_t* a, int n, uint32_t k)
 {
@@ -119,6 +141,8 @@ mirres_status mr_env_alloc(mirres_scene* s)
     e = e ? e : cudaMalloc((void**)&s->env_marg, sizeof(uint32_t) * (H + 1));
     e = e ? e : cudaMalloc((void**)&s->env_cond, sizeof(uint32_t) * H * (W + 1));
     e = e ? e : cudaMalloc((void**)&s->env_texel, sizeof(float4) * W * H);
+    e = e ? e : cudaMalloc((void**)&s->env_row, sizeof(float4) * H);
+    e = e ? e : cudaMalloc((void**)&s->env_col, sizeof(float2) * W);
     if (e != cudaSuccess) {
         cudaGetLastError();
         mr_set_error(std::string("env table allocation failed: ") + cudaGetErrorString(e));
@@ -130,7 +154,7 @@ mirres_status mr_env_alloc(mirres_scene* s)
 void mr_env_free(mirres_scene* s)
 {
     void* ptrs[] = {s->env_w,    s->env_rowsum, s->env_total, s->env_ok,   s->env_marg,
-                    s->env_cond, s->env_texel,  s->env_gmarg, s->env_gcond};
+                    s->env_cond, s->env_texel,  s->env_gmarg, s->env_gcond, s->env_row, s->env_col};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -143,6 +167,8 @@ mirres_status mr_env_build(mirres_scene* s, cudaStream_t st)
     const size_t n = (size_t)W * H;
     k_env_texels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->desc.env, s->env_w, W, H, s->env_total,
                                                              s->env_texel);
+    const int na = W > H ? W : H;
+    k_env_angles<<<(na + 127) / 128, 128, 0, st>>>(W, H, s->env_total, s->env_row, s->env_col);
     k_env_guide<<<(unsigned)((s->gm + 1 + 255) / 256), 256, 0, st>>>(s->env_marg, 1, H + 1, H, s->gm, s->gm_shift,
                                                                      s->env_gmarg);
     const size_t ng = (size_t)H * (s->gc + 1);

@@ -81,6 +81,8 @@ struct mirres_scene {
     float4* env_texel = nullptr;     // [eh][ew]
     uint32_t* env_gmarg = nullptr;   // [gm+1]
     uint32_t* env_gcond = nullptr;   // [eh][gc+1]
+    float4* env_row = nullptr;       // [eh]: (cos, sin of the row centre, RIS weight factor, 0)
+    float2* env_col = nullptr;       // [ew]: (cos, sin of the column centre angle)
     int gm_shift = 0, gc_shift = 0, gm = 1, gc = 1;
 };
 

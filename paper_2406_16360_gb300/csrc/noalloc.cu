@@ -115,7 +115,7 @@ extern "C" mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int3
         total += n;
         total_pix += (uint64_t)v.width * (uint64_t)v.height;
     }
-    if (tape_bytes < 36ull * total) return fail(MIRRES_ERR_ARG, "tape_bytes is smaller than mirres_tape_bytes(views)");
+    if (tape_bytes < (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total) return fail(MIRRES_ERR_ARG, "tape_bytes is smaller than mirres_tape_bytes(views)");
 
     MR_CUDA(cudaSetDevice(ctx->device));
     unsigned char* base = nullptr;

@@ -3,16 +3,30 @@
 // and warp-aggregated queue appends.
 #pragma once
 
+#include "../../include/mirres.h"
 #include "device.cuh"
 
 namespace {
 
+constexpr int kCandUnroll = MR_CAND_UNROLL;
+
+// The tape: TAPE_WORDS 32-bit words per path sample, structure of arrays over the samples.
+// It holds what the PRIMARY-mode adjoint needs to replay the primary vertex without
+// re-drawing any sample: the hit triangle, the RIS selection, the continuation and the
+// radiance the rest of the path brought back.
+enum { TAPE_WORDS = MIRRES_TAPE_BYTES_PER_SAMPLE / 4 };
+static_assert(TAPE_WORDS == 17, "tape_of lays out 17 words");
+
 struct TapeDev {
-    int32_t* tri;
-    int32_t* cand;
-    float* wv;
-    float* lind[3];
-    float* rad[3];
+    int32_t* tri;    // primary triangle, -1 when the primary ray escaped
+    int32_t* cand;   // index of the selected RIS candidate at the primary vertex, -1 if none
+    float* wv;       // V * W of that candidate (0 when occluded)
+    float* lind[3];  // L_ind arriving at the primary vertex along the continuation
+    float* rad[3];   // radiance of the whole sample
+    int32_t* ytex;   // env texel of the selected candidate (valid when cand >= 0)
+    float* y[3];     // its direction (valid when cand >= 0)
+    float* wc[3];    // continuation direction at the primary vertex (valid when L_ind != 0)
+    float* pind;     // its mixture pdf (valid when L_ind != 0)
 };
 
 __device__ __forceinline__ TapeDev tape_of(void* base, uint64_t n)
@@ -24,6 +38,10 @@ __device__ __forceinline__ TapeDev tape_of(void* base, uint64_t n)
     t.wv = reinterpret_cast<float*>(w + 2 * n);
     for (int k = 0; k < 3; ++k) t.lind[k] = reinterpret_cast<float*>(w + (3 + k) * n);
     for (int k = 0; k < 3; ++k) t.rad[k] = reinterpret_cast<float*>(w + (6 + k) * n);
+    t.ytex = reinterpret_cast<int32_t*>(w + 9 * n);
+    for (int k = 0; k < 3; ++k) t.y[k] = reinterpret_cast<float*>(w + (10 + k) * n);
+    for (int k = 0; k < 3; ++k) t.wc[k] = reinterpret_cast<float*>(w + (13 + k) * n);
+    t.pind = reinterpret_cast<float*>(w + 16 * n);
     return t;
 }
 
@@ -39,9 +57,22 @@ struct VertexOut {
     bool cont;
     float3 c_d, c_beta, c_bind;
     float3 x;
-    int cand;
-    float W;
+    int cand, ytex;
+    float W, c_pind;
 };
+
+// the directions the primary vertex drew, for the adjoint's replay (written at bounce 0)
+__device__ __forceinline__ void tape_directions(const TapeDev& tp, uint64_t g, const VertexOut& out)
+{
+    tp.ytex[g] = out.ytex;
+    tp.y[0][g] = out.sh_d.x;
+    tp.y[1][g] = out.sh_d.y;
+    tp.y[2][g] = out.sh_d.z;
+    tp.wc[0][g] = out.c_d.x;
+    tp.wc[1][g] = out.c_d.y;
+    tp.wc[2][g] = out.c_d.z;
+    tp.pind[g] = out.c_pind;
+}
 
 __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, const Rng& rng, uint32_t pixel,
                                              uint32_t smp, uint32_t view, int b, int B, int M, const Hit& h,
@@ -54,7 +85,11 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
     out.shadow = false;
     out.cont = false;
     out.cand = -1;
+    out.ytex = -1;
     out.W = 0.0f;
+    out.c_pind = 0.0f;
+    out.sh_d = f3(0.f, 0.f, 0.f);
+    out.c_d = f3(0.f, 0.f, 0.f);
     if (env_ok && M > 0) {
         // per-vertex parts of the BRDF: the candidates need only the luminance of f_r cos
         // (p_hat = Y(L_env) Y(f_r) cos); the selected one's RGB is rebuilt after the loop
@@ -66,44 +101,44 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
                              0.04f * (1.0f - sh.m.metal) + sh.m.metal * sh.m.alb.y,
                              0.04f * (1.0f - sh.m.metal) + sh.m.metal * sh.m.alb.z);
         const float ykd = lum(kd) * MR_INV_PI, yf0 = lum(f0);
-        float wsum = 0.0f, phat_sel = 0.0f;
+        float wsum = 0.0f, yfc_sel = 0.0f;
         float dv_sel = 0.0f, w5_sel = 0.0f, ci_sel = 0.0f;
         int sel = -1, ytex = 0;
         float3 ysel = f3(0.f, 0.f, 0.f);
-#pragma unroll 2
+#pragma unroll kCandUnroll
         for (int j = 0; j < M; ++j) {
             const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j);
             float3 dir;
             int tex;
-            const float q = env_sample(s, x.x, x.y, x.w, dir, tex);
+            const float gq = env_candidate(s, x.x, x.y, x.w, dir, tex);  // Y(L_env) / q_dir
             const float ci = dot(sh.n, dir);
-            float phat = 0.0f, dv = 0.0f, w5 = 0.0f;
+            float yfc = 0.0f, dv = 0.0f, w5 = 0.0f;
             if (co > 0.0f && ci > 0.0f) {
                 const float3 h = normalize(add(wo, dir));
                 const float cnh = dot(sh.n, h), coh = dot(wo, h);
                 const float k = ggx_k(sh.n, h, cnh, a2);
-                const float D = a2 / (MR_PI * k * k);
-                dv = D * (0.5f / (ci * Ao + co * smith_a(a2, ci)));
+                const float D = __fdividef(a2, MR_PI * k * k);
+                dv = D * __fdividef(0.5f, ci * Ao + co * smith_a(a2, ci));
                 const float om = 1.0f - coh;
                 w5 = (om * om) * (om * om) * om;
-                const float yfc = (ykd + dv * (yf0 * (1.0f - w5) + w5)) * ci;
-                phat = lum(xyz(__ldg(s.env_texel + tex))) * yfc;  // p_hat = Y(L_env) Y(f_r) cos
+                yfc = (ykd + dv * (yf0 * (1.0f - w5) + w5)) * ci;  // Y(f_r) cos
             }
-            const float gamma = phat / q;  // gamma = p_hat / q_dir
+            const float gamma = yfc * gq;  // gamma = p_hat / q_dir, p_hat = Y(L_env) Y(f_r) cos
             wsum += gamma;
             if (u24(x.z) * wsum < gamma) {
                 sel = j;
                 ytex = tex;
                 ysel = dir;
-                phat_sel = phat;
+                yfc_sel = yfc;
                 dv_sel = dv;
                 w5_sel = w5;
                 ci_sel = ci;
             }
         }
-        if (sel >= 0 && wsum > 0.0f) {
+        const float4 L = (sel >= 0) ? __ldg(s.env_texel + ytex) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float phat_sel = lum(xyz(L)) * yfc_sel;
+        if (sel >= 0 && wsum > 0.0f && phat_sel > 0.0f) {
             const float W = wsum / ((float)M * phat_sel);
-            const float4 L = __ldg(s.env_texel + ytex);
             const float3 fsel = f3((kd.x * MR_INV_PI + dv_sel * (f0.x * (1.0f - w5_sel) + w5_sel)) * ci_sel,
                                    (kd.y * MR_INV_PI + dv_sel * (f0.y * (1.0f - w5_sel) + w5_sel)) * ci_sel,
                                    (kd.z * MR_INV_PI + dv_sel * (f0.z * (1.0f - w5_sel) + w5_sel)) * ci_sel);
@@ -115,6 +150,7 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
             out.sh_d = ysel;
             if (b == 0) {
                 out.cand = sel;
+                out.ytex = ytex;
                 out.W = W;
             }
         }
@@ -128,6 +164,7 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
             const float3 f = f3(fc.x / pind, fc.y / pind, fc.z / pind);
             out.cont = true;
             out.c_d = wc;
+            out.c_pind = pind;
             out.c_beta = hmul_rn(beta, f);
             out.c_bind = (b >= 1) ? hmul_rn(bind, f) : bind;
         }

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_closest(SceneDev s, ViewDev v, int b, Q
 }
 
 // shade every compacted hit: RIS + shadow ray + continuation (next-bounce queue)
-__global__ void __launch_bounds__(256, 4) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev hq,
+__global__ void __launch_bounds__(256, MR_SHADE_MINB) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev hq,
                                                const unsigned int* count_hit, QueueDev qout,
                                                unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
                                                void* tape, uint64_t ntot, unsigned long long* counters)
@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(256, 4) k_shade(SceneDev s, ViewDev v, Rng rng
                 tp.tri[g] = tri;
                 tp.cand[g] = out.cand;
                 tp.wv[g] = out.W;
+                tape_directions(tp, g, out);
             }
         }
         const unsigned int ss = warp_append(out.shadow, count_sh);
@@ -309,6 +310,7 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
             if (b == 0) {
                 cand0 = out.cand;
                 wv0 = out.W;
+                tape_directions(tp, g, out);
             }
         }
         if (out.shadow) {
@@ -451,32 +453,31 @@ __device__ __forceinline__ void brdf_cos_adjoint(float3 n, float3 wo, float3 wi,
     gm[7] += g_ci * wi.z + g_co * wo.z + g_cnh * h.z;
 }
 
-// Warp-aggregated scatter: lanes with the same key (>= 0) sum their NV values with a
-// butterfly and one lane issues the atomics; singletons add directly. All 32 lanes call.
-template <int NV, typename Emit>
+// warp-aggregated scatter: lanes holding the same key add their values and the key's first
+// lane issues one set of atomics. The sums are segmented suffix sums by pointer jumping along
+// each key's lanes in lane order, every key at once: ceil(log2(largest group)) steps of
+// NV + 1 shuffles, however many distinct keys the warp holds.
+template <int NV, class Emit>
 __device__ __forceinline__ void scatter_agg(int key, const float (&v)[NV], const Emit& emit)
 {
     const int lane = lane_id();
     const unsigned peers = __match_any_sync(MR_FULL, key);
-    const bool valid = key >= 0;
-    const bool single = __popc(peers) == 1;
-    if (valid && single) emit(key, v);
-    unsigned multi = __ballot_sync(MR_FULL, valid && !single && (__ffs(peers) - 1) == lane);
-    while (multi) {
-        const int l = __ffs(multi) - 1;
-        multi &= multi - 1;
-        const int kk = __shfl_sync(MR_FULL, key, l);
-        const bool mine = key == kk;
-        float s[NV];
+    const unsigned after = peers & ~((2u << lane) - 1u);  // my key's lanes above me
+    int nxt = (key >= 0 && after) ? __ffs(after) - 1 : -1;
+    float acc[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] = v[c];
+    while (__any_sync(MR_FULL, nxt >= 0)) {
+        const int src = nxt >= 0 ? nxt : lane;
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-            float x = mine ? v[c] : 0.0f;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(MR_FULL, x, off);
-            s[c] = x;
+            const float o = __shfl_sync(MR_FULL, acc[c], src);
+            if (nxt >= 0) acc[c] += o;
         }
-        if (lane == l) emit(kk, s);
+        const int n2 = __shfl_sync(MR_FULL, nxt, src);
+        nxt = nxt >= 0 ? n2 : -1;
     }
+    if (key >= 0 && (__ffs(peers) - 1) == lane) emit(key, acc);
 }
 
 struct EmitEnv {
@@ -515,7 +516,7 @@ struct EmitVert {
     }
 };
 
-__global__ void __launch_bounds__(256, 4) k_backward(const SceneDev* __restrict__ scenes,
+__global__ void __launch_bounds__(256, MR_BWD_MINB) k_backward(const SceneDev* __restrict__ scenes,
                                                   const ViewDev* __restrict__ views, int n_views, uint64_t total,
                                                   Rng rng, const float* const* __restrict__ d_images,
                                                   const GradDev* __restrict__ grads, const void* tape,
@@ -565,15 +566,13 @@ __global__ void __launch_bounds__(256, 4) k_backward(const SceneDev* __restrict_
                     Shade sh;
                     shade_at(s, tri, u, vv, d, sh);
                     const float3 wo = f3(-d.x, -d.y, -d.z);
-                    const int env_ok = *s.env_ok_dev;
                     float gm[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     const int cand = tp.cand[g];
                     const float wv = tp.wv[g];
                     if (cand >= 0 && wv != 0.0f) {
-                        const uint4 x = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_CANDIDATE, (uint32_t)cand);
-                        float3 y;
-                        int ytex;
-                        env_sample(s, x.x, x.y, x.w, y, ytex);
+                        // the selected candidate's direction and texel, as the forward drew them
+                        const float3 y = f3(tp.y[0][g], tp.y[1][g], tp.y[2][g]);
+                        const int ytex = tp.ytex[g];
                         const float3 fc = brdf_cos(sh.n, wo, y, sh.m);
                         const float4 L = __ldg(s.env_texel + ytex);
                         env_key = ytex;
@@ -584,9 +583,9 @@ __global__ void __launch_bounds__(256, 4) k_backward(const SceneDev* __restrict_
                     }
                     const float3 li = f3(tp.lind[0][g], tp.lind[1][g], tp.lind[2][g]);
                     if (v.bounces > 1 && (li.x != 0.0f || li.y != 0.0f || li.z != 0.0f)) {
-                        const uint4 x = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_CONTINUE, 0u);
-                        float3 wc;
-                        const float pind = sample_continuation(s, env_ok, sh.n, wo, sh.m, x, wc);
+                        // the continuation the forward drew (L_ind != 0 implies it was taken)
+                        const float3 wc = f3(tp.wc[0][g], tp.wc[1][g], tp.wc[2][g]);
+                        const float pind = tp.pind[g];
                         if (pind > 0.0f)
                             brdf_cos_adjoint(sh.n, wo, wc, sh.m,
                                              f3(gI.x * li.x / pind, gI.y * li.y / pind, gI.z * li.z / pind), gm);

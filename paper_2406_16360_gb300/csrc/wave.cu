@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_wclosest(const SceneDev* __restrict__ s
     }
 }
 
-__global__ void __launch_bounds__(256, 4) k_wshade(const SceneDev* __restrict__ scenes,
+__global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* __restrict__ scenes,
                                                 const ViewDev* __restrict__ views, Rng rng, int b, int M,
                                                 QueueDev hq, const unsigned int* count_hit, QueueDev qout,
                                                 unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(256, 4) k_wshade(const SceneDev* __restrict__ 
                 tp.tri[g] = tri;
                 tp.cand[g] = out.cand;
                 tp.wv[g] = out.W;
+                tape_directions(tp, g, out);
             }
         }
         const unsigned int ss = warp_append(out.shadow, count_sh);

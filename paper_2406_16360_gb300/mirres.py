@@ -23,6 +23,8 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_reset_counters", "mirres_last_error", "library_path"]
 
 # limits of mirres_render_noalloc (include/mirres.h)
+MIRRES_TAPE_BYTES_PER_SAMPLE = 68  # 17 words per path sample, one array per word
+TAPE_WORDS = MIRRES_TAPE_BYTES_PER_SAMPLE // 4
 MIRRES_NOALLOC_SCRATCH_BYTES = 512 * 1024
 MIRRES_NOALLOC_MAX_VIEWS = 4096
 MIRRES_NOALLOC_MAX_SCENES = 256

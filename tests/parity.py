@@ -51,3 +51,24 @@ def compare_grads(gpu, ora, ora_abs, ora_sens=None, rtol=GRAD_RTOL, floor=GRAD_A
     detail = [(int(i), float(gpu[i]), float(ora[i]), float(ab[i])) for i in bi[:6]]
     return dict(n=len(ora), nonzero=int(nz.sum()), failures=int(bad.sum()), bad_idx=bi, detail=detail,
                 median_rel=float(np.median(rel)) if len(rel) else 0.0, max_rel=float(rel.max()) if len(rel) else 0.0)
+
+
+def compare_tapes(a, b, rtol=2e-6):
+    """Two tapes of the same views (uint32 words, shape [TAPE_WORDS, n]) took the same discrete
+    decisions (hit triangle, selected candidate and its texel) and hold the same floats up to
+    rtol, word by word, wherever the word is defined (words 9-12 where a candidate was
+    selected, 13-16 where L_ind != 0)."""
+    import numpy as np
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    sel = a[1].view(np.int32) >= 0
+    assert np.array_equal(a[9][sel], b[9][sel])
+    fa, fb = a.view(np.float32), b.view(np.float32)
+    ind = np.any(fa[3:6] != 0.0, axis=0) | np.any(fb[3:6] != 0.0, axis=0)
+
+    def close(x, y, floor=1e-30):
+        return np.all(np.abs(x - y) <= rtol * np.maximum(np.abs(x), floor))
+
+    assert close(fa[2:9], fb[2:9])
+    assert close(fa[10:13][:, sel], fb[10:13][:, sel], floor=1.0)  # unit vectors
+    assert close(fa[13:16][:, ind], fb[13:16][:, ind], floor=1.0)
+    assert close(fa[16][ind], fb[16][ind])

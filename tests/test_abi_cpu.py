@@ -57,12 +57,14 @@ def test_host_side_argument_checks(lib):
     assert lib.mirres_context_create(0, None) == 1
 
 
-def test_tape_bytes_is_36_per_sample(lib):
+def test_tape_bytes_per_sample(lib):
     from paper_2406_16360_gb300 import mirres as M
+    hdr = open(os.path.join(ROOT, "include", "mirres.h")).read()
+    assert re.search(r"#define MIRRES_TAPE_BYTES_PER_SAMPLE (\d+)", hdr).group(1) == str(M.MIRRES_TAPE_BYTES_PER_SAMPLE)
     views = (M.View * 2)(M.make_view([1, 1, 0, 0], [0] * 12, 64, 32, 4, 2), M.make_view([1, 1, 0, 0], [0] * 12, 5, 3, 7, 3))
     lib.mirres_tape_bytes.restype = C.c_size_t
     lib.mirres_tape_bytes.argtypes = [C.POINTER(M.View), C.c_int32]
-    assert lib.mirres_tape_bytes(views, 2) == 36 * (64 * 32 * 4 + 5 * 3 * 7)
+    assert lib.mirres_tape_bytes(views, 2) == M.MIRRES_TAPE_BYTES_PER_SAMPLE * (64 * 32 * 4 + 5 * 3 * 7)
     assert lib.mirres_tape_bytes(views, 0) == 0
 
 

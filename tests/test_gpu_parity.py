@@ -5,10 +5,11 @@ import torch
 
 from oracle import oracle as O
 from paper_2406_16360_gb300 import synth
+from paper_2406_16360_gb300.mirres import TAPE_WORDS
 
 pytestmark = pytest.mark.gpu
 
-from tests.parity import compare_grads, compare_pixels  # noqa: E402
+from tests.parity import compare_grads, compare_pixels, compare_tapes  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -216,14 +217,12 @@ def test_config1_forward_plain_and_batched_identical(M, ctx):
     # the launch paths take every discrete decision identically (hit triangle, selected
     # candidate); their values differ only by FP32 contraction choices of the kernels
     N = w.samples
-    a = tape0.cpu().numpy().view(np.uint32).reshape(9, N)
+    a = tape0.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, N)
     for launch in (1, 2):
         imgs1, tape1 = gw.render(launch=launch)
         torch.cuda.synchronize()
-        b = tape1.cpu().numpy().view(np.uint32).reshape(9, N)
-        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
-        fa, fb = a[2:].view(np.float32), b[2:].view(np.float32)
-        assert np.all(np.abs(fa - fb) <= 2e-6 * np.maximum(np.abs(fa), 1e-30))
+        b = tape1.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, N)
+        compare_tapes(a, b, rtol=2e-6)
         torch.testing.assert_close(imgs0[0], imgs1[0], rtol=2e-6, atol=0)
     print("config1 forward:", {k: st[0][k] for k in ("n", "flagged", "max_err_unflagged", "median_err")})
 

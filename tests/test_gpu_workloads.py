@@ -10,6 +10,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2406_16360_gb300 import synth
+from paper_2406_16360_gb300.mirres import TAPE_WORDS
 from tests.parity import compare_grads, compare_pixels
 
 pytestmark = pytest.mark.gpu
@@ -132,7 +133,7 @@ def test_edge_cases_forward(M, ctx, name, launch):
     if name == "black_env":
         assert float(images[0].abs().max()) == 0.0
     if name == "empty_scene":
-        t = tape.cpu().numpy().view(np.int32).reshape(9, -1)
+        t = tape.cpu().numpy().view(np.int32).reshape(TAPE_WORDS, -1)
         assert np.all(t[0] == -1)
     for s in gw.scenes:
         s.close()
@@ -159,8 +160,8 @@ def test_multi_scene_batch_mixed_bounces(M, ctx):
     for launch in (1, 2):
         img, tape = _forward_parity(gw, w, launch, max_flag_frac=0.15)
         n = w.samples
-        a = tape0.cpu().numpy().view(np.uint32).reshape(9, n)
-        b = tape.cpu().numpy().view(np.uint32).reshape(9, n)
+        a = tape0.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, n)
+        b = tape.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, n)
         assert np.array_equal(a[:2], b[:2])
     _grad_parity(gw, w, tape0)
     for s in gw.scenes:
@@ -325,8 +326,8 @@ def test_autotune_and_set_launch(M, ctx):
         img, t = gw.render(launch=2)
         torch.cuda.synchronize()
         n = w.samples
-        assert np.array_equal(t.cpu().numpy().view(np.uint32).reshape(9, n)[:2],
-                              reft.cpu().numpy().view(np.uint32).reshape(9, n)[:2])
+        assert np.array_equal(t.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, n)[:2],
+                              reft.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, n)[:2])
     M.mirres_set_launch(ctx, 0, 0, 0)
     for s in gw.scenes:
         s.close()

@@ -7,6 +7,7 @@ import pytest
 import torch
 
 from paper_2406_16360_gb300 import synth
+from paper_2406_16360_gb300.mirres import TAPE_WORDS
 from tests.parity import FWD_RTOL
 
 pytestmark = pytest.mark.gpu
@@ -35,8 +36,8 @@ def test_noalloc_matches_render_on_two_calls():
         M.mirres_render_noalloc(scenes, gw.views, gw.params(1), img, tape)
         torch.cuda.synchronize()
         n = w.samples
-        a = tape.cpu().numpy().view(np.uint32).reshape(9, n)
-        b = ref_tape.cpu().numpy().view(np.uint32).reshape(9, n)
+        a = tape.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, n)
+        b = ref_tape.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, n)
         assert np.array_equal(a[:2], b[:2])  # hit triangles and selected candidates
         for x, y in zip(img, ref_img):
             assert _relerr(x, y) <= FWD_RTOL
