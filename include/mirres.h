@@ -94,7 +94,7 @@ typedef struct {
  *   launch   0 = plain: per-view wavefront launches (ray generation, closest hit with hit
  *                 compaction, shade + RIS + next-bounce queue, shadow rays, resolve);
  *            1 = batched wavefront: every view of every scene flattened into waves of up to
- *                 2^24 samples; the whole forward is one CUDA graph, captured on first use and
+ *                 2^25 samples; the whole forward is one CUDA graph, captured on first use and
  *                 replayed while the shape, tape, seed and workspace stay the same;
  *            2 = persistent kernel: one launch over every view of every scene, each warp
  *                 pulling samples from a device counter and refilling lanes by ballot.

@@ -302,8 +302,12 @@ static Rng make_rng(const mirres_params* p)
     return r;
 }
 
-// samples per wave of the batched wavefront
-static const uint64_t kWave = 1ull << 24;
+// samples per wave of the batched wavefront (queues take 256 bytes per sample of a wave)
+#ifndef MR_WAVE_LOG2
+#define MR_WAVE_LOG2 25
+#endif
+static_assert(MR_WAVE_LOG2 >= 10 && MR_WAVE_LOG2 <= 28, "wave size out of range");
+static const uint64_t kWave = 1ull << MR_WAVE_LOG2;
 
 struct GraphKey {
     uint64_t total, total_pix, wave;

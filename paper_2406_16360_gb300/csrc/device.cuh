@@ -456,12 +456,13 @@ __device__ __forceinline__ float safe_inv(float x)
     return 1.0f / (fabsf(x) > 1e-30f ? x : copysignf(1e-30f, x));
 }
 
-// slab test of one box; returns the entry distance, or NaN on a miss (NaN <= t is false)
-__device__ __forceinline__ float slab(float3 lo, float3 hi, float3 o, float3 inv, float tmin, float tmax)
+// slab test of one box; returns the entry distance, or NaN on a miss (NaN <= t is false).
+// Plane distances as one FMA each, (plane * inv) - (o * inv) with oi = o * inv per ray.
+__device__ __forceinline__ float slab(float3 lo, float3 hi, float3 oi, float3 inv, float tmin, float tmax)
 {
-    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
-    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
-    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+    const float tx0 = fmaf(lo.x, inv.x, -oi.x), tx1 = fmaf(hi.x, inv.x, -oi.x);
+    const float ty0 = fmaf(lo.y, inv.y, -oi.y), ty1 = fmaf(hi.y, inv.y, -oi.y);
+    const float tz0 = fmaf(lo.z, inv.z, -oi.z), tz1 = fmaf(hi.z, inv.z, -oi.z);
     const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
     const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
     // a few ulp of slack so that rounding never culls a box the ray touches
@@ -485,6 +486,7 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
         return 1;
     }
     const float3 inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    const float3 oi = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
     uint32_t lstk[MR_LSTACK];
     int sp = 0;
     int node = 0;
@@ -499,8 +501,8 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
         const float4 n1 = __ldg(s.nodes + 4 * (size_t)node + 1);
         const float4 n2 = __ldg(s.nodes + 4 * (size_t)node + 2);
         const int2 ch = *reinterpret_cast<const int2*>(&s.nodes[4 * (size_t)node + 3]);
-        const float tl = slab(f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), o, inv, tmin, best.t);
-        const float tr = slab(f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), o, inv, tmin, best.t);
+        const float tl = slab(f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), oi, inv, tmin, best.t);
+        const float tr = slab(f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), oi, inv, tmin, best.t);
         bool gl = tl <= best.t, gr = tr <= best.t;
         // leaves are tested on the spot
         if (gl && ch.x < 0) {
