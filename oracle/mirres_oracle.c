@@ -910,6 +910,18 @@ typedef struct {
     v3 wc;
     double p_ind;
     double Lind[3];
+    int nv;           /* vertices recorded below (FULL mode) */
+    struct {
+        int tri;
+        double u, v, t;
+        v3 d;         /* incoming ray direction */
+        int sel, y_texel;
+        v3 y;
+        double WV;    /* V W of the direct term (0: none) */
+        int has_cont;
+        v3 wc;
+        double p_ind;
+    } vx[ORC_MAXB];
 } Rec;
 
 static void rng(const Ctx* c, uint32_t pixel, uint32_t sample, uint32_t bounce, uint32_t purpose, uint32_t j, uint32_t out[4])
@@ -968,6 +980,12 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         Shade sh;
         shade_at(s, h.tri, h.u, h.v, h.t, d, &sh, mg);
         v3 wo = vscale(d, -1.0);
+        if (b < ORC_MAXB) {
+            rec->nv = b + 1;
+            rec->vx[b].tri = h.tri; rec->vx[b].u = h.u; rec->vx[b].v = h.v; rec->vx[b].t = h.t;
+            rec->vx[b].d = d;
+            rec->vx[b].sel = -1; rec->vx[b].y_texel = -1; rec->vx[b].WV = 0.0; rec->vx[b].has_cont = 0;
+        }
         if (b == 0) note(mg, vdot(sh.n, wo) / TAU_GRAZE, MK_GRAZE);
         /* ---- direct light: RIS over M env candidates, streamed through a reservoir ---- */
         double direct[3] = {0, 0, 0};
@@ -1002,6 +1020,9 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
                 double V = occluded ? 0.0 : 1.0;
                 for (int k = 0; k < 3; ++k) direct[k] = V * W * s->env[3 * ytex + k] * fsel[k];
                 if (b == 0) { rec->sel = rs.sel; rec->y = ysel; rec->y_texel = ytex; rec->WV = V * W; }
+                if (b < ORC_MAXB) {
+                    rec->vx[b].sel = rs.sel; rec->vx[b].y = ysel; rec->vx[b].y_texel = ytex; rec->vx[b].WV = V * W;
+                }
             }
         }
         for (int k = 0; k < 3; ++k) {
@@ -1018,6 +1039,7 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         brdf_cos(sh.n, wo, wc, sh.alb, sh.rgh, sh.met, kind, fc);
         if (!(pind > 0.0) || (fc[0] <= 0.0 && fc[1] <= 0.0 && fc[2] <= 0.0)) break;
         if (b == 0) { rec->has_cont = 1; rec->wc = wc; rec->p_ind = pind; }
+        if (b < ORC_MAXB) { rec->vx[b].has_cont = 1; rec->vx[b].wc = wc; rec->vx[b].p_ind = pind; }
         for (int k = 0; k < 3; ++k) {
             double f = fc[k] / pind;
             beta[k] *= f;
@@ -1146,6 +1168,132 @@ static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], Sparse*
     }
 }
 
+/* FULL mode: the vertices after the primary one (the gradients of indirect rays that Sec. 4.2
+ * detaches and Appendix C lists as missing). With L = sum_b beta_b direct_b, beta_{b+1} =
+ * beta_b (f_r cos)(wc_b) / p_b, direct_b = WV_b L_env(y_b) (f_r cos)(y_b), every sampling
+ * decision, W, V and p_ind detached and the hit points of vertices b >= 1 held fixed on their
+ * triangles, the derivative w.r.t. the material at x_b (b >= 1) is, per channel,
+ *   beta_b [ WV_b L_env(y_b) d(f_r cos)(y_b) + (Lin_b / p_b) d(f_r cos)(wc_b) ]
+ * and w.r.t. the env texel of y_b it is beta_b WV_b (f_r cos)(y_b); Lin_b is the radiance
+ * arriving at x_b along wc_b from the rest of the path. The normal's derivative is dropped
+ * (geometry detached beyond the primary vertex). */
+static void sample_grad_secondary(const Ctx* c, const Rec* rec, const double g[3], Sparse* sp)
+{
+    const orc_scene* s = c->s;
+    const int kind = c->p->brdf_kind;
+    const int nv = rec->nv;
+    if (rec->prim_tri < 0 || nv < 2) return;
+    Shade sh[ORC_MAXB];
+    double fy[ORC_MAXB][3], fc[ORC_MAXB][3], dir[ORC_MAXB][3], beta[ORC_MAXB][3], lin[ORC_MAXB][3];
+    for (int b = 0; b < nv; ++b) {
+        shade_at(s, rec->vx[b].tri, rec->vx[b].u, rec->vx[b].v, rec->vx[b].t, rec->vx[b].d, &sh[b], NULL);
+        v3 wo = vscale(rec->vx[b].d, -1.0);
+        for (int k = 0; k < 3; ++k) fy[b][k] = fc[b][k] = dir[b][k] = 0.0;
+        if (rec->vx[b].sel >= 0 && rec->vx[b].WV != 0.0) {
+            brdf_cos(sh[b].n, wo, rec->vx[b].y, sh[b].alb, sh[b].rgh, sh[b].met, kind, fy[b]);
+            for (int k = 0; k < 3; ++k) dir[b][k] = rec->vx[b].WV * s->env[3 * rec->vx[b].y_texel + k] * fy[b][k];
+        }
+        if (rec->vx[b].has_cont) brdf_cos(sh[b].n, wo, rec->vx[b].wc, sh[b].alb, sh[b].rgh, sh[b].met, kind, fc[b]);
+    }
+    for (int k = 0; k < 3; ++k) beta[0][k] = 1.0;
+    for (int b = 1; b < nv; ++b)
+        for (int k = 0; k < 3; ++k) beta[b][k] = beta[b - 1][k] * fc[b - 1][k] / rec->vx[b - 1].p_ind;
+    for (int k = 0; k < 3; ++k) lin[nv - 1][k] = 0.0;
+    for (int b = nv - 2; b >= 0; --b)
+        for (int k = 0; k < 3; ++k)
+            lin[b][k] = dir[b + 1][k] +
+                        (rec->vx[b + 1].has_cont ? fc[b + 1][k] / rec->vx[b + 1].p_ind * lin[b + 1][k] : 0.0);
+    for (int b = 1; b < nv; ++b) {
+        const Shade* h = &sh[b];
+        v3 wo = vscale(rec->vx[b].d, -1.0);
+        double gm[8] = {0, 0, 0, 0, 0, 0, 0, 0}, tmp[8], gq[3];
+        if (rec->vx[b].sel >= 0 && rec->vx[b].WV != 0.0) {
+            for (int k = 0; k < 3; ++k) {
+                double le = s->env[3 * rec->vx[b].y_texel + k];
+                sp_add(sp, GB_ENV, 3 * (int64_t)rec->vx[b].y_texel + k, g[k] * beta[b][k] * rec->vx[b].WV * fy[b][k]);
+                gq[k] = g[k] * beta[b][k] * rec->vx[b].WV * le;
+            }
+            brdf_cos_grad(h->n, wo, rec->vx[b].y, h->alb, h->rgh, h->met, kind, gq, tmp);
+            for (int k = 0; k < 8; ++k) gm[k] += tmp[k];
+        }
+        if (rec->vx[b].has_cont) {
+            for (int k = 0; k < 3; ++k) gq[k] = g[k] * beta[b][k] * lin[b][k] / rec->vx[b].p_ind;
+            brdf_cos_grad(h->n, wo, rec->vx[b].wc, h->alb, h->rgh, h->met, kind, gq, tmp);
+            for (int k = 0; k < 8; ++k) gm[k] += tmp[k];
+        }
+        /* FP32 sensitivity (test tolerance only): a single-precision path reaches x_b with a
+         * position error of a few FP32 units of the distances involved, amplified along the
+         * path; bounded generously by 64 u (t + |x_{b-1} - v0| + |x_{b-1}|) |row of A^-1| */
+        {
+            const double u32 = 1.0 / 16777216.0;
+            const double* uv = s->UV + 6 * h->tri;
+            v3 md = vscale(rec->vx[b].d, -1.0);
+            v3 r0 = vcross(h->e2, md), r1 = vcross(md, h->e1);
+            double det = vdot(h->e1, r0);
+            v3 a, bb, cc;
+            tri_verts(s, h->tri, &a, &bb, &cc);
+            v3 o = sh[b - 1].x;
+            double lever = 64.0 * u32 * (h->t + vlen(vsub(o, a)) + vlen(o)) / fabs(det);
+            double du = lever * vlen(r0), dv = lever * vlen(r1);
+            double dfx = s->tw * (fabs(uv[2] - uv[0]) * du + fabs(uv[4] - uv[0]) * dv);
+            double dfy = s->th * (fabs(uv[3] - uv[1]) * du + fabs(uv[5] - uv[1]) * dv);
+            double dw = dfx + dfy;
+            for (int k = 0; k < 4; ++k) {
+                int i = h->tp.idx[k];
+                for (int ch = 0; ch < 3; ++ch) sp_add(sp, GB_ALB_S, 3 * (int64_t)i + ch, dw * fabs(gm[ch]));
+                sp_add(sp, GB_RGH_S, i, dw * fabs(gm[3]));
+                sp_add(sp, GB_MET_S, i, dw * fabs(gm[4]));
+            }
+        }
+        for (int k = 0; k < 4; ++k) {
+            int i = h->tp.idx[k];
+            double w = h->tp.w[k];
+            for (int ch = 0; ch < 3; ++ch) sp_add(sp, GB_ALB, 3 * (int64_t)i + ch, w * gm[ch]);
+            sp_add(sp, GB_RGH, i, w * gm[3]);
+            sp_add(sp, GB_MET, i, w * gm[4]);
+        }
+    }
+}
+
+/* the material of a fixed surface point re-fetched from the textures of `ev` */
+static void refetch_material(const orc_scene* ev, Shade* sh)
+{
+    sh->alb[0] = sh->alb[1] = sh->alb[2] = sh->rgh = sh->met = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        int i = sh->tp.idx[k];
+        double w = sh->tp.w[k];
+        for (int ch = 0; ch < 3; ++ch) sh->alb[ch] += w * ev->alb[3 * i + ch];
+        sh->rgh += w * ev->rgh[i];
+        sh->met += w * ev->met[i];
+    }
+}
+
+/* FULL mode detached evaluation: the light arriving at the primary vertex along wc_0 (Lin_0),
+ * re-evaluated with the materials and env of `ev` at the recorded vertices b >= 1 */
+static void detached_lin0(const Ctx* c, const orc_scene* ev, const Rec* rec, double lin0[3])
+{
+    const int kind = c->p->brdf_kind;
+    const int nv = rec->nv;
+    double lin[3] = {0, 0, 0};
+    for (int b = nv - 1; b >= 1; --b) {
+        Shade sh;
+        shade_at(c->s, rec->vx[b].tri, rec->vx[b].u, rec->vx[b].v, rec->vx[b].t, rec->vx[b].d, &sh, NULL);
+        refetch_material(ev, &sh);
+        v3 wo = vscale(rec->vx[b].d, -1.0);
+        double nl[3] = {0, 0, 0}, f[3];
+        if (rec->vx[b].sel >= 0 && rec->vx[b].WV != 0.0) {
+            brdf_cos(sh.n, wo, rec->vx[b].y, sh.alb, sh.rgh, sh.met, kind, f);
+            for (int k = 0; k < 3; ++k) nl[k] += rec->vx[b].WV * ev->env[3 * rec->vx[b].y_texel + k] * f[k];
+        }
+        if (rec->vx[b].has_cont) {
+            brdf_cos(sh.n, wo, rec->vx[b].wc, sh.alb, sh.rgh, sh.met, kind, f);
+            for (int k = 0; k < 3; ++k) nl[k] += f[k] / rec->vx[b].p_ind * lin[k];
+        }
+        for (int k = 0; k < 3; ++k) lin[k] = nl[k];
+    }
+    for (int k = 0; k < 3; ++k) lin0[k] = lin[k];
+}
+
 /* detached evaluation of one sample's primary-vertex terms with the parameters of `ev` */
 static void sample_detached(const Ctx* c, const orc_scene* ev, const Rec* rec, double out[3])
 {
@@ -1167,9 +1315,10 @@ static void sample_detached(const Ctx* c, const orc_scene* ev, const Rec* rec, d
         for (int k = 0; k < 3; ++k) out[k] += rec->WV * ev->env[3 * rec->y_texel + k] * fc[k];
     }
     if (rec->has_cont) {
-        double fc[3];
+        double fc[3], lin[3] = {rec->Lind[0], rec->Lind[1], rec->Lind[2]};
+        if (c->p->grad_mode == 1) detached_lin0(c, ev, rec, lin);
         brdf_cos(sh.n, wo, rec->wc, sh.alb, sh.rgh, sh.met, kind, fc);
-        for (int k = 0; k < 3; ++k) out[k] += fc[k] / rec->p_ind * rec->Lind[k];
+        for (int k = 0; k < 3; ++k) out[k] += fc[k] / rec->p_ind * lin[k];
     }
 }
 
@@ -1208,7 +1357,10 @@ static void* job_run(void* arg)
             } else if (jb->mode == 1) {
                 double g[3];
                 for (int k = 0; k < 3; ++k) g[k] = jb->d_rgb[3 * (size_t)i + k] / spp;
-                if (g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0) sample_grad(c, &rec, g, &jb->sp);
+                if (g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0) {
+                    sample_grad(c, &rec, g, &jb->sp);
+                    if (c->p->grad_mode == 1) sample_grad_secondary(c, &rec, g, &jb->sp);
+                }
             } else {
                 double o3[3];
                 sample_detached(c, jb->ev, &rec, o3);
@@ -1230,6 +1382,7 @@ static int run_jobs(int mode, const orc_scene* s, const orc_scene* ev, const orc
                     const double* d_rgb, const orc_grads* g, int64_t* counts)
 {
     if (!s || !v || !p || v->width < 1 || v->height < 1 || v->spp < 1 || v->bounces < 1 || p->ris_m < 0) return 1;
+    if (p->grad_mode != 0 && (p->grad_mode != 1 || v->bounces > ORC_MAXB)) return 1;
     if (!pixels) n = v->width * v->height;
     for (int i = 0; pixels && i < n; ++i)
         if (pixels[i] < 0 || pixels[i] >= v->width * v->height) return 1;

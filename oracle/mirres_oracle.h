@@ -50,7 +50,11 @@ typedef struct {
     int32_t brdf_kind;   /* 0 = GGX + Lambert (the method); 1 = Lambert only (furnace pin) */
     int32_t threads;     /* worker threads (>= 1) */
     int32_t want_margin; /* 1: track decision margins */
+    int32_t grad_mode;   /* 0 = PRIMARY (the paper's); 1 = FULL (every vertex, at most ORC_MAXB) */
 } orc_params;
+
+/* vertices per path recorded for the FULL-mode adjoint */
+#define ORC_MAXB 16
 
 /* per-pixel gradient destinations; any pointer may be NULL */
 typedef struct {
@@ -79,16 +83,21 @@ int orc_render(const orc_scene* s, const orc_view* v, const orc_params* p,
                const int32_t* pixels, int32_t n_pixels,
                double* out_rgb, double* out_margin, int32_t* out_prim_tri, int64_t* counts);
 
-/* Adjoint (PRIMARY mode: gradients of the primary-vertex terms, indirect light, visibility,
- * the RIS weight and all sampling decisions detached). d_rgb [n][3] = dL/dI at the listed
- * pixels. Gradients are accumulated (+=). */
+/* Adjoint. PRIMARY mode: gradients of the primary-vertex terms, indirect light, visibility,
+ * the RIS weight and all sampling decisions detached. FULL mode: in addition the terms of
+ * every later vertex (its direct light and the BRDF factor it puts on the light arriving from
+ * the rest of the path), with the same quantities detached and the later hit points held
+ * fixed on their triangles (no geometric derivative beyond the primary vertex); requires
+ * bounces <= ORC_MAXB. d_rgb [n][3] = dL/dI at the listed pixels. Gradients are accumulated (+=). */
 int orc_backward(const orc_scene* s, const orc_view* v, const orc_params* p,
                  const int32_t* pixels, int32_t n_pixels, const double* d_rgb,
                  const orc_grads* g, int64_t* counts);
 
-/* Detached forward: the primary-vertex terms evaluated with the parameters of `eval`, every
- * detached quantity (sampling decisions, W, V, L_ind, p_ind, hit triangle) taken from
- * `frozen`. Its derivative w.r.t. `eval` at eval == frozen is what orc_backward returns. */
+/* Detached forward: the sample's radiance re-evaluated with the parameters of `eval`, every
+ * detached quantity (sampling decisions, W, V, p_ind, hit triangles) taken from `frozen`.
+ * PRIMARY mode: the primary-vertex terms with L_ind detached too. FULL mode: the whole path,
+ * later hit points fixed on their triangles (geometry from `frozen`, materials and env from
+ * `eval`). Its derivative w.r.t. `eval` at eval == frozen is what orc_backward returns. */
 int orc_render_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v,
                         const orc_params* p, const int32_t* pixels, int32_t n_pixels,
                         double* out_rgb);

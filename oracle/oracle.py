@@ -50,7 +50,8 @@ class View(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("ris_m", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32),
-                ("brdf_kind", C.c_int32), ("threads", C.c_int32), ("want_margin", C.c_int32)]
+                ("brdf_kind", C.c_int32), ("threads", C.c_int32), ("want_margin", C.c_int32),
+                ("grad_mode", C.c_int32)]
 
 
 GRAD_FIELDS = ("albedo", "roughness", "metallic", "env", "verts", "albedo_abs", "roughness_abs", "metallic_abs",
@@ -152,11 +153,11 @@ def make_view(view, index):
                 int(view.width), int(view.height), int(view.spp), int(view.bounces), int(index))
 
 
-def make_params(ris_m, seed=0, threads=None, brdf_kind=0, want_margin=1):
+def make_params(ris_m, seed=0, threads=None, brdf_kind=0, want_margin=1, grad_mode=0):
     if threads is None:
         threads = os.cpu_count() or 1
     return Params(int(ris_m), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(brdf_kind), int(threads),
-                  int(want_margin))
+                  int(want_margin), int(grad_mode))
 
 
 def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind=0, margins=True,
@@ -178,8 +179,10 @@ def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind
                 kind=None if mg is None else mg[:, 1].astype(np.int32), prim=pr, counts=cnt)
 
 
-def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, brdf_kind=0, want_abs=True):
-    """Adjoint of the listed pixels; returns dict of FP64 gradients (and abs-sums)."""
+def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, brdf_kind=0, want_abs=True,
+             grad_mode=0):
+    """Adjoint of the listed pixels (grad_mode 0 PRIMARY, 1 FULL); returns dict of FP64
+    gradients (and abs-sums)."""
     L = lib()
     s = osc.scene
     n = view.width * view.height if pixels is None else len(pixels)
@@ -195,7 +198,7 @@ def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, 
     g = Grads(*[_p(out.get(k)) for k in GRAD_FIELDS])
     cnt = np.zeros(8, dtype=np.int64)
     v = make_view(view, index)
-    p = make_params(ris_m, seed, threads, brdf_kind, 0)
+    p = make_params(ris_m, seed, threads, brdf_kind, 0, grad_mode)
     rc = L.orc_backward(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(d), C.byref(g), _p(cnt))
     if rc:
         raise ValueError("orc_backward rejected its arguments")
@@ -203,13 +206,14 @@ def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, 
     return out
 
 
-def render_detached(frozen, evaled, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind=0):
+def render_detached(frozen, evaled, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind=0,
+                    grad_mode=0):
     L = lib()
     n = view.width * view.height if pixels is None else len(pixels)
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
     rgb = np.zeros((n, 3))
     v = make_view(view, index)
-    p = make_params(ris_m, seed, threads, brdf_kind, 0)
+    p = make_params(ris_m, seed, threads, brdf_kind, 0, grad_mode)
     rc = L.orc_render_detached(frozen.h, evaled.h, C.byref(v), C.byref(p), _p(pix), n, _p(rgb))
     if rc:
         raise ValueError("orc_render_detached rejected its arguments")
