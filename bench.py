@@ -7,7 +7,8 @@ image loss against reference images and the adjoint (PRIMARY mode) into the grad
 textures, env map and vertices. Metric: forward+backward path samples per second (one path
 sample = one pixel sample of one view), for the batched launch (every view in one
 graph-captured wavefront: the headline value), the plain per-view wavefront launch and the
-single persistent kernel; Mrays/s alongside.
+single persistent kernel; Mrays/s alongside. The same step with the FULL-mode adjoint
+(gradients through every vertex) is reported as `full_adjoint` when its tape fits.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config3|config5|config2]
   python bench.py --impl reference ...   (the CPU oracle on the host cores, bounded sample)
@@ -203,6 +204,7 @@ def main():
     ap.add_argument("--views", type=int, default=None, help="override the view / scene count (smaller runs)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-launch arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-full", action="store_true", help="skip the FULL-mode adjoint arm")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -236,7 +238,12 @@ def main():
     stream = torch.cuda.current_stream()
     scenes = [s.handle for s in gw.scenes]
     images = gw.new_images()
-    tape = gw.new_tape()
+    # one tape for every arm: FULL-mode size when it fits (a FULL tape also serves PRIMARY mode),
+    # leaving room for the wavefront queues and the workspace
+    full_bytes = M.mirres_tape_bytes_mode(gw.views, M.GRAD_FULL)
+    free_bytes, _ = torch.cuda.mem_get_info(dev)
+    want_full = (not args.no_full) and full_bytes + (24 << 30) < free_bytes
+    tape = gw.new_tape(M.GRAD_FULL if want_full else M.GRAD_PRIMARY)
     grads = gw.zero_grads()
     tuned = None
     if not args.block:
@@ -254,21 +261,22 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def step(launch, ev_render=None, ev_bwd=None):
+    def step(launch, ev_render=None, ev_bwd=None, grad_mode=0):
         for s in gw.scenes:
             M.mirres_bvh_build(s.handle)
         if ev_render is not None:
             ev_render[0].record()
         # the batched wavefront records stage events (graph event nodes) for the roofline
         M.mirres_render(gw.ctx, scenes, gw.views, gw.params(launch, block=args.block, blocks_per_sm=args.blocks_per_sm,
-                                                            flags=1 if launch == 1 else 0), images, tape)
+                                                            flags=1 if launch == 1 else 0, grad_mode=grad_mode),
+                        images, tape)
         if ev_render is not None:
             ev_render[1].record()
         for img, ref, d in zip(images, refs, d_images):
             M.mirres_l2_loss(img, ref, d, loss)
         if ev_bwd is not None:
             ev_bwd[0].record()
-        M.mirres_backward(gw.ctx, scenes, gw.views, gw.params(launch), d_images, tape, grads)
+        M.mirres_backward(gw.ctx, scenes, gw.views, gw.params(launch, grad_mode=grad_mode), d_images, tape, grads)
         if ev_bwd is not None:
             ev_bwd[1].record()
 
@@ -278,10 +286,10 @@ def main():
                 t.zero_()
         loss.zero_()
 
-    def timed(launch, steps, warmup):
+    def timed(launch, steps, warmup, grad_mode=0):
         for _ in range(warmup):
             zero()
-            step(launch)
+            step(launch, grad_mode=grad_mode)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -293,7 +301,7 @@ def main():
             flush.fill_(float(i))  # evict L2 between timed steps (outside the timed window)
             zero()
             evs[i][0].record()
-            step(launch, evr[i], evg[i])
+            step(launch, evr[i], evg[i], grad_mode=grad_mode)
             evs[i][1].record()
         torch.cuda.synchronize()
         barrier()
@@ -364,6 +372,17 @@ def main():
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
+    # FULL-mode adjoint (gradients through every vertex): the same step with grad_mode 1
+    full = None
+    if want_full:
+        ms_f, msr_f, _, launches_f, _ = timed(1, args.steps, args.warmup, grad_mode=M.GRAD_FULL)
+        ms_f = max_over_ranks(ms_f)
+        full = {"value": world * samples * args.steps / (ms_f / 1e3), "ms_per_step": ms_f / args.steps,
+                "render_ms_per_step": msr_f / args.steps, "backward_ms_per_step": timed.backward_ms,
+                "tape_bytes": full_bytes, "gpu_launches": launches_f}
+    elif not args.no_full:
+        full = {"skipped": f"FULL tape of {full_bytes / 2**30:.1f} GiB does not fit next to the workload"}
+
     value = world * samples * args.steps / (ms_b / 1e3)
     mrays = world * rays_b / (ms_b / 1e3) / 1e6
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -378,6 +397,7 @@ def main():
                         "stage_launches_per_render": {k: v[1] for k, v in stages.items()}},
             "plain": plain,
             "persistent": persistent,
+            "full_adjoint": full,
             "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
             "counters_per_step": {"primary_rays": cnt_b[0] // args.steps, "continuation_rays": cnt_b[1] // args.steps,
                                   "shadow_rays": cnt_b[2] // args.steps, "ris_candidates": cnt_b[5] // args.steps,

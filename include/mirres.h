@@ -91,6 +91,10 @@ typedef struct {
  *            P = 0 camera jitter, 1 RIS candidate j, 2 continuation. v is the view's index
  *            in the call's view array (< 65536); bounces < 256.
  *   grad_mode 0 = PRIMARY (the paper: gradients of indirect rays detached, Sec. 4.2)
+ *            1 = FULL: also the gradients through every later vertex (the part Sec. 4.2
+ *                detaches and Appendix C names as missing); the forward then records every
+ *                vertex on the tape (mirres_tape_bytes_mode) and mirres_backward walks them;
+ *                at most MIRRES_FULL_MAX_BOUNCES bounces per view
  *   launch   0 = plain: per-view wavefront launches (ray generation, closest hit with hit
  *                 compaction, shade + RIS + next-bounce queue, shadow rays, resolve);
  *            1 = batched wavefront: every view of every scene flattened into waves of up to
@@ -150,6 +154,13 @@ mirres_status mirres_bvh_refit(mirres_scene* scene, void* stream);
 
 /* Tape bytes per path sample: 17 32-bit words, stored as 17 arrays over the samples. */
 #define MIRRES_TAPE_BYTES_PER_SAMPLE 68
+/* FULL mode (grad_mode 1) adds, per sample, one record of 9 words for each vertex b = 1 ..
+ * max_bounces - 1 (max over the call's views), stored as arrays after the 17 primary words:
+ * word ((b - 1) * 9 + w) of sample g at index 17 * n + ((b - 1) * 9 + w) * n + g, n = samples;
+ * w: 0 hit triangle (-1: the path never reached vertex b), 1-2 barycentrics (u, v), 3 selected
+ * RIS candidate (-1: none), 4 V * W, 5-7 continuation direction, 8 its pdf (0: the path ended). */
+#define MIRRES_TAPE_BYTES_PER_VERTEX 36
+#define MIRRES_FULL_MAX_BOUNCES 16
 
 /* Bytes of tape needed for these views: MIRRES_TAPE_BYTES_PER_SAMPLE per path sample (sum of
  * width*height*spp). The tape records, per sample (word: content): 0 primary triangle (-1 if
@@ -160,6 +171,11 @@ mirres_status mirres_bvh_refit(mirres_scene* scene, void* stream);
  * p_ind. Words 9-16 are meaningful only where word 1 >= 0, resp. L_ind != 0. The adjoint
  * replays the primary vertex from it and the camera's random numbers; no sample is re-drawn. */
 size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views);
+
+/* Tape bytes for a gradient mode: mirres_tape_bytes for grad_mode 0 (PRIMARY); for 1 (FULL)
+ * MIRRES_TAPE_BYTES_PER_SAMPLE + MIRRES_TAPE_BYTES_PER_VERTEX * (max bounces - 1) per sample.
+ * 0 for invalid arguments. A FULL-mode tape also serves PRIMARY-mode calls. */
+size_t mirres_tape_bytes_mode(const mirres_view* views, int32_t n_views, int32_t grad_mode);
 
 /* Forward render (Eq. pbr_render with Eq. incident: direct light by RIS over ris_m env
  * candidates streamed through a weighted reservoir, Eq. restir and Appendix A; indirect light

@@ -165,7 +165,7 @@ static mirres_status check_params(const mirres_params* p)
 {
     if (!p) return arg_error("params is NULL");
     if (p->ris_m < 1) return arg_error("ris_m must be >= 1");
-    if (p->grad_mode != 0) return arg_error("grad_mode: only 0 (PRIMARY) is implemented");
+    if (p->grad_mode != 0 && p->grad_mode != 1) return arg_error("grad_mode must be 0 (PRIMARY) or 1 (FULL)");
     if (p->launch < 0 || p->launch > 2)
         return arg_error("launch must be 0 (plain), 1 (batched wavefront) or 2 (persistent kernel)");
     if (p->block != 0 && (p->block < 32 || p->block > 1024 || p->block % 32))
@@ -283,22 +283,51 @@ extern "C" mirres_status mirres_bvh_refit(mirres_scene* s, void* stream)
     return MIRRES_OK;
 }
 
-extern "C" size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views)
+// FULL mode records vertices 1 .. max_bounces - 1 of every sample after the primary words
+static int full_vertices(const mirres_view* views, int32_t n_views, int32_t grad_mode)
+{
+    if (grad_mode != 1) return 0;
+    int max_b = 1;
+    for (int i = 0; i < n_views; ++i) max_b = std::max(max_b, views[i].bounces);
+    return max_b - 1;
+}
+
+static uint64_t tape_bytes_per_sample(int nvx)
+{
+    return (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE + (uint64_t)MIRRES_TAPE_BYTES_PER_VERTEX * (uint64_t)nvx;
+}
+
+extern "C" size_t mirres_tape_bytes_mode(const mirres_view* views, int32_t n_views, int32_t grad_mode)
 {
     if (!views || n_views < 1) return 0;
     uint64_t n = 0;
     for (int i = 0; i < n_views; ++i)
         n += (uint64_t)std::max(views[i].width, 0) * (uint64_t)std::max(views[i].height, 0) *
              (uint64_t)std::max(views[i].spp, 0);
-    return (size_t)((uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * n);
+    return (size_t)(tape_bytes_per_sample(full_vertices(views, n_views, grad_mode)) * n);
+}
+
+extern "C" size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views)
+{
+    return mirres_tape_bytes_mode(views, n_views, 0);
+}
+
+// FULL mode walks at most MIRRES_FULL_MAX_BOUNCES vertices per path
+static mirres_status check_full(const mirres_params* p, const mirres_view* views, int32_t n_views)
+{
+    if (p->grad_mode != 1) return MIRRES_OK;
+    for (int i = 0; i < n_views; ++i)
+        if (views[i].bounces > MIRRES_FULL_MAX_BOUNCES)
+            return arg_error("grad_mode 1 (FULL) supports at most " + std::to_string(MIRRES_FULL_MAX_BOUNCES) +
+                             " bounces (view " + std::to_string(i) + ")");
+    return MIRRES_OK;
 }
 
 // ---- forward ---------------------------------------------------------------------------------
 static Rng make_rng(const mirres_params* p)
 {
     Rng r;
-    r.k0 = p->seed_lo;
-    r.k1 = p->seed_hi;
+    r.set(p->seed_lo, p->seed_hi);
     return r;
 }
 
@@ -311,7 +340,7 @@ static const uint64_t kWave = 1ull << MR_WAVE_LOG2;
 
 struct GraphKey {
     uint64_t total, total_pix, wave;
-    int32_t n_views, n_scenes, max_b, M, sms, flags;
+    int32_t n_views, n_scenes, max_b, M, sms, flags, nvx;
     uint32_t k0, k1;
     const void* tape;
     const void* ws;
@@ -339,7 +368,7 @@ static mirres_status stage_events(mirres_context* ctx, int pairs)
 
 static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev>& sdev,
                                  const std::vector<ViewDev>& vdev, uint64_t total, float* const* images, void* tape,
-                                 int M, Rng rng, int flags, cudaStream_t st)
+                                 int M, Rng rng, int flags, int nvx, cudaStream_t st)
 {
     const int n_views = (int)vdev.size(), n_scenes = (int)sdev.size();
     int max_b = 1;
@@ -352,7 +381,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     }
     const uint64_t wave = std::min<uint64_t>(total, kWave);
     Carver plan(nullptr);
-    plan.take<char>(tape ? 0 : (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total);
+    plan.take<char>(tape ? 0 : tape_bytes_per_sample(nvx) * total);
     plan.take<ViewDev>((size_t)n_views);
     plan.take<SceneDev>((size_t)n_scenes);
     plan.take<float*>((size_t)n_views);
@@ -361,7 +390,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     plan.take<float4>(16ull * wave);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
-    void* internal_tape = cv.take<char>(tape ? 0 : (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total);
+    void* internal_tape = cv.take<char>(tape ? 0 : tape_bytes_per_sample(nvx) * total);
     void* tp = tape ? tape : internal_tape;
     ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
     SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
@@ -388,8 +417,9 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     key.M = M;
     key.sms = ctx->sm_count;
     key.flags = flags & 1;
-    key.k0 = rng.k0;
-    key.k1 = rng.k1;
+    key.nvx = nvx;
+    key.k0 = rng.rk0[0];
+    key.k1 = rng.rk1[0];
     key.tape = tp;
     key.ws = ctx->ws.ptr;
     key.ws_bytes = ctx->ws.bytes;
@@ -405,7 +435,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         MR_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
         mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave, qa, qb, hq, sq, qc, tp, ctx->counters,
                        d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
-                       (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr);
+                       (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr, nvx);
         ctx->stage_pairs = (flags & 1) ? pairs : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -441,7 +471,10 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     if (!images) return arg_error("images is NULL");
     for (int i = 0; i < n_views; ++i)
         if (!images[i]) return arg_error("images[" + std::to_string(i) + "] is NULL");
-    if (tape && tape_bytes < (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total) return arg_error("tape_bytes is smaller than mirres_tape_bytes(views)");
+    MR_TRY(check_full(params, views, n_views));
+    const int nvx = full_vertices(views, n_views, params->grad_mode);
+    if (tape && tape_bytes < tape_bytes_per_sample(nvx) * total)
+        return arg_error("tape_bytes is smaller than mirres_tape_bytes_mode(views, grad_mode)");
     if (tape && (reinterpret_cast<uintptr_t>(tape) & 15)) return arg_error("tape must be 16-byte aligned");
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
@@ -450,13 +483,13 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     const int M = params->ris_m;
     const int sms = ctx->sm_count;
 
-    if (params->launch == 1) return render_wave(ctx, sdev, vdev, total, images, tape, M, rng, params->flags, st);
+    if (params->launch == 1) return render_wave(ctx, sdev, vdev, total, images, tape, M, rng, params->flags, nvx, st);
 
     // workspace layout
     const bool batched = params->launch == 2;
     const uint32_t chunk = (uint32_t)std::min<uint64_t>(max_view, kChunk);
     Carver plan(nullptr);
-    plan.take<char>(tape ? 0 : (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total);
+    plan.take<char>(tape ? 0 : tape_bytes_per_sample(nvx) * total);
     plan.take<ViewDev>((size_t)n_views);
     plan.take<SceneDev>((size_t)n_scenes);
     plan.take<float*>((size_t)n_views);
@@ -465,7 +498,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     if (!batched) plan.take<float4>(16ull * chunk);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
-    void* internal_tape = cv.take<char>(tape ? 0 : (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total);
+    void* internal_tape = cv.take<char>(tape ? 0 : tape_bytes_per_sample(nvx) * total);
     void* tp = tape ? tape : internal_tape;
     ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
     SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
@@ -493,7 +526,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
         }
         const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy_v(var);
         MR_CUDA(mr_launch_persistent_v(var, d_scenes, d_views, n_views, total, rng, M, d_work, chunk_w, tp,
-                                       ctx->counters, per_sm * sms, st));
+                                       ctx->counters, per_sm * sms, st, nvx));
         mr_launch_resolve_all(d_views, n_views, d_pixoff, tp_pix, d_images, tp, total, sms, st);
         MR_CUDA(cudaGetLastError());
         ctx->host_launches += 2;
@@ -513,15 +546,15 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
             const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, nv - first);
             unsigned int* qc = ctx->queue_cnt;
             MR_CUDA(cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (3 * v.bounces + 3), st));
-            mr_launch_raygen(v, rng, (uint32_t)first, n, qa, tp, total, sms, st);
+            mr_launch_raygen(v, rng, (uint32_t)first, n, qa, tp, total, sms, st, nvx);
             QueueDev cur = qa, nxt = qb;
             for (int b = 0; b < v.bounces; ++b) {
                 // ray queue of bounce b: the raygen output, then the continuations of bounce b-1
                 const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
                 mr_launch_closest(s, v, b, cur, cnt_in, n, n, hq, qc + 3 * b, tp, total, sms, st);
                 mr_launch_shade(s, v, rng, b, M, hq, qc + 3 * b, n, nxt, qc + 3 * b + 1, sq, qc + 3 * b + 2, tp,
-                                total, ctx->counters, sms, st);
-                mr_launch_shadow(s, v, b, sq, qc + 3 * b + 2, n, tp, total, sms, st);
+                                total, ctx->counters, sms, st, nvx);
+                mr_launch_shadow(s, v, b, sq, qc + 3 * b + 2, n, tp, total, sms, st, nvx);
                 std::swap(cur, nxt);
             }
             mr_launch_account(ctx->counters, qc, v.bounces, n, st);
@@ -666,7 +699,10 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
     for (int i = 0; i < n_views; ++i)
         if (!d_images[i]) return arg_error("d_images[" + std::to_string(i) + "] is NULL");
     if (!tape) return arg_error("mirres_backward needs the tape written by mirres_render");
-    if (tape_bytes < (uint64_t)MIRRES_TAPE_BYTES_PER_SAMPLE * total) return arg_error("tape_bytes is smaller than mirres_tape_bytes(views)");
+    MR_TRY(check_full(params, views, n_views));
+    const int nvx = full_vertices(views, n_views, params->grad_mode);
+    if (tape_bytes < tape_bytes_per_sample(nvx) * total)
+        return arg_error("tape_bytes is smaller than mirres_tape_bytes_mode(views, grad_mode)");
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
     ctx->last_stream = st;
@@ -689,7 +725,7 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
     MR_CUDA(cudaMemcpyAsync(d_dimg, d_images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_grads, gdev.data(), sizeof(GradDev) * gdev.size(), cudaMemcpyHostToDevice, st));
     mr_launch_backward(d_scenes, d_views, n_views, total, make_rng(params), d_dimg, d_grads, tape, ctx->counters,
-                       ctx->sm_count, st);
+                       ctx->sm_count, st, nvx);
     MR_CUDA(cudaGetLastError());
     ctx->host_launches += 1;
     return MIRRES_OK;

@@ -93,27 +93,34 @@ __device__ __forceinline__ float3 add_rn(float3 a, float3 b)
 // ---------------------------------------------------------------------------------------
 // Philox4x32-10 counter-based generator (Salmon et al., SC'11)
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
 enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2 };
 
+// The key schedule (k += Weyl constants each round) depends on the seed only, so the ten round
+// keys are computed once on the host and travel in the kernel parameters, where each round
+// reads its keys as constant operands.
 struct Rng {
-    uint32_t k0, k1;
+    uint32_t rk0[10], rk1[10];
+    __host__ __device__ void set(uint32_t k0, uint32_t k1)
+    {
+        for (int i = 0; i < 10; ++i) {
+            rk0[i] = k0 + (uint32_t)i * 0x9E3779B9u;
+            rk1[i] = k1 + (uint32_t)i * 0xBB67AE85u;
+        }
+    }
+    __device__ __forceinline__ uint4 philox(uint4 c) const
+    {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) {
+            const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+            const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+            c = make_uint4(hi1 ^ c.y ^ rk0[i], lo1, hi0 ^ c.w ^ rk1[i], lo0);
+        }
+        return c;
+    }
     __device__ __forceinline__ uint4 draw(uint32_t pixel, uint32_t sample, uint32_t view, uint32_t bounce,
                                           uint32_t purpose, uint32_t j) const
     {
-        return philox(make_uint4(pixel, sample, (view << 16) | (bounce << 8) | purpose, j), k0, k1);
+        return philox(make_uint4(pixel, sample, (view << 16) | (bounce << 8) | purpose, j));
     }
 };
 

@@ -74,6 +74,8 @@ extern "C" mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int3
         return fail(MIRRES_ERR_ARG, "n_views = " + std::to_string(n_views) + " exceeds the static maximum of " +
                                         std::to_string(kMaxViews));
     if (!params || params->ris_m < 1) return fail(MIRRES_ERR_ARG, "params missing or ris_m < 1");
+    if (params->grad_mode != 0)
+        return fail(MIRRES_ERR_ARG, "mirres_render_noalloc writes the PRIMARY-mode tape only (grad_mode 0)");
     if (params->block != 0 && (params->block < 32 || params->block > 1024 || params->block % 32))
         return fail(MIRRES_ERR_ARG, "block must be 0 or a multiple of 32 in [32, 1024]");
     if (params->blocks_per_sm < 0) return fail(MIRRES_ERR_ARG, "blocks_per_sm must be >= 0");
@@ -133,8 +135,7 @@ extern "C" mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int3
     MR_CUDA(cudaMemcpyAsync(d_pixoff, g_pixoff, sizeof(uint64_t) * (size_t)n_views, cudaMemcpyHostToDevice, s));
     MR_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), s));  // the previous call left it spent
     Rng rng;
-    rng.k0 = params->seed_lo;
-    rng.k1 = params->seed_hi;
+    rng.set(params->seed_lo, params->seed_hi);
     const int block = params->block ? params->block : 128;
     const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy(block);
     MR_CUDA(mr_launch_persistent(d_scenes, d_views, n_views, total, rng, params->ris_m, d_work, 32u * 8u, tape,

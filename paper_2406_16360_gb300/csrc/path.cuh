@@ -27,11 +27,29 @@ struct TapeDev {
     float* y[3];     // its direction (valid when cand >= 0)
     float* wc[3];    // continuation direction at the primary vertex (valid when L_ind != 0)
     float* pind;     // its mixture pdf (valid when L_ind != 0)
+    // FULL-mode vertex records of vertices 1 .. nvx, VX_WORDS words each, after the primary
+    // words: vx[((b - 1) * VX_WORDS + w) * n + g]; nvx = 0 in PRIMARY mode
+    uint32_t* vx;
+    int nvx;
+    uint64_t n;
 };
 
-__device__ __forceinline__ TapeDev tape_of(void* base, uint64_t n)
+// words of a FULL-mode vertex record: hit triangle (-1: the path never reached the vertex),
+// barycentrics, selected RIS candidate (-1: none), V * W, continuation direction and pdf
+// (0: the path ended here)
+enum { VX_TRI = 0, VX_U, VX_V, VX_CAND, VX_WV, VX_WC, VX_P = VX_WC + 3, VX_WORDS };
+
+__device__ __forceinline__ uint32_t* vx_at(const TapeDev& t, int b, int w, uint64_t g)
+{
+    return t.vx + ((uint64_t)(b - 1) * VX_WORDS + (uint64_t)w) * t.n + g;
+}
+
+__device__ __forceinline__ TapeDev tape_of(void* base, uint64_t n, int nvx = 0)
 {
     TapeDev t;
+    t.n = n;
+    t.nvx = nvx;
+    t.vx = reinterpret_cast<uint32_t*>(base) + (uint64_t)TAPE_WORDS * n;
     uint32_t* w = reinterpret_cast<uint32_t*>(base);
     t.tri = reinterpret_cast<int32_t*>(w);
     t.cand = reinterpret_cast<int32_t*>(w + n);
@@ -60,6 +78,33 @@ struct VertexOut {
     int cand, ytex;
     float W, c_pind;
 };
+
+// FULL mode: no later vertex reached yet (written when the sample starts)
+__device__ __forceinline__ void tape_vx_init(const TapeDev& tp, uint64_t g)
+{
+    for (int b = 1; b <= tp.nvx; ++b) *vx_at(tp, b, VX_TRI, g) = 0xFFFFFFFFu;
+}
+
+// FULL mode: the record of vertex b >= 1 (V * W is cleared later if the shadow ray is blocked)
+__device__ __forceinline__ void tape_vx_record(const TapeDev& tp, uint64_t g, int b, const Hit& h,
+                                               const VertexOut& out)
+{
+    if (b < 1 || b > tp.nvx) return;
+    *vx_at(tp, b, VX_TRI, g) = (uint32_t)h.tri;
+    *vx_at(tp, b, VX_U, g) = __float_as_uint(h.u);
+    *vx_at(tp, b, VX_V, g) = __float_as_uint(h.v);
+    *vx_at(tp, b, VX_CAND, g) = (uint32_t)out.cand;
+    *vx_at(tp, b, VX_WV, g) = __float_as_uint(out.W);
+    *vx_at(tp, b, VX_WC, g) = __float_as_uint(out.c_d.x);
+    *vx_at(tp, b, VX_WC + 1, g) = __float_as_uint(out.c_d.y);
+    *vx_at(tp, b, VX_WC + 2, g) = __float_as_uint(out.c_d.z);
+    *vx_at(tp, b, VX_P, g) = __float_as_uint(out.c_pind);
+}
+
+__device__ __forceinline__ void tape_vx_occluded(const TapeDev& tp, uint64_t g, int b)
+{
+    if (b >= 1 && b <= tp.nvx) *vx_at(tp, b, VX_WV, g) = 0u;
+}
 
 // the directions the primary vertex drew, for the adjoint's replay (written at bounce 0)
 __device__ __forceinline__ void tape_directions(const TapeDev& tp, uint64_t g, const VertexOut& out)
@@ -148,11 +193,9 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
             out.shadow = true;
             out.sh_o = sh.x;
             out.sh_d = ysel;
-            if (b == 0) {
-                out.cand = sel;
-                out.ytex = ytex;
-                out.W = W;
-            }
+            out.cand = sel;
+            out.ytex = ytex;
+            out.W = W;
         }
     }
     if (b < B - 1) {

@@ -13,9 +13,9 @@ namespace {
 // wavefront (plain) kernels: one view chunk at a time
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_raygen(ViewDev v, Rng rng, uint32_t first, uint32_t n, QueueDev q,
-                                                void* tape, uint64_t ntot)
+                                                void* tape, uint64_t ntot, int nvx)
 {
-    const TapeDev tp = tape_of(tape, ntot);
+    const TapeDev tp = tape_of(tape, ntot, nvx);
     const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t sid = first + i;
@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256) k_raygen(ViewDev v, Rng rng, uint32_t fir
             tp.lind[k][g] = 0.0f;
             tp.rad[k][g] = 0.0f;
         }
+        tape_vx_init(tp, g);
     }
 }
 
@@ -87,9 +88,9 @@ __global__ void __launch_bounds__(256) k_closest(SceneDev s, ViewDev v, int b, Q
 __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_shade(SceneDev s, ViewDev v, Rng rng, int b, int M, QueueDev hq,
                                                const unsigned int* count_hit, QueueDev qout,
                                                unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
-                                               void* tape, uint64_t ntot, unsigned long long* counters)
+                                               void* tape, uint64_t ntot, int nvx, unsigned long long* counters)
 {
-    const TapeDev tp = tape_of(tape, ntot);
+    const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count_hit;
     unsigned long long n_cand = 0;
     const int env_ok = *s.env_ok_dev;
@@ -123,6 +124,8 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_shade(SceneDev s, ViewDe
                 tp.cand[g] = out.cand;
                 tp.wv[g] = out.W;
                 tape_directions(tp, g, out);
+            } else {
+                tape_vx_record(tp, g, b, h, out);
             }
         }
         const unsigned int ss = warp_append(out.shadow, count_sh);
@@ -146,10 +149,10 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_shade(SceneDev s, ViewDe
 
 // shadow rays: any hit; unoccluded rays add their contribution to the sample
 __global__ void __launch_bounds__(256) k_shadow(SceneDev s, ViewDev v, int b, ShadowDev sq,
-                                                const unsigned int* count, void* tape, uint64_t ntot)
+                                                const unsigned int* count, void* tape, uint64_t ntot, int nvx)
 {
     extern __shared__ uint32_t sstk[];
-    const TapeDev tp = tape_of(tape, ntot);
+    const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count;
     const float tmin = *s.tmin_dev;
     for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -169,6 +172,8 @@ __global__ void __launch_bounds__(256) k_shadow(SceneDev s, ViewDev v, int b, Sh
             }
         } else if (b == 0) {
             tp.wv[g] = 0.0f;
+        } else {
+            tape_vx_occluded(tp, g, b);
         }
     }
 }
@@ -198,10 +203,10 @@ __global__ void __launch_bounds__(256) k_resolve(ViewDev v, const void* tape, ui
 __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ scenes,
                                                 const ViewDev* __restrict__ views, int n_views, uint64_t total,
                                                 Rng rng, int M, unsigned long long* work, uint32_t chunk,
-                                                void* tape, unsigned long long* counters)
+                                                void* tape, int nvx, unsigned long long* counters)
 {
     extern __shared__ uint32_t sstk[];
-    const TapeDev tp = tape_of(tape, total);
+    const TapeDev tp = tape_of(tape, total, nvx);
     const int lane = lane_id();
     uint32_t* mystk = sstk + threadIdx.x;
     const int sstride = blockDim.x;
@@ -261,6 +266,7 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
                     wv0 = 0.0f;
                     env_ok = *sp->env_ok_dev;
                     tmin = *sp->tmin_dev;
+                    tape_vx_init(tp, g);
                     has_path = true;
                     has_hit = false;
                     ++n_prim;
@@ -311,6 +317,8 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
                 cand0 = out.cand;
                 wv0 = out.W;
                 tape_directions(tp, g, out);
+            } else {
+                tape_vx_record(tp, g, b, h, out);
             }
         }
         if (out.shadow) {
@@ -322,6 +330,8 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
                 if (b >= 1) lind = add_rn(lind, out.add_lind);
             } else if (b == 0) {
                 wv0 = 0.0f;
+            } else {
+                tape_vx_occluded(tp, g, b);
             }
         }
         if (has_hit) {
@@ -368,9 +378,10 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
 template <int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB)
     k_persistent(const SceneDev* __restrict__ scenes, const ViewDev* __restrict__ views, int n_views, uint64_t total,
-                 Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape, unsigned long long* counters)
+                 Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape, int nvx,
+                 unsigned long long* counters)
 {
-    persistent_body(scenes, views, n_views, total, rng, M, work, chunk, tape, counters);
+    persistent_body(scenes, views, n_views, total, rng, M, work, chunk, tape, nvx, counters);
 }
 
 // resolve every view of a batch in one launch: one thread per pixel over all views
@@ -516,13 +527,148 @@ struct EmitVert {
     }
 };
 
-__global__ void __launch_bounds__(256, MR_BWD_MINB) k_backward(const SceneDev* __restrict__ scenes,
-                                                  const ViewDev* __restrict__ views, int n_views, uint64_t total,
-                                                  Rng rng, const float* const* __restrict__ d_images,
-                                                  const GradDev* __restrict__ grads, const void* tape,
-                                                  unsigned long long* counters)
+// vertices per path the FULL-mode adjoint walks (primary included)
+#define MR_FULL_MAXV 16
+static_assert(MR_FULL_MAXV == MIRRES_FULL_MAX_BOUNCES, "FULL-mode vertex limit");
+
+// FULL mode, forward pass over the vertices b >= 1 of one sample (the gradients of indirect
+// rays, which the paper detaches in Sec. 4.2 and names as missing in Appendix C): from the
+// tape records, the throughput beta_b into each vertex, its direct light V W L_env(y) f_r(y)
+// and its continuation factor f_r(wc) / p_ind. Returns the number of vertices (primary
+// included). beta = throughput into vertex 1, d = the primary continuation direction.
+__device__ __forceinline__ int full_forward(const SceneDev& s, const Rng& rng, const TapeDev& tp, uint64_t g,
+                                            uint32_t pixel, uint32_t smp, uint32_t view, int bounces, float3 beta,
+                                            float3 d, float3* vbeta, float3* vdir, float3* vfcp)
 {
-    const TapeDev tp = tape_of(const_cast<void*>(tape), total);
+    int nv = 1;
+    const int last = min(min(bounces - 1, tp.nvx), MR_FULL_MAXV - 1);
+    for (int b = 1; b <= last; ++b) {
+        const int tri = (int)*vx_at(tp, b, VX_TRI, g);
+        if (tri < 0) break;
+        Shade sh;
+        shade_at(s, tri, __uint_as_float(*vx_at(tp, b, VX_U, g)), __uint_as_float(*vx_at(tp, b, VX_V, g)), d, sh);
+        const float3 wo = f3(-d.x, -d.y, -d.z);
+        float3 dir = f3(0.f, 0.f, 0.f), fcp = f3(0.f, 0.f, 0.f);
+        const int cand = (int)*vx_at(tp, b, VX_CAND, g);
+        const float wv = __uint_as_float(*vx_at(tp, b, VX_WV, g));
+        if (cand >= 0 && wv != 0.0f) {
+            const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)cand);
+            float3 y;
+            int ytex;
+            env_candidate(s, x.x, x.y, x.w, y, ytex);
+            const float3 fy = brdf_cos(sh.n, wo, y, sh.m);
+            const float4 L = __ldg(s.env_texel + ytex);
+            dir = f3(wv * L.x * fy.x, wv * L.y * fy.y, wv * L.z * fy.z);
+        }
+        const float p = __uint_as_float(*vx_at(tp, b, VX_P, g));
+        const float3 wc = f3(__uint_as_float(*vx_at(tp, b, VX_WC, g)), __uint_as_float(*vx_at(tp, b, VX_WC + 1, g)),
+                             __uint_as_float(*vx_at(tp, b, VX_WC + 2, g)));
+        if (p > 0.0f) {
+            const float3 fc = brdf_cos(sh.n, wo, wc, sh.m);
+            fcp = f3(fc.x / p, fc.y / p, fc.z / p);
+        }
+        vbeta[b] = beta;
+        vdir[b] = dir;
+        vfcp[b] = fcp;
+        beta = f3(beta.x * fcp.x, beta.y * fcp.y, beta.z * fcp.z);
+        d = wc;
+        nv = b + 1;
+        if (!(p > 0.0f)) break;
+    }
+    return nv;
+}
+
+// FULL mode, backward pass from the last vertex to vertex 1: with Lin_b the light arriving at
+// x_b along wc_b from the rest of the path (Lin = direct_{b+1} + f_r/p_{b+1} Lin_{b+1}), the
+// material at x_b receives beta_b [V W L_env(y) d f_r(y) + Lin_b / p_b d f_r(wc)] and the env
+// texel of y receives beta_b V W f_r(y), per channel and weighted by dL/dI. The hit point is
+// held fixed on its triangle (no geometric derivative beyond the primary vertex). Every lane
+// of the warp calls this (the scatters are warp-collective); lanes with nv < 2 only take part.
+__device__ __forceinline__ void full_backward(const SceneDev& s, const Rng& rng, const TapeDev& tp, uint64_t g,
+                                              uint32_t pixel, uint32_t smp, uint32_t view, int nv, float3 gI,
+                                              const float3* vbeta, const float3* vdir, const float3* vfcp,
+                                              const GradDev& gd, bool uniform_scene)
+{
+    const int wnv = __reduce_max_sync(MR_FULL, nv);
+    float3 lin = f3(0.f, 0.f, 0.f);
+    for (int b = wnv - 1; b >= 1; --b) {
+        int env_key = -1, tex_key[4] = {-1, -1, -1, -1};
+        float env_v[3] = {0.f, 0.f, 0.f};
+        float tex_v[4][5];
+        if (b < nv) {
+            const float3 d = (b == 1) ? f3(tp.wc[0][g], tp.wc[1][g], tp.wc[2][g])
+                                      : f3(__uint_as_float(*vx_at(tp, b - 1, VX_WC, g)),
+                                           __uint_as_float(*vx_at(tp, b - 1, VX_WC + 1, g)),
+                                           __uint_as_float(*vx_at(tp, b - 1, VX_WC + 2, g)));
+            const int tri = (int)*vx_at(tp, b, VX_TRI, g);
+            Shade sh;
+            shade_at(s, tri, __uint_as_float(*vx_at(tp, b, VX_U, g)), __uint_as_float(*vx_at(tp, b, VX_V, g)), d, sh);
+            const float3 wo = f3(-d.x, -d.y, -d.z);
+            const float3 bt = vbeta[b];
+            float gm[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const int cand = (int)*vx_at(tp, b, VX_CAND, g);
+            const float wv = __uint_as_float(*vx_at(tp, b, VX_WV, g));
+            if (cand >= 0 && wv != 0.0f) {
+                const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)cand);
+                float3 y;
+                int ytex;
+                env_candidate(s, x.x, x.y, x.w, y, ytex);
+                const float3 fy = brdf_cos(sh.n, wo, y, sh.m);
+                const float4 L = __ldg(s.env_texel + ytex);
+                env_key = ytex;
+                env_v[0] = gI.x * bt.x * wv * fy.x;
+                env_v[1] = gI.y * bt.y * wv * fy.y;
+                env_v[2] = gI.z * bt.z * wv * fy.z;
+                brdf_cos_adjoint(sh.n, wo, y, sh.m, f3(gI.x * bt.x * wv * L.x, gI.y * bt.y * wv * L.y, gI.z * bt.z * wv * L.z),
+                                 gm);
+            }
+            const float p = __uint_as_float(*vx_at(tp, b, VX_P, g));
+            if (p > 0.0f && (lin.x != 0.0f || lin.y != 0.0f || lin.z != 0.0f)) {
+                const float3 wc = f3(__uint_as_float(*vx_at(tp, b, VX_WC, g)),
+                                     __uint_as_float(*vx_at(tp, b, VX_WC + 1, g)),
+                                     __uint_as_float(*vx_at(tp, b, VX_WC + 2, g)));
+                brdf_cos_adjoint(sh.n, wo, wc, sh.m,
+                                 f3(gI.x * bt.x * lin.x / p, gI.y * bt.y * lin.y / p, gI.z * bt.z * lin.z / p), gm);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                tex_key[q] = sh.tp.idx[q];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) tex_v[q][c] = sh.tp.w[q] * gm[c];
+            }
+            const float3 dr = vdir[b], fp = vfcp[b];
+            lin = f3(dr.x + fp.x * lin.x, dr.y + fp.y * lin.y, dr.z + fp.z * lin.z);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 5; ++c) tex_v[q][c] = 0.0f;
+        }
+        if (uniform_scene) {
+            scatter_agg<3>(env_key, env_v, EmitEnv{gd.env});
+#pragma unroll
+            for (int q = 0; q < 4; ++q) scatter_agg<5>(tex_key[q], tex_v[q], EmitTex{gd.albedo, gd.rough, gd.metal});
+        } else {
+            if (env_key >= 0) EmitEnv{gd.env}(env_key, env_v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (tex_key[q] >= 0) EmitTex{gd.albedo, gd.rough, gd.metal}(tex_key[q], tex_v[q]);
+        }
+    }
+}
+
+// Adjoint of every sample. PRIMARY mode (FULL = false): the primary vertex, replayed from the
+// tape. FULL mode: in addition the vertices b >= 1 from their tape records (see
+// full_vertices below). All 32 lanes of a warp run the same number of rounds, so the
+// warp-collective scatters see every lane.
+template <bool FULL, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restrict__ scenes,
+                                                        const ViewDev* __restrict__ views, int n_views, uint64_t total,
+                                                        Rng rng, const float* const* __restrict__ d_images,
+                                                        const GradDev* __restrict__ grads, const void* tape, int nvx,
+                                                        unsigned long long* counters)
+{
+    const TapeDev tp = tape_of(const_cast<void*>(tape), total, nvx);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t rounds = (total + stride - 1) / stride;
     unsigned long long n_diff = 0;
@@ -534,6 +680,11 @@ __global__ void __launch_bounds__(256, MR_BWD_MINB) k_backward(const SceneDev* _
         float tex_v[4][5];
         float vert_v[3][3];
         int scene_id = 0;
+        // FULL mode: the later vertices' throughput, direct light and continuation factor
+        int nv = 0;
+        float3 gI_f = f3(0.f, 0.f, 0.f);
+        float3 vbeta[FULL ? MR_FULL_MAXV : 1], vdir[FULL ? MR_FULL_MAXV : 1], vfcp[FULL ? MR_FULL_MAXV : 1];
+        uint32_t f_pixel = 0, f_smp = 0, f_view = 0;
         if (live) {
             int vi;
             const ViewDev& v = view_of(views, n_views, g, vi);
@@ -586,6 +737,16 @@ __global__ void __launch_bounds__(256, MR_BWD_MINB) k_backward(const SceneDev* _
                         // the continuation the forward drew (L_ind != 0 implies it was taken)
                         const float3 wc = f3(tp.wc[0][g], tp.wc[1][g], tp.wc[2][g]);
                         const float pind = tp.pind[g];
+                        if (FULL && pind > 0.0f) {
+                            // throughput into vertex 1, then the later vertices' forward pass
+                            const float3 fc0 = brdf_cos(sh.n, wo, wc, sh.m);
+                            gI_f = gI;
+                            f_pixel = pixel;
+                            f_smp = smp;
+                            f_view = (uint32_t)v.index;
+                            nv = full_forward(s, rng, tp, g, pixel, smp, (uint32_t)v.index, v.bounces,
+                                              f3(fc0.x / pind, fc0.y / pind, fc0.z / pind), wc, vbeta, vdir, vfcp);
+                        }
                         if (pind > 0.0f)
                             brdf_cos_adjoint(sh.n, wo, wc, sh.m,
                                              f3(gI.x * li.x / pind, gI.y * li.y / pind, gI.z * li.z / pind), gm);
@@ -658,6 +819,11 @@ __global__ void __launch_bounds__(256, MR_BWD_MINB) k_backward(const SceneDev* _
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 if (vert_key[c] >= 0) EmitVert{gd.verts}(vert_key[c], vert_v[c]);
+        }
+        if (FULL) {
+            const SceneDev* sp = scenes + scene_id;
+            full_backward(*sp, rng, tp, g, f_pixel, f_smp, f_view, nv, gI_f, vbeta, vdir, vfcp, gd,
+                          same_scene == MR_FULL);
         }
     }
     for (int off = 16; off > 0; off >>= 1) n_diff += __shfl_xor_sync(MR_FULL, n_diff, off);
@@ -741,9 +907,9 @@ static unsigned grid_cap(uint64_t n, int block, int cap)
 static size_t stack_bytes(int block) { return sizeof(uint32_t) * MR_SSTACK * (size_t)block; }
 
 void mr_launch_raygen(const ViewDev& v, Rng rng, uint32_t first, uint32_t n, const QueueDev& q, void* tape,
-                      uint64_t ntot, int sms, cudaStream_t st)
+                      uint64_t ntot, int sms, cudaStream_t st, int nvx)
 {
-    k_raygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(v, rng, first, n, q, tape, ntot);
+    k_raygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(v, rng, first, n, q, tape, ntot, nvx);
 }
 
 void mr_launch_closest(const SceneDev& s, const ViewDev& v, int b, const QueueDev& q, const unsigned int* count,
@@ -757,16 +923,16 @@ void mr_launch_closest(const SceneDev& s, const ViewDev& v, int b, const QueueDe
 void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& hq,
                      const unsigned int* count_hit, uint64_t upper, const QueueDev& qout, unsigned int* count_out,
                      const ShadowDev& sq, unsigned int* count_sh, void* tape, uint64_t ntot,
-                     unsigned long long* counters, int sms, cudaStream_t st)
+                     unsigned long long* counters, int sms, cudaStream_t st, int nvx)
 {
     k_shade<<<grid_cap(upper, 256, sms * 8), 256, 0, st>>>(s, v, rng, b, M, hq, count_hit, qout, count_out, sq,
-                                                          count_sh, tape, ntot, counters);
+                                                          count_sh, tape, ntot, nvx, counters);
 }
 
 void mr_launch_shadow(const SceneDev& s, const ViewDev& v, int b, const ShadowDev& sq, const unsigned int* count,
-                      uint64_t upper, void* tape, uint64_t ntot, int sms, cudaStream_t st)
+                      uint64_t upper, void* tape, uint64_t ntot, int sms, cudaStream_t st, int nvx)
 {
-    k_shadow<<<grid_cap(upper, 256, sms * 8), 256, stack_bytes(256), st>>>(s, v, b, sq, count, tape, ntot);
+    k_shadow<<<grid_cap(upper, 256, sms * 8), 256, stack_bytes(256), st>>>(s, v, b, sq, count, tape, ntot, nvx);
 }
 
 void mr_launch_resolve(const ViewDev& v, const void* tape, uint64_t ntot, float* img, int sms, cudaStream_t st)
@@ -775,7 +941,7 @@ void mr_launch_resolve(const ViewDev& v, const void* tape, uint64_t ntot, float*
 }
 
 typedef void (*PersistentFn)(const SceneDev*, const ViewDev*, int, uint64_t, Rng, int, unsigned long long*, uint32_t,
-                             void*, unsigned long long*);
+                             void*, int, unsigned long long*);
 
 struct PersistentVariant {
     int block, minb;
@@ -830,23 +996,24 @@ int mr_persistent_occupancy_v(int v)
 
 cudaError_t mr_launch_persistent_v(int v, const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total,
                                    Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
-                                   unsigned long long* counters, int blocks, cudaStream_t st)
+                                   unsigned long long* counters, int blocks, cudaStream_t st, int nvx)
 {
     const PersistentVariant& pv = kVariants[v];
     const size_t smem = stack_bytes(pv.block);
     cudaError_t e = cudaFuncSetAttribute(pv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    pv.fn<<<blocks, pv.block, smem, st>>>(scenes, views, n_views, total, rng, M, work, chunk, tape, counters);
+    pv.fn<<<blocks, pv.block, smem, st>>>(scenes, views, n_views, total, rng, M, work, chunk, tape, nvx, counters);
     return cudaGetLastError();
 }
 
 // the launch used before variants existed: (block, blocks per SM) mapped to a variant
 cudaError_t mr_launch_persistent(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
                                  int M, unsigned long long* work, uint32_t chunk, void* tape,
-                                 unsigned long long* counters, int block, int blocks, cudaStream_t st)
+                                 unsigned long long* counters, int block, int blocks, cudaStream_t st, int nvx)
 {
     const int v = mr_persistent_pick(block, 0);
-    return mr_launch_persistent_v(v, scenes, views, n_views, total, rng, M, work, chunk, tape, counters, blocks, st);
+    return mr_launch_persistent_v(v, scenes, views, n_views, total, rng, M, work, chunk, tape, counters, blocks, st,
+                                  nvx);
 }
 
 int mr_persistent_occupancy(int block) { return mr_persistent_occupancy_v(mr_persistent_pick(block, 0)); }
@@ -860,10 +1027,14 @@ void mr_launch_resolve_all(const ViewDev* views, int n_views, const uint64_t* pi
 
 void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
                         const float* const* d_images, const GradDev* grads, const void* tape,
-                        unsigned long long* counters, int sms, cudaStream_t st)
+                        unsigned long long* counters, int sms, cudaStream_t st, int nvx)
 {
-    k_backward<<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng, d_images, grads,
-                                                             tape, counters);
+    if (nvx > 0)
+        k_backward<true, 2><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng,
+                                                                          d_images, grads, tape, nvx, counters);
+    else
+        k_backward<false, MR_BWD_MINB><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(
+            scenes, views, n_views, total, rng, d_images, grads, tape, 0, counters);
 }
 
 void mr_launch_account(unsigned long long* counters, const unsigned int* qcnt, int bounces, uint64_t primary,

@@ -28,22 +28,22 @@ struct GradDev {
 };
 
 void mr_launch_raygen(const ViewDev& v, Rng rng, uint32_t first, uint32_t n, const QueueDev& q, void* tape,
-                      uint64_t ntot, int sms, cudaStream_t st);
+                      uint64_t ntot, int sms, cudaStream_t st, int nvx = 0);
 void mr_launch_closest(const SceneDev& s, const ViewDev& v, int b, const QueueDev& q, const unsigned int* count,
                        unsigned int count_fixed, uint64_t upper, const QueueDev& hq, unsigned int* count_hit,
                        void* tape, uint64_t ntot, int sms, cudaStream_t st);
 void mr_launch_shade(const SceneDev& s, const ViewDev& v, Rng rng, int b, int M, const QueueDev& hq,
                      const unsigned int* count_hit, uint64_t upper, const QueueDev& qout, unsigned int* count_out,
                      const ShadowDev& sq, unsigned int* count_sh, void* tape, uint64_t ntot,
-                     unsigned long long* counters, int sms, cudaStream_t st);
+                     unsigned long long* counters, int sms, cudaStream_t st, int nvx = 0);
 void mr_launch_shadow(const SceneDev& s, const ViewDev& v, int b, const ShadowDev& sq, const unsigned int* count,
-                      uint64_t upper, void* tape, uint64_t ntot, int sms, cudaStream_t st);
+                      uint64_t upper, void* tape, uint64_t ntot, int sms, cudaStream_t st, int nvx = 0);
 void mr_launch_resolve(const ViewDev& v, const void* tape, uint64_t ntot, float* img, int sms, cudaStream_t st);
 void mr_launch_account(unsigned long long* counters, const unsigned int* qcnt, int bounces, uint64_t primary,
                        cudaStream_t st);
 cudaError_t mr_launch_persistent(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
                                  int M, unsigned long long* work, uint32_t chunk, void* tape,
-                                 unsigned long long* counters, int block, int blocks, cudaStream_t st);
+                                 unsigned long long* counters, int block, int blocks, cudaStream_t st, int nvx = 0);
 int mr_persistent_occupancy(int block);
 int mr_persistent_variants();
 void mr_persistent_variant_shape(int v, int* block, int* minb);
@@ -51,12 +51,13 @@ int mr_persistent_pick(int block, int per_sm);
 int mr_persistent_occupancy_v(int v);
 cudaError_t mr_launch_persistent_v(int v, const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total,
                                    Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
-                                   unsigned long long* counters, int blocks, cudaStream_t st);
+                                   unsigned long long* counters, int blocks, cudaStream_t st, int nvx = 0);
 void mr_launch_resolve_all(const ViewDev* views, int n_views, const uint64_t* pix_off, uint64_t total_pix,
                            float* const* images, const void* tape, uint64_t ntot, int sms, cudaStream_t st);
+// nvx = 0: PRIMARY-mode adjoint; nvx > 0: FULL mode over vertex records 1 .. nvx
 void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
                         const float* const* d_images, const GradDev* grads, const void* tape,
-                        unsigned long long* counters, int sms, cudaStream_t st);
+                        unsigned long long* counters, int sms, cudaStream_t st, int nvx = 0);
 void mr_launch_l2(const float* img, const float* ref, int64_t n, float* dimg, float* loss, int sms, cudaStream_t st);
 void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* skip, int64_t n, int any,
                           int32_t* hit_tri, float* hit_tuv, int sms, cudaStream_t st);
@@ -66,6 +67,6 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,
                     const ShadowDev& sq, unsigned int* qc, void* tape, unsigned long long* counters,
                     const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaStream_t st,
-                    cudaEvent_t* ev, int* kind);
+                    cudaEvent_t* ev, int* kind, int nvx);
 int mr_wave_launches(uint64_t total, uint64_t wave, int max_bounces);
 int mr_wave_stage_pairs(uint64_t total, uint64_t wave, int max_bounces);

@@ -10,9 +10,10 @@
 namespace {
 
 __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ views, int n_views, Rng rng,
-                                                 uint64_t first, uint32_t n, QueueDev q, void* tape, uint64_t ntot)
+                                                 uint64_t first, uint32_t n, QueueDev q, void* tape, uint64_t ntot,
+                                                 int nvx)
 {
-    const TapeDev tp = tape_of(tape, ntot);
+    const TapeDev tp = tape_of(tape, ntot, nvx);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint64_t g = first + i;
         int vi;
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ vie
             tp.lind[k][g] = 0.0f;
             tp.rad[k][g] = 0.0f;
         }
+        tape_vx_init(tp, g);
     }
 }
 
@@ -83,9 +85,9 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* _
                                                 const ViewDev* __restrict__ views, Rng rng, int b, int M,
                                                 QueueDev hq, const unsigned int* count_hit, QueueDev qout,
                                                 unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
-                                                void* tape, uint64_t ntot, unsigned long long* counters)
+                                                void* tape, uint64_t ntot, int nvx, unsigned long long* counters)
 {
-    const TapeDev tp = tape_of(tape, ntot);
+    const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count_hit;
     unsigned long long n_cand = 0;
     const unsigned int stride = gridDim.x * blockDim.x;
@@ -122,6 +124,8 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* _
                 tp.cand[g] = out.cand;
                 tp.wv[g] = out.W;
                 tape_directions(tp, g, out);
+            } else {
+                tape_vx_record(tp, g, b, h, out);
             }
         }
         const unsigned int ss = warp_append(out.shadow, count_sh);
@@ -145,10 +149,10 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* _
 
 __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ scenes,
                                                  const ViewDev* __restrict__ views, int b, ShadowDev sq,
-                                                 const unsigned int* count, void* tape, uint64_t ntot)
+                                                 const unsigned int* count, void* tape, uint64_t ntot, int nvx)
 {
     extern __shared__ uint32_t sstk[];
-    const TapeDev tp = tape_of(tape, ntot);
+    const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count;
     for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 a = sq.o[i], dd = sq.d[i], ad = sq.add[i];
@@ -170,6 +174,8 @@ __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ sc
             }
         } else if (b == 0) {
             tp.wv[g] = 0.0f;
+        } else {
+            tape_vx_occluded(tp, g, b);
         }
     }
 }
@@ -189,7 +195,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,
                     const ShadowDev& sq, unsigned int* qc, void* tape, unsigned long long* counters,
                     const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaStream_t st,
-                    cudaEvent_t* ev, int* kind)
+                    cudaEvent_t* ev, int* kind, int nvx)
 {
     const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
     int pair = 0;
@@ -203,7 +209,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         const uint32_t n = (uint32_t)(total - first < wave ? total - first : wave);
         cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (3 * max_bounces + 3), st);
         mark(3, true);
-        k_wraygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(views, n_views, rng, first, n, qa, tape, total);
+        k_wraygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(views, n_views, rng, first, n, qa, tape, total, nvx);
         mark(3, false);
         QueueDev cur = qa, nxt = qb;
         for (int b = 0; b < max_bounces; ++b) {
@@ -214,10 +220,12 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
             mark(0, false);
             mark(1, true);
             k_wshade<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, b, M, hq, qc + 3 * b, nxt,
-                                                                qc + 3 * b + 1, sq, qc + 3 * b + 2, tape, total, counters);
+                                                                qc + 3 * b + 1, sq, qc + 3 * b + 2, tape, total, nvx,
+                                                                counters);
             mark(1, false);
             mark(2, true);
-            k_wshadow<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(scenes, views, b, sq, qc + 3 * b + 2, tape, total);
+            k_wshadow<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(scenes, views, b, sq, qc + 3 * b + 2, tape, total,
+                                                                    nvx);
             mark(2, false);
             QueueDev t = cur;
             cur = nxt;

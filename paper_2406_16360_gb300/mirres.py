@@ -17,7 +17,8 @@ from . import build as _build
 
 __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_view", "make_params",
            "mirres_context_create", "mirres_context_destroy", "mirres_scene_create", "mirres_scene_destroy",
-           "mirres_bvh_build", "mirres_bvh_refit", "mirres_tape_bytes", "mirres_render", "mirres_render_noalloc",
+           "mirres_bvh_build", "mirres_bvh_refit", "mirres_tape_bytes", "mirres_tape_bytes_mode", "mirres_render",
+           "mirres_render_noalloc",
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
@@ -25,6 +26,9 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
 # limits of mirres_render_noalloc (include/mirres.h)
 MIRRES_TAPE_BYTES_PER_SAMPLE = 68  # 17 words per path sample, one array per word
 TAPE_WORDS = MIRRES_TAPE_BYTES_PER_SAMPLE // 4
+MIRRES_TAPE_BYTES_PER_VERTEX = 36  # FULL mode: 9 words per later vertex
+MIRRES_FULL_MAX_BOUNCES = 16
+GRAD_PRIMARY, GRAD_FULL = 0, 1
 MIRRES_NOALLOC_SCRATCH_BYTES = 512 * 1024
 MIRRES_NOALLOC_MAX_VIEWS = 4096
 MIRRES_NOALLOC_MAX_SCENES = 256
@@ -87,6 +91,7 @@ def lib():
                 "mirres_bvh_build": (st, [vp, vp]),
                 "mirres_bvh_refit": (st, [vp, vp]),
                 "mirres_tape_bytes": (sz, [C.POINTER(View), i32]),
+                "mirres_tape_bytes_mode": (sz, [C.POINTER(View), i32, i32]),
                 "mirres_render": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
                                        C.POINTER(vp), vp, sz, vp]),
                 "mirres_autotune": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params), vp, sz,
@@ -221,6 +226,11 @@ def mirres_bvh_refit(scene: Scene, stream=None):
 def mirres_tape_bytes(views) -> int:
     vs = _views(views)
     return int(lib().mirres_tape_bytes(vs, len(vs)))
+
+
+def mirres_tape_bytes_mode(views, grad_mode) -> int:
+    vs = _views(views)
+    return int(lib().mirres_tape_bytes_mode(vs, len(vs), int(grad_mode)))
 
 
 def mirres_render(ctx: Context, scenes, views, params: Params, images, tape=None, stream=None):

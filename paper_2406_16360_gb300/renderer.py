@@ -65,19 +65,21 @@ class GpuWorkload:
     def new_images(self):
         return [torch.empty((v.height, v.width, 3), device=self.device, dtype=torch.float32) for v in self.views]
 
-    def new_tape(self):
-        n = M.mirres_tape_bytes(self.views)
+    def new_tape(self, grad_mode=0):
+        n = M.mirres_tape_bytes_mode(self.views, grad_mode)
         return torch.empty(n // 4, device=self.device, dtype=torch.int32)
 
-    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0, flags=0):
+    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0, flags=0, grad_mode=0):
         s = self.workload.seed if seed is None else seed
-        return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm, flags=flags)
+        return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm, grad_mode=grad_mode, flags=flags)
 
-    def render(self, launch=0, images=None, tape=None, seed=None, block=0, blocks_per_sm=0, flags=0, stream=None):
+    def render(self, launch=0, images=None, tape=None, seed=None, block=0, blocks_per_sm=0, flags=0, stream=None,
+               grad_mode=0):
+        """Forward render; grad_mode 1 (FULL) also records every vertex for the FULL adjoint."""
         images = images if images is not None else self.new_images()
-        tape = tape if tape is not None else self.new_tape()
+        tape = tape if tape is not None else self.new_tape(grad_mode)
         M.mirres_render(self.ctx, [s.handle for s in self.scenes], self.views,
-                        self.params(launch, seed, block, blocks_per_sm, flags), images, tape, stream)
+                        self.params(launch, seed, block, blocks_per_sm, flags, grad_mode), images, tape, stream)
         return images, tape
 
     def tune_key(self):
@@ -117,10 +119,11 @@ class GpuWorkload:
             out.append({k: torch.zeros_like(t) for k, t in s.params().items()})
         return out
 
-    def backward(self, d_images, tape, grads=None, launch=0, seed=None, stream=None):
+    def backward(self, d_images, tape, grads=None, launch=0, seed=None, stream=None, grad_mode=0):
+        """Adjoint from the tape of a render with the same seed (and grad_mode)."""
         grads = grads if grads is not None else self.zero_grads()
-        M.mirres_backward(self.ctx, [s.handle for s in self.scenes], self.views, self.params(launch, seed),
-                          d_images, tape, grads, stream)
+        M.mirres_backward(self.ctx, [s.handle for s in self.scenes], self.views,
+                          self.params(launch, seed, grad_mode=grad_mode), d_images, tape, grads, stream)
         return grads
 
     def close(self):

@@ -51,7 +51,7 @@ def _forward_parity(gw, w, launch, pixels=None, max_flag_frac=0.08):
     return images, tape
 
 
-def _grad_parity(gw, w, tape, pixels_per_view=None, seed=7):
+def _grad_parity(gw, w, tape, pixels_per_view=None, seed=7, grad_mode=0):
     rng = np.random.Generator(np.random.PCG64(seed))
     d_imgs, plist = [], []
     for vi, v in enumerate(w.views):
@@ -69,7 +69,7 @@ def _grad_parity(gw, w, tape, pixels_per_view=None, seed=7):
             full[pix] = g
         d_imgs.append(torch.as_tensor(full.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda"))
         plist.append((pix, full if pix is None else full[pix]))
-    grads = gw.backward(d_imgs, tape)
+    grads = gw.backward(d_imgs, tape, grad_mode=grad_mode)
     torch.cuda.synchronize()
     for si, sc in enumerate(w.scenes):
         osc = O.OracleScene(sc)
@@ -80,7 +80,7 @@ def _grad_parity(gw, w, tape, pixels_per_view=None, seed=7):
             pix, g = plist[vi]
             gi = O.backward(osc, v, vi, w.ris_m, d_imgs[vi].double().cpu().numpy().reshape(-1, 3)[pix]
                             if pix is not None else d_imgs[vi].double().cpu().numpy().reshape(-1, 3),
-                            seed=w.seed, pixels=pix)
+                            seed=w.seed, pixels=pix, grad_mode=grad_mode)
             if acc is None:
                 acc = gi
             else:
@@ -330,4 +330,85 @@ def test_autotune_and_set_launch(M, ctx):
                               reft.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, n)[:2])
     M.mirres_set_launch(ctx, 0, 0, 0)
     for s in gw.scenes:
+        s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# FULL-mode adjoint (the gradients of the indirect rays at every vertex)
+# ---------------------------------------------------------------------------------------
+def _full_workload():
+    w = synth.config2(res=40, n_views=2, tex=32, spp=4, bounces=4)
+    for s in w.scenes:
+        s.env[:] = np.minimum(s.env, 80.0)  # keep the per-pixel check well conditioned
+    return w
+
+
+@pytest.mark.parametrize("launch", [0, 1, 2])
+def test_full_mode_gradients_match_oracle(M, ctx, launch):
+    """FULL-mode gradients from the tape of each launch mode against the oracle's FULL adjoint"""
+    w = _full_workload()
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=launch, grad_mode=1)
+    torch.cuda.synchronize()
+    _grad_parity(gw, w, tape, grad_mode=1)
+    for s in gw.scenes:
+        s.close()
+
+
+def test_full_mode_records_identical_across_launches(M, ctx):
+    w = _full_workload()
+    gw = _gw(ctx, w)
+    n = w.samples
+    nvx = max(v.bounces for v in w.views) - 1
+    words = TAPE_WORDS + 9 * nvx
+    tapes = []
+    for launch in (0, 1, 2):
+        _, t = gw.render(launch=launch, grad_mode=1)
+        torch.cuda.synchronize()
+        tapes.append(t.cpu().numpy().view(np.uint32).reshape(words, n))
+    a = tapes[0]
+    for b in tapes[1:]:
+        assert np.array_equal(a[:2], b[:2])
+        for k in range(nvx):
+            r0, r1 = a[TAPE_WORDS + 9 * k:TAPE_WORDS + 9 * (k + 1)], b[TAPE_WORDS + 9 * k:TAPE_WORDS + 9 * (k + 1)]
+            assert np.array_equal(r0[0], r1[0])  # the vertex reached, by the same triangle
+            live = r0[0].view(np.int32) >= 0
+            assert np.array_equal(r0[3][live], r1[3][live])  # the same RIS candidate
+            f0, f1 = r0.view(np.float32), r1.view(np.float32)
+            for wd in (1, 2, 5, 6, 7, 8):
+                assert np.all(np.abs(f0[wd][live] - f1[wd][live]) <= 2e-6 * np.maximum(np.abs(f0[wd][live]), 1.0))
+    # reached vertices thin out along the path, and every FULL record sits behind a hit
+    reach = [(a[TAPE_WORDS + 9 * k].view(np.int32) >= 0).sum() for k in range(nvx)]
+    assert reach[0] > 0 and all(x >= y for x, y in zip(reach, reach[1:]))
+    assert np.all(a[0].view(np.int32)[a[TAPE_WORDS].view(np.int32) >= 0] >= 0)
+    for s in gw.scenes:
+        s.close()
+
+
+def test_full_mode_edge_cases(M, ctx):
+    for name in ("single_triangle", "tiny_views", "empty_scene"):
+        w = _edge_workloads()[name]
+        gw = _gw(ctx, w)
+        images, tape = gw.render(launch=1, grad_mode=1)
+        _grad_parity(gw, w, tape, grad_mode=1)
+        for s in gw.scenes:
+            s.close()
+
+
+def test_full_mode_argument_checks(M, ctx):
+    w = synth.config1()
+    gw = _gw(ctx, w)
+    assert M.mirres_tape_bytes_mode(gw.views, 1) == M.mirres_tape_bytes(gw.views) + 36 * w.samples * (
+        w.views[0].bounces - 1)
+    images, tape = gw.render(launch=1)  # a PRIMARY-size tape is too small for FULL mode
+    with pytest.raises(M.MirresError):
+        gw.render(launch=1, tape=tape, grad_mode=1)
+    with pytest.raises(M.MirresError):
+        M.mirres_render_noalloc([s.handle for s in gw.scenes], gw.views, gw.params(1, grad_mode=1), images,
+                                gw.new_tape(1))
+    deep = synth.Workload("deep", w.scenes, [synth.View(w.views[0].K, w.views[0].c2w, 4, 4, 1, 17)], ris_m=2)
+    gd = _gw(ctx, deep)
+    with pytest.raises(M.MirresError):
+        gd.render(launch=1, grad_mode=1)
+    for s in gw.scenes + gd.scenes:
         s.close()
