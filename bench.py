@@ -323,6 +323,12 @@ def main():
     backward_ms = timed.backward_ms
     stages = M.mirres_stage_times(gw.ctx)  # stage times of the last timed batched render
     ms_b = max_over_ranks(ms_b)
+    # traversal work of one render, counted outside the timed region by the separately compiled
+    # counting variant of the traversal kernels (deterministic: the same rays visit the same
+    # nodes in every render)
+    w0 = M.mirres_get_work_counters(gw.ctx)
+    M.mirres_render(gw.ctx, scenes, gw.views, gw.params(1, flags=2), images, tape)
+    work = [b - a for a, b in zip(w0, M.mirres_get_work_counters(gw.ctx))]
 
     def arm(launch):
         ms, msr, rays, launches, _ = timed(launch, args.steps, args.warmup)
@@ -407,21 +413,36 @@ def main():
             "e2e": {"value": world * samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
 
-    # roofline of the dominant kernel, the shading stage (k_wshade): FP32 ALU bound; algorithmic
-    # FLOPs = RIS candidates x (60 BRDF FLOPs + 2 log2(env texels) search steps) per candidate,
-    # candidates counted by the library, time from the stage events captured in the graph
+    # roofline of the dominant stage kernel of the batched forward. All three are bound by FP32
+    # arithmetic (their data is L2-resident, no tensor-core work); algorithmic FLOPs per unit:
+    # shade (k_wshade): per RIS candidate 60 (BRDF luminance and cosine) + 2 log2(env texels)
+    # (the two CDF inversions); closest hit and shadow rays (k_wclosest, k_wshadow): 12 per box
+    # test (slab) + 27 per triangle test. Candidates and box / triangle tests are counted by the
+    # library; times come from the stage events captured in the graph.
     env_texels = sum(s.env.shape[0] * s.env.shape[1] for s in w.scenes) / len(w.scenes)
     per_cand = 60 + 2 * math.log2(env_texels)
     cand_per_render = cnt_b[5] / args.steps
-    shade_ms, shade_launches = stages["shade"]
-    achieved = cand_per_render * per_cand / (shade_ms / 1e3) / 1e12
     peak = 152 * 128 * 2 * 2.070e9 / 1e12
-    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None, "kernel": "k_wshade (shade + RIS stage)",
-                        "kernel_ms_per_launch": shade_ms / max(shade_launches, 1),
-                        "kernel_share_of_render": shade_ms / max(sum(v[0] for v in stages.values()), 1e-9),
-                        "flops_per_candidate": per_cand, "candidates_per_render": cand_per_render,
-                        "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock), non-tensor"}
+    total_stage_ms = max(sum(v[0] for v in stages.values()), 1e-9)
+    stage_flops = {"shade": cand_per_render * per_cand,
+                   "closest": 12.0 * work[0] + 27.0 * work[1],
+                   "shadow": 12.0 * work[2] + 27.0 * work[3]}
+    names = {"shade": "k_wshade (shade + RIS stage)", "closest": "k_wclosest (closest-hit stage)",
+             "shadow": "k_wshadow (shadow-ray stage)"}
+    roofs = {}
+    for k in ("closest", "shade", "shadow"):
+        ms_k, launches_k = stages[k]
+        achieved = stage_flops[k] / (ms_k / 1e3) / 1e12
+        roofs[k] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": names[k], "kernel_ms_per_launch": ms_k / max(launches_k, 1),
+                    "kernel_share_of_render": ms_k / total_stage_ms, "flops_per_render": stage_flops[k],
+                    "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock), non-tensor"}
+    roofs["shade"].update(flops_per_candidate=per_cand, candidates_per_render=cand_per_render)
+    roofs["closest"].update(box_tests_per_render=work[0], triangle_tests_per_render=work[1])
+    roofs["shadow"].update(box_tests_per_render=work[2], triangle_tests_per_render=work[3])
+    dominant = max(("closest", "shade", "shadow"), key=lambda k: stages[k][0])
+    line["roofline"] = dict(roofs[dominant])
+    line["stage_rooflines"] = roofs
     if rank == 0 and not args.no_cpu:
         cb, counts, osamples = cpu_baseline(w)
         line["cpu_baseline"] = cb

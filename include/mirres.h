@@ -107,7 +107,9 @@ typedef struct {
  *            multiply-adds differently).
  *   block, blocks_per_sm  launch shape of the persistent kernel (0 = autotuned / default)
  *   flags    bit 0: record CUDA events around every stage kernel of the batched wavefront
- *            (read back with mirres_stage_times) */
+ *            (read back with mirres_stage_times); bit 1: the batched wavefront counts its
+ *            traversal work (mirres_get_work_counters) -- a separately compiled variant of the
+ *            traversal kernels, so that the uncounted launch keeps its register budget */
 typedef struct {
     int32_t ris_m;
     uint32_t seed_lo, seed_hi;
@@ -291,6 +293,14 @@ mirres_status mirres_env_export(const mirres_scene* scene, uint32_t* marg, uint3
  * stream): [0] primary rays, [1] continuation rays, [2] shadow rays, [3] samples rendered,
  * [4] samples differentiated, [5] RIS candidates, [6] kernel launches, [7] error flag. */
 mirres_status mirres_get_counters(mirres_context* ctx, uint64_t out[8]);
+
+/* Cumulative traversal work of the batched launches (launch 1) issued with params.flags bit 1
+ * since the context was created
+ * (synchronises like mirres_get_counters): [0] box tests and [1] triangle tests of closest-hit
+ * rays, [2] box tests and [3] triangle tests of shadow rays. A box test is one slab test of a
+ * child box (two per node visited), a triangle test one ray/triangle solve. Reset with
+ * mirres_reset_counters. */
+mirres_status mirres_get_work_counters(mirres_context* ctx, uint64_t out[4]);
 mirres_status mirres_reset_counters(mirres_context* ctx);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -416,7 +416,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     key.max_b = max_b;
     key.M = M;
     key.sms = ctx->sm_count;
-    key.flags = flags & 1;
+    key.flags = flags & 3;
     key.nvx = nvx;
     key.k0 = rng.rk0[0];
     key.k1 = rng.rk1[0];
@@ -435,7 +435,8 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         MR_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
         mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave, qa, qb, hq, sq, qc, tp, ctx->counters,
                        d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
-                       (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr, nvx);
+                       (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr, nvx,
+                       (flags & 2) != 0);
         ctx->stage_pairs = (flags & 1) ? pairs : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -810,6 +811,17 @@ extern "C" mirres_status mirres_get_counters(mirres_context* ctx, uint64_t out[8
     MR_CUDA(cudaMemcpy(h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 8; ++i) out[i] = (uint64_t)h[i];
     out[CNT_LAUNCH] = ctx->host_launches;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_get_work_counters(mirres_context* ctx, uint64_t out[4])
+{
+    if (!ctx || !out) return arg_error("ctx and out must not be NULL");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    unsigned long long h[CNT_N];
+    MR_CUDA(cudaStreamSynchronize(ctx->last_stream));
+    MR_CUDA(cudaMemcpy(h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) out[i] = (uint64_t)h[CNT_CBOX + i];
     return MIRRES_OK;
 }
 

@@ -477,11 +477,12 @@ __device__ __forceinline__ float slab(float3 lo, float3 hi, float3 oi, float3 in
 }
 
 // Closest (any = false) or any hit with t in (tmin, tmax). `sstk` = this thread's shared
-// stack column (stride `sstride`). Returns the number of nodes visited (for counters), or
-// -1 if the iteration cap was reached (a malformed tree; the ray reports a miss).
+// stack column (stride `sstride`). Returns the number of nodes visited (two box tests each),
+// or -1 if the iteration cap was reached (a malformed tree; the ray reports a miss); adds the
+// triangle tests to *ntri when given.
 template <bool ANY>
 __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, int skip, float tmin, float tmax,
-                                        Hit& best, uint32_t* sstk, int sstride)
+                                        Hit& best, uint32_t* sstk, int sstride, int* ntri = nullptr)
 {
     best.t = tmax;
     best.tri = -1;
@@ -489,8 +490,9 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
     const int F = s.n_tris;
     if (F <= 0) return 0;
     if (F == 1) {
+        if (ntri) ++*ntri;
         test_leaf(s, 0, o, d, skip, tmin, best);
-        return 1;
+        return 0;
     }
     const float3 inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
     const float3 oi = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
@@ -513,10 +515,12 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
         bool gl = tl <= best.t, gr = tr <= best.t;
         // leaves are tested on the spot
         if (gl && ch.x < 0) {
+            if (ntri) ++*ntri;
             if (test_leaf(s, ~ch.x, o, d, skip, tmin, best) && ANY) return visited;
             gl = false;
         }
         if (gr && ch.y < 0) {
+            if (ntri) ++*ntri;
             if (test_leaf(s, ~ch.y, o, d, skip, tmin, best) && ANY) return visited;
             gr = false;
         }

@@ -25,7 +25,10 @@ struct Workspace {
     size_t bytes = 0;
 };
 
-enum { CNT_PRIMARY = 0, CNT_CONT, CNT_SHADOW, CNT_SAMPLES, CNT_DIFF, CNT_CAND, CNT_LAUNCH, CNT_ERROR, CNT_N };
+enum { CNT_PRIMARY = 0, CNT_CONT, CNT_SHADOW, CNT_SAMPLES, CNT_DIFF, CNT_CAND, CNT_LAUNCH, CNT_ERROR,
+       // traversal work of the batched wavefront: box tests and triangle tests of closest-hit
+       // rays, then of shadow rays
+       CNT_CBOX, CNT_CTRI, CNT_SBOX, CNT_STRI, CNT_N };
 
 struct mirres_context {
     int device = 0;

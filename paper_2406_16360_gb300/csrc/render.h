@@ -67,6 +67,6 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,
                     const ShadowDev& sq, unsigned int* qc, void* tape, unsigned long long* counters,
                     const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaStream_t st,
-                    cudaEvent_t* ev, int* kind, int nvx);
+                    cudaEvent_t* ev, int* kind, int nvx, bool count);
 int mr_wave_launches(uint64_t total, uint64_t wave, int max_bounces);
 int mr_wave_stage_pairs(uint64_t total, uint64_t wave, int max_bounces);

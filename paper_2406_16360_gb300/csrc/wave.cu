@@ -9,6 +9,17 @@
 
 namespace {
 
+// per-warp flush of a traversal stage's box and triangle test counts (counters idx, idx + 1)
+__device__ __forceinline__ void flush_work(unsigned long long* counters, int idx, unsigned int box, unsigned int tri)
+{
+    box = __reduce_add_sync(MR_FULL, box);
+    tri = __reduce_add_sync(MR_FULL, tri);
+    if (lane_id() == 0) {
+        atomicAdd(counters + idx, (unsigned long long)box);
+        atomicAdd(counters + idx + 1, (unsigned long long)tri);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ views, int n_views, Rng rng,
                                                  uint64_t first, uint32_t n, QueueDev q, void* tape, uint64_t ntot,
                                                  int nvx)
@@ -39,14 +50,18 @@ __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ vie
     }
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(256) k_wclosest(const SceneDev* __restrict__ scenes,
                                                   const ViewDev* __restrict__ views, int b, QueueDev q,
                                                   const unsigned int* count, unsigned int count_fixed, QueueDev hq,
-                                                  unsigned int* count_hit, void* tape, uint64_t ntot)
+                                                  unsigned int* count_hit, void* tape, uint64_t ntot,
+                                                  unsigned long long* counters)
 {
     extern __shared__ uint32_t sstk[];
     const TapeDev tp = tape_of(tape, ntot);
     const unsigned int n = count ? *count : count_fixed;
+    unsigned int n_box = 0;
+    int n_tri = 0;
     const unsigned int stride = gridDim.x * blockDim.x;
     const unsigned int rounds = (n + stride - 1) / stride;
     for (unsigned int r = 0; r < rounds; ++r) {
@@ -60,8 +75,10 @@ __global__ void __launch_bounds__(256) k_wclosest(const SceneDev* __restrict__ s
             qb = q.b[i];
             const ViewDev& v = views[__float_as_int(qb.w)];
             const SceneDev& s = scenes[v.scene];
-            traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), *s.tmin_dev, __int_as_float(0x7f800000), h,
-                            sstk + threadIdx.x, blockDim.x);
+            const int nodes = traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), *s.tmin_dev,
+                                              __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x,
+                                              COUNT ? &n_tri : nullptr);
+            if (COUNT) n_box += 2u * (unsigned int)max(nodes, 0);
             if (h.tri < 0 && b == 0) {
                 const uint64_t g = v.offset + __float_as_uint(qd.w);
                 const float4 L = __ldg(s.env_texel + env_texel_of(s, xyz(qd)));
@@ -79,6 +96,7 @@ __global__ void __launch_bounds__(256) k_wclosest(const SceneDev* __restrict__ s
             hq.bi[slot] = q.bi[i];
         }
     }
+    if (COUNT) flush_work(counters, CNT_CBOX, n_box, (unsigned int)n_tri);
 }
 
 __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* __restrict__ scenes,
@@ -147,20 +165,26 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* _
     if (lane_id() == 0 && n_cand) atomicAdd(counters + 5, n_cand);
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ scenes,
                                                  const ViewDev* __restrict__ views, int b, ShadowDev sq,
-                                                 const unsigned int* count, void* tape, uint64_t ntot, int nvx)
+                                                 const unsigned int* count, void* tape, uint64_t ntot, int nvx,
+                                                 unsigned long long* counters)
 {
     extern __shared__ uint32_t sstk[];
     const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count;
+    unsigned int n_box = 0;
+    int n_tri = 0;
     for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 a = sq.o[i], dd = sq.d[i], ad = sq.add[i];
         const ViewDev& v = views[__float_as_int(ad.w)];
         const SceneDev& s = scenes[v.scene];
         Hit h;
-        traverse<true>(s, xyz(a), xyz(dd), __float_as_int(a.w), *s.tmin_dev, __int_as_float(0x7f800000), h,
-                       sstk + threadIdx.x, blockDim.x);
+        const int nodes = traverse<true>(s, xyz(a), xyz(dd), __float_as_int(a.w), *s.tmin_dev,
+                                         __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x,
+                                         COUNT ? &n_tri : nullptr);
+        if (COUNT) n_box += 2u * (unsigned int)max(nodes, 0);
         const uint64_t g = v.offset + __float_as_uint(dd.w);
         if (h.tri < 0) {
             const float4 ai = sq.addi[i];
@@ -178,6 +202,7 @@ __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ sc
             tape_vx_occluded(tp, g, b);
         }
     }
+    if (COUNT) flush_work(counters, CNT_SBOX, n_box, (unsigned int)n_tri);
 }
 
 unsigned grid_cap(uint64_t n, int block, int cap)
@@ -195,7 +220,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,
                     const ShadowDev& sq, unsigned int* qc, void* tape, unsigned long long* counters,
                     const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaStream_t st,
-                    cudaEvent_t* ev, int* kind, int nvx)
+                    cudaEvent_t* ev, int* kind, int nvx, bool count)
 {
     const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
     int pair = 0;
@@ -215,8 +240,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         for (int b = 0; b < max_bounces; ++b) {
             const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
             mark(0, true);
-            k_wclosest<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(scenes, views, b, cur, cnt_in, n, hq,
-                                                                     qc + 3 * b, tape, total);
+            (count ? k_wclosest<true> : k_wclosest<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
+                scenes, views, b, cur, cnt_in, n, hq, qc + 3 * b, tape, total, counters);
             mark(0, false);
             mark(1, true);
             k_wshade<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, b, M, hq, qc + 3 * b, nxt,
@@ -224,8 +249,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                                                                 counters);
             mark(1, false);
             mark(2, true);
-            k_wshadow<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(scenes, views, b, sq, qc + 3 * b + 2, tape, total,
-                                                                    nvx);
+            (count ? k_wshadow<true> : k_wshadow<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
+                scenes, views, b, sq, qc + 3 * b + 2, tape, total, nvx, counters);
             mark(2, false);
             QueueDev t = cur;
             cur = nxt;

@@ -21,6 +21,7 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_render_noalloc",
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
+           "mirres_get_work_counters",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
 
 # limits of mirres_render_noalloc (include/mirres.h)
@@ -108,6 +109,7 @@ def lib():
                 "mirres_bvh_export": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "mirres_env_export": (st, [vp, vp, vp, vp, vp, vp]),
                 "mirres_get_counters": (st, [vp, C.POINTER(C.c_uint64)]),
+                "mirres_get_work_counters": (st, [vp, C.POINTER(C.c_uint64)]),
                 "mirres_reset_counters": (st, [vp]),
                 "mirres_last_error": (C.c_char_p, []),
             }
@@ -312,6 +314,13 @@ def mirres_env_export(scene: Scene, marg=None, cond=None, texel=None, total=None
 def mirres_get_counters(ctx: Context):
     out = (C.c_uint64 * 8)()
     _check("mirres_get_counters", lib().mirres_get_counters(ctx.handle, out))
+    return [int(x) for x in out]
+
+
+def mirres_get_work_counters(ctx: Context):
+    """[closest-hit box tests, closest-hit triangle tests, shadow box tests, shadow triangle tests]"""
+    out = (C.c_uint64 * 4)()
+    _check("mirres_get_work_counters", lib().mirres_get_work_counters(ctx.handle, out))
     return [int(x) for x in out]
 
 

@@ -412,3 +412,26 @@ def test_full_mode_argument_checks(M, ctx):
         gd.render(launch=1, grad_mode=1)
     for s in gw.scenes + gd.scenes:
         s.close()
+
+
+def test_work_counters_are_deterministic_and_change_nothing(M, ctx):
+    """the counting variant of the traversal stages renders the same image and counts the
+    same work every time (the roofline uses one counted render for the timed ones)"""
+    w = synth.config2(res=48, n_views=2, tex=32, spp=4)
+    gw = _gw(ctx, w)
+    ref, tape = gw.render(launch=1)
+    counts = []
+    for _ in range(2):
+        w0 = M.mirres_get_work_counters(ctx)
+        img, _ = gw.render(launch=1, tape=tape, flags=2)
+        torch.cuda.synchronize()
+        counts.append([b - a for a, b in zip(w0, M.mirres_get_work_counters(ctx))])
+        for x, y in zip(img, ref):
+            assert torch.equal(x, y)
+    assert counts[0] == counts[1]
+    c = counts[0]
+    assert c[0] > 0 and c[1] > 0 and c[2] > 0  # box and triangle tests of both ray kinds
+    # at least one box test per primary ray; at most two per node of the tree per ray
+    assert c[0] >= w.samples and c[0] <= 2 * w.scenes[0].n_tris * 2 * w.samples
+    for s in gw.scenes:
+        s.close()
