@@ -28,6 +28,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd path-samples/s (batched launch; plain per-view launch and Mrays/s alongside)"
+# denoiser sigmas (colour, normal, position) of the EAWT arm, and the measured HBM copy rate
+EAWT_SIGMAS = (0.5, 0.3, 0.2)
+
+
+def _hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                 "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0  # fallback figure when the measured peaks are absent
+
+
+HBM_PEAK = _hbm_peak()
 UNIT = "path-samples/s"
 
 
@@ -205,6 +218,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-launch arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-full", action="store_true", help="skip the FULL-mode adjoint arm")
+    ap.add_argument("--no-eawt", action="store_true", help="skip the denoiser arm")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -378,6 +392,53 @@ def main():
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
+    # the denoiser between image and loss (EAWT, Appendix A), every view: G-buffer, forward and
+    # adjoint; HBM-bound stencils (taps hit L1/L2), algorithmic bytes per pixel: forward 24 (input
+    # copy) + 3 x 52 (colour, normal, position in; colour, normaliser out), adjoint 3 x 64
+    # (gradient, recorded colour, normaliser, normal, position in; gradient out)
+    eawt = None
+    if not args.no_eawt:
+        ep = M.EawtParams(EAWT_SIGMAS[0], EAWT_SIGMAS[1], EAWT_SIGMAS[2], 3)
+        gbn = [torch.empty_like(im) for im in images]
+        gbx = [torch.empty_like(im) for im in images]
+        dn_out = [torch.empty_like(im) for im in images]
+        dn_grad = [torch.empty_like(im) for im in images]
+        recs = [torch.empty(M.mirres_eawt_record_bytes(v.width, v.height, 3) // 4, device=dev) for v in gw.views]
+
+        def eawt_pass(ev=None):
+            for vi, v in enumerate(gw.views):
+                M.mirres_gbuffer(gw.ctx, gw.scenes[v.scene].handle, v, gbn[vi], gbx[vi])
+            if ev is not None:
+                ev[0].record()
+            for vi in range(len(gw.views)):
+                M.mirres_eawt(gw.ctx, images[vi], gbn[vi], gbx[vi], ep, dn_out[vi], recs[vi])
+            for vi in range(len(gw.views)):
+                M.mirres_eawt_backward(gw.ctx, d_images[vi], gbn[vi], gbx[vi], ep, recs[vi], dn_grad[vi])
+            if ev is not None:
+                ev[1].record()
+
+        for _ in range(args.warmup):
+            eawt_pass()
+        torch.cuda.synchronize()
+        e_all = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e_dn = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e_all[0].record()
+        for _ in range(args.steps):
+            eawt_pass(e_dn)
+        e_all[1].record()
+        torch.cuda.synchronize()
+        pix = sum(v.width * v.height for v in gw.views)
+        ms_all = e_all[0].elapsed_time(e_all[1]) / args.steps
+        ms_dn = e_dn[0].elapsed_time(e_dn[1])  # the last pass
+        bytes_px = 24 + 3 * 52 + 3 * 64
+        ach = pix * bytes_px / (ms_dn / 1e3) / 1e9
+        eawt = {"mpix_per_s": pix / (ms_all / 1e3) / 1e6, "ms_per_step": ms_all,
+                "ms_denoise_fwd_bwd": ms_dn, "pixels": pix, "levels": 3, "sigmas": list(EAWT_SIGMAS),
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK, "unit": "GB/s",
+                             "frac": ach / HBM_PEAK, "traffic": None, "bytes_per_pixel": bytes_px,
+                             "kernel": "k_eawt_level + k_eawt_level_adjoint",
+                             "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}}
+
     # FULL-mode adjoint (gradients through every vertex): the same step with grad_mode 1
     full = None
     if want_full:
@@ -404,6 +465,7 @@ def main():
             "plain": plain,
             "persistent": persistent,
             "full_adjoint": full,
+            "denoiser": eawt,
             "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
             "counters_per_step": {"primary_rays": cnt_b[0] // args.steps, "continuation_rays": cnt_b[1] // args.steps,
                                   "shadow_rays": cnt_b[2] // args.steps, "ris_candidates": cnt_b[5] // args.steps,

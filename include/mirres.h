@@ -289,6 +289,49 @@ mirres_status mirres_bvh_export(const mirres_scene* scene, uint64_t* keys, int32
 mirres_status mirres_env_export(const mirres_scene* scene, uint32_t* marg, uint32_t* cond, float* texel,
                                 double* total, void* stream);
 
+/* ---- denoiser between the rendered image and the loss (Appendix A, "Denoiser") ------------- */
+
+/* Edge-avoiding a-trous wavelet denoiser. Level i (i = 0 .. levels-1) smooths c_i into
+ *   c_{i+1}(p) = sum_q h(q - p) w(p, q) c_i(q) / sum_q h(q - p) w(p, q)
+ * over 5 x 5 B3-spline taps (1, 4, 6, 4, 1) / 16 per axis placed 2^i pixels apart (taps outside
+ * the image left out), with w(p, q) = exp(-|c_i(p) - c_i(q)|^2 / (sigma_rt / 2^i)^2
+ * - |n_p - n_q|^2 / sigma_n^2 - |x_p - x_q|^2 / sigma_x^2) on the colour of the level's input
+ * and the G-buffer normals n and positions x. The paper uses three levels. */
+#define MIRRES_EAWT_MAX_LEVELS 8
+typedef struct {
+    float sigma_rt, sigma_n, sigma_x;  /* > 0 */
+    int32_t levels;                    /* 1 .. MIRRES_EAWT_MAX_LEVELS */
+} mirres_eawt_params;
+
+/* Bytes of the record mirres_eawt writes for mirres_eawt_backward: 16 * levels * width * height
+ * (each level's input image and normaliser). 0 for invalid arguments. */
+size_t mirres_eawt_record_bytes(int32_t width, int32_t height, int32_t levels);
+
+/* G-buffer of one view: the primary hit through each pixel centre (camera as in mirres_render,
+ * jitter 1/2), face normal turned towards the camera and hit position; both 0 where the ray
+ * escapes. normal, position: device [height][width][3], caller-owned. view->scene is ignored
+ * (the scene is `scene`). Asynchronous. */
+mirres_status mirres_gbuffer(mirres_context* ctx, const mirres_scene* scene, const mirres_view* view,
+                             float* normal, float* position, void* stream);
+
+/* Denoise one image: image, normal, position [height][width][3] device (read-only), out
+ * [height][width][3] device, record (mirres_eawt_record_bytes, device) receives what the
+ * adjoint needs; the image may be overwritten after the call. Asynchronous.
+ * MIRRES_ERR_ARG for NULL pointers, sizes < 1, sigmas <= 0, levels outside [1, 8] or a record
+ * that is too small. */
+mirres_status mirres_eawt(mirres_context* ctx, const float* image, const float* normal, const float* position,
+                          int32_t width, int32_t height, const mirres_eawt_params* params, float* out,
+                          void* record, size_t record_bytes, void* stream);
+
+/* Adjoint of mirres_eawt with its weights held fixed (they depend on the forward's images and
+ * are treated as constants): d_image = A^T d_out, A the linear filter the recorded forward
+ * applied. d_out, d_image [height][width][3] device; record, normal, position, params those of
+ * the forward. d_image is overwritten (not accumulated). Uses the context workspace. */
+mirres_status mirres_eawt_backward(mirres_context* ctx, const float* d_out, const float* normal,
+                                   const float* position, int32_t width, int32_t height,
+                                   const mirres_eawt_params* params, const void* record, size_t record_bytes,
+                                   float* d_image, void* stream);
+
 /* Cumulative counters since the context was created (synchronises the context's last
  * stream): [0] primary rays, [1] continuation rays, [2] shadow rays, [3] samples rendered,
  * [4] samples differentiated, [5] RIS candidates, [6] kernel launches, [7] error flag. */

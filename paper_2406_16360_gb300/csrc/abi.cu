@@ -386,7 +386,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     plan.take<SceneDev>((size_t)n_scenes);
     plan.take<float*>((size_t)n_views);
     plan.take<uint64_t>((size_t)n_views);
-    plan.take<unsigned int>(3 * (size_t)max_b + 3);
+    plan.take<unsigned int>(5 * (size_t)max_b + 3);
     plan.take<float4>(16ull * wave);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
@@ -396,7 +396,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
     float** d_images = cv.take<float*>((size_t)n_views);
     uint64_t* d_pixoff = cv.take<uint64_t>((size_t)n_views);
-    unsigned int* qc = cv.take<unsigned int>(3 * (size_t)max_b + 3);
+    unsigned int* qc = cv.take<unsigned int>(5 * (size_t)max_b + 3);
     QueueDev qa{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
     QueueDev qb{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
     QueueDev hq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
@@ -760,6 +760,109 @@ extern "C" mirres_status mirres_trace(mirres_context* ctx, const mirres_scene* s
                          as_stream(stream));
     MR_CUDA(cudaGetLastError());
     ctx->host_launches += 1;
+    return MIRRES_OK;
+}
+
+// ---- denoiser (Appendix A, "Denoiser") -------------------------------------------------------
+static mirres_status check_eawt(int32_t width, int32_t height, const mirres_eawt_params* p)
+{
+    if (width < 1 || height < 1) return arg_error("width and height must be >= 1");
+    if ((int64_t)width * height > (int64_t)1 << 31) return arg_error("image larger than 2^31 pixels");
+    if (!p) return arg_error("eawt params is NULL");
+    if (p->levels < 1 || p->levels > MIRRES_EAWT_MAX_LEVELS)
+        return arg_error("levels must be in [1, " + std::to_string(MIRRES_EAWT_MAX_LEVELS) + "]");
+    if (!(p->sigma_rt > 0.0f) || !(p->sigma_n > 0.0f) || !(p->sigma_x > 0.0f))
+        return arg_error("sigma_rt, sigma_n and sigma_x must be > 0");
+    return MIRRES_OK;
+}
+
+extern "C" size_t mirres_eawt_record_bytes(int32_t width, int32_t height, int32_t levels)
+{
+    if (width < 1 || height < 1 || levels < 1 || levels > MIRRES_EAWT_MAX_LEVELS) return 0;
+    return (size_t)16 * (size_t)levels * (size_t)width * (size_t)height;
+}
+
+extern "C" mirres_status mirres_gbuffer(mirres_context* ctx, const mirres_scene* scene, const mirres_view* view,
+                                        float* normal, float* position, void* stream)
+{
+    if (!ctx || !scene || !view || !normal || !position) return arg_error("ctx, scene, view, normal, position required");
+    if (!scene->built) {
+        g_err = "mirres_gbuffer: call mirres_bvh_build first";
+        return MIRRES_ERR_STATE;
+    }
+    mirres_view one = *view;
+    one.scene = 0;
+    std::vector<ViewDev> vdev;
+    uint64_t total = 0, max_view = 0;
+    MR_TRY(check_views(&one, 1, 1, vdev, total, max_view));
+    MR_CUDA(cudaSetDevice(ctx->device));
+    mr_launch_gbuffer(mr_scene_dev(scene), vdev[0], normal, position, ctx->sm_count, as_stream(stream));
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += 1;
+    return MIRRES_OK;
+}
+
+// record layout: levels x [H][W][3] level inputs c_i, then levels x [H][W] normalisers k_i
+extern "C" mirres_status mirres_eawt(mirres_context* ctx, const float* image, const float* normal,
+                                     const float* position, int32_t width, int32_t height,
+                                     const mirres_eawt_params* params, float* out, void* record,
+                                     size_t record_bytes, void* stream)
+{
+    if (!ctx || !image || !normal || !position || !out || !record)
+        return arg_error("ctx, image, normal, position, out and record required");
+    MR_TRY(check_eawt(width, height, params));
+    if (record_bytes < mirres_eawt_record_bytes(width, height, params->levels))
+        return arg_error("record_bytes is smaller than mirres_eawt_record_bytes");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    const size_t npx = (size_t)width * height;
+    const int L = params->levels;
+    float* c = reinterpret_cast<float*>(record);
+    float* k = c + 3 * npx * (size_t)L;
+    MR_CUDA(cudaMemcpyAsync(c, image, sizeof(float) * 3 * npx, cudaMemcpyDeviceToDevice, st));
+    const float in2 = 1.0f / (params->sigma_n * params->sigma_n), ix2 = 1.0f / (params->sigma_x * params->sigma_x);
+    for (int i = 0; i < L; ++i) {
+        const int step = 1 << i;
+        const float srt = params->sigma_rt / (float)step;
+        float* dst = (i + 1 < L) ? c + 3 * npx * (size_t)(i + 1) : out;
+        mr_launch_eawt_level(c + 3 * npx * (size_t)i, normal, position, width, height, step, 1.0f / (srt * srt), in2,
+                             ix2, dst, k + npx * (size_t)i, ctx->sm_count, st);
+    }
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += (unsigned long long)L;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_eawt_backward(mirres_context* ctx, const float* d_out, const float* normal,
+                                              const float* position, int32_t width, int32_t height,
+                                              const mirres_eawt_params* params, const void* record,
+                                              size_t record_bytes, float* d_image, void* stream)
+{
+    if (!ctx || !d_out || !normal || !position || !record || !d_image)
+        return arg_error("ctx, d_out, normal, position, record and d_image required");
+    MR_TRY(check_eawt(width, height, params));
+    if (record_bytes < mirres_eawt_record_bytes(width, height, params->levels))
+        return arg_error("record_bytes is smaller than mirres_eawt_record_bytes");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    const size_t npx = (size_t)width * height;
+    const int L = params->levels;
+    MR_TRY(ws_reserve(ctx, sizeof(float) * 6 * npx + 256));
+    float* tmp[2] = {reinterpret_cast<float*>(ctx->ws.ptr), reinterpret_cast<float*>(ctx->ws.ptr) + 3 * npx};
+    const float* c = reinterpret_cast<const float*>(record);
+    const float* k = c + 3 * npx * (size_t)L;
+    const float in2 = 1.0f / (params->sigma_n * params->sigma_n), ix2 = 1.0f / (params->sigma_x * params->sigma_x);
+    const float* g = d_out;
+    for (int i = L - 1; i >= 0; --i) {
+        const int step = 1 << i;
+        const float srt = params->sigma_rt / (float)step;
+        float* dst = (i == 0) ? d_image : tmp[i & 1];
+        mr_launch_eawt_level_adjoint(g, c + 3 * npx * (size_t)i, k + npx * (size_t)i, normal, position, width, height,
+                                     step, 1.0f / (srt * srt), in2, ix2, dst, ctx->sm_count, st);
+        g = dst;
+    }
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += (unsigned long long)L;
     return MIRRES_OK;
 }
 

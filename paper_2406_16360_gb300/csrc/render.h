@@ -62,6 +62,14 @@ void mr_launch_l2(const float* img, const float* ref, int64_t n, float* dimg, fl
 void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* skip, int64_t n, int any,
                           int32_t* hit_tri, float* hit_tuv, int sms, cudaStream_t st);
 
+// denoise.cu: EAWT levels, their adjoints, the pixel-centre G-buffer
+void mr_launch_eawt_level(const float* cin, const float* nrm, const float* pos, int W, int H, int step, float inv_rt2,
+                          float inv_n2, float inv_x2, float* cout, float* kout, int sms, cudaStream_t st);
+void mr_launch_eawt_level_adjoint(const float* gin, const float* c, const float* kin, const float* nrm, const float* pos,
+                                  int W, int H, int step, float inv_rt2, float inv_n2, float inv_x2, float* gout, int sms,
+                                  cudaStream_t st);
+void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* pos, int sms, cudaStream_t st);
+
 // wave.cu: the batched wavefront forward (recorded on a stream, captured as a graph)
 void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,
                     Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,

@@ -205,6 +205,158 @@ __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ sc
     if (COUNT) flush_work(counters, CNT_SBOX, n_box, (unsigned int)n_tri);
 }
 
+// Lane refill for the incoherent stages (continuation and shadow rays): each warp takes rays
+// from its stage's queue 32 at a time (one atomic per 32 rays) and advances its lanes' rays
+// MR_REFILL_STEPS node visits at a time; once MR_REFILL_MIN lanes are done (or all, when the
+// queue is drained) they take new rays, so a warp does not wait for its longest ray. The grid
+// is one resident wave of blocks; `fetch` is the stage's ray counter, zero at launch.
+struct RefillPool {
+    unsigned int pool, pool_end;
+    bool drained;
+};
+
+// hands rays to idle lanes; returns this lane's new ray index, or -1
+__device__ __forceinline__ long long refill(RefillPool& rp, bool has, unsigned int n, unsigned int* fetch)
+{
+    const unsigned idle = __ballot_sync(MR_FULL, !has);
+    const int n_idle = __popc(idle);
+    if (n_idle < MR_REFILL_MIN && idle != MR_FULL) return -1;
+    if (rp.pool == rp.pool_end && !rp.drained) {
+        unsigned int base = 0;
+        if (lane_id() == 0) base = atomicAdd(fetch, 32u);
+        base = __shfl_sync(MR_FULL, base, 0);
+        if (base >= n) {
+            rp.drained = true;
+        } else {
+            rp.pool = base;
+            rp.pool_end = (n - base < 32u) ? n : base + 32u;
+        }
+    }
+    long long mine = -1;
+    if (rp.pool < rp.pool_end) {
+        const unsigned avail = rp.pool_end - rp.pool;
+        const unsigned rank = __popc(idle & lanemask_lt());
+        if (!has && rank < avail) mine = (long long)(rp.pool + rank);
+        rp.pool += ((unsigned)n_idle < avail) ? (unsigned)n_idle : avail;
+    }
+    return mine;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_wclosest_refill(const SceneDev* __restrict__ scenes,
+                                                         const ViewDev* __restrict__ views, QueueDev q,
+                                                         const unsigned int* count, QueueDev hq,
+                                                         unsigned int* count_hit, unsigned int* fetch,
+                                                         unsigned long long* counters)
+{
+    extern __shared__ uint32_t sstk[];
+    const unsigned int n = *count;
+    uint32_t lstk[MR_LSTACK];
+    Trav T;
+    T.node = -1;
+    bool has = false;
+    unsigned int i = 0;
+    RefillPool rp{0u, 0u, false};
+    float4 qd = make_float4(0.f, 0.f, 0.f, 0.f), qb = qd;
+    const SceneDev* sp = scenes;
+    unsigned int n_box = 0;
+    int n_tri = 0;
+    while (true) {
+        const long long ni = refill(rp, has, n, fetch);
+        if (ni >= 0) {
+            i = (unsigned int)ni;
+            const float4 a = q.o[i];
+            qd = q.d[i];
+            qb = q.b[i];
+            sp = scenes + views[__float_as_int(qb.w)].scene;
+            trav_begin(*sp, T, xyz(a), xyz(qd), __float_as_int(a.w), *sp->tmin_dev, __int_as_float(0x7f800000),
+                       COUNT ? &n_tri : nullptr);
+            has = true;
+        }
+        if (!__any_sync(MR_FULL, has)) break;
+        bool done = false;
+        if (has) {
+            const int v0 = T.visited;
+            done = trav_run<false>(*sp, T, sstk + threadIdx.x, blockDim.x, lstk, MR_REFILL_STEPS,
+                                   COUNT ? &n_tri : nullptr);
+            if (COUNT) n_box += 2u * (unsigned int)max(T.visited - v0, 0);
+        }
+        if (__any_sync(MR_FULL, done)) {
+            const bool hit = done && T.best.tri >= 0;
+            const unsigned int slot = warp_append(hit, count_hit);
+            if (hit) {
+                hq.o[slot] = make_float4(T.best.t, T.best.u, T.best.v, __int_as_float(T.best.tri));
+                hq.d[slot] = qd;
+                hq.b[slot] = qb;
+                hq.bi[slot] = q.bi[i];
+            }
+            if (done) has = false;
+        }
+    }
+    if (COUNT) flush_work(counters, CNT_CBOX, n_box, (unsigned int)n_tri);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_wshadow_refill(const SceneDev* __restrict__ scenes,
+                                                        const ViewDev* __restrict__ views, int b, ShadowDev sq,
+                                                        const unsigned int* count, unsigned int* fetch, void* tape,
+                                                        uint64_t ntot, int nvx, unsigned long long* counters)
+{
+    extern __shared__ uint32_t sstk[];
+    const TapeDev tp = tape_of(tape, ntot, nvx);
+    const unsigned int n = *count;
+    uint32_t lstk[MR_LSTACK];
+    Trav T;
+    T.node = -1;
+    bool has = false;
+    unsigned int i = 0;
+    RefillPool rp{0u, 0u, false};
+    float4 dd = make_float4(0.f, 0.f, 0.f, 0.f), ad = dd;
+    const SceneDev* sp = scenes;
+    unsigned int n_box = 0;
+    int n_tri = 0;
+    while (true) {
+        const long long ni = refill(rp, has, n, fetch);
+        if (ni >= 0) {
+            i = (unsigned int)ni;
+            const float4 a = sq.o[i];
+            dd = sq.d[i];
+            ad = sq.add[i];
+            sp = scenes + views[__float_as_int(ad.w)].scene;
+            trav_begin(*sp, T, xyz(a), xyz(dd), __float_as_int(a.w), *sp->tmin_dev, __int_as_float(0x7f800000),
+                       COUNT ? &n_tri : nullptr);
+            has = true;
+        }
+        if (!__any_sync(MR_FULL, has)) break;
+        if (has) {
+            const int v0 = T.visited;
+            const bool done = trav_run<true>(*sp, T, sstk + threadIdx.x, blockDim.x, lstk, MR_REFILL_STEPS,
+                                             COUNT ? &n_tri : nullptr);
+            if (COUNT) n_box += 2u * (unsigned int)max(T.visited - v0, 0);
+            if (done) {
+                has = false;
+                const uint64_t g = views[__float_as_int(ad.w)].offset + __float_as_uint(dd.w);
+                if (T.best.tri < 0) {
+                    const float4 ai = sq.addi[i];
+                    tp.rad[0][g] = __fadd_rn(tp.rad[0][g], ad.x);
+                    tp.rad[1][g] = __fadd_rn(tp.rad[1][g], ad.y);
+                    tp.rad[2][g] = __fadd_rn(tp.rad[2][g], ad.z);
+                    if (b >= 1) {
+                        tp.lind[0][g] = __fadd_rn(tp.lind[0][g], ai.x);
+                        tp.lind[1][g] = __fadd_rn(tp.lind[1][g], ai.y);
+                        tp.lind[2][g] = __fadd_rn(tp.lind[2][g], ai.z);
+                    }
+                } else if (b == 0) {
+                    tp.wv[g] = 0.0f;
+                } else {
+                    tape_vx_occluded(tp, g, b);
+                }
+            }
+        }
+    }
+    if (COUNT) flush_work(counters, CNT_SBOX, n_box, (unsigned int)n_tri);
+}
+
 unsigned grid_cap(uint64_t n, int block, int cap)
 {
     const uint64_t g = (n + block - 1) / block;
@@ -223,6 +375,15 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     cudaEvent_t* ev, int* kind, int nvx, bool count)
 {
     const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
+    // the refilling kernels run one resident wave of blocks
+    int occ_c = 0, occ_s = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, count ? k_wclosest_refill<true> : k_wclosest_refill<false>,
+                                                  256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, count ? k_wshadow_refill<true> : k_wshadow_refill<false>,
+                                                  256, smem);
+    const unsigned grid_c = (unsigned)(sms * (occ_c > 0 ? occ_c : 1));
+    const unsigned grid_s = (unsigned)(sms * (occ_s > 0 ? occ_s : 1));
+    unsigned int* fetch = qc + 3 * max_bounces + 3;  // [2 * max_bounces]: closest, shadow per bounce
     int pair = 0;
     auto mark = [&](int k, bool start) {
         if (!ev) return;
@@ -232,7 +393,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
     };
     for (uint64_t first = 0; first < total; first += wave) {
         const uint32_t n = (uint32_t)(total - first < wave ? total - first : wave);
-        cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (3 * max_bounces + 3), st);
+        cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (5 * max_bounces + 3), st);
         mark(3, true);
         k_wraygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(views, n_views, rng, first, n, qa, tape, total, nvx);
         mark(3, false);
@@ -240,8 +401,12 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         for (int b = 0; b < max_bounces; ++b) {
             const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
             mark(0, true);
-            (count ? k_wclosest<true> : k_wclosest<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
-                scenes, views, b, cur, cnt_in, n, hq, qc + 3 * b, tape, total, counters);
+            if (MR_REFILL_CLOSEST && b > 0)  // primary rays stay coherent in the plain stage kernel
+                (count ? k_wclosest_refill<true> : k_wclosest_refill<false>)<<<grid_c, 256, smem, st>>>(
+                    scenes, views, cur, cnt_in, hq, qc + 3 * b, fetch + 2 * b, counters);
+            else
+                (count ? k_wclosest<true> : k_wclosest<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
+                    scenes, views, b, cur, cnt_in, n, hq, qc + 3 * b, tape, total, counters);
             mark(0, false);
             mark(1, true);
             k_wshade<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, b, M, hq, qc + 3 * b, nxt,
@@ -249,8 +414,12 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                                                                 counters);
             mark(1, false);
             mark(2, true);
-            (count ? k_wshadow<true> : k_wshadow<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
-                scenes, views, b, sq, qc + 3 * b + 2, tape, total, nvx, counters);
+            if (MR_REFILL)
+                (count ? k_wshadow_refill<true> : k_wshadow_refill<false>)<<<grid_s, 256, smem, st>>>(
+                    scenes, views, b, sq, qc + 3 * b + 2, fetch + 2 * b + 1, tape, total, nvx, counters);
+            else
+                (count ? k_wshadow<true> : k_wshadow<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
+                    scenes, views, b, sq, qc + 3 * b + 2, tape, total, nvx, counters);
             mark(2, false);
             QueueDev t = cur;
             cur = nxt;

@@ -21,7 +21,8 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_render_noalloc",
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
-           "mirres_get_work_counters",
+           "mirres_get_work_counters", "EawtParams", "mirres_eawt_record_bytes", "mirres_gbuffer", "mirres_eawt",
+           "mirres_eawt_backward",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
 
 # limits of mirres_render_noalloc (include/mirres.h)
@@ -60,6 +61,10 @@ class Params(C.Structure):
     _fields_ = [("ris_m", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("grad_mode", C.c_int32),
                 ("launch", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("flags", C.c_int32)]
+
+
+class EawtParams(C.Structure):
+    _fields_ = [("sigma_rt", C.c_float), ("sigma_n", C.c_float), ("sigma_x", C.c_float), ("levels", C.c_int32)]
 
 
 class Grads(C.Structure):
@@ -106,6 +111,10 @@ def lib():
                                          C.POINTER(vp), vp, sz, C.POINTER(Grads), vp]),
                 "mirres_l2_loss": (st, [vp, vp, i64, vp, vp, vp]),
                 "mirres_trace": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
+                "mirres_eawt_record_bytes": (sz, [i32, i32, i32]),
+                "mirres_gbuffer": (st, [vp, vp, C.POINTER(View), vp, vp, vp]),
+                "mirres_eawt": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, vp, sz, vp]),
+                "mirres_eawt_backward": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, sz, vp, vp]),
                 "mirres_bvh_export": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "mirres_env_export": (st, [vp, vp, vp, vp, vp, vp]),
                 "mirres_get_counters": (st, [vp, C.POINTER(C.c_uint64)]),
@@ -299,6 +308,32 @@ def mirres_l2_loss(image, ref, d_image=None, loss=None, stream=None):
 def mirres_trace(ctx: Context, scene: Scene, rays, hit_tri, hit_tuv=None, skip=None, any_hit=False, stream=None):
     _check("mirres_trace", lib().mirres_trace(ctx.handle, scene.handle, _ptr(rays), _ptr(skip), rays.shape[0],
                                               1 if any_hit else 0, _ptr(hit_tri), _ptr(hit_tuv), _stream(stream)))
+
+
+def mirres_eawt_record_bytes(width, height, levels) -> int:
+    return int(lib().mirres_eawt_record_bytes(int(width), int(height), int(levels)))
+
+
+def mirres_gbuffer(ctx: Context, scene: Scene, view, normal, position, stream=None):
+    """pixel-centre G-buffer of one view into [H][W][3] float32 CUDA tensors"""
+    vs = _views([view])
+    _check("mirres_gbuffer", lib().mirres_gbuffer(ctx.handle, scene.handle, vs, _ptr(normal), _ptr(position),
+                                                  _stream(stream)))
+
+
+def mirres_eawt(ctx: Context, image, normal, position, params: EawtParams, out, record, stream=None):
+    H, W = image.shape[0], image.shape[1]
+    _check("mirres_eawt", lib().mirres_eawt(ctx.handle, _ptr(image), _ptr(normal), _ptr(position), W, H,
+                                            C.byref(params), _ptr(out), _ptr(record),
+                                            record.numel() * record.element_size(), _stream(stream)))
+
+
+def mirres_eawt_backward(ctx: Context, d_out, normal, position, params: EawtParams, record, d_image, stream=None):
+    H, W = d_out.shape[0], d_out.shape[1]
+    _check("mirres_eawt_backward", lib().mirres_eawt_backward(ctx.handle, _ptr(d_out), _ptr(normal), _ptr(position),
+                                                              W, H, C.byref(params), _ptr(record),
+                                                              record.numel() * record.element_size(), _ptr(d_image),
+                                                              _stream(stream)))
 
 
 def mirres_bvh_export(scene: Scene, keys=None, left=None, right=None, parent=None, lo=None, hi=None, stream=None):
