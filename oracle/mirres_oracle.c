@@ -81,7 +81,7 @@ double orc_uniform(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 static double sub_hi(uint32_t x) { return ((double)(x >> 16) + 0.5) / 65536.0; }
 static double sub_lo(uint32_t x) { return ((double)(x & 0xFFFFu) + 0.5) / 65536.0; }
 
-enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2 };
+enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2, PURPOSE_REUSE = 3 };
 
 /* ---------------------------------------------------------------------------------------
  * scene, env tables, median-split BVH
@@ -953,6 +953,107 @@ static v3 camera_dir(const Ctx* c, int px, int py, int smp)
     return vnorm(d);
 }
 
+/* RIS at one shading point (Eq. restir, N = 1): M env candidates streamed through a weighted
+ * reservoir (Appendix A). Out: the selection (sel < 0: none), its direction, texel, f_r cos,
+ * p_hat, the weight sum and the number of candidates behind the reservoir (m). */
+typedef struct { int sel, ytex; v3 y; double f[3], phat, wsum; int m; } Ris;
+
+static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, v3 wo, Margin* mg, int64_t* cnt,
+                   Ris* r)
+{
+    const orc_scene* s = c->s;
+    const int M = c->p->ris_m, kind = c->p->brdf_kind;
+    Reservoir rs = {0.0, -1};
+    r->sel = -1; r->ytex = -1; r->y = V3(0, 0, 0); r->phat = 0.0; r->m = M;
+    r->f[0] = r->f[1] = r->f[2] = 0.0;
+    for (int j = 0; j < M; ++j) {
+        uint32_t x[4];
+        rng(c, pix, (uint32_t)smp, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j, x);
+        v3 dir;
+        int tex;
+        double q = env_sample_m(s, orc_uniform(x[0]), orc_uniform(x[1]), x[3], &dir, &tex, mg);
+        double fc[3];
+        brdf_cos(sh->n, wo, dir, sh->alb, sh->rgh, sh->met, kind, fc);
+        double phat = lum(s->env + 3 * tex) * lum(fc); /* p_hat = Y(L_env) Y(f_r) cos */
+        double gamma = phat / q;                      /* gamma_s = p_hat / q_dir */
+        double ua = orc_uniform(x[2]);
+        if (cnt) cnt[5]++;
+        if (wrs_update(&rs, gamma, ua, j)) {
+            r->y = dir; r->ytex = tex; r->phat = phat;
+            for (int k = 0; k < 3; ++k) r->f[k] = fc[k];
+        }
+        if (gamma > 0.0) note(mg, fabs(ua * rs.wsum - gamma) / rs.wsum / TAU_ACC, MK_ACC);
+    }
+    r->sel = rs.sel;
+    r->wsum = rs.wsum;
+}
+
+/* the primary vertex's RIS reservoir of sample smp of pixel (qx, qy): 0 if its ray escapes */
+static int primary_reservoir(const Ctx* c, int qx, int qy, int smp, Margin* mg, int64_t* cnt, Ris* r)
+{
+    const orc_scene* s = c->s;
+    v3 o = vload(c->o), d = camera_dir(c, qx, qy, smp);
+    Hit h;
+    bvh_closest(s, o, d, -1, &h, cnt);
+    closest_margins(s, o, d, -1, &h, mg);
+    if (h.tri < 0) return 0;
+    Shade sh;
+    shade_at(s, h.tri, h.u, h.v, h.t, d, &sh, mg);
+    ris_at(c, (uint32_t)(qy * c->v->width + qx), smp, 0, &sh, vscale(d, -1.0), mg, cnt, r);
+    return 1;
+}
+
+/* Spatial reuse at the primary vertex (Appendix A, "Spatial-temporal Reuse": reservoirs of
+ * neighbouring pixels merged into the pixel's own). Reading: reuse_k neighbours of the same
+ * sample index, pixel offsets drawn uniformly from the (2 r + 1)^2 square (the pixel itself
+ * and pixels outside the image skipped; a neighbour whose primary ray escapes has no
+ * reservoir). Reservoirs are merged by the standard resampling rule: each enters with weight
+ * p_hat_here(y_i) W_i m_i, W_i = w_sum_i / (m_i p_hat_i(y_i)), i.e. p_hat_here(y_i) w_sum_i /
+ * p_hat_i(y_i), streamed through a reservoir (the pixel's own first), and the merged
+ * reservoir counts sum m_i candidates; W = w_sum / (m p_hat_here(y)). The paper gives no MIS
+ * weights, so this is the biased 1/m combination. */
+static void spatial_reuse(const Ctx* c, int px, int py, int smp, const Shade* sh, v3 wo, Margin* mg, int64_t* cnt,
+                          Ris* r)
+{
+    const orc_scene* s = c->s;
+    const int K = c->p->reuse_k, R = c->p->reuse_radius, kind = c->p->brdf_kind;
+    const uint32_t pix = (uint32_t)(py * c->v->width + px);
+    Ris out = *r;
+    out.wsum = 0.0;
+    out.sel = -1;
+    out.m = r->m;
+    if (r->sel >= 0 && r->wsum > 0.0) {
+        double w = r->phat * r->wsum / r->phat; /* own reservoir: p_hat_here = p_hat_own */
+        out.wsum = w;
+        out.sel = r->sel;
+    }
+    for (int j = 0; j < K; ++j) {
+        uint32_t x[4];
+        rng(c, pix, (uint32_t)smp, 0, PURPOSE_REUSE, (uint32_t)j, x);
+        int dx = (int)floor(orc_uniform(x[0]) * (2 * R + 1)) - R;
+        int dy = (int)floor(orc_uniform(x[1]) * (2 * R + 1)) - R;
+        int qx = px + dx, qy = py + dy;
+        if ((dx == 0 && dy == 0) || qx < 0 || qy < 0 || qx >= c->v->width || qy >= c->v->height) continue;
+        Ris nb;
+        if (!primary_reservoir(c, qx, qy, smp, mg, cnt, &nb)) continue;
+        out.m += nb.m;
+        if (nb.sel < 0 || !(nb.wsum > 0.0)) continue;
+        double fc[3];
+        brdf_cos(sh->n, wo, nb.y, sh->alb, sh->rgh, sh->met, kind, fc);
+        double phat = lum(s->env + 3 * nb.ytex) * lum(fc);
+        double w = phat * nb.wsum / nb.phat;
+        out.wsum += w;
+        double u = orc_uniform(x[2]);
+        if (u * out.wsum < w) {
+            out.sel = c->p->ris_m * (j + 1) + nb.sel;
+            out.y = nb.y; out.ytex = nb.ytex; out.phat = phat;
+            for (int k = 0; k < 3; ++k) out.f[k] = fc[k];
+        }
+        if (w > 0.0) note(mg, fabs(u * out.wsum - w) / out.wsum / TAU_ACC, MK_ACC);
+    }
+    *r = out;
+}
+
 static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin* mg, int64_t* cnt)
 {
     const orc_scene* s = c->s;
@@ -990,38 +1091,19 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         /* ---- direct light: RIS over M env candidates, streamed through a reservoir ---- */
         double direct[3] = {0, 0, 0};
         if (s->env_ok && M > 0) {
-            Reservoir rs = {0.0, -1};
-            v3 ysel = V3(0, 0, 0);
-            int ytex = -1;
-            double fsel[3] = {0, 0, 0}, phat_sel = 0.0;
-            for (int j = 0; j < M; ++j) {
-                uint32_t x[4];
-                rng(c, pix, (uint32_t)smp, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j, x);
-                v3 dir;
-                int tex;
-                double q = env_sample_m(s, orc_uniform(x[0]), orc_uniform(x[1]), x[3], &dir, &tex, mg);
-                double fc[3];
-                brdf_cos(sh.n, wo, dir, sh.alb, sh.rgh, sh.met, kind, fc);
-                double phat = lum(s->env + 3 * tex) * lum(fc); /* p_hat = Y(L_env) Y(f_r) cos */
-                double gamma = phat / q;                      /* gamma_s = p_hat / q_dir */
-                double ua = orc_uniform(x[2]);
-                if (cnt) cnt[5]++;
-                if (wrs_update(&rs, gamma, ua, j)) {
-                    ysel = dir; ytex = tex; phat_sel = phat;
-                    for (int k = 0; k < 3; ++k) fsel[k] = fc[k];
-                }
-                if (gamma > 0.0) note(mg, fabs(ua * rs.wsum - gamma) / rs.wsum / TAU_ACC, MK_ACC);
-            }
-            if (rs.sel >= 0 && rs.wsum > 0.0) {
-                /* Eq. restir with N = 1: f(y) / p_hat(y) * (1/M) sum gamma */
-                double W = rs.wsum / (M * phat_sel);
+            Ris r;
+            ris_at(c, pix, smp, b, &sh, wo, mg, cnt, &r);
+            if (b == 0 && c->p->reuse_k > 0) spatial_reuse(c, px, py, smp, &sh, wo, mg, cnt, &r);
+            if (r.sel >= 0 && r.wsum > 0.0) {
+                /* Eq. restir with N = 1: f(y) / p_hat(y) * (1/m) sum gamma */
+                double W = r.wsum / (r.m * r.phat);
                 if (cnt) cnt[2]++;
-                int occluded = bvh_any(s, sh.x, ysel, sh.tri, cnt, mg);
+                int occluded = bvh_any(s, sh.x, r.y, sh.tri, cnt, mg);
                 double V = occluded ? 0.0 : 1.0;
-                for (int k = 0; k < 3; ++k) direct[k] = V * W * s->env[3 * ytex + k] * fsel[k];
-                if (b == 0) { rec->sel = rs.sel; rec->y = ysel; rec->y_texel = ytex; rec->WV = V * W; }
+                for (int k = 0; k < 3; ++k) direct[k] = V * W * s->env[3 * r.ytex + k] * r.f[k];
+                if (b == 0) { rec->sel = r.sel; rec->y = r.y; rec->y_texel = r.ytex; rec->WV = V * W; }
                 if (b < ORC_MAXB) {
-                    rec->vx[b].sel = rs.sel; rec->vx[b].y = ysel; rec->vx[b].y_texel = ytex; rec->vx[b].WV = V * W;
+                    rec->vx[b].sel = r.sel; rec->vx[b].y = r.y; rec->vx[b].y_texel = r.ytex; rec->vx[b].WV = V * W;
                 }
             }
         }
@@ -1383,6 +1465,7 @@ static int run_jobs(int mode, const orc_scene* s, const orc_scene* ev, const orc
 {
     if (!s || !v || !p || v->width < 1 || v->height < 1 || v->spp < 1 || v->bounces < 1 || p->ris_m < 0) return 1;
     if (p->grad_mode != 0 && (p->grad_mode != 1 || v->bounces > ORC_MAXB)) return 1;
+    if (p->reuse_k < 0 || p->reuse_radius < 0 || (p->reuse_k > 0 && p->reuse_radius < 1)) return 1;
     if (!pixels) n = v->width * v->height;
     for (int i = 0; pixels && i < n; ++i)
         if (pixels[i] < 0 || pixels[i] >= v->width * v->height) return 1;

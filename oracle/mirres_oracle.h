@@ -51,6 +51,8 @@ typedef struct {
     int32_t threads;     /* worker threads (>= 1) */
     int32_t want_margin; /* 1: track decision margins */
     int32_t grad_mode;   /* 0 = PRIMARY (the paper's); 1 = FULL (every vertex, at most ORC_MAXB) */
+    int32_t reuse_k;      /* spatial reuse at the primary vertex: neighbouring reservoirs merged (0 = none) */
+    int32_t reuse_radius; /* ... drawn from the (2 r + 1)^2 pixel square around the pixel */
 } orc_params;
 
 /* vertices per path recorded for the FULL-mode adjoint */

@@ -51,7 +51,7 @@ class View(C.Structure):
 class Params(C.Structure):
     _fields_ = [("ris_m", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32),
                 ("brdf_kind", C.c_int32), ("threads", C.c_int32), ("want_margin", C.c_int32),
-                ("grad_mode", C.c_int32)]
+                ("grad_mode", C.c_int32), ("reuse_k", C.c_int32), ("reuse_radius", C.c_int32)]
 
 
 GRAD_FIELDS = ("albedo", "roughness", "metallic", "env", "verts", "albedo_abs", "roughness_abs", "metallic_abs",
@@ -153,15 +153,15 @@ def make_view(view, index):
                 int(view.width), int(view.height), int(view.spp), int(view.bounces), int(index))
 
 
-def make_params(ris_m, seed=0, threads=None, brdf_kind=0, want_margin=1, grad_mode=0):
+def make_params(ris_m, seed=0, threads=None, brdf_kind=0, want_margin=1, grad_mode=0, reuse=(0, 0)):
     if threads is None:
         threads = os.cpu_count() or 1
     return Params(int(ris_m), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(brdf_kind), int(threads),
-                  int(want_margin), int(grad_mode))
+                  int(want_margin), int(grad_mode), int(reuse[0]), int(reuse[1]))
 
 
 def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind=0, margins=True,
-           prim=False):
+           prim=False, reuse=(0, 0)):
     """Render pixels of one view. Returns dict(rgb [n,3], margin [n], prim [n,spp], counts [8])."""
     L = lib()
     n = view.width * view.height if pixels is None else len(pixels)
@@ -171,7 +171,7 @@ def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind
     pr = np.zeros((n, view.spp), dtype=np.int32) if prim else None
     cnt = np.zeros(8, dtype=np.int64)
     v = make_view(view, index)
-    p = make_params(ris_m, seed, threads, brdf_kind, int(margins))
+    p = make_params(ris_m, seed, threads, brdf_kind, int(margins), reuse=reuse)
     rc = L.orc_render(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(rgb), _p(mg), _p(pr), _p(cnt))
     if rc:
         raise ValueError("orc_render rejected its arguments")
@@ -180,7 +180,7 @@ def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind
 
 
 def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, brdf_kind=0, want_abs=True,
-             grad_mode=0):
+             grad_mode=0, reuse=(0, 0)):
     """Adjoint of the listed pixels (grad_mode 0 PRIMARY, 1 FULL); returns dict of FP64
     gradients (and abs-sums)."""
     L = lib()
@@ -198,7 +198,7 @@ def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, 
     g = Grads(*[_p(out.get(k)) for k in GRAD_FIELDS])
     cnt = np.zeros(8, dtype=np.int64)
     v = make_view(view, index)
-    p = make_params(ris_m, seed, threads, brdf_kind, 0, grad_mode)
+    p = make_params(ris_m, seed, threads, brdf_kind, 0, grad_mode, reuse)
     rc = L.orc_backward(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(d), C.byref(g), _p(cnt))
     if rc:
         raise ValueError("orc_backward rejected its arguments")
@@ -207,13 +207,13 @@ def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, 
 
 
 def render_detached(frozen, evaled, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind=0,
-                    grad_mode=0):
+                    grad_mode=0, reuse=(0, 0)):
     L = lib()
     n = view.width * view.height if pixels is None else len(pixels)
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
     rgb = np.zeros((n, 3))
     v = make_view(view, index)
-    p = make_params(ris_m, seed, threads, brdf_kind, 0, grad_mode)
+    p = make_params(ris_m, seed, threads, brdf_kind, 0, grad_mode, reuse)
     rc = L.orc_render_detached(frozen.h, evaled.h, C.byref(v), C.byref(p), _p(pix), n, _p(rgb))
     if rc:
         raise ValueError("orc_render_detached rejected its arguments")
