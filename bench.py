@@ -393,9 +393,9 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
 
     # the denoiser between image and loss (EAWT, Appendix A), every view: G-buffer, forward and
-    # adjoint; HBM-bound stencils (taps hit L1/L2), algorithmic bytes per pixel: forward 24 (input
-    # copy) + 3 x 52 (colour, normal, position in; colour, normaliser out), adjoint 3 x 64
-    # (gradient, recorded colour, normaliser, normal, position in; gradient out)
+    # adjoint; HBM-bound stencils (taps hit L1/L2). Algorithmic bytes per pixel: forward 108 (pack
+    # image, normal, position: 36 in, 48 out) + 3 levels x (48 in, 20 out) - 4 (the last level
+    # writes 12-byte colour), adjoint 28 (pack the gradient) + 3 levels x (52 in, 16 out) - 4
     eawt = None
     if not args.no_eawt:
         ep = M.EawtParams(EAWT_SIGMAS[0], EAWT_SIGMAS[1], EAWT_SIGMAS[2], 3)
@@ -430,7 +430,7 @@ def main():
         pix = sum(v.width * v.height for v in gw.views)
         ms_all = e_all[0].elapsed_time(e_all[1]) / args.steps
         ms_dn = e_dn[0].elapsed_time(e_dn[1])  # the last pass
-        bytes_px = 24 + 3 * 52 + 3 * 64
+        bytes_px = (84 + 3 * 68 - 4) + (28 + 3 * 68 - 4)
         ach = pix * bytes_px / (ms_dn / 1e3) / 1e9
         eawt = {"mpix_per_s": pix / (ms_all / 1e3) / 1e6, "ms_per_step": ms_all,
                 "ms_denoise_fwd_bwd": ms_dn, "pixels": pix, "levels": 3, "sigmas": list(EAWT_SIGMAS),

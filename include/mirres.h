@@ -303,8 +303,9 @@ typedef struct {
     int32_t levels;                    /* 1 .. MIRRES_EAWT_MAX_LEVELS */
 } mirres_eawt_params;
 
-/* Bytes of the record mirres_eawt writes for mirres_eawt_backward: 16 * levels * width * height
- * (each level's input image and normaliser). 0 for invalid arguments. */
+/* Bytes of the record mirres_eawt writes for mirres_eawt_backward: (32 + 20 * levels) * width *
+ * height (the packed G-buffer, each level's input image and normaliser). 0 for invalid
+ * arguments. The record must be 16-byte aligned. */
 size_t mirres_eawt_record_bytes(int32_t width, int32_t height, int32_t levels);
 
 /* G-buffer of one view: the primary hit through each pixel centre (camera as in mirres_render,

@@ -779,7 +779,7 @@ static mirres_status check_eawt(int32_t width, int32_t height, const mirres_eawt
 extern "C" size_t mirres_eawt_record_bytes(int32_t width, int32_t height, int32_t levels)
 {
     if (width < 1 || height < 1 || levels < 1 || levels > MIRRES_EAWT_MAX_LEVELS) return 0;
-    return (size_t)16 * (size_t)levels * (size_t)width * (size_t)height;
+    return ((size_t)32 + (size_t)20 * (size_t)levels) * (size_t)width * (size_t)height;
 }
 
 extern "C" mirres_status mirres_gbuffer(mirres_context* ctx, const mirres_scene* scene, const mirres_view* view,
@@ -802,7 +802,19 @@ extern "C" mirres_status mirres_gbuffer(mirres_context* ctx, const mirres_scene*
     return MIRRES_OK;
 }
 
-// record layout: levels x [H][W][3] level inputs c_i, then levels x [H][W] normalisers k_i
+// record layout (16-byte aligned): packed normal and position [H][W] float4, the levels' inputs
+// c_i [levels][H][W] float4, their normalisers k_i [levels][H][W] float
+struct EawtRecord {
+    float4 *n, *x, *c;
+    float* k;
+};
+
+static EawtRecord eawt_record(void* base, size_t npx, int L)
+{
+    float4* f = reinterpret_cast<float4*>(base);
+    return EawtRecord{f, f + npx, f + 2 * npx, reinterpret_cast<float*>(f + (2 + (size_t)L) * npx)};
+}
+
 extern "C" mirres_status mirres_eawt(mirres_context* ctx, const float* image, const float* normal,
                                      const float* position, int32_t width, int32_t height,
                                      const mirres_eawt_params* params, float* out, void* record,
@@ -813,23 +825,26 @@ extern "C" mirres_status mirres_eawt(mirres_context* ctx, const float* image, co
     MR_TRY(check_eawt(width, height, params));
     if (record_bytes < mirres_eawt_record_bytes(width, height, params->levels))
         return arg_error("record_bytes is smaller than mirres_eawt_record_bytes");
+    if (reinterpret_cast<uintptr_t>(record) & 15) return arg_error("record must be 16-byte aligned");
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
     const size_t npx = (size_t)width * height;
-    const int L = params->levels;
-    float* c = reinterpret_cast<float*>(record);
-    float* k = c + 3 * npx * (size_t)L;
-    MR_CUDA(cudaMemcpyAsync(c, image, sizeof(float) * 3 * npx, cudaMemcpyDeviceToDevice, st));
+    const int L = params->levels, sms = ctx->sm_count;
+    const EawtRecord r = eawt_record(record, npx, L);
+    mr_launch_eawt_pack(normal, r.n, (int64_t)npx, sms, st);
+    mr_launch_eawt_pack(position, r.x, (int64_t)npx, sms, st);
+    mr_launch_eawt_pack(image, r.c, (int64_t)npx, sms, st);
     const float in2 = 1.0f / (params->sigma_n * params->sigma_n), ix2 = 1.0f / (params->sigma_x * params->sigma_x);
     for (int i = 0; i < L; ++i) {
         const int step = 1 << i;
         const float srt = params->sigma_rt / (float)step;
-        float* dst = (i + 1 < L) ? c + 3 * npx * (size_t)(i + 1) : out;
-        mr_launch_eawt_level(c + 3 * npx * (size_t)i, normal, position, width, height, step, 1.0f / (srt * srt), in2,
-                             ix2, dst, k + npx * (size_t)i, ctx->sm_count, st);
+        const bool last = i + 1 == L;
+        mr_launch_eawt_level(r.c + npx * (size_t)i, r.n, r.x, width, height, step, 1.0f / (srt * srt), in2, ix2,
+                             last ? nullptr : r.c + npx * (size_t)(i + 1), last ? out : nullptr, r.k + npx * (size_t)i,
+                             sms, st);
     }
     MR_CUDA(cudaGetLastError());
-    ctx->host_launches += (unsigned long long)L;
+    ctx->host_launches += (unsigned long long)L + 3;
     return MIRRES_OK;
 }
 
@@ -843,26 +858,27 @@ extern "C" mirres_status mirres_eawt_backward(mirres_context* ctx, const float* 
     MR_TRY(check_eawt(width, height, params));
     if (record_bytes < mirres_eawt_record_bytes(width, height, params->levels))
         return arg_error("record_bytes is smaller than mirres_eawt_record_bytes");
+    if (reinterpret_cast<uintptr_t>(record) & 15) return arg_error("record must be 16-byte aligned");
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
     const size_t npx = (size_t)width * height;
-    const int L = params->levels;
-    MR_TRY(ws_reserve(ctx, sizeof(float) * 6 * npx + 256));
-    float* tmp[2] = {reinterpret_cast<float*>(ctx->ws.ptr), reinterpret_cast<float*>(ctx->ws.ptr) + 3 * npx};
-    const float* c = reinterpret_cast<const float*>(record);
-    const float* k = c + 3 * npx * (size_t)L;
+    const int L = params->levels, sms = ctx->sm_count;
+    MR_TRY(ws_reserve(ctx, sizeof(float4) * 2 * npx + 256));
+    float4* tmp[2] = {reinterpret_cast<float4*>(ctx->ws.ptr), reinterpret_cast<float4*>(ctx->ws.ptr) + npx};
+    const EawtRecord r = eawt_record(const_cast<void*>(record), npx, L);
     const float in2 = 1.0f / (params->sigma_n * params->sigma_n), ix2 = 1.0f / (params->sigma_x * params->sigma_x);
-    const float* g = d_out;
+    mr_launch_eawt_pack(d_out, tmp[0], (int64_t)npx, sms, st);
+    int cur = 0;
     for (int i = L - 1; i >= 0; --i) {
         const int step = 1 << i;
         const float srt = params->sigma_rt / (float)step;
-        float* dst = (i == 0) ? d_image : tmp[i & 1];
-        mr_launch_eawt_level_adjoint(g, c + 3 * npx * (size_t)i, k + npx * (size_t)i, normal, position, width, height,
-                                     step, 1.0f / (srt * srt), in2, ix2, dst, ctx->sm_count, st);
-        g = dst;
+        mr_launch_eawt_level_adjoint(tmp[cur], r.c + npx * (size_t)i, r.k + npx * (size_t)i, r.n, r.x, width, height,
+                                     step, 1.0f / (srt * srt), in2, ix2, i == 0 ? nullptr : tmp[cur ^ 1],
+                                     i == 0 ? d_image : nullptr, sms, st);
+        cur ^= 1;
     }
     MR_CUDA(cudaGetLastError());
-    ctx->host_launches += (unsigned long long)L;
+    ctx->host_launches += (unsigned long long)L + 1;
     return MIRRES_OK;
 }
 

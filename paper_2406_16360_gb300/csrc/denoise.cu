@@ -13,29 +13,42 @@ namespace {
 
 __constant__ float kB3[5] = {1.0f / 16.0f, 4.0f / 16.0f, 6.0f / 16.0f, 4.0f / 16.0f, 1.0f / 16.0f};
 
-__device__ __forceinline__ float3 ld3(const float* a, size_t i)
+// The level kernels read packed float4 images (colour / normal / position in .xyz): one
+// 16-byte load per buffer and tap instead of three scalar loads.
+__global__ void __launch_bounds__(256) k_eawt_pack(const float* __restrict__ a, float4* __restrict__ out, int64_t npx)
 {
-    return f3(__ldg(a + 3 * i), __ldg(a + 3 * i + 1), __ldg(a + 3 * i + 2));
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = make_float4(__ldg(a + 3 * p), __ldg(a + 3 * p + 1), __ldg(a + 3 * p + 2), 0.0f);
 }
 
-__device__ __forceinline__ float d2(float3 a, float3 b)
+__device__ __forceinline__ float d2(float4 a, float4 b)
 {
     const float x = a.x - b.x, y = a.y - b.y, z = a.z - b.z;
     return x * x + y * y + z * z;
 }
 
-// forward level: cin -> cout, and the normaliser k
-__global__ void __launch_bounds__(256) k_eawt_level(const float* __restrict__ cin, const float* __restrict__ nrm,
-                                                    const float* __restrict__ pos, int W, int H, int step,
-                                                    float inv_rt2, float inv_n2, float inv_x2, float* __restrict__ cout,
-                                                    float* __restrict__ kout)
+__device__ __forceinline__ void store(float4* o4, float* o3, int64_t p, float x, float y, float z)
+{
+    if (o3) {
+        o3[3 * p] = x;
+        o3[3 * p + 1] = y;
+        o3[3 * p + 2] = z;
+    } else {
+        o4[p] = make_float4(x, y, z, 0.0f);
+    }
+}
+
+// forward level: cin -> cout (packed, or [H][W][3] when out3 is given), and the normaliser k
+__global__ void __launch_bounds__(256) k_eawt_level(const float4* __restrict__ cin, const float4* __restrict__ nrm,
+                                                    const float4* __restrict__ pos, int W, int H, int step,
+                                                    float inv_rt2, float inv_n2, float inv_x2, float4* __restrict__ cout,
+                                                    float* __restrict__ out3, float* __restrict__ kout)
 {
     const int64_t npx = (int64_t)W * H;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(p / W), x = (int)(p % W);
-        const float3 cp = ld3(cin, (size_t)p), np_ = ld3(nrm, (size_t)p), xp = ld3(pos, (size_t)p);
-        float3 acc = f3(0.f, 0.f, 0.f);
-        float k = 0.0f;
+        const float4 cp = __ldg(cin + p), np_ = __ldg(nrm + p), xp = __ldg(pos + p);
+        float ax = 0.f, ay = 0.f, az = 0.f, k = 0.f;
         for (int a = 0; a < 5; ++a) {
             const int qy = y + (a - 2) * step;
             if (qy < 0 || qy >= H) continue;
@@ -43,35 +56,35 @@ __global__ void __launch_bounds__(256) k_eawt_level(const float* __restrict__ ci
             for (int b = 0; b < 5; ++b) {
                 const int qx = x + (b - 2) * step;
                 if (qx < 0 || qx >= W) continue;
-                const size_t q = (size_t)qy * W + qx;
-                const float3 cq = ld3(cin, q);
-                const float e = d2(cp, cq) * inv_rt2 + d2(np_, ld3(nrm, q)) * inv_n2 + d2(xp, ld3(pos, q)) * inv_x2;
+                const int64_t q = (int64_t)qy * W + qx;
+                const float4 cq = __ldg(cin + q);
+                const float e = d2(cp, cq) * inv_rt2 + d2(np_, __ldg(nrm + q)) * inv_n2 + d2(xp, __ldg(pos + q)) * inv_x2;
                 const float w = kB3[a] * kB3[b] * __expf(-e);
-                acc = f3(acc.x + w * cq.x, acc.y + w * cq.y, acc.z + w * cq.z);
+                ax += w * cq.x;
+                ay += w * cq.y;
+                az += w * cq.z;
                 k += w;
             }
         }
         const float ik = 1.0f / k;  // k >= (6/16)^2: the centre tap has weight 1
-        cout[3 * p] = acc.x * ik;
-        cout[3 * p + 1] = acc.y * ik;
-        cout[3 * p + 2] = acc.z * ik;
+        store(cout, out3, p, ax * ik, ay * ik, az * ik);
         kout[p] = k;
     }
 }
 
 // adjoint level: gout(q) = sum over taps of h w(q, q + tap) gin(q + tap) / k(q + tap), the
 // weights recomputed from the level's recorded input c
-__global__ void __launch_bounds__(256) k_eawt_level_adjoint(const float* __restrict__ gin, const float* __restrict__ c,
-                                                            const float* __restrict__ kin, const float* __restrict__ nrm,
-                                                            const float* __restrict__ pos, int W, int H, int step,
+__global__ void __launch_bounds__(256) k_eawt_level_adjoint(const float4* __restrict__ gin, const float4* __restrict__ c,
+                                                            const float* __restrict__ kin, const float4* __restrict__ nrm,
+                                                            const float4* __restrict__ pos, int W, int H, int step,
                                                             float inv_rt2, float inv_n2, float inv_x2,
-                                                            float* __restrict__ gout)
+                                                            float4* __restrict__ gout, float* __restrict__ out3)
 {
     const int64_t npx = (int64_t)W * H;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(p / W), x = (int)(p % W);
-        const float3 cp = ld3(c, (size_t)p), np_ = ld3(nrm, (size_t)p), xp = ld3(pos, (size_t)p);
-        float3 acc = f3(0.f, 0.f, 0.f);
+        const float4 cp = __ldg(c + p), np_ = __ldg(nrm + p), xp = __ldg(pos + p);
+        float ax = 0.f, ay = 0.f, az = 0.f;
         for (int a = 0; a < 5; ++a) {
             const int qy = y + (a - 2) * step;
             if (qy < 0 || qy >= H) continue;
@@ -79,16 +92,16 @@ __global__ void __launch_bounds__(256) k_eawt_level_adjoint(const float* __restr
             for (int b = 0; b < 5; ++b) {
                 const int qx = x + (b - 2) * step;
                 if (qx < 0 || qx >= W) continue;
-                const size_t q = (size_t)qy * W + qx;
-                const float e = d2(cp, ld3(c, q)) * inv_rt2 + d2(np_, ld3(nrm, q)) * inv_n2 + d2(xp, ld3(pos, q)) * inv_x2;
+                const int64_t q = (int64_t)qy * W + qx;
+                const float e = d2(cp, __ldg(c + q)) * inv_rt2 + d2(np_, __ldg(nrm + q)) * inv_n2 + d2(xp, __ldg(pos + q)) * inv_x2;
                 const float w = kB3[a] * kB3[b] * __expf(-e) / __ldg(kin + q);
-                const float3 g = ld3(gin, q);
-                acc = f3(acc.x + w * g.x, acc.y + w * g.y, acc.z + w * g.z);
+                const float4 g = __ldg(gin + q);
+                ax += w * g.x;
+                ay += w * g.y;
+                az += w * g.z;
             }
         }
-        gout[3 * p] = acc.x;
-        gout[3 * p + 1] = acc.y;
-        gout[3 * p + 2] = acc.z;
+        store(gout, out3, p, ax, ay, az);
     }
 }
 
@@ -132,19 +145,24 @@ unsigned grid_for_pixels(int64_t n, int sms)
 
 }  // namespace
 
-void mr_launch_eawt_level(const float* cin, const float* nrm, const float* pos, int W, int H, int step, float inv_rt2,
-                          float inv_n2, float inv_x2, float* cout, float* kout, int sms, cudaStream_t st)
+void mr_launch_eawt_pack(const float* a, float4* out, int64_t npx, int sms, cudaStream_t st)
 {
-    k_eawt_level<<<grid_for_pixels((int64_t)W * H, sms), 256, 0, st>>>(cin, nrm, pos, W, H, step, inv_rt2, inv_n2,
-                                                                      inv_x2, cout, kout);
+    k_eawt_pack<<<grid_for_pixels(npx, sms), 256, 0, st>>>(a, out, npx);
 }
 
-void mr_launch_eawt_level_adjoint(const float* gin, const float* c, const float* kin, const float* nrm, const float* pos,
-                                  int W, int H, int step, float inv_rt2, float inv_n2, float inv_x2, float* gout, int sms,
-                                  cudaStream_t st)
+void mr_launch_eawt_level(const float4* cin, const float4* nrm, const float4* pos, int W, int H, int step, float inv_rt2,
+                          float inv_n2, float inv_x2, float4* cout, float* out3, float* kout, int sms, cudaStream_t st)
+{
+    k_eawt_level<<<grid_for_pixels((int64_t)W * H, sms), 256, 0, st>>>(cin, nrm, pos, W, H, step, inv_rt2, inv_n2,
+                                                                      inv_x2, cout, out3, kout);
+}
+
+void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const float* kin, const float4* nrm,
+                                  const float4* pos, int W, int H, int step, float inv_rt2, float inv_n2, float inv_x2,
+                                  float4* gout, float* out3, int sms, cudaStream_t st)
 {
     k_eawt_level_adjoint<<<grid_for_pixels((int64_t)W * H, sms), 256, 0, st>>>(gin, c, kin, nrm, pos, W, H, step,
-                                                                              inv_rt2, inv_n2, inv_x2, gout);
+                                                                              inv_rt2, inv_n2, inv_x2, gout, out3);
 }
 
 void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* pos, int sms, cudaStream_t st)

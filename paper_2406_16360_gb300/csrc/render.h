@@ -63,11 +63,12 @@ void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* s
                           int32_t* hit_tri, float* hit_tuv, int sms, cudaStream_t st);
 
 // denoise.cu: EAWT levels, their adjoints, the pixel-centre G-buffer
-void mr_launch_eawt_level(const float* cin, const float* nrm, const float* pos, int W, int H, int step, float inv_rt2,
-                          float inv_n2, float inv_x2, float* cout, float* kout, int sms, cudaStream_t st);
-void mr_launch_eawt_level_adjoint(const float* gin, const float* c, const float* kin, const float* nrm, const float* pos,
-                                  int W, int H, int step, float inv_rt2, float inv_n2, float inv_x2, float* gout, int sms,
-                                  cudaStream_t st);
+void mr_launch_eawt_pack(const float* a, float4* out, int64_t npx, int sms, cudaStream_t st);
+void mr_launch_eawt_level(const float4* cin, const float4* nrm, const float4* pos, int W, int H, int step, float inv_rt2,
+                          float inv_n2, float inv_x2, float4* cout, float* out3, float* kout, int sms, cudaStream_t st);
+void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const float* kin, const float4* nrm,
+                                  const float4* pos, int W, int H, int step, float inv_rt2, float inv_n2, float inv_x2,
+                                  float4* gout, float* out3, int sms, cudaStream_t st);
 void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* pos, int sms, cudaStream_t st);
 
 // wave.cu: the batched wavefront forward (recorded on a stream, captured as a graph)

@@ -122,5 +122,5 @@ def test_eawt_argument_checks(M, ctx):
     small = torch.empty(8, device="cuda")
     with pytest.raises(M.MirresError):
         M.mirres_eawt(ctx, img, img, img, M.EawtParams(1.0, 1.0, 1.0, 3), img.clone(), small)
-    assert M.mirres_eawt_record_bytes(4, 4, 3) == 16 * 3 * 16
+    assert M.mirres_eawt_record_bytes(4, 4, 3) == (32 + 20 * 3) * 16
     assert M.mirres_eawt_record_bytes(0, 4, 3) == 0
