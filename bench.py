@@ -8,7 +8,8 @@ textures, env map and vertices. Metric: forward+backward path samples per second
 sample = one pixel sample of one view), for the batched launch (every view in one
 graph-captured wavefront: the headline value), the plain per-view wavefront launch and the
 single persistent kernel; Mrays/s alongside. The same step with the FULL-mode adjoint
-(gradients through every vertex) is reported as `full_adjoint` when its tape fits.
+(gradients through every vertex) is reported as `full_adjoint` when its tape fits, the step with
+spatial reservoir reuse as `spatial_reuse`, and the denoiser as `denoiser`.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config3|config5|config2]
   python bench.py --impl reference ...   (the CPU oracle on the host cores, bounded sample)
@@ -30,6 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd path-samples/s (batched launch; plain per-view launch and Mrays/s alongside)"
 # denoiser sigmas (colour, normal, position) of the EAWT arm, and the measured HBM copy rate
 EAWT_SIGMAS = (0.5, 0.3, 0.2)
+# spatial reuse arm: neighbours merged per pixel and the radius they are drawn from
+REUSE = (4, 8)
 
 
 def _hbm_peak():
@@ -219,6 +222,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-full", action="store_true", help="skip the FULL-mode adjoint arm")
     ap.add_argument("--no-eawt", action="store_true", help="skip the denoiser arm")
+    ap.add_argument("--no-reuse", action="store_true", help="skip the spatial-reuse arm")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -275,14 +279,15 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def step(launch, ev_render=None, ev_bwd=None, grad_mode=0):
+    def step(launch, ev_render=None, ev_bwd=None, grad_mode=0, reuse=(0, 0)):
         for s in gw.scenes:
             M.mirres_bvh_build(s.handle)
         if ev_render is not None:
             ev_render[0].record()
         # the batched wavefront records stage events (graph event nodes) for the roofline
         M.mirres_render(gw.ctx, scenes, gw.views, gw.params(launch, block=args.block, blocks_per_sm=args.blocks_per_sm,
-                                                            flags=1 if launch == 1 else 0, grad_mode=grad_mode),
+                                                            flags=1 if launch == 1 else 0, grad_mode=grad_mode,
+                                                            reuse=reuse),
                         images, tape)
         if ev_render is not None:
             ev_render[1].record()
@@ -290,7 +295,8 @@ def main():
             M.mirres_l2_loss(img, ref, d, loss)
         if ev_bwd is not None:
             ev_bwd[0].record()
-        M.mirres_backward(gw.ctx, scenes, gw.views, gw.params(launch, grad_mode=grad_mode), d_images, tape, grads)
+        M.mirres_backward(gw.ctx, scenes, gw.views, gw.params(launch, grad_mode=grad_mode, reuse=reuse), d_images,
+                          tape, grads)
         if ev_bwd is not None:
             ev_bwd[1].record()
 
@@ -300,10 +306,10 @@ def main():
                 t.zero_()
         loss.zero_()
 
-    def timed(launch, steps, warmup, grad_mode=0):
+    def timed(launch, steps, warmup, grad_mode=0, reuse=(0, 0)):
         for _ in range(warmup):
             zero()
-            step(launch, grad_mode=grad_mode)
+            step(launch, grad_mode=grad_mode, reuse=reuse)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -315,7 +321,7 @@ def main():
             flush.fill_(float(i))  # evict L2 between timed steps (outside the timed window)
             zero()
             evs[i][0].record()
-            step(launch, evr[i], evg[i], grad_mode=grad_mode)
+            step(launch, evr[i], evg[i], grad_mode=grad_mode, reuse=reuse)
             evs[i][1].record()
         torch.cuda.synchronize()
         barrier()
@@ -450,6 +456,16 @@ def main():
     elif not args.no_full:
         full = {"skipped": f"FULL tape of {full_bytes / 2**30:.1f} GiB does not fit next to the workload"}
 
+    # spatial reservoir reuse at the primary vertex (Appendix A), REUSE neighbours in a square of
+    # radius REUSE_RADIUS: the same step
+    reuse_arm = None
+    if not args.no_reuse:
+        ms_r, msr_r, _, launches_r, _ = timed(1, args.steps, args.warmup, reuse=REUSE)
+        ms_r = max_over_ranks(ms_r)
+        reuse_arm = {"value": world * samples * args.steps / (ms_r / 1e3), "ms_per_step": ms_r / args.steps,
+                     "render_ms_per_step": msr_r / args.steps, "backward_ms_per_step": timed.backward_ms,
+                     "neighbours": REUSE[0], "radius": REUSE[1], "gpu_launches": launches_r}
+
     value = world * samples * args.steps / (ms_b / 1e3)
     mrays = world * rays_b / (ms_b / 1e3) / 1e6
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -466,6 +482,7 @@ def main():
             "persistent": persistent,
             "full_adjoint": full,
             "denoiser": eawt,
+            "spatial_reuse": reuse_arm,
             "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
             "counters_per_step": {"primary_rays": cnt_b[0] // args.steps, "continuation_rays": cnt_b[1] // args.steps,
                                   "shadow_rays": cnt_b[2] // args.steps, "ris_candidates": cnt_b[5] // args.steps,

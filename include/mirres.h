@@ -105,6 +105,16 @@ typedef struct {
  *            All take every discrete decision identically (hit triangles, selected
  *            candidates, lobes); values agree to FP32 rounding (the kernels may contract
  *            multiply-adds differently).
+ *   reuse_k, reuse_radius  spatial reuse at the primary vertex (Appendix A, "Spatial-temporal
+ *            Reuse"): each bounce-0 reservoir merges those of reuse_k neighbouring pixels (same
+ *            sample index; offsets (dx, dy) = ((x >> 8) (2 r + 1) >> 24) - r of the first two
+ *            words of the reuse stream P = 3, j = neighbour; the pixel itself and pixels outside
+ *            the image skipped, a neighbour whose primary ray escaped has no reservoir). Each
+ *            reservoir enters with weight p_hat_here(y) w_sum / p_hat_there(y), accepted iff
+ *            u w_sum < weight with u from the third word; the merged reservoir counts ris_m
+ *            candidates per reservoir (own and neighbours that hit), W = w_sum / (m p_hat(y)).
+ *            The paper gives no MIS weights: this is the biased 1/m combination. Batched
+ *            launch only (whole views per wave); reuse_k in [0, 64], reuse_radius >= 1.
  *   block, blocks_per_sm  launch shape of the persistent kernel (0 = autotuned / default)
  *   flags    bit 0: record CUDA events around every stage kernel of the batched wavefront
  *            (read back with mirres_stage_times); bit 1: the batched wavefront counts its
@@ -118,7 +128,10 @@ typedef struct {
     int32_t block;
     int32_t blocks_per_sm;
     int32_t flags;
+    int32_t reuse_k;       /* spatial reuse: neighbouring reservoirs merged per pixel (0 = off) */
+    int32_t reuse_radius;  /* ... drawn from the (2 r + 1)^2 pixel square around the pixel */
 } mirres_params;
+#define MIRRES_REUSE_MAX_K 64
 
 /* Gradient destinations for one scene (device pointers, shapes of the scene's inputs).
  * Accumulated (+=); a NULL pointer skips that parameter. */

@@ -171,6 +171,9 @@ static mirres_status check_params(const mirres_params* p)
     if (p->block != 0 && (p->block < 32 || p->block > 1024 || p->block % 32))
         return arg_error("block must be 0 or a multiple of 32 in [32, 1024]");
     if (p->blocks_per_sm < 0) return arg_error("blocks_per_sm must be >= 0");
+    if (p->reuse_k < 0 || p->reuse_k > MIRRES_REUSE_MAX_K) return arg_error("reuse_k must be in [0, 64]");
+    if (p->reuse_k > 0 && (p->reuse_radius < 1 || p->reuse_radius > 1024))
+        return arg_error("reuse_radius must be in [1, 1024] when reuse_k > 0");
     return MIRRES_OK;
 }
 
@@ -340,7 +343,7 @@ static const uint64_t kWave = 1ull << MR_WAVE_LOG2;
 
 struct GraphKey {
     uint64_t total, total_pix, wave;
-    int32_t n_views, n_scenes, max_b, M, sms, flags, nvx;
+    int32_t n_views, n_scenes, max_b, M, sms, flags, nvx, reuse_k, reuse_radius;
     uint32_t k0, k1;
     const void* tape;
     const void* ws;
@@ -368,7 +371,7 @@ static mirres_status stage_events(mirres_context* ctx, int pairs)
 
 static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev>& sdev,
                                  const std::vector<ViewDev>& vdev, uint64_t total, float* const* images, void* tape,
-                                 int M, Rng rng, int flags, int nvx, cudaStream_t st)
+                                 int M, Rng rng, int flags, int nvx, int reuse_k, int reuse_radius, cudaStream_t st)
 {
     const int n_views = (int)vdev.size(), n_scenes = (int)sdev.size();
     int max_b = 1;
@@ -380,6 +383,27 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         total_pix += (uint64_t)vdev[(size_t)i].width * vdev[(size_t)i].height;
     }
     const uint64_t wave = std::min<uint64_t>(total, kWave);
+    // wave boundaries: every kWave samples, or with spatial reuse whole views per wave (a
+    // pixel's neighbours must have been shaded in the same wave)
+    std::vector<uint64_t> wave_first;
+    if (reuse_k > 0) {
+        uint64_t in_wave = 0;
+        for (int i = 0; i < n_views; ++i) {
+            const ViewDev& v = vdev[(size_t)i];
+            const uint64_t nv = (uint64_t)v.width * v.height * v.spp;
+            if (nv > kWave)
+                return arg_error("spatial reuse needs every view to fit one wave (" + std::to_string(kWave) +
+                                 " samples); view " + std::to_string(i) + " has " + std::to_string(nv));
+            if (wave_first.empty() || in_wave + nv > kWave) {
+                wave_first.push_back(v.offset);
+                in_wave = 0;
+            }
+            in_wave += nv;
+        }
+    } else {
+        for (uint64_t f = 0; f < total; f += wave) wave_first.push_back(f);
+    }
+    const int n_waves = (int)wave_first.size();
     Carver plan(nullptr);
     plan.take<char>(tape ? 0 : tape_bytes_per_sample(nvx) * total);
     plan.take<ViewDev>((size_t)n_views);
@@ -388,6 +412,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     plan.take<uint64_t>((size_t)n_views);
     plan.take<unsigned int>(5 * (size_t)max_b + 3);
     plan.take<float4>(16ull * wave);
+    for (int k = 0; k < 5; ++k) plan.take<uint32_t>(reuse_k > 0 ? total : 0);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
     void* internal_tape = cv.take<char>(tape ? 0 : tape_bytes_per_sample(nvx) * total);
@@ -401,6 +426,14 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     QueueDev qb{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
     QueueDev hq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
     ShadowDev sq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+    ResDev res{};
+    if (reuse_k > 0) {
+        res.ytex = reinterpret_cast<int32_t*>(cv.take<uint32_t>(total));
+        res.sel = reinterpret_cast<int32_t*>(cv.take<uint32_t>(total));
+        res.ysub = cv.take<uint32_t>(total);
+        res.wsum = reinterpret_cast<float*>(cv.take<uint32_t>(total));
+        res.phat = reinterpret_cast<float*>(cv.take<uint32_t>(total));
+    }
     MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_images, images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
@@ -418,6 +451,8 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     key.sms = ctx->sm_count;
     key.flags = flags & 3;
     key.nvx = nvx;
+    key.reuse_k = reuse_k;
+    key.reuse_radius = reuse_radius;
     key.k0 = rng.rk0[0];
     key.k1 = rng.rk1[0];
     key.tape = tp;
@@ -430,13 +465,13 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
             ctx->graph = nullptr;
         }
         if (!ctx->capture_stream) MR_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
-        const int pairs = mr_wave_stage_pairs(total, wave, max_b);
+        const int pairs = mr_wave_stage_pairs(n_waves, max_b);
         if (flags & 1) MR_TRY(stage_events(ctx, pairs));
         MR_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave, qa, qb, hq, sq, qc, tp, ctx->counters,
-                       d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
+        mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave_first.data(), n_waves, qa, qb, hq, sq,
+                       qc, tp, ctx->counters, d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
                        (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr, nvx,
-                       (flags & 2) != 0);
+                       (flags & 2) != 0, reuse_k, reuse_radius, res);
         ctx->stage_pairs = (flags & 1) ? pairs : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -451,7 +486,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
             return mr_cuda_status(ei, "mirres_render: graph instantiation");
         }
         std::memcpy(ctx->graph_key, &key, sizeof(key));
-        ctx->graph_launches = (unsigned long long)mr_wave_launches(total, wave, max_b);
+        ctx->graph_launches = (unsigned long long)mr_wave_launches(n_waves, max_b, reuse_k > 0);
     }
     MR_CUDA(cudaGraphLaunch(ctx->graph, st));
     ctx->host_launches += ctx->graph_launches;
@@ -484,7 +519,11 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     const int M = params->ris_m;
     const int sms = ctx->sm_count;
 
-    if (params->launch == 1) return render_wave(ctx, sdev, vdev, total, images, tape, M, rng, params->flags, nvx, st);
+    if (params->reuse_k > 0 && params->launch != 1)
+        return arg_error("spatial reuse (reuse_k > 0) is implemented for the batched launch (launch 1)");
+    if (params->launch == 1)
+        return render_wave(ctx, sdev, vdev, total, images, tape, M, rng, params->flags, nvx, params->reuse_k,
+                           params->reuse_radius, st);
 
     // workspace layout
     const bool batched = params->launch == 2;

@@ -105,7 +105,7 @@ __device__ __forceinline__ float3 add_rn(float3 a, float3 b)
 // ---------------------------------------------------------------------------------------
 // Philox4x32-10 counter-based generator (Salmon et al., SC'11)
 // ---------------------------------------------------------------------------------------
-enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2 };
+enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2, PURPOSE_REUSE = 3 };
 
 // The key schedule (k += Weyl constants each round) depends on the seed only, so the ten round
 // keys are computed once on the host and travel in the kernel parameters, where each round

@@ -77,6 +77,10 @@ struct VertexOut {
     float3 x;
     int cand, ytex;
     float W, c_pind;
+    // the vertex's RIS reservoir (for spatial reuse): selected candidate's sub-texel word,
+    // weight sum and target p_hat of the selection
+    uint32_t ysub;
+    float wsum, phat;
 };
 
 // FULL mode: no later vertex reached yet (written when the sample starts)
@@ -132,6 +136,9 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
     out.cand = -1;
     out.ytex = -1;
     out.W = 0.0f;
+    out.ysub = 0u;
+    out.wsum = 0.0f;
+    out.phat = 0.0f;
     out.c_pind = 0.0f;
     out.sh_d = f3(0.f, 0.f, 0.f);
     out.c_d = f3(0.f, 0.f, 0.f);
@@ -149,6 +156,7 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
         float wsum = 0.0f, yfc_sel = 0.0f;
         float dv_sel = 0.0f, w5_sel = 0.0f, ci_sel = 0.0f;
         int sel = -1, ytex = 0;
+        uint32_t ysub = 0u;
         float3 ysel = f3(0.f, 0.f, 0.f);
 #pragma unroll kCandUnroll
         for (int j = 0; j < M; ++j) {
@@ -173,6 +181,7 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
             if (u24(x.z) * wsum < gamma) {
                 sel = j;
                 ytex = tex;
+                ysub = x.w;
                 ysel = dir;
                 yfc_sel = yfc;
                 dv_sel = dv;
@@ -182,6 +191,9 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
         }
         const float4 L = (sel >= 0) ? __ldg(s.env_texel + ytex) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float phat_sel = lum(xyz(L)) * yfc_sel;
+        out.wsum = wsum;
+        out.phat = phat_sel;
+        out.ysub = ysub;
         if (sel >= 0 && wsum > 0.0f && phat_sel > 0.0f) {
             const float W = wsum / ((float)M * phat_sel);
             const float3 fsel = f3((kd.x * MR_INV_PI + dv_sel * (f0.x * (1.0f - w5_sel) + w5_sel)) * ci_sel,

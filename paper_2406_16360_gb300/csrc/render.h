@@ -3,6 +3,19 @@
 
 #include "internal.h"
 
+// Reservoirs of the primary vertices for spatial reuse, one per path sample (SoA): env texel of
+// the selection (RES_MISS: the primary ray escaped, RES_NONE: a hit without a selection), the
+// selection's index among the vertex's own candidates, its sub-texel word, the weight sum and
+// p_hat of the selection at its own vertex. All null when reuse is off.
+enum { RES_MISS = -1, RES_NONE = -2 };
+struct ResDev {
+    int32_t* ytex;
+    int32_t* sel;
+    uint32_t* ysub;
+    float* wsum;
+    float* phat;
+};
+
 // ray queue (SoA of float4): (o, origin triangle), (d, sample id), throughput, indirect throughput
 struct QueueDev {
     float4* o;
@@ -73,9 +86,10 @@ void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* p
 
 // wave.cu: the batched wavefront forward (recorded on a stream, captured as a graph)
 void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,
-                    Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,
-                    const ShadowDev& sq, unsigned int* qc, void* tape, unsigned long long* counters,
-                    const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaStream_t st,
-                    cudaEvent_t* ev, int* kind, int nvx, bool count);
-int mr_wave_launches(uint64_t total, uint64_t wave, int max_bounces);
-int mr_wave_stage_pairs(uint64_t total, uint64_t wave, int max_bounces);
+                    Rng rng, int M, const uint64_t* wave_first, int n_waves, const QueueDev& qa, const QueueDev& qb,
+                    const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
+                    unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
+                    int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
+                    int reuse_radius, const ResDev& res);
+int mr_wave_launches(int n_waves, int max_bounces, bool reuse);
+int mr_wave_stage_pairs(int n_waves, int max_bounces);

@@ -22,7 +22,7 @@ __device__ __forceinline__ void flush_work(unsigned long long* counters, int idx
 
 __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ views, int n_views, Rng rng,
                                                  uint64_t first, uint32_t n, QueueDev q, void* tape, uint64_t ntot,
-                                                 int nvx)
+                                                 int nvx, ResDev res)
 {
     const TapeDev tp = tape_of(tape, ntot, nvx);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ vie
             tp.rad[k][g] = 0.0f;
         }
         tape_vx_init(tp, g);
+        if (res.ytex) res.ytex[g] = RES_MISS;
     }
 }
 
@@ -99,11 +100,13 @@ __global__ void __launch_bounds__(256) k_wclosest(const SceneDev* __restrict__ s
     if (COUNT) flush_work(counters, CNT_CBOX, n_box, (unsigned int)n_tri);
 }
 
+template <bool REUSE>
 __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* __restrict__ scenes,
                                                 const ViewDev* __restrict__ views, Rng rng, int b, int M,
                                                 QueueDev hq, const unsigned int* count_hit, QueueDev qout,
                                                 unsigned int* count_out, ShadowDev sq, unsigned int* count_sh,
-                                                void* tape, uint64_t ntot, int nvx, unsigned long long* counters)
+                                                void* tape, uint64_t ntot, int nvx, ResDev res,
+                                                unsigned long long* counters)
 {
     const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count_hit;
@@ -142,6 +145,15 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* _
                 tp.cand[g] = out.cand;
                 tp.wv[g] = out.W;
                 tape_directions(tp, g, out);
+                if (REUSE) {
+                    // spatial reuse: publish the reservoir; k_wreuse merges and traces the shadow ray
+                    res.ytex[g] = out.cand >= 0 ? out.ytex : RES_NONE;
+                    res.sel[g] = out.cand;
+                    res.ysub[g] = out.ysub;
+                    res.wsum[g] = out.wsum;
+                    res.phat[g] = out.phat;
+                    out.shadow = false;
+                }
             } else {
                 tape_vx_record(tp, g, b, h, out);
             }
@@ -203,6 +215,111 @@ __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ sc
         }
     }
     if (COUNT) flush_work(counters, CNT_SBOX, n_box, (unsigned int)n_tri);
+}
+
+// Spatial reuse at the primary vertex (Appendix A, "Spatial-temporal Reuse"): every bounce-0
+// hit merges the reservoirs of K neighbouring pixels (same sample index; offsets drawn from the
+// (2R+1)^2 square by the reuse stream) into its own. Each reservoir enters with weight
+// p_hat_here(y) w_sum / p_hat_there(y), the merged reservoir counts M candidates per reservoir
+// whose primary ray hit, W = w_sum / (m p_hat_here(y)); then the shadow ray of the merged
+// selection is queued. Reads only what k_wshade published for the whole wave (waves hold whole
+// views), writes only its own sample's tape words.
+__global__ void __launch_bounds__(256) k_wreuse(const SceneDev* __restrict__ scenes, const ViewDev* __restrict__ views,
+                                                Rng rng, int M, int K, int R, QueueDev hq,
+                                                const unsigned int* count_hit, ShadowDev sq, unsigned int* count_sh,
+                                                ResDev res, void* tape, uint64_t ntot, int nvx)
+{
+    const TapeDev tp = tape_of(tape, ntot, nvx);
+    const unsigned int n = *count_hit;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    const unsigned int rounds = (n + stride - 1) / stride;
+    for (unsigned int r = 0; r < rounds; ++r) {
+        const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        bool emit = false;
+        float3 so = f3(0.f, 0.f, 0.f), sd = so, add = so;
+        int tri = -1, vi = 0;
+        uint32_t sid = 0;
+        if (i < n) {
+            const float4 hd = hq.o[i], qd = hq.d[i], qb = hq.b[i];
+            vi = __float_as_int(qb.w);
+            const ViewDev& v = views[vi];
+            const SceneDev& s = scenes[v.scene];
+            tri = __float_as_int(hd.w);
+            sid = __float_as_uint(qd.w);
+            const uint64_t g = v.offset + sid;
+            const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
+            const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+            const float3 d = xyz(qd), wo = f3(-d.x, -d.y, -d.z);
+            Shade sh;
+            shade_at(s, tri, hd.y, hd.z, d, sh);
+            float wsum = 0.0f, phat_sel = 0.0f;
+            int m = M, sel = -1, ytex = 0;
+            uint32_t ysub = 0u;
+            const int own = res.ytex[g];
+            if (own >= 0) {  // the vertex's own reservoir first: p_hat_here = p_hat_own
+                const float ph = res.phat[g];
+                wsum = ph * res.wsum[g] / ph;
+                sel = res.sel[g];
+                ytex = own;
+                ysub = res.ysub[g];
+                phat_sel = ph;
+            }
+            for (int j = 0; j < K; ++j) {
+                const uint4 x = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_REUSE, (uint32_t)j);
+                const int dx = (int)(((uint64_t)(x.x >> 8) * (uint64_t)(2 * R + 1)) >> 24) - R;
+                const int dy = (int)(((uint64_t)(x.y >> 8) * (uint64_t)(2 * R + 1)) >> 24) - R;
+                const int qx = px + dx, qy = py + dy;
+                if ((dx == 0 && dy == 0) || qx < 0 || qy < 0 || qx >= v.width || qy >= v.height) continue;
+                const uint64_t gq = v.offset + ((uint64_t)qy * (uint64_t)v.width + (uint64_t)qx) * (uint64_t)v.spp + smp;
+                const int nt = res.ytex[gq];
+                if (nt == RES_MISS) continue;
+                m += M;
+                if (nt < 0) continue;
+                float4 rowv;
+                float3 y;
+                env_dir(s, nt / s.ew, nt % s.ew, res.ysub[gq], y, rowv);
+                const float3 fc = brdf_cos(sh.n, wo, y, sh.m);
+                const float ph = lum(xyz(__ldg(s.env_texel + nt))) * lum(fc);
+                const float w = ph * res.wsum[gq] / res.phat[gq];
+                wsum += w;
+                if (u24(x.z) * wsum < w) {
+                    sel = M * (j + 1) + res.sel[gq];
+                    ytex = nt;
+                    ysub = res.ysub[gq];
+                    phat_sel = ph;
+                }
+            }
+            float W = 0.0f;
+            float3 y = f3(0.f, 0.f, 0.f);
+            if (sel >= 0 && wsum > 0.0f && phat_sel > 0.0f) {
+                float4 rowv;
+                env_dir(s, ytex / s.ew, ytex % s.ew, ysub, y, rowv);
+                const float3 fsel = brdf_cos(sh.n, wo, y, sh.m);
+                const float4 L = __ldg(s.env_texel + ytex);
+                W = wsum / ((float)m * phat_sel);
+                const float3 contrib = mul(hmul(xyz(L), fsel), W);
+                add = hmul_rn(xyz(qb), contrib);
+                emit = true;
+                so = sh.x;
+                sd = y;
+            } else {
+                sel = -1;
+            }
+            tp.cand[g] = sel;
+            tp.wv[g] = W;
+            tp.ytex[g] = sel >= 0 ? ytex : -1;
+            tp.y[0][g] = y.x;
+            tp.y[1][g] = y.y;
+            tp.y[2][g] = y.z;
+        }
+        const unsigned int ss = warp_append(emit, count_sh);
+        if (emit) {
+            sq.o[ss] = make_float4(so.x, so.y, so.z, __int_as_float(tri));
+            sq.d[ss] = make_float4(sd.x, sd.y, sd.z, __uint_as_float(sid));
+            sq.add[ss] = make_float4(add.x, add.y, add.z, __int_as_float(vi));
+            sq.addi[ss] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
 }
 
 // Lane refill for the incoherent stages (continuation and shadow rays): each warp takes rays
@@ -369,10 +486,11 @@ unsigned grid_cap(uint64_t n, int block, int cap)
 // With `ev` non-null, an event pair is recorded around every stage launch: ev[2k], ev[2k+1]
 // for pair k, whose stage kind (0 closest, 1 shade, 2 shadow, 3 raygen) goes to kind[k].
 void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,
-                    Rng rng, int M, uint64_t wave, const QueueDev& qa, const QueueDev& qb, const QueueDev& hq,
-                    const ShadowDev& sq, unsigned int* qc, void* tape, unsigned long long* counters,
-                    const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaStream_t st,
-                    cudaEvent_t* ev, int* kind, int nvx, bool count)
+                    Rng rng, int M, const uint64_t* wave_first, int n_waves, const QueueDev& qa, const QueueDev& qb,
+                    const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
+                    unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
+                    int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
+                    int reuse_radius, const ResDev& res)
 {
     const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
     // the refilling kernels run one resident wave of blocks
@@ -391,11 +509,13 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         cudaEventRecordWithFlags(ev[2 * pair + (start ? 0 : 1)], st, cudaEventRecordExternal);
         if (!start) ++pair;
     };
-    for (uint64_t first = 0; first < total; first += wave) {
-        const uint32_t n = (uint32_t)(total - first < wave ? total - first : wave);
+    for (int wv = 0; wv < n_waves; ++wv) {
+        const uint64_t first = wave_first[wv];
+        const uint32_t n = (uint32_t)((wv + 1 < n_waves ? wave_first[wv + 1] : total) - first);
         cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (5 * max_bounces + 3), st);
         mark(3, true);
-        k_wraygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(views, n_views, rng, first, n, qa, tape, total, nvx);
+        k_wraygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(views, n_views, rng, first, n, qa, tape, total, nvx,
+                                                             res);
         mark(3, false);
         QueueDev cur = qa, nxt = qb;
         for (int b = 0; b < max_bounces; ++b) {
@@ -409,9 +529,13 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     scenes, views, b, cur, cnt_in, n, hq, qc + 3 * b, tape, total, counters);
             mark(0, false);
             mark(1, true);
-            k_wshade<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, b, M, hq, qc + 3 * b, nxt,
-                                                                qc + 3 * b + 1, sq, qc + 3 * b + 2, tape, total, nvx,
-                                                                counters);
+            const bool reuse_b = b == 0 && res.ytex != nullptr;
+            (reuse_b ? k_wshade<true> : k_wshade<false>)<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(
+                scenes, views, rng, b, M, hq, qc + 3 * b, nxt, qc + 3 * b + 1, sq, qc + 3 * b + 2, tape, total, nvx,
+                res, counters);
+            if (reuse_b)
+                k_wreuse<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, M, reuse_k, reuse_radius, hq,
+                                                                    qc, sq, qc + 2, res, tape, total, nvx);
             mark(1, false);
             mark(2, true);
             if (MR_REFILL)
@@ -430,14 +554,9 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
     mr_launch_resolve_all(views, n_views, pix_off, total_pix, images, tape, total, sms, st);
 }
 
-int mr_wave_stage_pairs(uint64_t total, uint64_t wave, int max_bounces)
-{
-    const uint64_t waves = (total + wave - 1) / wave;
-    return (int)(waves * (1 + 3 * (uint64_t)max_bounces));
-}
+int mr_wave_stage_pairs(int n_waves, int max_bounces) { return n_waves * (1 + 3 * max_bounces); }
 
-int mr_wave_launches(uint64_t total, uint64_t wave, int max_bounces)
+int mr_wave_launches(int n_waves, int max_bounces, bool reuse)
 {
-    const uint64_t waves = (total + wave - 1) / wave;
-    return (int)(waves * (2 + 3 * (uint64_t)max_bounces) + 1);
+    return n_waves * (2 + 3 * max_bounces + (reuse ? 1 : 0)) + 1;
 }

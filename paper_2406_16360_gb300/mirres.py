@@ -60,7 +60,7 @@ class View(C.Structure):
 class Params(C.Structure):
     _fields_ = [("ris_m", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("grad_mode", C.c_int32),
                 ("launch", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("reuse_k", C.c_int32), ("reuse_radius", C.c_int32)]
 
 
 class EawtParams(C.Structure):
@@ -185,9 +185,10 @@ def make_view(K, c2w, width, height, spp, bounces, scene=0) -> View:
                 int(height), int(spp), int(bounces), int(scene))
 
 
-def make_params(ris_m, seed=0, launch=0, block=0, blocks_per_sm=0, grad_mode=0, flags=0) -> Params:
+def make_params(ris_m, seed=0, launch=0, block=0, blocks_per_sm=0, grad_mode=0, flags=0, reuse=(0, 0)) -> Params:
+    """reuse = (neighbours, radius) of the spatial reuse at the primary vertex; (0, 0) = off"""
     return Params(int(ris_m), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(grad_mode), int(launch), int(block),
-                  int(blocks_per_sm), int(flags))
+                  int(blocks_per_sm), int(flags), int(reuse[0]), int(reuse[1]))
 
 
 def _views(views):

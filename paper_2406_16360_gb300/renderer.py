@@ -69,17 +69,19 @@ class GpuWorkload:
         n = M.mirres_tape_bytes_mode(self.views, grad_mode)
         return torch.empty(n // 4, device=self.device, dtype=torch.int32)
 
-    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0, flags=0, grad_mode=0):
+    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0, flags=0, grad_mode=0, reuse=(0, 0)):
         s = self.workload.seed if seed is None else seed
-        return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm, grad_mode=grad_mode, flags=flags)
+        return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm, grad_mode=grad_mode, flags=flags,
+                             reuse=reuse)
 
     def render(self, launch=0, images=None, tape=None, seed=None, block=0, blocks_per_sm=0, flags=0, stream=None,
-               grad_mode=0):
-        """Forward render; grad_mode 1 (FULL) also records every vertex for the FULL adjoint."""
+               grad_mode=0, reuse=(0, 0)):
+        """Forward render; grad_mode 1 (FULL) also records every vertex for the FULL adjoint;
+        reuse = (neighbours, radius) turns on spatial reuse at the primary vertex."""
         images = images if images is not None else self.new_images()
         tape = tape if tape is not None else self.new_tape(grad_mode)
         M.mirres_render(self.ctx, [s.handle for s in self.scenes], self.views,
-                        self.params(launch, seed, block, blocks_per_sm, flags, grad_mode), images, tape, stream)
+                        self.params(launch, seed, block, blocks_per_sm, flags, grad_mode, reuse), images, tape, stream)
         return images, tape
 
     def tune_key(self):

@@ -1,0 +1,94 @@
+"""GPU parity of the spatial reservoir reuse at the primary vertex (Appendix A, "Spatial-temporal
+Reuse") through the C ABI, against the FP64 oracle's restatement (same random streams, same
+neighbours, same merge rule), forward and PRIMARY-mode adjoint."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2406_16360_gb300 import synth
+from tests.parity import compare_grads, compare_pixels
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_16360_gb300 import mirres
+    return mirres
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.mirres_context_create(0)
+    yield c
+    c.close()
+
+
+def _gw(ctx, w):
+    from paper_2406_16360_gb300.renderer import GpuWorkload
+    return GpuWorkload(w, 0, ctx=ctx)
+
+
+@pytest.mark.parametrize("which,reuse", [("config1", (4, 3)), ("config2", (6, 5)), ("config1", (1, 1))])
+def test_reuse_forward_and_adjoint_match_oracle(M, ctx, which, reuse):
+    if which == "config1":
+        w = synth.config1(width=40, height=36)
+    else:
+        w = synth.config2(res=40, n_views=2, tex=32, spp=4)
+        for s in w.scenes:
+            s.env[:] = np.minimum(s.env, 80.0)
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1, reuse=reuse)
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(4))
+    d_imgs, dlist = [], []
+    for vi, v in enumerate(w.views):
+        osc = O.OracleScene(w.scenes[v.scene])
+        r = O.render(osc, v, vi, w.ris_m, seed=w.seed, reuse=reuse)
+        st = compare_pixels(images[vi].cpu().numpy().reshape(-1, 3), r["rgb"], r["margin"])
+        assert st["failures"] == 0, (vi, st["failures"], st["max_err_unflagged"])
+        assert st["flagged"] <= 0.15 * st["n"] + 1, (vi, st["flagged"], st["n"])
+        g = rng.normal(size=(v.width * v.height, 3))
+        g[r["margin"] < 1.0] = 0.0
+        d_imgs.append(torch.as_tensor(g.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda"))
+        dlist.append(g)
+    grads = gw.backward(d_imgs, tape)
+    torch.cuda.synchronize()
+    acc = None
+    for vi, v in enumerate(w.views):
+        gi = O.backward(O.OracleScene(w.scenes[v.scene]), v, vi, w.ris_m, dlist[vi], seed=w.seed, reuse=reuse)
+        acc = gi if acc is None else {k: acc[k] + gi[k] for k in gi if k != "counts"}
+    for k in ("albedo", "roughness", "metallic", "env", "verts"):
+        st = compare_grads(grads[0][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"))
+        assert st["failures"] == 0, (k, st["failures"], st["detail"])
+    for s in gw.scenes:
+        s.close()
+
+
+def test_reuse_changes_the_estimate_and_off_changes_nothing(M, ctx):
+    w = synth.config1(width=32, height=32)
+    gw = _gw(ctx, w)
+    a, _ = gw.render(launch=1)
+    b, _ = gw.render(launch=1, reuse=(0, 0))
+    c, _ = gw.render(launch=1, reuse=(4, 3))
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0])
+    assert not torch.equal(a[0], c[0])
+    for s in gw.scenes:
+        s.close()
+
+
+def test_reuse_argument_checks(M, ctx):
+    w = synth.config1(width=8, height=8)
+    gw = _gw(ctx, w)
+    for launch in (0, 2):
+        with pytest.raises(M.MirresError):
+            gw.render(launch=launch, reuse=(4, 3))
+    for bad in ((65, 3), (4, 0), (-1, 3)):
+        with pytest.raises(M.MirresError):
+            gw.render(launch=1, reuse=bad)
+    for s in gw.scenes:
+        s.close()
