@@ -956,7 +956,7 @@ static v3 camera_dir(const Ctx* c, int px, int py, int smp)
 /* RIS at one shading point (Eq. restir, N = 1): M env candidates streamed through a weighted
  * reservoir (Appendix A). Out: the selection (sel < 0: none), its direction, texel, f_r cos,
  * p_hat, the weight sum and the number of candidates behind the reservoir (m). */
-typedef struct { int sel, ytex; v3 y; double f[3], phat, wsum; int m; } Ris;
+typedef struct { int sel, ytex; uint32_t ysub; v3 y; double f[3], phat, wsum, m; } Ris;
 
 static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, v3 wo, Margin* mg, int64_t* cnt,
                    Ris* r)
@@ -964,7 +964,7 @@ static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, 
     const orc_scene* s = c->s;
     const int M = c->p->ris_m, kind = c->p->brdf_kind;
     Reservoir rs = {0.0, -1};
-    r->sel = -1; r->ytex = -1; r->y = V3(0, 0, 0); r->phat = 0.0; r->m = M;
+    r->sel = -1; r->ytex = -1; r->ysub = 0u; r->y = V3(0, 0, 0); r->phat = 0.0; r->m = M;
     r->f[0] = r->f[1] = r->f[2] = 0.0;
     for (int j = 0; j < M; ++j) {
         uint32_t x[4];
@@ -979,7 +979,7 @@ static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, 
         double ua = orc_uniform(x[2]);
         if (cnt) cnt[5]++;
         if (wrs_update(&rs, gamma, ua, j)) {
-            r->y = dir; r->ytex = tex; r->phat = phat;
+            r->y = dir; r->ytex = tex; r->ysub = x[3]; r->phat = phat;
             for (int k = 0; k < 3; ++k) r->f[k] = fc[k];
         }
         if (gamma > 0.0) note(mg, fabs(ua * rs.wsum - gamma) / rs.wsum / TAU_ACC, MK_ACC);
@@ -988,7 +988,52 @@ static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, 
     r->wsum = rs.wsum;
 }
 
-/* the primary vertex's RIS reservoir of sample smp of pixel (qx, qy): 0 if its ray escapes */
+/* direction of the sub-texel position `sub` of env texel `texel` (as env_sample_m draws it) */
+static v3 texel_dir(const orc_scene* s, int texel, uint32_t sub)
+{
+    int r = texel / s->ew, cidx = texel % s->ew;
+    double uu = (cidx + sub_hi(sub)) / s->ew, vv = (r + sub_lo(sub)) / s->eh;
+    double phi = 2.0 * PI * (uu - 0.5), theta = PI * vv;
+    double st = sin(theta);
+    return V3(st * sin(phi), cos(theta), -st * cos(phi));
+}
+
+/* Temporal reuse (Appendix A, "Spatial-temporal Reuse": reservoirs of previous frames merged):
+ * the sample's reservoir of the previous call, its candidate count capped at temporal_cap *
+ * ris_m, enters after the fresh one with weight p_hat_here(y) w_sum / p_hat_then(y) (m_capped /
+ * m), accepted with the third word of reuse draw j = 65535. Its selection code is 65 ris_m. */
+static void temporal_merge(const Ctx* c, int px, int py, int smp, const Shade* sh, v3 wo, Margin* mg, Ris* r)
+{
+    const orc_params* p = c->p;
+    if (p->temporal != 2 || !p->history_in) return;
+    const orc_scene* s = c->s;
+    const int M = p->ris_m;
+    const uint32_t pix = (uint32_t)(py * c->v->width + px);
+    const double* h = p->history_in + 5 * ((size_t)pix * c->v->spp + smp);
+    const int ht = (int)h[0];
+    if (ht == -1) return;  /* the primary ray escaped last time */
+    const double mc = dmin(h[4], (double)p->temporal_cap * M);
+    r->m += mc;
+    if (ht < 0 || !(h[2] > 0.0) || !(h[3] > 0.0) || !(h[4] > 0.0)) return;
+    v3 y = texel_dir(s, ht, (uint32_t)h[1]);
+    double fc[3];
+    brdf_cos(sh->n, wo, y, sh->alb, sh->rgh, sh->met, c->p->brdf_kind, fc);
+    double phat = lum(s->env + 3 * ht) * lum(fc);
+    double w = phat * h[2] / h[3] * (mc / h[4]);
+    uint32_t x[4];
+    rng(c, pix, (uint32_t)smp, 0, PURPOSE_REUSE, 65535u, x);
+    double u = orc_uniform(x[2]);
+    r->wsum += w;
+    if (u * r->wsum < w) {
+        r->sel = 65 * M;
+        r->y = y; r->ytex = ht; r->ysub = (uint32_t)h[1]; r->phat = phat;
+        for (int k = 0; k < 3; ++k) r->f[k] = fc[k];
+    }
+    if (w > 0.0) note(mg, fabs(u * r->wsum - w) / r->wsum / TAU_ACC, MK_ACC);
+}
+
+/* the primary vertex's RIS reservoir of sample smp of pixel (qx, qy), merged with its history
+ * when temporal reuse is on: 0 if its ray escapes */
 static int primary_reservoir(const Ctx* c, int qx, int qy, int smp, Margin* mg, int64_t* cnt, Ris* r)
 {
     const orc_scene* s = c->s;
@@ -1000,6 +1045,7 @@ static int primary_reservoir(const Ctx* c, int qx, int qy, int smp, Margin* mg, 
     Shade sh;
     shade_at(s, h.tri, h.u, h.v, h.t, d, &sh, mg);
     ris_at(c, (uint32_t)(qy * c->v->width + qx), smp, 0, &sh, vscale(d, -1.0), mg, cnt, r);
+    temporal_merge(c, qx, qy, smp, &sh, vscale(d, -1.0), mg, r);
     return 1;
 }
 
@@ -1022,7 +1068,7 @@ static void spatial_reuse(const Ctx* c, int px, int py, int smp, const Shade* sh
     out.wsum = 0.0;
     out.sel = -1;
     out.m = r->m;
-    if (r->sel >= 0 && r->wsum > 0.0) {
+    if (r->sel >= 0 && r->wsum > 0.0 && r->phat > 0.0) {
         double w = r->phat * r->wsum / r->phat; /* own reservoir: p_hat_here = p_hat_own */
         out.wsum = w;
         out.sel = r->sel;
@@ -1037,7 +1083,7 @@ static void spatial_reuse(const Ctx* c, int px, int py, int smp, const Shade* sh
         Ris nb;
         if (!primary_reservoir(c, qx, qy, smp, mg, cnt, &nb)) continue;
         out.m += nb.m;
-        if (nb.sel < 0 || !(nb.wsum > 0.0)) continue;
+        if (nb.sel < 0 || !(nb.wsum > 0.0) || !(nb.phat > 0.0)) continue;
         double fc[3];
         brdf_cos(sh->n, wo, nb.y, sh->alb, sh->rgh, sh->met, kind, fc);
         double phat = lum(s->env + 3 * nb.ytex) * lum(fc);
@@ -1046,7 +1092,7 @@ static void spatial_reuse(const Ctx* c, int px, int py, int smp, const Shade* sh
         double u = orc_uniform(x[2]);
         if (u * out.wsum < w) {
             out.sel = c->p->ris_m * (j + 1) + nb.sel;
-            out.y = nb.y; out.ytex = nb.ytex; out.phat = phat;
+            out.y = nb.y; out.ytex = nb.ytex; out.ysub = nb.ysub; out.phat = phat;
             for (int k = 0; k < 3; ++k) out.f[k] = fc[k];
         }
         if (w > 0.0) note(mg, fabs(u * out.wsum - w) / out.wsum / TAU_ACC, MK_ACC);
@@ -1069,6 +1115,10 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
     closest_margins(s, o, d, -1, &h, mg);
     if (h.tri < 0) {
         /* primary miss: the environment seen directly */
+        if (c->p->temporal && c->p->history_out) {
+            double* ho = c->p->history_out + 5 * ((size_t)pix * c->v->spp + smp);
+            ho[0] = -1; ho[1] = ho[2] = ho[3] = ho[4] = 0.0;
+        }
         int tx = env_texel_m(s, d, mg);
         rec->bg_texel = tx;
         for (int k = 0; k < 3; ++k) rec->rgb[k] = s->env[3 * tx + k];
@@ -1093,7 +1143,15 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         if (s->env_ok && M > 0) {
             Ris r;
             ris_at(c, pix, smp, b, &sh, wo, mg, cnt, &r);
-            if (b == 0 && c->p->reuse_k > 0) spatial_reuse(c, px, py, smp, &sh, wo, mg, cnt, &r);
+            if (b == 0 && (c->p->reuse_k > 0 || c->p->temporal)) {
+                temporal_merge(c, px, py, smp, &sh, wo, mg, &r);
+                spatial_reuse(c, px, py, smp, &sh, wo, mg, cnt, &r);
+                if (c->p->temporal && c->p->history_out) {
+                    double* ho = c->p->history_out + 5 * ((size_t)pix * c->v->spp + smp);
+                    int ok = r.sel >= 0 && r.wsum > 0.0 && r.phat > 0.0;
+                    ho[0] = ok ? r.ytex : -2; ho[1] = r.ysub; ho[2] = r.wsum; ho[3] = r.phat; ho[4] = r.m;
+                }
+            }
             if (r.sel >= 0 && r.wsum > 0.0) {
                 /* Eq. restir with N = 1: f(y) / p_hat(y) * (1/m) sum gamma */
                 double W = r.wsum / (r.m * r.phat);
@@ -1466,6 +1524,7 @@ static int run_jobs(int mode, const orc_scene* s, const orc_scene* ev, const orc
     if (!s || !v || !p || v->width < 1 || v->height < 1 || v->spp < 1 || v->bounces < 1 || p->ris_m < 0) return 1;
     if (p->grad_mode != 0 && (p->grad_mode != 1 || v->bounces > ORC_MAXB)) return 1;
     if (p->reuse_k < 0 || p->reuse_radius < 0 || (p->reuse_k > 0 && p->reuse_radius < 1)) return 1;
+    if (p->temporal < 0 || p->temporal > 2 || (p->temporal == 2 && (!p->history_in || p->temporal_cap < 1))) return 1;
     if (!pixels) n = v->width * v->height;
     for (int i = 0; pixels && i < n; ++i)
         if (pixels[i] < 0 || pixels[i] >= v->width * v->height) return 1;

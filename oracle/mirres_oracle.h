@@ -53,6 +53,10 @@ typedef struct {
     int32_t grad_mode;   /* 0 = PRIMARY (the paper's); 1 = FULL (every vertex, at most ORC_MAXB) */
     int32_t reuse_k;      /* spatial reuse at the primary vertex: neighbouring reservoirs merged (0 = none) */
     int32_t reuse_radius; /* ... drawn from the (2 r + 1)^2 pixel square around the pixel */
+    int32_t temporal;     /* 0 off; 1 write the reservoir history; 2 merge the history first, then write it */
+    int32_t temporal_cap; /* the history counts at most temporal_cap * ris_m candidates */
+    const double* history_in; /* [view samples][5]: texel (-1 miss, -2 none), sub word, w_sum, p_hat, m */
+    double* history_out;      /* the same layout, written for every rendered sample (may alias nothing) */
 } orc_params;
 
 /* vertices per path recorded for the FULL-mode adjoint */

@@ -51,7 +51,9 @@ class View(C.Structure):
 class Params(C.Structure):
     _fields_ = [("ris_m", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32),
                 ("brdf_kind", C.c_int32), ("threads", C.c_int32), ("want_margin", C.c_int32),
-                ("grad_mode", C.c_int32), ("reuse_k", C.c_int32), ("reuse_radius", C.c_int32)]
+                ("grad_mode", C.c_int32), ("reuse_k", C.c_int32), ("reuse_radius", C.c_int32),
+                ("temporal", C.c_int32), ("temporal_cap", C.c_int32), ("history_in", C.c_void_p),
+                ("history_out", C.c_void_p)]
 
 
 GRAD_FIELDS = ("albedo", "roughness", "metallic", "env", "verts", "albedo_abs", "roughness_abs", "metallic_abs",
@@ -153,16 +155,21 @@ def make_view(view, index):
                 int(view.width), int(view.height), int(view.spp), int(view.bounces), int(index))
 
 
-def make_params(ris_m, seed=0, threads=None, brdf_kind=0, want_margin=1, grad_mode=0, reuse=(0, 0)):
+def make_params(ris_m, seed=0, threads=None, brdf_kind=0, want_margin=1, grad_mode=0, reuse=(0, 0), temporal=0,
+                temporal_cap=20, history_in=None, history_out=None):
     if threads is None:
         threads = os.cpu_count() or 1
     return Params(int(ris_m), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(brdf_kind), int(threads),
-                  int(want_margin), int(grad_mode), int(reuse[0]), int(reuse[1]))
+                  int(want_margin), int(grad_mode), int(reuse[0]), int(reuse[1]), int(temporal), int(temporal_cap),
+                  _p(history_in), _p(history_out))
 
 
 def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind=0, margins=True,
-           prim=False, reuse=(0, 0)):
-    """Render pixels of one view. Returns dict(rgb [n,3], margin [n], prim [n,spp], counts [8])."""
+           prim=False, reuse=(0, 0), temporal=0, temporal_cap=20, history=None):
+    """Render pixels of one view. Returns dict(rgb [n,3], margin [n], prim [n,spp], counts [8]).
+    With temporal reuse (1: record, 2: merge then record) also `history` [samples][5], the
+    reservoir history of the view (input for 2; the output is a new array, unrendered
+    samples copied from the input)."""
     L = lib()
     n = view.width * view.height if pixels is None else len(pixels)
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
@@ -171,16 +178,21 @@ def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind
     pr = np.zeros((n, view.spp), dtype=np.int32) if prim else None
     cnt = np.zeros(8, dtype=np.int64)
     v = make_view(view, index)
-    p = make_params(ris_m, seed, threads, brdf_kind, int(margins), reuse=reuse)
+    hin = None if history is None else _f64(history).reshape(-1, 5)
+    hout = None
+    if temporal:
+        hout = np.zeros((view.width * view.height * view.spp, 5)) if hin is None else hin.copy()
+    p = make_params(ris_m, seed, threads, brdf_kind, int(margins), reuse=reuse, temporal=temporal,
+                    temporal_cap=temporal_cap, history_in=hin, history_out=hout)
     rc = L.orc_render(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(rgb), _p(mg), _p(pr), _p(cnt))
     if rc:
         raise ValueError("orc_render rejected its arguments")
     return dict(rgb=rgb, margin=None if mg is None else mg[:, 0],
-                kind=None if mg is None else mg[:, 1].astype(np.int32), prim=pr, counts=cnt)
+                kind=None if mg is None else mg[:, 1].astype(np.int32), prim=pr, counts=cnt, history=hout)
 
 
 def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, brdf_kind=0, want_abs=True,
-             grad_mode=0, reuse=(0, 0)):
+             grad_mode=0, reuse=(0, 0), temporal=0, temporal_cap=20, history=None):
     """Adjoint of the listed pixels (grad_mode 0 PRIMARY, 1 FULL); returns dict of FP64
     gradients (and abs-sums)."""
     L = lib()
@@ -198,7 +210,8 @@ def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, 
     g = Grads(*[_p(out.get(k)) for k in GRAD_FIELDS])
     cnt = np.zeros(8, dtype=np.int64)
     v = make_view(view, index)
-    p = make_params(ris_m, seed, threads, brdf_kind, 0, grad_mode, reuse)
+    hin = None if history is None else _f64(history).reshape(-1, 5)
+    p = make_params(ris_m, seed, threads, brdf_kind, 0, grad_mode, reuse, temporal, temporal_cap, hin, None)
     rc = L.orc_backward(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(d), C.byref(g), _p(cnt))
     if rc:
         raise ValueError("orc_backward rejected its arguments")

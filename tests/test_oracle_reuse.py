@@ -64,3 +64,40 @@ def test_reuse_is_unbiased_where_targets_agree_and_reduces_variance():
         se = img.std(0) / math.sqrt(n)
         assert np.all(np.abs(img.mean(0) - exact) <= 6 * se + 1e-9), (img.mean(0), exact, se)
     assert plain.var(0).sum() > 1.5 * reuse.var(0).sum()
+
+
+def test_temporal_record_only_is_the_plain_estimate_and_history_is_consistent():
+    w = synth.config1(width=20, height=16)
+    v = w.views[0]
+    osc = O.OracleScene(w.scenes[0])
+    a = O.render(osc, v, 0, w.ris_m, seed=2)
+    b = O.render(osc, v, 0, w.ris_m, seed=2, temporal=1)
+    np.testing.assert_allclose(b["rgb"], a["rgb"], rtol=1e-12, atol=1e-14)
+    h = b["history"]
+    prim = O.render(osc, v, 0, w.ris_m, seed=2, prim=True)["prim"].reshape(-1)
+    assert np.all(h[prim < 0, 0] == -1)            # escaped primary rays leave no reservoir
+    hit = prim >= 0
+    assert np.all(h[hit, 0] >= -2) and np.all(h[hit, 4] == w.ris_m)  # one fresh reservoir of M candidates
+    sel = h[:, 0] >= 0
+    assert sel.any() and np.all(h[sel, 2] > 0) and np.all(h[sel, 3] > 0)
+
+
+def test_temporal_and_spatial_reuse_unbiased_where_targets_agree():
+    env = synth.env_lognormal_sun(32, 16, seed=4, sigma=1.0, sun=60.0)
+    rho = 0.6
+    sc = _plane_scene(rho, env)
+    K, c2w = synth.look_at((0.0, 6.0, 0.01), (0.0, 0.0, 0.0), 48, 48, 50.0)
+    view = synth.View(K, c2w, 48, 48, 4, 1)
+    osc = O.OracleScene(sc)
+    exact = rho / math.pi * _exact_irradiance(env)
+    plain = O.render(osc, view, 0, 4, seed=12, brdf_kind=1)["rgb"]
+    for reuse in ((0, 0), (4, 4)):
+        f1 = O.render(osc, view, 0, 4, seed=11, brdf_kind=1, reuse=reuse, temporal=1)
+        f2 = O.render(osc, view, 0, 4, seed=12, brdf_kind=1, reuse=reuse, temporal=2, temporal_cap=8,
+                      history=f1["history"])
+        img = f2["rgb"]
+        se = img.std(0) / math.sqrt(img.shape[0])
+        assert np.all(np.abs(img.mean(0) - exact) <= 6 * se + 1e-9), (reuse, img.mean(0), exact, se)
+        assert plain.var(0).sum() > 1.3 * img.var(0).sum(), reuse
+        hit = f2["history"][:, 4] > 0
+        assert np.all(f2["history"][hit, 4] >= 4 + 1)  # the history's candidates were counted too
