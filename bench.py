@@ -279,7 +279,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def step(launch, ev_render=None, ev_bwd=None, grad_mode=0, reuse=(0, 0)):
+    history = None
+
+    def step(launch, ev_render=None, ev_bwd=None, grad_mode=0, reuse=(0, 0), temporal=0):
         for s in gw.scenes:
             M.mirres_bvh_build(s.handle)
         if ev_render is not None:
@@ -287,7 +289,7 @@ def main():
         # the batched wavefront records stage events (graph event nodes) for the roofline
         M.mirres_render(gw.ctx, scenes, gw.views, gw.params(launch, block=args.block, blocks_per_sm=args.blocks_per_sm,
                                                             flags=1 if launch == 1 else 0, grad_mode=grad_mode,
-                                                            reuse=reuse),
+                                                            reuse=reuse, temporal=temporal, history=history),
                         images, tape)
         if ev_render is not None:
             ev_render[1].record()
@@ -306,10 +308,10 @@ def main():
                 t.zero_()
         loss.zero_()
 
-    def timed(launch, steps, warmup, grad_mode=0, reuse=(0, 0)):
-        for _ in range(warmup):
+    def timed(launch, steps, warmup, grad_mode=0, reuse=(0, 0), temporal=0):
+        for k in range(warmup):
             zero()
-            step(launch, grad_mode=grad_mode, reuse=reuse)
+            step(launch, grad_mode=grad_mode, reuse=reuse, temporal=1 if (temporal and k == 0) else temporal)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -321,7 +323,7 @@ def main():
             flush.fill_(float(i))  # evict L2 between timed steps (outside the timed window)
             zero()
             evs[i][0].record()
-            step(launch, evr[i], evg[i], grad_mode=grad_mode, reuse=reuse)
+            step(launch, evr[i], evg[i], grad_mode=grad_mode, reuse=reuse, temporal=temporal)
             evs[i][1].record()
         torch.cuda.synchronize()
         barrier()
@@ -465,6 +467,14 @@ def main():
         reuse_arm = {"value": world * samples * args.steps / (ms_r / 1e3), "ms_per_step": ms_r / args.steps,
                      "render_ms_per_step": msr_r / args.steps, "backward_ms_per_step": timed.backward_ms,
                      "neighbours": REUSE[0], "radius": REUSE[1], "gpu_launches": launches_r}
+        # spatial and temporal reuse: each step merges the reservoir history the previous one left
+        history = gw.new_history()
+        ms_t, msr_t, _, launches_t, _ = timed(1, args.steps, args.warmup, reuse=REUSE, temporal=2)
+        ms_t = max_over_ranks(ms_t)
+        reuse_arm["spatial_temporal"] = {"value": world * samples * args.steps / (ms_t / 1e3),
+                                         "ms_per_step": ms_t / args.steps, "render_ms_per_step": msr_t / args.steps,
+                                         "temporal_cap": 20, "gpu_launches": launches_t}
+        history = None
 
     value = world * samples * args.steps / (ms_b / 1e3)
     mrays = world * rays_b / (ms_b / 1e3) / 1e6

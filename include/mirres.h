@@ -115,6 +115,13 @@ typedef struct {
  *            candidates per reservoir (own and neighbours that hit), W = w_sum / (m p_hat(y)).
  *            The paper gives no MIS weights: this is the biased 1/m combination. Batched
  *            launch only (whole views per wave); reuse_k in [0, 64], reuse_radius >= 1.
+ *   temporal, temporal_cap, reuse_history  temporal reuse (Appendix A: reservoirs of previous
+ *            frames merged): with temporal = 2 every primary vertex first merges the reservoir
+ *            its sample left in reuse_history (candidate count capped at temporal_cap * ris_m,
+ *            weight p_hat_here(y) w_sum / p_hat_then(y) (m_capped / m), accepted with the third
+ *            word of reuse draw j = 65535), before spatial reuse; with temporal = 1 or 2 the
+ *            final reservoirs are written back to reuse_history (the same views, in the same
+ *            order, must come in the next call). Batched launch only.
  *   block, blocks_per_sm  launch shape of the persistent kernel (0 = autotuned / default)
  *   flags    bit 0: record CUDA events around every stage kernel of the batched wavefront
  *            (read back with mirres_stage_times); bit 1: the batched wavefront counts its
@@ -130,6 +137,10 @@ typedef struct {
     int32_t flags;
     int32_t reuse_k;       /* spatial reuse: neighbouring reservoirs merged per pixel (0 = off) */
     int32_t reuse_radius;  /* ... drawn from the (2 r + 1)^2 pixel square around the pixel */
+    int32_t temporal;      /* temporal reuse: 0 off, 1 record the reservoir history, 2 merge it, then record */
+    int32_t temporal_cap;  /* the history counts at most temporal_cap * ris_m candidates */
+    void* reuse_history;   /* device, mirres_reuse_history_bytes(views) bytes, caller-owned, kept across calls */
+    uint64_t reuse_history_bytes;
 } mirres_params;
 #define MIRRES_REUSE_MAX_K 64
 
@@ -186,6 +197,11 @@ mirres_status mirres_bvh_refit(mirres_scene* scene, void* stream);
  * p_ind. Words 9-16 are meaningful only where word 1 >= 0, resp. L_ind != 0. The adjoint
  * replays the primary vertex from it and the camera's random numbers; no sample is re-drawn. */
 size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views);
+
+/* Bytes of the reservoir history of temporal reuse: 20 per path sample, stored as 5 arrays over
+ * the samples (selection's env texel: -1 primary ray escaped, -2 no selection; sub-texel word;
+ * weight sum; p_hat of the selection; candidate count). 0 for invalid arguments. */
+size_t mirres_reuse_history_bytes(const mirres_view* views, int32_t n_views);
 
 /* Tape bytes for a gradient mode: mirres_tape_bytes for grad_mode 0 (PRIMARY); for 1 (FULL)
  * MIRRES_TAPE_BYTES_PER_SAMPLE + MIRRES_TAPE_BYTES_PER_VERTEX * (max bounces - 1) per sample.

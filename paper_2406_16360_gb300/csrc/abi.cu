@@ -174,6 +174,9 @@ static mirres_status check_params(const mirres_params* p)
     if (p->reuse_k < 0 || p->reuse_k > MIRRES_REUSE_MAX_K) return arg_error("reuse_k must be in [0, 64]");
     if (p->reuse_k > 0 && (p->reuse_radius < 1 || p->reuse_radius > 1024))
         return arg_error("reuse_radius must be in [1, 1024] when reuse_k > 0");
+    if (p->temporal < 0 || p->temporal > 2) return arg_error("temporal must be 0, 1 or 2");
+    if (p->temporal == 2 && (p->temporal_cap < 1 || p->temporal_cap > 1 << 20))
+        return arg_error("temporal_cap must be in [1, 2^20] when temporal = 2");
     return MIRRES_OK;
 }
 
@@ -310,6 +313,16 @@ extern "C" size_t mirres_tape_bytes_mode(const mirres_view* views, int32_t n_vie
     return (size_t)(tape_bytes_per_sample(full_vertices(views, n_views, grad_mode)) * n);
 }
 
+extern "C" size_t mirres_reuse_history_bytes(const mirres_view* views, int32_t n_views)
+{
+    if (!views || n_views < 1) return 0;
+    uint64_t n = 0;
+    for (int i = 0; i < n_views; ++i)
+        n += (uint64_t)std::max(views[i].width, 0) * (uint64_t)std::max(views[i].height, 0) *
+             (uint64_t)std::max(views[i].spp, 0);
+    return (size_t)(20 * n);
+}
+
 extern "C" size_t mirres_tape_bytes(const mirres_view* views, int32_t n_views)
 {
     return mirres_tape_bytes_mode(views, n_views, 0);
@@ -343,8 +356,9 @@ static const uint64_t kWave = 1ull << MR_WAVE_LOG2;
 
 struct GraphKey {
     uint64_t total, total_pix, wave;
-    int32_t n_views, n_scenes, max_b, M, sms, flags, nvx, reuse_k, reuse_radius;
+    int32_t n_views, n_scenes, max_b, M, sms, flags, nvx, reuse_k, reuse_radius, temporal, temporal_cap;
     uint32_t k0, k1;
+    const void* history;
     const void* tape;
     const void* ws;
     size_t ws_bytes;
@@ -371,8 +385,10 @@ static mirres_status stage_events(mirres_context* ctx, int pairs)
 
 static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev>& sdev,
                                  const std::vector<ViewDev>& vdev, uint64_t total, float* const* images, void* tape,
-                                 int M, Rng rng, int flags, int nvx, int reuse_k, int reuse_radius, cudaStream_t st)
+                                 int M, Rng rng, int flags, int nvx, int reuse_k, int reuse_radius, int temporal,
+                                 int temporal_cap, void* history, cudaStream_t st)
 {
+    const bool reuse = reuse_k > 0 || temporal > 0;
     const int n_views = (int)vdev.size(), n_scenes = (int)sdev.size();
     int max_b = 1;
     uint64_t total_pix = 0;
@@ -386,7 +402,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     // wave boundaries: every kWave samples, or with spatial reuse whole views per wave (a
     // pixel's neighbours must have been shaded in the same wave)
     std::vector<uint64_t> wave_first;
-    if (reuse_k > 0) {
+    if (reuse) {
         uint64_t in_wave = 0;
         for (int i = 0; i < n_views; ++i) {
             const ViewDev& v = vdev[(size_t)i];
@@ -412,7 +428,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     plan.take<uint64_t>((size_t)n_views);
     plan.take<unsigned int>(5 * (size_t)max_b + 3);
     plan.take<float4>(16ull * wave);
-    for (int k = 0; k < 5; ++k) plan.take<uint32_t>(reuse_k > 0 ? total : 0);
+    for (int k = 0; k < 6; ++k) plan.take<uint32_t>(reuse ? total : 0);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
     void* internal_tape = cv.take<char>(tape ? 0 : tape_bytes_per_sample(nvx) * total);
@@ -427,12 +443,22 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     QueueDev hq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
     ShadowDev sq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
     ResDev res{};
-    if (reuse_k > 0) {
+    if (reuse) {
         res.ytex = reinterpret_cast<int32_t*>(cv.take<uint32_t>(total));
         res.sel = reinterpret_cast<int32_t*>(cv.take<uint32_t>(total));
         res.ysub = cv.take<uint32_t>(total);
         res.wsum = reinterpret_cast<float*>(cv.take<uint32_t>(total));
         res.phat = reinterpret_cast<float*>(cv.take<uint32_t>(total));
+        res.m = reinterpret_cast<float*>(cv.take<uint32_t>(total));
+    }
+    HistDev hist{};
+    if (temporal > 0) {
+        uint32_t* h = reinterpret_cast<uint32_t*>(history);
+        hist.ytex = reinterpret_cast<int32_t*>(h);
+        hist.ysub = h + total;
+        hist.wsum = reinterpret_cast<float*>(h + 2 * total);
+        hist.phat = reinterpret_cast<float*>(h + 3 * total);
+        hist.m = reinterpret_cast<float*>(h + 4 * total);
     }
     MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
@@ -453,6 +479,9 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     key.nvx = nvx;
     key.reuse_k = reuse_k;
     key.reuse_radius = reuse_radius;
+    key.temporal = temporal;
+    key.temporal_cap = temporal_cap;
+    key.history = history;
     key.k0 = rng.rk0[0];
     key.k1 = rng.rk1[0];
     key.tape = tp;
@@ -471,7 +500,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave_first.data(), n_waves, qa, qb, hq, sq,
                        qc, tp, ctx->counters, d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
                        (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr, nvx,
-                       (flags & 2) != 0, reuse_k, reuse_radius, res);
+                       (flags & 2) != 0, reuse_k, reuse_radius, res, temporal, temporal_cap, hist);
         ctx->stage_pairs = (flags & 1) ? pairs : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -486,7 +515,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
             return mr_cuda_status(ei, "mirres_render: graph instantiation");
         }
         std::memcpy(ctx->graph_key, &key, sizeof(key));
-        ctx->graph_launches = (unsigned long long)mr_wave_launches(n_waves, max_b, reuse_k > 0);
+        ctx->graph_launches = (unsigned long long)mr_wave_launches(n_waves, max_b, reuse, temporal);
     }
     MR_CUDA(cudaGraphLaunch(ctx->graph, st));
     ctx->host_launches += ctx->graph_launches;
@@ -519,11 +548,18 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     const int M = params->ris_m;
     const int sms = ctx->sm_count;
 
-    if (params->reuse_k > 0 && params->launch != 1)
-        return arg_error("spatial reuse (reuse_k > 0) is implemented for the batched launch (launch 1)");
+    if ((params->reuse_k > 0 || params->temporal > 0) && params->launch != 1)
+        return arg_error("reservoir reuse (reuse_k > 0 or temporal > 0) is implemented for the batched launch");
+    if (params->temporal > 0) {
+        if (!params->reuse_history) return arg_error("temporal reuse needs reuse_history");
+        if (params->reuse_history_bytes < mirres_reuse_history_bytes(views, n_views))
+            return arg_error("reuse_history_bytes is smaller than mirres_reuse_history_bytes(views)");
+        if (reinterpret_cast<uintptr_t>(params->reuse_history) & 15)
+            return arg_error("reuse_history must be 16-byte aligned");
+    }
     if (params->launch == 1)
         return render_wave(ctx, sdev, vdev, total, images, tape, M, rng, params->flags, nvx, params->reuse_k,
-                           params->reuse_radius, st);
+                           params->reuse_radius, params->temporal, params->temporal_cap, params->reuse_history, st);
 
     // workspace layout
     const bool batched = params->launch == 2;

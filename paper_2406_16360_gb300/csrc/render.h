@@ -14,6 +14,18 @@ struct ResDev {
     uint32_t* ysub;
     float* wsum;
     float* phat;
+    float* m;  // candidates behind the reservoir
+};
+
+// The caller's reservoir history for temporal reuse (SoA over the call's samples): the final
+// reservoir of each sample's primary vertex (texel or RES_MISS / RES_NONE, sub-texel word, weight
+// sum, p_hat of the selection, candidate count). All null when temporal reuse is off.
+struct HistDev {
+    int32_t* ytex;
+    uint32_t* ysub;
+    float* wsum;
+    float* phat;
+    float* m;
 };
 
 // ray queue (SoA of float4): (o, origin triangle), (d, sample id), throughput, indirect throughput
@@ -90,6 +102,6 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
                     unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
                     int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
-                    int reuse_radius, const ResDev& res);
-int mr_wave_launches(int n_waves, int max_bounces, bool reuse);
+                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist);
+int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal);
 int mr_wave_stage_pairs(int n_waves, int max_bounces);

@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* _
                     res.ysub[g] = out.ysub;
                     res.wsum[g] = out.wsum;
                     res.phat[g] = out.phat;
+                    res.m[g] = (float)M;
                     out.shadow = false;
                 }
             } else {
@@ -217,6 +218,69 @@ __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ sc
     if (COUNT) flush_work(counters, CNT_SBOX, n_box, (unsigned int)n_tri);
 }
 
+// Temporal reuse (Appendix A, reservoirs of previous frames): every bounce-0 hit merges the
+// history reservoir its sample left in the previous call, the candidate count capped at
+// cap * M, after its fresh one, with weight p_hat_here(y) w_sum / p_hat_then(y) (m_capped / m)
+// and accept word 65535 of the reuse stream (selection code 65 M); the merged reservoir is
+// what spatial reuse sees. Reads the history and writes the reservoir of its own sample only.
+__global__ void __launch_bounds__(256) k_wtemporal(const SceneDev* __restrict__ scenes,
+                                                   const ViewDev* __restrict__ views, Rng rng, int M, int cap,
+                                                   QueueDev hq, const unsigned int* count_hit, ResDev res,
+                                                   HistDev hist)
+{
+    const unsigned int n = *count_hit;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 hd = hq.o[i], qd = hq.d[i], qb = hq.b[i];
+        const ViewDev& v = views[__float_as_int(qb.w)];
+        const SceneDev& s = scenes[v.scene];
+        const uint32_t sid = __float_as_uint(qd.w);
+        const uint64_t g = v.offset + sid;
+        const int ht = hist.ytex[g];
+        if (ht == RES_MISS) continue;
+        const float hm = hist.m[g];
+        const float mc = fminf(hm, (float)cap * (float)M);
+        res.m[g] += mc;
+        const float hw = hist.wsum[g], hp = hist.phat[g];
+        if (ht < 0 || !(hw > 0.0f) || !(hp > 0.0f) || !(hm > 0.0f)) continue;
+        const float3 d = xyz(qd), wo = f3(-d.x, -d.y, -d.z);
+        Shade sh;
+        shade_at(s, __float_as_int(hd.w), hd.y, hd.z, d, sh);
+        float4 rowv;
+        float3 y;
+        env_dir(s, ht / s.ew, ht % s.ew, hist.ysub[g], y, rowv);
+        const float3 fc = brdf_cos(sh.n, wo, y, sh.m);
+        const float ph = lum(xyz(__ldg(s.env_texel + ht))) * lum(fc);
+        const float w = ph * hw / hp * (mc / hm);
+        const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
+        const uint4 x = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_REUSE, 65535u);
+        const float ws = res.wsum[g] + w;  // the fresh reservoir's sum (zero when nothing had weight)
+        res.wsum[g] = ws;
+        if (u24(x.z) * ws < w) {
+            res.ytex[g] = ht;
+            res.sel[g] = 65 * M;
+            res.ysub[g] = hist.ysub[g];
+            res.phat[g] = ph;
+        }
+    }
+}
+
+// primary rays that escaped leave no reservoir in the history
+__global__ void __launch_bounds__(256) k_whist_miss(uint64_t first, uint32_t n, void* tape, uint64_t ntot,
+                                                    HistDev hist)
+{
+    const TapeDev tp = tape_of(tape, ntot);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t g = first + i;
+        if (tp.tri[g] < 0) {
+            hist.ytex[g] = RES_MISS;
+            hist.ysub[g] = 0u;
+            hist.wsum[g] = 0.0f;
+            hist.phat[g] = 0.0f;
+            hist.m[g] = 0.0f;
+        }
+    }
+}
+
 // Spatial reuse at the primary vertex (Appendix A, "Spatial-temporal Reuse"): every bounce-0
 // hit merges the reservoirs of K neighbouring pixels (same sample index; offsets drawn from the
 // (2R+1)^2 square by the reuse stream) into its own. Each reservoir enters with weight
@@ -227,7 +291,7 @@ __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ sc
 __global__ void __launch_bounds__(256) k_wreuse(const SceneDev* __restrict__ scenes, const ViewDev* __restrict__ views,
                                                 Rng rng, int M, int K, int R, QueueDev hq,
                                                 const unsigned int* count_hit, ShadowDev sq, unsigned int* count_sh,
-                                                ResDev res, void* tape, uint64_t ntot, int nvx)
+                                                ResDev res, HistDev hist, void* tape, uint64_t ntot, int nvx)
 {
     const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count_hit;
@@ -252,8 +316,8 @@ __global__ void __launch_bounds__(256) k_wreuse(const SceneDev* __restrict__ sce
             const float3 d = xyz(qd), wo = f3(-d.x, -d.y, -d.z);
             Shade sh;
             shade_at(s, tri, hd.y, hd.z, d, sh);
-            float wsum = 0.0f, phat_sel = 0.0f;
-            int m = M, sel = -1, ytex = 0;
+            float wsum = 0.0f, phat_sel = 0.0f, m = res.m[g];
+            int sel = -1, ytex = 0;
             uint32_t ysub = 0u;
             const int own = res.ytex[g];
             if (own >= 0) {  // the vertex's own reservoir first: p_hat_here = p_hat_own
@@ -273,7 +337,7 @@ __global__ void __launch_bounds__(256) k_wreuse(const SceneDev* __restrict__ sce
                 const uint64_t gq = v.offset + ((uint64_t)qy * (uint64_t)v.width + (uint64_t)qx) * (uint64_t)v.spp + smp;
                 const int nt = res.ytex[gq];
                 if (nt == RES_MISS) continue;
-                m += M;
+                m += res.m[gq];
                 if (nt < 0) continue;
                 float4 rowv;
                 float3 y;
@@ -296,7 +360,7 @@ __global__ void __launch_bounds__(256) k_wreuse(const SceneDev* __restrict__ sce
                 env_dir(s, ytex / s.ew, ytex % s.ew, ysub, y, rowv);
                 const float3 fsel = brdf_cos(sh.n, wo, y, sh.m);
                 const float4 L = __ldg(s.env_texel + ytex);
-                W = wsum / ((float)m * phat_sel);
+                W = wsum / (m * phat_sel);
                 const float3 contrib = mul(hmul(xyz(L), fsel), W);
                 add = hmul_rn(xyz(qb), contrib);
                 emit = true;
@@ -304,6 +368,13 @@ __global__ void __launch_bounds__(256) k_wreuse(const SceneDev* __restrict__ sce
                 sd = y;
             } else {
                 sel = -1;
+            }
+            if (hist.ytex) {  // the final reservoir becomes the next call's history
+                hist.ytex[g] = sel >= 0 ? ytex : RES_NONE;
+                hist.ysub[g] = ysub;
+                hist.wsum[g] = wsum;
+                hist.phat[g] = phat_sel;
+                hist.m[g] = m;
             }
             tp.cand[g] = sel;
             tp.wv[g] = W;
@@ -490,7 +561,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
                     unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
                     int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
-                    int reuse_radius, const ResDev& res)
+                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist)
 {
     const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
     // the refilling kernels run one resident wave of blocks
@@ -533,9 +604,14 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
             (reuse_b ? k_wshade<true> : k_wshade<false>)<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(
                 scenes, views, rng, b, M, hq, qc + 3 * b, nxt, qc + 3 * b + 1, sq, qc + 3 * b + 2, tape, total, nvx,
                 res, counters);
+            if (reuse_b && temporal == 2)
+                k_wtemporal<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, M, temporal_cap, hq, qc,
+                                                                       res, hist);
             if (reuse_b)
                 k_wreuse<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, M, reuse_k, reuse_radius, hq,
-                                                                    qc, sq, qc + 2, res, tape, total, nvx);
+                                                                    qc, sq, qc + 2, res, hist, tape, total, nvx);
+            if (reuse_b && temporal)
+                k_whist_miss<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(first, n, tape, total, hist);
             mark(1, false);
             mark(2, true);
             if (MR_REFILL)
@@ -556,7 +632,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
 
 int mr_wave_stage_pairs(int n_waves, int max_bounces) { return n_waves * (1 + 3 * max_bounces); }
 
-int mr_wave_launches(int n_waves, int max_bounces, bool reuse)
+int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal)
 {
-    return n_waves * (2 + 3 * max_bounces + (reuse ? 1 : 0)) + 1;
+    const int extra = (reuse ? 1 : 0) + (temporal == 2 ? 1 : 0) + (temporal ? 1 : 0);
+    return n_waves * (2 + 3 * max_bounces + extra) + 1;
 }

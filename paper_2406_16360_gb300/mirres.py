@@ -17,7 +17,8 @@ from . import build as _build
 
 __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_view", "make_params",
            "mirres_context_create", "mirres_context_destroy", "mirres_scene_create", "mirres_scene_destroy",
-           "mirres_bvh_build", "mirres_bvh_refit", "mirres_tape_bytes", "mirres_tape_bytes_mode", "mirres_render",
+           "mirres_bvh_build", "mirres_bvh_refit", "mirres_tape_bytes", "mirres_tape_bytes_mode",
+           "mirres_reuse_history_bytes", "mirres_render",
            "mirres_render_noalloc",
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
@@ -60,7 +61,9 @@ class View(C.Structure):
 class Params(C.Structure):
     _fields_ = [("ris_m", C.c_int32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("grad_mode", C.c_int32),
                 ("launch", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("flags", C.c_int32), ("reuse_k", C.c_int32), ("reuse_radius", C.c_int32)]
+                ("flags", C.c_int32), ("reuse_k", C.c_int32), ("reuse_radius", C.c_int32),
+                ("temporal", C.c_int32), ("temporal_cap", C.c_int32), ("reuse_history", C.c_void_p),
+                ("reuse_history_bytes", C.c_uint64)]
 
 
 class EawtParams(C.Structure):
@@ -98,6 +101,7 @@ def lib():
                 "mirres_bvh_refit": (st, [vp, vp]),
                 "mirres_tape_bytes": (sz, [C.POINTER(View), i32]),
                 "mirres_tape_bytes_mode": (sz, [C.POINTER(View), i32, i32]),
+                "mirres_reuse_history_bytes": (sz, [C.POINTER(View), i32]),
                 "mirres_render": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
                                        C.POINTER(vp), vp, sz, vp]),
                 "mirres_autotune": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params), vp, sz,
@@ -185,10 +189,15 @@ def make_view(K, c2w, width, height, spp, bounces, scene=0) -> View:
                 int(height), int(spp), int(bounces), int(scene))
 
 
-def make_params(ris_m, seed=0, launch=0, block=0, blocks_per_sm=0, grad_mode=0, flags=0, reuse=(0, 0)) -> Params:
-    """reuse = (neighbours, radius) of the spatial reuse at the primary vertex; (0, 0) = off"""
+def make_params(ris_m, seed=0, launch=0, block=0, blocks_per_sm=0, grad_mode=0, flags=0, reuse=(0, 0), temporal=0,
+                temporal_cap=20, history=None) -> Params:
+    """reuse = (neighbours, radius) of the spatial reuse at the primary vertex, (0, 0) = off;
+    temporal = 1 records the reservoir history into `history` (a CUDA tensor of
+    mirres_reuse_history_bytes), 2 merges it first"""
+    hb = 0 if history is None else history.numel() * history.element_size()
     return Params(int(ris_m), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(grad_mode), int(launch), int(block),
-                  int(blocks_per_sm), int(flags), int(reuse[0]), int(reuse[1]))
+                  int(blocks_per_sm), int(flags), int(reuse[0]), int(reuse[1]), int(temporal), int(temporal_cap),
+                  None if history is None else history.data_ptr(), int(hb))
 
 
 def _views(views):
@@ -238,6 +247,11 @@ def mirres_bvh_refit(scene: Scene, stream=None):
 def mirres_tape_bytes(views) -> int:
     vs = _views(views)
     return int(lib().mirres_tape_bytes(vs, len(vs)))
+
+
+def mirres_reuse_history_bytes(views) -> int:
+    vs = _views(views)
+    return int(lib().mirres_reuse_history_bytes(vs, len(vs)))
 
 
 def mirres_tape_bytes_mode(views, grad_mode) -> int:

@@ -69,19 +69,26 @@ class GpuWorkload:
         n = M.mirres_tape_bytes_mode(self.views, grad_mode)
         return torch.empty(n // 4, device=self.device, dtype=torch.int32)
 
-    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0, flags=0, grad_mode=0, reuse=(0, 0)):
+    def params(self, launch=0, seed=None, block=0, blocks_per_sm=0, flags=0, grad_mode=0, reuse=(0, 0), temporal=0,
+               temporal_cap=20, history=None):
         s = self.workload.seed if seed is None else seed
         return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm, grad_mode=grad_mode, flags=flags,
-                             reuse=reuse)
+                             reuse=reuse, temporal=temporal, temporal_cap=temporal_cap, history=history)
+
+    def new_history(self):
+        """reservoir history for temporal reuse (kept across renders of the same views)"""
+        return torch.zeros(M.mirres_reuse_history_bytes(self.views) // 4, device=self.device, dtype=torch.int32)
 
     def render(self, launch=0, images=None, tape=None, seed=None, block=0, blocks_per_sm=0, flags=0, stream=None,
-               grad_mode=0, reuse=(0, 0)):
+               grad_mode=0, reuse=(0, 0), temporal=0, temporal_cap=20, history=None):
         """Forward render; grad_mode 1 (FULL) also records every vertex for the FULL adjoint;
-        reuse = (neighbours, radius) turns on spatial reuse at the primary vertex."""
+        reuse = (neighbours, radius) turns on spatial reuse at the primary vertex; temporal = 1
+        records the reservoir history into `history`, 2 merges it first."""
         images = images if images is not None else self.new_images()
         tape = tape if tape is not None else self.new_tape(grad_mode)
         M.mirres_render(self.ctx, [s.handle for s in self.scenes], self.views,
-                        self.params(launch, seed, block, blocks_per_sm, flags, grad_mode, reuse), images, tape, stream)
+                        self.params(launch, seed, block, blocks_per_sm, flags, grad_mode, reuse, temporal,
+                                    temporal_cap, history), images, tape, stream)
         return images, tape
 
     def tune_key(self):

@@ -92,3 +92,70 @@ def test_reuse_argument_checks(M, ctx):
             gw.render(launch=1, reuse=bad)
     for s in gw.scenes:
         s.close()
+
+
+def _history_np(h, n):
+    """GPU history (5 word arrays over the samples) -> the oracle's [samples][5] doubles"""
+    a = h.cpu().numpy().view(np.uint32).reshape(5, n)
+    return np.stack([a[0].view(np.int32).astype(np.float64), a[1].astype(np.float64),
+                     a[2].view(np.float32).astype(np.float64), a[3].view(np.float32).astype(np.float64),
+                     a[4].view(np.float32).astype(np.float64)], axis=1)
+
+
+@pytest.mark.parametrize("reuse", [(0, 0), (4, 3)])
+def test_temporal_reuse_two_frames_match_oracle(M, ctx, reuse):
+    """frame 1 records the reservoir history, frame 2 (another seed) merges it: images, the
+    recorded histories and the adjoint against the oracle, frame 2 fed the GPU's own history"""
+    w = synth.config1(width=40, height=36)
+    gw = _gw(ctx, w)
+    v = w.views[0]
+    n = w.samples
+    osc = O.OracleScene(w.scenes[0])
+    hist = gw.new_history()
+    img1, _ = gw.render(launch=1, reuse=reuse, temporal=1, history=hist)
+    torch.cuda.synchronize()
+    h1 = _history_np(hist, n)
+    r1 = O.render(osc, v, 0, w.ris_m, seed=w.seed, reuse=reuse, temporal=1)
+    st = compare_pixels(img1[0].cpu().numpy().reshape(-1, 3), r1["rgb"], r1["margin"])
+    assert st["failures"] == 0, st["max_err_unflagged"]
+    sure = np.repeat(r1["margin"] >= 1.0, v.spp)  # samples of unflagged pixels
+    oh = r1["history"]
+    assert np.array_equal(h1[sure, 0], oh[sure, 0]) and np.array_equal(h1[sure, 4], oh[sure, 4])
+    sel = sure & (oh[:, 0] >= 0)
+    for k in (2, 3):
+        assert np.all(np.abs(h1[sel, k] - oh[sel, k]) <= 1e-4 * np.abs(oh[sel, k]))
+    # frame 2: another seed, the history merged first
+    img2, tape2 = gw.render(launch=1, seed=w.seed + 7, reuse=reuse, temporal=2, temporal_cap=8, history=hist)
+    torch.cuda.synchronize()
+    r2 = O.render(osc, v, 0, w.ris_m, seed=w.seed + 7, reuse=reuse, temporal=2, temporal_cap=8, history=h1)
+    st = compare_pixels(img2[0].cpu().numpy().reshape(-1, 3), r2["rgb"], r2["margin"])
+    assert st["failures"] == 0, st["max_err_unflagged"]
+    assert st["flagged"] <= 0.15 * st["n"] + 1
+    g = np.random.Generator(np.random.PCG64(8)).normal(size=(v.width * v.height, 3))
+    g[r2["margin"] < 1.0] = 0.0
+    grads = gw.backward([torch.as_tensor(g.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda")],
+                        tape2, seed=w.seed + 7)
+    torch.cuda.synchronize()
+    og = O.backward(osc, v, 0, w.ris_m, g, seed=w.seed + 7, reuse=reuse, temporal=2, temporal_cap=8, history=h1)
+    for k in ("albedo", "roughness", "metallic", "env", "verts"):
+        st = compare_grads(grads[0][k].cpu().numpy(), og[k], og[k + "_abs"], og.get(k + "_sens"))
+        assert st["failures"] == 0, (k, st["detail"])
+    for s in gw.scenes:
+        s.close()
+
+
+def test_temporal_reuse_argument_checks(M, ctx):
+    w = synth.config1(width=8, height=8)
+    gw = _gw(ctx, w)
+    with pytest.raises(M.MirresError):
+        gw.render(launch=1, temporal=1)  # no history buffer
+    small = torch.zeros(16, device="cuda", dtype=torch.int32)
+    with pytest.raises(M.MirresError):
+        gw.render(launch=1, temporal=1, history=small)
+    with pytest.raises(M.MirresError):
+        gw.render(launch=0, temporal=1, history=gw.new_history())
+    with pytest.raises(M.MirresError):
+        gw.render(launch=1, temporal=2, temporal_cap=0, history=gw.new_history())
+    assert M.mirres_reuse_history_bytes(gw.views) == 20 * w.samples
+    for s in gw.scenes:
+        s.close()
