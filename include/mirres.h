@@ -362,6 +362,21 @@ mirres_status mirres_eawt_backward(mirres_context* ctx, const float* d_out, cons
                                    const mirres_eawt_params* params, const void* record, size_t record_bytes,
                                    float* d_image, void* stream);
 
+/* Mesh regularisers added to the rendering loss while the geometry is refined (Appendix A,
+ * "Training details"):
+ *   L_smooth = sum_i sum_{j in X_i} |v_i - v_j|^2 / |X_i|   (X_i: vertices sharing an edge with i)
+ *   L_offset = sum_i |v_i - v0_i|^2                         (v0 = rest_verts)
+ * on the scene's current vertices (desc.verts). Adds w_smooth L_smooth + w_offset L_offset to
+ * loss[0] and its gradient to grad_verts [n_verts][3] (device, both accumulated, either may be
+ * NULL). rest_verts [n_verts][3] device, needed only when w_offset != 0. X_i comes from the
+ * triangles' edges, each neighbour counted once; the edge list is built on the first call with
+ * w_smooth != 0 and kept by the scene (the topology is fixed; allocates once). Asynchronous;
+ * the loss is an FP32 sum in no fixed order. MIRRES_ERR_ARG for a NULL ctx/scene, a negative
+ * weight or a missing rest_verts; MIRRES_ERR_STATE before mirres_bvh_build. */
+mirres_status mirres_mesh_regularizers(mirres_context* ctx, mirres_scene* scene, const float* rest_verts,
+                                       float w_smooth, float w_offset, float* loss, float* grad_verts,
+                                       void* stream);
+
 /* Cumulative counters since the context was created (synchronises the context's last
  * stream): [0] primary rays, [1] continuation rays, [2] shadow rays, [3] samples rendered,
  * [4] samples differentiated, [5] RIS candidates, [6] kernel launches, [7] error flag. */

@@ -258,6 +258,7 @@ extern "C" mirres_status mirres_scene_destroy(mirres_scene* s)
     cudaDeviceSynchronize();
     mr_bvh_free(s);
     mr_env_free(s);
+    mr_edges_free(s);
     delete s;
     return MIRRES_OK;
 }
@@ -954,6 +955,27 @@ extern "C" mirres_status mirres_eawt_backward(mirres_context* ctx, const float* 
     }
     MR_CUDA(cudaGetLastError());
     ctx->host_launches += (unsigned long long)L + 1;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_mesh_regularizers(mirres_context* ctx, mirres_scene* scene,
+                                                  const float* rest_verts, float w_smooth, float w_offset,
+                                                  float* loss, float* grad_verts, void* stream)
+{
+    if (!ctx || !scene) return arg_error("ctx and scene required");
+    if (!(w_smooth >= 0.0f) || !(w_offset >= 0.0f)) return arg_error("weights must be >= 0");
+    if (w_offset != 0.0f && !rest_verts) return arg_error("rest_verts required when w_offset != 0");
+    if (!scene->built) {
+        g_err = "mirres_mesh_regularizers: call mirres_bvh_build first";
+        return MIRRES_ERR_STATE;
+    }
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    if (w_smooth != 0.0f) MR_TRY(mr_edges_build(scene, st));
+    if (!loss && !grad_verts) return MIRRES_OK;
+    mr_launch_regularizers(scene, rest_verts, w_smooth, w_offset, loss, grad_verts, ctx->sm_count, st);
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += (unsigned long long)(w_smooth != 0.0f) + (unsigned long long)(w_offset != 0.0f);
     return MIRRES_OK;
 }
 

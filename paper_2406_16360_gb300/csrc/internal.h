@@ -87,6 +87,12 @@ struct mirres_scene {
     float4* env_row = nullptr;       // [eh]: (cos, sin of the row centre, RIS weight factor, 0)
     float2* env_col = nullptr;       // [ew]: (cos, sin of the column centre angle)
     int gm_shift = 0, gc_shift = 0, gm = 1, gc = 1;
+    // mesh edges for the regularisers (built on first use; the topology is fixed per scene)
+    int2* edges = nullptr;              // [<= 3F] unique undirected edges (a < b)
+    float* inv_deg = nullptr;           // [V] 1 / neighbour count (0 for isolated vertices)
+    unsigned int* n_edges = nullptr;    // [1] device count
+    unsigned int* deg = nullptr;        // [V] neighbour counts (build scratch)
+    unsigned long long* ehash = nullptr;  // open-addressing table of edge keys (build scratch)
 };
 
 SceneDev mr_scene_dev(const mirres_scene* s);
@@ -96,6 +102,9 @@ mirres_status mr_bvh_alloc(mirres_scene* s);
 void mr_bvh_free(mirres_scene* s);
 mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st);
 mirres_status mr_bvh_refit(mirres_scene* s, cudaStream_t st);
+// regular.cu
+mirres_status mr_edges_build(mirres_scene* s, cudaStream_t st);
+void mr_edges_free(mirres_scene* s);
 // env.cu
 mirres_status mr_env_alloc(mirres_scene* s);
 void mr_env_free(mirres_scene* s);

@@ -1,0 +1,186 @@
+// regular.cu -- the mesh regularisers added to the rendering loss (Appendix A, "Training
+// details"): Laplacian smoothness of the refined vertices,
+//   L_smooth = sum_i sum_{j in X_i} |v_i - v_j|^2 / |X_i|,
+// X_i the vertices sharing an edge with i, and the offset penalty L_offset = sum_i |v_i - v0_i|^2.
+// Each undirected edge (a, b) appears in X_a and X_b, so L_smooth = sum over edges of
+// |v_a - v_b|^2 (1/|X_a| + 1/|X_b|): one thread per edge. The edge list is built once per scene
+// (the topology is fixed) by inserting every triangle edge into an open-addressing hash table.
+#include "render.h"
+
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+__global__ void __launch_bounds__(256) k_edges_insert(const int32_t* __restrict__ tris, int F, int V,
+                                                      unsigned long long* table, unsigned long long mask, int2* edges,
+                                                      unsigned int* n_edges, unsigned int* deg)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)F; t += (int64_t)gridDim.x * blockDim.x) {
+        int v[3];
+        for (int c = 0; c < 3; ++c) v[c] = __ldg(tris + 3 * t + c);
+        for (int c = 0; c < 3; ++c) {
+            int a = v[c], b = v[(c + 1) % 3];
+            if (a == b || a < 0 || b < 0 || a >= V || b >= V) continue;
+            if (a > b) {
+                const int x = a;
+                a = b;
+                b = x;
+            }
+            const unsigned long long key = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+            unsigned long long h = mix64(key) & mask;
+            for (unsigned long long probe = 0; probe <= mask; ++probe) {  // the table is never full
+                const unsigned long long prev = atomicCAS(table + h, kEmpty, key);
+                if (prev == kEmpty) {
+                    const unsigned int i = atomicAdd(n_edges, 1u);
+                    edges[i] = make_int2(a, b);
+                    atomicAdd(deg + a, 1u);
+                    atomicAdd(deg + b, 1u);
+                    break;
+                }
+                if (prev == key) break;
+                h = (h + 1) & mask;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_inv_deg(const unsigned int* __restrict__ deg, int V, float* inv_deg)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x)
+        inv_deg[i] = deg[i] ? 1.0f / (float)deg[i] : 0.0f;
+}
+
+__device__ __forceinline__ void flush_loss(float* loss, float x)
+{
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(MR_FULL, x, off);
+    if (lane_id() == 0 && x != 0.0f) atomicAdd(loss, x);
+}
+
+// w |v_a - v_b|^2 (1/|X_a| + 1/|X_b|) per edge, and its gradient
+__global__ void __launch_bounds__(256) k_smooth(const int2* __restrict__ edges, const unsigned int* __restrict__ n_edges,
+                                                const float* __restrict__ inv_deg, const float* __restrict__ verts,
+                                                float w, float* loss, float* grad)
+{
+    const unsigned int n = *n_edges;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    float acc = 0.0f;
+    // uniform trip count per warp (the loss is reduced across the warp at the end)
+    for (unsigned int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const unsigned int e = base + threadIdx.x;
+        if (e < n) {
+            const int2 ab = edges[e];
+            const float3 va = f3(verts[3 * (size_t)ab.x], verts[3 * (size_t)ab.x + 1], verts[3 * (size_t)ab.x + 2]);
+            const float3 vb = f3(verts[3 * (size_t)ab.y], verts[3 * (size_t)ab.y + 1], verts[3 * (size_t)ab.y + 2]);
+            const float3 d = sub(va, vb);
+            const float c = w * (__ldg(inv_deg + ab.x) + __ldg(inv_deg + ab.y));
+            acc += c * dot(d, d);
+            if (grad) {
+                const float3 g = mul(d, 2.0f * c);
+                atomicAdd(grad + 3 * (size_t)ab.x, g.x);
+                atomicAdd(grad + 3 * (size_t)ab.x + 1, g.y);
+                atomicAdd(grad + 3 * (size_t)ab.x + 2, g.z);
+                atomicAdd(grad + 3 * (size_t)ab.y, -g.x);
+                atomicAdd(grad + 3 * (size_t)ab.y + 1, -g.y);
+                atomicAdd(grad + 3 * (size_t)ab.y + 2, -g.z);
+            }
+        }
+    }
+    if (loss) flush_loss(loss, acc);
+}
+
+// w |v_i - v0_i|^2 per vertex, and its gradient
+__global__ void __launch_bounds__(256) k_offset(const float* __restrict__ verts, const float* __restrict__ rest, int V,
+                                                float w, float* loss, float* grad)
+{
+    const unsigned int stride = gridDim.x * blockDim.x;
+    float acc = 0.0f;
+    for (unsigned int base = blockIdx.x * blockDim.x; base < (unsigned)V; base += stride) {
+        const unsigned int i = base + threadIdx.x;
+        if (i < (unsigned)V) {
+            const float3 d = f3(verts[3 * (size_t)i] - rest[3 * (size_t)i], verts[3 * (size_t)i + 1] - rest[3 * (size_t)i + 1],
+                                verts[3 * (size_t)i + 2] - rest[3 * (size_t)i + 2]);
+            acc += w * dot(d, d);
+            if (grad) {
+                grad[3 * (size_t)i] += 2.0f * w * d.x;
+                grad[3 * (size_t)i + 1] += 2.0f * w * d.y;
+                grad[3 * (size_t)i + 2] += 2.0f * w * d.z;
+            }
+        }
+    }
+    if (loss) flush_loss(loss, acc);
+}
+
+unsigned grid_of(int64_t n, int sms)
+{
+    const int64_t g = (n + 255) / 256;
+    const int64_t cap = (int64_t)sms * 8;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+mirres_status mr_edges_build(mirres_scene* s, cudaStream_t st)
+{
+    if (s->edges) return MIRRES_OK;
+    const int F = s->desc.n_tris, V = s->desc.n_verts;
+    const size_t cap = (size_t)3 * (F > 0 ? F : 1);
+    size_t tsize = 1;
+    while (tsize < 2 * cap) tsize <<= 1;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc((void**)&s->edges, sizeof(int2) * cap);
+    e = e ? e : cudaMalloc((void**)&s->inv_deg, sizeof(float) * (size_t)(V > 0 ? V : 1));
+    e = e ? e : cudaMalloc((void**)&s->n_edges, sizeof(unsigned int));
+    e = e ? e : cudaMalloc((void**)&s->deg, sizeof(unsigned int) * (size_t)(V > 0 ? V : 1));
+    e = e ? e : cudaMalloc((void**)&s->ehash, sizeof(unsigned long long) * tsize);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mr_edges_free(s);
+        mr_set_error(std::string("edge table allocation failed: ") + cudaGetErrorString(e));
+        return MIRRES_ERR_OOM;
+    }
+    int dev = 0, sms = 1;
+    MR_CUDA(cudaGetDevice(&dev));
+    MR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MR_CUDA(cudaMemsetAsync(s->ehash, 0xFF, sizeof(unsigned long long) * tsize, st));
+    MR_CUDA(cudaMemsetAsync(s->n_edges, 0, sizeof(unsigned int), st));
+    MR_CUDA(cudaMemsetAsync(s->deg, 0, sizeof(unsigned int) * (size_t)(V > 0 ? V : 1), st));
+    if (F > 0)
+        k_edges_insert<<<grid_of(F, sms), 256, 0, st>>>(s->desc.tris, F, V, s->ehash, (unsigned long long)(tsize - 1),
+                                                        s->edges, s->n_edges, s->deg);
+    if (V > 0) k_inv_deg<<<grid_of(V, sms), 256, 0, st>>>(s->deg, V, s->inv_deg);
+    MR_CUDA(cudaGetLastError());
+    return MIRRES_OK;
+}
+
+void mr_edges_free(mirres_scene* s)
+{
+    void* ptrs[] = {s->edges, s->inv_deg, s->n_edges, s->deg, s->ehash};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    s->edges = nullptr;
+    s->inv_deg = nullptr;
+    s->n_edges = nullptr;
+    s->deg = nullptr;
+    s->ehash = nullptr;
+}
+
+void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_smooth, float w_offset, float* loss,
+                            float* grad, int sms, cudaStream_t st)
+{
+    const int F = s->desc.n_tris, V = s->desc.n_verts;
+    if (w_smooth != 0.0f && F > 0)
+        k_smooth<<<grid_of(3 * (int64_t)F, sms), 256, 0, st>>>(s->edges, s->n_edges, s->inv_deg, s->desc.verts, w_smooth,
+                                                               loss, grad);
+    if (w_offset != 0.0f && V > 0)
+        k_offset<<<grid_of(V, sms), 256, 0, st>>>(s->desc.verts, rest, V, w_offset, loss, grad);
+}

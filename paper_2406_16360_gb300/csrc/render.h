@@ -95,6 +95,9 @@ void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const floa
                                   const float4* pos, int W, int H, int step, float inv_rt2, float inv_n2, float inv_x2,
                                   float4* gout, float* out3, int sms, cudaStream_t st);
 void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* pos, int sms, cudaStream_t st);
+// regular.cu: mesh regularisers over the scene's edge list (built by mr_edges_build)
+void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_smooth, float w_offset, float* loss,
+                            float* grad, int sms, cudaStream_t st);
 
 // wave.cu: the batched wavefront forward (recorded on a stream, captured as a graph)
 void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,

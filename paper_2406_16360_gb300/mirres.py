@@ -23,7 +23,7 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
            "mirres_get_work_counters", "EawtParams", "mirres_eawt_record_bytes", "mirres_gbuffer", "mirres_eawt",
-           "mirres_eawt_backward",
+           "mirres_eawt_backward", "mirres_mesh_regularizers",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
 
 # limits of mirres_render_noalloc (include/mirres.h)
@@ -119,6 +119,7 @@ def lib():
                 "mirres_gbuffer": (st, [vp, vp, C.POINTER(View), vp, vp, vp]),
                 "mirres_eawt": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, vp, sz, vp]),
                 "mirres_eawt_backward": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, sz, vp, vp]),
+                "mirres_mesh_regularizers": (st, [vp, vp, vp, C.c_float, C.c_float, vp, vp, vp]),
                 "mirres_bvh_export": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "mirres_env_export": (st, [vp, vp, vp, vp, vp, vp]),
                 "mirres_get_counters": (st, [vp, C.POINTER(C.c_uint64)]),
@@ -349,6 +350,15 @@ def mirres_eawt_backward(ctx: Context, d_out, normal, position, params: EawtPara
                                                               W, H, C.byref(params), _ptr(record),
                                                               record.numel() * record.element_size(), _ptr(d_image),
                                                               _stream(stream)))
+
+
+def mirres_mesh_regularizers(ctx: Context, scene: Scene, rest_verts, w_smooth, w_offset, loss, grad_verts,
+                             stream=None):
+    """adds w_smooth L_smooth + w_offset L_offset of the scene's current vertices to loss[0] and its
+    gradient to grad_verts (float32 CUDA tensors; either may be None)"""
+    _check("mirres_mesh_regularizers", lib().mirres_mesh_regularizers(ctx.handle, scene.handle, _ptr(rest_verts),
+                                                                      float(w_smooth), float(w_offset), _ptr(loss),
+                                                                      _ptr(grad_verts), _stream(stream)))
 
 
 def mirres_bvh_export(scene: Scene, keys=None, left=None, right=None, parent=None, lo=None, hi=None, stream=None):
