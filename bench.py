@@ -196,6 +196,15 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _unique_edges(tris):
+    """number of unique undirected edges of a triangle list (for the regulariser byte count)"""
+    import numpy as np
+    t = np.asarray(tris, dtype=np.int64).reshape(-1, 3)
+    e = np.sort(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]]), axis=1)
+    e = e[e[:, 0] != e[:, 1]]
+    return int(np.unique(e[:, 0] << 32 | e[:, 1]).size)
+
+
 def reduce_max(x, device):
     """max of a per-rank number over all ranks (the slowest replica sets the time)"""
     import torch
@@ -222,6 +231,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-full", action="store_true", help="skip the FULL-mode adjoint arm")
     ap.add_argument("--no-eawt", action="store_true", help="skip the denoiser arm")
+    ap.add_argument("--no-regularizers", action="store_true", help="skip the mesh regulariser arm")
     ap.add_argument("--no-reuse", action="store_true", help="skip the spatial-reuse arm")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--block", type=int, default=0)
@@ -447,6 +457,40 @@ def main():
                              "kernel": "k_eawt_level + k_eawt_level_adjoint",
                              "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}}
 
+    # mesh regularisers added to the loss (L_smooth + L_offset, Appendix A) on every scene: one
+    # call per scene. Algorithmic bytes: per vertex 12 (position) + 12 (rest position) + 4 (1 /
+    # neighbour count) + 24 (gradient read and written), per unique edge 8 (its two indices)
+    regs = None
+    if not args.no_regularizers:
+        rests = [s.verts.clone() for s in gw.scenes]
+        rl = torch.zeros(1, device=dev)
+        rg = [torch.zeros_like(s.verts) for s in gw.scenes]
+
+        def reg_pass():
+            for si, s in enumerate(gw.scenes):
+                M.mirres_mesh_regularizers(gw.ctx, s.handle, rests[si], 0.1, 0.01, rl, rg[si])
+
+        for _ in range(max(args.warmup, 3)):
+            reg_pass()
+        torch.cuda.synchronize()
+        e_rg = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e_rg[0].record()
+        for _ in range(args.steps):
+            reg_pass()
+        e_rg[1].record()
+        torch.cuda.synchronize()
+        ms_rg = e_rg[0].elapsed_time(e_rg[1]) / args.steps
+        nv = sum(int(s.verts.shape[0]) for s in gw.scenes)
+        ne = sum(_unique_edges(sc.tris) for sc in w.scenes)
+        bytes_rg = nv * 52 + 8 * ne
+        ach = bytes_rg / (ms_rg / 1e3) / 1e9
+        regs = {"ms_per_step": ms_rg, "vertices": nv, "edges": ne, "weights": [0.1, 0.01],
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK, "unit": "GB/s", "frac": ach / HBM_PEAK,
+                             "traffic": None, "kernel": "k_smooth + k_offset",
+                             "bytes_note": "52 B per vertex + 8 B per unique edge; the mesh is L2-resident",
+                             "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}}
+        rests = rg = None
+
     # FULL-mode adjoint (gradients through every vertex): the same step with grad_mode 1
     full = None
     if want_full:
@@ -492,6 +536,7 @@ def main():
             "persistent": persistent,
             "full_adjoint": full,
             "denoiser": eawt,
+            "mesh_regularizers": regs,
             "spatial_reuse": reuse_arm,
             "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
             "counters_per_step": {"primary_rays": cnt_b[0] // args.steps, "continuation_rays": cnt_b[1] // args.steps,
