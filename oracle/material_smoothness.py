@@ -92,15 +92,19 @@ def pixel_centre_hits(osc, view):
     return tri, st, mg
 
 
-def material_smoothness(osc, view, view_index, sigma, w_albedo, w_rough, seed=0, tau=1e-3):
+def material_smoothness(osc, view, view_index, sigma, w_albedo, w_rough, seed=0, tau=None):
     """Returns (loss, d loss / d albedo [th][tw][3], d loss / d roughness [th][tw], info) with info
     = {n_points, flagged (pixels whose hit or sign decision lies within the FP32 error of its
     threshold: trace margin < 1 or some |k(x) - k(x + eps)| < tau), abs_albedo, abs_rough (per
-    texel, the sum of |gradient terms| of the flagged pixels)}."""
+    texel, the sum of |gradient terms| of the flagged pixels)}. tau defaults to about ten times
+    the FP32 error of a lookup difference: a texture coordinate is good to ~1e-7, i.e. 1e-7 x size
+    texels, and texel values lie in [0, 1]."""
     sc = osc.scene
     alb = np.asarray(sc.albedo, dtype=np.float64)
     rough = np.asarray(sc.roughness, dtype=np.float64)
     th, tw = rough.shape
+    if tau is None:
+        tau = 1e-6 * max(th, tw) + 1e-6
     tri, st, mg = pixel_centre_hits(osc, view)
     eps = offsets(tri.size, view_index, sigma, seed)
     hit = tri >= 0
