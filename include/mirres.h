@@ -377,6 +377,30 @@ mirres_status mirres_mesh_regularizers(mirres_context* ctx, mirres_scene* scene,
                                        float w_smooth, float w_offset, float* loss, float* grad_verts,
                                        void* stream);
 
+/* Material smoothness regulariser (Appendix A, "Training details"):
+ *   L_k = (1 / |X|) sum_{x in X} |k(x) - k(x + eps)|,  k in {albedo, roughness}
+ * X = the surface points seen through the pixel centres of `view` (camera as in mirres_render,
+ * jitter 1/2; escaped pixels are not in X). The materials are textures, so the small random
+ * offset is taken in texture space: k(x + eps) is the bilinear lookup at the hit's texture
+ * coordinates + eps, eps uniform in [-sigma, sigma]^2 from Philox4x32-10 (key = seed, counter
+ * (pixel, 0, view_index << 16 | 4, 0), eps = sigma (2 u - 1) with u the 24-bit uniforms of the
+ * first two words). |.| of the albedo is the mean of its three channels' absolute differences.
+ * (The paper's normal term has no counterpart: normals are the mesh's face normals.) Adds
+ * w_albedo L_albedo + w_roughness L_roughness to loss[0] and its gradient (sign(0) = 0) to
+ * grad_albedo [tex_h][tex_w][3] and grad_roughness [tex_h][tex_w]; all device, accumulated,
+ * any may be NULL. view->scene is ignored. Uses the context workspace (16 B per pixel);
+ * asynchronous; FP32 sums in no fixed order. MIRRES_ERR_ARG for NULL ctx/scene/view/params,
+ * sigma <= 0, a negative weight, a bad view or view_index outside [0, 65535];
+ * MIRRES_ERR_STATE before mirres_bvh_build. */
+typedef struct {
+    float sigma;                /* half-width of the texture-space offset, > 0 */
+    float w_albedo, w_roughness; /* weights, >= 0 */
+    uint32_t seed_lo, seed_hi;  /* Philox key */
+} mirres_lk_params;
+mirres_status mirres_material_smoothness(mirres_context* ctx, const mirres_scene* scene, const mirres_view* view,
+                                         int32_t view_index, const mirres_lk_params* params, float* loss,
+                                         float* grad_albedo, float* grad_roughness, void* stream);
+
 /* Cumulative counters since the context was created (synchronises the context's last
  * stream): [0] primary rays, [1] continuation rays, [2] shadow rays, [3] samples rendered,
  * [4] samples differentiated, [5] RIS candidates, [6] kernel launches, [7] error flag. */

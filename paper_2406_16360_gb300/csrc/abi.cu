@@ -979,6 +979,42 @@ extern "C" mirres_status mirres_mesh_regularizers(mirres_context* ctx, mirres_sc
     return MIRRES_OK;
 }
 
+extern "C" mirres_status mirres_material_smoothness(mirres_context* ctx, const mirres_scene* scene,
+                                                    const mirres_view* view, int32_t view_index,
+                                                    const mirres_lk_params* params, float* loss, float* grad_albedo,
+                                                    float* grad_roughness, void* stream)
+{
+    if (!ctx || !scene || !view || !params) return arg_error("ctx, scene, view and params required");
+    if (!(params->sigma > 0.0f) || !(params->w_albedo >= 0.0f) || !(params->w_roughness >= 0.0f))
+        return arg_error("sigma must be > 0 and the weights >= 0");
+    if (view_index < 0 || view_index > 65535) return arg_error("view_index outside [0, 65535]");
+    if (!scene->built) {
+        g_err = "mirres_material_smoothness: call mirres_bvh_build first";
+        return MIRRES_ERR_STATE;
+    }
+    mirres_view one = *view;
+    one.scene = 0;
+    std::vector<ViewDev> vdev;
+    uint64_t total = 0, max_view = 0;
+    MR_TRY(check_views(&one, 1, 1, vdev, total, max_view));
+    if (!loss && !grad_albedo && !grad_roughness) return MIRRES_OK;
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    const size_t npx = (size_t)view->width * view->height;
+    MR_TRY(ws_reserve(ctx, sizeof(float4) * npx + 256));
+    float4* rec = reinterpret_cast<float4*>(ctx->ws.ptr);
+    unsigned int* n_hit = reinterpret_cast<unsigned int*>(rec + npx);
+    MR_CUDA(cudaMemsetAsync(n_hit, 0, sizeof(unsigned int), st));
+    Rng rng;
+    rng.set(params->seed_lo, params->seed_hi);
+    mr_launch_material_smoothness(mr_scene_dev(scene), vdev[0], (uint32_t)view_index, rng, params->sigma,
+                                  params->w_albedo, params->w_roughness, rec, n_hit, loss, grad_albedo,
+                                  grad_roughness, ctx->sm_count, st);
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += 2;
+    return MIRRES_OK;
+}
+
 extern "C" mirres_status mirres_bvh_export(const mirres_scene* s, uint64_t* keys, int32_t* left, int32_t* right,
                                            int32_t* parent, float* lo, float* hi, void* stream)
 {

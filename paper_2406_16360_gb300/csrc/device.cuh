@@ -105,7 +105,7 @@ __device__ __forceinline__ float3 add_rn(float3 a, float3 b)
 // ---------------------------------------------------------------------------------------
 // Philox4x32-10 counter-based generator (Salmon et al., SC'11)
 // ---------------------------------------------------------------------------------------
-enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2, PURPOSE_REUSE = 3 };
+enum { PURPOSE_CAMERA = 0, PURPOSE_CANDIDATE = 1, PURPOSE_CONTINUE = 2, PURPOSE_REUSE = 3, PURPOSE_SMOOTH = 4 };
 
 // The key schedule (k += Weyl constants each round) depends on the seed only, so the ten round
 // keys are computed once on the host and travel in the kernel parameters, where each round
@@ -734,3 +734,30 @@ __device__ __forceinline__ float3 camera_dir(const ViewDev& v, int px, int py, f
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// warp-aggregated scatter: lanes holding the same key add their values and the key's first
+// lane issues one set of atomics. The sums are segmented suffix sums by pointer jumping along
+// each key's lanes in lane order, every key at once: ceil(log2(largest group)) steps of
+// NV + 1 shuffles, however many distinct keys the warp holds.
+template <int NV, class Emit>
+__device__ __forceinline__ void scatter_agg(int key, const float (&v)[NV], const Emit& emit)
+{
+    const int lane = lane_id();
+    const unsigned peers = __match_any_sync(MR_FULL, key);
+    const unsigned after = peers & ~((2u << lane) - 1u);  // my key's lanes above me
+    int nxt = (key >= 0 && after) ? __ffs(after) - 1 : -1;
+    float acc[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] = v[c];
+    while (__any_sync(MR_FULL, nxt >= 0)) {
+        const int src = nxt >= 0 ? nxt : lane;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            const float o = __shfl_sync(MR_FULL, acc[c], src);
+            if (nxt >= 0) acc[c] += o;
+        }
+        const int n2 = __shfl_sync(MR_FULL, nxt, src);
+        nxt = nxt >= 0 ? n2 : -1;
+    }
+    if (key >= 0 && (__ffs(peers) - 1) == lane) emit(key, acc);
+}

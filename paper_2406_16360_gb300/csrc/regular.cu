@@ -5,6 +5,12 @@
 // Each undirected edge (a, b) appears in X_a and X_b, so L_smooth = sum over edges of
 // |v_a - v_b|^2 (1/|X_a| + 1/|X_b|): one thread per edge. The edge list is built once per scene
 // (the topology is fixed) by inserting every triangle edge into an open-addressing hash table.
+//
+// Also the material smoothness term L_k = (1/|X|) sum_{x in X} |k(x) - k(x + eps)| for the
+// albedo and roughness textures: X is the set of surface points seen through one view's pixel
+// centres, the offset eps is taken in texture space (uniform in [-sigma, sigma]^2, Philox
+// purpose 4), |.| of the albedo is the mean of its channels' absolute differences, and the
+// gradient (sign(0) = 0) is scattered to the eight bilinear taps by warp-aggregated atomics.
 #include "render.h"
 
 namespace {
@@ -120,6 +126,116 @@ __global__ void __launch_bounds__(256) k_offset(const float* __restrict__ verts,
     if (loss) flush_loss(loss, acc);
 }
 
+// one closest-hit ray through each pixel centre: (triangle, s, t) of its hit; triangle -1 where
+// the ray escapes. Hits are counted per warp (one atomic per warp and iteration).
+__global__ void __launch_bounds__(256) k_lk_hits(SceneDev s, ViewDev v, float4* __restrict__ rec,
+                                                 unsigned int* __restrict__ n_hit)
+{
+    extern __shared__ uint32_t sstk[];
+    const int64_t npx = (int64_t)v.width * v.height;
+    const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+    const float tmin = *s.tmin_dev;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // uniform trip count per warp (the hit count is taken with a ballot)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npx; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        bool hit = false;
+        if (p < npx) {
+            const int px = (int)(p % v.width), py = (int)(p / v.width);
+            const float3 d = camera_dir(v, px, py, 0.5f, 0.5f);
+            Hit h;
+            traverse<false>(s, o, d, -1, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x);
+            float4 r = make_float4(__int_as_float(-1), 0.0f, 0.0f, 0.0f);
+            if (h.tri >= 0) {
+                const float* uv = s.tri_uv + 6 * (size_t)h.tri;
+                const float w0 = 1.0f - h.u - h.v;
+                r = make_float4(__int_as_float(h.tri), w0 * __ldg(uv + 0) + h.u * __ldg(uv + 2) + h.v * __ldg(uv + 4),
+                                w0 * __ldg(uv + 1) + h.u * __ldg(uv + 3) + h.v * __ldg(uv + 5), 0.0f);
+                hit = true;
+            }
+            rec[p] = r;
+        }
+        const unsigned b = __ballot_sync(MR_FULL, hit);
+        if (lane_id() == 0 && b) atomicAdd(n_hit, (unsigned)__popc(b));
+    }
+}
+
+struct EmitLk {
+    float* ga;
+    float* gr;
+    __device__ void operator()(int key, const float (&v)[4]) const
+    {
+        if (ga) {
+            atomicAdd(ga + 3 * (size_t)key, v[0]);
+            atomicAdd(ga + 3 * (size_t)key + 1, v[1]);
+            atomicAdd(ga + 3 * (size_t)key + 2, v[2]);
+        }
+        if (gr) atomicAdd(gr + key, v[3]);
+    }
+};
+
+__device__ __forceinline__ float sgn(float x) { return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f); }
+
+__global__ void __launch_bounds__(256) k_lk_apply(SceneDev s, const float4* __restrict__ rec, int64_t npx,
+                                                  const unsigned int* __restrict__ n_hit, Rng rng, uint32_t view_index,
+                                                  float sigma, float wa, float wr, float* loss, float* ga, float* gr)
+{
+    const unsigned int n = *n_hit;
+    if (n == 0) return;  // uniform
+    const float inv = 1.0f / (float)n;
+    const float ca = wa * inv * (1.0f / 3.0f), cr = wr * inv;
+    const bool want_grad = ga || gr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float acc = 0.0f;
+    // uniform trip count per warp (the scatter and the loss reduction use every lane)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npx; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        int tri = -1;
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < npx) {
+            r = __ldg(rec + p);
+            tri = __float_as_int(r.x);
+        }
+        Taps t[2] = {};
+        float sa[3] = {0.f, 0.f, 0.f}, sr = 0.0f;
+        if (tri >= 0) {
+            const uint4 x = rng.draw((uint32_t)p, 0u, view_index, 0u, PURPOSE_SMOOTH, 0u);
+            const float es = sigma * (2.0f * u24(x.x) - 1.0f), et = sigma * (2.0f * u24(x.y) - 1.0f);
+            taps_at(s.tw, s.th, r.y, r.z, t[0]);
+            taps_at(s.tw, s.th, r.y + es, r.z + et, t[1]);
+            float da[3] = {0.f, 0.f, 0.f}, dr = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float sj = j ? -1.0f : 1.0f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = t[j].idx[k];
+                    const float w = sj * t[j].w[k];
+                    da[0] += w * __ldg(s.albedo + 3 * (size_t)i);
+                    da[1] += w * __ldg(s.albedo + 3 * (size_t)i + 1);
+                    da[2] += w * __ldg(s.albedo + 3 * (size_t)i + 2);
+                    dr += w * __ldg(s.rough + i);
+                }
+            }
+            acc += ca * (fabsf(da[0]) + fabsf(da[1]) + fabsf(da[2])) + cr * fabsf(dr);
+            for (int c = 0; c < 3; ++c) sa[c] = ca * sgn(da[c]);
+            sr = cr * sgn(dr);
+        }
+        if (want_grad) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float w = (j ? -1.0f : 1.0f) * t[j].w[k];
+                    const float vals[4] = {sa[0] * w, sa[1] * w, sa[2] * w, sr * w};
+                    scatter_agg<4>(tri >= 0 ? t[j].idx[k] : -1, vals, EmitLk{ga, gr});
+                }
+            }
+        }
+    }
+    if (loss) flush_loss(loss, acc);
+}
+
 unsigned grid_of(int64_t n, int sms)
 {
     const int64_t g = (n + 255) / 256;
@@ -172,6 +288,15 @@ void mr_edges_free(mirres_scene* s)
     s->n_edges = nullptr;
     s->deg = nullptr;
     s->ehash = nullptr;
+}
+
+void mr_launch_material_smoothness(const SceneDev& s, const ViewDev& v, uint32_t view_index, const Rng& rng,
+                                   float sigma, float wa, float wr, float4* rec, unsigned int* n_hit, float* loss,
+                                   float* ga, float* gr, int sms, cudaStream_t st)
+{
+    const int64_t npx = (int64_t)v.width * v.height;
+    k_lk_hits<<<grid_of(npx, sms), 256, sizeof(uint32_t) * MR_SSTACK * 256, st>>>(s, v, rec, n_hit);
+    k_lk_apply<<<grid_of(npx, sms), 256, 0, st>>>(s, rec, npx, n_hit, rng, view_index, sigma, wa, wr, loss, ga, gr);
 }
 
 void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_smooth, float w_offset, float* loss,

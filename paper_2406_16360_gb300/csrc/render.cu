@@ -464,33 +464,6 @@ __device__ __forceinline__ void brdf_cos_adjoint(float3 n, float3 wo, float3 wi,
     gm[7] += g_ci * wi.z + g_co * wo.z + g_cnh * h.z;
 }
 
-// warp-aggregated scatter: lanes holding the same key add their values and the key's first
-// lane issues one set of atomics. The sums are segmented suffix sums by pointer jumping along
-// each key's lanes in lane order, every key at once: ceil(log2(largest group)) steps of
-// NV + 1 shuffles, however many distinct keys the warp holds.
-template <int NV, class Emit>
-__device__ __forceinline__ void scatter_agg(int key, const float (&v)[NV], const Emit& emit)
-{
-    const int lane = lane_id();
-    const unsigned peers = __match_any_sync(MR_FULL, key);
-    const unsigned after = peers & ~((2u << lane) - 1u);  // my key's lanes above me
-    int nxt = (key >= 0 && after) ? __ffs(after) - 1 : -1;
-    float acc[NV];
-#pragma unroll
-    for (int c = 0; c < NV; ++c) acc[c] = v[c];
-    while (__any_sync(MR_FULL, nxt >= 0)) {
-        const int src = nxt >= 0 ? nxt : lane;
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-            const float o = __shfl_sync(MR_FULL, acc[c], src);
-            if (nxt >= 0) acc[c] += o;
-        }
-        const int n2 = __shfl_sync(MR_FULL, nxt, src);
-        nxt = nxt >= 0 ? n2 : -1;
-    }
-    if (key >= 0 && (__ffs(peers) - 1) == lane) emit(key, acc);
-}
-
 struct EmitEnv {
     float* g;
     __device__ void operator()(int key, const float (&v)[3]) const

@@ -96,6 +96,9 @@ void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const floa
                                   float4* gout, float* out3, int sms, cudaStream_t st);
 void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* pos, int sms, cudaStream_t st);
 // regular.cu: mesh regularisers over the scene's edge list (built by mr_edges_build)
+void mr_launch_material_smoothness(const SceneDev& s, const ViewDev& v, uint32_t view_index, const Rng& rng,
+                                   float sigma, float wa, float wr, float4* rec, unsigned int* n_hit, float* loss,
+                                   float* ga, float* gr, int sms, cudaStream_t st);
 void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_smooth, float w_offset, float* loss,
                             float* grad, int sms, cudaStream_t st);
 

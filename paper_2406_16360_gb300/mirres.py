@@ -23,7 +23,7 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
            "mirres_get_work_counters", "EawtParams", "mirres_eawt_record_bytes", "mirres_gbuffer", "mirres_eawt",
-           "mirres_eawt_backward", "mirres_mesh_regularizers",
+           "mirres_eawt_backward", "mirres_mesh_regularizers", "LkParams", "mirres_material_smoothness",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
 
 # limits of mirres_render_noalloc (include/mirres.h)
@@ -68,6 +68,11 @@ class Params(C.Structure):
 
 class EawtParams(C.Structure):
     _fields_ = [("sigma_rt", C.c_float), ("sigma_n", C.c_float), ("sigma_x", C.c_float), ("levels", C.c_int32)]
+
+
+class LkParams(C.Structure):
+    _fields_ = [("sigma", C.c_float), ("w_albedo", C.c_float), ("w_roughness", C.c_float), ("seed_lo", C.c_uint32),
+                ("seed_hi", C.c_uint32)]
 
 
 class Grads(C.Structure):
@@ -120,6 +125,8 @@ def lib():
                 "mirres_eawt": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, vp, sz, vp]),
                 "mirres_eawt_backward": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, sz, vp, vp]),
                 "mirres_mesh_regularizers": (st, [vp, vp, vp, C.c_float, C.c_float, vp, vp, vp]),
+                "mirres_material_smoothness": (st, [vp, vp, C.POINTER(View), i32, C.POINTER(LkParams), vp, vp, vp,
+                                                    vp]),
                 "mirres_bvh_export": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "mirres_env_export": (st, [vp, vp, vp, vp, vp, vp]),
                 "mirres_get_counters": (st, [vp, C.POINTER(C.c_uint64)]),
@@ -359,6 +366,16 @@ def mirres_mesh_regularizers(ctx: Context, scene: Scene, rest_verts, w_smooth, w
     _check("mirres_mesh_regularizers", lib().mirres_mesh_regularizers(ctx.handle, scene.handle, _ptr(rest_verts),
                                                                       float(w_smooth), float(w_offset), _ptr(loss),
                                                                       _ptr(grad_verts), _stream(stream)))
+
+
+def mirres_material_smoothness(ctx: Context, scene: Scene, view, view_index, params: LkParams, loss=None,
+                               grad_albedo=None, grad_roughness=None, stream=None):
+    """adds w_albedo L_albedo + w_roughness L_roughness of one view's pixel-centre hits to loss[0]
+    and its gradient to the texture gradients (float32 CUDA tensors; any may be None)"""
+    vs = _views([view])
+    _check("mirres_material_smoothness", lib().mirres_material_smoothness(
+        ctx.handle, scene.handle, vs, int(view_index), C.byref(params), _ptr(loss), _ptr(grad_albedo),
+        _ptr(grad_roughness), _stream(stream)))
 
 
 def mirres_bvh_export(scene: Scene, keys=None, left=None, right=None, parent=None, lo=None, hi=None, stream=None):
