@@ -489,7 +489,33 @@ def main():
                              "traffic": None, "kernel": "k_smooth + k_offset",
                              "bytes_note": "52 B per vertex + 8 B per unique edge; the mesh is L2-resident",
                              "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}}
-        rests = rg = None
+        # material smoothness L_k over every view's pixel-centre hits (one closest-hit ray per
+        # pixel, then the albedo / roughness lookup differences and their scattered gradient)
+        lkp = M.LkParams(0.01, 0.1, 0.1, 0, 0)
+        lk_l = torch.zeros(1, device=dev)
+        lk_ga = [torch.zeros_like(s.albedo) for s in gw.scenes]
+        lk_gr = [torch.zeros_like(s.roughness) for s in gw.scenes]
+
+        def lk_pass():
+            for vi, v in enumerate(gw.views):
+                sc_i = v.scene
+                M.mirres_material_smoothness(gw.ctx, gw.scenes[sc_i].handle, v, vi, lkp, lk_l, lk_ga[sc_i],
+                                             lk_gr[sc_i])
+
+        for _ in range(max(args.warmup, 3)):
+            lk_pass()
+        torch.cuda.synchronize()
+        e_lk = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e_lk[0].record()
+        for _ in range(args.steps):
+            lk_pass()
+        e_lk[1].record()
+        torch.cuda.synchronize()
+        ms_lk = e_lk[0].elapsed_time(e_lk[1]) / args.steps
+        pix = sum(v.width * v.height for v in gw.views)
+        regs["material_smoothness"] = {"ms_per_step": ms_lk, "pixels": pix, "mpix_per_s": pix / (ms_lk / 1e3) / 1e6,
+                                       "sigma": 0.01, "kernel": "k_lk_hits + k_lk_apply"}
+        rests = rg = lk_ga = lk_gr = None
 
     # FULL-mode adjoint (gradients through every vertex): the same step with grad_mode 1
     full = None
