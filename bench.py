@@ -233,6 +233,8 @@ def main():
     ap.add_argument("--no-eawt", action="store_true", help="skip the denoiser arm")
     ap.add_argument("--no-regularizers", action="store_true", help="skip the mesh regulariser arm")
     ap.add_argument("--no-reuse", action="store_true", help="skip the spatial-reuse arm")
+    ap.add_argument("--bvh", default="lbvh", choices=["lbvh", "ploc"],
+                    help="hierarchy builder run every step: Karras LBVH (the paper's) or PLOC clustering")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -261,7 +263,8 @@ def main():
     from paper_2406_16360_gb300.renderer import GpuWorkload
 
     w = make_workload(args.workload, args.views)
-    gw = GpuWorkload(w, local)
+    builder = M.MIRRES_BVH_PLOC if args.bvh == "ploc" else M.MIRRES_BVH_LBVH
+    gw = GpuWorkload(w, local, builder=builder)
     samples = w.samples
     stream = torch.cuda.current_stream()
     scenes = [s.handle for s in gw.scenes]
@@ -551,7 +554,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}",
+            "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}", bvh=args.bvh,
                            l2="flushed between timed steps (512 MiB write) and each step writes > 40 GB"),
             "mrays_per_s": mrays, "render_ms_per_step": msr_b / args.steps, "backward_ms_per_step": backward_ms,
             "batched": {"value": value, "ms_per_step": ms_b / args.steps, "mrays_per_s": mrays,

@@ -171,6 +171,21 @@ mirres_status mirres_scene_destroy(mirres_scene* scene);
  * stream once to read the check; MIRRES_ERR_ARG if any index is out of range). */
 mirres_status mirres_bvh_build(mirres_scene* scene, void* stream);
 
+/* Hierarchy builder used by the next mirres_bvh_build of this scene:
+ *   MIRRES_BVH_LBVH (default): Karras's binary radix tree over the Morton-sorted triangles, the
+ *     linear BVH the paper names (Appendix A, "Visibility estimation");
+ *   MIRRES_BVH_PLOC: parallel locally-ordered clustering (Meister and Bittner 2018) over the same
+ *     Morton-sorted triangles: each cluster pairs with the cluster within 16 positions whose
+ *     union box has the smallest surface area, mutual pairs merge, repeat. A lower-SAH tree
+ *     (fewer nodes visited per ray) for a slower build (about log F host round trips). Not in
+ *     the paper.
+ * Both write the same layout (root 0, leaves by Morton position), so refit, traversal and
+ * mirres_bvh_export are unchanged, and closest / any hits do not depend on the tree.
+ * MIRRES_ERR_ARG for an unknown builder. */
+#define MIRRES_BVH_LBVH 0
+#define MIRRES_BVH_PLOC 1
+mirres_status mirres_bvh_set_builder(mirres_scene* scene, int32_t builder);
+
 /* Refit after the vertices moved (the paper keeps its LBVH in step with the mesh at every
  * iteration, Appendix A): topology kept, boxes and packed triangles recomputed bottom-up; env tables
  * rebuilt. Asynchronous. Requires a prior mirres_bvh_build. */

@@ -263,6 +263,14 @@ extern "C" mirres_status mirres_scene_destroy(mirres_scene* s)
     return MIRRES_OK;
 }
 
+extern "C" mirres_status mirres_bvh_set_builder(mirres_scene* s, int32_t builder)
+{
+    if (!s) return arg_error("scene is NULL");
+    if (builder != MIRRES_BVH_LBVH && builder != MIRRES_BVH_PLOC) return arg_error("unknown BVH builder");
+    s->builder = builder;
+    return MIRRES_OK;
+}
+
 extern "C" mirres_status mirres_bvh_build(mirres_scene* s, void* stream)
 {
     if (!s) return arg_error("scene is NULL");

@@ -7,7 +7,11 @@
 //         per-node hierarchy construction -> bottom-up boxes with arrival counters, which
 //         also writes the traversal layout (both child boxes in the parent, 64 bytes) and
 //         the packed triangles (v0, e1, e2; 48 bytes) in leaf order.
+//         With the PLOC builder selected the Karras step is replaced by locally-ordered
+//         clustering over the same Morton-sorted leaves (a lower-SAH tree, same layout).
 // refit:  bounds (vertex box only) -> bottom-up boxes, topology kept.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace {
@@ -341,6 +345,225 @@ __global__ void k_bottom_up(const float* __restrict__ verts, const int32_t* __re
     }
 }
 
+// ---- PLOC hierarchy: parallel locally-ordered clustering (Meister and Bittner 2018) ------
+// The clusters start as the leaves in Morton order. In every iteration each cluster finds,
+// among the PLOC_R clusters on either side of it, the one whose union box has the smallest
+// surface area; pairs are ordered by (area, smaller position, larger position), a total order,
+// so the least pair of the array is always mutual and every iteration merges at least once.
+// Mutual pairs merge into a new node that takes the lower position, and the array is compacted
+// in order (a block scan of (kept, merged) flags). Node ids are handed out downwards from F - 2,
+// so the last merge -- the root -- gets id 0, and the left / right / parent arrays have the
+// layout the Karras build writes (leaves as ~position): bottom_up and refit work unchanged.
+constexpr int PLOC_R = 16;
+constexpr int PLOC_T = 256;
+constexpr int PLOC_ITEMS = 4;
+constexpr int PLOC_TILE = PLOC_T * PLOC_ITEMS;
+
+__global__ void __launch_bounds__(256) k_ploc_leaves(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                                                     int F, int V, const int32_t* __restrict__ perm, float4* lo,
+                                                     float4* hi, int32_t* node, int32_t* state)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) {
+        state[0] = F;
+        state[1] = F;
+        state[2] = F - 2;
+        state[3] = F - 2;
+    }
+    if (j >= F) return;
+    const int t = perm[j];
+    float3 p[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        int v = __ldg(tris + 3 * (size_t)t + c);
+        v = (v >= 0 && v < V) ? v : 0;
+        p[c] = f3(verts[3 * (size_t)v], verts[3 * (size_t)v + 1], verts[3 * (size_t)v + 2]);
+    }
+    lo[j] = make_float4(fminf(fminf(p[0].x, p[1].x), p[2].x), fminf(fminf(p[0].y, p[1].y), p[2].y),
+                        fminf(fminf(p[0].z, p[1].z), p[2].z), 0.0f);
+    hi[j] = make_float4(fmaxf(fmaxf(p[0].x, p[1].x), p[2].x), fmaxf(fmaxf(p[0].y, p[1].y), p[2].y),
+                        fmaxf(fmaxf(p[0].z, p[1].z), p[2].z), 0.0f);
+    node[j] = ~j;
+}
+
+// half the surface area of the union of two boxes; symmetric bit for bit, non-finite -> +inf
+__device__ __forceinline__ float union_area(float4 alo, float4 ahi, float4 blo, float4 bhi)
+{
+    const float dx = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
+    const float dy = fmaxf(ahi.y, bhi.y) - fminf(alo.y, blo.y);
+    const float dz = fmaxf(ahi.z, bhi.z) - fminf(alo.z, blo.z);
+    const float a = dx * dy + dy * dz + dz * dx;
+    return (a <= 3.402823466e38f) ? a : __int_as_float(0x7f800000);
+}
+
+__global__ void __launch_bounds__(PLOC_T) k_ploc_nn(const int32_t* __restrict__ state, int par,
+                                                    const float4* __restrict__ lo, const float4* __restrict__ hi,
+                                                    int32_t* __restrict__ nn)
+{
+    __shared__ float4 slo[PLOC_T + 2 * PLOC_R], shi[PLOC_T + 2 * PLOC_R];
+    const int n = state[par];
+    for (int base = blockIdx.x * PLOC_T; base < n; base += gridDim.x * PLOC_T) {  // block-uniform
+        for (int k = threadIdx.x; k < PLOC_T + 2 * PLOC_R; k += PLOC_T) {
+            const int g = base - PLOC_R + k;
+            if (g >= 0 && g < n) {
+                slo[k] = lo[g];
+                shi[k] = hi[g];
+            }
+        }
+        __syncthreads();
+        const int i = base + (int)threadIdx.x;
+        if (i < n) {
+            const float4 alo = slo[threadIdx.x + PLOC_R], ahi = shi[threadIdx.x + PLOC_R];
+            float best = __int_as_float(0x7f800000);
+            int bj = -1;
+            const int j0 = max(0, i - PLOC_R), j1 = min(n - 1, i + PLOC_R);
+            for (int j = j0; j <= j1; ++j) {
+                if (j == i) continue;
+                const int k = j - base + PLOC_R;
+                const float d = union_area(alo, ahi, slo[k], shi[k]);
+                // equal areas: the pair with the smaller (min, max) positions wins
+                bool take = d < best;
+                if (d == best) {
+                    if (bj < 0) {
+                        take = true;
+                    } else {
+                        const int a0 = min(i, j), a1 = max(i, j), b0 = min(i, bj), b1 = max(i, bj);
+                        take = (a0 < b0) || (a0 == b0 && a1 < b1);
+                    }
+                }
+                if (take) {
+                    best = d;
+                    bj = j;
+                }
+            }
+            nn[i] = bj;
+        }
+        __syncthreads();
+    }
+}
+
+// (kept, merged) of cluster i: a mutual pair keeps its lower position, which also merges
+__device__ __forceinline__ uint2 ploc_flags(const int32_t* __restrict__ nn, int i)
+{
+    const int j = nn[i];
+    const bool mutual = j >= 0 && nn[j] == i;
+    return make_uint2((mutual && j < i) ? 0u : 1u, (mutual && i < j) ? 1u : 0u);
+}
+
+__device__ __forceinline__ uint2 add2(uint2 a, uint2 b) { return make_uint2(a.x + b.x, a.y + b.y); }
+
+// exclusive scan of one uint2 per thread over a block of PLOC_T threads; returns the total
+__device__ __forceinline__ uint2 block_scan2(uint2 v, uint2& excl)
+{
+    __shared__ uint2 warp_sum[PLOC_T / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint2 inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned ox = __shfl_up_sync(0xffffffffu, inc.x, off), oy = __shfl_up_sync(0xffffffffu, inc.y, off);
+        if (lane >= off) inc = add2(inc, make_uint2(ox, oy));
+    }
+    if (lane == 31) warp_sum[w] = inc;
+    __syncthreads();
+    uint2 before = make_uint2(0u, 0u), total = make_uint2(0u, 0u);
+#pragma unroll
+    for (int k = 0; k < PLOC_T / 32; ++k) {
+        if (k < w) before = add2(before, warp_sum[k]);
+        total = add2(total, warp_sum[k]);
+    }
+    __syncthreads();
+    excl = add2(before, make_uint2(inc.x - v.x, inc.y - v.y));
+    return total;
+}
+
+__global__ void __launch_bounds__(PLOC_T) k_ploc_count(const int32_t* __restrict__ state, int par,
+                                                       const int32_t* __restrict__ nn, uint2* __restrict__ part)
+{
+    const int n = state[par];
+    const int nb = (n + PLOC_TILE - 1) / PLOC_TILE;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {  // block-uniform
+        uint2 c = make_uint2(0u, 0u);
+#pragma unroll
+        for (int k = 0; k < PLOC_ITEMS; ++k) {
+            const int i = b * PLOC_TILE + (int)threadIdx.x * PLOC_ITEMS + k;
+            if (i < n) c = add2(c, ploc_flags(nn, i));
+        }
+        uint2 excl;
+        const uint2 tot = block_scan2(c, excl);
+        if (threadIdx.x == 0) part[b] = tot;
+    }
+}
+
+// one block: exclusive scan of the per-block counts in place; the next iteration's cluster
+// count and node-id base go to the other parity's slots
+__global__ void __launch_bounds__(PLOC_T) k_ploc_scan(int32_t* __restrict__ state, int par, uint2* __restrict__ part)
+{
+    const int n = state[par];
+    const int nb = (n + PLOC_TILE - 1) / PLOC_TILE;
+    uint2 carry = make_uint2(0u, 0u);
+    for (int base = 0; base < nb; base += PLOC_T) {  // block-uniform
+        const int b = base + (int)threadIdx.x;
+        const uint2 v = b < nb ? part[b] : make_uint2(0u, 0u);
+        uint2 excl;
+        const uint2 tot = block_scan2(v, excl);
+        if (b < nb) part[b] = add2(carry, excl);
+        carry = add2(carry, tot);
+    }
+    if (threadIdx.x == 0) {
+        state[1 - par] = (int32_t)carry.x;
+        state[3 - par] = state[2 + par] - (int32_t)carry.y;
+    }
+}
+
+__global__ void __launch_bounds__(PLOC_T) k_ploc_compact(const int32_t* __restrict__ state, int par, int F,
+                                                         const int32_t* __restrict__ nn, const uint2* __restrict__ part,
+                                                         const float4* __restrict__ lo, const float4* __restrict__ hi,
+                                                         const int32_t* __restrict__ node, float4* __restrict__ olo,
+                                                         float4* __restrict__ ohi, int32_t* __restrict__ onode,
+                                                         int32_t* __restrict__ left, int32_t* __restrict__ right,
+                                                         int32_t* __restrict__ parent)
+{
+    const int n = state[par];
+    const int idb = state[2 + par];
+    const int nb = (n + PLOC_TILE - 1) / PLOC_TILE;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {  // block-uniform
+        const int i0 = b * PLOC_TILE + (int)threadIdx.x * PLOC_ITEMS;
+        uint2 f[PLOC_ITEMS];
+        uint2 c = make_uint2(0u, 0u);
+#pragma unroll
+        for (int k = 0; k < PLOC_ITEMS; ++k) {
+            f[k] = (i0 + k < n) ? ploc_flags(nn, i0 + k) : make_uint2(0u, 0u);
+            c = add2(c, f[k]);
+        }
+        uint2 excl;
+        block_scan2(c, excl);
+        uint2 pos = add2(part[b], excl);
+#pragma unroll
+        for (int k = 0; k < PLOC_ITEMS; ++k) {
+            const int i = i0 + k;
+            if (i >= n || !f[k].x) continue;
+            if (f[k].y) {
+                const int j = nn[i];
+                const int id = idb - (int)pos.y;
+                const int cl = node[i], cr = node[j];
+                left[id] = cl;
+                right[id] = cr;
+                parent[cl >= 0 ? cl : (F - 1) + ~cl] = id;
+                parent[cr >= 0 ? cr : (F - 1) + ~cr] = id;
+                const float4 al = lo[i], ah = hi[i], bl = lo[j], bh = hi[j];
+                olo[pos.x] = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.0f);
+                ohi[pos.x] = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.0f);
+                onode[pos.x] = id;
+            } else {
+                olo[pos.x] = lo[i];
+                ohi[pos.x] = hi[i];
+                onode[pos.x] = node[i];
+            }
+            pos = add2(pos, f[k]);
+        }
+    }
+}
+
 int grid_for(int n, int block) { return (n + block - 1) / block; }
 
 }  // namespace
@@ -396,7 +619,7 @@ void mr_bvh_free(mirres_scene* s)
 {
     void* ptrs[] = {s->keys, s->perm, s->left, s->right, s->parent, s->lo, s->hi, s->flags, s->nodes, s->ptri,
                     s->leaf_of, s->cent, s->codes[0], s->codes[1], s->vals[0], s->vals[1], s->hist, s->bounds,
-                    s->tmin, s->bad};
+                    s->tmin, s->bad, s->ploc_box, s->ploc_node, s->ploc_nn, s->ploc_part, s->ploc_state};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -428,6 +651,63 @@ static mirres_status bounds(mirres_scene* s, cudaStream_t st, int with_centroids
     return MIRRES_OK;
 }
 
+static mirres_status ploc_alloc(mirres_scene* s)
+{
+    if (s->ploc_box) return MIRRES_OK;
+    const size_t F = (size_t)s->desc.n_tris;
+    MR_TRY(mr_alloc(&s->ploc_box, 4 * F));
+    MR_TRY(mr_alloc(&s->ploc_node, 2 * F));
+    MR_TRY(mr_alloc(&s->ploc_nn, F));
+    MR_TRY(mr_alloc(&s->ploc_part, (F + PLOC_TILE - 1) / PLOC_TILE));
+    MR_TRY(mr_alloc(&s->ploc_state, 4));
+    return MIRRES_OK;
+}
+
+// PLOC hierarchy over the Morton-sorted leaves (F >= 2): batches of 16 iterations between
+// host checks of the cluster count; every iteration merges at least one pair
+static mirres_status ploc_build(mirres_scene* s, cudaStream_t st)
+{
+    MR_TRY(ploc_alloc(s));
+    const int F = s->desc.n_tris;
+    int dev = 0, sms = 1;
+    MR_CUDA(cudaGetDevice(&dev));
+    MR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    float4* lo[2] = {s->ploc_box, s->ploc_box + 2 * (size_t)F};
+    float4* hi[2] = {s->ploc_box + (size_t)F, s->ploc_box + 3 * (size_t)F};
+    int32_t* node[2] = {s->ploc_node, s->ploc_node + (size_t)F};
+    int32_t* state = s->ploc_state;
+    k_ploc_leaves<<<grid_for(F, 256), 256, 0, st>>>(s->desc.verts, s->desc.tris, F, s->desc.n_verts, s->perm, lo[0],
+                                                    hi[0], node[0], state);
+    const int g_nn = std::min(grid_for(F, PLOC_T), sms * 8), g_t = std::min(grid_for(F, PLOC_TILE), sms * 8);
+    int par = 0, n_prev = F;
+    int32_t h[5] = {F, F, 0, 0, -1};
+    while (h[par] > 1) {
+        for (int k = 0; k < 16; ++k) {
+            k_ploc_nn<<<g_nn, PLOC_T, 0, st>>>(state, par, lo[par], hi[par], s->ploc_nn);
+            k_ploc_count<<<g_t, PLOC_T, 0, st>>>(state, par, s->ploc_nn, s->ploc_part);
+            k_ploc_scan<<<1, PLOC_T, 0, st>>>(state, par, s->ploc_part);
+            k_ploc_compact<<<g_t, PLOC_T, 0, st>>>(state, par, F, s->ploc_nn, s->ploc_part, lo[par], hi[par], node[par],
+                                                   lo[par ^ 1], hi[par ^ 1], node[par ^ 1], s->left, s->right,
+                                                   s->parent);
+            par ^= 1;
+        }
+        MR_CUDA(cudaGetLastError());
+        MR_CUDA(cudaMemcpyAsync(h, state, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
+        MR_CUDA(cudaMemcpyAsync(h + 4, node[par], sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MR_CUDA(cudaStreamSynchronize(st));
+        if (h[par] > 1 && h[par] >= n_prev) {
+            mr_set_error("mirres_bvh_build: PLOC made no progress");
+            return MIRRES_ERR_STATE;
+        }
+        n_prev = h[par];
+    }
+    if (h[4] != 0 || h[2 + par] != -1) {
+        mr_set_error("mirres_bvh_build: PLOC did not end at the root");
+        return MIRRES_ERR_STATE;
+    }
+    return MIRRES_OK;
+}
+
 mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st)
 {
     const int F = s->desc.n_tris;
@@ -445,7 +725,11 @@ mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st)
         }
         k_keys<<<grid_for(F, 256), 256, 0, st>>>(s->codes[cur], s->vals[cur], F, s->keys, s->perm);
         MR_CUDA(cudaMemsetAsync(s->parent, 0xFF, sizeof(int32_t) * (size_t)(2 * F - 1), st));
-        if (F > 1) k_karras<<<grid_for(F - 1, 256), 256, 0, st>>>(s->keys, F, s->left, s->right, s->parent);
+        if (F > 1 && s->builder == MIRRES_BVH_PLOC) {
+            MR_TRY(ploc_build(s, st));
+        } else if (F > 1) {
+            k_karras<<<grid_for(F - 1, 256), 256, 0, st>>>(s->keys, F, s->left, s->right, s->parent);
+        }
         MR_CUDA(cudaGetLastError());
         MR_TRY(bottom_up(s, st));
     }

@@ -74,6 +74,13 @@ struct mirres_scene {
     unsigned int* bounds = nullptr;  // [12] ordered-uint bounds: centroid lo/hi, vertex lo/hi
     float* tmin = nullptr;           // [1]
     int32_t* bad = nullptr;          // [1] invalid index flag
+    // hierarchy builder: MIRRES_BVH_LBVH (Karras) or MIRRES_BVH_PLOC (clustering); PLOC scratch
+    int32_t builder = 0;
+    float4* ploc_box = nullptr;      // [2][2][F] cluster boxes (lo, hi), ping-pong
+    int32_t* ploc_node = nullptr;    // [2][F] cluster node ids, ping-pong
+    int32_t* ploc_nn = nullptr;      // [F] nearest neighbour of each cluster
+    uint2* ploc_part = nullptr;      // [ceil(F / 1024)] per-block (kept, merged) counts, then offsets
+    int32_t* ploc_state = nullptr;   // [4]: cluster count and next free node id, by iteration parity
     // env tables
     double* env_w = nullptr;         // [eh][ew]
     double* env_rowsum = nullptr;    // [eh]

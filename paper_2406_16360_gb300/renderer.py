@@ -19,7 +19,7 @@ def _dev(a, dtype, device):
 class DeviceScene:
     """Scene inputs as CUDA tensors plus the library scene handle (LBVH and env tables built)."""
 
-    def __init__(self, ctx: M.Context, scene, device="cuda"):
+    def __init__(self, ctx: M.Context, scene, device="cuda", builder=M.MIRRES_BVH_LBVH):
         self.device = torch.device(device)
         self.verts = _dev(scene.verts, torch.float32, self.device)
         self.tris = _dev(scene.tris, torch.int32, self.device)
@@ -30,6 +30,7 @@ class DeviceScene:
         self.env = _dev(scene.env, torch.float32, self.device)
         self.handle = M.mirres_scene_create(ctx, self.verts, self.tris, self.tri_uv, self.albedo, self.roughness,
                                             self.metallic, self.env)
+        M.mirres_bvh_set_builder(self.handle, builder)
         M.mirres_bvh_build(self.handle)
         self._versions = self._param_versions()
 
@@ -54,11 +55,11 @@ class DeviceScene:
 class GpuWorkload:
     """A synthetic workload resident on one GPU."""
 
-    def __init__(self, workload, device=0, ctx=None):
+    def __init__(self, workload, device=0, ctx=None, builder=M.MIRRES_BVH_LBVH):
         self.workload = workload
         self.ctx = ctx or M.mirres_context_create(device)
         self.device = torch.device("cuda", device)
-        self.scenes = [DeviceScene(self.ctx, s, self.device) for s in workload.scenes]
+        self.scenes = [DeviceScene(self.ctx, s, self.device, builder=builder) for s in workload.scenes]
         self.views = list(workload.views)
         self.samples = workload.samples
 
