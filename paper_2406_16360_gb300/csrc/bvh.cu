@@ -564,6 +564,19 @@ __global__ void __launch_bounds__(PLOC_T) k_ploc_compact(const int32_t* __restri
     }
 }
 
+// depth of every leaf (edges to the root), maximum into *depth; the walk stops after 1024 steps
+__global__ void __launch_bounds__(256) k_leaf_depth(const int32_t* __restrict__ parent, int F, int32_t* depth)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= F) return;
+    int d = 0, p = parent[(F - 1) + j];
+    while (p >= 0 && d < 1024) {
+        ++d;
+        p = parent[p];
+    }
+    atomicMax(depth, d);
+}
+
 int grid_for(int n, int block) { return (n + block - 1) / block; }
 
 }  // namespace
@@ -665,8 +678,9 @@ static mirres_status ploc_alloc(mirres_scene* s)
 
 // PLOC hierarchy over the Morton-sorted leaves (F >= 2): batches of 16 iterations between
 // host checks of the cluster count; every iteration merges at least one pair
-static mirres_status ploc_build(mirres_scene* s, cudaStream_t st)
+static mirres_status ploc_build(mirres_scene* s, cudaStream_t st, bool& too_deep)
 {
+    too_deep = false;
     MR_TRY(ploc_alloc(s));
     const int F = s->desc.n_tris;
     int dev = 0, sms = 1;
@@ -705,6 +719,13 @@ static mirres_status ploc_build(mirres_scene* s, cudaStream_t st)
         mr_set_error("mirres_bvh_build: PLOC did not end at the root");
         return MIRRES_ERR_STATE;
     }
+    // the traversal stack holds MR_SSTACK + MR_LSTACK entries, at most one per level below the
+    // root: a deeper clustering tree is replaced by the Karras tree (at most 63 deep)
+    MR_CUDA(cudaMemsetAsync(state, 0, sizeof(int32_t), st));
+    k_leaf_depth<<<grid_for(F, 256), 256, 0, st>>>(s->parent, F, state);
+    MR_CUDA(cudaMemcpyAsync(h, state, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MR_CUDA(cudaStreamSynchronize(st));
+    too_deep = h[0] > MR_SSTACK + MR_LSTACK;
     return MIRRES_OK;
 }
 
@@ -725,11 +746,14 @@ mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st)
         }
         k_keys<<<grid_for(F, 256), 256, 0, st>>>(s->codes[cur], s->vals[cur], F, s->keys, s->perm);
         MR_CUDA(cudaMemsetAsync(s->parent, 0xFF, sizeof(int32_t) * (size_t)(2 * F - 1), st));
+        bool karras = F > 1;
         if (F > 1 && s->builder == MIRRES_BVH_PLOC) {
-            MR_TRY(ploc_build(s, st));
-        } else if (F > 1) {
-            k_karras<<<grid_for(F - 1, 256), 256, 0, st>>>(s->keys, F, s->left, s->right, s->parent);
+            bool too_deep = false;
+            MR_TRY(ploc_build(s, st, too_deep));
+            karras = too_deep;
+            if (too_deep) MR_CUDA(cudaMemsetAsync(s->parent, 0xFF, sizeof(int32_t) * (size_t)(2 * F - 1), st));
         }
+        if (karras) k_karras<<<grid_for(F - 1, 256), 256, 0, st>>>(s->keys, F, s->left, s->right, s->parent);
         MR_CUDA(cudaGetLastError());
         MR_TRY(bottom_up(s, st));
     }

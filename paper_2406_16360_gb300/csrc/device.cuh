@@ -12,12 +12,21 @@
 #define MR_FULL 0xffffffffu
 
 // launch tuning knobs (overridable with -D at build time): minimum resident blocks of 256
-// threads per SM for the shading and adjoint kernels, and the RIS candidate loop's unroll
+// threads per SM for the shading, adjoint and traversal kernels, and the RIS candidate loop's
+// unroll
 #ifndef MR_SHADE_MINB
 #define MR_SHADE_MINB 4
 #endif
 #ifndef MR_BWD_MINB
 #define MR_BWD_MINB 4
+#endif
+#ifndef MR_TRACE_MINB
+#define MR_TRACE_MINB 0  // the batched closest-hit and shadow-ray kernels (0: no minimum)
+#endif
+#if MR_TRACE_MINB > 0
+#define MR_TRACE_BOUNDS __launch_bounds__(256, MR_TRACE_MINB)
+#else
+#define MR_TRACE_BOUNDS __launch_bounds__(256)
 #endif
 #ifndef MR_REFILL
 #define MR_REFILL 1  // batched wavefront: shadow rays traced by lane-refilling warps
@@ -37,8 +46,12 @@
 
 // traversal stack: the first MR_SSTACK entries live in shared memory (column per thread),
 // deeper entries in a small local array; an LBVH over 64-bit unique keys is at most 63 deep
+// (a clustering tree deeper than the stack is not used)
+#ifndef MR_SSTACK
 #define MR_SSTACK 32
-#define MR_LSTACK 32
+#endif
+#define MR_LSTACK (64 - MR_SSTACK)
+static_assert(MR_SSTACK >= 8 && MR_SSTACK <= 56, "MR_SSTACK out of range");
 
 // ---------------------------------------------------------------------------------------
 // scene as seen by the kernels

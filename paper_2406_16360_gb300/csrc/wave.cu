@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ vie
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(256) k_wclosest(const SceneDev* __restrict__ scenes,
+__global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
                                                   const ViewDev* __restrict__ views, int b, QueueDev q,
                                                   const unsigned int* count, unsigned int count_fixed, QueueDev hq,
                                                   unsigned int* count_hit, void* tape, uint64_t ntot,
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256) k_wclosest_refill(const SceneDev* __restr
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(256) k_wshadow_refill(const SceneDev* __restrict__ scenes,
+__global__ void MR_TRACE_BOUNDS k_wshadow_refill(const SceneDev* __restrict__ scenes,
                                                         const ViewDev* __restrict__ views, int b, ShadowDev sq,
                                                         const unsigned int* count, unsigned int* fetch, void* tape,
                                                         uint64_t ntot, int nvx, unsigned long long* counters)

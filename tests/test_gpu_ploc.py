@@ -165,6 +165,24 @@ def test_ploc_render_equals_lbvh_render(M, ctx):
         assert np.array_equal(x, y)
 
 
+def test_too_deep_clustering_falls_back_to_karras(M, ctx):
+    """triangles at x = 3^k: every cluster's nearest neighbour is the previous one, so the
+    clustering degenerates into a chain 79 deep, deeper than the 64-entry traversal stack; the
+    build then keeps the Karras tree, bit for bit the oracle's LBVH"""
+    from oracle import oracle as O
+    n = 80
+    x = 3.0 ** np.arange(n)
+    v = np.stack([np.c_[x, np.zeros(n), np.zeros(n)], np.c_[x, np.ones(n), np.zeros(n)],
+                  np.c_[x, np.zeros(n), np.ones(n)]], 1).reshape(-1, 3).astype(np.float32)
+    sc = _mesh_scene(v, np.arange(3 * n).reshape(-1, 3))
+    ds = _scene(ctx, M, sc, M.MIRRES_BVH_PLOC)
+    g = _export(M, ds, n)
+    o = O.lbvh(sc.verts, sc.tris)
+    for k in ("keys", "left", "right", "parent", "lo", "hi"):
+        assert np.array_equal(g[k], o[k]), k
+    ds.close()
+
+
 def test_set_builder_rejects_unknown(M, ctx):
     from paper_2406_16360_gb300.renderer import DeviceScene
     ds = DeviceScene(ctx, synth.tiny_scene(subdiv=1))
