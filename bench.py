@@ -35,6 +35,26 @@ EAWT_SIGMAS = (0.5, 0.3, 0.2)
 REUSE = (4, 8)
 
 
+# DRAM bytes per unit of the three stage kernels (closest-hit ray, RIS candidate, shadow ray),
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the first render's
+# launches on config 3 reduced to 2 views, divided by that render's unit counts; the 1-view
+# capture gives per-unit figures within 8%, so traffic is taken to grow in proportion and is
+# scaled to the bench's launches by their unit counts. Valid only for the kernel sources they
+# were measured on (SHA-256 prefix of wave.cu, device.cuh, path.cuh, bvh.cu); otherwise null.
+TRAFFIC_SOURCES = ("wave.cu", "device.cuh", "path.cuh", "bvh.cu")
+TRAFFIC_SHA = "ddd8900ce4598b52"
+TRAFFIC_PER_UNIT = {"closest": 97.89, "shade": 10.17, "shadow": 150.0}
+
+
+def _traffic_valid():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2406_16360_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16] == TRAFFIC_SHA
+
+
 def _hbm_peak():
     try:
         return float(json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
@@ -592,12 +612,18 @@ def main():
                    "shadow": 12.0 * work[2] + 27.0 * work[3]}
     names = {"shade": "k_wshade (shade + RIS stage)", "closest": "k_wclosest (closest-hit stage)",
              "shadow": "k_wshadow (shadow-ray stage)"}
+    units_per_render = {"closest": (cnt_b[0] + cnt_b[1]) / args.steps, "shade": cand_per_render,
+                        "shadow": cnt_b[2] / args.steps}
+    traffic_ok = _traffic_valid()
     roofs = {}
     for k in ("closest", "shade", "shadow"):
         ms_k, launches_k = stages[k]
         achieved = stage_flops[k] / (ms_k / 1e3) / 1e12
+        traffic = (TRAFFIC_PER_UNIT[k] * units_per_render[k] / max(launches_k, 1)) if traffic_ok else None
         roofs[k] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": names[k], "kernel_ms_per_launch": ms_k / max(launches_k, 1),
+                    "traffic": traffic, "traffic_unit": "bytes per launch",
+                    "traffic_basis": "ncu DRAM bytes per unit on a 2-view capture x units per launch",
+                    "kernel": names[k], "kernel_ms_per_launch": ms_k / max(launches_k, 1),
                     "kernel_share_of_render": ms_k / total_stage_ms, "flops_per_render": stage_flops[k],
                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock), non-tensor"}
     roofs["shade"].update(flops_per_candidate=per_cand, candidates_per_render=cand_per_render)
