@@ -799,20 +799,23 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
     plan.take<SceneDev>((size_t)n_scenes);
     plan.take<const float*>((size_t)n_views);
     plan.take<GradDev>((size_t)n_scenes);
+    plan.take<char>(nvx > 0 ? mr_full_scratch_bytes() : 0);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
     ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
     SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
     const float** d_dimg = cv.take<const float*>((size_t)n_views);
     GradDev* d_grads = cv.take<GradDev>((size_t)n_scenes);
+    void* full_scratch = cv.take<char>(nvx > 0 ? mr_full_scratch_bytes() : 0);
     MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_dimg, d_images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_grads, gdev.data(), sizeof(GradDev) * gdev.size(), cudaMemcpyHostToDevice, st));
     mr_launch_backward(d_scenes, d_views, n_views, total, make_rng(params), d_dimg, d_grads, tape, ctx->counters,
-                       ctx->sm_count, st, nvx);
+                       ctx->sm_count, st, nvx, full_scratch);
     MR_CUDA(cudaGetLastError());
-    ctx->host_launches += 1;
+    const uint64_t full_chunk = mr_full_chunk();
+    ctx->host_launches += 1 + ((nvx > 0 && full_chunk) ? 4 * ((total + full_chunk - 1) / full_chunk) : 0);
     return MIRRES_OK;
 }
 

@@ -500,6 +500,69 @@ struct EmitVert {
     }
 };
 
+// The FULL-mode vertex loops call the heavy helpers (shading point, BRDF, its adjoint, the
+// candidate redraw, the gradient scatters) through these wrappers; MR_FULL_NOINLINE=1 makes
+// them single out-of-line copies. That helped while one kernel held the primary and the later
+// vertices (it outgrew the instruction cache); the later-vertex kernel alone is faster inlined.
+#ifndef MR_FULL_NOINLINE
+#define MR_FULL_NOINLINE 0
+#endif
+#ifndef MR_FULL_MINB
+#define MR_FULL_MINB 2  // resident blocks of 256 threads per SM for the FULL-mode adjoint
+#endif
+#ifndef MR_FULL_SPLIT
+#define MR_FULL_SPLIT 1  // later vertices in their own kernel over samples grouped by vertex count
+#endif
+#define MR_FULL_CHUNK (1u << 25)  // samples classified per pass
+#if MR_FULL_NOINLINE
+#define MR_FULL_FN __device__ __noinline__
+#else
+#define MR_FULL_FN __device__ __forceinline__
+#endif
+
+MR_FULL_FN void fv_shade(const SceneDev& s, int tri, float u, float v, float3 d, Shade& sh)
+{
+    shade_at(s, tri, u, v, d, sh);
+}
+
+MR_FULL_FN float3 fv_brdf(float3 n, float3 wo, float3 wi, const Material& m) { return brdf_cos(n, wo, wi, m); }
+
+MR_FULL_FN void fv_brdf_adjoint(float3 n, float3 wo, float3 wi, const Material& m, float3 gq, float* gm)
+{
+    brdf_cos_adjoint(n, wo, wi, m, gq, gm);
+}
+
+// the selected candidate of vertex b, redrawn from its Philox block
+MR_FULL_FN void fv_candidate(const SceneDev& s, const Rng& rng, uint32_t pixel, uint32_t smp, uint32_t view,
+                             uint32_t b, uint32_t cand, float3& y, int& ytex)
+{
+    const uint4 x = rng.draw(pixel, smp, view, b, PURPOSE_CANDIDATE, cand);
+    env_candidate(s, x.x, x.y, x.w, y, ytex);
+}
+
+// one vertex's env and texture gradients; warp-collective when every lane is of one scene
+MR_FULL_FN void fv_scatter(int env_key, const float* env_v, const int* tex_key, const float* tex_v, const GradDev& gd,
+                           bool uniform_scene)
+{
+    if (uniform_scene) {
+        const float ev[3] = {env_v[0], env_v[1], env_v[2]};
+        scatter_agg<3>(env_key, ev, EmitEnv{gd.env});
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float tv[5] = {tex_v[5 * q], tex_v[5 * q + 1], tex_v[5 * q + 2], tex_v[5 * q + 3], tex_v[5 * q + 4]};
+            scatter_agg<5>(tex_key[q], tv, EmitTex{gd.albedo, gd.rough, gd.metal});
+        }
+    } else {
+        const float ev[3] = {env_v[0], env_v[1], env_v[2]};
+        if (env_key >= 0) EmitEnv{gd.env}(env_key, ev);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float tv[5] = {tex_v[5 * q], tex_v[5 * q + 1], tex_v[5 * q + 2], tex_v[5 * q + 3], tex_v[5 * q + 4]};
+            if (tex_key[q] >= 0) EmitTex{gd.albedo, gd.rough, gd.metal}(tex_key[q], tv);
+        }
+    }
+}
+
 // vertices per path the FULL-mode adjoint walks (primary included)
 #define MR_FULL_MAXV 16
 static_assert(MR_FULL_MAXV == MIRRES_FULL_MAX_BOUNCES, "FULL-mode vertex limit");
@@ -519,17 +582,16 @@ __device__ __forceinline__ int full_forward(const SceneDev& s, const Rng& rng, c
         const int tri = (int)*vx_at(tp, b, VX_TRI, g);
         if (tri < 0) break;
         Shade sh;
-        shade_at(s, tri, __uint_as_float(*vx_at(tp, b, VX_U, g)), __uint_as_float(*vx_at(tp, b, VX_V, g)), d, sh);
+        fv_shade(s, tri, __uint_as_float(*vx_at(tp, b, VX_U, g)), __uint_as_float(*vx_at(tp, b, VX_V, g)), d, sh);
         const float3 wo = f3(-d.x, -d.y, -d.z);
         float3 dir = f3(0.f, 0.f, 0.f), fcp = f3(0.f, 0.f, 0.f);
         const int cand = (int)*vx_at(tp, b, VX_CAND, g);
         const float wv = __uint_as_float(*vx_at(tp, b, VX_WV, g));
         if (cand >= 0 && wv != 0.0f) {
-            const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)cand);
             float3 y;
             int ytex;
-            env_candidate(s, x.x, x.y, x.w, y, ytex);
-            const float3 fy = brdf_cos(sh.n, wo, y, sh.m);
+            fv_candidate(s, rng, pixel, smp, view, (uint32_t)b, (uint32_t)cand, y, ytex);
+            const float3 fy = fv_brdf(sh.n, wo, y, sh.m);
             const float4 L = __ldg(s.env_texel + ytex);
             dir = f3(wv * L.x * fy.x, wv * L.y * fy.y, wv * L.z * fy.z);
         }
@@ -537,7 +599,7 @@ __device__ __forceinline__ int full_forward(const SceneDev& s, const Rng& rng, c
         const float3 wc = f3(__uint_as_float(*vx_at(tp, b, VX_WC, g)), __uint_as_float(*vx_at(tp, b, VX_WC + 1, g)),
                              __uint_as_float(*vx_at(tp, b, VX_WC + 2, g)));
         if (p > 0.0f) {
-            const float3 fc = brdf_cos(sh.n, wo, wc, sh.m);
+            const float3 fc = fv_brdf(sh.n, wo, wc, sh.m);
             fcp = f3(fc.x / p, fc.y / p, fc.z / p);
         }
         vbeta[b] = beta;
@@ -567,7 +629,7 @@ __device__ __forceinline__ void full_backward(const SceneDev& s, const Rng& rng,
     for (int b = wnv - 1; b >= 1; --b) {
         int env_key = -1, tex_key[4] = {-1, -1, -1, -1};
         float env_v[3] = {0.f, 0.f, 0.f};
-        float tex_v[4][5];
+        float tex_v[20];
         if (b < nv) {
             const float3 d = (b == 1) ? f3(tp.wc[0][g], tp.wc[1][g], tp.wc[2][g])
                                       : f3(__uint_as_float(*vx_at(tp, b - 1, VX_WC, g)),
@@ -575,58 +637,46 @@ __device__ __forceinline__ void full_backward(const SceneDev& s, const Rng& rng,
                                            __uint_as_float(*vx_at(tp, b - 1, VX_WC + 2, g)));
             const int tri = (int)*vx_at(tp, b, VX_TRI, g);
             Shade sh;
-            shade_at(s, tri, __uint_as_float(*vx_at(tp, b, VX_U, g)), __uint_as_float(*vx_at(tp, b, VX_V, g)), d, sh);
+            fv_shade(s, tri, __uint_as_float(*vx_at(tp, b, VX_U, g)), __uint_as_float(*vx_at(tp, b, VX_V, g)), d, sh);
             const float3 wo = f3(-d.x, -d.y, -d.z);
             const float3 bt = vbeta[b];
             float gm[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const int cand = (int)*vx_at(tp, b, VX_CAND, g);
             const float wv = __uint_as_float(*vx_at(tp, b, VX_WV, g));
             if (cand >= 0 && wv != 0.0f) {
-                const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)cand);
                 float3 y;
                 int ytex;
-                env_candidate(s, x.x, x.y, x.w, y, ytex);
-                const float3 fy = brdf_cos(sh.n, wo, y, sh.m);
+                fv_candidate(s, rng, pixel, smp, view, (uint32_t)b, (uint32_t)cand, y, ytex);
+                const float3 fy = fv_brdf(sh.n, wo, y, sh.m);
                 const float4 L = __ldg(s.env_texel + ytex);
                 env_key = ytex;
                 env_v[0] = gI.x * bt.x * wv * fy.x;
                 env_v[1] = gI.y * bt.y * wv * fy.y;
                 env_v[2] = gI.z * bt.z * wv * fy.z;
-                brdf_cos_adjoint(sh.n, wo, y, sh.m, f3(gI.x * bt.x * wv * L.x, gI.y * bt.y * wv * L.y, gI.z * bt.z * wv * L.z),
-                                 gm);
+                fv_brdf_adjoint(sh.n, wo, y, sh.m, f3(gI.x * bt.x * wv * L.x, gI.y * bt.y * wv * L.y, gI.z * bt.z * wv * L.z),
+                                gm);
             }
             const float p = __uint_as_float(*vx_at(tp, b, VX_P, g));
             if (p > 0.0f && (lin.x != 0.0f || lin.y != 0.0f || lin.z != 0.0f)) {
                 const float3 wc = f3(__uint_as_float(*vx_at(tp, b, VX_WC, g)),
                                      __uint_as_float(*vx_at(tp, b, VX_WC + 1, g)),
                                      __uint_as_float(*vx_at(tp, b, VX_WC + 2, g)));
-                brdf_cos_adjoint(sh.n, wo, wc, sh.m,
-                                 f3(gI.x * bt.x * lin.x / p, gI.y * bt.y * lin.y / p, gI.z * bt.z * lin.z / p), gm);
+                fv_brdf_adjoint(sh.n, wo, wc, sh.m,
+                                f3(gI.x * bt.x * lin.x / p, gI.y * bt.y * lin.y / p, gI.z * bt.z * lin.z / p), gm);
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 tex_key[q] = sh.tp.idx[q];
 #pragma unroll
-                for (int c = 0; c < 5; ++c) tex_v[q][c] = sh.tp.w[q] * gm[c];
+                for (int c = 0; c < 5; ++c) tex_v[5 * q + c] = sh.tp.w[q] * gm[c];
             }
             const float3 dr = vdir[b], fp = vfcp[b];
             lin = f3(dr.x + fp.x * lin.x, dr.y + fp.y * lin.y, dr.z + fp.z * lin.z);
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int c = 0; c < 5; ++c) tex_v[q][c] = 0.0f;
+            for (int c = 0; c < 20; ++c) tex_v[c] = 0.0f;
         }
-        if (uniform_scene) {
-            scatter_agg<3>(env_key, env_v, EmitEnv{gd.env});
-#pragma unroll
-            for (int q = 0; q < 4; ++q) scatter_agg<5>(tex_key[q], tex_v[q], EmitTex{gd.albedo, gd.rough, gd.metal});
-        } else {
-            if (env_key >= 0) EmitEnv{gd.env}(env_key, env_v);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (tex_key[q] >= 0) EmitTex{gd.albedo, gd.rough, gd.metal}(tex_key[q], tex_v[q]);
-        }
+        fv_scatter(env_key, env_v, tex_key, tex_v, gd, uniform_scene);
     }
 }
 
@@ -801,6 +851,143 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
     }
     for (int off = 16; off > 0; off >>= 1) n_diff += __shfl_xor_sync(MR_FULL, n_diff, off);
     if (lane_id() == 0 && n_diff) atomicAdd(counters + 4, n_diff);
+}
+
+// ---------------------------------------------------------------------------------------
+// FULL mode, later vertices: the primary vertex of every sample is differentiated by the
+// PRIMARY kernel; the vertices b >= 1 run here over the samples that have any, grouped by
+// their vertex count (longest first) so that the warp-uniform vertex loops keep their lanes
+// busy. Per chunk of samples: count per class, scan, scatter the sample ids, walk them.
+// ---------------------------------------------------------------------------------------
+// vertices the FULL walk of sample g visits (primary included), 0 when it has nothing to
+// walk: the same conditions and the same stopping rule as the walk itself
+__device__ __forceinline__ int full_count(const ViewDev* views, int n_views, const float* const* d_images,
+                                          const TapeDev& tp, uint64_t g)
+{
+    int vi;
+    const ViewDev& v = view_of(views, n_views, g, vi);
+    if (v.bounces < 2 || tp.tri[g] < 0) return 0;
+    const uint32_t pixel = (uint32_t)(g - v.offset) / (uint32_t)v.spp;
+    const float* dimg = d_images[vi];
+    const float inv_spp = 1.0f / (float)v.spp;
+    if (dimg[3 * (size_t)pixel] * inv_spp == 0.0f && dimg[3 * (size_t)pixel + 1] * inv_spp == 0.0f &&
+        dimg[3 * (size_t)pixel + 2] * inv_spp == 0.0f)
+        return 0;
+    if (tp.lind[0][g] == 0.0f && tp.lind[1][g] == 0.0f && tp.lind[2][g] == 0.0f) return 0;
+    if (!(tp.pind[g] > 0.0f)) return 0;
+    int nv = 1;
+    const int last = min(min(v.bounces - 1, tp.nvx), MR_FULL_MAXV - 1);
+    for (int b = 1; b <= last; ++b) {
+        if ((int)*vx_at(tp, b, VX_TRI, g) < 0) break;
+        nv = b + 1;
+        if (!(__uint_as_float(*vx_at(tp, b, VX_P, g)) > 0.0f)) break;
+    }
+    return nv;
+}
+
+// warp-aggregated add of 1 to counter[bin] for every lane with bin >= 0; returns the lane's
+// rank within its bin's block of slots (old value + lanes of the same bin below it)
+__device__ __forceinline__ unsigned int bin_append(int bin, unsigned int* counter)
+{
+    const unsigned peers = __match_any_sync(MR_FULL, bin);
+    const int leader = __ffs(peers) - 1;
+    unsigned int base = 0;
+    if (bin >= 0 && lane_id() == leader) base = atomicAdd(counter + bin, (unsigned)__popc(peers));
+    base = __shfl_sync(MR_FULL, base, leader);
+    return base + (unsigned)__popc(peers & lanemask_lt());
+}
+
+// pass 1 (scatter = false): per-class counts; pass 3 (scatter = true): sample ids (relative to
+// `first`) into their class's slots, classes ordered by decreasing vertex count
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_full_classify(const ViewDev* __restrict__ views, int n_views,
+                                                       const float* const* __restrict__ d_images, const void* tape,
+                                                       uint64_t total, int nvx, uint64_t first, uint32_t n,
+                                                       unsigned int* __restrict__ bins, uint32_t* __restrict__ list)
+{
+    const TapeDev tp = tape_of(const_cast<void*>(tape), total, nvx);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t rounds = (n + stride - 1) / stride;
+    for (uint32_t r = 0; r < rounds; ++r) {  // warp-uniform
+        const uint32_t i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const int nv = i < n ? full_count(views, n_views, d_images, tp, first + i) : 0;
+        const int bin = nv >= 2 ? MR_FULL_MAXV - nv : -1;
+        const unsigned int slot = bin_append(bin, SCATTER ? bins + 16 : bins);
+        if (SCATTER && bin >= 0) list[slot] = i;
+    }
+}
+
+// pass 2: cursors = exclusive scan of the counts, bins[32] = the number of listed samples
+__global__ void k_full_scan(unsigned int* bins)
+{
+    if (threadIdx.x != 0) return;
+    unsigned int acc = 0;
+    for (int k = 0; k < 16; ++k) {
+        bins[16 + k] = acc;
+        acc += bins[k];
+    }
+    bins[32] = acc;
+}
+
+// pass 4: the later vertices of the listed samples
+__global__ void __launch_bounds__(256, MR_FULL_MINB) k_full(const SceneDev* __restrict__ scenes,
+                                                           const ViewDev* __restrict__ views, int n_views,
+                                                           uint64_t total, Rng rng,
+                                                           const float* const* __restrict__ d_images,
+                                                           const GradDev* __restrict__ grads, const void* tape, int nvx,
+                                                           uint64_t first, const uint32_t* __restrict__ list,
+                                                           const unsigned int* __restrict__ bins, uint32_t cap)
+{
+    const TapeDev tp = tape_of(const_cast<void*>(tape), total, nvx);
+    const uint32_t n = min(bins[32], cap);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t rounds = (n + stride - 1) / stride;
+    for (uint32_t r = 0; r < rounds; ++r) {  // warp-uniform: full_backward's scatters are warp-collective
+        const uint32_t i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        int nv = 0, scene_id = 0;
+        float3 gI = f3(0.f, 0.f, 0.f);
+        float3 vbeta[MR_FULL_MAXV], vdir[MR_FULL_MAXV], vfcp[MR_FULL_MAXV];
+        uint32_t pixel = 0, smp = 0, view = 0;
+        uint64_t g = 0;
+        if (i < n) {
+            g = first + list[i];
+            int vi;
+            const ViewDev& v = view_of(views, n_views, g, vi);
+            scene_id = v.scene;
+            const SceneDev s = scenes[v.scene];
+            const uint32_t sid = (uint32_t)(g - v.offset);
+            pixel = sid / (uint32_t)v.spp;
+            smp = sid % (uint32_t)v.spp;
+            view = (uint32_t)v.index;
+            const float* dimg = d_images[vi];
+            const float inv_spp = 1.0f / (float)v.spp;
+            gI = f3(dimg[3 * (size_t)pixel] * inv_spp, dimg[3 * (size_t)pixel + 1] * inv_spp,
+                    dimg[3 * (size_t)pixel + 2] * inv_spp);
+            // the primary vertex again, for the throughput into vertex 1
+            const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+            const uint4 xc = rng.draw(pixel, smp, view, 0u, PURPOSE_CAMERA, 0u);
+            const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+            const float3 d = camera_dir(v, px, py, u24(xc.x), u24(xc.y));
+            const int tri = tp.tri[g];
+            float3 v0, e1, e2;
+            int tchk;
+            load_tri(s, __ldg(s.leaf_of + tri), v0, e1, e2, tchk);
+            float t, u, vv;
+            tri_solve(o, d, v0, e1, e2, t, u, vv);
+            Shade sh;
+            shade_at(s, tri, u, vv, d, sh);
+            const float3 wo = f3(-d.x, -d.y, -d.z);
+            const float3 wc = f3(tp.wc[0][g], tp.wc[1][g], tp.wc[2][g]);
+            const float pind = tp.pind[g];
+            const float3 fc0 = brdf_cos(sh.n, wo, wc, sh.m);
+            nv = full_forward(s, rng, tp, g, pixel, smp, view, v.bounces, f3(fc0.x / pind, fc0.y / pind, fc0.z / pind),
+                              wc, vbeta, vdir, vfcp);
+        }
+        const GradDev gd = grads[scene_id];
+        const unsigned same_scene = __match_any_sync(MR_FULL, scene_id);
+        full_backward(scenes[scene_id], rng, tp, g, pixel, smp, view, nv, gI, vbeta, vdir, vfcp, gd,
+                      same_scene == MR_FULL);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -998,16 +1185,39 @@ void mr_launch_resolve_all(const ViewDev* views, int n_views, const uint64_t* pi
                                                                      ntot);
 }
 
+size_t mr_full_scratch_bytes() { return sizeof(uint32_t) * ((size_t)MR_FULL_CHUNK + 64); }
+uint64_t mr_full_chunk() { return MR_FULL_SPLIT ? MR_FULL_CHUNK : 0; }
+
 void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
                         const float* const* d_images, const GradDev* grads, const void* tape,
-                        unsigned long long* counters, int sms, cudaStream_t st, int nvx)
+                        unsigned long long* counters, int sms, cudaStream_t st, int nvx, void* full_scratch)
 {
+#if MR_FULL_SPLIT
+    // the primary vertex of every sample (the tape's FULL records are read by k_full only)
+    k_backward<false, MR_BWD_MINB><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(
+        scenes, views, n_views, total, rng, d_images, grads, tape, nvx, counters);
+    if (nvx <= 0) return;
+    unsigned int* bins = static_cast<unsigned int*>(full_scratch);  // [0, 16) counts, [16, 32) cursors, [32] total
+    uint32_t* list = bins + 64;
+    for (uint64_t first = 0; first < total; first += MR_FULL_CHUNK) {
+        const uint32_t n = (uint32_t)std::min<uint64_t>(MR_FULL_CHUNK, total - first);
+        const unsigned grid = grid_cap(n, 256, sms * 8);
+        cudaMemsetAsync(bins, 0, sizeof(unsigned int) * 64, st);
+        k_full_classify<false><<<grid, 256, 0, st>>>(views, n_views, d_images, tape, total, nvx, first, n, bins, list);
+        k_full_scan<<<1, 32, 0, st>>>(bins);
+        k_full_classify<true><<<grid, 256, 0, st>>>(views, n_views, d_images, tape, total, nvx, first, n, bins, list);
+        k_full<<<grid, 256, 0, st>>>(scenes, views, n_views, total, rng, d_images, grads, tape, nvx, first, list, bins,
+                                     n);
+    }
+#else
+    (void)full_scratch;
     if (nvx > 0)
-        k_backward<true, 2><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng,
+        k_backward<true, MR_FULL_MINB><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng,
                                                                           d_images, grads, tape, nvx, counters);
     else
         k_backward<false, MR_BWD_MINB><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(
             scenes, views, n_views, total, rng, d_images, grads, tape, 0, counters);
+#endif
 }
 
 void mr_launch_account(unsigned long long* counters, const unsigned int* qcnt, int bounces, uint64_t primary,
