@@ -126,7 +126,11 @@ typedef struct {
  *   flags    bit 0: record CUDA events around every stage kernel of the batched wavefront
  *            (read back with mirres_stage_times); bit 1: the batched wavefront counts its
  *            traversal work (mirres_get_work_counters) -- a separately compiled variant of the
- *            traversal kernels, so that the uncounted launch keeps its register budget */
+ *            traversal kernels, so that the uncounted launch keeps its register budget; bit 2: the
+ *            batched wavefront resolves primary visibility by rasterisation (each triangle
+ *            projected into the view, each camera sample in its screen box tested with the
+ *            traversal's FP32 ray/triangle solve, closest by a 64-bit atomicMin on (t, triangle)),
+ *            as the paper does with a rasteriser, instead of tracing primary rays */
 typedef struct {
     int32_t ris_m;
     uint32_t seed_lo, seed_hi;

@@ -484,7 +484,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     key.max_b = max_b;
     key.M = M;
     key.sms = ctx->sm_count;
-    key.flags = flags & 3;
+    key.flags = flags & 7;
     key.nvx = nvx;
     key.reuse_k = reuse_k;
     key.reuse_radius = reuse_radius;
@@ -509,7 +509,8 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave_first.data(), n_waves, qa, qb, hq, sq,
                        qc, tp, ctx->counters, d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
                        (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr, nvx,
-                       (flags & 2) != 0, reuse_k, reuse_radius, res, temporal, temporal_cap, hist);
+                       (flags & 2) != 0, reuse_k, reuse_radius, res, temporal, temporal_cap, hist, vdev.data(),
+                       sdev.data(), (flags & 4) != 0);
         ctx->stage_pairs = (flags & 1) ? pairs : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -524,7 +525,18 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
             return mr_cuda_status(ei, "mirres_render: graph instantiation");
         }
         std::memcpy(ctx->graph_key, &key, sizeof(key));
-        ctx->graph_launches = (unsigned long long)mr_wave_launches(n_waves, max_b, reuse, temporal);
+        int raster_launches = 0;
+        if (flags & 4) {
+            for (int wv = 0; wv < n_waves; ++wv) {
+                const uint64_t f0 = wave_first[(size_t)wv];
+                const uint64_t f1 = wv + 1 < n_waves ? wave_first[(size_t)wv + 1] : total;
+                for (const ViewDev& v : vdev) {
+                    const uint64_t vn = (uint64_t)v.width * v.height * v.spp;
+                    if (v.offset < f1 && v.offset + vn > f0 && sdev[(size_t)v.scene].n_tris > 0) raster_launches += 2;
+                }
+            }
+        }
+        ctx->graph_launches = (unsigned long long)mr_wave_launches(n_waves, max_b, reuse, temporal, raster_launches);
     }
     MR_CUDA(cudaGraphLaunch(ctx->graph, st));
     ctx->host_launches += ctx->graph_launches;

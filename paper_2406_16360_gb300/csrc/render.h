@@ -111,6 +111,6 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
                     unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
                     int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
-                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist);
-int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal);
+                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist, const ViewDev* hviews, const SceneDev* hscenes, bool raster);
+int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal, int raster_launches);
 int mr_wave_stage_pairs(int n_waves, int max_bounces);

@@ -56,7 +56,7 @@ __global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
                                                   const ViewDev* __restrict__ views, int b, QueueDev q,
                                                   const unsigned int* count, unsigned int count_fixed, QueueDev hq,
                                                   unsigned int* count_hit, void* tape, uint64_t ntot,
-                                                  unsigned long long* counters)
+                                                  unsigned long long* counters, const unsigned long long* raster)
 {
     extern __shared__ uint32_t sstk[];
     const TapeDev tp = tape_of(tape, ntot);
@@ -76,10 +76,26 @@ __global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
             qb = q.b[i];
             const ViewDev& v = views[__float_as_int(qb.w)];
             const SceneDev& s = scenes[v.scene];
-            const int nodes = traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), *s.tmin_dev,
-                                              __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x,
-                                              COUNT ? &n_tri : nullptr);
-            if (COUNT) n_box += 2u * (unsigned int)max(nodes, 0);
+            if (raster) {
+                // primary visibility from the rasteriser: the winning triangle, solved again
+                // with the same arithmetic for its (t, u, v)
+                const unsigned long long key = raster[i];
+                h.t = __int_as_float(0x7f800000);
+                h.u = h.v = 0.0f;
+                if (key != ~0ull) {
+                    const int tri = (int)(unsigned)(key & 0xffffffffull);
+                    float3 v0, e1, e2;
+                    int tchk;
+                    load_tri(s, __ldg(s.leaf_of + tri), v0, e1, e2, tchk);
+                    tri_solve(xyz(a), xyz(qd), v0, e1, e2, h.t, h.u, h.v);
+                    h.tri = tri;
+                }
+            } else {
+                const int nodes = traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), *s.tmin_dev,
+                                                  __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x,
+                                                  COUNT ? &n_tri : nullptr);
+                if (COUNT) n_box += 2u * (unsigned int)max(nodes, 0);
+            }
             if (h.tri < 0 && b == 0) {
                 const uint64_t g = v.offset + __float_as_uint(qd.w);
                 const float4 L = __ldg(s.env_texel + env_texel_of(s, xyz(qd)));
@@ -545,6 +561,138 @@ __global__ void MR_TRACE_BOUNDS k_wshadow_refill(const SceneDev* __restrict__ sc
     if (COUNT) flush_work(counters, CNT_SBOX, n_box, (unsigned int)n_tri);
 }
 
+// ---- primary visibility by rasterisation ------------------------------------------------
+// The paper resolves primary visibility with a rasteriser (nvdiffrast). Here each triangle is
+// projected into every view of the wave, and each camera sample inside its conservative
+// screen box is tested with the same FP32 ray/triangle solve the traversal runs, against the
+// sample's own jittered direction from the ray queue; a 64-bit atomicMin on (t bits, triangle)
+// keeps the smallest t, then the smallest triangle id -- the traversal's closest-hit rule. The
+// closest-hit stage then reads the winner instead of traversing. Small triangles take one
+// thread each; triangles whose box holds more than RASTER_SMALL samples (or that cross the
+// camera plane) take a block each.
+constexpr int RASTER_SMALL = 256;
+constexpr unsigned long long RASTER_NONE = ~0ull;
+
+struct RasterBox {
+    int x0, y0, x1, y1;  // inclusive pixel range, empty when x0 > x1
+    bool all;            // crosses the camera plane: every pixel
+};
+
+__device__ __forceinline__ RasterBox raster_box(const ViewDev& v, float3 a, float3 b, float3 c)
+{
+    const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+    const float3 p[3] = {sub(a, o), sub(b, o), sub(c, o)};
+    float zs[3], xs[3], ys[3];
+    int behind = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float cx = v.c2w[0] * p[k].x + v.c2w[4] * p[k].y + v.c2w[8] * p[k].z;
+        const float cy = v.c2w[1] * p[k].x + v.c2w[5] * p[k].y + v.c2w[9] * p[k].z;
+        zs[k] = v.c2w[2] * p[k].x + v.c2w[6] * p[k].y + v.c2w[10] * p[k].z;
+        behind += zs[k] <= 1e-6f ? 1 : 0;
+        xs[k] = v.K[0] * cx / zs[k] + v.K[2];
+        ys[k] = v.K[1] * cy / zs[k] + v.K[3];
+    }
+    RasterBox r{0, 0, v.width - 1, v.height - 1, true};
+    if (behind == 3) {  // no forward ray reaches a point on or behind the camera plane
+        r.x0 = 1;
+        r.x1 = 0;
+        r.all = false;
+        return r;
+    }
+    if (behind > 0) return r;
+    // a sample at (X, Y) = (px + jx, py + jy) lies in pixel (floor X, floor Y); 0.01 px of slack
+    // covers the rounding of the projection
+    const float xmin = fminf(fminf(xs[0], xs[1]), xs[2]) - 0.01f, xmax = fmaxf(fmaxf(xs[0], xs[1]), xs[2]) + 0.01f;
+    const float ymin = fminf(fminf(ys[0], ys[1]), ys[2]) - 0.01f, ymax = fmaxf(fmaxf(ys[0], ys[1]), ys[2]) + 0.01f;
+    r.all = false;
+    r.x0 = (int)fmaxf(floorf(xmin), 0.0f);
+    r.y0 = (int)fmaxf(floorf(ymin), 0.0f);
+    r.x1 = (int)fminf(floorf(xmax), (float)(v.width - 1));
+    r.y1 = (int)fminf(floorf(ymax), (float)(v.height - 1));
+    if (!(xmax >= 0.0f) || !(ymax >= 0.0f) || !(xmin <= (float)v.width) || !(ymin <= (float)v.height)) {
+        r.x0 = 1;
+        r.x1 = 0;
+    }
+    return r;
+}
+
+// test sample (pixel, s) of view v against triangle `tri` (samples outside the wave are skipped)
+__device__ __forceinline__ void raster_sample(const ViewDev& v, float3 o, const float4* __restrict__ qd, uint64_t first,
+                                              uint32_t n, uint32_t pixel, int s, float3 v0, float3 e1, float3 e2,
+                                              int tri, float tmin, unsigned long long* keys, int& tests)
+{
+    const int64_t i = (int64_t)(v.offset + (uint64_t)pixel * (uint32_t)v.spp + (uint32_t)s) - (int64_t)first;
+    if (i < 0 || i >= (int64_t)n) return;
+    const float3 d = xyz(__ldg(qd + i));
+    float t, u, w;
+    ++tests;
+    if (!tri_solve(o, d, v0, e1, e2, t, u, w)) return;
+    if (!(u >= 0.0f && w >= 0.0f && u + w <= 1.0f && t > tmin)) return;
+    const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)tri;
+    if (key < keys[i]) atomicMin(keys + i, key);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_raster_small(const SceneDev* __restrict__ scenes,
+                                                      const ViewDev* __restrict__ views, int vi, uint64_t first,
+                                                      uint32_t n, const float4* __restrict__ qd,
+                                                      unsigned long long* keys, unsigned long long* counters)
+{
+    const ViewDev& v = views[vi];
+    const SceneDev& s = scenes[v.scene];
+    const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+    const float tmin = *s.tmin_dev;
+    int tests = 0;
+    for (int leaf = blockIdx.x * blockDim.x + threadIdx.x; leaf < s.n_tris; leaf += gridDim.x * blockDim.x) {
+        float3 v0, e1, e2;
+        int tri;
+        load_tri(s, leaf, v0, e1, e2, tri);
+        const RasterBox r = raster_box(v, v0, add(v0, e1), add(v0, e2));
+        if (r.all || r.x0 > r.x1 || r.y0 > r.y1) continue;
+        if ((int64_t)(r.x1 - r.x0 + 1) * (r.y1 - r.y0 + 1) * v.spp > RASTER_SMALL) continue;
+        for (int py = r.y0; py <= r.y1; ++py)
+            for (int px = r.x0; px <= r.x1; ++px)
+                for (int k = 0; k < v.spp; ++k)
+                    raster_sample(v, o, qd, first, n, (uint32_t)(py * v.width + px), k, v0, e1, e2, tri, tmin, keys,
+                                  tests);
+    }
+    if (COUNT) flush_work(counters, CNT_CBOX, 0u, (unsigned int)tests);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_raster_big(const SceneDev* __restrict__ scenes,
+                                                    const ViewDev* __restrict__ views, int vi, uint64_t first,
+                                                    uint32_t n, const float4* __restrict__ qd,
+                                                    unsigned long long* keys, unsigned long long* counters)
+{
+    const ViewDev& v = views[vi];
+    const SceneDev& s = scenes[v.scene];
+    const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+    const float tmin = *s.tmin_dev;
+    int tests = 0;
+    for (int leaf = blockIdx.x; leaf < s.n_tris; leaf += gridDim.x) {  // block-uniform
+        float3 v0, e1, e2;
+        int tri;
+        load_tri(s, leaf, v0, e1, e2, tri);
+        const RasterBox r = raster_box(v, v0, add(v0, e1), add(v0, e2));
+        if (r.x0 > r.x1 || r.y0 > r.y1) continue;
+        const int bw = r.x1 - r.x0 + 1, bh = r.y1 - r.y0 + 1;
+        const int64_t cnt = (int64_t)bw * bh * v.spp;
+        if (!r.all && cnt <= RASTER_SMALL) continue;
+        for (int64_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const int k = (int)(j % v.spp);
+            const int64_t pj = j / v.spp;
+            const int px = r.x0 + (int)(pj % bw), py = r.y0 + (int)(pj / bw);
+            raster_sample(v, o, qd, first, n, (uint32_t)(py * v.width + px), k, v0, e1, e2, tri, tmin, keys, tests);
+        }
+    }
+    if (COUNT) {
+        // every lane of the block reaches here; reduce per warp
+        flush_work(counters, CNT_CBOX, 0u, (unsigned int)tests);
+    }
+}
+
 unsigned grid_cap(uint64_t n, int block, int cap)
 {
     const uint64_t g = (n + block - 1) / block;
@@ -561,7 +709,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
                     unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
                     int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
-                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist)
+                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist,
+                    const ViewDev* hviews, const SceneDev* hscenes, bool raster)
 {
     const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
     // the refilling kernels run one resident wave of blocks
@@ -592,12 +741,31 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         for (int b = 0; b < max_bounces; ++b) {
             const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
             mark(0, true);
+            unsigned long long* keys = nullptr;
+            if (raster && b == 0) {
+                // the next-bounce queue is free until shading fills it: its last array holds
+                // the per-sample depth keys (8 of its 16 bytes per entry)
+                keys = reinterpret_cast<unsigned long long*>(nxt.bi);
+                cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * n, st);
+                for (int vi = 0; vi < n_views; ++vi) {
+                    const ViewDev& hv = hviews[vi];
+                    const uint64_t vn = (uint64_t)hv.width * hv.height * hv.spp;
+                    if (hv.offset >= first + n || hv.offset + vn <= first) continue;
+                    const int F = hscenes[hv.scene].n_tris;
+                    if (F <= 0) continue;
+                    (count ? k_raster_small<true> : k_raster_small<false>)<<<grid_cap((uint64_t)F, 256, sms * 8), 256,
+                                                                            0, st>>>(scenes, views, vi, first, n,
+                                                                                     cur.d, keys, counters);
+                    (count ? k_raster_big<true> : k_raster_big<false>)<<<(unsigned)(sms * 2), 256, 0, st>>>(
+                        scenes, views, vi, first, n, cur.d, keys, counters);
+                }
+            }
             if (MR_REFILL_CLOSEST && b > 0)  // primary rays stay coherent in the plain stage kernel
                 (count ? k_wclosest_refill<true> : k_wclosest_refill<false>)<<<grid_c, 256, smem, st>>>(
                     scenes, views, cur, cnt_in, hq, qc + 3 * b, fetch + 2 * b, counters);
             else
                 (count ? k_wclosest<true> : k_wclosest<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
-                    scenes, views, b, cur, cnt_in, n, hq, qc + 3 * b, tape, total, counters);
+                    scenes, views, b, cur, cnt_in, n, hq, qc + 3 * b, tape, total, counters, keys);
             mark(0, false);
             mark(1, true);
             const bool reuse_b = b == 0 && res.ytex != nullptr;
@@ -632,8 +800,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
 
 int mr_wave_stage_pairs(int n_waves, int max_bounces) { return n_waves * (1 + 3 * max_bounces); }
 
-int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal)
+int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal, int raster_launches)
 {
     const int extra = (reuse ? 1 : 0) + (temporal == 2 ? 1 : 0) + (temporal ? 1 : 0);
-    return n_waves * (2 + 3 * max_bounces + extra) + 1;
+    return n_waves * (2 + 3 * max_bounces + extra) + 1 + raster_launches;
 }
