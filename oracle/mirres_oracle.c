@@ -34,8 +34,11 @@
 #define TAU_FRAME 1e-5  /* |n.z| in the orthonormal-basis sign choice */
 #define TAU_GRAZE 2e-3  /* cos of the viewing angle at the primary vertex: below it an FP32
                          * evaluation of the BRDF carries a relative error above ~3e-5 */
+#define TAU_LEAK 1e-5   /* |dir . n_face| of a light or continuation direction when shading
+                         * normals are interpolated (directions below the face are dropped) */
 
-enum { MK_NONE = 0, MK_BARY, MK_TMIN, MK_TDEPTH, MK_ACC, MK_CDF, MK_LOBE, MK_FLIP, MK_ENV, MK_FRAME, MK_GRAZE };
+enum { MK_NONE = 0, MK_BARY, MK_TMIN, MK_TDEPTH, MK_ACC, MK_CDF, MK_LOBE, MK_FLIP, MK_ENV, MK_FRAME, MK_GRAZE,
+       MK_LEAK };
 
 /* ---------------------------------------------------------------------------------------
  * small vector algebra (FP64)
@@ -96,6 +99,11 @@ struct orc_scene {
     double* cond; double* marg; double* prob; double total; int env_ok;
     double tmin, diag;
     int nnodes; Node* nodes; int32_t* order;
+    /* shading normals: 0 face normal, 1 interpolated from area-weighted vertex normals */
+    int normals;
+    double* VA;  /* [V][3] sum of the incident faces' (b - a) x (c - a) */
+    double* VN;  /* [V][3] VA normalised (0 for a vertex without area) */
+    int32_t* vf_off; int32_t* vf;  /* incident faces of each vertex (CSR) */
 };
 
 static __thread const double* g_cent;
@@ -232,6 +240,33 @@ orc_scene* orc_scene_new(const orc_scene_desc* d)
     s->diag = s->nf ? sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
                            (hi[2] - lo[2]) * (hi[2] - lo[2])) : 0.0;
     s->tmin = 1e-5 * s->diag; /* self-intersection threshold: 1e-5 of the scene diagonal */
+    /* area-weighted vertex normals and the faces around every vertex (interpolated normals) */
+    s->VA = (double*)calloc((size_t)3 * (s->nv ? s->nv : 1), sizeof(double));
+    s->VN = (double*)calloc((size_t)3 * (s->nv ? s->nv : 1), sizeof(double));
+    s->vf_off = (int32_t*)calloc((size_t)s->nv + 1, sizeof(int32_t));
+    s->vf = (int32_t*)malloc(sizeof(int32_t) * (size_t)3 * (s->nf ? s->nf : 1));
+    for (int t = 0; t < s->nf; ++t) {
+        v3 a, b, c;
+        tri_verts(s, t, &a, &b, &c);
+        v3 N = vcross(vsub(b, a), vsub(c, a));
+        for (int k = 0; k < 3; ++k) {
+            int vi = s->F[3 * t + k];
+            vstore(s->VA + 3 * vi, vadd(vload(s->VA + 3 * vi), N));
+            s->vf_off[vi + 1]++;
+        }
+    }
+    for (int i = 0; i < s->nv; ++i) {
+        s->vf_off[i + 1] += s->vf_off[i];
+        double l = vlen(vload(s->VA + 3 * i));
+        if (l > 0.0) vstore(s->VN + 3 * i, vscale(vload(s->VA + 3 * i), 1.0 / l));
+    }
+    {
+        int32_t* cur = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->nv > 0 ? s->nv : 1));
+        for (int i = 0; i < s->nv; ++i) cur[i] = s->vf_off[i];
+        for (int t = 0; t < s->nf; ++t)
+            for (int k = 0; k < 3; ++k) s->vf[cur[s->F[3 * t + k]]++] = t;
+        free(cur);
+    }
     /* median-split BVH */
     s->order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->nf ? s->nf : 1));
     s->nodes = (Node*)malloc(sizeof(Node) * (size_t)(2 * s->nf + 1));
@@ -256,7 +291,15 @@ void orc_scene_free(orc_scene* s)
     if (!s) return;
     free(s->V); free(s->F); free(s->UV); free(s->alb); free(s->rgh); free(s->met); free(s->env);
     free(s->cond); free(s->marg); free(s->prob); free(s->nodes); free(s->order);
+    free(s->VA); free(s->VN); free(s->vf_off); free(s->vf);
     free(s);
+}
+
+void orc_scene_set_normals(orc_scene* s, int32_t mode) { s->normals = mode ? 1 : 0; }
+
+void orc_vertex_normals(const orc_scene* s, double* out)
+{
+    memcpy(out, s->VN, sizeof(double) * (size_t)3 * s->nv);
 }
 
 double orc_scene_tmin(const orc_scene* s) { return s->tmin; }
@@ -851,7 +894,11 @@ typedef struct {
     int tri;
     double u, v, t;
     v3 x, n, N;      /* hit point, shading normal (flipped towards -d), unflipped face normal */
-    double sign;     /* n = sign * N / |N| */
+    double sign;     /* face normal towards the viewer: ng = sign * N / |N| */
+    v3 ng;           /* face normal towards the viewer */
+    int interp;      /* 1: n is the interpolated normal nsg * S / |S| */
+    v3 S;            /* w0 VN_a + u VN_b + v VN_c */
+    double nsg;      /* +-1: S turned to the side of ng */
     v3 e1, e2;
     double su, sv;   /* texture coordinate */
     Taps tp;
@@ -870,9 +917,27 @@ static void shade_at(const orc_scene* s, int tri, double u, double v, double t, 
     note(mg, fabs(nd) / TAU_FLIP, MK_FLIP);
     sh->sign = (nd > 0.0) ? -1.0 : 1.0;
     sh->n = vscale(nh, sh->sign);
+    sh->ng = sh->n;
     sh->x = vadd(a, vadd(vscale(sh->e1, u), vscale(sh->e2, v)));
     const double* uv = s->UV + 6 * tri;
     double w0 = 1.0 - u - v;
+    sh->interp = 0; sh->nsg = 1.0; sh->S = V3(0, 0, 0);
+    if (s->normals) {
+        /* interpolated shading normal: the barycentric blend of the vertex normals, turned to
+         * the viewer's side of the face */
+        const int32_t* f = s->F + 3 * tri;
+        v3 S = vadd(vadd(vscale(vload(s->VN + 3 * f[0]), w0), vscale(vload(s->VN + 3 * f[1]), u)),
+                    vscale(vload(s->VN + 3 * f[2]), v));
+        double l = vlen(S);
+        if (l > 0.0) {
+            double cg = vdot(S, sh->ng) / l;
+            note(mg, fabs(cg) / TAU_FLIP, MK_FLIP);
+            sh->nsg = cg < 0.0 ? -1.0 : 1.0;
+            sh->n = vscale(S, sh->nsg / l);
+            sh->S = S;
+            sh->interp = 1;
+        }
+    }
     sh->su = w0 * uv[0] + u * uv[2] + v * uv[4];
     sh->sv = w0 * uv[1] + u * uv[3] + v * uv[5];
     taps_at(s->tw, s->th, sh->su, sh->sv, &sh->tp);
@@ -958,6 +1023,21 @@ static v3 camera_dir(const Ctx* c, int px, int py, int smp)
  * p_hat, the weight sum and the number of candidates behind the reservoir (m). */
 typedef struct { int sel, ytex; uint32_t ysub; v3 y; double f[3], phat, wsum, m; } Ris;
 
+/* f_r cos of a light direction at a shading point; with interpolated normals a direction
+ * below the face gets nothing (its shadow ray would leave through the surface) */
+static void light_brdf(const Shade* sh, v3 wo, v3 dir, int kind, double fc[3], Margin* mg)
+{
+    if (sh->interp) {
+        double cg = vdot(dir, sh->ng);
+        note(mg, fabs(cg) / TAU_LEAK, MK_LEAK);
+        if (!(cg > 0.0)) {
+            fc[0] = fc[1] = fc[2] = 0.0;
+            return;
+        }
+    }
+    brdf_cos(sh->n, wo, dir, sh->alb, sh->rgh, sh->met, kind, fc);
+}
+
 static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, v3 wo, Margin* mg, int64_t* cnt,
                    Ris* r)
 {
@@ -973,7 +1053,7 @@ static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, 
         int tex;
         double q = env_sample_m(s, orc_uniform(x[0]), orc_uniform(x[1]), x[3], &dir, &tex, mg);
         double fc[3];
-        brdf_cos(sh->n, wo, dir, sh->alb, sh->rgh, sh->met, kind, fc);
+        light_brdf(sh, wo, dir, kind, fc, mg);
         double phat = lum(s->env + 3 * tex) * lum(fc); /* p_hat = Y(L_env) Y(f_r) cos */
         double gamma = phat / q;                      /* gamma_s = p_hat / q_dir */
         double ua = orc_uniform(x[2]);
@@ -1017,7 +1097,7 @@ static void temporal_merge(const Ctx* c, int px, int py, int smp, const Shade* s
     if (ht < 0 || !(h[2] > 0.0) || !(h[3] > 0.0) || !(h[4] > 0.0)) return;
     v3 y = texel_dir(s, ht, (uint32_t)h[1]);
     double fc[3];
-    brdf_cos(sh->n, wo, y, sh->alb, sh->rgh, sh->met, c->p->brdf_kind, fc);
+    light_brdf(sh, wo, y, c->p->brdf_kind, fc, mg);
     double phat = lum(s->env + 3 * ht) * lum(fc);
     double w = phat * h[2] / h[3] * (mc / h[4]);
     uint32_t x[4];
@@ -1085,7 +1165,7 @@ static void spatial_reuse(const Ctx* c, int px, int py, int smp, const Shade* sh
         out.m += nb.m;
         if (nb.sel < 0 || !(nb.wsum > 0.0) || !(nb.phat > 0.0)) continue;
         double fc[3];
-        brdf_cos(sh->n, wo, nb.y, sh->alb, sh->rgh, sh->met, kind, fc);
+        light_brdf(sh, wo, nb.y, kind, fc, mg);
         double phat = lum(s->env + 3 * nb.ytex) * lum(fc);
         double w = phat * nb.wsum / nb.phat;
         out.wsum += w;
@@ -1175,6 +1255,12 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         rng(c, pix, (uint32_t)smp, (uint32_t)b, PURPOSE_CONTINUE, 0, x);
         v3 wc;
         double pind = sample_cont_m(s, sh.n, wo, sh.alb, sh.rgh, sh.met, x, &wc, mg);
+        if (sh.interp) {
+            /* with interpolated normals a continuation below the face ends the path */
+            double cg = vdot(wc, sh.ng);
+            note(mg, fabs(cg) / TAU_LEAK, MK_LEAK);
+            if (!(cg > 0.0)) break;
+        }
         double fc[3];
         brdf_cos(sh.n, wo, wc, sh.alb, sh.rgh, sh.met, kind, fc);
         if (!(pind > 0.0) || (fc[0] <= 0.0 && fc[1] <= 0.0 && fc[2] <= 0.0)) break;
@@ -1284,22 +1370,61 @@ static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], Sparse*
         gsu += sh.tp.dw_dx[k] * dot;
         gsv += sh.tp.dw_dy[k] * dot;
     }
-    /* vertices: (u, v) through the intersection, n through the face normal */
+    /* vertices: (u, v) through the intersection, n through the face normal -- or, with
+     * interpolated normals, through S = w0 VN_a + u VN_b + v VN_c to (u, v) and to the vertex
+     * normals VN_i = VA_i / |VA_i|, VA_i the sum of the incident faces' e1 x e2 */
     double gu = gsu * (uv[2] - uv[0]) + gsv * (uv[3] - uv[1]);
     double gv = gsu * (uv[4] - uv[0]) + gsv * (uv[5] - uv[1]);
-    v3 z = vscale(vadd(vscale(r0, gu), vscale(r1, gv)), 1.0 / det); /* A^-T (gu, gv, 0) */
+    v3 gn = V3(gm[5], gm[6], gm[7]);
+    const int32_t* fv = s->F + 3 * sh.tri;
     double bw[3] = {1.0 - sh.u - sh.v, sh.u, sh.v};
+    v3 gS = V3(0, 0, 0);
+    if (sh.interp) {
+        double Sl = vlen(sh.S);
+        v3 sn = vscale(sh.S, 1.0 / Sl);
+        v3 gsn = vscale(gn, sh.nsg);
+        gS = vscale(vsub(gsn, vscale(sn, vdot(sn, gsn))), 1.0 / Sl);
+        v3 na = vload(s->VN + 3 * fv[0]), nb = vload(s->VN + 3 * fv[1]), nc = vload(s->VN + 3 * fv[2]);
+        gu += vdot(gS, vsub(nb, na));
+        gv += vdot(gS, vsub(nc, na));
+    }
+    v3 z = vscale(vadd(vscale(r0, gu), vscale(r1, gv)), 1.0 / det); /* A^-T (gu, gv, 0) */
     v3 gvert[3];
     for (int k = 0; k < 3; ++k) gvert[k] = vscale(z, -bw[k]);
-    v3 gn = V3(gm[5], gm[6], gm[7]);
-    double Nl = vlen(sh.N);
-    v3 Nh = vscale(sh.N, 1.0 / Nl);
-    v3 gNh = vscale(gn, sh.sign);
-    v3 gN = vscale(vsub(gNh, vscale(Nh, vdot(Nh, gNh))), 1.0 / Nl);
-    v3 ge1 = vcross(sh.e2, gN), ge2 = vcross(gN, sh.e1);
-    gvert[0] = vsub(gvert[0], vadd(ge1, ge2));
-    gvert[1] = vadd(gvert[1], ge1);
-    gvert[2] = vadd(gvert[2], ge2);
+    if (sh.interp) {
+        for (int k = 0; k < 3; ++k) {
+            const int vi = fv[k];
+            v3 A = vload(s->VA + 3 * vi);
+            double Al = vlen(A);
+            if (!(Al > 0.0)) continue;
+            v3 vn = vscale(A, 1.0 / Al);
+            v3 gvn = vscale(gS, bw[k]);
+            v3 gA = vscale(vsub(gvn, vscale(vn, vdot(vn, gvn))), 1.0 / Al);
+            for (int q = s->vf_off[vi]; q < s->vf_off[vi + 1]; ++q) {
+                const int f = s->vf[q];
+                v3 a, b, cc;
+                tri_verts(s, f, &a, &b, &cc);
+                v3 fe1 = vsub(b, a), fe2 = vsub(cc, a);
+                v3 ge1 = vcross(fe2, gA), ge2 = vcross(gA, fe1);
+                v3 gf[3] = {vscale(vadd(ge1, ge2), -1.0), ge1, ge2};
+                for (int m = 0; m < 3; ++m) {
+                    int vj = s->F[3 * f + m];
+                    sp_add(sp, GB_VERT, 3 * (int64_t)vj + 0, gf[m].x);
+                    sp_add(sp, GB_VERT, 3 * (int64_t)vj + 1, gf[m].y);
+                    sp_add(sp, GB_VERT, 3 * (int64_t)vj + 2, gf[m].z);
+                }
+            }
+        }
+    } else {
+        double Nl = vlen(sh.N);
+        v3 Nh = vscale(sh.N, 1.0 / Nl);
+        v3 gNh = vscale(gn, sh.sign);
+        v3 gN = vscale(vsub(gNh, vscale(Nh, vdot(Nh, gNh))), 1.0 / Nl);
+        v3 ge1 = vcross(sh.e2, gN), ge2 = vcross(gN, sh.e1);
+        gvert[0] = vsub(gvert[0], vadd(ge1, ge2));
+        gvert[1] = vadd(gvert[1], ge1);
+        gvert[2] = vadd(gvert[2], ge2);
+    }
     for (int k = 0; k < 3; ++k) {
         int vi = s->F[3 * sh.tri + k];
         sp_add(sp, GB_VERT, 3 * (int64_t)vi + 0, gvert[k].x);

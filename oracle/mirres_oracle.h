@@ -79,6 +79,12 @@ typedef struct {
 #define ORC_NCOUNT 8
 
 orc_scene* orc_scene_new(const orc_scene_desc* d);
+/* shading normals of the scene: 0 the face normal (default), 1 the barycentric blend of
+ * area-weighted vertex normals, turned to the viewer's side of the face; light and
+ * continuation directions below the face are then dropped */
+void orc_scene_set_normals(orc_scene* s, int32_t mode);
+/* the area-weighted vertex normals [V][3] (0 for a vertex without area) */
+void orc_vertex_normals(const orc_scene* s, double* out);
 void orc_scene_free(orc_scene* s);
 double orc_scene_tmin(const orc_scene* s);
 

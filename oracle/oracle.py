@@ -75,6 +75,8 @@ def lib():
             L.orc_scene_free.argtypes = [vp]
             L.orc_scene_tmin.restype = dbl
             L.orc_scene_tmin.argtypes = [vp]
+            L.orc_scene_set_normals.argtypes = [vp, i32]
+            L.orc_vertex_normals.argtypes = [vp, vp]
             L.orc_render.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp, vp]
             L.orc_backward.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, C.POINTER(Grads), vp]
             L.orc_render_detached.argtypes = [vp, vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp]
@@ -121,7 +123,8 @@ def _f64(x):
 class OracleScene:
     """FP64 copy of a scene plus the oracle's own median-split BVH and env tables."""
 
-    def __init__(self, scene):
+    def __init__(self, scene, normals=0):
+        """normals: 0 face normals, 1 interpolated (area-weighted vertex normals)"""
         L = lib()
         self._keep = [np.ascontiguousarray(a) for a in (scene.verts, scene.tris, scene.tri_uv, scene.albedo,
                                                          scene.roughness, scene.metallic, scene.env)]
@@ -133,7 +136,14 @@ class OracleScene:
         if not self.h:
             raise ValueError("oracle rejected the scene description")
         self.scene = scene
+        self.normals = int(normals)
+        L.orc_scene_set_normals(self.h, self.normals)
         self.tmin = L.orc_scene_tmin(self.h)
+
+    def vertex_normals(self):
+        out = np.zeros((self.scene.verts.shape[0], 3))
+        lib().orc_vertex_normals(self.h, _p(out))
+        return out
 
     def __del__(self):
         if getattr(self, "h", None):
