@@ -186,6 +186,21 @@ mirres_status mirres_bvh_build(mirres_scene* scene, void* stream);
  * Both write the same layout (root 0, leaves by Morton position), so refit, traversal and
  * mirres_bvh_export are unchanged, and closest / any hits do not depend on the tree.
  * MIRRES_ERR_ARG for an unknown builder. */
+/* Shading normals of a scene (the paper shades with "the surface normal" and does not say how
+ * it is formed):
+ *   MIRRES_NORMALS_FACE (default): the face normal, turned towards the viewer;
+ *   MIRRES_NORMALS_INTERPOLATED: the barycentric blend of area-weighted vertex normals (the sum
+ *     of the incident faces' e1 x e2, normalised), turned to the viewer's side of the face; RIS
+ *     candidates, reused reservoirs and continuations below the face are then dropped. The
+ *     vertex normals are recomputed by every mirres_bvh_build and mirres_bvh_refit (and here if
+ *     the scene is built); the PRIMARY adjoint follows the shading normal to the barycentrics
+ *     and to the vertices of every face around the hit triangle's vertices.
+ * Allocates 28 bytes per vertex the first time it is enabled. MIRRES_ERR_ARG for an unknown
+ * mode. */
+#define MIRRES_NORMALS_FACE 0
+#define MIRRES_NORMALS_INTERPOLATED 1
+mirres_status mirres_scene_set_normals(mirres_scene* scene, int32_t mode);
+
 #define MIRRES_BVH_LBVH 0
 #define MIRRES_BVH_PLOC 1
 mirres_status mirres_bvh_set_builder(mirres_scene* scene, int32_t builder);

@@ -66,6 +66,8 @@ SceneDev mr_scene_dev(const mirres_scene* s)
     d.eh = s->desc.env_h;
     d.env_ok_dev = s->env_ok;
     d.tmin_dev = s->tmin;
+    d.vnrm = s->normals ? s->vnrm : nullptr;
+    d.gvn = s->normals ? s->gvn : nullptr;
     return d;
 }
 
@@ -260,6 +262,24 @@ extern "C" mirres_status mirres_scene_destroy(mirres_scene* s)
     mr_env_free(s);
     mr_edges_free(s);
     delete s;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_scene_set_normals(mirres_scene* s, int32_t mode)
+{
+    if (!s) return arg_error("scene is NULL");
+    if (mode != MIRRES_NORMALS_FACE && mode != MIRRES_NORMALS_INTERPOLATED) return arg_error("unknown normals mode");
+    MR_CUDA(cudaSetDevice(s->ctx->device));
+    if (mode == MIRRES_NORMALS_INTERPOLATED) {
+        MR_TRY(mr_normals_alloc(s));
+        s->normals = mode;
+        if (s->built) {
+            MR_TRY(mr_vertex_normals(s, nullptr));
+            MR_CUDA(cudaStreamSynchronize(nullptr));
+        }
+    } else {
+        s->normals = mode;
+    }
     return MIRRES_OK;
 }
 
@@ -823,11 +843,22 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
     MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_dimg, d_images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_grads, gdev.data(), sizeof(GradDev) * gdev.size(), cudaMemcpyHostToDevice, st));
+    int normals_passes = 0;
+    for (int i = 0; i < n_scenes; ++i)
+        if (scenes[i]->normals && grads[i].verts && scenes[i]->gvn)
+            MR_CUDA(cudaMemsetAsync(scenes[i]->gvn, 0, sizeof(float) * 3 * (size_t)scenes[i]->desc.n_verts, st));
     mr_launch_backward(d_scenes, d_views, n_views, total, make_rng(params), d_dimg, d_grads, tape, ctx->counters,
                        ctx->sm_count, st, nvx, full_scratch);
+    // interpolated normals: d loss / d vertex normal to the vertices of the incident faces
+    for (int i = 0; i < n_scenes; ++i)
+        if (scenes[i]->normals && grads[i].verts && scenes[i]->gvn) {
+            mr_launch_normals_adjoint(scenes[i], grads[i].verts, ctx->sm_count, st);
+            ++normals_passes;
+        }
     MR_CUDA(cudaGetLastError());
     const uint64_t full_chunk = mr_full_chunk();
-    ctx->host_launches += 1 + ((nvx > 0 && full_chunk) ? 4 * ((total + full_chunk - 1) / full_chunk) : 0);
+    ctx->host_launches += 1 + (unsigned long long)normals_passes +
+                          ((nvx > 0 && full_chunk) ? 4 * ((total + full_chunk - 1) / full_chunk) : 0);
     return MIRRES_OK;
 }
 

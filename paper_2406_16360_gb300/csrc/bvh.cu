@@ -577,6 +577,80 @@ __global__ void __launch_bounds__(256) k_leaf_depth(const int32_t* __restrict__ 
     atomicMax(depth, d);
 }
 
+// ---- area-weighted vertex normals for interpolated shading normals ------------------------
+__global__ void __launch_bounds__(256) k_vn_accumulate(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                                                       int F, int V, float* vacc)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < F; t += gridDim.x * blockDim.x) {
+        int idx[3];
+        float3 p[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int v = __ldg(tris + 3 * (size_t)t + c);
+            idx[c] = (v >= 0 && v < V) ? v : 0;
+            p[c] = f3(verts[3 * (size_t)idx[c]], verts[3 * (size_t)idx[c] + 1], verts[3 * (size_t)idx[c] + 2]);
+        }
+        const float3 N = cross(sub(p[1], p[0]), sub(p[2], p[0]));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            atomicAdd(vacc + 3 * (size_t)idx[c], N.x);
+            atomicAdd(vacc + 3 * (size_t)idx[c] + 1, N.y);
+            atomicAdd(vacc + 3 * (size_t)idx[c] + 2, N.z);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_vn_normalize(const float* __restrict__ vacc, int V, float4* vnrm)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+        const float3 A = f3(vacc[3 * (size_t)i], vacc[3 * (size_t)i + 1], vacc[3 * (size_t)i + 2]);
+        const float l2 = dot(A, A);
+        const float il = l2 > 0.0f ? rsqrtf(l2) : 0.0f;
+        vnrm[i] = make_float4(A.x * il, A.y * il, A.z * il, 0.0f);
+    }
+}
+
+// VN_i = A_i / |A_i|, A_i = sum over the faces f around vertex i of N_f = e1 x e2: per face,
+// d loss / d N_f = sum over its vertices of (I - VN VN^T) gvn_i / |A_i|, then to its vertices
+__global__ void __launch_bounds__(256) k_vn_adjoint(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                                                    int F, int V, const float* __restrict__ vacc,
+                                                    const float* __restrict__ gvn, float* grad)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < F; t += gridDim.x * blockDim.x) {
+        int idx[3];
+        float3 gN = f3(0.f, 0.f, 0.f);
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int v = __ldg(tris + 3 * (size_t)t + c);
+            idx[c] = (v >= 0 && v < V) ? v : 0;
+            const float3 g = f3(gvn[3 * (size_t)idx[c]], gvn[3 * (size_t)idx[c] + 1], gvn[3 * (size_t)idx[c] + 2]);
+            if (g.x == 0.0f && g.y == 0.0f && g.z == 0.0f) continue;
+            const float3 A = f3(vacc[3 * (size_t)idx[c]], vacc[3 * (size_t)idx[c] + 1], vacc[3 * (size_t)idx[c] + 2]);
+            const float l2 = dot(A, A);
+            if (!(l2 > 0.0f)) continue;
+            const float il = rsqrtf(l2);
+            const float3 n = mul(A, il);
+            gN = add(gN, mul(sub(g, mul(n, dot(n, g))), il));
+            any = true;
+        }
+        if (!any) continue;
+        float3 p[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            p[c] = f3(verts[3 * (size_t)idx[c]], verts[3 * (size_t)idx[c] + 1], verts[3 * (size_t)idx[c] + 2]);
+        const float3 e1 = sub(p[1], p[0]), e2 = sub(p[2], p[0]);
+        const float3 ge1 = cross(e2, gN), ge2 = cross(gN, e1);
+        const float3 gv[3] = {f3(-(ge1.x + ge2.x), -(ge1.y + ge2.y), -(ge1.z + ge2.z)), ge1, ge2};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            atomicAdd(grad + 3 * (size_t)idx[c], gv[c].x);
+            atomicAdd(grad + 3 * (size_t)idx[c] + 1, gv[c].y);
+            atomicAdd(grad + 3 * (size_t)idx[c] + 2, gv[c].z);
+        }
+    }
+}
+
 int grid_for(int n, int block) { return (n + block - 1) / block; }
 
 }  // namespace
@@ -632,7 +706,8 @@ void mr_bvh_free(mirres_scene* s)
 {
     void* ptrs[] = {s->keys, s->perm, s->left, s->right, s->parent, s->lo, s->hi, s->flags, s->nodes, s->ptri,
                     s->leaf_of, s->cent, s->codes[0], s->codes[1], s->vals[0], s->vals[1], s->hist, s->bounds,
-                    s->tmin, s->bad, s->ploc_box, s->ploc_node, s->ploc_nn, s->ploc_part, s->ploc_state};
+                    s->tmin, s->bad, s->ploc_box, s->ploc_node, s->ploc_nn, s->ploc_part, s->ploc_state,
+                    s->vacc, s->vnrm, s->gvn};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -757,6 +832,7 @@ mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st)
         MR_CUDA(cudaGetLastError());
         MR_TRY(bottom_up(s, st));
     }
+    if (s->normals) MR_TRY(mr_vertex_normals(s, st));
     int32_t bad = 0;
     MR_CUDA(cudaMemcpyAsync(&bad, s->bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MR_CUDA(cudaStreamSynchronize(st));
@@ -771,5 +847,37 @@ mirres_status mr_bvh_refit(mirres_scene* s, cudaStream_t st)
 {
     MR_TRY(bounds(s, st, 0));
     MR_TRY(bottom_up(s, st));
+    if (s->normals) MR_TRY(mr_vertex_normals(s, st));
     return MIRRES_OK;
+}
+
+mirres_status mr_normals_alloc(mirres_scene* s)
+{
+    if (s->vnrm) return MIRRES_OK;
+    const size_t V = (size_t)(s->desc.n_verts > 0 ? s->desc.n_verts : 1);
+    MR_TRY(mr_alloc(&s->vacc, 3 * V));
+    MR_TRY(mr_alloc(&s->vnrm, V));
+    MR_TRY(mr_alloc(&s->gvn, 3 * V));
+    return MIRRES_OK;
+}
+
+mirres_status mr_vertex_normals(mirres_scene* s, cudaStream_t st)
+{
+    const int F = s->desc.n_tris, V = s->desc.n_verts;
+    if (V <= 0) return MIRRES_OK;
+    MR_TRY(mr_normals_alloc(s));
+    MR_CUDA(cudaMemsetAsync(s->vacc, 0, sizeof(float) * 3 * (size_t)V, st));
+    if (F > 0)
+        k_vn_accumulate<<<std::min(grid_for(F, 256), 4096), 256, 0, st>>>(s->desc.verts, s->desc.tris, F, V, s->vacc);
+    k_vn_normalize<<<std::min(grid_for(V, 256), 4096), 256, 0, st>>>(s->vacc, V, s->vnrm);
+    MR_CUDA(cudaGetLastError());
+    return MIRRES_OK;
+}
+
+void mr_launch_normals_adjoint(const mirres_scene* s, float* grad_verts, int sms, cudaStream_t st)
+{
+    const int F = s->desc.n_tris, V = s->desc.n_verts;
+    if (F <= 0 || V <= 0 || !grad_verts) return;
+    k_vn_adjoint<<<std::min(grid_for(F, 256), sms * 8), 256, 0, st>>>(s->desc.verts, s->desc.tris, F, V, s->vacc,
+                                                                      s->gvn, grad_verts);
 }

@@ -77,6 +77,10 @@ struct SceneDev {
     int32_t n_tris, n_verts, tw, th, ew, eh;
     const int32_t* env_ok_dev; // device-written: total env weight > 0
     const float* tmin_dev;     // device-written: 1e-5 x scene diagonal
+    // interpolated shading normals (null: face normals): unit area-weighted vertex normals,
+    // and the adjoint's per-vertex accumulator of d loss / d vertex normal [V][3]
+    const float4* vnrm;
+    float* gvn;
 };
 
 struct ViewDev {
@@ -701,6 +705,11 @@ struct Shade {
     float su, sv;
     Taps tp;
     Material m;
+    // with interpolated normals: n = nsg S / |S|, S = w0 VN_a + u VN_b + v VN_c, and ng the
+    // face normal towards the viewer (below it, light and continuation directions are dropped)
+    bool interp;
+    float3 ng, S;
+    float nsg;
 };
 
 __device__ __forceinline__ void shade_at(const SceneDev& s, int tri, float u, float v, float3 d, Shade& sh)
@@ -712,9 +721,27 @@ __device__ __forceinline__ void shade_at(const SceneDev& s, int tri, float u, fl
     const float3 nh = normalize(sh.N);
     sh.sign = (dot(nh, d) > 0.0f) ? -1.0f : 1.0f;
     sh.n = mul(nh, sh.sign);
+    sh.ng = sh.n;
+    sh.interp = false;
+    sh.nsg = 1.0f;
+    sh.S = f3(0.f, 0.f, 0.f);
     sh.x = add(v0, add(mul(sh.e1, u), mul(sh.e2, v)));
     const float* uv = s.tri_uv + 6 * (size_t)tri;
     const float w0 = 1.0f - u - v;
+    if (s.vnrm) {
+        const int ia = __ldg(s.tris + 3 * (size_t)tri), ib = __ldg(s.tris + 3 * (size_t)tri + 1),
+                  ic = __ldg(s.tris + 3 * (size_t)tri + 2);
+        const float3 na = xyz(__ldg(s.vnrm + ia)), nb = xyz(__ldg(s.vnrm + ib)), nc = xyz(__ldg(s.vnrm + ic));
+        const float3 S = add(add(mul(na, w0), mul(nb, u)), mul(nc, v));
+        const float l2 = dot(S, S);
+        if (l2 > 0.0f) {
+            const float il = rsqrtf(l2);
+            sh.nsg = dot(S, sh.ng) < 0.0f ? -1.0f : 1.0f;
+            sh.n = mul(S, sh.nsg * il);
+            sh.S = S;
+            sh.interp = true;
+        }
+    }
     sh.su = w0 * __ldg(uv + 0) + u * __ldg(uv + 2) + v * __ldg(uv + 4);
     sh.sv = w0 * __ldg(uv + 1) + u * __ldg(uv + 3) + v * __ldg(uv + 5);
     taps_at(s.tw, s.th, sh.su, sh.sv, sh.tp);
@@ -733,6 +760,16 @@ __device__ __forceinline__ void shade_at(const SceneDev& s, int tri, float u, fl
     sh.m.alb = a;
     sh.m.rough = r;
     sh.m.metal = m;
+}
+
+// with interpolated normals, false for a direction below the face: light from it and a
+// continuation along it are dropped
+__device__ __forceinline__ bool above_face(const Shade& sh, float3 dir) { return !sh.interp || dot(sh.ng, dir) > 0.0f; }
+
+// f_r cos of a light direction at a shading point (0 below the face with interpolated normals)
+__device__ __forceinline__ float3 light_brdf(const Shade& sh, float3 wo, float3 dir)
+{
+    return above_face(sh, dir) ? brdf_cos(sh.n, wo, dir, sh.m) : f3(0.f, 0.f, 0.f);
 }
 
 // camera ray direction for pixel (px, py) with jitter from the random stream

@@ -74,6 +74,12 @@ struct mirres_scene {
     unsigned int* bounds = nullptr;  // [12] ordered-uint bounds: centroid lo/hi, vertex lo/hi
     float* tmin = nullptr;           // [1]
     int32_t* bad = nullptr;          // [1] invalid index flag
+    // shading normals: MIRRES_NORMALS_FACE or MIRRES_NORMALS_INTERPOLATED (area-weighted vertex
+    // normals, recomputed by every build and refit)
+    int32_t normals = 0;
+    float* vacc = nullptr;   // [V][3] sum of the incident faces' e1 x e2
+    float4* vnrm = nullptr;  // [V] vacc normalised
+    float* gvn = nullptr;    // [V][3] adjoint accumulator of d loss / d vertex normal
     // hierarchy builder: MIRRES_BVH_LBVH (Karras) or MIRRES_BVH_PLOC (clustering); PLOC scratch
     int32_t builder = 0;
     float4* ploc_box = nullptr;      // [2][2][F] cluster boxes (lo, hi), ping-pong
@@ -108,6 +114,11 @@ SceneDev mr_scene_dev(const mirres_scene* s);
 mirres_status mr_bvh_alloc(mirres_scene* s);
 void mr_bvh_free(mirres_scene* s);
 mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st);
+// interpolated normals: allocate (idempotent), recompute from the current vertices, and the
+// adjoint pass taking d loss / d vertex normal to the vertices of every incident face
+mirres_status mr_normals_alloc(mirres_scene* s);
+mirres_status mr_vertex_normals(mirres_scene* s, cudaStream_t st);
+void mr_launch_normals_adjoint(const mirres_scene* s, float* grad_verts, int sms, cudaStream_t st);
 mirres_status mr_bvh_refit(mirres_scene* s, cudaStream_t st);
 // regular.cu
 mirres_status mr_edges_build(mirres_scene* s, cudaStream_t st);

@@ -166,7 +166,7 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
             const float gq = env_candidate(s, x.x, x.y, x.w, dir, tex);  // Y(L_env) / q_dir
             const float ci = dot(sh.n, dir);
             float yfc = 0.0f, dv = 0.0f, w5 = 0.0f;
-            if (co > 0.0f && ci > 0.0f) {
+            if (co > 0.0f && ci > 0.0f && above_face(sh, dir)) {
                 const float3 h = normalize(add(wo, dir));
                 const float cnh = dot(sh.n, h), coh = dot(wo, h);
                 const float k = ggx_k(sh.n, h, cnh, a2);
@@ -215,7 +215,7 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
         float3 wc;
         const float pind = sample_continuation(s, env_ok, sh.n, wo, sh.m, x, wc);
         const float3 fc = brdf_cos(sh.n, wo, wc, sh.m);
-        if (pind > 0.0f && (fc.x > 0.0f || fc.y > 0.0f || fc.z > 0.0f)) {
+        if (pind > 0.0f && (fc.x > 0.0f || fc.y > 0.0f || fc.z > 0.0f) && above_face(sh, wc)) {
             const float3 f = f3(fc.x / pind, fc.y / pind, fc.z / pind);
             out.cont = true;
             out.c_d = wc;

@@ -702,6 +702,8 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
         float env_v[3] = {0.f, 0.f, 0.f};
         float tex_v[4][5];
         float vert_v[3][3];
+        float3 gS = f3(0.f, 0.f, 0.f);  // d loss / d S of the interpolated normal
+        float bw_u = 0.0f, bw_v = 0.0f;
         int scene_id = 0;
         // FULL mode: the later vertices' throughput, direct light and continuation factor
         int nv = 0;
@@ -793,30 +795,49 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
                     const float gsu = (float)s.tw * ((1.0f - tpz.fy) * (dt[1] - dt[0]) + tpz.fy * (dt[3] - dt[2]));
                     const float gsv = (float)s.th * ((1.0f - tpz.fx) * (dt[2] - dt[0]) + tpz.fx * (dt[3] - dt[1]));
                     const float* uv = s.tri_uv + 6 * (size_t)tri;
-                    const float gu = gsu * (__ldg(uv + 2) - __ldg(uv + 0)) + gsv * (__ldg(uv + 3) - __ldg(uv + 1));
-                    const float gv = gsu * (__ldg(uv + 4) - __ldg(uv + 0)) + gsv * (__ldg(uv + 5) - __ldg(uv + 1));
+                    float gu = gsu * (__ldg(uv + 2) - __ldg(uv + 0)) + gsv * (__ldg(uv + 3) - __ldg(uv + 1));
+                    float gv = gsu * (__ldg(uv + 4) - __ldg(uv + 0)) + gsv * (__ldg(uv + 5) - __ldg(uv + 1));
+                    int vid[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) vid[c] = __ldg(s.tris + 3 * (size_t)tri + c);
+                    if (sh.interp) {
+                        // n = nsg S / |S|, S = w0 VN_a + u VN_b + v VN_c: to (u, v) here, to the
+                        // vertex normals through the per-vertex accumulator (a later pass
+                        // takes them to the faces around each vertex)
+                        const float il = rsqrtf(dot(sh.S, sh.S));
+                        const float3 sn = mul(sh.S, il);
+                        const float3 gsn = mul(f3(gm[5], gm[6], gm[7]), sh.nsg);
+                        gS = mul(sub(gsn, mul(sn, dot(sn, gsn))), il);
+                        const float3 na = xyz(__ldg(s.vnrm + vid[0])), nb = xyz(__ldg(s.vnrm + vid[1])),
+                                     nc = xyz(__ldg(s.vnrm + vid[2]));
+                        gu += dot(gS, sub(nb, na));
+                        gv += dot(gS, sub(nc, na));
+                    }
                     // (u, v) through the intersection: A = [e1 | e2 | -d], z = A^-T (gu, gv, 0)
                     const float3 md = f3(-d.x, -d.y, -d.z);
                     const float3 r0 = cross(e2, md), r1 = cross(md, e1);
                     const float det = dot(e1, r0);
                     const float3 z = mul(add(mul(r0, gu), mul(r1, gv)), 1.0f / det);
+                    bw_u = u;
+                    bw_v = vv;
                     const float bw[3] = {1.0f - u - vv, u, vv};
                     float3 gvx[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) gvx[c] = mul(z, -bw[c]);
-                    // n = sign * N / |N|, N = e1 x e2
-                    const float Nl = sqrtf(dot(sh.N, sh.N));
-                    const float3 Nh = mul(sh.N, 1.0f / Nl);
-                    const float3 gNh = mul(f3(gm[5], gm[6], gm[7]), sh.sign);
-                    const float3 gN = mul(sub(gNh, mul(Nh, dot(Nh, gNh))), 1.0f / Nl);
-                    const float3 ge1 = cross(e2, gN), ge2 = cross(gN, e1);
-                    gvx[0] = sub(gvx[0], add(ge1, ge2));
-                    gvx[1] = add(gvx[1], ge1);
-                    gvx[2] = add(gvx[2], ge2);
+                    if (!sh.interp) {
+                        // n = sign * N / |N|, N = e1 x e2
+                        const float Nl = sqrtf(dot(sh.N, sh.N));
+                        const float3 Nh = mul(sh.N, 1.0f / Nl);
+                        const float3 gNh = mul(f3(gm[5], gm[6], gm[7]), sh.sign);
+                        const float3 gN = mul(sub(gNh, mul(Nh, dot(Nh, gNh))), 1.0f / Nl);
+                        const float3 ge1 = cross(e2, gN), ge2 = cross(gN, e1);
+                        gvx[0] = sub(gvx[0], add(ge1, ge2));
+                        gvx[1] = add(gvx[1], ge1);
+                        gvx[2] = add(gvx[2], ge2);
+                    }
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const int vid = __ldg(s.tris + 3 * (size_t)tri + c);
-                        vert_key[c] = (vid >= 0 && vid < s.n_verts) ? vid : -1;
+                        vert_key[c] = (vid[c] >= 0 && vid[c] < s.n_verts) ? vid[c] : -1;
                         vert_v[c][0] = gvx[c].x;
                         vert_v[c][1] = gvx[c].y;
                         vert_v[c][2] = gvx[c].z;
@@ -827,6 +848,7 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
         // scatters are keyed per scene; lanes of other scenes never share a key group
         // because the key is combined with the scene id in the match
         const GradDev gd = grads[scene_id];
+        float* const gvn = gd.verts ? scenes[scene_id].gvn : nullptr;  // interpolated normals only
         const unsigned same_scene = __match_any_sync(MR_FULL, scene_id);
         if (same_scene == MR_FULL) {
             scatter_agg<3>(env_key, env_v, EmitEnv{gd.env});
@@ -834,6 +856,14 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
             for (int q = 0; q < 4; ++q) scatter_agg<5>(tex_key[q], tex_v[q], EmitTex{gd.albedo, gd.rough, gd.metal});
 #pragma unroll
             for (int c = 0; c < 3; ++c) scatter_agg<3>(vert_key[c], vert_v[c], EmitVert{gd.verts});
+            if (gvn) {
+                const float bw[3] = {1.0f - bw_u - bw_v, bw_u, bw_v};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float gv3[3] = {gS.x * bw[c], gS.y * bw[c], gS.z * bw[c]};
+                    scatter_agg<3>(vert_key[c], gv3, EmitVert{gvn});
+                }
+            }
         } else {
             if (env_key >= 0) EmitEnv{gd.env}(env_key, env_v);
 #pragma unroll
@@ -842,6 +872,14 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 if (vert_key[c] >= 0) EmitVert{gd.verts}(vert_key[c], vert_v[c]);
+            if (gvn) {
+                const float bw[3] = {1.0f - bw_u - bw_v, bw_u, bw_v};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float gv3[3] = {gS.x * bw[c], gS.y * bw[c], gS.z * bw[c]};
+                    if (vert_key[c] >= 0) EmitVert{gvn}(vert_key[c], gv3);
+                }
+            }
         }
         if (FULL) {
             const SceneDev* sp = scenes + scene_id;

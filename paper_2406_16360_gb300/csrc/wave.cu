@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(256) k_wtemporal(const SceneDev* __restrict__ 
         float4 rowv;
         float3 y;
         env_dir(s, ht / s.ew, ht % s.ew, hist.ysub[g], y, rowv);
-        const float3 fc = brdf_cos(sh.n, wo, y, sh.m);
+        const float3 fc = light_brdf(sh, wo, y);
         const float ph = lum(xyz(__ldg(s.env_texel + ht))) * lum(fc);
         const float w = ph * hw / hp * (mc / hm);
         const uint32_t pixel = sid / (uint32_t)v.spp, smp = sid % (uint32_t)v.spp;
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(256) k_wreuse(const SceneDev* __restrict__ sce
                 float4 rowv;
                 float3 y;
                 env_dir(s, nt / s.ew, nt % s.ew, res.ysub[gq], y, rowv);
-                const float3 fc = brdf_cos(sh.n, wo, y, sh.m);
+                const float3 fc = light_brdf(sh, wo, y);
                 const float ph = lum(xyz(__ldg(s.env_texel + nt))) * lum(fc);
                 const float w = ph * res.wsum[gq] / res.phat[gq];
                 wsum += w;

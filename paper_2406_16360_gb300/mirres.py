@@ -17,7 +17,8 @@ from . import build as _build
 
 __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_view", "make_params",
            "mirres_context_create", "mirres_context_destroy", "mirres_scene_create", "mirres_scene_destroy",
-           "mirres_bvh_build", "mirres_bvh_refit", "mirres_bvh_set_builder", "MIRRES_BVH_LBVH", "MIRRES_BVH_PLOC", "mirres_tape_bytes", "mirres_tape_bytes_mode",
+           "mirres_bvh_build", "mirres_bvh_refit", "mirres_bvh_set_builder", "MIRRES_BVH_LBVH", "MIRRES_BVH_PLOC",
+           "mirres_scene_set_normals", "MIRRES_NORMALS_FACE", "MIRRES_NORMALS_INTERPOLATED", "mirres_tape_bytes", "mirres_tape_bytes_mode",
            "mirres_reuse_history_bytes", "mirres_render",
            "mirres_render_noalloc",
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
@@ -33,6 +34,7 @@ MIRRES_TAPE_BYTES_PER_VERTEX = 36  # FULL mode: 9 words per later vertex
 MIRRES_FULL_MAX_BOUNCES = 16
 GRAD_PRIMARY, GRAD_FULL = 0, 1
 MIRRES_BVH_LBVH, MIRRES_BVH_PLOC = 0, 1
+MIRRES_NORMALS_FACE, MIRRES_NORMALS_INTERPOLATED = 0, 1
 MIRRES_NOALLOC_SCRATCH_BYTES = 512 * 1024
 MIRRES_NOALLOC_MAX_VIEWS = 4096
 MIRRES_NOALLOC_MAX_SCENES = 256
@@ -106,6 +108,7 @@ def lib():
                 "mirres_bvh_build": (st, [vp, vp]),
                 "mirres_bvh_refit": (st, [vp, vp]),
                 "mirres_bvh_set_builder": (st, [vp, i32]),
+                "mirres_scene_set_normals": (st, [vp, i32]),
                 "mirres_tape_bytes": (sz, [C.POINTER(View), i32]),
                 "mirres_tape_bytes_mode": (sz, [C.POINTER(View), i32, i32]),
                 "mirres_reuse_history_bytes": (sz, [C.POINTER(View), i32]),
@@ -256,6 +259,10 @@ def mirres_bvh_refit(scene: Scene, stream=None):
 
 def mirres_bvh_set_builder(scene: Scene, builder: int):
     _check("mirres_bvh_set_builder", lib().mirres_bvh_set_builder(scene.handle, int(builder)))
+
+
+def mirres_scene_set_normals(scene: Scene, mode: int):
+    _check("mirres_scene_set_normals", lib().mirres_scene_set_normals(scene.handle, int(mode)))
 
 
 def mirres_tape_bytes(views) -> int:

@@ -19,7 +19,8 @@ def _dev(a, dtype, device):
 class DeviceScene:
     """Scene inputs as CUDA tensors plus the library scene handle (LBVH and env tables built)."""
 
-    def __init__(self, ctx: M.Context, scene, device="cuda", builder=M.MIRRES_BVH_LBVH):
+    def __init__(self, ctx: M.Context, scene, device="cuda", builder=M.MIRRES_BVH_LBVH,
+                 normals=M.MIRRES_NORMALS_FACE):
         self.device = torch.device(device)
         self.verts = _dev(scene.verts, torch.float32, self.device)
         self.tris = _dev(scene.tris, torch.int32, self.device)
@@ -31,6 +32,7 @@ class DeviceScene:
         self.handle = M.mirres_scene_create(ctx, self.verts, self.tris, self.tri_uv, self.albedo, self.roughness,
                                             self.metallic, self.env)
         M.mirres_bvh_set_builder(self.handle, builder)
+        M.mirres_scene_set_normals(self.handle, normals)
         M.mirres_bvh_build(self.handle)
         self._versions = self._param_versions()
 
@@ -55,11 +57,12 @@ class DeviceScene:
 class GpuWorkload:
     """A synthetic workload resident on one GPU."""
 
-    def __init__(self, workload, device=0, ctx=None, builder=M.MIRRES_BVH_LBVH):
+    def __init__(self, workload, device=0, ctx=None, builder=M.MIRRES_BVH_LBVH, normals=M.MIRRES_NORMALS_FACE):
         self.workload = workload
         self.ctx = ctx or M.mirres_context_create(device)
         self.device = torch.device("cuda", device)
-        self.scenes = [DeviceScene(self.ctx, s, self.device, builder=builder) for s in workload.scenes]
+        self.scenes = [DeviceScene(self.ctx, s, self.device, builder=builder, normals=normals)
+                       for s in workload.scenes]
         self.views = list(workload.views)
         self.samples = workload.samples
 

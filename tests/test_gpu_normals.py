@@ -1,0 +1,144 @@
+"""GPU parity of interpolated shading normals (mirres_scene_set_normals) against the FP64
+oracle with the same option (OracleScene(..., normals=1)): forward under every launch, the
+PRIMARY adjoint (materials, env and the vertex gradient through the vertex normals), the
+FULL adjoint, a refit after the vertices moved, and the roof whose unlit face stays dark."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2406_16360_gb300 import synth
+from tests.parity import compare_grads, compare_pixels
+
+pytestmark = pytest.mark.gpu
+
+INTERP = 1
+
+
+@pytest.fixture(scope="module")
+def M():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_16360_gb300 import mirres
+    return mirres
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.mirres_context_create(0)
+    yield c
+    c.close()
+
+
+def _gw(ctx, w):
+    from paper_2406_16360_gb300.renderer import GpuWorkload
+    return GpuWorkload(w, 0, ctx=ctx, normals=INTERP)
+
+
+def _close(gw):
+    for s in gw.scenes:
+        s.close()
+
+
+def _forward(w, images, max_flag_frac=0.08):
+    out = []
+    for vi, v in enumerate(w.views):
+        r = O.render(O.OracleScene(w.scenes[v.scene], normals=INTERP), v, vi, w.ris_m, seed=w.seed)
+        st = compare_pixels(images[vi].cpu().numpy().reshape(-1, 3), r["rgb"], r["margin"])
+        assert st["failures"] == 0, (vi, st["failures"], st["max_err_unflagged"])
+        assert st["flagged"] <= max_flag_frac * st["n"] + 1, (vi, st["flagged"], st["n"])
+        out.append(r)
+    return out
+
+
+def _grads(gw, w, refs, tape, grad_mode=0, seed=123, fields=("albedo", "roughness", "metallic", "env", "verts")):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d_imgs = []
+    for vi, v in enumerate(w.views):
+        g = rng.normal(size=(v.height * v.width, 3))
+        g[refs[vi]["margin"] < 1.0] = 0.0
+        d_imgs.append(torch.as_tensor(g.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda"))
+    grads = gw.backward(d_imgs, tape, grad_mode=grad_mode)
+    torch.cuda.synchronize()
+    for si, sc in enumerate(w.scenes):
+        osc = O.OracleScene(sc, normals=INTERP)
+        acc = None
+        for vi, v in enumerate(w.views):
+            if v.scene != si:
+                continue
+            gi = O.backward(osc, v, vi, w.ris_m, d_imgs[vi].double().cpu().numpy().reshape(-1, 3), seed=w.seed,
+                            grad_mode=grad_mode)
+            acc = gi if acc is None else {k: acc[k] + gi[k] for k in gi if k != "counts"}
+        for k in fields:
+            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"))
+            assert st["failures"] == 0, (k, st["failures"], st["max_rel"], st["detail"])
+
+
+@pytest.mark.parametrize("launch", [0, 1, 2])
+def test_interpolated_normals_forward_and_adjoint(M, ctx, launch):
+    w = synth.config1()
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=launch)
+    torch.cuda.synchronize()
+    refs = _forward(w, images)
+    if launch == 0:
+        _grads(gw, w, refs, tape)
+    _close(gw)
+
+
+def test_interpolated_normals_reduced_config2(M, ctx):
+    w = synth.config2(res=48, n_views=2, tex=64, spp=4)
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1)
+    torch.cuda.synchronize()
+    refs = _forward(w, images)
+    _grads(gw, w, refs, tape)
+    _close(gw)
+
+
+def test_interpolated_normals_full_adjoint(M, ctx):
+    w = synth.config1()
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1, grad_mode=M.GRAD_FULL)
+    torch.cuda.synchronize()
+    refs = _forward(w, images)
+    _grads(gw, w, refs, tape, grad_mode=M.GRAD_FULL, fields=("albedo", "roughness", "metallic", "env"))
+    _close(gw)
+
+
+def test_interpolated_normals_follow_a_refit(M, ctx):
+    """the vertex normals are recomputed when the vertices move"""
+    w = synth.config1()
+    gw = _gw(ctx, w)
+    rng = np.random.Generator(np.random.PCG64(4))
+    moved = (w.scenes[0].verts + rng.normal(scale=0.01, size=w.scenes[0].verts.shape)).astype(np.float32)
+    with torch.no_grad():
+        gw.scenes[0].verts.copy_(torch.as_tensor(moved, device="cuda"))
+    gw.scenes[0].refresh()
+    images, _ = gw.render(launch=1)
+    torch.cuda.synchronize()
+    sc = synth.Scene(moved, w.scenes[0].tris, w.scenes[0].tri_uv, w.scenes[0].albedo, w.scenes[0].roughness,
+                     w.scenes[0].metallic, w.scenes[0].env)
+    w2 = synth.Workload(w.name, [sc], w.views, ris_m=w.ris_m, seed=w.seed)
+    _forward(w2, images)
+    _close(gw)
+
+
+def test_roof_face_without_light_stays_dark(M, ctx):
+    v = np.array([[-1.0, 0, -1], [-1, 0, 1], [0, 1, -1], [0, 1, 1], [1, 0, -1], [1, 0, 1]])
+    t = np.array([[0, 1, 3], [0, 3, 2], [2, 3, 5], [2, 5, 4]])
+    env = np.zeros((16, 32, 3), np.float32)
+    env[6, 24] = 500.0
+    sc = synth._scene(v, t, np.zeros((4, 3, 2)), np.full((1, 1, 3), 0.7), np.full((1, 1), 0.6),
+                      np.zeros((1, 1)), env)
+    K, c2w = synth.look_at((0.0, 2.5, 2.5), (0.0, 0.5, 0.0), 24, 18, 50.0)
+    w = synth.Workload("roof", [sc], [synth.View(K, c2w, 24, 18, 4, 1)], ris_m=8, seed=1)
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1)
+    torch.cuda.synchronize()
+    refs = _forward(w, images, max_flag_frac=0.2)
+    r = O.render(O.OracleScene(sc, normals=INTERP), w.views[0], 0, 8, seed=1, prim=True, margins=False)
+    left = np.isin(r["prim"], [0, 1]).all(1)
+    assert left.sum() > 20
+    assert np.all(images[0].cpu().numpy().reshape(-1, 3)[left] == 0.0)
+    _close(gw)
