@@ -13,6 +13,11 @@ from tests.parity import compare_grads, compare_pixels
 pytestmark = pytest.mark.gpu
 
 INTERP = 1
+# The shading normal is a blend of three vertex normals, each a sum of FP32 face normals added
+# by atomics in any order and renormalised: a few 1e-7 of direction error, which the GGX lobe
+# of the glossiest texels (alpha = r^2 down to 2.5e-3) amplifies by ~1/alpha in D. Measured
+# worst case 1.4e-4 of the pixel on the reduced config 2; the face-normal tests keep 1e-4.
+FWD_RTOL = 3e-4
 
 
 @pytest.fixture(scope="module")
@@ -44,7 +49,7 @@ def _forward(w, images, max_flag_frac=0.08):
     out = []
     for vi, v in enumerate(w.views):
         r = O.render(O.OracleScene(w.scenes[v.scene], normals=INTERP), v, vi, w.ris_m, seed=w.seed)
-        st = compare_pixels(images[vi].cpu().numpy().reshape(-1, 3), r["rgb"], r["margin"])
+        st = compare_pixels(images[vi].cpu().numpy().reshape(-1, 3), r["rgb"], r["margin"], rtol=FWD_RTOL)
         assert st["failures"] == 0, (vi, st["failures"], st["max_err_unflagged"])
         assert st["flagged"] <= max_flag_frac * st["n"] + 1, (vi, st["flagged"], st["n"])
         out.append(r)
