@@ -92,7 +92,14 @@ def test_interpolated_normals_forward_and_adjoint(M, ctx, launch):
 
 
 def test_interpolated_normals_reduced_config2(M, ctx):
+    """With interpolated normals the shading normal varies across a triangle, so the FP32 hit
+    point's barycentric error (~1e-6) moves it by ~1e-6 |VN_b - VN_a|, and the GGX lobe
+    amplifies that by up to 1/alpha^2 (1.6e5 at roughness 0.05): the vertex gradients of the
+    glossiest pixels are then not determined to 1e-3 in FP32 at all. Roughness is held at
+    0.3 or more here (amplification <= 120) so that the comparison tests the chain itself."""
     w = synth.config2(res=48, n_views=2, tex=64, spp=4)
+    for sc in w.scenes:
+        sc.roughness = np.maximum(sc.roughness, 0.3).astype(np.float32)
     gw = _gw(ctx, w)
     images, tape = gw.render(launch=1)
     torch.cuda.synchronize()
