@@ -2,6 +2,8 @@
 oracle with the same option (OracleScene(..., normals=1)): forward under every launch, the
 PRIMARY adjoint (materials, env and the vertex gradient through the vertex normals), the
 FULL adjoint, a refit after the vertices moved, and the roof whose unlit face stays dark."""
+import copy
+
 import numpy as np
 import pytest
 import torch
@@ -65,7 +67,7 @@ def _grads(gw, w, refs, tape, grad_mode=0, seed=123, fields=("albedo", "roughnes
         d_imgs.append(torch.as_tensor(g.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda"))
     grads = gw.backward(d_imgs, tape, grad_mode=grad_mode)
     torch.cuda.synchronize()
-    for si, sc in enumerate(w.scenes):
+    def oracle(sc):
         osc = O.OracleScene(sc, normals=INTERP)
         acc = None
         for vi, v in enumerate(w.views):
@@ -74,8 +76,26 @@ def _grads(gw, w, refs, tape, grad_mode=0, seed=123, fields=("albedo", "roughnes
             gi = O.backward(osc, v, vi, w.ris_m, d_imgs[vi].double().cpu().numpy().reshape(-1, 3), seed=w.seed,
                             grad_mode=grad_mode)
             acc = gi if acc is None else {k: acc[k] + gi[k] for k in gi if k != "counts"}
+        return acc
+
+    for si, sc in enumerate(w.scenes):
+        acc = oracle(sc)
         for k in fields:
-            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"))
+            sens = acc.get(k + "_sens")
+            if k == "verts":
+                # Through the interpolated normal a vertex gradient depends on differences of
+                # nearby vertex normals and on 1 / |vertex normal sum|: moving every vertex by
+                # one FP32 ulp moves some of the oracle's own FP64 values by several 1e-3. The
+                # comparison allows that spread (the oracle's, at two random ulp moves).
+                rng = np.random.Generator(np.random.PCG64(99))
+                spread = np.zeros_like(acc[k])
+                for _ in range(2):
+                    moved = copy.deepcopy(sc)
+                    away = np.where(rng.uniform(size=sc.verts.shape) < 0.5, -np.inf, np.inf).astype(np.float32)
+                    moved.verts = np.nextafter(sc.verts.astype(np.float32), away)
+                    spread = np.maximum(spread, np.abs(oracle(moved)[k] - acc[k]))
+                sens = 2.0 * spread
+            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], sens)
             assert st["failures"] == 0, (k, st["failures"], st["max_rel"], st["detail"])
 
 
@@ -92,14 +112,7 @@ def test_interpolated_normals_forward_and_adjoint(M, ctx, launch):
 
 
 def test_interpolated_normals_reduced_config2(M, ctx):
-    """With interpolated normals the shading normal varies across a triangle, so the FP32 hit
-    point's barycentric error (~1e-6) moves it by ~1e-6 |VN_b - VN_a|, and the GGX lobe
-    amplifies that by up to 1/alpha^2 (1.6e5 at roughness 0.05): the vertex gradients of the
-    glossiest pixels are then not determined to 1e-3 in FP32 at all. Roughness is held at
-    0.3 or more here (amplification <= 120) so that the comparison tests the chain itself."""
     w = synth.config2(res=48, n_views=2, tex=64, spp=4)
-    for sc in w.scenes:
-        sc.roughness = np.maximum(sc.roughness, 0.3).astype(np.float32)
     gw = _gw(ctx, w)
     images, tape = gw.render(launch=1)
     torch.cuda.synchronize()
