@@ -847,8 +847,10 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
     for (int i = 0; i < n_scenes; ++i)
         if (scenes[i]->normals && grads[i].verts && scenes[i]->gvn)
             MR_CUDA(cudaMemsetAsync(scenes[i]->gvn, 0, sizeof(float) * 3 * (size_t)scenes[i]->desc.n_verts, st));
+    bool interp = false;
+    for (int i = 0; i < n_scenes; ++i) interp = interp || scenes[i]->normals != 0;
     mr_launch_backward(d_scenes, d_views, n_views, total, make_rng(params), d_dimg, d_grads, tape, ctx->counters,
-                       ctx->sm_count, st, nvx, full_scratch);
+                       ctx->sm_count, st, nvx, full_scratch, interp);
     // interpolated normals: d loss / d vertex normal to the vertices of the incident faces
     for (int i = 0; i < n_scenes; ++i)
         if (scenes[i]->normals && grads[i].verts && scenes[i]->gvn) {

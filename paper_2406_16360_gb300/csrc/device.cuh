@@ -712,6 +712,9 @@ struct Shade {
     float nsg;
 };
 
+// INTERP = false compiles the interpolated-normal path out (kernels launched for scenes that
+// all use face normals); INTERP = true follows the scene (s.vnrm)
+template <bool INTERP = true>
 __device__ __forceinline__ void shade_at(const SceneDev& s, int tri, float u, float v, float3 d, Shade& sh)
 {
     float3 v0;
@@ -728,7 +731,7 @@ __device__ __forceinline__ void shade_at(const SceneDev& s, int tri, float u, fl
     sh.x = add(v0, add(mul(sh.e1, u), mul(sh.e2, v)));
     const float* uv = s.tri_uv + 6 * (size_t)tri;
     const float w0 = 1.0f - u - v;
-    if (s.vnrm) {
+    if (INTERP && s.vnrm) {
         const int ia = __ldg(s.tris + 3 * (size_t)tri), ib = __ldg(s.tris + 3 * (size_t)tri + 1),
                   ic = __ldg(s.tris + 3 * (size_t)tri + 2);
         const float3 na = xyz(__ldg(s.vnrm + ia)), nb = xyz(__ldg(s.vnrm + ib)), nc = xyz(__ldg(s.vnrm + ic));

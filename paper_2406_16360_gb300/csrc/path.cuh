@@ -123,12 +123,13 @@ __device__ __forceinline__ void tape_directions(const TapeDev& tp, uint64_t g, c
     tp.pind[g] = out.c_pind;
 }
 
+template <bool INTERP = true>
 __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, const Rng& rng, uint32_t pixel,
                                              uint32_t smp, uint32_t view, int b, int B, int M, const Hit& h,
                                              float3 d, float3 beta, float3 bind, VertexOut& out)
 {
     Shade sh;
-    shade_at(s, h.tri, h.u, h.v, d, sh);
+    shade_at<INTERP>(s, h.tri, h.u, h.v, d, sh);
     const float3 wo = f3(-d.x, -d.y, -d.z);
     out.x = sh.x;
     out.shadow = false;

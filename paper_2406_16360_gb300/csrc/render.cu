@@ -684,7 +684,7 @@ __device__ __forceinline__ void full_backward(const SceneDev& s, const Rng& rng,
 // tape. FULL mode: in addition the vertices b >= 1 from their tape records (see
 // full_vertices below). All 32 lanes of a warp run the same number of rounds, so the
 // warp-collective scatters see every lane.
-template <bool FULL, int MINB>
+template <bool FULL, int MINB, bool INTERP>
 __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restrict__ scenes,
                                                         const ViewDev* __restrict__ views, int n_views, uint64_t total,
                                                         Rng rng, const float* const* __restrict__ d_images,
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
                     float t, u, vv;
                     tri_solve(o, d, v0, e1, e2, t, u, vv);
                     Shade sh;
-                    shade_at(s, tri, u, vv, d, sh);
+                    shade_at<INTERP>(s, tri, u, vv, d, sh);
                     const float3 wo = f3(-d.x, -d.y, -d.z);
                     float gm[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     const int cand = tp.cand[g];
@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
         // scatters are keyed per scene; lanes of other scenes never share a key group
         // because the key is combined with the scene id in the match
         const GradDev gd = grads[scene_id];
-        float* const gvn = gd.verts ? scenes[scene_id].gvn : nullptr;  // interpolated normals only
+        float* const gvn = (INTERP && gd.verts) ? scenes[scene_id].gvn : nullptr;  // interpolated normals only
         const unsigned same_scene = __match_any_sync(MR_FULL, scene_id);
         if (same_scene == MR_FULL) {
             scatter_agg<3>(env_key, env_v, EmitEnv{gd.env});
@@ -1228,12 +1228,14 @@ uint64_t mr_full_chunk() { return MR_FULL_SPLIT ? MR_FULL_CHUNK : 0; }
 
 void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
                         const float* const* d_images, const GradDev* grads, const void* tape,
-                        unsigned long long* counters, int sms, cudaStream_t st, int nvx, void* full_scratch)
+                        unsigned long long* counters, int sms, cudaStream_t st, int nvx, void* full_scratch,
+                        bool interp)
 {
 #if MR_FULL_SPLIT
     // the primary vertex of every sample (the tape's FULL records are read by k_full only)
-    k_backward<false, MR_BWD_MINB><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(
-        scenes, views, n_views, total, rng, d_images, grads, tape, nvx, counters);
+    (interp ? k_backward<false, MR_BWD_MINB, true> : k_backward<false, MR_BWD_MINB, false>)<<<
+        grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng, d_images, grads, tape, nvx,
+                                                     counters);
     if (nvx <= 0) return;
     unsigned int* bins = static_cast<unsigned int*>(full_scratch);  // [0, 16) counts, [16, 32) cursors, [32] total
     uint32_t* list = bins + 64;
@@ -1249,11 +1251,12 @@ void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_view
     }
 #else
     (void)full_scratch;
+    (void)interp;
     if (nvx > 0)
-        k_backward<true, MR_FULL_MINB><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng,
+        k_backward<true, MR_FULL_MINB, true><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng,
                                                                           d_images, grads, tape, nvx, counters);
     else
-        k_backward<false, MR_BWD_MINB><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(
+        k_backward<false, MR_BWD_MINB, true><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(
             scenes, views, n_views, total, rng, d_images, grads, tape, 0, counters);
 #endif
 }

@@ -85,7 +85,8 @@ size_t mr_full_scratch_bytes();
 uint64_t mr_full_chunk();  // samples per FULL-mode pass (0: one kernel does every vertex)
 void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
                         const float* const* d_images, const GradDev* grads, const void* tape,
-                        unsigned long long* counters, int sms, cudaStream_t st, int nvx, void* full_scratch);
+                        unsigned long long* counters, int sms, cudaStream_t st, int nvx, void* full_scratch,
+                        bool interp);
 void mr_launch_l2(const float* img, const float* ref, int64_t n, float* dimg, float* loss, int sms, cudaStream_t st);
 void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* skip, int64_t n, int any,
                           int32_t* hit_tri, float* hit_tuv, int sms, cudaStream_t st);

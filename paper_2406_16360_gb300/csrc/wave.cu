@@ -116,7 +116,7 @@ __global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
     if (COUNT) flush_work(counters, CNT_CBOX, n_box, (unsigned int)n_tri);
 }
 
-template <bool REUSE>
+template <bool REUSE, bool INTERP>
 __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* __restrict__ scenes,
                                                 const ViewDev* __restrict__ views, Rng rng, int b, int M,
                                                 QueueDev hq, const unsigned int* count_hit, QueueDev qout,
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* _
             h.v = hd.z;
             h.tri = tri;
             const int env_ok = *s.env_ok_dev;
-            shade_vertex(s, env_ok, rng, pixel, smp, (uint32_t)v.index, b, v.bounces, M, h, xyz(qd), xyz(qb),
+            shade_vertex<INTERP>(s, env_ok, rng, pixel, smp, (uint32_t)v.index, b, v.bounces, M, h, xyz(qd), xyz(qb),
                          xyz(hq.bi[i]), out);
             if (env_ok) n_cand += (unsigned long long)M;
             if (b == 0) {
@@ -712,6 +712,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist,
                     const ViewDev* hviews, const SceneDev* hscenes, bool raster)
 {
+    bool interp = false;  // any scene with interpolated normals
+    for (int i = 0; i < n_views; ++i) interp = interp || hscenes[hviews[i].scene].vnrm != nullptr;
     const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
     // the refilling kernels run one resident wave of blocks
     int occ_c = 0, occ_s = 0;
@@ -769,7 +771,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
             mark(0, false);
             mark(1, true);
             const bool reuse_b = b == 0 && res.ytex != nullptr;
-            (reuse_b ? k_wshade<true> : k_wshade<false>)<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(
+            (reuse_b ? (interp ? k_wshade<true, true> : k_wshade<true, false>)
+                     : (interp ? k_wshade<false, true> : k_wshade<false, false>))<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(
                 scenes, views, rng, b, M, hq, qc + 3 * b, nxt, qc + 3 * b + 1, sq, qc + 3 * b + 2, tape, total, nvx,
                 res, counters);
             if (reuse_b && temporal == 2)
