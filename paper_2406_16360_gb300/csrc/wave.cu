@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ vie
     }
 }
 
-template <bool COUNT>
+template <bool COUNT, bool RASTER>
 __global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
                                                   const ViewDev* __restrict__ views, int b, QueueDev q,
                                                   const unsigned int* count, unsigned int count_fixed, QueueDev hq,
@@ -76,7 +76,7 @@ __global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
             qb = q.b[i];
             const ViewDev& v = views[__float_as_int(qb.w)];
             const SceneDev& s = scenes[v.scene];
-            if (raster) {
+            if (RASTER) {
                 // primary visibility from the rasteriser: the winning triangle, solved again
                 // with the same arithmetic for its (t, u, v)
                 const unsigned long long key = raster[i];
@@ -766,7 +766,9 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                 (count ? k_wclosest_refill<true> : k_wclosest_refill<false>)<<<grid_c, 256, smem, st>>>(
                     scenes, views, cur, cnt_in, hq, qc + 3 * b, fetch + 2 * b, counters);
             else
-                (count ? k_wclosest<true> : k_wclosest<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
+                (keys ? (count ? k_wclosest<true, true> : k_wclosest<false, true>)
+                      : (count ? k_wclosest<true, false> : k_wclosest<false, false>))<<<grid_cap(n, 256, sms * 8), 256,
+                                                                                        smem, st>>>(
                     scenes, views, b, cur, cnt_in, n, hq, qc + 3 * b, tape, total, counters, keys);
             mark(0, false);
             mark(1, true);
