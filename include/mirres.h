@@ -195,7 +195,7 @@ mirres_status mirres_bvh_build(mirres_scene* scene, void* stream);
  *     vertex normals are recomputed by every mirres_bvh_build and mirres_bvh_refit (and here if
  *     the scene is built); the PRIMARY adjoint follows the shading normal to the barycentrics
  *     and to the vertices of every face around the hit triangle's vertices.
- * Allocates 28 bytes per vertex the first time it is enabled. MIRRES_ERR_ARG for an unknown
+ * Allocates 40 bytes per vertex the first time it is enabled. MIRRES_ERR_ARG for an unknown
  * mode. */
 #define MIRRES_NORMALS_FACE 0
 #define MIRRES_NORMALS_INTERPOLATED 1
