@@ -167,3 +167,42 @@ def test_roof_face_without_light_stays_dark(M, ctx):
     assert left.sum() > 20
     assert np.all(images[0].cpu().numpy().reshape(-1, 3)[left] == 0.0)
     _close(gw)
+
+
+def test_mixed_scenes_one_interpolated(M, ctx):
+    """two scenes in one call, only the second with interpolated normals: each scene is shaded
+    and differentiated with its own normals"""
+    from paper_2406_16360_gb300.renderer import GpuWorkload
+    w = synth.config5(seed=3, n_scenes=2, max_tris=6000, res_choices=(16, 24), spp_choices=(2, 3), tex=16)
+    for s in w.scenes:
+        s.env[:] = np.minimum(s.env, 50.0)
+    gw = GpuWorkload(w, 0, ctx=ctx)  # face normals everywhere ...
+    M.mirres_scene_set_normals(gw.scenes[1].handle, INTERP)  # ... but in the second scene
+    images, tape = gw.render(launch=1)
+    torch.cuda.synchronize()
+    modes = [0, INTERP]
+    rng = np.random.Generator(np.random.PCG64(8))
+    d_imgs, refs = [], []
+    for vi, v in enumerate(w.views):
+        r = O.render(O.OracleScene(w.scenes[v.scene], normals=modes[v.scene]), v, vi, w.ris_m, seed=w.seed)
+        st = compare_pixels(images[vi].cpu().numpy().reshape(-1, 3), r["rgb"], r["margin"], rtol=FWD_RTOL)
+        assert st["failures"] == 0, (vi, st["failures"], st["max_err_unflagged"])
+        g = rng.normal(size=(v.height * v.width, 3))
+        g[r["margin"] < 1.0] = 0.0
+        d_imgs.append(torch.as_tensor(g.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda"))
+    grads = gw.backward(d_imgs, tape)
+    torch.cuda.synchronize()
+    for si, sc in enumerate(w.scenes):
+        osc = O.OracleScene(sc, normals=modes[si])
+        acc = None
+        for vi, v in enumerate(w.views):
+            if v.scene != si:
+                continue
+            gi = O.backward(osc, v, vi, w.ris_m, d_imgs[vi].double().cpu().numpy().reshape(-1, 3), seed=w.seed)
+            acc = gi if acc is None else {k: acc[k] + gi[k] for k in gi if k != "counts"}
+        if acc is None:
+            continue
+        for k in ("albedo", "roughness", "env"):
+            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"))
+            assert st["failures"] == 0, (si, k, st["failures"], st["max_rel"], st["detail"])
+    _close(gw)
