@@ -314,7 +314,7 @@ def main():
 
     history = None
 
-    def step(launch, ev_render=None, ev_bwd=None, grad_mode=0, reuse=(0, 0), temporal=0):
+    def step(launch, ev_render=None, ev_bwd=None, grad_mode=0, reuse=(0, 0), temporal=0, before_loss=None):
         for s in gw.scenes:
             M.mirres_bvh_build(s.handle)
         if ev_render is not None:
@@ -326,6 +326,8 @@ def main():
                         images, tape)
         if ev_render is not None:
             ev_render[1].record()
+        if before_loss is not None:
+            before_loss()
         for img, ref, d in zip(images, refs, d_images):
             M.mirres_l2_loss(img, ref, d, loss)
         if ev_bwd is not None:
@@ -404,14 +406,23 @@ def main():
         sum(t.numel() * t.element_size() for t in host_refs)
     d2h = sum(t.numel() * t.element_size() for hg in host_grads for t in hg.values()) + 4
 
+    copy_stream = torch.cuda.Stream(device=dev)
+
     def e2e_step():
+        # this step's inputs from pinned host memory: the scene parameters before the render on
+        # the compute stream, the reference images (the bulk) on a copy stream that overlaps the
+        # render and is waited for before the loss
         for s, hp in zip(gw.scenes, host_params):
             for k, t in s.params().items():
                 t.copy_(hp[k], non_blocking=True)
-        for r, hr in zip(refs, host_refs):
-            r.copy_(hr, non_blocking=True)
+        copy_stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(copy_stream):
+            for r, hr in zip(refs, host_refs):
+                r.copy_(hr, non_blocking=True)
+        refs_ready = torch.cuda.Event()
+        refs_ready.record(copy_stream)
         zero()
-        step(1)
+        step(1, before_loss=lambda: torch.cuda.current_stream().wait_event(refs_ready))
         for g, hg in zip(grads, host_grads):
             for k in g:
                 hg[k].copy_(g[k], non_blocking=True)
