@@ -345,12 +345,20 @@ mirres_status mirres_trace(mirres_context* ctx, const mirres_scene* scene, const
 mirres_status mirres_bvh_export(const mirres_scene* scene, uint64_t* keys, int32_t* left, int32_t* right,
                                 int32_t* parent, float* lo, float* hi, void* stream);
 
-/* Copy the env sampling tables to caller device buffers (any may be NULL): marg [env_h + 1]
- * and cond [env_h][env_w + 1] as uint32 thresholds ceil(cdf * 2^24) (cdf <= u exactly when
- * threshold <= u * 2^24 for a 24-bit uniform u), texel [env_h][env_w][4] = (r, g, b,
- * probability * env_w * env_h) and the FP64 total weight (device double). */
+/* Copy the env sampling tables to caller device buffers (any may be NULL): the factorised
+ * form of the proposal, marg [env_h + 1] and cond [env_h][env_w + 1] as uint32 thresholds
+ * ceil(cdf * 2^24) (cdf <= u exactly when threshold <= u * 2^24 for a 24-bit uniform u),
+ * texel [env_h][env_w][4] = (r, g, b, probability * env_w * env_h) and the FP64 total weight
+ * (device double). The draw itself inverts the CDF of mirres_env_export_flat. */
 mirres_status mirres_env_export(const mirres_scene* scene, uint32_t* marg, uint32_t* cond, float* texel,
                                 double* total, void* stream);
+
+/* The CDF over all env texels in row-major order that every env draw inverts (RIS candidates,
+ * the env lobe of the continuation mixture): thresholds [env_h env_w + 1] = ceil(cdf 2^53),
+ * cdf = (weights of the rows before + of the texels before in the row) / total, each sum in
+ * order. A draw takes k = w0 2^21 + (w1 >> 11) from two random words and the texel t with
+ * thresholds[t] <= k < thresholds[t + 1]. Device copy (asynchronous); for tests. */
+mirres_status mirres_env_export_flat(const mirres_scene* scene, uint64_t* thresholds, void* stream);
 
 /* ---- denoiser between the rendered image and the loss (Appendix A, "Denoiser") ------------- */
 

@@ -97,6 +97,7 @@ struct orc_scene {
     int tw, th; double* alb; double* rgh; double* met;
     int ew, eh; double* env;
     double* cond; double* marg; double* prob; double total; int env_ok;
+    double* flat; /* [H W + 1] CDF over all texels in row-major order (the one the draw inverts) */
     double tmin, diag;
     int nnodes; Node* nodes; int32_t* order;
     /* shading normals: 0 face normal, 1 interpolated from area-weighted vertex normals */
@@ -162,8 +163,9 @@ static int bvh_build(orc_scene* s, const double* cent, int first, int count)
 }
 
 /* Environment sampling distribution, the proposal q_dir of Sec. 4.1 (proportional to L_env):
- * texel weight Y(L) * sin(theta_row), a marginal CDF over rows and a conditional CDF per row,
- * built in FP64 by sequential prefix sums. */
+ * texel weight Y(L) * sin(theta_row); a marginal CDF over rows and a conditional CDF per row
+ * (their factorisation, kept for the tables' pins), and the CDF over all texels that the draw
+ * inverts, built in FP64 by sequential prefix sums. */
 static void env_build(orc_scene* s)
 {
     int W = s->ew, H = s->eh;
@@ -198,6 +200,22 @@ static void env_build(orc_scene* s)
         if (r < H) acc += rowsum[r];
     }
     for (size_t i = 0; i < (size_t)W * H; ++i) s->prob[i] = s->env_ok ? w[i] / s->total : 0.0;
+    /* the same distribution over all texels in row-major order: entry r W + c is
+     * (rows before r + texels before c in row r) / total, each sum taken in order */
+    {
+        double base = 0.0;
+        const size_t N = (size_t)W * H;
+        for (int r = 0; r < H; ++r) {
+            double within = 0.0;
+            for (int c = 0; c < W; ++c) {
+                const size_t i = (size_t)r * W + c;
+                s->flat[i] = s->env_ok ? (base + within) / s->total : (double)i / (double)N;
+                within += w[i];
+            }
+            base += rowsum[r];
+        }
+        s->flat[N] = 1.0;
+    }
     free(w);
     free(rowsum);
 }
@@ -229,6 +247,7 @@ orc_scene* orc_scene_new(const orc_scene_desc* d)
     s->cond = (double*)malloc(sizeof(double) * (size_t)s->eh * (s->ew + 1));
     s->marg = (double*)malloc(sizeof(double) * (size_t)(s->eh + 1));
     s->prob = (double*)malloc(sizeof(double) * (size_t)s->eh * s->ew);
+    s->flat = (double*)malloc(sizeof(double) * ((size_t)s->eh * s->ew + 1));
     env_build(s);
     /* scene extent: AABB of all vertices referenced by triangles */
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -290,7 +309,7 @@ void orc_scene_free(orc_scene* s)
 {
     if (!s) return;
     free(s->V); free(s->F); free(s->UV); free(s->alb); free(s->rgh); free(s->met); free(s->env);
-    free(s->cond); free(s->marg); free(s->prob); free(s->nodes); free(s->order);
+    free(s->cond); free(s->marg); free(s->prob); free(s->flat); free(s->nodes); free(s->order);
     free(s->VA); free(s->VN); free(s->vf_off); free(s->vf);
     free(s);
 }
@@ -303,6 +322,11 @@ void orc_vertex_normals(const orc_scene* s, double* out)
 }
 
 double orc_scene_tmin(const orc_scene* s) { return s->tmin; }
+
+void orc_env_flat(const orc_scene* s, double* flat)
+{
+    memcpy(flat, s->flat, sizeof(double) * ((size_t)s->eh * s->ew + 1));
+}
 
 double orc_env_tables(const orc_scene* s, double* cond, double* marg, double* prob)
 {
@@ -565,18 +589,21 @@ static int cdf_search(const double* cdf, int n, double u)
     return lo;
 }
 
-/* inverse-CDF sample: row from the marginal, column from the row's conditional, a uniform
- * position inside the texel from a 16+16-bit word; returns the solid-angle pdf */
-static double env_sample_m(const orc_scene* s, double urow, double ucol, uint32_t sub, v3* dir, int* texel, Margin* mg)
+/* 53-bit uniform from two random words: the high 32 bits from a, the low 21 from the top of b */
+static double u53(uint32_t a, uint32_t b)
+{
+    return (double)(((uint64_t)a << 21) | (uint64_t)(b >> 11)) * (1.0 / 9007199254740992.0);
+}
+
+/* inverse-CDF sample over all texels (row-major CDF, a 53-bit uniform from two words), a
+ * uniform position inside the texel from a 16+16-bit word; returns the solid-angle pdf */
+static double env_sample_m(const orc_scene* s, uint32_t xa, uint32_t xb, uint32_t sub, v3* dir, int* texel, Margin* mg)
 {
     int W = s->ew, H = s->eh;
-    int r = cdf_search(s->marg, H, urow);
-    const double* cr = s->cond + (size_t)r * (W + 1);
-    int c = cdf_search(cr, W, ucol);
-    if (mg) {
-        note(mg, dmin(urow - s->marg[r], s->marg[r + 1] - urow) / TAU_CDF, MK_CDF);
-        note(mg, dmin(ucol - cr[c], cr[c + 1] - ucol) / TAU_CDF, MK_CDF);
-    }
+    const double u = u53(xa, xb);
+    int t = cdf_search(s->flat, W * H, u);
+    if (mg) note(mg, dmin(u - s->flat[t], s->flat[t + 1] - u) / TAU_CDF, MK_CDF);
+    int r = t / W, c = t % W;
     double uu = (c + sub_hi(sub)) / W, vv = (r + sub_lo(sub)) / H;
     double phi = 2.0 * PI * (uu - 0.5), theta = PI * vv;
     double st = sin(theta);
@@ -589,7 +616,7 @@ double orc_env_sample(const orc_scene* s, const uint32_t x[4], double out_dir[3]
 {
     v3 d;
     int t;
-    double p = env_sample_m(s, orc_uniform(x[0]), orc_uniform(x[1]), x[3], &d, &t, NULL);
+    double p = env_sample_m(s, x[0], x[1], x[3], &d, &t, NULL);
     vstore(out_dir, d);
     *out_texel = t;
     return p;
@@ -815,7 +842,7 @@ static double sample_cont_m(const orc_scene* s, v3 n, v3 wo, const double alb[3]
     note(mg, fabs(u - t2) / TAU_LOBE, MK_LOBE);
     if (u < mx.c_env) {
         int tex;
-        env_sample_m(s, orc_uniform(x[1]), orc_uniform(x[2]), x[3], dir, &tex, mg);
+        env_sample_m(s, x[1], x[2], x[3], dir, &tex, mg);
     } else if (u < t2) {
         *dir = vndf_sample_m(n, wo, alpha_of(r), orc_uniform(x[1]), orc_uniform(x[2]), mg);
     } else {
@@ -1051,7 +1078,7 @@ static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, 
         rng(c, pix, (uint32_t)smp, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j, x);
         v3 dir;
         int tex;
-        double q = env_sample_m(s, orc_uniform(x[0]), orc_uniform(x[1]), x[3], &dir, &tex, mg);
+        double q = env_sample_m(s, x[0], x[1], x[3], &dir, &tex, mg);
         double fc[3];
         light_brdf(sh, wo, dir, kind, fc, mg);
         double phat = lum(s->env + 3 * tex) * lum(fc); /* p_hat = Y(L_env) Y(f_r) cos */

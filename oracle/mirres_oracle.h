@@ -128,6 +128,8 @@ int orc_lbvh(const float* verts, const int32_t* tris, int32_t n_tris,
 
 /* Environment sampling tables: cond [h][w+1], marg [h+1], prob [h][w]; returns total weight. */
 double orc_env_tables(const orc_scene* s, double* cond, double* marg, double* prob);
+/* the CDF over all texels in row-major order that the draw inverts [h w + 1] */
+void orc_env_flat(const orc_scene* s, double* flat);
 
 /* ---- unit functions, exported for the pins ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -84,6 +84,7 @@ def lib():
             L.orc_lbvh.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp]
             L.orc_env_tables.restype = dbl
             L.orc_env_tables.argtypes = [vp, vp, vp, vp]
+            L.orc_env_flat.argtypes = [vp, vp]
             L.orc_philox4x32_10.argtypes = [vp, vp, vp]
             L.orc_uniform.restype = dbl
             L.orc_uniform.argtypes = [C.c_uint32]
@@ -158,6 +159,13 @@ class OracleScene:
         prob = np.zeros((eh, ew))
         total = lib().orc_env_tables(self.h, _p(cond), _p(marg), _p(prob))
         return cond, marg, prob, total
+
+    def env_flat(self):
+        """the CDF over all texels (row-major) that the env draw inverts, [h w + 1]"""
+        eh, ew = self.scene.env.shape[:2]
+        out = np.zeros(eh * ew + 1)
+        lib().orc_env_flat(self.h, _p(out))
+        return out
 
 
 def make_view(view, index):

@@ -48,16 +48,12 @@ SceneDev mr_scene_dev(const mirres_scene* s)
     d.rough = s->desc.roughness;
     d.metal = s->desc.metallic;
     d.env_texel = s->env_texel;
-    d.env_marg = s->env_marg;
-    d.env_cond = s->env_cond;
-    d.env_gmarg = s->env_gmarg;
-    d.env_gcond = s->env_gcond;
     d.env_row = s->env_row;
     d.env_col = s->env_col;
     d.env_fine = (s->desc.env_w >= 64 && s->desc.env_h >= 32) ? 1 : 0;
-    d.gm_shift = s->gm_shift;
-    d.gc_shift = s->gc_shift;
-    d.gc = s->gc;
+    d.env_flat = s->env_flat;
+    d.env_gflat = s->env_gflat;
+    d.gf_shift = s->gf_shift;
     d.n_tris = s->desc.n_tris;
     d.n_verts = s->desc.n_verts;
     d.tw = s->desc.tex_w;
@@ -1089,6 +1085,19 @@ extern "C" mirres_status mirres_bvh_export(const mirres_scene* s, uint64_t* keys
     if (parent) MR_CUDA(cudaMemcpyAsync(parent, s->parent, sizeof(int32_t) * (2 * F - 1), k, st));
     if (lo) MR_CUDA(cudaMemcpyAsync(lo, s->lo, sizeof(float) * 3 * (2 * F - 1), k, st));
     if (hi) MR_CUDA(cudaMemcpyAsync(hi, s->hi, sizeof(float) * 3 * (2 * F - 1), k, st));
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_env_export_flat(const mirres_scene* s, uint64_t* thresholds, void* stream)
+{
+    if (!s || !thresholds) return arg_error("scene and thresholds required");
+    if (!s->built) {
+        g_err = "mirres_env_export_flat: call mirres_bvh_build first";
+        return MIRRES_ERR_STATE;
+    }
+    const size_t n = (size_t)s->desc.env_w * s->desc.env_h + 1;
+    MR_CUDA(cudaMemcpyAsync(thresholds, s->env_flat, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice,
+                            as_stream(stream)));
     return MIRRES_OK;
 }
 

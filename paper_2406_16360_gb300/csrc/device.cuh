@@ -66,14 +66,12 @@ struct SceneDev {
     const float* rough;       // [th][tw]
     const float* metal;       // [th][tw]
     const float4* env_texel;  // [eh][ew]: (r, g, b, prob * ew * eh)
-    const uint32_t* env_marg; // [eh + 1] thresholds ceil(cdf * 2^24)
-    const uint32_t* env_cond; // [eh][ew + 1]
-    const uint32_t* env_gmarg; // [gm + 1] guide: answer of the marginal search at bucket starts
-    const uint32_t* env_gcond; // [eh][gc + 1] guide of every row's conditional search
     const float4* env_row;    // [eh]: (cos th_r, sin th_r, 2 pi^2 total / (ew eh sin th_r), 0) at row centres
     const float2* env_col;    // [ew]: (cos psi_c, sin psi_c), psi = 2 pi u - pi at column centres
     int32_t env_fine;         // 1 when a texel spans at most pi/32 in both angles (tables used)
-    int32_t gm_shift, gc_shift, gc;
+    const unsigned long long* env_flat; // [eh ew + 1] ceil(cdf 2^53) of the CDF over all texels
+    const uint32_t* env_gflat;          // [gf + 1] guide: answer of the search at bucket starts
+    int32_t gf_shift;
     int32_t n_tris, n_verts, tw, th, ew, eh;
     const int32_t* env_ok_dev; // device-written: total env weight > 0
     const float* tmin_dev;     // device-written: 1e-5 x scene diagonal
@@ -191,17 +189,6 @@ __device__ __forceinline__ float env_pdf_dir(const SceneDev& s, float3 d, int te
     return __ldg(&s.env_texel[texel].w) / (2.0f * MR_PI * MR_PI * st);
 }
 
-// largest i in [lo, hi] with a[i] <= k, given a[lo] <= k
-__device__ __forceinline__ int search_range(const uint32_t* __restrict__ a, int lo, int hi, uint32_t k)
-{
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(a + mid) <= k) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // sin and cos of a small angle by their Taylor series; for |x| <= pi/64 the truncation error
 // is below 2e-13, far under FP32 rounding
 __device__ __forceinline__ void sincos_small(float x, float& sn, float& cs)
@@ -243,14 +230,21 @@ __device__ __forceinline__ float env_dir(const SceneDev& s, int r, int c, uint32
 // searches start from guide tables (cut-point method): the answer at the start of the
 // uniform's bucket and at the next bucket bound the answer, so the search is the same
 // function of the uniform as a full binary search, over a range of ~1-2 entries.
-__device__ __forceinline__ void env_texel_draw(const SceneDev& s, uint32_t xrow, uint32_t xcol, int& r, int& c)
+// the texel of the CDF over all texels (row-major) at the 53-bit uniform k 2^-53,
+// k = xa 2^21 + (xb >> 11): the largest t with threshold[t] <= k, searched inside the range
+// the guide gives for k's bucket
+__device__ __forceinline__ void env_texel_draw(const SceneDev& s, uint32_t xa, uint32_t xb, int& r, int& c)
 {
-    const uint32_t kr = xrow >> 8, kc = xcol >> 8;
-    const uint32_t bm = kr >> s.gm_shift;
-    r = search_range(s.env_marg, (int)__ldg(s.env_gmarg + bm), (int)__ldg(s.env_gmarg + bm + 1), kr);
-    const uint32_t* grow = s.env_gcond + (size_t)r * (s.gc + 1);
-    const uint32_t bc = kc >> s.gc_shift;
-    c = search_range(s.env_cond + (size_t)r * (s.ew + 1), (int)__ldg(grow + bc), (int)__ldg(grow + bc + 1), kc);
+    const unsigned long long k = ((unsigned long long)xa << 21) | (unsigned long long)(xb >> 11);
+    const uint32_t b = (uint32_t)(k >> s.gf_shift);
+    int lo = (int)__ldg(s.env_gflat + b), hi = (int)__ldg(s.env_gflat + b + 1);
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(s.env_flat + mid) <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    r = lo / s.ew;
+    c = lo - r * s.ew;
 }
 
 // sample a direction with probability proportional to Y(L) sin(theta_row); returns pdf.

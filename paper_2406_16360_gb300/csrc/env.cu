@@ -6,6 +6,10 @@
 // over the row, so every sum has a fixed order), converted to uint32 thresholds
 // ceil(cdf * 2^24): for a 24-bit uniform u = k 2^-24, cdf <= u exactly when threshold <= k,
 // so the search needs no FP64 arithmetic. The texel table packs (r, g, b, P * W * H).
+// The draw inverts the CDF over all texels in row-major order, (rows before + texels before in
+// the row) / total, as 53-bit thresholds ceil(cdf * 2^53) for a 53-bit uniform made of two
+// random words, through a guide with about two buckets per texel: one short search instead of
+// a row search followed by a column search.
 #include "internal.h"
 
 namespace {
@@ -42,7 +46,7 @@ __global__ void k_env_rows(const float* __restrict__ env, int W, int H, double* 
 }
 
 __global__ void k_env_marg(const double* __restrict__ rowsum, int H, double* total_out, int32_t* ok_out,
-                           uint32_t* __restrict__ marg)
+                           uint32_t* __restrict__ marg, double* __restrict__ rowbase)
 {
     if (threadIdx.x != 0) return;
     double total = 0.0;
@@ -54,10 +58,57 @@ __global__ void k_env_marg(const double* __restrict__ rowsum, int H, double* tot
         if (ok) v = (r == H) ? 1.0 : run / total;
         else v = (double)r / (double)H;
         marg[r] = threshold(v);
-        if (r < H) run += rowsum[r];
+        if (r < H) {
+            rowbase[r] = run;
+            run += rowsum[r];
+        }
     }
     *total_out = total;
     *ok_out = ok;
+}
+
+__device__ __forceinline__ unsigned long long threshold53(double cdf)
+{
+    const double x = ceil(cdf * 9007199254740992.0);
+    return x <= 0.0 ? 0ull : (x >= 9007199254740992.0 ? 9007199254740992ull : (unsigned long long)x);
+}
+
+// one thread per row: thresholds of the CDF over all texels, (rows before + texels before in
+// the row) / total, each sum in order
+__global__ void k_env_flat(const double* __restrict__ w, const double* __restrict__ rowbase,
+                           const double* __restrict__ total, int W, int H, unsigned long long* __restrict__ flat)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H) return;
+    const double tot = *total, base = rowbase[r];
+    const double n = (double)W * (double)H;
+    double within = 0.0;
+    for (int c = 0; c < W; ++c) {
+        const size_t i = (size_t)r * W + c;
+        flat[i] = threshold53(tot > 0.0 ? (base + within) / tot : (double)i / n);
+        within += w[i];
+    }
+    if (r == H - 1) flat[(size_t)W * H] = 9007199254740992ull;
+}
+
+// guide of the flat CDF: bucket b answers the search at k = b << shift; entry g is n - 1
+__global__ void k_env_flat_guide(const unsigned long long* __restrict__ flat, int n, int g, int shift,
+                                 uint32_t* __restrict__ guide)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > g) return;
+    if (b == g) {
+        guide[b] = (uint32_t)(n - 1);
+        return;
+    }
+    const unsigned long long k = (unsigned long long)b << shift;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (flat[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    guide[b] = (uint32_t)lo;
 }
 
 __global__ void k_env_texels(const float* __restrict__ env, const double* __restrict__ w, int W, int H,
@@ -131,6 +182,13 @@ mirres_status mr_env_alloc(mirres_scene* s)
     const size_t W = (size_t)s->desc.env_w, H = (size_t)s->desc.env_h;
     guide_shape((int)H, s->gm, s->gm_shift);
     guide_shape((int)W, s->gc, s->gc_shift);
+    {
+        // about two guide buckets per texel over the 53-bit uniform
+        int lg = 1;
+        while (((size_t)1 << lg) < 2 * W * H && lg < 30) ++lg;
+        s->gf = 1 << lg;
+        s->gf_shift = 53 - lg;
+    }
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaMalloc((void**)&s->env_gmarg, sizeof(uint32_t) * (size_t)(s->gm + 1));
     e = e ? e : cudaMalloc((void**)&s->env_gcond, sizeof(uint32_t) * H * (size_t)(s->gc + 1));
@@ -143,6 +201,9 @@ mirres_status mr_env_alloc(mirres_scene* s)
     e = e ? e : cudaMalloc((void**)&s->env_texel, sizeof(float4) * W * H);
     e = e ? e : cudaMalloc((void**)&s->env_row, sizeof(float4) * H);
     e = e ? e : cudaMalloc((void**)&s->env_col, sizeof(float2) * W);
+    e = e ? e : cudaMalloc((void**)&s->env_flat, sizeof(unsigned long long) * (W * H + 1));
+    e = e ? e : cudaMalloc((void**)&s->env_gflat, sizeof(uint32_t) * ((size_t)s->gf + 1));
+    e = e ? e : cudaMalloc((void**)&s->env_rowbase, sizeof(double) * H);
     if (e != cudaSuccess) {
         cudaGetLastError();
         mr_set_error(std::string("env table allocation failed: ") + cudaGetErrorString(e));
@@ -154,7 +215,8 @@ mirres_status mr_env_alloc(mirres_scene* s)
 void mr_env_free(mirres_scene* s)
 {
     void* ptrs[] = {s->env_w,    s->env_rowsum, s->env_total, s->env_ok,   s->env_marg,
-                    s->env_cond, s->env_texel,  s->env_gmarg, s->env_gcond, s->env_row, s->env_col};
+                    s->env_cond, s->env_texel,  s->env_gmarg, s->env_gcond, s->env_row, s->env_col,
+                    s->env_flat, s->env_gflat,  s->env_rowbase};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -163,7 +225,10 @@ mirres_status mr_env_build(mirres_scene* s, cudaStream_t st)
 {
     const int W = s->desc.env_w, H = s->desc.env_h;
     k_env_rows<<<(H + 63) / 64, 64, 0, st>>>(s->desc.env, W, H, s->env_w, s->env_rowsum, s->env_cond);
-    k_env_marg<<<1, 32, 0, st>>>(s->env_rowsum, H, s->env_total, s->env_ok, s->env_marg);
+    k_env_marg<<<1, 32, 0, st>>>(s->env_rowsum, H, s->env_total, s->env_ok, s->env_marg, s->env_rowbase);
+    k_env_flat<<<(H + 63) / 64, 64, 0, st>>>(s->env_w, s->env_rowbase, s->env_total, W, H, s->env_flat);
+    k_env_flat_guide<<<(unsigned)((s->gf + 1 + 255) / 256), 256, 0, st>>>(s->env_flat, W * H + 1, s->gf,
+                                                                         s->gf_shift, s->env_gflat);
     const size_t n = (size_t)W * H;
     k_env_texels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->desc.env, s->env_w, W, H, s->env_total,
                                                              s->env_texel);

@@ -100,6 +100,12 @@ struct mirres_scene {
     float4* env_row = nullptr;       // [eh]: (cos, sin of the row centre, RIS weight factor, 0)
     float2* env_col = nullptr;       // [ew]: (cos, sin of the column centre angle)
     int gm_shift = 0, gc_shift = 0, gm = 1, gc = 1;
+    // the CDF over all texels (row-major) that the draw inverts: 53-bit thresholds, its guide
+    // and the FP64 sums of the rows before each row
+    unsigned long long* env_flat = nullptr;  // [eh ew + 1] ceil(cdf 2^53)
+    uint32_t* env_gflat = nullptr;           // [gf + 1]
+    double* env_rowbase = nullptr;           // [eh]
+    int gf = 1, gf_shift = 0;
     // mesh edges for the regularisers (built on first use; the topology is fixed per scene)
     int2* edges = nullptr;              // [<= 3F] unique undirected edges (a < b)
     float* inv_deg = nullptr;           // [V] 1 / neighbour count (0 for isolated vertices)

@@ -22,7 +22,8 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_reuse_history_bytes", "mirres_render",
            "mirres_render_noalloc",
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
-           "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_get_counters",
+           "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_env_export_flat",
+           "mirres_get_counters",
            "mirres_get_work_counters", "EawtParams", "mirres_eawt_record_bytes", "mirres_gbuffer", "mirres_eawt",
            "mirres_eawt_backward", "mirres_mesh_regularizers", "LkParams", "mirres_material_smoothness",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
@@ -134,6 +135,7 @@ def lib():
                                                     vp]),
                 "mirres_bvh_export": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "mirres_env_export": (st, [vp, vp, vp, vp, vp, vp]),
+                "mirres_env_export_flat": (st, [vp, vp, vp]),
                 "mirres_get_counters": (st, [vp, C.POINTER(C.c_uint64)]),
                 "mirres_get_work_counters": (st, [vp, C.POINTER(C.c_uint64)]),
                 "mirres_reset_counters": (st, [vp]),
@@ -394,6 +396,10 @@ def mirres_material_smoothness(ctx: Context, scene: Scene, view, view_index, par
 def mirres_bvh_export(scene: Scene, keys=None, left=None, right=None, parent=None, lo=None, hi=None, stream=None):
     _check("mirres_bvh_export", lib().mirres_bvh_export(scene.handle, _ptr(keys), _ptr(left), _ptr(right),
                                                         _ptr(parent), _ptr(lo), _ptr(hi), _stream(stream)))
+
+
+def mirres_env_export_flat(scene: Scene, thresholds, stream=None):
+    _check("mirres_env_export_flat", lib().mirres_env_export_flat(scene.handle, _ptr(thresholds), _stream(stream)))
 
 
 def mirres_env_export(scene: Scene, marg=None, cond=None, texel=None, total=None, stream=None):

@@ -142,6 +142,16 @@ def test_env_tables(M, ctx, which):
     assert abs(total.item() - ototal) <= 1e-12 * ototal
     np.testing.assert_allclose(texel.cpu().numpy()[..., 3], oprob * ew * eh, rtol=1e-6)
     np.testing.assert_array_equal(texel.cpu().numpy()[..., :3], sc.env)
+    # the CDF over all texels the draw inverts: 53-bit thresholds, the same ordered sums; an
+    # ulp of difference in a weight's sin moves a threshold by a few units of 2^-53 at most
+    flat = torch.zeros(eh * ew + 1, dtype=torch.int64, device=dev)
+    M.mirres_env_export_flat(ds.handle, flat)
+    torch.cuda.synchronize()
+    oflat = O.OracleScene(sc).env_flat()
+    ref = np.array([int(np.ceil(x * 2.0 ** 53)) for x in oflat], dtype=object)
+    got = flat.cpu().numpy().view(np.uint64).astype(object)
+    diff = np.array([int(a) - int(b) for a, b in zip(got, ref)])
+    assert np.abs(diff).max() <= 64, np.abs(diff).max()
     ds.close()
 
 

@@ -73,6 +73,30 @@ def test_env_pdf_integrates_to_one_and_samples_follow_table():
     assert chi2 < dof + 6 * math.sqrt(2 * dof)
 
 
+def test_env_draw_inverts_the_texel_cdf_with_a_53_bit_uniform():
+    """the draw takes u = (w0 2^21 + (w1 >> 11)) / 2^53 and the texel t with flat[t] <= u <
+    flat[t + 1]; flat is the marginal-times-conditional factorisation written out per texel"""
+    rng = np.random.Generator(np.random.PCG64(2))
+    W, H = 8, 4
+    env = np.exp(rng.normal(0, 1.5, size=(H, W, 3))).astype(np.float32)
+    env[2, 3] = 0.0  # a black texel
+    osc = O.OracleScene(_scene_with_env(env))
+    cond, marg, prob, total = osc.env_tables()
+    flat = osc.env_flat()
+    fact = (marg[:-1, None] + (marg[1:] - marg[:-1])[:, None] * cond[:, :-1]).reshape(-1)
+    np.testing.assert_allclose(flat[:-1], fact, rtol=0, atol=1e-15)
+    assert flat[-1] == 1.0 and np.all(np.diff(flat) >= 0)
+    np.testing.assert_allclose(np.diff(flat), prob.reshape(-1), rtol=0, atol=1e-15)
+    words = rng.integers(0, 2 ** 32, size=(3000, 4), dtype=np.uint64).astype(np.uint32)
+    words[0, :2] = 0  # u = 0: the first texel with weight
+    words[1, :2] = 0xFFFFFFFF  # u just below 1: the last texel with weight
+    for k in range(len(words)):
+        _, tex, _ = O.env_sample(osc, words[k])
+        u = ((int(words[k, 0]) << 21) | (int(words[k, 1]) >> 11)) / 2.0 ** 53
+        assert flat[tex] <= u < flat[tex + 1], (k, tex, u)
+        assert tex != 2 * W + 3
+
+
 @pytest.mark.parametrize("alpha", [0.05, 0.3, 1.0])
 def test_ggx_d_normalised(alpha):
     val, _ = integrate.quad(lambda mu: 2 * np.pi * O.ggx_d(alpha, mu) * mu, 0, 1, limit=200, points=[1 - alpha])

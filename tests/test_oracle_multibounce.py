@@ -93,13 +93,14 @@ def test_multibounce_matches_independent_path_tracer():
     rho, L = 0.8, 1.0
     sc = synth.tiny_scene(albedo=rho, env_value=L, sun=None, subdiv=2)
     K, c2w = synth.look_at((0.0, 0.9, 3.0), (0.0, 0.55, 0.0), 12, 12, 50.0)
-    view = synth.View(K, c2w, 12, 12, 2048, 3)
+    view = synth.View(K, c2w, 12, 12, 1024, 3)
     pixels = np.arange(144, dtype=np.int32)
     osc = O.OracleScene(sc)
-    # oracle: four independent seeds give its per-pixel standard error
-    runs = np.stack([O.render(osc, view, 0, 4, seed=s, brdf_kind=1, margins=False)["rgb"][:, 0] for s in range(4)])
+    # oracle: eight independent seeds give its per-pixel standard error (seven degrees of
+    # freedom: with four seeds the estimate's heavy t tails alone push some |z| past 5)
+    runs = np.stack([O.render(osc, view, 0, 4, seed=s, brdf_kind=1, margins=False)["rgb"][:, 0] for s in range(8)])
     o_mean = runs.mean(0)
-    o_se = runs.std(0, ddof=1) / 2.0
+    o_se = runs.std(0, ddof=1) / math.sqrt(runs.shape[0])
     rng = np.random.Generator(np.random.PCG64(123))
     pt = _path_trace(sc, view, pixels, 1024, 3, rho, L, rng)
     p_mean = pt.mean(1)
