@@ -1244,7 +1244,12 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
             rec->vx[b].d = d;
             rec->vx[b].sel = -1; rec->vx[b].y_texel = -1; rec->vx[b].WV = 0.0; rec->vx[b].has_cont = 0;
         }
-        if (b == 0) note(mg, vdot(sh.n, wo) / TAU_GRAZE, MK_GRAZE);
+        if (b == 0) {
+            note(mg, vdot(sh.n, wo) / TAU_GRAZE, MK_GRAZE);
+            /* with interpolated normals the hit can graze the face while the shading normal
+             * does not: the intersection's derivative grows as 1 / (n_face . d) all the same */
+            if (sh.interp) note(mg, fabs(vdot(sh.ng, wo)) / TAU_GRAZE, MK_GRAZE);
+        }
         /* ---- direct light: RIS over M env candidates, streamed through a reservoir ---- */
         double direct[3] = {0, 0, 0};
         if (s->env_ok && M > 0) {
