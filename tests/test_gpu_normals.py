@@ -10,7 +10,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2406_16360_gb300 import synth
-from tests.parity import compare_grads, compare_pixels
+from tests.parity import compare_grads, grad_tolerance, compare_pixels
 
 pytestmark = pytest.mark.gpu
 
@@ -98,7 +98,8 @@ def _grads(gw, w, refs, tape, grad_mode=0, seed=123, fields=("albedo", "roughnes
                     moved.verts = np.nextafter(sc.verts.astype(np.float32), away)
                     spread = np.maximum(spread, np.abs(oracle(moved)[k] - acc[k]))
                 sens = 10.0 * spread
-            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], sens)
+            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], sens,
+                               **grad_tolerance(k))
             assert st["failures"] == 0, (k, st["failures"], st["max_rel"], st["detail"])
 
 
@@ -206,6 +207,7 @@ def test_mixed_scenes_one_interpolated(M, ctx):
         if acc is None:
             continue
         for k in ("albedo", "roughness", "env"):
-            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"))
+            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"),
+                               **grad_tolerance(k))
             assert st["failures"] == 0, (si, k, st["failures"], st["max_rel"], st["detail"])
     _close(gw)

@@ -11,7 +11,7 @@ import torch
 from oracle import oracle as O
 from paper_2406_16360_gb300 import synth
 from paper_2406_16360_gb300.mirres import TAPE_WORDS
-from tests.parity import compare_grads, compare_pixels
+from tests.parity import compare_grads, grad_tolerance, compare_pixels
 
 pytestmark = pytest.mark.gpu
 
@@ -90,7 +90,8 @@ def _grad_parity(gw, w, tape, pixels_per_view=None, seed=7, grad_mode=0):
         if acc is None:
             continue
         for k in ("albedo", "roughness", "metallic", "env", "verts"):
-            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"))
+            st = compare_grads(grads[si][k].cpu().numpy(), acc[k], acc[k + "_abs"], acc.get(k + "_sens"),
+                               **grad_tolerance(k))
             assert st["failures"] == 0, (si, k, st["failures"], st["detail"])
 
 
@@ -199,7 +200,8 @@ def test_config3_full_size_sampled(M, ctx):
     torch.cuda.synchronize()
     og = O.backward(osc, v, 37, w.ris_m, d[37].double().cpu().numpy().reshape(-1, 3)[pix], seed=w.seed, pixels=pix)
     for k in ("albedo", "roughness", "metallic", "env", "verts"):
-        st = compare_grads(grads[0][k].cpu().numpy(), og[k], og[k + "_abs"], og.get(k + "_sens"))
+        st = compare_grads(grads[0][k].cpu().numpy(), og[k], og[k + "_abs"], og.get(k + "_sens"),
+                               **grad_tolerance(k))
         assert st["failures"] == 0, (k, st["detail"])
     for s in gw.scenes:
         s.close()
