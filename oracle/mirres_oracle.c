@@ -641,7 +641,11 @@ static double smith_a(double a, double c) { return sqrt(a * a + (1.0 - a * a) * 
 
 double orc_smith_g1(double a, double c) { return 2.0 * c / (c + smith_a(a, c)); }
 
-/* f_r * max(0, n.wi): returns 0 outside the upper hemispheres */
+/* f_r * max(0, n.wi): returns 0 outside the upper hemispheres. kind 0 = the method's GGX +
+ * Lambert; 1 = Lambert only (furnace pin); 2 = the demodulated lobes of the monochrome light
+ * regulariser (Appendix A, L_light): the diffuse lobe with its reflectance (1 - m) albedo
+ * divided out, i.e. 1 / pi, plus the specular lobe unchanged (Schlick's F0 mixes albedo and
+ * metallic inside F, which is not a factor that could be divided out) */
 static void brdf_cos(v3 n, v3 wo, v3 wi, const double alb[3], double r, double m, int kind, double out[3])
 {
     double co = vdot(n, wo), ci = vdot(n, wi);
@@ -658,7 +662,7 @@ static void brdf_cos(v3 n, v3 wo, v3 wi, const double alb[3], double r, double m
     double vis = 0.5 / (ci * smith_a(a, co) + co * smith_a(a, ci)); /* G2 / (4 ci co) */
     double w5 = pow(1.0 - coh, 5.0);
     for (int k = 0; k < 3; ++k) {
-        double kd = (1.0 - m) * alb[k];
+        double kd = kind == 2 ? 1.0 : (1.0 - m) * alb[k];
         double f0 = 0.04 * (1.0 - m) + m * alb[k];
         double F = f0 + (1.0 - f0) * w5;
         out[k] = (kd / PI + D * vis * F) * ci;
@@ -705,14 +709,17 @@ static void brdf_cos_grad(v3 n, v3 wo, v3 wi, const double alb[3], double r, dou
     /* value Q_k = (kd_k/pi + D vis F_k) ci */
     double sum_gF = 0.0, sum_gdiff = 0.0;
     double dm = 0.0;
+    /* kd_k = (1 - m) alb_k (kind 0) or 1 (kind 2, demodulated): d kd / d alb, d kd / d m */
+    const double dkd_da = kind == 2 ? 0.0 : 1.0 - m;
     for (int k = 0; k < 3; ++k) {
-        double kd = (1.0 - m) * alb[k];
+        double kd = kind == 2 ? 1.0 : (1.0 - m) * alb[k];
+        double dkd_dm = kind == 2 ? 0.0 : -alb[k];
         double f0 = 0.04 * (1.0 - m) + m * alb[k];
         double F = f0 + (1.0 - f0) * w5;
-        /* dQ/dalb_k = ((1-m)/pi + D vis m (1 - w5)) ci */
-        out[k] = g[k] * ((1.0 - m) / PI + D * vis * m * (1.0 - w5)) * ci;
-        /* dQ/dm = (-alb/pi + D vis (alb - 0.04)(1 - w5)) ci */
-        dm += g[k] * (-alb[k] / PI + D * vis * (alb[k] - 0.04) * (1.0 - w5)) * ci;
+        /* dQ/dalb_k = (dkd/dalb / pi + D vis m (1 - w5)) ci */
+        out[k] = g[k] * (dkd_da / PI + D * vis * m * (1.0 - w5)) * ci;
+        /* dQ/dm = (dkd/dm / pi + D vis (alb - 0.04)(1 - w5)) ci */
+        dm += g[k] * (dkd_dm / PI + D * vis * (alb[k] - 0.04) * (1.0 - w5)) * ci;
         sum_gF += g[k] * F;
         sum_gdiff += g[k] * kd / PI;
     }
@@ -1332,11 +1339,14 @@ static void sp_add(Sparse* sp, int buf, int64_t idx, double val)
     sp->n++;
 }
 
-static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], Sparse* sp)
+/* demod = 0: the sample's radiance. demod = 1: its demodulated lighting at the primary vertex
+ * (the same terms with the kind-2 lobes; an escaping primary ray has none) */
+static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], int demod, Sparse* sp)
 {
     const orc_scene* s = c->s;
-    const int kind = c->p->brdf_kind;
+    const int kind = demod ? 2 : c->p->brdf_kind;
     if (rec->prim_tri < 0) {
+        if (demod) return;
         for (int k = 0; k < 3; ++k) sp_add(sp, GB_ENV, 3 * (int64_t)rec->bg_texel + k, g[k]);
         return;
     }
@@ -1592,11 +1602,13 @@ static void detached_lin0(const Ctx* c, const orc_scene* ev, const Rec* rec, dou
 }
 
 /* detached evaluation of one sample's primary-vertex terms with the parameters of `ev` */
-static void sample_detached(const Ctx* c, const orc_scene* ev, const Rec* rec, double out[3])
+/* demod = 1: the demodulated lighting at the primary vertex instead (kind-2 lobes, L_ind
+ * detached in either grad mode, nothing for an escaping primary ray) */
+static void sample_detached(const Ctx* c, const orc_scene* ev, const Rec* rec, int demod, double out[3])
 {
-    const int kind = c->p->brdf_kind;
+    const int kind = demod ? 2 : c->p->brdf_kind;
     if (rec->prim_tri < 0) {
-        for (int k = 0; k < 3; ++k) out[k] = ev->env[3 * rec->bg_texel + k];
+        for (int k = 0; k < 3; ++k) out[k] = demod ? 0.0 : ev->env[3 * rec->bg_texel + k];
         return;
     }
     v3 o = vload(c->o);
@@ -1613,7 +1625,7 @@ static void sample_detached(const Ctx* c, const orc_scene* ev, const Rec* rec, d
     }
     if (rec->has_cont) {
         double fc[3], lin[3] = {rec->Lind[0], rec->Lind[1], rec->Lind[2]};
-        if (c->p->grad_mode == 1) detached_lin0(c, ev, rec, lin);
+        if (c->p->grad_mode == 1 && !demod) detached_lin0(c, ev, rec, lin);
         brdf_cos(sh.n, wo, rec->wc, sh.alb, sh.rgh, sh.met, kind, fc);
         for (int k = 0; k < 3; ++k) out[k] += fc[k] / rec->p_ind * lin[k];
     }
@@ -1623,7 +1635,9 @@ static void sample_detached(const Ctx* c, const orc_scene* ev, const Rec* rec, d
  * pixel loops, threaded over contiguous chunks of the pixel list
  * ------------------------------------------------------------------------------------- */
 typedef struct {
-    int mode; /* 0 render, 1 backward, 2 detached */
+    int mode;  /* 0 render, 1 backward, 2 detached */
+    int demod; /* 1: the demodulated lighting of the primary vertex (L_light) instead of the
+                * radiance; mode 0 then writes [c_d + c_s (3), fraction of samples that hit] */
     Ctx c;
     const orc_scene* ev;
     const int32_t* pixels;
@@ -1642,29 +1656,37 @@ static void* job_run(void* arg)
     for (int i = jb->i0; i < jb->i1; ++i) {
         int pix = jb->pixels ? jb->pixels[i] : i;
         int px = pix % W, py = pix / W;
-        double acc[3] = {0, 0, 0};
+        double acc[3] = {0, 0, 0}, hits = 0.0;
         Margin mg = {INFINITY, 0};
         Margin* pmg = (jb->mode == 0 && jb->out_margin && c->p->want_margin) ? &mg : NULL;
         for (int smp = 0; smp < spp; ++smp) {
             Rec rec;
             path_sample(c, px, py, smp, &rec, pmg, jb->cnt);
-            if (jb->mode == 0) {
+            if (jb->mode == 0 && jb->demod) {
+                double o3[3];
+                sample_detached(c, c->s, &rec, 1, o3);
+                for (int k = 0; k < 3; ++k) acc[k] += o3[k];
+                hits += rec.prim_tri >= 0 ? 1.0 : 0.0;
+            } else if (jb->mode == 0) {
                 for (int k = 0; k < 3; ++k) acc[k] += rec.rgb[k];
                 if (jb->out_prim) jb->out_prim[(size_t)i * spp + smp] = rec.prim_tri;
             } else if (jb->mode == 1) {
                 double g[3];
                 for (int k = 0; k < 3; ++k) g[k] = jb->d_rgb[3 * (size_t)i + k] / spp;
                 if (g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0) {
-                    sample_grad(c, &rec, g, &jb->sp);
+                    sample_grad(c, &rec, g, jb->demod, &jb->sp);
                     if (c->p->grad_mode == 1) sample_grad_secondary(c, &rec, g, &jb->sp);
                 }
             } else {
                 double o3[3];
-                sample_detached(c, jb->ev, &rec, o3);
+                sample_detached(c, jb->ev, &rec, jb->demod, o3);
                 for (int k = 0; k < 3; ++k) acc[k] += o3[k];
             }
         }
-        if (jb->mode != 1)
+        if (jb->mode == 0 && jb->demod) {
+            for (int k = 0; k < 3; ++k) jb->out_rgb[4 * (size_t)i + k] = acc[k] / spp;
+            jb->out_rgb[4 * (size_t)i + 3] = hits / spp;
+        } else if (jb->mode != 1)
             for (int k = 0; k < 3; ++k) jb->out_rgb[3 * (size_t)i + k] = acc[k] / spp;
         if (jb->mode == 0 && jb->out_margin) {
             jb->out_margin[2 * (size_t)i] = mg.m;
@@ -1674,10 +1696,11 @@ static void* job_run(void* arg)
     return NULL;
 }
 
-static int run_jobs(int mode, const orc_scene* s, const orc_scene* ev, const orc_view* v, const orc_params* p,
-                    const int32_t* pixels, int32_t n, double* out_rgb, double* out_margin, int32_t* out_prim,
-                    const double* d_rgb, const orc_grads* g, int64_t* counts)
+static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev, const orc_view* v,
+                    const orc_params* p, const int32_t* pixels, int32_t n, double* out_rgb, double* out_margin,
+                    int32_t* out_prim, const double* d_rgb, const orc_grads* g, int64_t* counts)
 {
+    if (demod && p && p->grad_mode != 0) return 1;
     if (!s || !v || !p || v->width < 1 || v->height < 1 || v->spp < 1 || v->bounces < 1 || p->ris_m < 0) return 1;
     if (p->grad_mode != 0 && (p->grad_mode != 1 || v->bounces > ORC_MAXB)) return 1;
     if (p->reuse_k < 0 || p->reuse_radius < 0 || (p->reuse_k > 0 && p->reuse_radius < 1)) return 1;
@@ -1692,6 +1715,7 @@ static int run_jobs(int mode, const orc_scene* s, const orc_scene* ev, const orc
     for (int t = 0; t < nt; ++t) {
         Job* jb = &jobs[t];
         jb->mode = mode;
+        jb->demod = demod;
         ctx_init(&jb->c, s, v, p);
         jb->ev = ev;
         jb->pixels = pixels;
@@ -1729,21 +1753,48 @@ int orc_render(const orc_scene* s, const orc_view* v, const orc_params* p, const
                double* out_rgb, double* out_margin, int32_t* out_prim_tri, int64_t* counts)
 {
     if (!out_rgb) return 1;
-    return run_jobs(0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, out_prim_tri, NULL, NULL, counts);
+    return run_jobs(0, 0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, out_prim_tri, NULL, NULL, counts);
 }
 
 int orc_backward(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels, int32_t n_pixels,
                  const double* d_rgb, const orc_grads* g, int64_t* counts)
 {
     if (!d_rgb || !g) return 1;
-    return run_jobs(1, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_rgb, g, counts);
+    return run_jobs(1, 0, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_rgb, g, counts);
 }
 
 int orc_render_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v, const orc_params* p,
                         const int32_t* pixels, int32_t n_pixels, double* out_rgb)
 {
     if (!eval || !out_rgb) return 1;
-    return run_jobs(2, frozen, eval, v, p, pixels, n_pixels, out_rgb, NULL, NULL, NULL, NULL, NULL);
+    return run_jobs(2, 0, frozen, eval, v, p, pixels, n_pixels, out_rgb, NULL, NULL, NULL, NULL, NULL);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * monochrome light regulariser (Appendix A, L_light): the demodulated diffuse and specular
+ * lighting c_d + c_s of each pixel's primary vertex, estimated from the same samples as the
+ * render (kind-2 lobes in place of the BRDF in the primary vertex's direct and continuation
+ * terms), and the adjoint of its PRIMARY-mode dependence on the parameters
+ * ------------------------------------------------------------------------------------- */
+int orc_light_demod(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
+                    int32_t n_pixels, double* out, double* out_margin, int64_t* counts)
+{
+    if (!out) return 1;
+    return run_jobs(0, 1, s, NULL, v, p, pixels, n_pixels, out, out_margin, NULL, NULL, NULL, counts);
+}
+
+int orc_light_backward(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
+                       int32_t n_pixels, const double* d_c, const orc_grads* g, int64_t* counts)
+{
+    if (!d_c || !g) return 1;
+    return run_jobs(1, 1, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_c, g, counts);
+}
+
+int orc_light_demod_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v,
+                             const orc_params* p, const int32_t* pixels, int32_t n_pixels, double* out)
+{
+    if (!eval || !out) return 1;
+    return run_jobs(2, 1, frozen, eval, v, p, pixels, n_pixels, out, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ---------------------------------------------------------------------------------------

@@ -47,7 +47,8 @@ typedef struct {
 typedef struct {
     int32_t ris_m;       /* RIS candidates per shading point */
     uint32_t seed_lo, seed_hi;
-    int32_t brdf_kind;   /* 0 = GGX + Lambert (the method); 1 = Lambert only (furnace pin) */
+    int32_t brdf_kind;   /* 0 = GGX + Lambert (the method); 1 = Lambert only (furnace pin);
+                          * 2 (orc_brdf_cos only) = the demodulated lobes of L_light */
     int32_t threads;     /* worker threads (>= 1) */
     int32_t want_margin; /* 1: track decision margins */
     int32_t grad_mode;   /* 0 = PRIMARY (the paper's); 1 = FULL (every vertex, at most ORC_MAXB) */
@@ -113,6 +114,23 @@ int orc_backward(const orc_scene* s, const orc_view* v, const orc_params* p,
 int orc_render_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v,
                         const orc_params* p, const int32_t* pixels, int32_t n_pixels,
                         double* out_rgb);
+
+/* Monochrome light regulariser (Appendix A, L_light), PRIMARY mode only (grad_mode 0).
+ * orc_light_demod: per pixel, out[4] = the mean over its samples of the demodulated lighting
+ * c_d + c_s at the primary vertex (the direct and continuation terms of the render's primary
+ * vertex with the BRDF replaced by the kind-2 lobes: 1 / pi for the diffuse lobe, the GGX
+ * lobe unchanged; RIS weight, visibility, directions, p_ind and L_ind as the render drew them;
+ * 0 for an escaping primary ray), then the fraction of its samples whose primary ray hit.
+ * out_margin as orc_render's. orc_light_backward: the adjoint of the per-pixel mean c for the
+ * upstream gradient d_c [n][3] (the same scatters as orc_backward, no env term for escaping
+ * rays). orc_light_demod_detached: c re-evaluated with the parameters of `eval`, everything
+ * else from `frozen` ([n][3]); its derivative at eval == frozen is orc_light_backward's. */
+int orc_light_demod(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
+                    int32_t n_pixels, double* out, double* out_margin, int64_t* counts);
+int orc_light_backward(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
+                       int32_t n_pixels, const double* d_c, const orc_grads* g, int64_t* counts);
+int orc_light_demod_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v,
+                             const orc_params* p, const int32_t* pixels, int32_t n_pixels, double* out);
 
 /* Ray queries against the oracle's own BVH (mode 0 closest, 1 any) or brute force (2, 3).
  * rays [n][6] = origin, direction; skip_tri [n] (-1 none); out_tri [n]; out_tuv [n][3];

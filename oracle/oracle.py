@@ -80,6 +80,10 @@ def lib():
             L.orc_render.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp, vp]
             L.orc_backward.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, C.POINTER(Grads), vp]
             L.orc_render_detached.argtypes = [vp, vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp]
+            L.orc_light_demod.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp]
+            L.orc_light_backward.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, C.POINTER(Grads),
+                                             vp]
+            L.orc_light_demod_detached.argtypes = [vp, vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp]
             L.orc_trace.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp]
             L.orc_lbvh.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp]
             L.orc_env_tables.restype = dbl
@@ -249,6 +253,64 @@ def render_detached(frozen, evaled, view, index, ris_m, seed=0, pixels=None, thr
     if rc:
         raise ValueError("orc_render_detached rejected its arguments")
     return rgb
+
+
+def _grad_out(s, want_abs):
+    out = dict(albedo=np.zeros(s.albedo.shape), roughness=np.zeros(s.roughness.shape),
+               metallic=np.zeros(s.metallic.shape), env=np.zeros(s.env.shape), verts=np.zeros(s.verts.shape))
+    if want_abs:
+        for k in list(out):
+            out[k + "_abs"] = np.zeros(out[k].shape)
+        for k in ("albedo", "roughness", "metallic"):
+            out[k + "_sens"] = np.zeros(out[k].shape)
+    return out
+
+
+def light_demod(osc, view, index, ris_m, seed=0, pixels=None, threads=None, margins=True, reuse=(0, 0)):
+    """Demodulated lighting of the monochrome light regulariser (Appendix A, L_light) per
+    pixel: dict(c [n,3] = mean over samples of c_d + c_s at the primary vertex, cov [n] =
+    fraction of samples that hit a surface, margin [n] as render's)."""
+    L = lib()
+    n = view.width * view.height if pixels is None else len(pixels)
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
+    out = np.zeros((n, 4))
+    mg = np.zeros((n, 2)) if margins else None
+    cnt = np.zeros(8, dtype=np.int64)
+    v = make_view(view, index)
+    p = make_params(ris_m, seed, threads, 0, int(margins), reuse=reuse)
+    if L.orc_light_demod(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(out), _p(mg), _p(cnt)):
+        raise ValueError("orc_light_demod rejected its arguments")
+    return dict(c=out[:, :3].copy(), cov=out[:, 3].copy(), margin=None if mg is None else mg[:, 0], counts=cnt)
+
+
+def light_backward(osc, view, index, ris_m, d_c, seed=0, pixels=None, threads=None, want_abs=True, reuse=(0, 0)):
+    """Adjoint of light_demod's c for the upstream gradient d_c [n,3]; dict of FP64 gradients."""
+    L = lib()
+    n = view.width * view.height if pixels is None else len(pixels)
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
+    d = _f64(d_c).reshape(n, 3)
+    out = _grad_out(osc.scene, want_abs)
+    g = Grads(*[_p(out.get(k)) for k in GRAD_FIELDS])
+    cnt = np.zeros(8, dtype=np.int64)
+    v = make_view(view, index)
+    p = make_params(ris_m, seed, threads, 0, 0, 0, reuse)
+    if L.orc_light_backward(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(d), C.byref(g), _p(cnt)):
+        raise ValueError("orc_light_backward rejected its arguments")
+    out["counts"] = cnt
+    return out
+
+
+def light_demod_detached(frozen, evaled, view, index, ris_m, seed=0, pixels=None, threads=None, reuse=(0, 0)):
+    """light_demod's c re-evaluated with `evaled`'s parameters, every sampled quantity from `frozen`."""
+    L = lib()
+    n = view.width * view.height if pixels is None else len(pixels)
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
+    out = np.zeros((n, 3))
+    v = make_view(view, index)
+    p = make_params(ris_m, seed, threads, 0, 0, 0, reuse)
+    if L.orc_light_demod_detached(frozen.h, evaled.h, C.byref(v), C.byref(p), _p(pix), n, _p(out)):
+        raise ValueError("orc_light_demod_detached rejected its arguments")
+    return out
 
 
 def trace(osc, origins, dirs, mode=0, skip=None, margins=False):
