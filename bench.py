@@ -550,6 +550,35 @@ def main():
         regs["material_smoothness"] = {"ms_per_step": ms_lk, "pixels": pix, "mpix_per_s": pix / (ms_lk / 1e3) / 1e6,
                                        "sigma": 0.01, "kernel": "k_lk_hits + k_lk_apply"}
         rests = rg = lk_ga = lk_gr = None
+        # monochrome light regulariser L_light over every view, from the tape of the last render:
+        # the demodulated lighting per pixel (the primary vertex replayed for each sample), the
+        # loss against the reference images and its seed, and the adjoint (replayed again)
+        lp = gw.params(1)
+        ll_c = [torch.empty((v.height, v.width, 4), device=dev) for v in gw.views]
+        ll_d = [torch.empty((v.height, v.width, 3), device=dev) for v in gw.views]
+        ll_l = torch.zeros(1, device=dev)
+        ll_g = gw.zero_grads()
+
+        def light_pass():
+            M.mirres_light_demod(gw.ctx, scenes, gw.views, lp, tape, ll_c)
+            M.mirres_light_loss(gw.ctx, gw.views, ll_c, refs, 0.1, ll_l, ll_d)
+            M.mirres_light_backward(gw.ctx, scenes, gw.views, lp, ll_d, tape, ll_g)
+
+        for _ in range(max(args.warmup, 3)):
+            light_pass()
+        torch.cuda.synchronize()
+        e_ll = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e_ll[0].record()
+        for _ in range(args.steps):
+            light_pass()
+        e_ll[1].record()
+        torch.cuda.synchronize()
+        ms_ll = e_ll[0].elapsed_time(e_ll[1]) / args.steps
+        regs["light"] = {"ms_per_step": ms_ll, "pixels": pix, "samples": samples,
+                         "mpix_per_s": pix / (ms_ll / 1e3) / 1e6,
+                         "msamples_per_s": samples / (ms_ll / 1e3) / 1e6, "weight": 0.1,
+                         "kernel": "k_light_demod + k_light_count + k_light_apply + k_backward<DEMOD>"}
+        ll_c = ll_d = ll_g = None
 
     # FULL-mode adjoint (gradients through every vertex): the same step with grad_mode 1
     full = None

@@ -443,6 +443,44 @@ mirres_status mirres_material_smoothness(mirres_context* ctx, const mirres_scene
                                          int32_t view_index, const mirres_lk_params* params, float* loss,
                                          float* grad_albedo, float* grad_roughness, void* stream);
 
+/* Monochrome light regulariser (Appendix A, "Training details", after NVdiffrec-MC):
+ *   L_light = | Y(c_d + c_s) - V(I_ref) |,  Y = (r + g + b) / 3,  V = max(r, g, b)
+ * with c_d, c_s the demodulated diffuse and specular lighting. Readings: both are taken at each
+ * pixel's primary vertex from the samples of the render that wrote `tape`: the primary
+ * vertex's direct term V W L_env(y) Q(y) plus its continuation term Q(wc) L_ind / p_ind, with
+ * the BRDF-times-cosine replaced by Q = (1 / pi + the GGX lobe) max(0, n.wi) -- the diffuse
+ * lobe's reflectance (1 - metallic) albedo divided out, the specular lobe (whose Schlick F0
+ * mixes albedo and metallic inside F, not as a factor) unchanged -- averaged over the pixel's
+ * samples; an escaping primary ray contributes nothing. The loss is the mean over P, the pixels
+ * of all the call's views with at least one sample on a surface, and the gradient takes
+ * sign(0) = 0. Three calls:
+ *
+ * mirres_light_demod: demod[v] device [height][width][4] (16-byte aligned), overwritten with
+ *   (c_d + c_s (3 channels), fraction of the pixel's samples whose primary ray hit). scenes,
+ *   views, params and tape are those of the render (any launch; any grad_mode, whose tape
+ *   size is checked); one thread per pixel, samples summed in order.
+ * mirres_light_loss: loss[0] += weight L_light (device float, FP32 sums in no fixed order;
+ *   may be NULL) and, if d_demod is not NULL, d_demod[v] device [height][width][3] overwritten
+ *   with d(weight L_light) / d(c_d + c_s) = weight sign(Y - V) / (3 |P|) per channel (0 outside
+ *   P). ref_images[v] device [height][width][3]; weight >= 0. |P| = 0 adds nothing.
+ * mirres_light_backward: the PRIMARY-mode adjoint of c_d + c_s (RIS weight, visibility,
+ *   directions, p_ind and L_ind held fixed, as in mirres_backward) for the upstream gradient
+ *   d_demod[v] [height][width][3]: accumulated into the albedo (through F0 only), roughness,
+ *   metallic and env texels and the primary triangle's vertices (and, with interpolated
+ *   normals, the vertices around them), like mirres_backward; no env term for escaping rays.
+ * All asynchronous on `stream` and use the context workspace. MIRRES_ERR_ARG for NULL or
+ * misaligned buffers, a short tape or bad views; MIRRES_ERR_STATE for an unbuilt scene. */
+mirres_status mirres_light_demod(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                 const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                 const void* tape, size_t tape_bytes, float* const* demod, void* stream);
+mirres_status mirres_light_loss(mirres_context* ctx, const mirres_view* views, int32_t n_views,
+                                const float* const* demod, const float* const* ref_images, float weight,
+                                float* loss, float* const* d_demod, void* stream);
+mirres_status mirres_light_backward(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                    const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                    const float* const* d_demod, const void* tape, size_t tape_bytes,
+                                    const mirres_grads* grads, void* stream);
+
 /* Cumulative counters since the context was created (synchronises the context's last
  * stream): [0] primary rays, [1] continuation rays, [2] shadow rays, [3] samples rendered,
  * [4] samples differentiated, [5] RIS candidates, [6] kernel launches, [7] error flag. */

@@ -796,10 +796,12 @@ extern "C" mirres_status mirres_stage_times(mirres_context* ctx, double out_ms[4
 }
 
 // ---- adjoint ---------------------------------------------------------------------------------
-extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
-                                         const mirres_view* views, int32_t n_views, const mirres_params* params,
-                                         const float* const* d_images, const void* tape, size_t tape_bytes,
-                                         const mirres_grads* grads, void* stream)
+// demod = false: mirres_backward; true: mirres_light_backward (the demodulated lighting of the
+// primary vertex, PRIMARY mode whatever params->grad_mode says)
+static mirres_status backward_impl(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                   const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                   const float* const* d_images, const void* tape, size_t tape_bytes,
+                                   const mirres_grads* grads, void* stream, bool demod)
 {
     if (!ctx) return arg_error("ctx is NULL");
     MR_TRY(check_params(params));
@@ -813,9 +815,10 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
         if (!d_images[i]) return arg_error("d_images[" + std::to_string(i) + "] is NULL");
     if (!tape) return arg_error("mirres_backward needs the tape written by mirres_render");
     MR_TRY(check_full(params, views, n_views));
-    const int nvx = full_vertices(views, n_views, params->grad_mode);
-    if (tape_bytes < tape_bytes_per_sample(nvx) * total)
+    const int tape_nvx = full_vertices(views, n_views, params->grad_mode);
+    if (tape_bytes < tape_bytes_per_sample(tape_nvx) * total)
         return arg_error("tape_bytes is smaller than mirres_tape_bytes_mode(views, grad_mode)");
+    const int nvx = demod ? 0 : tape_nvx;
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
     ctx->last_stream = st;
@@ -845,8 +848,12 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
             MR_CUDA(cudaMemsetAsync(scenes[i]->gvn, 0, sizeof(float) * 3 * (size_t)scenes[i]->desc.n_verts, st));
     bool interp = false;
     for (int i = 0; i < n_scenes; ++i) interp = interp || scenes[i]->normals != 0;
-    mr_launch_backward(d_scenes, d_views, n_views, total, make_rng(params), d_dimg, d_grads, tape, ctx->counters,
-                       ctx->sm_count, st, nvx, full_scratch, interp);
+    if (demod)
+        mr_launch_light_backward(d_scenes, d_views, n_views, total, make_rng(params), d_dimg, d_grads, tape,
+                                 ctx->counters, ctx->sm_count, st, interp);
+    else
+        mr_launch_backward(d_scenes, d_views, n_views, total, make_rng(params), d_dimg, d_grads, tape, ctx->counters,
+                           ctx->sm_count, st, nvx, full_scratch, interp);
     // interpolated normals: d loss / d vertex normal to the vertices of the incident faces
     for (int i = 0; i < n_scenes; ++i)
         if (scenes[i]->normals && grads[i].verts && scenes[i]->gvn) {
@@ -858,6 +865,130 @@ extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* cons
     ctx->host_launches += 1 + (unsigned long long)normals_passes +
                           ((nvx > 0 && full_chunk) ? 4 * ((total + full_chunk - 1) / full_chunk) : 0);
     return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_backward(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                         const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                         const float* const* d_images, const void* tape, size_t tape_bytes,
+                                         const mirres_grads* grads, void* stream)
+{
+    return backward_impl(ctx, scenes, n_scenes, views, n_views, params, d_images, tape, tape_bytes, grads, stream,
+                         false);
+}
+
+// ---- monochrome light regulariser (Appendix A, L_light) --------------------------------------
+static std::vector<uint64_t> pixel_offsets(const std::vector<ViewDev>& vdev, uint64_t& total_pix)
+{
+    std::vector<uint64_t> off(vdev.size());
+    total_pix = 0;
+    for (size_t i = 0; i < vdev.size(); ++i) {
+        off[i] = total_pix;
+        total_pix += (uint64_t)vdev[i].width * (uint64_t)vdev[i].height;
+    }
+    return off;
+}
+
+extern "C" mirres_status mirres_light_demod(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                            const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                            const void* tape, size_t tape_bytes, float* const* demod, void* stream)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    MR_TRY(check_params(params));
+    std::vector<SceneDev> sdev;
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev));
+    std::vector<ViewDev> vdev;
+    uint64_t total = 0, max_view = 0;
+    MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
+    if (!demod) return arg_error("demod must not be NULL");
+    for (int i = 0; i < n_views; ++i) {
+        if (!demod[i]) return arg_error("demod[" + std::to_string(i) + "] is NULL");
+        if (reinterpret_cast<uintptr_t>(demod[i]) % 16) return arg_error("demod[" + std::to_string(i) + "] is not 16-byte aligned");
+    }
+    if (!tape) return arg_error("mirres_light_demod needs the tape written by mirres_render");
+    MR_TRY(check_full(params, views, n_views));
+    if (tape_bytes < tape_bytes_per_sample(full_vertices(views, n_views, params->grad_mode)) * total)
+        return arg_error("tape_bytes is smaller than mirres_tape_bytes_mode(views, grad_mode)");
+    uint64_t total_pix = 0;
+    const std::vector<uint64_t> pix_off = pixel_offsets(vdev, total_pix);
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    ctx->last_stream = st;
+    Carver plan(nullptr);
+    plan.take<ViewDev>((size_t)n_views);
+    plan.take<SceneDev>((size_t)n_scenes);
+    plan.take<uint64_t>((size_t)n_views);
+    plan.take<float*>((size_t)n_views);
+    MR_TRY(ws_reserve(ctx, plan.off));
+    Carver cv(ctx->ws.ptr);
+    ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
+    SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
+    uint64_t* d_pixoff = cv.take<uint64_t>((size_t)n_views);
+    float** d_out = cv.take<float*>((size_t)n_views);
+    MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_pixoff, pix_off.data(), sizeof(uint64_t) * pix_off.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_out, demod, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
+    bool interp = false;
+    for (int i = 0; i < n_scenes; ++i) interp = interp || scenes[i]->normals != 0;
+    mr_launch_light_demod(d_scenes, d_views, d_pixoff, n_views, total_pix, total, make_rng(params), tape, d_out,
+                          ctx->sm_count, st, interp);
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += 1;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_light_loss(mirres_context* ctx, const mirres_view* views, int32_t n_views,
+                                           const float* const* demod, const float* const* ref_images, float weight,
+                                           float* loss, float* const* d_demod, void* stream)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    std::vector<ViewDev> vdev;
+    uint64_t total = 0, max_view = 0;
+    MR_TRY(check_views(views, n_views, 0x7FFFFFFF, vdev, total, max_view));
+    if (!demod || !ref_images) return arg_error("demod and ref_images must not be NULL");
+    if (!(weight >= 0.0f)) return arg_error("weight must be >= 0");
+    for (int i = 0; i < n_views; ++i) {
+        if (!demod[i] || !ref_images[i]) return arg_error("view " + std::to_string(i) + ": NULL demod or reference");
+        if (reinterpret_cast<uintptr_t>(demod[i]) % 16) return arg_error("demod[" + std::to_string(i) + "] is not 16-byte aligned");
+        if (d_demod && !d_demod[i]) return arg_error("d_demod[" + std::to_string(i) + "] is NULL");
+    }
+    uint64_t total_pix = 0;
+    const std::vector<uint64_t> pix_off = pixel_offsets(vdev, total_pix);
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    ctx->last_stream = st;
+    Carver plan(nullptr);
+    plan.take<uint64_t>((size_t)n_views);
+    plan.take<const float*>((size_t)n_views);
+    plan.take<const float*>((size_t)n_views);
+    plan.take<float*>((size_t)n_views);
+    plan.take<unsigned int>(1);
+    MR_TRY(ws_reserve(ctx, plan.off));
+    Carver cv(ctx->ws.ptr);
+    uint64_t* d_pixoff = cv.take<uint64_t>((size_t)n_views);
+    const float** d_c = cv.take<const float*>((size_t)n_views);
+    const float** d_ref = cv.take<const float*>((size_t)n_views);
+    float** d_dc = cv.take<float*>((size_t)n_views);
+    unsigned int* d_count = cv.take<unsigned int>(1);
+    MR_CUDA(cudaMemcpyAsync(d_pixoff, pix_off.data(), sizeof(uint64_t) * pix_off.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_c, demod, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_ref, ref_images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
+    if (d_demod) MR_CUDA(cudaMemcpyAsync(d_dc, d_demod, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
+    mr_launch_light_loss(d_pixoff, n_views, total_pix, d_c, d_ref, weight, d_count, loss, d_demod ? d_dc : nullptr,
+                         ctx->sm_count, st);
+    MR_CUDA(cudaGetLastError());
+    ctx->host_launches += 2;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_light_backward(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                               const mirres_view* views, int32_t n_views,
+                                               const mirres_params* params, const float* const* d_demod,
+                                               const void* tape, size_t tape_bytes, const mirres_grads* grads,
+                                               void* stream)
+{
+    return backward_impl(ctx, scenes, n_scenes, views, n_views, params, d_demod, tape, tape_bytes, grads, stream,
+                         true);
 }
 
 extern "C" mirres_status mirres_l2_loss(const float* image, const float* ref, int64_t n, float* d_image,

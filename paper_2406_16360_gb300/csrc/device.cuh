@@ -292,7 +292,10 @@ struct Material {
     float rough, metal;
 };
 
-// f_r(wo, wi) * max(0, n.wi), zero outside both upper hemispheres
+// f_r(wo, wi) * max(0, n.wi), zero outside both upper hemispheres. DEMOD: the demodulated
+// lobes of the monochrome light regulariser (Appendix A, L_light): the diffuse lobe's
+// reflectance (1 - metallic) albedo divided out (1 / pi), the GGX lobe unchanged
+template <bool DEMOD = false>
 __device__ __forceinline__ float3 brdf_cos(float3 n, float3 wo, float3 wi, const Material& m)
 {
     const float co = dot(n, wo), ci = dot(n, wi);
@@ -308,15 +311,18 @@ __device__ __forceinline__ float3 brdf_cos(float3 n, float3 wo, float3 wi, const
     const float dv = D * vis;
     float3 out;
     {
-        const float kd = (1.0f - m.metal) * m.alb.x, f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.x;
+        const float kd = DEMOD ? 1.0f : (1.0f - m.metal) * m.alb.x;
+        const float f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.x;
         out.x = (kd * MR_INV_PI + dv * (f0 + (1.0f - f0) * w5)) * ci;
     }
     {
-        const float kd = (1.0f - m.metal) * m.alb.y, f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.y;
+        const float kd = DEMOD ? 1.0f : (1.0f - m.metal) * m.alb.y;
+        const float f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.y;
         out.y = (kd * MR_INV_PI + dv * (f0 + (1.0f - f0) * w5)) * ci;
     }
     {
-        const float kd = (1.0f - m.metal) * m.alb.z, f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.z;
+        const float kd = DEMOD ? 1.0f : (1.0f - m.metal) * m.alb.z;
+        const float f0 = 0.04f * (1.0f - m.metal) + m.metal * m.alb.z;
         out.z = (kd * MR_INV_PI + dv * (f0 + (1.0f - f0) * w5)) * ci;
     }
     return out;

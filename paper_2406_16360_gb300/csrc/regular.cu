@@ -236,6 +236,74 @@ __global__ void __launch_bounds__(256) k_lk_apply(SceneDev s, const float4* __re
     if (loss) flush_loss(loss, acc);
 }
 
+// ---------------------------------------------------------------------------------------
+// monochrome light regulariser (Appendix A, L_light): mean over the covered pixels of
+// |Y(c_d + c_s) - V(I_ref)|, Y = channel mean, V = channel maximum; sign(0) = 0
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int view_of_pixel(const uint64_t* __restrict__ pix_off, int n_views, uint64_t q)
+{
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pix_off[mid] <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// |P|: pixels whose demodulated lighting has coverage > 0
+__global__ void __launch_bounds__(256) k_light_count(const uint64_t* __restrict__ pix_off, int n_views,
+                                                     uint64_t total_pixels, const float* const* __restrict__ demod,
+                                                     unsigned int* count)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < total_pixels; base += stride) {
+        const uint64_t q = base + threadIdx.x;
+        bool in = false;
+        if (q < total_pixels) {
+            const int vi = view_of_pixel(pix_off, n_views, q);
+            in = demod[vi][4 * (q - pix_off[vi]) + 3] > 0.0f;
+        }
+        const unsigned b = __ballot_sync(MR_FULL, in);
+        if (lane_id() == 0 && b) atomicAdd(count, (unsigned)__popc(b));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_light_apply(const uint64_t* __restrict__ pix_off, int n_views,
+                                                     uint64_t total_pixels, const float* const* __restrict__ demod,
+                                                     const float* const* __restrict__ ref, float w,
+                                                     const unsigned int* __restrict__ count, float* loss,
+                                                     float* const* __restrict__ d_demod)
+{
+    const unsigned int n = *count;
+    const float inv = n ? 1.0f / (float)n : 0.0f;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    float acc = 0.0f;
+    // uniform trip count per warp (the loss reduction uses every lane)
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < total_pixels; base += stride) {
+        const uint64_t q = base + threadIdx.x;
+        if (q < total_pixels) {
+            const int vi = view_of_pixel(pix_off, n_views, q);
+            const uint64_t p = q - pix_off[vi];
+            const float4 c = __ldg(reinterpret_cast<const float4*>(demod[vi]) + p);
+            float g = 0.0f;
+            if (c.w > 0.0f && n) {
+                const float* r = ref[vi] + 3 * p;
+                const float diff = (c.x + c.y + c.z) * (1.0f / 3.0f) - fmaxf(fmaxf(__ldg(r), __ldg(r + 1)), __ldg(r + 2));
+                acc += fabsf(diff);
+                g = w * inv * (1.0f / 3.0f) * sgn(diff);
+            }
+            if (d_demod) {
+                float* d = d_demod[vi] + 3 * p;
+                d[0] = g;
+                d[1] = g;
+                d[2] = g;
+            }
+        }
+    }
+    if (loss) flush_loss(loss, acc * w * inv);
+}
+
 unsigned grid_of(int64_t n, int sms)
 {
     const int64_t g = (n + 255) / 256;
@@ -308,4 +376,15 @@ void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_sm
                                                                loss, grad);
     if (w_offset != 0.0f && V > 0)
         k_offset<<<grid_of(V, sms), 256, 0, st>>>(s->desc.verts, rest, V, w_offset, loss, grad);
+}
+
+void mr_launch_light_loss(const uint64_t* pix_off, int n_views, uint64_t total_pixels, const float* const* demod,
+                          const float* const* ref, float w, unsigned int* count, float* loss, float* const* d_demod,
+                          int sms, cudaStream_t st)
+{
+    cudaMemsetAsync(count, 0, sizeof(unsigned int), st);
+    if (total_pixels == 0) return;
+    k_light_count<<<grid_of((int64_t)total_pixels, sms), 256, 0, st>>>(pix_off, n_views, total_pixels, demod, count);
+    k_light_apply<<<grid_of((int64_t)total_pixels, sms), 256, 0, st>>>(pix_off, n_views, total_pixels, demod, ref, w,
+                                                                       count, loss, d_demod);
 }

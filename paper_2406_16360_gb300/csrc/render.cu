@@ -416,7 +416,9 @@ __global__ void __launch_bounds__(256) k_resolve_all(const ViewDev* __restrict__
 // adjoint (PRIMARY mode): replay of the primary vertex from the tape and the random stream
 // ---------------------------------------------------------------------------------------
 // reverse-mode derivative of Q = f_r(wo, wi) max(0, n.wi) (per channel) for the upstream
-// gradient gq: gm = (d/d albedo[3], d/d roughness, d/d metallic, d/d n[3])
+// gradient gq: gm = (d/d albedo[3], d/d roughness, d/d metallic, d/d n[3]). DEMOD: of the
+// demodulated lobes (diffuse reflectance 1: no albedo or metallic term through it)
+template <bool DEMOD = false>
 __device__ __forceinline__ void brdf_cos_adjoint(float3 n, float3 wo, float3 wi, const Material& m, float3 gq,
                                                  float gm[8])
 {
@@ -438,11 +440,11 @@ __device__ __forceinline__ void brdf_cos_adjoint(float3 n, float3 wo, float3 wi,
     float S = 0.0f, g_ci = 0.0f, g_m = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float kd = (1.0f - m.metal) * alb[c];
+        const float kd = DEMOD ? 1.0f : (1.0f - m.metal) * alb[c];
         const float f0 = 0.04f * (1.0f - m.metal) + m.metal * alb[c];
         const float F = f0 * (1.0f - w5) + w5;
         const float gF = g[c] * D * vis * ci;
-        const float gkd = g[c] * ci * MR_INV_PI;
+        const float gkd = DEMOD ? 0.0f : g[c] * ci * MR_INV_PI;
         gm[c] += gkd * (1.0f - m.metal) + gF * (1.0f - w5) * m.metal;
         g_m += -gkd * alb[c] + gF * (1.0f - w5) * (alb[c] - 0.04f);
         S += g[c] * F;
@@ -682,15 +684,18 @@ __device__ __forceinline__ void full_backward(const SceneDev& s, const Rng& rng,
 
 // Adjoint of every sample. PRIMARY mode (FULL = false): the primary vertex, replayed from the
 // tape. FULL mode: in addition the vertices b >= 1 from their tape records (see
-// full_vertices below). All 32 lanes of a warp run the same number of rounds, so the
-// warp-collective scatters see every lane.
-template <bool FULL, int MINB, bool INTERP>
+// full_vertices below). DEMOD (PRIMARY only): of the demodulated lighting of the monochrome
+// light regulariser instead of the radiance -- the same primary-vertex terms with the
+// demodulated lobes, and nothing for an escaping primary ray. All 32 lanes of a warp run the
+// same number of rounds, so the warp-collective scatters see every lane.
+template <bool FULL, int MINB, bool INTERP, bool DEMOD = false>
 __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restrict__ scenes,
                                                         const ViewDev* __restrict__ views, int n_views, uint64_t total,
                                                         Rng rng, const float* const* __restrict__ d_images,
                                                         const GradDev* __restrict__ grads, const void* tape, int nvx,
                                                         unsigned long long* counters)
 {
+    static_assert(!(FULL && DEMOD), "the demodulated lighting is differentiated in PRIMARY mode only");
     const TapeDev tp = tape_of(const_cast<void*>(tape), total, nvx);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t rounds = (total + stride - 1) / stride;
@@ -729,10 +734,12 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
                 const float3 d = camera_dir(v, px, py, u24(xc.x), u24(xc.y));
                 const int tri = tp.tri[g];
                 if (tri < 0) {
-                    env_key = env_texel_of(s, d);
-                    env_v[0] = gI.x;
-                    env_v[1] = gI.y;
-                    env_v[2] = gI.z;
+                    if (!DEMOD) {
+                        env_key = env_texel_of(s, d);
+                        env_v[0] = gI.x;
+                        env_v[1] = gI.y;
+                        env_v[2] = gI.z;
+                    }
                 } else {
                     float3 v0, e1, e2;
                     int tchk;
@@ -749,13 +756,14 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
                         // the selected candidate's direction and texel, as the forward drew them
                         const float3 y = f3(tp.y[0][g], tp.y[1][g], tp.y[2][g]);
                         const int ytex = tp.ytex[g];
-                        const float3 fc = brdf_cos(sh.n, wo, y, sh.m);
+                        const float3 fc = brdf_cos<DEMOD>(sh.n, wo, y, sh.m);
                         const float4 L = __ldg(s.env_texel + ytex);
                         env_key = ytex;
                         env_v[0] = gI.x * wv * fc.x;
                         env_v[1] = gI.y * wv * fc.y;
                         env_v[2] = gI.z * wv * fc.z;
-                        brdf_cos_adjoint(sh.n, wo, y, sh.m, f3(gI.x * wv * L.x, gI.y * wv * L.y, gI.z * wv * L.z), gm);
+                        brdf_cos_adjoint<DEMOD>(sh.n, wo, y, sh.m, f3(gI.x * wv * L.x, gI.y * wv * L.y, gI.z * wv * L.z),
+                                                gm);
                     }
                     const float3 li = f3(tp.lind[0][g], tp.lind[1][g], tp.lind[2][g]);
                     if (v.bounces > 1 && (li.x != 0.0f || li.y != 0.0f || li.z != 0.0f)) {
@@ -773,8 +781,9 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
                                               f3(fc0.x / pind, fc0.y / pind, fc0.z / pind), wc, vbeta, vdir, vfcp);
                         }
                         if (pind > 0.0f)
-                            brdf_cos_adjoint(sh.n, wo, wc, sh.m,
-                                             f3(gI.x * li.x / pind, gI.y * li.y / pind, gI.z * li.z / pind), gm);
+                            brdf_cos_adjoint<DEMOD>(sh.n, wo, wc, sh.m,
+                                                    f3(gI.x * li.x / pind, gI.y * li.y / pind, gI.z * li.z / pind),
+                                                    gm);
                     }
                     // textures (bilinear) and the texture coordinate
                     const Taps& tpz = sh.tp;
@@ -887,8 +896,73 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
                           same_scene == MR_FULL);
         }
     }
+    if (DEMOD) return;  // counters[4] counts the samples of mirres_backward
     for (int off = 16; off > 0; off >>= 1) n_diff += __shfl_xor_sync(MR_FULL, n_diff, off);
     if (lane_id() == 0 && n_diff) atomicAdd(counters + 4, n_diff);
+}
+
+// ---------------------------------------------------------------------------------------
+// Monochrome light regulariser (Appendix A, L_light): the demodulated diffuse + specular
+// lighting at each pixel's primary vertex, from the tape of the render. One thread per pixel
+// (flattened over the views: pix_off[i] is view i's first pixel, views[i].offset its first
+// sample) sums its samples in order: out[view][pixel] = (mean c_d + c_s, fraction of samples
+// whose primary ray hit). The primary vertex is replayed as the adjoint does.
+// ---------------------------------------------------------------------------------------
+template <bool INTERP>
+__global__ void __launch_bounds__(256) k_light_demod(const SceneDev* __restrict__ scenes,
+                                                     const ViewDev* __restrict__ views,
+                                                     const uint64_t* __restrict__ pix_off, int n_views,
+                                                     uint64_t total_pixels, uint64_t total, Rng rng,
+                                                     const void* tape, float* const* __restrict__ out)
+{
+    const TapeDev tp = tape_of(const_cast<void*>(tape), total, 0);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < total_pixels; p += stride) {
+        int vi = 0, hi = n_views - 1;
+        while (vi < hi) {
+            const int mid = (vi + hi + 1) >> 1;
+            if (pix_off[mid] <= p) vi = mid;
+            else hi = mid - 1;
+        }
+        const ViewDev& v = views[vi];
+        const SceneDev s = scenes[v.scene];
+        const uint32_t pixel = (uint32_t)(p - pix_off[vi]);
+        const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+        const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+        float3 acc = f3(0.f, 0.f, 0.f);
+        int hits = 0;
+        for (int smp = 0; smp < v.spp; ++smp) {
+            const uint64_t g = v.offset + (uint64_t)pixel * (uint64_t)v.spp + (uint64_t)smp;
+            const int tri = tp.tri[g];
+            if (tri < 0) continue;
+            ++hits;
+            const uint4 xc = rng.draw(pixel, (uint32_t)smp, (uint32_t)v.index, 0u, PURPOSE_CAMERA, 0u);
+            const float3 d = camera_dir(v, px, py, u24(xc.x), u24(xc.y));
+            float3 v0, e1, e2;
+            int tchk;
+            load_tri(s, __ldg(s.leaf_of + tri), v0, e1, e2, tchk);
+            float t, u, vv;
+            tri_solve(o, d, v0, e1, e2, t, u, vv);
+            Shade sh;
+            shade_at<INTERP>(s, tri, u, vv, d, sh);
+            const float3 wo = f3(-d.x, -d.y, -d.z);
+            const float wv = tp.wv[g];
+            if (tp.cand[g] >= 0 && wv != 0.0f) {
+                const float3 fc = brdf_cos<true>(sh.n, wo, f3(tp.y[0][g], tp.y[1][g], tp.y[2][g]), sh.m);
+                const float4 L = __ldg(s.env_texel + tp.ytex[g]);
+                acc = add(acc, f3(wv * L.x * fc.x, wv * L.y * fc.y, wv * L.z * fc.z));
+            }
+            const float3 li = f3(tp.lind[0][g], tp.lind[1][g], tp.lind[2][g]);
+            const float pind = tp.pind[g];
+            if (v.bounces > 1 && (li.x != 0.0f || li.y != 0.0f || li.z != 0.0f) && pind > 0.0f) {
+                const float3 fc = brdf_cos<true>(sh.n, wo, f3(tp.wc[0][g], tp.wc[1][g], tp.wc[2][g]), sh.m);
+                acc = add(acc, f3(fc.x / pind * li.x, fc.y / pind * li.y, fc.z / pind * li.z));
+            }
+        }
+        const float inv_spp = 1.0f / (float)v.spp;
+        float4* o4 = reinterpret_cast<float4*>(out[vi]) + pixel;
+        *o4 = make_float4(acc.x * inv_spp, acc.y * inv_spp, acc.z * inv_spp, (float)hits * inv_spp);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1259,6 +1333,24 @@ void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_view
         k_backward<false, MR_BWD_MINB, true><<<grid_cap(total, 256, sms * 8), 256, 0, st>>>(
             scenes, views, n_views, total, rng, d_images, grads, tape, 0, counters);
 #endif
+}
+
+void mr_launch_light_demod(const SceneDev* scenes, const ViewDev* views, const uint64_t* pix_off, int n_views,
+                           uint64_t total_pixels, uint64_t total, Rng rng, const void* tape, float* const* out,
+                           int sms, cudaStream_t st, bool interp)
+{
+    if (total_pixels == 0) return;
+    (interp ? k_light_demod<true> : k_light_demod<false>)<<<grid_cap(total_pixels, 256, sms * 8), 256, 0, st>>>(
+        scenes, views, pix_off, n_views, total_pixels, total, rng, tape, out);
+}
+
+void mr_launch_light_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
+                              const float* const* d_demod, const GradDev* grads, const void* tape,
+                              unsigned long long* counters, int sms, cudaStream_t st, bool interp)
+{
+    (interp ? k_backward<false, MR_BWD_MINB, true, true> : k_backward<false, MR_BWD_MINB, false, true>)<<<
+        grid_cap(total, 256, sms * 8), 256, 0, st>>>(scenes, views, n_views, total, rng, d_demod, grads, tape, 0,
+                                                     counters);
 }
 
 void mr_launch_account(unsigned long long* counters, const unsigned int* qcnt, int bounces, uint64_t primary,

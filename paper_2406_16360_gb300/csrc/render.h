@@ -88,6 +88,14 @@ void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_view
                         unsigned long long* counters, int sms, cudaStream_t st, int nvx, void* full_scratch,
                         bool interp);
 void mr_launch_l2(const float* img, const float* ref, int64_t n, float* dimg, float* loss, int sms, cudaStream_t st);
+// monochrome light regulariser: the demodulated lighting per pixel (out[view] [h][w][4]) and
+// the PRIMARY-mode adjoint of it (d_demod[view] [h][w][3])
+void mr_launch_light_demod(const SceneDev* scenes, const ViewDev* views, const uint64_t* pix_off, int n_views,
+                           uint64_t total_pixels, uint64_t total, Rng rng, const void* tape, float* const* out,
+                           int sms, cudaStream_t st, bool interp);
+void mr_launch_light_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
+                              const float* const* d_demod, const GradDev* grads, const void* tape,
+                              unsigned long long* counters, int sms, cudaStream_t st, bool interp);
 void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* skip, int64_t n, int any,
                           int32_t* hit_tri, float* hit_tuv, int sms, cudaStream_t st);
 
@@ -105,6 +113,11 @@ void mr_launch_material_smoothness(const SceneDev& s, const ViewDev& v, uint32_t
                                    float* ga, float* gr, int sms, cudaStream_t st);
 void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_smooth, float w_offset, float* loss,
                             float* grad, int sms, cudaStream_t st);
+// L_light from the demodulated lighting: loss[0] += w mean |Y(c) - V(ref)| over the covered
+// pixels of every view (count is device scratch), d_demod = its gradient (overwritten)
+void mr_launch_light_loss(const uint64_t* pix_off, int n_views, uint64_t total_pixels,
+                          const float* const* demod, const float* const* ref, float w, unsigned int* count,
+                          float* loss, float* const* d_demod, int sms, cudaStream_t st);
 
 // wave.cu: the batched wavefront forward (recorded on a stream, captured as a graph)
 void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,

@@ -26,6 +26,7 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_get_counters",
            "mirres_get_work_counters", "EawtParams", "mirres_eawt_record_bytes", "mirres_gbuffer", "mirres_eawt",
            "mirres_eawt_backward", "mirres_mesh_regularizers", "LkParams", "mirres_material_smoothness",
+           "mirres_light_demod", "mirres_light_loss", "mirres_light_backward",
            "mirres_reset_counters", "mirres_last_error", "library_path"]
 
 # limits of mirres_render_noalloc (include/mirres.h)
@@ -133,6 +134,12 @@ def lib():
                 "mirres_mesh_regularizers": (st, [vp, vp, vp, C.c_float, C.c_float, vp, vp, vp]),
                 "mirres_material_smoothness": (st, [vp, vp, C.POINTER(View), i32, C.POINTER(LkParams), vp, vp, vp,
                                                     vp]),
+                "mirres_light_demod": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params), vp,
+                                            sz, C.POINTER(vp), vp]),
+                "mirres_light_loss": (st, [vp, C.POINTER(View), i32, C.POINTER(vp), C.POINTER(vp), C.c_float, vp,
+                                           C.POINTER(vp), vp]),
+                "mirres_light_backward": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
+                                               C.POINTER(vp), vp, sz, C.POINTER(Grads), vp]),
                 "mirres_bvh_export": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "mirres_env_export": (st, [vp, vp, vp, vp, vp, vp]),
                 "mirres_env_export_flat": (st, [vp, vp, vp]),
@@ -336,6 +343,40 @@ def mirres_backward(ctx: Context, scenes, views, params: Params, d_images, tape,
     nbytes = tape.numel() * tape.element_size()
     _check("mirres_backward", lib().mirres_backward(ctx.handle, sc, len(scenes), vs, len(vs), C.byref(params), di,
                                                     _ptr(tape), nbytes, ga, _stream(stream)))
+
+
+def mirres_light_demod(ctx: Context, scenes, views, params: Params, tape, demod, stream=None):
+    """demodulated lighting of the render that wrote `tape`: demod[v] float32 [H][W][4] CUDA tensors"""
+    vs = _views(views)
+    sc = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    out = (C.c_void_p * len(demod))(*[_ptr(t).value for t in demod])
+    nbytes = tape.numel() * tape.element_size()
+    _check("mirres_light_demod", lib().mirres_light_demod(ctx.handle, sc, len(scenes), vs, len(vs), C.byref(params),
+                                                          _ptr(tape), nbytes, out, _stream(stream)))
+
+
+def mirres_light_loss(ctx: Context, views, demod, ref_images, weight=1.0, loss=None, d_demod=None, stream=None):
+    """L_light from the demodulated lighting: adds weight * L_light to loss[0] and writes d_demod[v] [H][W][3]"""
+    vs = _views(views)
+    c = (C.c_void_p * len(demod))(*[_ptr(t).value for t in demod])
+    r = (C.c_void_p * len(ref_images))(*[_ptr(t).value for t in ref_images])
+    d = None if d_demod is None else (C.c_void_p * len(d_demod))(*[_ptr(t).value for t in d_demod])
+    _check("mirres_light_loss", lib().mirres_light_loss(ctx.handle, vs, len(vs), c, r, float(weight), _ptr(loss), d,
+                                                        _stream(stream)))
+
+
+def mirres_light_backward(ctx: Context, scenes, views, params: Params, d_demod, tape, grads, stream=None):
+    """adjoint of the demodulated lighting; grads as for mirres_backward (accumulated)"""
+    vs = _views(views)
+    sc = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    di = (C.c_void_p * len(d_demod))(*[_ptr(t).value for t in d_demod])
+    ga = (Grads * len(scenes))()
+    for i, g in enumerate(grads):
+        ga[i] = Grads(*[_ptr(g.get(k)) for k in ("albedo", "roughness", "metallic", "env", "verts")])
+    nbytes = tape.numel() * tape.element_size()
+    _check("mirres_light_backward", lib().mirres_light_backward(ctx.handle, sc, len(scenes), vs, len(vs),
+                                                                C.byref(params), di, _ptr(tape), nbytes, ga,
+                                                                _stream(stream)))
 
 
 def mirres_l2_loss(image, ref, d_image=None, loss=None, stream=None):

@@ -139,6 +139,28 @@ class GpuWorkload:
                           self.params(launch, seed, grad_mode=grad_mode), d_images, tape, grads, stream)
         return grads
 
+    def light_demod(self, tape, launch=0, seed=None, grad_mode=0, demod=None, stream=None):
+        """demodulated lighting c_d + c_s and coverage per pixel ([H][W][4] per view) of the
+        render that wrote `tape` (the monochrome light regulariser's input)"""
+        demod = demod if demod is not None else [
+            torch.empty((v.height, v.width, 4), device=self.device, dtype=torch.float32) for v in self.views]
+        M.mirres_light_demod(self.ctx, [s.handle for s in self.scenes], self.views,
+                             self.params(launch, seed, grad_mode=grad_mode), tape, demod, stream)
+        return demod
+
+    def light_loss(self, demod, refs, weight=1.0, loss=None, stream=None):
+        """adds weight * L_light to loss[0]; returns (loss, d_demod per view)"""
+        loss = loss if loss is not None else torch.zeros(1, device=self.device, dtype=torch.float32)
+        d = [torch.empty((v.height, v.width, 3), device=self.device, dtype=torch.float32) for v in self.views]
+        M.mirres_light_loss(self.ctx, self.views, demod, refs, weight, loss, d, stream)
+        return loss, d
+
+    def light_backward(self, d_demod, tape, grads=None, launch=0, seed=None, grad_mode=0, stream=None):
+        grads = grads if grads is not None else self.zero_grads()
+        M.mirres_light_backward(self.ctx, [s.handle for s in self.scenes], self.views,
+                                self.params(launch, seed, grad_mode=grad_mode), d_demod, tape, grads, stream)
+        return grads
+
     def close(self):
         for s in self.scenes:
             s.close()
