@@ -43,6 +43,9 @@
 #ifndef MR_CAND_UNROLL
 #define MR_CAND_UNROLL 1
 #endif
+#ifndef MR_CAND_PAIR
+#define MR_CAND_PAIR 1  // RIS candidates drawn two at a time (interleaved env searches)
+#endif
 
 // traversal stack: the first MR_SSTACK entries live in shared memory (column per thread),
 // deeper entries in a small local array; an LBVH over 64-bit unique keys is at most 63 deep
@@ -245,6 +248,36 @@ __device__ __forceinline__ void env_texel_draw(const SceneDev& s, uint32_t xa, u
     }
     r = lo / s.ew;
     c = lo - r * s.ew;
+}
+
+// two independent draws at once: the two guided searches step in lock-step, so each round
+// issues both threshold loads before waiting on either (the same texels as two single draws)
+__device__ __forceinline__ void env_texel_draw2(const SceneDev& s, uint32_t xa0, uint32_t xb0, uint32_t xa1,
+                                                uint32_t xb1, int& r0, int& c0, int& r1, int& c1)
+{
+    const unsigned long long k0 = ((unsigned long long)xa0 << 21) | (unsigned long long)(xb0 >> 11);
+    const unsigned long long k1 = ((unsigned long long)xa1 << 21) | (unsigned long long)(xb1 >> 11);
+    const uint32_t b0 = (uint32_t)(k0 >> s.gf_shift), b1 = (uint32_t)(k1 >> s.gf_shift);
+    int lo0 = (int)__ldg(s.env_gflat + b0), hi0 = (int)__ldg(s.env_gflat + b0 + 1);
+    int lo1 = (int)__ldg(s.env_gflat + b1), hi1 = (int)__ldg(s.env_gflat + b1 + 1);
+    while (lo0 < hi0 || lo1 < hi1) {
+        const int m0 = (lo0 + hi0 + 1) >> 1, m1 = (lo1 + hi1 + 1) >> 1;
+        const bool a0 = lo0 < hi0, a1 = lo1 < hi1;
+        const unsigned long long t0 = a0 ? __ldg(s.env_flat + m0) : 0ull;
+        const unsigned long long t1 = a1 ? __ldg(s.env_flat + m1) : 0ull;
+        if (a0) {
+            if (t0 <= k0) lo0 = m0;
+            else hi0 = m0 - 1;
+        }
+        if (a1) {
+            if (t1 <= k1) lo1 = m1;
+            else hi1 = m1 - 1;
+        }
+    }
+    r0 = lo0 / s.ew;
+    c0 = lo0 - r0 * s.ew;
+    r1 = lo1 / s.ew;
+    c1 = lo1 - r1 * s.ew;
 }
 
 // sample a direction with probability proportional to Y(L) sin(theta_row); returns pdf.

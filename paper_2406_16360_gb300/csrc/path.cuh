@@ -159,12 +159,8 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
         int sel = -1, ytex = 0;
         uint32_t ysub = 0u;
         float3 ysel = f3(0.f, 0.f, 0.f);
-#pragma unroll kCandUnroll
-        for (int j = 0; j < M; ++j) {
-            const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j);
-            float3 dir;
-            int tex;
-            const float gq = env_candidate(s, x.x, x.y, x.w, dir, tex);  // Y(L_env) / q_dir
+        // candidate j with direction dir, texel tex and gq = Y(L_env) / q_dir into the reservoir
+        auto consider = [&](int j, const uint4& x, float3 dir, int tex, float gq) {
             const float ci = dot(sh.n, dir);
             float yfc = 0.0f, dv = 0.0f, w5 = 0.0f;
             if (co > 0.0f && ci > 0.0f && above_face(sh, dir)) {
@@ -189,6 +185,31 @@ __device__ __forceinline__ void shade_vertex(const SceneDev& s, int env_ok, cons
                 w5_sel = w5;
                 ci_sel = ci;
             }
+        };
+        int j = 0;
+#if MR_CAND_PAIR
+        // two candidates per round: both env searches and row loads in flight together, then
+        // the reservoir takes them in order (the same arithmetic as one at a time)
+        for (; j + 1 < M; j += 2) {
+            const uint4 x0 = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j);
+            const uint4 x1 = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)(j + 1));
+            int r0, c0, r1, c1;
+            env_texel_draw2(s, x0.x, x0.y, x1.x, x1.y, r0, c0, r1, c1);
+            float3 d0, d1;
+            float4 rv0, rv1;
+            const float st0 = env_dir(s, r0, c0, x0.w, d0, rv0);
+            const float st1 = env_dir(s, r1, c1, x1.w, d1, rv1);
+            consider(j, x0, d0, r0 * s.ew + c0, st0 * rv0.z);
+            consider(j + 1, x1, d1, r1 * s.ew + c1, st1 * rv1.z);
+        }
+#endif
+#pragma unroll kCandUnroll
+        for (; j < M; ++j) {
+            const uint4 x = rng.draw(pixel, smp, view, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j);
+            float3 dir;
+            int tex;
+            const float gq = env_candidate(s, x.x, x.y, x.w, dir, tex);
+            consider(j, x, dir, tex, gq);
         }
         const float4 L = (sel >= 0) ? __ldg(s.env_texel + ytex) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float phat_sel = lum(xyz(L)) * yfc_sel;
