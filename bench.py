@@ -42,8 +42,8 @@ REUSE = (4, 8)
 # scaled to the bench's launches by their unit counts. Valid only for the kernel sources they
 # were measured on (SHA-256 prefix of wave.cu, device.cuh, path.cuh, bvh.cu); otherwise null.
 TRAFFIC_SOURCES = ("wave.cu", "device.cuh", "path.cuh", "bvh.cu")
-TRAFFIC_SHA = "9b107e8d88291925"
-TRAFFIC_PER_UNIT = {"closest": 97.93, "shade": 10.43, "shadow": 150.14}
+TRAFFIC_SHA = "ce343adad802fa22"
+TRAFFIC_PER_UNIT = {"closest": 97.89, "shade": 11.63, "shadow": 150.74}
 
 
 def _traffic_valid():

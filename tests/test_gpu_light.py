@@ -200,3 +200,64 @@ def test_arguments_are_checked(M, ctx):
     with pytest.raises(RuntimeError):
         gw.light_loss(demod, [torch.zeros((1,), device="cuda")], weight=-1.0)
     _close(gw)
+
+
+def test_config3_full_size_sampled(M, ctx):
+    """config 3 at full size in the batched launch (100 views of 800 x 800, 16 spp, 4 bounces):
+    the demodulated lighting of sampled pixels of three views, the loss over every pixel of
+    every view, and the adjoint of sampled pixels of one view"""
+    w = synth.config3(n_views=100)
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1)
+    demod = gw.light_demod(tape, launch=1)
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(17))
+    sc = w.scenes[0]
+    osc = O.OracleScene(sc)
+    dark = copy.deepcopy(sc)
+    dark.env = np.zeros_like(sc.env)
+    odark = O.OracleScene(dark)
+    for vi in (0, 37, 99):
+        v = w.views[vi]
+        pix = np.sort(rng.choice(v.width * v.height, size=96, replace=False)).astype(np.int32)
+        r = O.light_demod(osc, v, vi, w.ris_m, seed=w.seed, pixels=pix)
+        c_ind = O.light_demod_detached(osc, odark, v, vi, w.ris_m, seed=w.seed, pixels=pix)
+        g = demod[vi].cpu().numpy().reshape(-1, 4)[pix].astype(np.float64)
+        ok = r["margin"] >= 1.0
+        err = np.abs(g[:, :3] - r["c"]).max(axis=1)
+        tol = DEMOD_RTOL * np.abs(r["c"]).max(axis=1) + IND_RTOL * np.abs(c_ind).max(axis=1)
+        assert not (ok & (err > tol)).any(), (vi, np.flatnonzero(ok & (err > tol)))
+        assert ok.sum() >= 0.5 * len(pix)
+        np.testing.assert_array_equal(g[ok, 3], r["cov"][ok].astype(np.float32))
+    # the loss over all 64 M pixels against the oracle's formula on the same buffers
+    loss, d = gw.light_loss(demod, images, weight=1.0)
+    torch.cuda.synchronize()
+    c_np = [x.cpu().numpy().reshape(-1, 4).astype(np.float64) for x in demod]
+    want, wgrad = light_loss([c[:, :3] for c in c_np], [c[:, 3] for c in c_np],
+                             [im.cpu().numpy().reshape(-1, 3).astype(np.float64) for im in images])
+    assert float(loss.item()) == pytest.approx(want, rel=1e-4)
+    # seeds: equal wherever the sign is not a near tie in FP32
+    for vi in (0, 99):
+        c = c_np[vi]
+        diff = c[:, :3].mean(axis=1) - images[vi].cpu().numpy().reshape(-1, 3).astype(np.float64).max(axis=1)
+        clear = np.abs(diff) > 1e-5 * np.maximum(np.abs(c[:, :3]).max(axis=1), 1e-30)
+        np.testing.assert_allclose(d[vi].cpu().numpy().reshape(-1, 3)[clear], wgrad[vi][clear], rtol=1e-6, atol=0)
+    del c_np, wgrad
+    # the adjoint of 48 sampled pixels of view 37
+    v = w.views[37]
+    pix = np.sort(rng.choice(v.width * v.height, size=48, replace=False)).astype(np.int32)
+    r = O.light_demod(osc, v, 37, w.ris_m, seed=w.seed, pixels=pix)
+    gs = rng.normal(size=(len(pix), 3))
+    gs[r["margin"] < 1.0] = 0.0
+    d_c = [torch.zeros((vv.height, vv.width, 3), device="cuda") for vv in w.views]
+    d_c[37].view(-1, 3)[torch.as_tensor(pix.astype(np.int64), device="cuda")] = torch.as_tensor(
+        gs, dtype=torch.float32, device="cuda")
+    grads = gw.light_backward(d_c, tape)
+    torch.cuda.synchronize()
+    og = O.light_backward(osc, v, 37, w.ris_m, d_c[37].double().cpu().numpy().reshape(-1, 3)[pix], seed=w.seed,
+                          pixels=pix)
+    for k in FIELDS:
+        st = compare_grads(grads[0][k].cpu().numpy(), og[k], og[k + "_abs"], og.get(k + "_sens"),
+                           **grad_tolerance(k))
+        assert st["failures"] == 0, (k, st["detail"])
+    _close(gw)
