@@ -132,6 +132,53 @@ def test_demod_and_adjoint_reduced_config2(M, ctx, normals):
     _close(gw)
 
 
+@pytest.mark.parametrize("mode", ["spatial_reuse", "full_tape"])
+def test_demod_after_reuse_and_from_a_full_tape(M, ctx, mode):
+    """the demodulated lighting reads the tape's primary words only: after spatial reuse (the
+    primary vertex's selection merged from neighbours) it follows the merged selection, and a
+    FULL-mode tape (vertex records after the primary words) gives the same as a PRIMARY one"""
+    w = synth.config1(width=40, height=36)
+    gw = _gw(ctx, w)
+    if mode == "spatial_reuse":
+        reuse = (4, 3)
+        _, tape = gw.render(launch=1, reuse=reuse)
+        demod = gw.light_demod(tape, launch=1)
+        torch.cuda.synchronize()
+        refs = []
+        for vi, v in enumerate(w.views):
+            osc = O.OracleScene(w.scenes[v.scene])
+            r = O.light_demod(osc, v, vi, w.ris_m, seed=w.seed, reuse=reuse)
+            dark = copy.deepcopy(w.scenes[v.scene])
+            dark.env = np.zeros_like(dark.env)
+            r["c_ind"] = O.light_demod_detached(osc, O.OracleScene(dark), v, vi, w.ris_m, seed=w.seed, reuse=reuse)
+            refs.append(r)
+        _check_demod(w, demod, refs)
+        # the adjoint follows the merged selection too
+        rng = np.random.Generator(np.random.PCG64(5))
+        v = w.views[0]
+        g = rng.normal(size=(v.height * v.width, 3))
+        g[refs[0]["margin"] < 1.0] = 0.0
+        d_c = [torch.as_tensor(g.reshape(v.height, v.width, 3), dtype=torch.float32, device="cuda")]
+        grads = gw.light_backward(d_c, tape)
+        torch.cuda.synchronize()
+        og = O.light_backward(O.OracleScene(w.scenes[0]), v, 0, w.ris_m, d_c[0].double().cpu().numpy().reshape(-1, 3),
+                              seed=w.seed, reuse=reuse)
+        for k in FIELDS:
+            st = compare_grads(grads[0][k].cpu().numpy(), og[k], og[k + "_abs"], og.get(k + "_sens"),
+                               **grad_tolerance(k))
+            assert st["failures"] == 0, (k, st["detail"])
+    else:
+        _, tape_p = gw.render(launch=1)
+        a = gw.light_demod(tape_p, launch=1)
+        _, tape_f = gw.render(launch=1, grad_mode=M.GRAD_FULL)
+        b = gw.light_demod(tape_f, launch=1, grad_mode=M.GRAD_FULL)
+        torch.cuda.synchronize()
+        assert tape_f.numel() > tape_p.numel()
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    _close(gw)
+
+
 def test_several_scenes_and_a_sky_view(M, ctx):
     w = synth.config5(seed=3, n_scenes=2, max_tris=6000, res_choices=(16, 24), spp_choices=(2, 3), tex=16)
     for s in w.scenes:
