@@ -427,7 +427,8 @@ mirres_status mirres_mesh_regularizers(mirres_context* ctx, mirres_scene* scene,
  * coordinates + eps, eps uniform in [-sigma, sigma]^2 from Philox4x32-10 (key = seed, counter
  * (pixel, 0, view_index << 16 | 4, 0), eps = sigma (2 u - 1) with u the 24-bit uniforms of the
  * first two words). |.| of the albedo is the mean of its three channels' absolute differences.
- * (The paper's normal term has no counterpart: normals are the mesh's face normals.) Adds
+ * (The paper's normal term has no counterpart: the normals come from the mesh -- face normals
+ * or interpolated vertex normals -- not from a texture a texture-space offset could move along.) Adds
  * w_albedo L_albedo + w_roughness L_roughness to loss[0] and its gradient (sign(0) = 0) to
  * grad_albedo [tex_h][tex_w][3] and grad_roughness [tex_h][tex_w]; all device, accumulated,
  * any may be NULL. view->scene is ignored. Uses the context workspace (16 B per pixel);

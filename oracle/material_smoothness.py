@@ -14,8 +14,9 @@ textures):
   * eps comes from Philox4x32-10 with counter (pixel, 0, view << 16 | 4, 0) and key = seed:
     eps = sigma (2 u - 1) with u = (x >> 8) 2^-24 of the first two output words;
   * |.| of the three-channel albedo is the mean of its channels' absolute differences;
-  * the normal term is left out: normals are the mesh's face normals, with no parameters of
-    their own (the mesh regularisers act on the geometry);
+  * the normal term is left out: the normals come from the mesh (face normals, or the
+    interpolated vertex normals), with no texture of their own that a texture-space offset
+    could move along (the mesh regularisers act on the geometry);
   * the gradient takes sign(0) = 0.
 L = w_albedo L_albedo + w_roughness L_roughness; its gradient with respect to the texels is
 (w / |X|) sign(k(x) - k(x + eps)) (bilinear weights at x - bilinear weights at x + eps), with a
