@@ -381,6 +381,7 @@ static const uint64_t kWave = 1ull << MR_WAVE_LOG2;
 
 struct GraphKey {
     uint64_t total, total_pix, wave;
+    uint64_t layout;  // digest of what the capture decides on the host (layout_digest)
     int32_t n_views, n_scenes, max_b, M, sms, flags, nvx, reuse_k, reuse_radius, temporal, temporal_cap;
     uint32_t k0, k1;
     const void* history;
@@ -389,9 +390,32 @@ struct GraphKey {
     size_t ws_bytes;
 };
 
+// The host-side choices baked into a captured forward: every view's size, samples, bounces and
+// scene (the wave partition, which views a rasterising wave covers) and every scene's triangle
+// count and normal mode (raster grids, the interpolated-normal shading kernels). FNV-1a over
+// those fields; the cameras and the scenes' device buffers are read from the tables at run time
+// and stay out of it.
+static uint64_t layout_digest(const std::vector<ViewDev>& vdev, const std::vector<SceneDev>& sdev)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](uint64_t x) {
+        for (int k = 0; k < 8; ++k) {
+            h ^= (x >> (8 * k)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    };
+    for (const ViewDev& v : vdev) {
+        mix(((uint64_t)(uint32_t)v.width << 32) | (uint32_t)v.height);
+        mix(((uint64_t)(uint32_t)v.spp << 32) | (uint32_t)v.bounces);
+        mix((uint64_t)(uint32_t)v.scene);
+    }
+    for (const SceneDev& sc : sdev) mix(((uint64_t)(uint32_t)sc.n_tris << 1) | (sc.vnrm != nullptr ? 1u : 0u));
+    return h;
+}
+
 // Batched wavefront: tables uploaded to the workspace, then the whole forward replayed from a
-// CUDA graph captured on the context's capture stream (re-captured when the shape, the tape,
-// the seed or the workspace changes).
+// CUDA graph captured on the context's capture stream (re-captured when the shape, the layout
+// digest, the tape, the seed or the workspace changes).
 static mirres_status stage_events(mirres_context* ctx, int pairs)
 {
     if (ctx->n_stage_events >= 2 * pairs) return MIRRES_OK;
@@ -495,6 +519,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     key.total = total;
     key.total_pix = total_pix;
     key.wave = wave;
+    key.layout = layout_digest(vdev, sdev);
     key.n_views = n_views;
     key.n_scenes = n_scenes;
     key.max_b = max_b;

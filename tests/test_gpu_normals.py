@@ -211,3 +211,31 @@ def test_mixed_scenes_one_interpolated(M, ctx):
                                **grad_tolerance(k))
             assert st["failures"] == 0, (si, k, st["failures"], st["max_rel"], st["detail"])
     _close(gw)
+
+
+def test_graph_recaptured_when_the_normal_mode_changes(M, ctx):
+    """the batched forward's graph bakes the shading kernels in: a render with interpolated
+    normals after a face-normal render of the same shapes, into the same tape and images, must
+    capture a new graph (the kernels read the scene tables at run time, the kernel choice not)"""
+    w = synth.config1()
+    face = _gw_mode(ctx, w, 0)
+    images = face.new_images()
+    tape = face.new_tape()
+    face.render(launch=1, images=images, tape=tape)
+    interp = _gw(ctx, w)
+    interp.render(launch=1, images=images, tape=tape)
+    torch.cuda.synchronize()
+    _forward(w, images)
+    # and back: face normals again replay nothing stale
+    face.render(launch=1, images=images, tape=tape)
+    torch.cuda.synchronize()
+    r = O.render(O.OracleScene(w.scenes[0]), w.views[0], 0, w.ris_m, seed=w.seed)
+    st = compare_pixels(images[0].cpu().numpy().reshape(-1, 3), r["rgb"], r["margin"])
+    assert st["failures"] == 0, st["max_err_unflagged"]
+    _close(face)
+    _close(interp)
+
+
+def _gw_mode(ctx, w, normals):
+    from paper_2406_16360_gb300.renderer import GpuWorkload
+    return GpuWorkload(w, 0, ctx=ctx, normals=normals)
