@@ -99,7 +99,9 @@ typedef struct {
  *                 compaction, shade + RIS + next-bounce queue, shadow rays, resolve);
  *            1 = batched wavefront: every view of every scene flattened into waves of up to
  *                 2^25 samples; the whole forward is one CUDA graph, captured on first use and
- *                 replayed while the shape, tape, seed and workspace stay the same;
+ *                 replayed while the shape (each view's size, samples, bounces and scene; each
+ *                 scene's triangle count and normal mode), tape, seed and workspace stay the
+ *                 same (cameras and scene contents may change between replays);
  *            2 = persistent kernel: one launch over every view of every scene, each warp
  *                 pulling samples from a device counter and refilling lanes by ballot.
  *            All take every discrete decision identically (hit triangles, selected
