@@ -574,10 +574,28 @@ def main():
         e_ll[1].record()
         torch.cuda.synchronize()
         ms_ll = e_ll[0].elapsed_time(e_ll[1]) / args.steps
+        # the demodulated-lighting kernel alone: a stream over the tape's primary words (4 B for
+        # a sample whose primary ray escaped, 56 B for one that hit) plus 16 B written per pixel;
+        # the hit count is exact from the coverage channel
+        e_dm = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e_dm[0].record()
+        M.mirres_light_demod(gw.ctx, scenes, gw.views, lp, tape, ll_c)
+        e_dm[1].record()
+        torch.cuda.synchronize()
+        ms_dm = e_dm[0].elapsed_time(e_dm[1])
+        hits = int(round(sum(float((c[..., 3].double() * v.spp).sum()) for c, v in zip(ll_c, gw.views))))
+        bytes_dm = 56 * hits + 4 * (samples - hits) + 16 * pix
+        ach_dm = bytes_dm / (ms_dm / 1e3) / 1e9
         regs["light"] = {"ms_per_step": ms_ll, "pixels": pix, "samples": samples,
                          "mpix_per_s": pix / (ms_ll / 1e3) / 1e6,
                          "msamples_per_s": samples / (ms_ll / 1e3) / 1e6, "weight": 0.1,
-                         "kernel": "k_light_demod + k_light_count + k_light_apply + k_backward<DEMOD>"}
+                         "kernel": "k_light_demod + k_light_count + k_light_apply + k_backward<DEMOD>",
+                         "demod_ms": ms_dm, "demod_hit_samples": hits,
+                         "roofline": {"bound": "hbm", "achieved": ach_dm, "peak": HBM_PEAK, "unit": "GB/s",
+                                      "frac": ach_dm / HBM_PEAK, "traffic": None, "bytes": bytes_dm,
+                                      "kernel": "k_light_demod",
+                                      "bytes_note": "56 B per hit sample, 4 B per escaped sample, 16 B per pixel",
+                                      "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}}
         ll_c = ll_d = ll_g = None
 
     # FULL-mode adjoint (gradients through every vertex): the same step with grad_mode 1
