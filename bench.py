@@ -33,6 +33,8 @@ METRIC = "fwd+bwd path-samples/s (batched launch; plain per-view launch and Mray
 EAWT_SIGMAS = (0.5, 0.3, 0.2)
 # spatial reuse arm: neighbours merged per pixel and the radius they are drawn from
 REUSE = (4, 8)
+# timed calls of the demodulated-lighting kernel for its roofline
+DEMOD_REPS = 5
 
 
 # DRAM bytes per unit of the three stage kernels (closest-hit ray, RIS candidate, shadow ray),
@@ -281,6 +283,22 @@ def main():
     __graft_entry__.build()
     from paper_2406_16360_gb300 import mirres as M
     from paper_2406_16360_gb300.renderer import GpuWorkload
+
+    # the roofline denominators, measured on this device before the workload is set up: the FP32
+    # FMA rate of the SMs (the stages' arithmetic) and the bandwidth of loads served by L2 (where
+    # the traversal's node and triangle loads hit)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_clk = ClockSampler(local)
+    peak_clk.start()
+    fp32_flops, fp32_ms = M.mirres_peak_fp32()
+    l2_bps, l2_ms = M.mirres_peak_l2()
+    peak_clocks = peak_clk.stop()
+    peaks = {"fp32_tflops": fp32_flops / 1e12, "fp32_basis": "FMA microbenchmark (mirres_peak_fp32): 16 independent "
+             f"chains per thread, {sm_count} SMs x 8 blocks of 256, {fp32_ms:.1f} ms timed launch",
+             "l2_gbs": l2_bps / 1e9, "l2_basis": "32 MiB L2-resident buffer, 40 passes of 16-byte ld.global.cg "
+             f"loads over all SMs (mirres_peak_l2), {l2_ms:.1f} ms timed launch",
+             "sm_count": sm_count, "nominal_fp32_tflops_at_max_clock": sm_count * 128 * 2 * 2.070e9 / 1e12,
+             "clocks_during_peaks": peak_clocks}
 
     w = make_workload(args.workload, args.views)
     builder = M.MIRRES_BVH_PLOC if args.bvh == "ploc" else M.MIRRES_BVH_LBVH
@@ -577,12 +595,17 @@ def main():
         # the demodulated-lighting kernel alone: a stream over the tape's primary words (4 B for
         # a sample whose primary ray escaped, 56 B for one that hit) plus 16 B written per pixel;
         # the hit count is exact from the coverage channel
-        e_dm = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        e_dm[0].record()
-        M.mirres_light_demod(gw.ctx, scenes, gw.views, lp, tape, ll_c)
-        e_dm[1].record()
+        # timed over DEMOD_REPS calls, one event pair each (the call's table uploads are a few
+        # hundred bytes); mean and spread reported
+        e_dm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(DEMOD_REPS)]
+        for a, b in e_dm:
+            a.record()
+            M.mirres_light_demod(gw.ctx, scenes, gw.views, lp, tape, ll_c)
+            b.record()
         torch.cuda.synchronize()
-        ms_dm = e_dm[0].elapsed_time(e_dm[1])
+        ms_all = [a.elapsed_time(b) for a, b in e_dm]
+        ms_dm = sum(ms_all) / len(ms_all)
         hits = int(round(sum(float((c[..., 3].double() * v.spp).sum()) for c, v in zip(ll_c, gw.views))))
         bytes_dm = 56 * hits + 4 * (samples - hits) + 16 * pix
         ach_dm = bytes_dm / (ms_dm / 1e3) / 1e9
@@ -590,7 +613,8 @@ def main():
                          "mpix_per_s": pix / (ms_ll / 1e3) / 1e6,
                          "msamples_per_s": samples / (ms_ll / 1e3) / 1e6, "weight": 0.1,
                          "kernel": "k_light_demod + k_light_count + k_light_apply + k_backward<DEMOD>",
-                         "demod_ms": ms_dm, "demod_hit_samples": hits,
+                         "demod_ms": ms_dm, "demod_ms_min": min(ms_all), "demod_ms_max": max(ms_all),
+                         "demod_repeats": len(ms_all), "demod_hit_samples": hits,
                          "roofline": {"bound": "hbm", "achieved": ach_dm, "peak": HBM_PEAK, "unit": "GB/s",
                                       "frac": ach_dm / HBM_PEAK, "traffic": None, "bytes": bytes_dm,
                                       "kernel": "k_light_demod",
@@ -651,6 +675,7 @@ def main():
                                   "samples_differentiated": cnt_b[4] // args.steps},
             "gpu_launches": launches_b,
             "clocks": clk,
+            "peaks": peaks,
             "e2e": {"value": world * samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
 
@@ -663,7 +688,7 @@ def main():
     env_texels = sum(s.env.shape[0] * s.env.shape[1] for s in w.scenes) / len(w.scenes)
     per_cand = 60 + 2 * math.log2(env_texels)
     cand_per_render = cnt_b[5] / args.steps
-    peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    peak = peaks["fp32_tflops"]
     total_stage_ms = max(sum(v[0] for v in stages.values()), 1e-9)
     stage_flops = {"shade": cand_per_render * per_cand,
                    "closest": 12.0 * work[0] + 27.0 * work[1],
@@ -683,7 +708,17 @@ def main():
                     "traffic_basis": "ncu DRAM bytes per unit on a 2-view capture x units per launch",
                     "kernel": names[k], "kernel_ms_per_launch": ms_k / max(launches_k, 1),
                     "kernel_share_of_render": ms_k / total_stage_ms, "flops_per_render": stage_flops[k],
-                    "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock), non-tensor"}
+                    "peak_basis": "measured FP32 FMA rate of this device (peaks.fp32_basis), non-tensor"}
+        if k in ("closest", "shadow"):
+            # the memory side: the traversal's algorithmic bytes (32 B per box test, i.e. per
+            # child box, + 36 B per triangle test) over the time, against the measured L2 load
+            # bandwidth (the nodes and triangles are L2-resident)
+            box, tri = (work[0], work[1]) if k == "closest" else (work[2], work[3])
+            nbytes = 32.0 * box + 36.0 * tri
+            ach = nbytes / (ms_k / 1e3) / 1e9
+            roofs[k]["memory"] = {"bound": "l2", "achieved": ach, "peak": peaks["l2_gbs"], "unit": "GB/s",
+                                  "frac": ach / peaks["l2_gbs"], "bytes_per_render": nbytes,
+                                  "peak_basis": "measured L2 load bandwidth (peaks.l2_basis)"}
     roofs["shade"].update(flops_per_candidate=per_cand, candidates_per_render=cand_per_render)
     roofs["closest"].update(box_tests_per_render=work[0], triangle_tests_per_render=work[1])
     roofs["shadow"].update(box_tests_per_render=work[2], triangle_tests_per_render=work[3])

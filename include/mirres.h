@@ -51,8 +51,10 @@ typedef struct mirres_scene mirres_scene;     /* BVH, env sampling tables, borro
 /* Scene description (Sec. 3.2: mesh M = {V, F}, material textures, env map 256x512 in the
  * paper; any size here). Every pointer is a device pointer, borrowed.
  *   verts    [n_verts][3]        world positions (y up)
- *   tris     [n_tris][3]         vertex indices, 0 <= index < n_verts (checked on device by
- *                                mirres_bvh_build, which then returns MIRRES_ERR_ARG)
+ *   tris     [n_tris][3]         vertex indices, 0 <= index < n_verts (checked on the device
+ *                                by mirres_scene_create and mirres_scene_validate, which then
+ *                                return MIRRES_ERR_ARG; builds and refits do not check and
+ *                                read an out-of-range index as vertex 0)
  *   tri_uv   [n_tris][3][2]      per-corner texture coordinates
  *   albedo   [tex_h][tex_w][3], roughness [tex_h][tex_w], metallic [tex_h][tex_w]
  *                                sampled bilinearly, texel centres at (i + 0.5) / size,
@@ -132,7 +134,12 @@ typedef struct {
  *            batched wavefront resolves primary visibility by rasterisation (each triangle
  *            projected into the view, each camera sample in its screen box tested with the
  *            traversal's FP32 ray/triangle solve, closest by a 64-bit atomicMin on (t, triangle)),
- *            as the paper does with a rasteriser, instead of tracing primary rays */
+ *            as the paper does with a rasteriser, instead of tracing primary rays
+ *   max_visits  failure detection: every ray traversal is a bounded loop of at most max_visits
+ *            node visits (0 = 4 n_tris + 64, more than any well-formed tree needs) on a bounded
+ *            stack; a traversal that reaches either bound ends as a miss and raises the
+ *            context's error counter, which mirres_get_counters reports as MIRRES_ERR_TIMEOUT.
+ *            The kernels never wait on anything, so nothing else can stall them. */
 typedef struct {
     int32_t ris_m;
     uint32_t seed_lo, seed_hi;
@@ -147,6 +154,7 @@ typedef struct {
     int32_t temporal_cap;  /* the history counts at most temporal_cap * ris_m candidates */
     void* reuse_history;   /* device, mirres_reuse_history_bytes(views) bytes, caller-owned, kept across calls */
     uint64_t reuse_history_bytes;
+    int32_t max_visits;    /* iteration cap of one ray traversal in node visits (0 = 4 n_tris + 64) */
 } mirres_params;
 #define MIRRES_REUSE_MAX_K 64
 
@@ -164,17 +172,24 @@ typedef struct {
 mirres_status mirres_context_create(int32_t device, mirres_context** out);
 mirres_status mirres_context_destroy(mirres_context* ctx);
 
-/* Create a scene from borrowed device arrays; validates sizes and pointers on the host.
- * The scene owns its LBVH and env-sampling tables (allocated here). */
+/* Create a scene from borrowed device arrays; validates sizes and pointers on the host and
+ * every triangle index on the device (synchronises the legacy default stream once;
+ * MIRRES_ERR_ARG if an index is outside [0, n_verts)). The scene owns its LBVH and
+ * env-sampling tables (allocated here). */
 mirres_status mirres_scene_create(mirres_context* ctx, const mirres_scene_desc* desc, mirres_scene** out);
 mirres_status mirres_scene_destroy(mirres_scene* scene);
+
+/* Check the scene's triangle indices again (for a caller that rewrote desc.tris in place):
+ * synchronises `stream`; MIRRES_ERR_ARG if an index is outside [0, n_verts). */
+mirres_status mirres_scene_validate(mirres_scene* scene, void* stream);
 
 /* LBVH build (Appendix A "Visibility estimation": a linear BVH after Karras 2012): FP32
  * triangle centroids (fixed operation order, no contraction), 30-bit Morton codes in the
  * centroid box, keys code << 32 | triangle, stable radix sort, binary radix tree, bottom-up
  * boxes, traversal layout. Also rebuilds the env sampling tables (FP64 prefix sums of
- * Y(L) sin(theta); Y = (r+g+b)/3, Appendix A). Checks triangle indices (synchronises the
- * stream once to read the check; MIRRES_ERR_ARG if any index is out of range). */
+ * Y(L) sin(theta); Y = (r+g+b)/3, Appendix A). Asynchronous: no host synchronisation (the
+ * triangle indices were checked by mirres_scene_create), so it can be captured into a graph
+ * with the default LBVH builder. */
 mirres_status mirres_bvh_build(mirres_scene* scene, void* stream);
 
 /* Hierarchy builder used by the next mirres_bvh_build of this scene:
@@ -289,12 +304,15 @@ mirres_status mirres_stage_times(mirres_context* ctx, double out_ms[4], int32_t 
  * device memory while they render: for example a process whose device memory is entirely
  * reserved by another allocator (a framework's caching allocator), or a latency-critical
  * serving loop that must not pay the device-wide synchronisation cudaMalloc / cudaFree can
- * bring. It runs the persistent-kernel forward of mirres_render (launch = 2; the launch
- * field is ignored) with the same results, but keeps its scratch -- the per-call view,
+ * bring. It runs the persistent-kernel forward of mirres_render (launch = 2, whatever valid
+ * launch is given; the launch shape follows params.block / blocks_per_sm, or the context's
+ * autotuned shape when block is 0) with the same results, but keeps its scratch -- the per-call view,
  * scene and image tables and the work counter -- in one static device array of
  * MIRRES_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process
  * exits. It calls no cudaMalloc, cudaFree or allocating library routine.
  *   - The tape is required (caller-owned, mirres_tape_bytes(views) bytes, 16-byte aligned).
+ *   - PRIMARY-mode tape only (grad_mode 0) and no reservoir reuse: reuse_k > 0 or temporal > 0
+ *     (which need per-sample scratch) is rejected with MIRRES_ERR_ARG.
  *   - n_views > MIRRES_NOALLOC_MAX_VIEWS or n_scenes > MIRRES_NOALLOC_MAX_SCENES is rejected
  *     with MIRRES_ERR_ARG and a message naming the limit; all scenes share one context.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
@@ -484,9 +502,12 @@ mirres_status mirres_light_backward(mirres_context* ctx, mirres_scene* const* sc
                                     const float* const* d_demod, const void* tape, size_t tape_bytes,
                                     const mirres_grads* grads, void* stream);
 
-/* Cumulative counters since the context was created (synchronises the context's last
- * stream): [0] primary rays, [1] continuation rays, [2] shadow rays, [3] samples rendered,
- * [4] samples differentiated, [5] RIS candidates, [6] kernel launches, [7] error flag. */
+/* Cumulative counters since the context was created or mirres_reset_counters (synchronises the
+ * context's last stream): [0] primary rays, [1] continuation rays, [2] shadow rays, [3] samples
+ * rendered, [4] samples differentiated, [5] RIS candidates, [6] kernel launches, [7] error
+ * count: ray traversals that reached their iteration cap (params.max_visits) or overflowed their
+ * stack and reported a miss. out[] is filled in either case; the call returns MIRRES_ERR_TIMEOUT
+ * (with a message) while [7] is not zero, until mirres_reset_counters clears it. */
 mirres_status mirres_get_counters(mirres_context* ctx, uint64_t out[8]);
 
 /* Cumulative traversal work of the batched launches (launch 1) issued with params.flags bit 1

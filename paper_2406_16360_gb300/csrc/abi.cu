@@ -64,6 +64,8 @@ SceneDev mr_scene_dev(const mirres_scene* s)
     d.tmin_dev = s->tmin;
     d.vnrm = s->normals ? s->vnrm : nullptr;
     d.gvn = s->normals ? s->gvn : nullptr;
+    d.err = s->ctx->counters + CNT_ERROR;
+    d.trav_cap = 0;
     return d;
 }
 
@@ -143,7 +145,7 @@ static mirres_status check_views(const mirres_view* views, int32_t n_views, int3
 }
 
 static mirres_status check_scenes(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
-                                  std::vector<SceneDev>& out)
+                                  std::vector<SceneDev>& out, int32_t trav_cap = 0)
 {
     if (n_scenes < 1 || !scenes) return arg_error("need at least one scene");
     out.resize((size_t)n_scenes);
@@ -155,6 +157,7 @@ static mirres_status check_scenes(mirres_context* ctx, mirres_scene* const* scen
             return MIRRES_ERR_STATE;
         }
         out[(size_t)i] = mr_scene_dev(scenes[i]);
+        out[(size_t)i].trav_cap = trav_cap;
     }
     return MIRRES_OK;
 }
@@ -175,6 +178,7 @@ static mirres_status check_params(const mirres_params* p)
     if (p->temporal < 0 || p->temporal > 2) return arg_error("temporal must be 0, 1 or 2");
     if (p->temporal == 2 && (p->temporal_cap < 1 || p->temporal_cap > 1 << 20))
         return arg_error("temporal_cap must be in [1, 2^20] when temporal = 2");
+    if (p->max_visits < 0) return arg_error("max_visits must be >= 0 (0 = 4 n_tris + 64)");
     return MIRRES_OK;
 }
 
@@ -239,6 +243,10 @@ extern "C" mirres_status mirres_scene_create(mirres_context* ctx, const mirres_s
     s->desc = *d;
     mirres_status st = mr_bvh_alloc(s);
     if (st == MIRRES_OK) st = mr_env_alloc(s);
+    if (st == MIRRES_OK) {
+        st = mr_check_indices(s, nullptr);
+        if (st == MIRRES_ERR_ARG) g_err = "mirres_scene_create: " + g_err;
+    }
     if (st != MIRRES_OK) {
         mr_bvh_free(s);
         mr_env_free(s);
@@ -247,6 +255,15 @@ extern "C" mirres_status mirres_scene_create(mirres_context* ctx, const mirres_s
     }
     *out = s;
     return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_scene_validate(mirres_scene* s, void* stream)
+{
+    if (!s) return arg_error("scene is NULL");
+    MR_CUDA(cudaSetDevice(s->ctx->device));
+    const mirres_status st = mr_check_indices(s, as_stream(stream));
+    if (st == MIRRES_ERR_ARG) g_err = "mirres_scene_validate: " + g_err;
+    return st;
 }
 
 extern "C" mirres_status mirres_scene_destroy(mirres_scene* s)
@@ -591,7 +608,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
     if (!ctx) return arg_error("ctx is NULL");
     MR_TRY(check_params(params));
     std::vector<SceneDev> sdev;
-    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev));
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev, params ? params->max_visits : 0));
     std::vector<ViewDev> vdev;
     uint64_t total = 0, max_view = 0;
     MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
@@ -715,7 +732,7 @@ extern "C" mirres_status mirres_autotune(mirres_context* ctx, mirres_scene* cons
     if (!ctx) return arg_error("ctx is NULL");
     MR_TRY(check_params(params));
     std::vector<SceneDev> sdev;
-    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev));
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev, params ? params->max_visits : 0));
     std::vector<ViewDev> vdev;
     uint64_t total = 0, max_view = 0;
     MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
@@ -831,7 +848,7 @@ static mirres_status backward_impl(mirres_context* ctx, mirres_scene* const* sce
     if (!ctx) return arg_error("ctx is NULL");
     MR_TRY(check_params(params));
     std::vector<SceneDev> sdev;
-    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev));
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev, params ? params->max_visits : 0));
     std::vector<ViewDev> vdev;
     uint64_t total = 0, max_view = 0;
     MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
@@ -920,7 +937,7 @@ extern "C" mirres_status mirres_light_demod(mirres_context* ctx, mirres_scene* c
     if (!ctx) return arg_error("ctx is NULL");
     MR_TRY(check_params(params));
     std::vector<SceneDev> sdev;
-    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev));
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev, params ? params->max_visits : 0));
     std::vector<ViewDev> vdev;
     uint64_t total = 0, max_view = 0;
     MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
@@ -999,9 +1016,8 @@ extern "C" mirres_status mirres_light_loss(mirres_context* ctx, const mirres_vie
     MR_CUDA(cudaMemcpyAsync(d_c, demod, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_ref, ref_images, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
     if (d_demod) MR_CUDA(cudaMemcpyAsync(d_dc, d_demod, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
-    mr_launch_light_loss(d_pixoff, n_views, total_pix, d_c, d_ref, weight, d_count, loss, d_demod ? d_dc : nullptr,
-                         ctx->sm_count, st);
-    MR_CUDA(cudaGetLastError());
+    MR_CUDA(mr_launch_light_loss(d_pixoff, n_views, total_pix, d_c, d_ref, weight, d_count, loss,
+                                 d_demod ? d_dc : nullptr, ctx->sm_count, st));
     ctx->host_launches += 2;
     return MIRRES_OK;
 }
@@ -1284,6 +1300,12 @@ extern "C" mirres_status mirres_get_counters(mirres_context* ctx, uint64_t out[8
     MR_CUDA(cudaMemcpy(h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 8; ++i) out[i] = (uint64_t)h[i];
     out[CNT_LAUNCH] = ctx->host_launches;
+    if (h[CNT_ERROR] != 0) {
+        g_err = std::to_string(h[CNT_ERROR]) +
+                " ray traversal(s) reached the iteration cap or overflowed the stack since the counters were "
+                "reset (malformed hierarchy or a max_visits below the tree's needs); those rays reported a miss";
+        return MIRRES_ERR_TIMEOUT;
+    }
     return MIRRES_OK;
 }
 

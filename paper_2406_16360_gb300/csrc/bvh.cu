@@ -92,6 +92,17 @@ __global__ void __launch_bounds__(256) k_bounds(const float* __restrict__ verts,
     }
 }
 
+__global__ void __launch_bounds__(256) k_check_indices(const int32_t* __restrict__ tris, int64_t n, int V,
+                                                       int32_t* bad)
+{
+    bool b = false;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = __ldg(tris + k);
+        b = b || i < 0 || i >= V;
+    }
+    if (__any_sync(MR_FULL, b) && (threadIdx.x & 31) == 0) *bad = 1;
+}
+
 __global__ void k_finish_bounds(const unsigned int* bounds, int F, float* tmin)
 {
     if (threadIdx.x != 0) return;
@@ -833,11 +844,25 @@ mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st)
         MR_TRY(bottom_up(s, st));
     }
     if (s->normals) MR_TRY(mr_vertex_normals(s, st));
+    return MIRRES_OK;
+}
+
+// Triangle indices are checked once, when the scene is created (and again on request), not
+// by every build: the build would have to wait for the check on the host. The build kernels
+// read an out-of-range index as vertex 0.
+mirres_status mr_check_indices(mirres_scene* s, cudaStream_t st)
+{
+    const int F = s->desc.n_tris;
+    if (F <= 0) return MIRRES_OK;
+    MR_CUDA(cudaMemsetAsync(s->bad, 0, sizeof(int32_t), st));
+    k_check_indices<<<std::min(grid_for(3 * F, 256), 4096), 256, 0, st>>>(s->desc.tris, 3 * (int64_t)F,
+                                                                         s->desc.n_verts, s->bad);
+    MR_CUDA(cudaGetLastError());
     int32_t bad = 0;
     MR_CUDA(cudaMemcpyAsync(&bad, s->bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MR_CUDA(cudaStreamSynchronize(st));
     if (bad) {
-        mr_set_error("mirres_bvh_build: a triangle index is outside [0, n_verts)");
+        mr_set_error("a triangle index is outside [0, n_verts)");
         return MIRRES_ERR_ARG;
     }
     return MIRRES_OK;

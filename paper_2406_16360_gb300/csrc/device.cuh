@@ -82,7 +82,22 @@ struct SceneDev {
     // and the adjoint's per-vertex accumulator of d loss / d vertex normal [V][3]
     const float4* vnrm;
     float* gvn;
+    // failure detection: a traversal that reaches its iteration cap (trav_cap node visits, 0 =
+    // 4 n_tris + 64) or overflows its stack ends as a miss and adds 1 to *err (the context's
+    // error counter, read back by mirres_get_counters)
+    unsigned long long* err;
+    int32_t trav_cap;
 };
+
+// iteration cap of one traversal
+__device__ __forceinline__ int trav_cap_of(const SceneDev& s)
+{
+    return s.trav_cap > 0 ? s.trav_cap : 4 * s.n_tris + 64;
+}
+__device__ __forceinline__ void trav_fail(const SceneDev& s)
+{
+    if (s.err) atomicAdd(s.err, 1ull);
+}
 
 struct ViewDev {
     float K[4];
@@ -540,8 +555,9 @@ __device__ __forceinline__ float slab(float3 lo, float3 hi, float3 oi, float3 in
 
 // Closest (any = false) or any hit with t in (tmin, tmax). `sstk` = this thread's shared
 // stack column (stride `sstride`). Returns the number of nodes visited (two box tests each),
-// or -1 if the iteration cap was reached (a malformed tree; the ray reports a miss); adds the
-// triangle tests to *ntri when given.
+// or -1 if the iteration cap was reached or the stack overflowed (a malformed tree: the ray
+// reports a miss and the scene's error counter is raised); adds the triangle tests to *ntri
+// when given.
 template <bool ANY>
 __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, int skip, float tmin, float tmax,
                                         Hit& best, uint32_t* sstk, int sstride, int* ntri = nullptr)
@@ -562,10 +578,11 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
     int sp = 0;
     int node = 0;
     int visited = 0;
-    const int cap = 4 * F + 64;
+    const int cap = trav_cap_of(s);
     while (true) {
         if (++visited > cap) {
             best.tri = -1;
+            trav_fail(s);
             return -1;
         }
         const float4 n0 = __ldg(s.nodes + 4 * (size_t)node);
@@ -589,8 +606,15 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
         if (gl && gr) {
             const bool lfirst = tl <= tr;
             const int nearc = lfirst ? ch.x : ch.y, farc = lfirst ? ch.y : ch.x;
-            if (sp < MR_SSTACK) sstk[sp * sstride] = (uint32_t)farc;
-            else lstk[min(sp - MR_SSTACK, MR_LSTACK - 1)] = (uint32_t)farc;
+            if (sp < MR_SSTACK) {
+                sstk[sp * sstride] = (uint32_t)farc;
+            } else if (sp < MR_SSTACK + MR_LSTACK) {
+                lstk[sp - MR_SSTACK] = (uint32_t)farc;
+            } else {  // deeper than any tree the builders keep: a malformed tree
+                best.tri = -1;
+                trav_fail(s);
+                return -1;
+            }
             ++sp;
             node = nearc;
         } else if (gl) {
@@ -600,7 +624,7 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
         } else {
             if (sp == 0) break;
             --sp;
-            node = (int)(sp < MR_SSTACK ? sstk[sp * sstride] : lstk[min(sp - MR_SSTACK, MR_LSTACK - 1)]);
+            node = (int)(sp < MR_SSTACK ? sstk[sp * sstride] : lstk[sp - MR_SSTACK]);
         }
     }
     return visited;
@@ -646,12 +670,13 @@ __device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, uint32_t* s
                                          int steps, int* ntri)
 {
     if (T.node < 0) return true;
-    const int cap = 4 * s.n_tris + 64;
+    const int cap = trav_cap_of(s);
     for (int k = 0; k < steps; ++k) {
         if (++T.visited > cap) {
             T.best.tri = -1;
             T.visited = -1;
             T.node = -1;
+            trav_fail(s);
             return true;
         }
         const int node = T.node;
@@ -681,8 +706,17 @@ __device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, uint32_t* s
         if (gl && gr) {
             const bool lfirst = tl <= tr;
             const int nearc = lfirst ? ch.x : ch.y, farc = lfirst ? ch.y : ch.x;
-            if (T.sp < MR_SSTACK) sstk[T.sp * sstride] = (uint32_t)farc;
-            else lstk[min(T.sp - MR_SSTACK, MR_LSTACK - 1)] = (uint32_t)farc;
+            if (T.sp < MR_SSTACK) {
+                sstk[T.sp * sstride] = (uint32_t)farc;
+            } else if (T.sp < MR_SSTACK + MR_LSTACK) {
+                lstk[T.sp - MR_SSTACK] = (uint32_t)farc;
+            } else {
+                T.best.tri = -1;
+                T.visited = -1;
+                T.node = -1;
+                trav_fail(s);
+                return true;
+            }
             ++T.sp;
             T.node = nearc;
         } else if (gl) {
@@ -695,7 +729,7 @@ __device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, uint32_t* s
                 return true;
             }
             --T.sp;
-            T.node = (int)(T.sp < MR_SSTACK ? sstk[T.sp * sstride] : lstk[min(T.sp - MR_SSTACK, MR_LSTACK - 1)]);
+            T.node = (int)(T.sp < MR_SSTACK ? sstk[T.sp * sstride] : lstk[T.sp - MR_SSTACK]);
         }
     }
     return false;

@@ -120,6 +120,8 @@ SceneDev mr_scene_dev(const mirres_scene* s);
 mirres_status mr_bvh_alloc(mirres_scene* s);
 void mr_bvh_free(mirres_scene* s);
 mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st);
+// checks every triangle index against n_verts (synchronises st); MIRRES_ERR_ARG if one is out of range
+mirres_status mr_check_indices(mirres_scene* s, cudaStream_t st);
 // interpolated normals: allocate (idempotent), recompute from the current vertices, and the
 // adjoint pass taking d loss / d vertex normal to the vertices of every incident face
 mirres_status mr_normals_alloc(mirres_scene* s);

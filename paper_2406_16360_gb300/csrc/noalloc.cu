@@ -76,9 +76,16 @@ extern "C" mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int3
     if (!params || params->ris_m < 1) return fail(MIRRES_ERR_ARG, "params missing or ris_m < 1");
     if (params->grad_mode != 0)
         return fail(MIRRES_ERR_ARG, "mirres_render_noalloc writes the PRIMARY-mode tape only (grad_mode 0)");
+    if (params->launch < 0 || params->launch > 2)
+        return fail(MIRRES_ERR_ARG, "launch must be 0, 1 or 2 (the persistent kernel runs whichever is given)");
     if (params->block != 0 && (params->block < 32 || params->block > 1024 || params->block % 32))
         return fail(MIRRES_ERR_ARG, "block must be 0 or a multiple of 32 in [32, 1024]");
     if (params->blocks_per_sm < 0) return fail(MIRRES_ERR_ARG, "blocks_per_sm must be >= 0");
+    if (params->max_visits < 0) return fail(MIRRES_ERR_ARG, "max_visits must be >= 0");
+    // reservoir reuse needs per-sample scratch that this entry point does not have (mirres_render
+    // offers it with the batched launch only)
+    if (params->reuse_k != 0 || params->temporal != 0)
+        return fail(MIRRES_ERR_ARG, "reservoir reuse (reuse_k > 0 or temporal > 0) is not available here");
     if (!images) return fail(MIRRES_ERR_ARG, "images is NULL");
     if (!tape) return fail(MIRRES_ERR_ARG, "a caller-owned tape is required (this entry point allocates nothing)");
     if (reinterpret_cast<uintptr_t>(tape) & 15) return fail(MIRRES_ERR_ARG, "tape must be 16-byte aligned");
@@ -91,6 +98,7 @@ extern "C" mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int3
         if (scenes[i]->ctx != ctx) return fail(MIRRES_ERR_ARG, "all scenes must share one context");
         if (!scenes[i]->built) return fail(MIRRES_ERR_STATE, "scene " + std::to_string(i) + " is not built");
         g_scenes[i] = mr_scene_dev(scenes[i]);
+        g_scenes[i].trav_cap = params->max_visits;
     }
     uint64_t total = 0, total_pix = 0;
     for (int i = 0; i < n_views; ++i) {
@@ -136,10 +144,17 @@ extern "C" mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int3
     MR_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), s));  // the previous call left it spent
     Rng rng;
     rng.set(params->seed_lo, params->seed_hi);
-    const int block = params->block ? params->block : 128;
-    const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy(block);
-    MR_CUDA(mr_launch_persistent(d_scenes, d_views, n_views, total, rng, params->ris_m, d_work, 32u * 8u, tape,
-                                 ctx->counters, block, per_sm * ctx->sm_count, s));
+    // the launch shape follows mirres_render's persistent launch: the compiled variant that fits
+    // (block, blocks_per_sm), or the context's autotuned variant and chunk when block is 0
+    int var = mr_persistent_pick(params->block, params->blocks_per_sm);
+    unsigned int chunk_w = 256;
+    if (params->block == 0 && ctx->tuned_variant >= 0) {
+        var = ctx->tuned_variant;
+        chunk_w = ctx->tuned_chunk;
+    }
+    const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy_v(var);
+    MR_CUDA(mr_launch_persistent_v(var, d_scenes, d_views, n_views, total, rng, params->ris_m, d_work, chunk_w, tape,
+                                   ctx->counters, per_sm * ctx->sm_count, s));
     mr_launch_resolve_all(d_views, n_views, d_pixoff, total_pix, d_images, tape, total, ctx->sm_count, s);
     MR_CUDA(cudaGetLastError());
     return MIRRES_OK;

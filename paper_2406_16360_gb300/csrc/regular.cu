@@ -378,13 +378,15 @@ void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_sm
         k_offset<<<grid_of(V, sms), 256, 0, st>>>(s->desc.verts, rest, V, w_offset, loss, grad);
 }
 
-void mr_launch_light_loss(const uint64_t* pix_off, int n_views, uint64_t total_pixels, const float* const* demod,
-                          const float* const* ref, float w, unsigned int* count, float* loss, float* const* d_demod,
-                          int sms, cudaStream_t st)
+cudaError_t mr_launch_light_loss(const uint64_t* pix_off, int n_views, uint64_t total_pixels,
+                                 const float* const* demod, const float* const* ref, float w, unsigned int* count,
+                                 float* loss, float* const* d_demod, int sms, cudaStream_t st)
 {
-    cudaMemsetAsync(count, 0, sizeof(unsigned int), st);
-    if (total_pixels == 0) return;
+    // |P| is counted from zero: a failed reset would scale the loss and its gradient wrongly
+    const cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess || total_pixels == 0) return e;
     k_light_count<<<grid_of((int64_t)total_pixels, sms), 256, 0, st>>>(pix_off, n_views, total_pixels, demod, count);
     k_light_apply<<<grid_of((int64_t)total_pixels, sms), 256, 0, st>>>(pix_off, n_views, total_pixels, demod, ref, w,
                                                                        count, loss, d_demod);
+    return cudaGetLastError();
 }

@@ -115,7 +115,7 @@ void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_sm
                             float* grad, int sms, cudaStream_t st);
 // L_light from the demodulated lighting: loss[0] += w mean |Y(c) - V(ref)| over the covered
 // pixels of every view (count is device scratch), d_demod = its gradient (overwritten)
-void mr_launch_light_loss(const uint64_t* pix_off, int n_views, uint64_t total_pixels,
+cudaError_t mr_launch_light_loss(const uint64_t* pix_off, int n_views, uint64_t total_pixels,
                           const float* const* demod, const float* const* ref, float w, unsigned int* count,
                           float* loss, float* const* d_demod, int sms, cudaStream_t st);
 

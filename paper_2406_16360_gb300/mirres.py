@@ -17,6 +17,7 @@ from . import build as _build
 
 __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_view", "make_params",
            "mirres_context_create", "mirres_context_destroy", "mirres_scene_create", "mirres_scene_destroy",
+           "mirres_scene_validate",
            "mirres_bvh_build", "mirres_bvh_refit", "mirres_bvh_set_builder", "MIRRES_BVH_LBVH", "MIRRES_BVH_PLOC",
            "mirres_scene_set_normals", "MIRRES_NORMALS_FACE", "MIRRES_NORMALS_INTERPOLATED", "mirres_tape_bytes", "mirres_tape_bytes_mode",
            "mirres_reuse_history_bytes", "mirres_render",
@@ -27,7 +28,7 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_get_work_counters", "EawtParams", "mirres_eawt_record_bytes", "mirres_gbuffer", "mirres_eawt",
            "mirres_eawt_backward", "mirres_mesh_regularizers", "LkParams", "mirres_material_smoothness",
            "mirres_light_demod", "mirres_light_loss", "mirres_light_backward",
-           "mirres_reset_counters", "mirres_last_error", "library_path"]
+           "mirres_reset_counters", "mirres_last_error", "library_path", "mirres_peak_fp32", "mirres_peak_l2"]
 
 # limits of mirres_render_noalloc (include/mirres.h)
 MIRRES_TAPE_BYTES_PER_SAMPLE = 68  # 17 words per path sample, one array per word
@@ -68,7 +69,7 @@ class Params(C.Structure):
                 ("launch", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("flags", C.c_int32), ("reuse_k", C.c_int32), ("reuse_radius", C.c_int32),
                 ("temporal", C.c_int32), ("temporal_cap", C.c_int32), ("reuse_history", C.c_void_p),
-                ("reuse_history_bytes", C.c_uint64)]
+                ("reuse_history_bytes", C.c_uint64), ("max_visits", C.c_int32)]
 
 
 class EawtParams(C.Structure):
@@ -107,6 +108,7 @@ def lib():
                 "mirres_context_destroy": (st, [vp]),
                 "mirres_scene_create": (st, [vp, C.POINTER(SceneDesc), C.POINTER(vp)]),
                 "mirres_scene_destroy": (st, [vp]),
+                "mirres_scene_validate": (st, [vp, vp]),
                 "mirres_bvh_build": (st, [vp, vp]),
                 "mirres_bvh_refit": (st, [vp, vp]),
                 "mirres_bvh_set_builder": (st, [vp, i32]),
@@ -147,6 +149,8 @@ def lib():
                 "mirres_get_work_counters": (st, [vp, C.POINTER(C.c_uint64)]),
                 "mirres_reset_counters": (st, [vp]),
                 "mirres_last_error": (C.c_char_p, []),
+                "mirres_peak_fp32": (C.c_int, [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+                "mirres_peak_l2": (C.c_int, [C.c_uint64, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -212,14 +216,15 @@ def make_view(K, c2w, width, height, spp, bounces, scene=0) -> View:
 
 
 def make_params(ris_m, seed=0, launch=0, block=0, blocks_per_sm=0, grad_mode=0, flags=0, reuse=(0, 0), temporal=0,
-                temporal_cap=20, history=None) -> Params:
+                temporal_cap=20, history=None, max_visits=0) -> Params:
     """reuse = (neighbours, radius) of the spatial reuse at the primary vertex, (0, 0) = off;
     temporal = 1 records the reservoir history into `history` (a CUDA tensor of
-    mirres_reuse_history_bytes), 2 merges it first"""
+    mirres_reuse_history_bytes), 2 merges it first; max_visits = iteration cap of one ray
+    traversal (0 = the library's default)"""
     hb = 0 if history is None else history.numel() * history.element_size()
     return Params(int(ris_m), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(grad_mode), int(launch), int(block),
                   int(blocks_per_sm), int(flags), int(reuse[0]), int(reuse[1]), int(temporal), int(temporal_cap),
-                  None if history is None else history.data_ptr(), int(hb))
+                  None if history is None else history.data_ptr(), int(hb), int(max_visits))
 
 
 def _views(views):
@@ -256,6 +261,10 @@ def mirres_scene_create(ctx: Context, verts, tris, tri_uv, albedo, roughness, me
 
 def mirres_scene_destroy(scene: Scene):
     scene.close()
+
+
+def mirres_scene_validate(scene: Scene, stream=None):
+    _check("mirres_scene_validate", lib().mirres_scene_validate(scene.handle, _stream(stream)))
 
 
 def mirres_bvh_build(scene: Scene, stream=None):
@@ -463,3 +472,21 @@ def mirres_get_work_counters(ctx: Context):
 
 def mirres_reset_counters(ctx: Context):
     _check("mirres_reset_counters", lib().mirres_reset_counters(ctx.handle))
+
+
+def mirres_peak_fp32(iters: int = 1 << 18):
+    """measured FP32 FMA rate of the current device: (FLOP/s, ms of the timed launch)"""
+    f, ms = C.c_double(), C.c_double()
+    e = lib().mirres_peak_fp32(int(iters), C.byref(f), C.byref(ms))
+    if e != 0:
+        raise RuntimeError(f"mirres_peak_fp32: CUDA error {e}")
+    return f.value, ms.value
+
+
+def mirres_peak_l2(nbytes: int = 32 << 20, passes: int = 40):
+    """measured bandwidth of loads served by L2 on the current device: (bytes/s, ms)"""
+    b, ms = C.c_double(), C.c_double()
+    e = lib().mirres_peak_l2(int(nbytes), int(passes), C.byref(b), C.byref(ms))
+    if e != 0:
+        raise RuntimeError(f"mirres_peak_l2: CUDA error {e}")
+    return b.value, ms.value

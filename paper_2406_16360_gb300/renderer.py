@@ -74,17 +74,18 @@ class GpuWorkload:
         return torch.empty(n // 4, device=self.device, dtype=torch.int32)
 
     def params(self, launch=0, seed=None, block=0, blocks_per_sm=0, flags=0, grad_mode=0, reuse=(0, 0), temporal=0,
-               temporal_cap=20, history=None):
+               temporal_cap=20, history=None, max_visits=0):
         s = self.workload.seed if seed is None else seed
         return M.make_params(self.workload.ris_m, s, launch, block, blocks_per_sm, grad_mode=grad_mode, flags=flags,
-                             reuse=reuse, temporal=temporal, temporal_cap=temporal_cap, history=history)
+                             reuse=reuse, temporal=temporal, temporal_cap=temporal_cap, history=history,
+                             max_visits=max_visits)
 
     def new_history(self):
         """reservoir history for temporal reuse (kept across renders of the same views)"""
         return torch.zeros(M.mirres_reuse_history_bytes(self.views) // 4, device=self.device, dtype=torch.int32)
 
     def render(self, launch=0, images=None, tape=None, seed=None, block=0, blocks_per_sm=0, flags=0, stream=None,
-               grad_mode=0, reuse=(0, 0), temporal=0, temporal_cap=20, history=None):
+               grad_mode=0, reuse=(0, 0), temporal=0, temporal_cap=20, history=None, max_visits=0):
         """Forward render; grad_mode 1 (FULL) also records every vertex for the FULL adjoint;
         reuse = (neighbours, radius) turns on spatial reuse at the primary vertex; temporal = 1
         records the reservoir history into `history`, 2 merges it first."""
@@ -92,7 +93,7 @@ class GpuWorkload:
         tape = tape if tape is not None else self.new_tape(grad_mode)
         M.mirres_render(self.ctx, [s.handle for s in self.scenes], self.views,
                         self.params(launch, seed, block, blocks_per_sm, flags, grad_mode, reuse, temporal,
-                                    temporal_cap, history), images, tape, stream)
+                                    temporal_cap, history, max_visits), images, tape, stream)
         return images, tape
 
     def tune_key(self):

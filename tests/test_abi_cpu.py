@@ -7,7 +7,8 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "mirres.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -18,15 +19,20 @@ def lib():
 
 
 def declared():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mirres_[a-z0-9_]+)\s*\(", text)))
+    """every entry point declared in include/*.h"""
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(mirres_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared()
     for n in ("mirres_context_create", "mirres_scene_create", "mirres_bvh_build", "mirres_bvh_refit",
-              "mirres_render", "mirres_backward", "mirres_last_error"):
+              "mirres_render", "mirres_backward", "mirres_last_error", "mirres_scene_validate",
+              "mirres_peak_fp32", "mirres_peak_l2"):
         assert n in names
 
 

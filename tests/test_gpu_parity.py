@@ -102,17 +102,51 @@ def test_refit_equals_rebuild(M, ctx):
 
 
 def test_bad_index_rejected(M, ctx):
+    """indices are checked when the scene is created and on request, not by every build (which
+    then needs no host synchronisation)"""
     sc = synth.config1().scenes[0]
     dev = torch.device("cuda")
     t = torch.as_tensor(sc.tris, device=dev).contiguous()
     t[5, 1] = 10 ** 6
     args = [torch.as_tensor(a, device=dev).contiguous() for a in (sc.verts, t, sc.tri_uv, sc.albedo, sc.roughness,
                                                                  sc.metallic, sc.env)]
-    s = M.mirres_scene_create(ctx, *args)
     with pytest.raises(M.MirresError) as e:
-        M.mirres_bvh_build(s)
+        M.mirres_scene_create(ctx, *args)
+    assert e.value.status == 1 and "n_verts" in str(e.value)
+    # a valid scene whose caller-owned indices go bad later: mirres_scene_validate finds it
+    t[5, 1] = 0
+    s = M.mirres_scene_create(ctx, *args)
+    M.mirres_bvh_build(s)
+    M.mirres_scene_validate(s)
+    t[7, 2] = -3
+    with pytest.raises(M.MirresError) as e:
+        M.mirres_scene_validate(s)
     assert e.value.status == 1
     s.close()
+
+
+def test_traversal_cap_reports_timeout(M, ctx):
+    """failure detection: a traversal that reaches its iteration cap ends as a miss and raises the
+    context's error counter, which mirres_get_counters reports as MIRRES_ERR_TIMEOUT; the context
+    stays usable (no fault, no hang) and a reset clears the error"""
+    from paper_2406_16360_gb300.renderer import GpuWorkload
+    w = synth.config1(width=24, height=16)
+    gw = GpuWorkload(w, 0, ctx=ctx)
+    M.mirres_reset_counters(ctx)
+    for launch in (0, 1, 2):
+        gw.render(launch=launch, max_visits=3)
+        torch.cuda.synchronize()
+        with pytest.raises(M.MirresError) as e:
+            M.mirres_get_counters(ctx)
+        assert e.value.status == 4 and "iteration cap" in str(e.value)
+        M.mirres_reset_counters(ctx)
+    images, _ = gw.render(launch=1)
+    torch.cuda.synchronize()
+    c = M.mirres_get_counters(ctx)
+    assert c[7] == 0 and c[0] == w.samples
+    assert torch.isfinite(images[0]).all()
+    for s in gw.scenes:
+        s.close()
 
 
 @pytest.mark.parametrize("which", ["config1", "config2"])

@@ -54,6 +54,11 @@ def test_noalloc_matches_render_on_two_calls():
     assert e.value.status == 1 and str(M.MIRRES_NOALLOC_MAX_VIEWS) in str(e.value)
     with pytest.raises(M.MirresError):
         M.mirres_render_noalloc([s.handle for s in gw.scenes], w.views, gw.params(1), gw.new_images(), None)
+    # reservoir reuse needs per-sample scratch this entry point does not have: refused, not ignored
+    with pytest.raises(M.MirresError) as e:
+        M.mirres_render_noalloc([s.handle for s in gw.scenes], w.views, gw.params(1, reuse=(1, 2)),
+                                gw.new_images(), gw.new_tape())
+    assert e.value.status == 1 and "reuse" in str(e.value)
     for s in gw.scenes:
         s.close()
     ctx.close()
