@@ -295,7 +295,7 @@ def main():
     peak_clocks = peak_clk.stop()
     peaks = {"fp32_tflops": fp32_flops / 1e12, "fp32_basis": "FMA microbenchmark (mirres_peak_fp32): 16 independent "
              f"chains per thread, {sm_count} SMs x 8 blocks of 256, {fp32_ms:.1f} ms timed launch",
-             "l2_gbs": l2_bps / 1e9, "l2_basis": "32 MiB L2-resident buffer, 40 passes of 16-byte ld.global.cg "
+             "l2_gbs": l2_bps / 1e9, "l2_basis": "32 MiB L2-resident buffer, 400 passes of 16-byte ld.global.cg "
              f"loads over all SMs (mirres_peak_l2), {l2_ms:.1f} ms timed launch",
              "sm_count": sm_count, "nominal_fp32_tflops_at_max_clock": sm_count * 128 * 2 * 2.070e9 / 1e12,
              "clocks_during_peaks": peak_clocks}

@@ -1324,7 +1324,7 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
 /* ---------------------------------------------------------------------------------------
  * adjoint of one sample (PRIMARY mode, Sec. 4.2 last sentence and Appendix C limitations)
  * ------------------------------------------------------------------------------------- */
-enum { GB_ALB = 0, GB_RGH, GB_MET, GB_ENV, GB_VERT, GB_ALB_S, GB_RGH_S, GB_MET_S, GB_N };
+enum { GB_ALB = 0, GB_RGH, GB_MET, GB_ENV, GB_VERT, GB_ALB_S, GB_RGH_S, GB_MET_S, GB_VERT_S, GB_N };
 typedef struct { int32_t buf; int64_t idx; double val; } Entry;
 typedef struct { Entry* e; size_t n, cap; } Sparse;
 
@@ -1339,52 +1339,86 @@ static void sp_add(Sparse* sp, int buf, int64_t idx, double val)
     sp->n++;
 }
 
-/* demod = 0: the sample's radiance. demod = 1: its demodulated lighting at the primary vertex
- * (the same terms with the kind-2 lobes; an escaping primary ray has none) */
-static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], int demod, Sparse* sp)
+/* Sparse lists of vertex terms that can be compared entry by entry: zero terms are kept (the
+ * entry structure must not depend on the values) */
+static void sp_put(Sparse* sp, int buf, int64_t idx, double val)
+{
+    if (sp->n == sp->cap) {
+        sp->cap = sp->cap ? 2 * sp->cap : 256;
+        sp->e = (Entry*)realloc(sp->e, sizeof(Entry) * sp->cap);
+    }
+    sp->e[sp->n].buf = buf; sp->e[sp->n].idx = idx; sp->e[sp->n].val = val;
+    sp->n++;
+}
+
+/* FP32 sensitivity of the vertex gradient (test tolerance only): one input of the primary
+ * vertex's adjoint moved by the rounding error an FP32 evaluation of it may carry. comp 0-2:
+ * the camera direction; 3-4: the barycentrics (by the FP32 error of a single-precision ray's
+ * intersection, du / dv); 5-7: the selected light direction; 8-10: the continuation direction;
+ * 11-13: the shading normal; sgn = +1 or -1. */
+typedef struct { int comp; double sgn, du, dv, dn; } Pert;
+#define U32 (1.0 / 16777216.0)
+
+/* a unit vector with component k moved by rel, renormalised */
+static v3 nudge(v3 a, int k, double rel)
+{
+    double q[3] = {a.x, a.y, a.z};
+    q[k] += rel;
+    return vnorm(V3(q[0], q[1], q[2]));
+}
+
+/* The primary vertex's adjoint of one sample (PRIMARY mode, the sample's primary triangle hit).
+ * tex = 1: every term (env, textures with their FP32 sensitivity, vertices); tex = 0: only the
+ * vertex terms, for the FP32 sensitivity (pt = the perturbed input, NULL = none). */
+static void prim_grad(const Ctx* c, const Rec* rec, const double g[3], int kind, const Pert* pt, int tex, Sparse* sp)
 {
     const orc_scene* s = c->s;
-    const int kind = demod ? 2 : c->p->brdf_kind;
-    if (rec->prim_tri < 0) {
-        if (demod) return;
-        for (int k = 0; k < 3; ++k) sp_add(sp, GB_ENV, 3 * (int64_t)rec->bg_texel + k, g[k]);
-        return;
+    void (*put)(Sparse*, int, int64_t, double) = tex ? sp_add : sp_put;
+    v3 d0 = rec->d0, y = rec->y, wc = rec->wc;
+    double pu = rec->pu, pv = rec->pv;
+    if (pt) {
+        const int k = pt->comp;
+        if (k < 3) d0 = nudge(d0, k, pt->sgn * 4.0 * U32);
+        else if (k == 3) pu += pt->sgn * pt->du;
+        else if (k == 4) pv += pt->sgn * pt->dv;
+        else if (k < 8) y = nudge(y, k - 5, pt->sgn * 8.0 * U32);
+        else if (k < 11) wc = nudge(wc, k - 8, pt->sgn * 8.0 * U32);
     }
     Shade sh;
-    shade_at(s, rec->prim_tri, rec->pu, rec->pv, rec->pt, rec->d0, &sh, NULL);
-    v3 wo = vscale(rec->d0, -1.0);
+    shade_at(s, rec->prim_tri, pu, pv, rec->pt, d0, &sh, NULL);
+    if (pt && pt->comp >= 11) sh.n = nudge(sh.n, pt->comp - 11, pt->sgn * pt->dn);
+    v3 wo = vscale(d0, -1.0);
     double gm[8] = {0, 0, 0, 0, 0, 0, 0, 0}, tmp[8];
     /* direct_1 = V W L_env(y) (f_r cos)(y) */
     if (rec->sel >= 0 && rec->WV != 0.0) {
         double fc[3], gq[3];
-        brdf_cos(sh.n, wo, rec->y, sh.alb, sh.rgh, sh.met, kind, fc);
+        brdf_cos(sh.n, wo, y, sh.alb, sh.rgh, sh.met, kind, fc);
         for (int k = 0; k < 3; ++k) {
             double le = s->env[3 * rec->y_texel + k];
-            sp_add(sp, GB_ENV, 3 * (int64_t)rec->y_texel + k, g[k] * rec->WV * fc[k]);
+            if (tex) sp_add(sp, GB_ENV, 3 * (int64_t)rec->y_texel + k, g[k] * rec->WV * fc[k]);
             gq[k] = g[k] * rec->WV * le;
         }
-        brdf_cos_grad(sh.n, wo, rec->y, sh.alb, sh.rgh, sh.met, kind, gq, tmp);
+        brdf_cos_grad(sh.n, wo, y, sh.alb, sh.rgh, sh.met, kind, gq, tmp);
         for (int k = 0; k < 8; ++k) gm[k] += tmp[k];
     }
     /* beta_1 L_ind = (f_r cos)(wc) / p_ind * L_ind */
     if (rec->has_cont) {
         double gq[3];
         for (int k = 0; k < 3; ++k) gq[k] = g[k] * rec->Lind[k] / rec->p_ind;
-        brdf_cos_grad(sh.n, wo, rec->wc, sh.alb, sh.rgh, sh.met, kind, gq, tmp);
+        brdf_cos_grad(sh.n, wo, wc, sh.alb, sh.rgh, sh.met, kind, gq, tmp);
         for (int k = 0; k < 8; ++k) gm[k] += tmp[k];
     }
     const double* uv = s->UV + 6 * sh.tri;
-    v3 md = vscale(rec->d0, -1.0);
+    v3 md = vscale(d0, -1.0);
     /* A = [e1 | e2 | -d]; rows of A^-1 are (e2 x -d, -d x e1, e1 x e2) / det */
     v3 r0 = vcross(sh.e2, md), r1 = vcross(md, sh.e1);
     double det = vdot(sh.e1, r0);
-    /* FP32 sensitivity (test tolerance only): barycentric error of a single-precision primary
-     * ray, ~8 u (t + |o - v0| + |o|) |row of A^-1|, mapped to the fractional texel position */
-    {
-        const double u32 = 1.0 / 16777216.0;
+    if (tex) {
+        /* FP32 sensitivity (test tolerance only): barycentric error of a single-precision primary
+         * ray, ~8 u (t + |o - v0| + |o|) |row of A^-1|, mapped to the fractional texel position */
         v3 o = vload(c->o), a, b, cc;
         tri_verts(s, sh.tri, &a, &b, &cc);
-        double lever = 8.0 * u32 * (sh.t + vlen(vsub(o, a)) + vlen(o)) / fabs(det);
+        double lever = 8.0 * U32 * (sh.t + vlen(vsub(o, a)) + vlen(o)) / fabs(det);
         double du = lever * vlen(r0), dv = lever * vlen(r1);
         double dfx = s->tw * (fabs(uv[2] - uv[0]) * du + fabs(uv[4] - uv[0]) * dv);
         double dfy = s->th * (fabs(uv[3] - uv[1]) * du + fabs(uv[5] - uv[1]) * dv);
@@ -1403,11 +1437,13 @@ static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], int dem
         double w = sh.tp.w[k];
         double dot = 0.0;
         for (int ch = 0; ch < 3; ++ch) {
-            sp_add(sp, GB_ALB, 3 * (int64_t)i + ch, w * gm[ch]);
+            if (tex) sp_add(sp, GB_ALB, 3 * (int64_t)i + ch, w * gm[ch]);
             dot += gm[ch] * s->alb[3 * i + ch];
         }
-        sp_add(sp, GB_RGH, i, w * gm[3]);
-        sp_add(sp, GB_MET, i, w * gm[4]);
+        if (tex) {
+            sp_add(sp, GB_RGH, i, w * gm[3]);
+            sp_add(sp, GB_MET, i, w * gm[4]);
+        }
         dot += gm[3] * s->rgh[i] + gm[4] * s->met[i];
         gsu += sh.tp.dw_dx[k] * dot;
         gsv += sh.tp.dw_dy[k] * dot;
@@ -1451,9 +1487,9 @@ static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], int dem
                 v3 gf[3] = {vscale(vadd(ge1, ge2), -1.0), ge1, ge2};
                 for (int m = 0; m < 3; ++m) {
                     int vj = s->F[3 * f + m];
-                    sp_add(sp, GB_VERT, 3 * (int64_t)vj + 0, gf[m].x);
-                    sp_add(sp, GB_VERT, 3 * (int64_t)vj + 1, gf[m].y);
-                    sp_add(sp, GB_VERT, 3 * (int64_t)vj + 2, gf[m].z);
+                    put(sp, GB_VERT, 3 * (int64_t)vj + 0, gf[m].x);
+                    put(sp, GB_VERT, 3 * (int64_t)vj + 1, gf[m].y);
+                    put(sp, GB_VERT, 3 * (int64_t)vj + 2, gf[m].z);
                 }
             }
         }
@@ -1469,10 +1505,76 @@ static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], int dem
     }
     for (int k = 0; k < 3; ++k) {
         int vi = s->F[3 * sh.tri + k];
-        sp_add(sp, GB_VERT, 3 * (int64_t)vi + 0, gvert[k].x);
-        sp_add(sp, GB_VERT, 3 * (int64_t)vi + 1, gvert[k].y);
-        sp_add(sp, GB_VERT, 3 * (int64_t)vi + 2, gvert[k].z);
+        put(sp, GB_VERT, 3 * (int64_t)vi + 0, gvert[k].x);
+        put(sp, GB_VERT, 3 * (int64_t)vi + 1, gvert[k].y);
+        put(sp, GB_VERT, 3 * (int64_t)vi + 2, gvert[k].z);
     }
+}
+
+/* FP32 sensitivity of one sample's vertex terms (test tolerance only): for every input of
+ * prim_grad, the larger change of each vertex term when that input moves by +- its FP32
+ * rounding scale, summed over the inputs (a first-order bound on what a single-precision
+ * evaluation of the same formulas may differ by; it also covers a texture coordinate that
+ * sits within rounding of a texel centre, where the bilinear derivative jumps). */
+static void vert_sens(const Ctx* c, const Rec* rec, const double g[3], int kind, Sparse* sp)
+{
+    const orc_scene* s = c->s;
+    Shade sh;
+    shade_at(s, rec->prim_tri, rec->pu, rec->pv, rec->pt, rec->d0, &sh, NULL);
+    v3 md = vscale(rec->d0, -1.0);
+    v3 r0 = vcross(sh.e2, md), r1 = vcross(md, sh.e1);
+    double det = vdot(sh.e1, r0);
+    v3 o = vload(c->o), a, b, cc;
+    tri_verts(s, sh.tri, &a, &b, &cc);
+    /* rounding of a single-precision Moller-Trumbore solve: a few units of |o - v0| |row| and
+     * |o| |row| over det (the direction's own rounding is comp 0-2) */
+    double lever = 3.0 * U32 * (vlen(vsub(o, a)) + vlen(o)) / fabs(det);
+    Pert pt;
+    pt.du = lever * vlen(r0);
+    pt.dv = lever * vlen(r1);
+    /* the face normal's FP32 direction error grows with the cross product's cancellation; the
+     * interpolated normal is a blend of three FP32 unit vectors */
+    pt.dn = sh.interp ? 8.0 * U32 : 4.0 * U32 * vlen(sh.e1) * vlen(sh.e2) / vlen(sh.N);
+    Sparse base = {0}, pe = {0};
+    /* tex = 0 keeps zero terms, so the lists of the perturbed evaluations line up entry by entry */
+    prim_grad(c, rec, g, kind, NULL, 0, &base);
+    double* acc = (double*)calloc(base.n ? base.n : 1, sizeof(double));
+    double* mx = (double*)calloc(base.n ? base.n : 1, sizeof(double));
+    const int has_y = rec->sel >= 0 && rec->WV != 0.0;
+    for (int comp = 0; comp < 14; ++comp) {
+        if (comp >= 5 && comp < 8 && !has_y) continue;
+        if (comp >= 8 && comp < 11 && !rec->has_cont) continue;
+        for (size_t e = 0; e < base.n; ++e) mx[e] = 0.0;
+        for (int sg = -1; sg <= 1; sg += 2) {
+            pt.comp = comp;
+            pt.sgn = (double)sg;
+            pe.n = 0;
+            prim_grad(c, rec, g, kind, &pt, 0, &pe);
+            const size_t n = pe.n < base.n ? pe.n : base.n;
+            for (size_t e = 0; e < n; ++e) mx[e] = dmax(mx[e], fabs(pe.e[e].val - base.e[e].val));
+        }
+        for (size_t e = 0; e < base.n; ++e) acc[e] += mx[e];
+    }
+    for (size_t e = 0; e < base.n; ++e) sp_add(sp, GB_VERT_S, base.e[e].idx, acc[e]);
+    free(acc);
+    free(mx);
+    free(base.e);
+    free(pe.e);
+}
+
+/* demod = 0: the sample's radiance. demod = 1: its demodulated lighting at the primary vertex
+ * (the same terms with the kind-2 lobes; an escaping primary ray has none). vsens = 1 also
+ * accumulates the FP32 sensitivity of the vertex terms (GB_VERT_S). */
+static void sample_grad(const Ctx* c, const Rec* rec, const double g[3], int demod, int vsens, Sparse* sp)
+{
+    const int kind = demod ? 2 : c->p->brdf_kind;
+    if (rec->prim_tri < 0) {
+        if (demod) return;
+        for (int k = 0; k < 3; ++k) sp_add(sp, GB_ENV, 3 * (int64_t)rec->bg_texel + k, g[k]);
+        return;
+    }
+    prim_grad(c, rec, g, kind, NULL, 1, sp);
+    if (vsens) vert_sens(c, rec, g, kind, sp);
 }
 
 /* FULL mode: the vertices after the primary one (the gradients of indirect rays that Sec. 4.2
@@ -1638,11 +1740,13 @@ typedef struct {
     int mode;  /* 0 render, 1 backward, 2 detached */
     int demod; /* 1: the demodulated lighting of the primary vertex (L_light) instead of the
                 * radiance; mode 0 then writes [c_d + c_s (3), fraction of samples that hit] */
+    int vsens; /* mode 1: also the FP32 sensitivity of the vertex terms */
     Ctx c;
     const orc_scene* ev;
     const int32_t* pixels;
     int32_t i0, i1;
     double* out_rgb; double* out_margin; int32_t* out_prim;
+    double* out_srgb; double* out_smargin; /* per sample: radiance [n][spp][3], margin [n][spp] */
     const double* d_rgb;
     Sparse sp;
     int64_t cnt[ORC_NCOUNT];
@@ -1661,7 +1765,13 @@ static void* job_run(void* arg)
         Margin* pmg = (jb->mode == 0 && jb->out_margin && c->p->want_margin) ? &mg : NULL;
         for (int smp = 0; smp < spp; ++smp) {
             Rec rec;
-            path_sample(c, px, py, smp, &rec, pmg, jb->cnt);
+            Margin smg = {INFINITY, 0};
+            path_sample(c, px, py, smp, &rec, pmg ? &smg : NULL, jb->cnt);
+            if (pmg && smg.m < mg.m) mg = smg;
+            if (jb->mode == 0 && !jb->demod && jb->out_srgb) {
+                for (int k = 0; k < 3; ++k) jb->out_srgb[3 * ((size_t)i * spp + smp) + k] = rec.rgb[k];
+                if (jb->out_smargin) jb->out_smargin[(size_t)i * spp + smp] = pmg ? smg.m : INFINITY;
+            }
             if (jb->mode == 0 && jb->demod) {
                 double o3[3];
                 sample_detached(c, c->s, &rec, 1, o3);
@@ -1674,7 +1784,7 @@ static void* job_run(void* arg)
                 double g[3];
                 for (int k = 0; k < 3; ++k) g[k] = jb->d_rgb[3 * (size_t)i + k] / spp;
                 if (g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0) {
-                    sample_grad(c, &rec, g, jb->demod, &jb->sp);
+                    sample_grad(c, &rec, g, jb->demod, jb->vsens, &jb->sp);
                     if (c->p->grad_mode == 1) sample_grad_secondary(c, &rec, g, &jb->sp);
                 }
             } else {
@@ -1698,7 +1808,8 @@ static void* job_run(void* arg)
 
 static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev, const orc_view* v,
                     const orc_params* p, const int32_t* pixels, int32_t n, double* out_rgb, double* out_margin,
-                    int32_t* out_prim, const double* d_rgb, const orc_grads* g, int64_t* counts)
+                    int32_t* out_prim, const double* d_rgb, const orc_grads* g, int64_t* counts,
+                    double* out_srgb, double* out_smargin)
 {
     if (demod && p && p->grad_mode != 0) return 1;
     if (!s || !v || !p || v->width < 1 || v->height < 1 || v->spp < 1 || v->bounces < 1 || p->ris_m < 0) return 1;
@@ -1716,12 +1827,14 @@ static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev
         Job* jb = &jobs[t];
         jb->mode = mode;
         jb->demod = demod;
+        jb->vsens = (mode == 1 && g && g->verts_sens) ? 1 : 0;
         ctx_init(&jb->c, s, v, p);
         jb->ev = ev;
         jb->pixels = pixels;
         jb->i0 = (int32_t)((int64_t)n * t / nt);
         jb->i1 = (int32_t)((int64_t)n * (t + 1) / nt);
         jb->out_rgb = out_rgb; jb->out_margin = out_margin; jb->out_prim = out_prim;
+        jb->out_srgb = out_srgb; jb->out_smargin = out_smargin;
         jb->d_rgb = d_rgb;
     }
     if (nt == 1) job_run(&jobs[0]);
@@ -1733,9 +1846,9 @@ static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev
         if (counts) for (int k = 0; k < ORC_NCOUNT; ++k) counts[k] += jobs[t].cnt[k];
         if (mode == 1 && g) {
             double* dst[GB_N] = {g->albedo, g->roughness, g->metallic, g->env, g->verts,
-                                 g->albedo_sens, g->roughness_sens, g->metallic_sens};
+                                 g->albedo_sens, g->roughness_sens, g->metallic_sens, g->verts_sens};
             double* dab[GB_N] = {g->albedo_abs, g->roughness_abs, g->metallic_abs, g->env_abs, g->verts_abs,
-                                 NULL, NULL, NULL};
+                                 NULL, NULL, NULL, NULL};
             for (size_t e = 0; e < jobs[t].sp.n; ++e) {
                 const Entry* en = &jobs[t].sp.e[e];
                 if (dst[en->buf]) dst[en->buf][en->idx] += en->val;
@@ -1749,25 +1862,34 @@ static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev
     return 0;
 }
 
+int orc_render_samples(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
+                       int32_t n_pixels, double* out_rgb, double* out_margin, double* out_sample_rgb,
+                       double* out_sample_margin, int64_t* counts)
+{
+    if (!out_rgb || !out_sample_rgb) return 1;
+    return run_jobs(0, 0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, NULL, NULL, NULL, counts,
+                    out_sample_rgb, out_sample_margin);
+}
+
 int orc_render(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels, int32_t n_pixels,
                double* out_rgb, double* out_margin, int32_t* out_prim_tri, int64_t* counts)
 {
     if (!out_rgb) return 1;
-    return run_jobs(0, 0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, out_prim_tri, NULL, NULL, counts);
+    return run_jobs(0, 0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, out_prim_tri, NULL, NULL, counts, NULL, NULL);
 }
 
 int orc_backward(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels, int32_t n_pixels,
                  const double* d_rgb, const orc_grads* g, int64_t* counts)
 {
     if (!d_rgb || !g) return 1;
-    return run_jobs(1, 0, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_rgb, g, counts);
+    return run_jobs(1, 0, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_rgb, g, counts, NULL, NULL);
 }
 
 int orc_render_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v, const orc_params* p,
                         const int32_t* pixels, int32_t n_pixels, double* out_rgb)
 {
     if (!eval || !out_rgb) return 1;
-    return run_jobs(2, 0, frozen, eval, v, p, pixels, n_pixels, out_rgb, NULL, NULL, NULL, NULL, NULL);
+    return run_jobs(2, 0, frozen, eval, v, p, pixels, n_pixels, out_rgb, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -1780,21 +1902,21 @@ int orc_light_demod(const orc_scene* s, const orc_view* v, const orc_params* p, 
                     int32_t n_pixels, double* out, double* out_margin, int64_t* counts)
 {
     if (!out) return 1;
-    return run_jobs(0, 1, s, NULL, v, p, pixels, n_pixels, out, out_margin, NULL, NULL, NULL, counts);
+    return run_jobs(0, 1, s, NULL, v, p, pixels, n_pixels, out, out_margin, NULL, NULL, NULL, counts, NULL, NULL);
 }
 
 int orc_light_backward(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
                        int32_t n_pixels, const double* d_c, const orc_grads* g, int64_t* counts)
 {
     if (!d_c || !g) return 1;
-    return run_jobs(1, 1, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_c, g, counts);
+    return run_jobs(1, 1, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_c, g, counts, NULL, NULL);
 }
 
 int orc_light_demod_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v,
                              const orc_params* p, const int32_t* pixels, int32_t n_pixels, double* out)
 {
     if (!eval || !out) return 1;
-    return run_jobs(2, 1, frozen, eval, v, p, pixels, n_pixels, out, NULL, NULL, NULL, NULL, NULL);
+    return run_jobs(2, 1, frozen, eval, v, p, pixels, n_pixels, out, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ---------------------------------------------------------------------------------------

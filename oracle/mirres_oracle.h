@@ -73,6 +73,12 @@ typedef struct {
      * neighbouring texels); a bound on how far an FP32 evaluation may legitimately differ.
      * May be NULL. */
     double* albedo_sens; double* roughness_sens; double* metallic_sens;
+    /* FP32 sensitivity of the vertex terms of the PRIMARY-mode adjoint: sum over samples and
+     * over the adjoint's inputs (camera direction, barycentrics, light and continuation
+     * directions, shading normal) of the largest change of the term when that input moves by
+     * its FP32 rounding scale. May be NULL (then not computed: it costs ~28 re-evaluations of
+     * the primary vertex's adjoint per sample). */
+    double* verts_sens;
 } orc_grads;
 
 /* counters: [0] primary rays, [1] continuation rays, [2] shadow rays, [3] BVH nodes visited,
@@ -95,6 +101,13 @@ double orc_scene_tmin(const orc_scene* s);
 int orc_render(const orc_scene* s, const orc_view* v, const orc_params* p,
                const int32_t* pixels, int32_t n_pixels,
                double* out_rgb, double* out_margin, int32_t* out_prim_tri, int64_t* counts);
+
+/* The same forward with each sample's own result: out_sample_rgb [n][spp][3] (the sample's
+ * radiance, whose mean is the pixel's) and out_sample_margin [n][spp] (the smallest normalised
+ * decision margin of that sample, +inf when p->want_margin is 0; may be NULL). */
+int orc_render_samples(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
+                       int32_t n_pixels, double* out_rgb, double* out_margin, double* out_sample_rgb,
+                       double* out_sample_margin, int64_t* counts);
 
 /* Adjoint. PRIMARY mode: gradients of the primary-vertex terms, indirect light, visibility,
  * the RIS weight and all sampling decisions detached. FULL mode: in addition the terms of

@@ -57,7 +57,7 @@ class Params(C.Structure):
 
 
 GRAD_FIELDS = ("albedo", "roughness", "metallic", "env", "verts", "albedo_abs", "roughness_abs", "metallic_abs",
-               "env_abs", "verts_abs", "albedo_sens", "roughness_sens", "metallic_sens")
+               "env_abs", "verts_abs", "albedo_sens", "roughness_sens", "metallic_sens", "verts_sens")
 
 
 class Grads(C.Structure):
@@ -78,6 +78,7 @@ def lib():
             L.orc_scene_set_normals.argtypes = [vp, i32]
             L.orc_vertex_normals.argtypes = [vp, vp]
             L.orc_render.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp, vp]
+            L.orc_render_samples.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp, vp, vp]
             L.orc_backward.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, C.POINTER(Grads), vp]
             L.orc_render_detached.argtypes = [vp, vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp]
             L.orc_light_demod.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp]
@@ -213,6 +214,24 @@ def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind
                 kind=None if mg is None else mg[:, 1].astype(np.int32), prim=pr, counts=cnt, history=hout)
 
 
+def render_samples(osc, view, index, ris_m, seed=0, pixels=None, threads=None):
+    """Render pixels of one view with every sample's own radiance and decision margin:
+    dict(rgb [n,3], margin [n], sample_rgb [n,spp,3], sample_margin [n,spp])."""
+    L = lib()
+    n = view.width * view.height if pixels is None else len(pixels)
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
+    rgb = np.zeros((n, 3))
+    mg = np.zeros((n, 2))
+    srgb = np.zeros((n, view.spp, 3))
+    smg = np.zeros((n, view.spp))
+    cnt = np.zeros(8, dtype=np.int64)
+    v = make_view(view, index)
+    p = make_params(ris_m, seed, threads, 0, 1)
+    if L.orc_render_samples(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(rgb), _p(mg), _p(srgb), _p(smg), _p(cnt)):
+        raise ValueError("orc_render_samples rejected its arguments")
+    return dict(rgb=rgb, margin=mg[:, 0], sample_rgb=srgb, sample_margin=smg, counts=cnt)
+
+
 def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, brdf_kind=0, want_abs=True,
              grad_mode=0, reuse=(0, 0), temporal=0, temporal_cap=20, history=None):
     """Adjoint of the listed pixels (grad_mode 0 PRIMARY, 1 FULL); returns dict of FP64
@@ -227,7 +246,7 @@ def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, 
     if want_abs:
         for k in list(out):
             out[k + "_abs"] = np.zeros(out[k].shape)
-        for k in ("albedo", "roughness", "metallic"):
+        for k in ("albedo", "roughness", "metallic", "verts"):
             out[k + "_sens"] = np.zeros(out[k].shape)
     g = Grads(*[_p(out.get(k)) for k in GRAD_FIELDS])
     cnt = np.zeros(8, dtype=np.int64)
@@ -261,7 +280,7 @@ def _grad_out(s, want_abs):
     if want_abs:
         for k in list(out):
             out[k + "_abs"] = np.zeros(out[k].shape)
-        for k in ("albedo", "roughness", "metallic"):
+        for k in ("albedo", "roughness", "metallic", "verts"):
             out[k + "_sens"] = np.zeros(out[k].shape)
     return out
 

@@ -483,7 +483,7 @@ def mirres_peak_fp32(iters: int = 1 << 18):
     return f.value, ms.value
 
 
-def mirres_peak_l2(nbytes: int = 32 << 20, passes: int = 40):
+def mirres_peak_l2(nbytes: int = 32 << 20, passes: int = 400):
     """measured bandwidth of loads served by L2 on the current device: (bytes/s, ms)"""
     b, ms = C.c_double(), C.c_double()
     e = lib().mirres_peak_l2(int(nbytes), int(passes), C.byref(b), C.byref(ms))
