@@ -257,6 +257,8 @@ def main():
     ap.add_argument("--no-reuse", action="store_true", help="skip the spatial-reuse arm")
     ap.add_argument("--bvh", default="lbvh", choices=["lbvh", "ploc"],
                     help="hierarchy builder run every step: Karras LBVH (the paper's) or PLOC clustering")
+    ap.add_argument("--traversal", default="binary", choices=["binary", "wide"],
+                    help="ray traversal through the binary tree (default) or the 8-wide BVH collapsed from it")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -302,7 +304,8 @@ def main():
 
     w = make_workload(args.workload, args.views)
     builder = M.MIRRES_BVH_PLOC if args.bvh == "ploc" else M.MIRRES_BVH_LBVH
-    gw = GpuWorkload(w, local, builder=builder)
+    traversal = M.MIRRES_TRAVERSAL_WIDE if args.traversal == "wide" else M.MIRRES_TRAVERSAL_BINARY
+    gw = GpuWorkload(w, local, builder=builder, traversal=traversal)
     samples = w.samples
     stream = torch.cuda.current_stream()
     scenes = [s.handle for s in gw.scenes]
@@ -339,8 +342,9 @@ def main():
             ev_render[0].record()
         # the batched wavefront records stage events (graph event nodes) for the roofline
         M.mirres_render(gw.ctx, scenes, gw.views, gw.params(launch, block=args.block, blocks_per_sm=args.blocks_per_sm,
-                                                            flags=1 if launch == 1 else 0, grad_mode=grad_mode,
-                                                            reuse=reuse, temporal=temporal, history=history),
+                                                            flags=1 if launch == 1 else 0,
+                                                            grad_mode=grad_mode, reuse=reuse, temporal=temporal,
+                                                            history=history),
                         images, tape)
         if ev_render is not None:
             ev_render[1].record()
@@ -657,10 +661,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}", bvh=args.bvh,
+                           traversal=args.traversal,
                            l2="flushed between timed steps (512 MiB write) and each step writes > 40 GB"),
             "mrays_per_s": mrays, "render_ms_per_step": msr_b / args.steps, "backward_ms_per_step": backward_ms,
             "batched": {"value": value, "ms_per_step": ms_b / args.steps, "mrays_per_s": mrays,
                         "launch": "batched wavefront, one CUDA graph per forward",
+                        "launch_shape": M.mirres_get_wave_shape(gw.ctx),
+                        "launch_shape_stages": list(M.WAVE_STAGES),
                         "stage_ms_per_render": {k: v[0] for k, v in stages.items()},
                         "stage_launches_per_render": {k: v[1] for k, v in stages.items()}},
             "plain": plain,

@@ -100,7 +100,8 @@ typedef struct {
  *   launch   0 = plain: per-view wavefront launches (ray generation, closest hit with hit
  *                 compaction, shade + RIS + next-bounce queue, shadow rays, resolve);
  *            1 = batched wavefront: every view of every scene flattened into waves of up to
- *                 2^25 samples; the whole forward is one CUDA graph, captured on first use and
+ *                 2^wave_log2 samples (mirres_wave_shape, default 2^25, autotuned by
+ *                 mirres_autotune_wave); the whole forward is one CUDA graph, captured on first use and
  *                 replayed while the shape (each view's size, samples, bounces and scene; each
  *                 scene's triangle count and normal mode), tape, seed and workspace stay the
  *                 same (cameras and scene contents may change between replays);
@@ -157,6 +158,9 @@ typedef struct {
     int32_t max_visits;    /* iteration cap of one ray traversal in node visits (0 = 4 n_tris + 64) */
 } mirres_params;
 #define MIRRES_REUSE_MAX_K 64
+#define MIRRES_FLAG_STAGE_EVENTS 1
+#define MIRRES_FLAG_COUNT_WORK 2
+#define MIRRES_FLAG_RASTER 4
 
 /* Gradient destinations for one scene (device pointers, shapes of the scene's inputs).
  * Accumulated (+=); a NULL pointer skips that parameter. */
@@ -186,7 +190,8 @@ mirres_status mirres_scene_validate(mirres_scene* scene, void* stream);
 /* LBVH build (Appendix A "Visibility estimation": a linear BVH after Karras 2012): FP32
  * triangle centroids (fixed operation order, no contraction), 30-bit Morton codes in the
  * centroid box, keys code << 32 | triangle, stable radix sort, binary radix tree, bottom-up
- * boxes, traversal layout. Also rebuilds the env sampling tables (FP64 prefix sums of
+ * boxes, traversal layout (and, with MIRRES_TRAVERSAL_WIDE, the 8-wide BVH collapsed from
+ * the binary tree). Also rebuilds the env sampling tables (FP64 prefix sums of
  * Y(L) sin(theta); Y = (r+g+b)/3, Appendix A). Asynchronous: no host synchronisation (the
  * triangle indices were checked by mirres_scene_create), so it can be captured into a graph
  * with the default LBVH builder. */
@@ -222,9 +227,23 @@ mirres_status mirres_scene_set_normals(mirres_scene* scene, int32_t mode);
 #define MIRRES_BVH_PLOC 1
 mirres_status mirres_bvh_set_builder(mirres_scene* scene, int32_t builder);
 
+/* The tree every ray traversal of this scene runs (not in the paper; both give the same hits,
+ * up to rays that touch a box within rounding):
+ *   MIRRES_TRAVERSAL_BINARY (default): the binary tree of mirres_bvh_build, two child boxes in
+ *     one 64-byte node, a stack of 32-bit node indices;
+ *   MIRRES_TRAVERSAL_WIDE: an 8-wide BVH collapsed from the binary tree after every build and
+ *     refit (80-byte nodes with 8-bit child boxes quantised outwards, leaves of up to three
+ *     triangles, children slotted by octant so that a ray visits them near to far; measured
+ *     slower than the binary tree on the 499k-triangle scene). Allocates ~200 bytes per
+ *     triangle the first time; collapses at once (synchronising) if the scene is built.
+ * MIRRES_ERR_ARG for an unknown mode. */
+#define MIRRES_TRAVERSAL_BINARY 0
+#define MIRRES_TRAVERSAL_WIDE 1
+mirres_status mirres_scene_set_traversal(mirres_scene* scene, int32_t mode);
+
 /* Refit after the vertices moved (the paper keeps its LBVH in step with the mesh at every
- * iteration, Appendix A): topology kept, boxes and packed triangles recomputed bottom-up; env tables
- * rebuilt. Asynchronous. Requires a prior mirres_bvh_build. */
+ * iteration, Appendix A): topology kept, boxes and packed triangles recomputed bottom-up and the
+ * wide BVH collapsed again; env tables rebuilt. Asynchronous. Requires a prior mirres_bvh_build. */
 mirres_status mirres_bvh_refit(mirres_scene* scene, void* stream);
 
 /* ---- forward / adjoint ----------------------------------------------------------------- */
@@ -288,6 +307,37 @@ mirres_status mirres_autotune(mirres_context* ctx, mirres_scene* const* scenes, 
 /* Set the batched launch shape of the context directly (e.g. from a cache of autotuner
  * results): block 0 restores the default. */
 mirres_status mirres_set_launch(mirres_context* ctx, int32_t block, int32_t blocks_per_sm, int32_t chunk);
+
+/* Launch shape of the batched wavefront (launch = 1; no counterpart in the paper): the wave size
+ * -- samples per wave, which is the capacity of every ray queue -- and, per stage kernel
+ * (index = stage: 0 closest hit, 1 shade + RIS (and the reuse kernels), 2 shadow rays, 3 ray
+ * generation), the threads per block and the grid of its grid-stride loop in blocks per SM.
+ * Default: 2^25 samples, 256 threads and 8 blocks per SM for every stage. */
+typedef struct {
+    int32_t wave_log2;        /* samples per wave = 2^wave_log2, in [16, 28] */
+    int32_t block[4];         /* 64, 128 or 256 */
+    int32_t blocks_per_sm[4]; /* in [1, 64] */
+} mirres_wave_shape;
+
+/* Set (shape = NULL: restore the default) or read the context's wavefront shape; used by every
+ * later batched render of the context (a changed shape re-captures the forward's graph).
+ * MIRRES_ERR_ARG for a value outside the ranges above. */
+mirres_status mirres_set_wave_shape(mirres_context* ctx, const mirres_wave_shape* shape);
+mirres_status mirres_get_wave_shape(mirres_context* ctx, mirres_wave_shape* out);
+
+/* Autotuner of the batched wavefront: renders the first views of the batch (up to
+ * budget_samples samples, at least one view; 0 = all) with the wavefront and CUDA events around
+ * every stage, for each of a set of (threads per block, blocks per SM) pairs applied to all
+ * stages at once; keeps the fastest pair per stage, then times the wave sizes 2^23, 2^24 and
+ * 2^25 (those the budget fills) with the chosen stage shapes and keeps the fastest forward.
+ * The result becomes the context's shape (mirres_set_wave_shape) and is written to *out, the
+ * tuned forward's time to *out_ms. The tape must hold these views (it is overwritten); the
+ * renders write temporary images (allocated and freed here). params as for mirres_render
+ * (launch, reuse and flags ignored). Synchronises `stream`. */
+mirres_status mirres_autotune_wave(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                   const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                   void* tape, size_t tape_bytes, uint64_t budget_samples, mirres_wave_shape* out,
+                                   float* out_ms, void* stream);
 
 /* Summed device time (ms) and launch count of each stage of the last batched-wavefront
  * render that was issued with params.flags bit 0: out_ms[0..3] = closest hit, shade (RIS),
@@ -440,29 +490,36 @@ mirres_status mirres_mesh_regularizers(mirres_context* ctx, mirres_scene* scene,
                                        void* stream);
 
 /* Material smoothness regulariser (Appendix A, "Training details"):
- *   L_k = (1 / |X|) sum_{x in X} |k(x) - k(x + eps)|,  k in {albedo, roughness}
+ *   L_k = (1 / |X|) sum_{x in X} |k(x) - k(x + eps)|,  k in {albedo, roughness, normal}
  * X = the surface points seen through the pixel centres of `view` (camera as in mirres_render,
  * jitter 1/2; escaped pixels are not in X). The materials are textures, so the small random
  * offset is taken in texture space: k(x + eps) is the bilinear lookup at the hit's texture
  * coordinates + eps, eps uniform in [-sigma, sigma]^2 from Philox4x32-10 (key = seed, counter
  * (pixel, 0, view_index << 16 | 4, 0), eps = sigma (2 u - 1) with u the 24-bit uniforms of the
- * first two words). |.| of the albedo is the mean of its three channels' absolute differences.
- * (The paper's normal term has no counterpart: the normals come from the mesh -- face normals
- * or interpolated vertex normals -- not from a texture a texture-space offset could move along.) Adds
- * w_albedo L_albedo + w_roughness L_roughness to loss[0] and its gradient (sign(0) = 0) to
- * grad_albedo [tex_h][tex_w][3] and grad_roughness [tex_h][tex_w]; all device, accumulated,
- * any may be NULL. view->scene is ignored. Uses the context workspace (16 B per pixel);
- * asynchronous; FP32 sums in no fixed order. MIRRES_ERR_ARG for NULL ctx/scene/view/params,
- * sigma <= 0, a negative weight, a bad view or view_index outside [0, 65535];
- * MIRRES_ERR_STATE before mirres_bvh_build. */
+ * first two words). |.| of the albedo and of the normal is the mean of the three channels'
+ * absolute differences. The normal is the shading normal of interpolated vertex normals
+ * (mirres_scene_set_normals), S / |S| with S = w0 VN_a + u VN_b + v VN_c; the texture-space
+ * offset moves the point within the hit triangle by the barycentric offset J^-1 eps (J = the
+ * triangle's texture-coordinate map [uv_b - uv_a | uv_c - uv_a]; the blend continued linearly
+ * where the offset leaves the triangle; no normal term where J is singular). With face normals
+ * the normal is constant on a triangle and the term is 0. Adds w_albedo L_albedo + w_roughness
+ * L_roughness + w_normal L_normal to loss[0] and its gradient (sign(0) = 0) to grad_albedo
+ * [tex_h][tex_w][3], grad_roughness [tex_h][tex_w] and grad_verts [n_verts][3] (the normal term,
+ * with the hit point held fixed: through the vertex normals to the vertices of every face
+ * around the hit triangle's vertices); all device, accumulated, any may be NULL. view->scene is
+ * ignored. Uses the context workspace (24 B per pixel); asynchronous; FP32 sums in no fixed
+ * order. MIRRES_ERR_ARG for NULL ctx/scene/view/params, sigma <= 0, a negative weight, a bad
+ * view or view_index outside [0, 65535]; MIRRES_ERR_STATE before mirres_bvh_build. */
 typedef struct {
     float sigma;                /* half-width of the texture-space offset, > 0 */
     float w_albedo, w_roughness; /* weights, >= 0 */
     uint32_t seed_lo, seed_hi;  /* Philox key */
+    float w_normal;             /* weight of the normal term, >= 0 (interpolated normals only) */
 } mirres_lk_params;
 mirres_status mirres_material_smoothness(mirres_context* ctx, const mirres_scene* scene, const mirres_view* view,
                                          int32_t view_index, const mirres_lk_params* params, float* loss,
-                                         float* grad_albedo, float* grad_roughness, void* stream);
+                                         float* grad_albedo, float* grad_roughness, float* grad_verts,
+                                         void* stream);
 
 /* Monochrome light regulariser (Appendix A, "Training details", after NVdiffrec-MC):
  *   L_light = | Y(c_d + c_s) - V(I_ref) |,  Y = (r + g + b) / 3,  V = max(r, g, b)

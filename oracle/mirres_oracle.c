@@ -376,6 +376,20 @@ static int tri_solve(const orc_scene* s, int tri, v3 o, v3 d, double* t, double*
 
 static int inside(double u, double v) { return u >= 0.0 && v >= 0.0 && u + v <= 1.0; }
 
+/* the distance and size terms of tri_solve's margin scale */
+static double tri_dist(const orc_scene* s, int tri, v3 o)
+{
+    v3 a, b, c;
+    tri_verts(s, tri, &a, &b, &c);
+    return vlen(vsub(o, a));
+}
+static double tri_size(const orc_scene* s, int tri)
+{
+    v3 a, b, c;
+    tri_verts(s, tri, &a, &b, &c);
+    return sqrt(vlen(vcross(vsub(b, a), vsub(c, a))));
+}
+
 static int slab(const Node* n, v3 o, v3 d, double tmin, double tmax)
 {
     const double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
@@ -424,8 +438,17 @@ static void bvh_closest(const orc_scene* s, v3 o, v3 d, int skip, Hit* best, int
     }
 }
 
+/* The margin scale of a hit decision (tri_solve's ms) is cos * size / (distance + size): an FP32
+ * ray moves its hit point by a few ulps of the distance. A ray that starts at an earlier hit
+ * (continuation and shadow rays) carries the rounding of every segment before it as well:
+ * `lever` = the path length up to the ray's origin (0 for camera rays) joins the distance. */
+static double lever_scale(double ms, double dist, double size, double lever)
+{
+    return lever > 0.0 ? ms * (dist + size) / (dist + size + lever) : ms;
+}
+
 /* margins of a closest-hit decision: every triangle that could be the first hit */
-static void closest_margins(const orc_scene* s, v3 o, v3 d, int skip, const Hit* best, Margin* mg)
+static void closest_margins_l(const orc_scene* s, v3 o, v3 d, int skip, const Hit* best, Margin* mg, double lever)
 {
     if (!mg || !s->nf) return;
     double tcut = (best->tri >= 0) ? best->t * (1.0 + 1e-6) : INFINITY;
@@ -440,6 +463,7 @@ static void closest_margins(const orc_scene* s, v3 o, v3 d, int skip, const Hit*
                 if (tri == skip) continue;
                 double t, u, v, ms;
                 if (!tri_solve(s, tri, o, d, &t, &u, &v, &ms)) continue;
+                if (lever > 0.0) ms = lever_scale(ms, tri_dist(s, tri, o), tri_size(s, tri), lever);
                 double e = dmin(dmin(u, v), 1.0 - u - v);
                 if (t > 0.5 * s->tmin && t < tcut) note(mg, fabs(e) * ms / TAU_BARY, MK_BARY);
                 if (e >= 0.0 && t > 0.25 * s->tmin && t < 4.0 * s->tmin)
@@ -454,8 +478,13 @@ static void closest_margins(const orc_scene* s, v3 o, v3 d, int skip, const Hit*
     }
 }
 
-/* any hit in (tmin, inf): visibility V of Eq. (incident) */
-static int bvh_any(const orc_scene* s, v3 o, v3 d, int skip, int64_t* cnt, Margin* mg)
+static void closest_margins(const orc_scene* s, v3 o, v3 d, int skip, const Hit* best, Margin* mg)
+{
+    closest_margins_l(s, o, d, skip, best, mg, 0.0);
+}
+
+/* any hit in (tmin, inf): visibility V of Eq. (incident); `lever` as for closest_margins_l */
+static int bvh_any_l(const orc_scene* s, v3 o, v3 d, int skip, int64_t* cnt, Margin* mg, double lever)
 {
     if (!s->nf) return 0;
     int stack[256], sp = 0;
@@ -475,6 +504,7 @@ static int bvh_any(const orc_scene* s, v3 o, v3 d, int skip, int64_t* cnt, Margi
                 if (!tri_solve(s, tri, o, d, &t, &u, &v, &ms)) continue;
                 int h = inside(u, v) && t > s->tmin;
                 if (mg && t > 0.5 * s->tmin) {
+                    if (lever > 0.0) ms = lever_scale(ms, tri_dist(s, tri, o), tri_size(s, tri), lever);
                     double e = dmin(dmin(u, v), 1.0 - u - v);
                     double r = fabs(e) * ms / TAU_BARY;
                     if (e >= 0.0 && t > 0.25 * s->tmin && t < 4.0 * s->tmin)
@@ -496,6 +526,11 @@ static int bvh_any(const orc_scene* s, v3 o, v3 d, int skip, int64_t* cnt, Margi
         else note(mg, best_out, MK_BARY);
     }
     return hit;
+}
+
+static int bvh_any(const orc_scene* s, v3 o, v3 d, int skip, int64_t* cnt, Margin* mg)
+{
+    return bvh_any_l(s, o, d, skip, cnt, mg, 0.0);
 }
 
 static void brute_closest(const orc_scene* s, v3 o, v3 d, int skip, Hit* best)
@@ -667,6 +702,36 @@ static void brdf_cos(v3 n, v3 wo, v3 wi, const double alb[3], double r, double m
         double F = f0 + (1.0 - f0) * w5;
         out[k] = (kd / PI + D * vis * F) * ci;
     }
+}
+
+/* FP32 conditioning of the GGX lobe (test tolerances only). A direction rounded to single
+ * precision is off by ~DTH radians; D moves by |d ln D / d theta_h| DTH of itself, with
+ * |d ln D / d theta_h| = 4 (1 - a^2) cos sin / (cos^2 (a^2 - 1) + 1) for the half vector at
+ * angle theta_h from the normal: up to ~2 / alpha near the specular peak. */
+#define DTH 3e-7
+static double ggx_slope(v3 n, v3 wo, v3 wi, double a)
+{
+    v3 hs = vadd(wo, wi);
+    double l = vlen(hs);
+    if (!(l > 0.0)) return 0.0;
+    double c = vdot(n, vscale(hs, 1.0 / l));
+    if (!(c > 0.0)) return 0.0;
+    double sn = sqrt(dmax(0.0, 1.0 - c * c)), a2 = a * a;
+    return 4.0 * (1.0 - a2) * c * sn / (c * c * (a2 - 1.0) + 1.0);
+}
+
+/* the specular lobe's share of Y(f_r cos) (0 for the Lambert-only kind) */
+static double spec_share(v3 n, v3 wo, v3 wi, const double alb[3], double r, double m, int kind)
+{
+    if (kind == 1) return 0.0;
+    double tot[3], dem[3] = {0, 0, 0};
+    brdf_cos(n, wo, wi, alb, r, m, kind, tot);
+    double yt = lum(tot);
+    if (!(yt > 0.0)) return 0.0;
+    double ci = vdot(n, wi);
+    for (int k = 0; k < 3; ++k) dem[k] = (kind == 2 ? 1.0 : (1.0 - m) * alb[k]) / PI * ci;
+    double ys = yt - lum(dem);
+    return dmin(1.0, dmax(0.0, ys / yt));
 }
 
 void orc_brdf_cos(const double n[3], const double wo[3], const double wi[3], const double albedo[3],
@@ -1009,6 +1074,8 @@ typedef struct {
     v3 wc;
     double p_ind;
     double Lind[3];
+    double sens;      /* FP32 sensitivity of rgb (test tolerance only): sum over the vertices of the
+                       * largest channel of each direct term times its relative FP32 error */
     int nv;           /* vertices recorded below (FULL mode) */
     struct {
         int tri;
@@ -1055,7 +1122,10 @@ static v3 camera_dir(const Ctx* c, int px, int py, int smp)
 /* RIS at one shading point (Eq. restir, N = 1): M env candidates streamed through a weighted
  * reservoir (Appendix A). Out: the selection (sel < 0: none), its direction, texel, f_r cos,
  * p_hat, the weight sum and the number of candidates behind the reservoir (m). */
-typedef struct { int sel, ytex; uint32_t ysub; v3 y; double f[3], phat, wsum, m; } Ris;
+typedef struct {
+    int sel, ytex; uint32_t ysub; v3 y; double f[3], phat, wsum, m;
+    double werr; /* FP32 sensitivity (test tolerance only): relative error of w_sum and of f(y) / p_hat(y) */
+} Ris;
 
 /* f_r cos of a light direction at a shading point; with interpolated normals a direction
  * below the face gets nothing (its shadow ray would leave through the surface) */
@@ -1080,6 +1150,9 @@ static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, 
     Reservoir rs = {0.0, -1};
     r->sel = -1; r->ytex = -1; r->ysub = 0u; r->y = V3(0, 0, 0); r->phat = 0.0; r->m = M;
     r->f[0] = r->f[1] = r->f[2] = 0.0;
+    r->werr = 0.0;
+    const double a = alpha_of(sh->rgh);
+    double esum = 0.0, esel = 0.0; /* FP32 error of w_sum (absolute) and of the selection's f / p_hat */
     for (int j = 0; j < M; ++j) {
         uint32_t x[4];
         rng(c, pix, (uint32_t)smp, (uint32_t)b, PURPOSE_CANDIDATE, (uint32_t)j, x);
@@ -1091,15 +1164,25 @@ static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, 
         double phat = lum(s->env + 3 * tex) * lum(fc); /* p_hat = Y(L_env) Y(f_r) cos */
         double gamma = phat / q;                      /* gamma_s = p_hat / q_dir */
         double ua = orc_uniform(x[2]);
+        /* relative FP32 error of gamma: the glossy lobe's conditioning (test tolerance only) */
+        double eg = gamma > 0.0 ? spec_share(sh->n, wo, dir, sh->alb, sh->rgh, sh->met, kind) *
+                                      ggx_slope(sh->n, wo, dir, a) * DTH
+                                : 0.0;
         if (cnt) cnt[5]++;
         if (wrs_update(&rs, gamma, ua, j)) {
             r->y = dir; r->ytex = tex; r->ysub = x[3]; r->phat = phat;
             for (int k = 0; k < 3; ++k) r->f[k] = fc[k];
+            esel = eg;
         }
-        if (gamma > 0.0) note(mg, fabs(ua * rs.wsum - gamma) / rs.wsum / TAU_ACC, MK_ACC);
+        esum += eg * gamma;
+        /* the accept decision's margin: its FP32 error is the base rounding plus the rounding of
+         * the weights, whose glossy lobes are conditioned like 1 / alpha (scales 10x the error) */
+        if (gamma > 0.0)
+            note(mg, fabs(ua * rs.wsum - gamma) / (TAU_ACC * rs.wsum + 10.0 * (ua * esum + eg * gamma)), MK_ACC);
     }
     r->sel = rs.sel;
     r->wsum = rs.wsum;
+    r->werr = (rs.wsum > 0.0 ? esum / rs.wsum : 0.0) + esel;
 }
 
 /* direction of the sub-texel position `sub` of env texel `texel` (as env_sample_m draws it) */
@@ -1241,6 +1324,8 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
     rec->prim_tri = h.tri; rec->pu = h.u; rec->pv = h.v; rec->pt = h.t;
     double beta[3] = {1, 1, 1}, beta_ind[3] = {1, 1, 1};
     double L[3] = {0, 0, 0}, Lind[3] = {0, 0, 0};
+    double rel_beta = 0.0; /* relative FP32 error of the throughput (test tolerance only) */
+    double plen = h.t;     /* path length to the current vertex: the lever of its rays' rounding */
     for (int b = 0; b < B; ++b) {
         Shade sh;
         shade_at(s, h.tri, h.u, h.v, h.t, d, &sh, mg);
@@ -1259,6 +1344,7 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         }
         /* ---- direct light: RIS over M env candidates, streamed through a reservoir ---- */
         double direct[3] = {0, 0, 0};
+        double werr = 0.0;
         if (s->env_ok && M > 0) {
             Ris r;
             ris_at(c, pix, smp, b, &sh, wo, mg, cnt, &r);
@@ -1275,19 +1361,23 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
                 /* Eq. restir with N = 1: f(y) / p_hat(y) * (1/m) sum gamma */
                 double W = r.wsum / (r.m * r.phat);
                 if (cnt) cnt[2]++;
-                int occluded = bvh_any(s, sh.x, r.y, sh.tri, cnt, mg);
+                int occluded = bvh_any_l(s, sh.x, r.y, sh.tri, cnt, mg, plen);
                 double V = occluded ? 0.0 : 1.0;
                 for (int k = 0; k < 3; ++k) direct[k] = V * W * s->env[3 * r.ytex + k] * r.f[k];
+                werr = r.werr;
                 if (b == 0) { rec->sel = r.sel; rec->y = r.y; rec->y_texel = r.ytex; rec->WV = V * W; }
                 if (b < ORC_MAXB) {
                     rec->vx[b].sel = r.sel; rec->vx[b].y = r.y; rec->vx[b].y_texel = r.ytex; rec->vx[b].WV = V * W;
                 }
             }
         }
+        double dmax_c = 0.0;
         for (int k = 0; k < 3; ++k) {
             L[k] += beta[k] * direct[k];
             if (b >= 1) Lind[k] += beta_ind[k] * direct[k];
+            dmax_c = dmax(dmax_c, fabs(beta[k] * direct[k]));
         }
+        rec->sens += dmax_c * (rel_beta + werr);
         if (b == B - 1) break;
         /* ---- indirect light: one continuation ray from the MIS mixture ---- */
         uint32_t x[4];
@@ -1305,6 +1395,15 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         if (!(pind > 0.0) || (fc[0] <= 0.0 && fc[1] <= 0.0 && fc[2] <= 0.0)) break;
         if (b == 0) { rec->has_cont = 1; rec->wc = wc; rec->p_ind = pind; }
         if (b < ORC_MAXB) { rec->vx[b].has_cont = 1; rec->vx[b].wc = wc; rec->vx[b].p_ind = pind; }
+        {
+            /* FP32 error of f cos / p_ind: the GGX D in f and in the VNDF part of the mixture pdf
+             * cancel to the extent their shares agree (test tolerance only) */
+            Mix mx = mixture(s, sh.alb, sh.met);
+            double a = alpha_of(sh.rgh);
+            double pshare = (1.0 - mx.c_env) * mx.c_s * vndf_pdf_v(sh.n, wo, wc, a) / pind;
+            double fshare = spec_share(sh.n, wo, wc, sh.alb, sh.rgh, sh.met, kind);
+            rel_beta += fabs(fshare - pshare) * ggx_slope(sh.n, wo, wc, a) * DTH;
+        }
         for (int k = 0; k < 3; ++k) {
             double f = fc[k] / pind;
             beta[k] *= f;
@@ -1313,10 +1412,11 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         if (cnt) cnt[1]++;
         Hit nh;
         bvh_closest(s, sh.x, wc, sh.tri, &nh, cnt);
-        closest_margins(s, sh.x, wc, sh.tri, &nh, mg);
+        closest_margins_l(s, sh.x, wc, sh.tri, &nh, mg, plen);
         if (nh.tri < 0) break; /* escaped: its env light is already in the direct term */
         h = nh;
         d = wc;
+        plen += nh.t;
     }
     for (int k = 0; k < 3; ++k) { rec->rgb[k] = L[k]; rec->Lind[k] = Lind[k]; }
 }
@@ -1747,6 +1847,7 @@ typedef struct {
     int32_t i0, i1;
     double* out_rgb; double* out_margin; int32_t* out_prim;
     double* out_srgb; double* out_smargin; /* per sample: radiance [n][spp][3], margin [n][spp] */
+    double* out_ssens;                     /* per sample: FP32 sensitivity of the radiance [n][spp] */
     const double* d_rgb;
     Sparse sp;
     int64_t cnt[ORC_NCOUNT];
@@ -1771,6 +1872,7 @@ static void* job_run(void* arg)
             if (jb->mode == 0 && !jb->demod && jb->out_srgb) {
                 for (int k = 0; k < 3; ++k) jb->out_srgb[3 * ((size_t)i * spp + smp) + k] = rec.rgb[k];
                 if (jb->out_smargin) jb->out_smargin[(size_t)i * spp + smp] = pmg ? smg.m : INFINITY;
+                if (jb->out_ssens) jb->out_ssens[(size_t)i * spp + smp] = rec.sens;
             }
             if (jb->mode == 0 && jb->demod) {
                 double o3[3];
@@ -1809,7 +1911,7 @@ static void* job_run(void* arg)
 static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev, const orc_view* v,
                     const orc_params* p, const int32_t* pixels, int32_t n, double* out_rgb, double* out_margin,
                     int32_t* out_prim, const double* d_rgb, const orc_grads* g, int64_t* counts,
-                    double* out_srgb, double* out_smargin)
+                    double* out_srgb, double* out_smargin, double* out_ssens)
 {
     if (demod && p && p->grad_mode != 0) return 1;
     if (!s || !v || !p || v->width < 1 || v->height < 1 || v->spp < 1 || v->bounces < 1 || p->ris_m < 0) return 1;
@@ -1834,7 +1936,7 @@ static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev
         jb->i0 = (int32_t)((int64_t)n * t / nt);
         jb->i1 = (int32_t)((int64_t)n * (t + 1) / nt);
         jb->out_rgb = out_rgb; jb->out_margin = out_margin; jb->out_prim = out_prim;
-        jb->out_srgb = out_srgb; jb->out_smargin = out_smargin;
+        jb->out_srgb = out_srgb; jb->out_smargin = out_smargin; jb->out_ssens = out_ssens;
         jb->d_rgb = d_rgb;
     }
     if (nt == 1) job_run(&jobs[0]);
@@ -1864,32 +1966,61 @@ static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev
 
 int orc_render_samples(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
                        int32_t n_pixels, double* out_rgb, double* out_margin, double* out_sample_rgb,
-                       double* out_sample_margin, int64_t* counts)
+                       double* out_sample_margin, double* out_sample_sens, int64_t* counts)
 {
     if (!out_rgb || !out_sample_rgb) return 1;
     return run_jobs(0, 0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, NULL, NULL, NULL, counts,
-                    out_sample_rgb, out_sample_margin);
+                    out_sample_rgb, out_sample_margin, out_sample_sens);
+}
+
+/* one sample's record (for comparisons word by word): out[0] primary triangle, [1] selected
+ * candidate, [2] V W, [3..5] L_ind, [6..8] radiance, [9] env texel of the selection, [10..12]
+ * its direction, [13..15] the continuation direction, [16] its pdf (0: none), [17] vertices
+ * recorded; then per vertex b < ORC_MAXB 12 values: triangle, u, v, selected candidate, texel,
+ * V W, continuation direction (3), its pdf, has continuation, t */
+int orc_sample_record(const orc_scene* s, const orc_view* v, const orc_params* p, int32_t px, int32_t py,
+                      int32_t smp, double* out)
+{
+    if (!s || !v || !p || !out || px < 0 || py < 0 || px >= v->width || py >= v->height || smp < 0 ||
+        smp >= v->spp)
+        return 1;
+    Ctx c;
+    ctx_init(&c, s, v, p);
+    Rec rec;
+    path_sample(&c, px, py, smp, &rec, NULL, NULL);
+    out[0] = rec.prim_tri; out[1] = rec.sel; out[2] = rec.WV;
+    for (int k = 0; k < 3; ++k) { out[3 + k] = rec.Lind[k]; out[6 + k] = rec.rgb[k]; }
+    out[9] = rec.y_texel; out[10] = rec.y.x; out[11] = rec.y.y; out[12] = rec.y.z;
+    out[13] = rec.wc.x; out[14] = rec.wc.y; out[15] = rec.wc.z; out[16] = rec.has_cont ? rec.p_ind : 0.0;
+    out[17] = rec.nv;
+    for (int b = 0; b < rec.nv && b < ORC_MAXB; ++b) {
+        double* o = out + 18 + 12 * b;
+        o[0] = rec.vx[b].tri; o[1] = rec.vx[b].u; o[2] = rec.vx[b].v; o[3] = rec.vx[b].sel;
+        o[4] = rec.vx[b].y_texel; o[5] = rec.vx[b].WV; o[6] = rec.vx[b].wc.x; o[7] = rec.vx[b].wc.y;
+        o[8] = rec.vx[b].wc.z; o[9] = rec.vx[b].p_ind; o[10] = rec.vx[b].has_cont; o[11] = rec.vx[b].t;
+    }
+    return 0;
 }
 
 int orc_render(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels, int32_t n_pixels,
                double* out_rgb, double* out_margin, int32_t* out_prim_tri, int64_t* counts)
 {
     if (!out_rgb) return 1;
-    return run_jobs(0, 0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, out_prim_tri, NULL, NULL, counts, NULL, NULL);
+    return run_jobs(0, 0, s, NULL, v, p, pixels, n_pixels, out_rgb, out_margin, out_prim_tri, NULL, NULL, counts, NULL, NULL, NULL);
 }
 
 int orc_backward(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels, int32_t n_pixels,
                  const double* d_rgb, const orc_grads* g, int64_t* counts)
 {
     if (!d_rgb || !g) return 1;
-    return run_jobs(1, 0, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_rgb, g, counts, NULL, NULL);
+    return run_jobs(1, 0, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_rgb, g, counts, NULL, NULL, NULL);
 }
 
 int orc_render_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v, const orc_params* p,
                         const int32_t* pixels, int32_t n_pixels, double* out_rgb)
 {
     if (!eval || !out_rgb) return 1;
-    return run_jobs(2, 0, frozen, eval, v, p, pixels, n_pixels, out_rgb, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+    return run_jobs(2, 0, frozen, eval, v, p, pixels, n_pixels, out_rgb, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -1902,21 +2033,21 @@ int orc_light_demod(const orc_scene* s, const orc_view* v, const orc_params* p, 
                     int32_t n_pixels, double* out, double* out_margin, int64_t* counts)
 {
     if (!out) return 1;
-    return run_jobs(0, 1, s, NULL, v, p, pixels, n_pixels, out, out_margin, NULL, NULL, NULL, counts, NULL, NULL);
+    return run_jobs(0, 1, s, NULL, v, p, pixels, n_pixels, out, out_margin, NULL, NULL, NULL, counts, NULL, NULL, NULL);
 }
 
 int orc_light_backward(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
                        int32_t n_pixels, const double* d_c, const orc_grads* g, int64_t* counts)
 {
     if (!d_c || !g) return 1;
-    return run_jobs(1, 1, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_c, g, counts, NULL, NULL);
+    return run_jobs(1, 1, s, NULL, v, p, pixels, n_pixels, NULL, NULL, NULL, d_c, g, counts, NULL, NULL, NULL);
 }
 
 int orc_light_demod_detached(const orc_scene* frozen, const orc_scene* eval, const orc_view* v,
                              const orc_params* p, const int32_t* pixels, int32_t n_pixels, double* out)
 {
     if (!eval || !out) return 1;
-    return run_jobs(2, 1, frozen, eval, v, p, pixels, n_pixels, out, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+    return run_jobs(2, 1, frozen, eval, v, p, pixels, n_pixels, out, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ---------------------------------------------------------------------------------------

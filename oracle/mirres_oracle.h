@@ -95,6 +95,11 @@ void orc_vertex_normals(const orc_scene* s, double* out);
 void orc_scene_free(orc_scene* s);
 double orc_scene_tmin(const orc_scene* s);
 
+/* One sample's path record for word-by-word comparisons: out [18 + 12 ORC_MAXB] (layout in
+ * mirres_oracle.c). Returns 0, or 1 for bad arguments. */
+int orc_sample_record(const orc_scene* s, const orc_view* v, const orc_params* p, int32_t px, int32_t py,
+                      int32_t smp, double* out);
+
 /* Forward render of listed pixels (pixel = py*width + px; NULL = all pixels in order).
  * out_rgb [n][3]; out_margin [n][2] (min normalised decision margin over the pixel's samples
  * and the kind of that decision, may be NULL); out_prim_tri [n][spp] (primary hit triangle or -1, may be NULL). */
@@ -103,11 +108,15 @@ int orc_render(const orc_scene* s, const orc_view* v, const orc_params* p,
                double* out_rgb, double* out_margin, int32_t* out_prim_tri, int64_t* counts);
 
 /* The same forward with each sample's own result: out_sample_rgb [n][spp][3] (the sample's
- * radiance, whose mean is the pixel's) and out_sample_margin [n][spp] (the smallest normalised
- * decision margin of that sample, +inf when p->want_margin is 0; may be NULL). */
+ * radiance, whose mean is the pixel's), out_sample_margin [n][spp] (the smallest normalised
+ * decision margin of that sample, +inf when p->want_margin is 0; may be NULL) and
+ * out_sample_sens [n][spp] (test tolerance only: the FP32 sensitivity of the radiance, the sum
+ * over the path's vertices of each direct term's largest channel times its relative FP32
+ * error -- the rounding of the RIS weights and of the throughput, whose glossy GGX lobes are
+ * conditioned like 1 / alpha near the specular peak; may be NULL). */
 int orc_render_samples(const orc_scene* s, const orc_view* v, const orc_params* p, const int32_t* pixels,
                        int32_t n_pixels, double* out_rgb, double* out_margin, double* out_sample_rgb,
-                       double* out_sample_margin, int64_t* counts);
+                       double* out_sample_margin, double* out_sample_sens, int64_t* counts);
 
 /* Adjoint. PRIMARY mode: gradients of the primary-vertex terms, indirect light, visibility,
  * the RIS weight and all sampling decisions detached. FULL mode: in addition the terms of

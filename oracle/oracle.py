@@ -78,7 +78,9 @@ def lib():
             L.orc_scene_set_normals.argtypes = [vp, i32]
             L.orc_vertex_normals.argtypes = [vp, vp]
             L.orc_render.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp, vp]
-            L.orc_render_samples.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp, vp, vp]
+            L.orc_render_samples.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp, vp, vp,
+                                             vp]
+            L.orc_sample_record.argtypes = [vp, C.POINTER(View), C.POINTER(Params), i32, i32, i32, vp]
             L.orc_backward.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, C.POINTER(Grads), vp]
             L.orc_render_detached.argtypes = [vp, vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp]
             L.orc_light_demod.argtypes = [vp, C.POINTER(View), C.POINTER(Params), vp, i32, vp, vp, vp]
@@ -214,9 +216,25 @@ def render(osc, view, index, ris_m, seed=0, pixels=None, threads=None, brdf_kind
                 kind=None if mg is None else mg[:, 1].astype(np.int32), prim=pr, counts=cnt, history=hout)
 
 
+def sample_record(osc, view, index, ris_m, pixel, sample, seed=0):
+    """one sample's path record: dict(prim_tri, sel, WV, Lind, rgb, y_texel, y, wc, p_ind, vertices
+    [nv][12]: triangle, u, v, sel, texel, WV, wc (3), p_ind, has continuation, t)"""
+    L = lib()
+    out = np.zeros(18 + 12 * 16)
+    v = make_view(view, index)
+    p = make_params(ris_m, seed, 1, 0, 0)
+    if L.orc_sample_record(osc.h, C.byref(v), C.byref(p), int(pixel % view.width), int(pixel // view.width),
+                           int(sample), _p(out)):
+        raise ValueError("orc_sample_record rejected its arguments")
+    nv = int(out[17])
+    return dict(prim_tri=int(out[0]), sel=int(out[1]), WV=out[2], Lind=out[3:6], rgb=out[6:9], y_texel=int(out[9]),
+                y=out[10:13], wc=out[13:16], p_ind=out[16], vertices=out[18:18 + 12 * nv].reshape(nv, 12))
+
+
 def render_samples(osc, view, index, ris_m, seed=0, pixels=None, threads=None):
-    """Render pixels of one view with every sample's own radiance and decision margin:
-    dict(rgb [n,3], margin [n], sample_rgb [n,spp,3], sample_margin [n,spp])."""
+    """Render pixels of one view with every sample's own radiance, decision margin and FP32
+    sensitivity: dict(rgb [n,3], margin [n], sample_rgb [n,spp,3], sample_margin [n,spp],
+    sample_sens [n,spp], sens [n] = the mean of the samples')."""
     L = lib()
     n = view.width * view.height if pixels is None else len(pixels)
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
@@ -224,12 +242,15 @@ def render_samples(osc, view, index, ris_m, seed=0, pixels=None, threads=None):
     mg = np.zeros((n, 2))
     srgb = np.zeros((n, view.spp, 3))
     smg = np.zeros((n, view.spp))
+    sse = np.zeros((n, view.spp))
     cnt = np.zeros(8, dtype=np.int64)
     v = make_view(view, index)
     p = make_params(ris_m, seed, threads, 0, 1)
-    if L.orc_render_samples(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(rgb), _p(mg), _p(srgb), _p(smg), _p(cnt)):
+    if L.orc_render_samples(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(rgb), _p(mg), _p(srgb), _p(smg), _p(sse),
+                            _p(cnt)):
         raise ValueError("orc_render_samples rejected its arguments")
-    return dict(rgb=rgb, margin=mg[:, 0], sample_rgb=srgb, sample_margin=smg, counts=cnt)
+    return dict(rgb=rgb, margin=mg[:, 0], sample_rgb=srgb, sample_margin=smg, sample_sens=sse,
+                sens=sse.mean(axis=1), counts=cnt)
 
 
 def backward(osc, view, index, ris_m, d_rgb, seed=0, pixels=None, threads=None, brdf_kind=0, want_abs=True,

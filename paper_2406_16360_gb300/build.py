@@ -14,8 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmirres.so")
-UNITS = ["abi.cu", "bvh.cu", "env.cu", "render.cu", "wave.cu", "noalloc.cu", "denoise.cu", "regular.cu",
-         "peaks.cu"]
+UNITS = ["abi.cu", "bvh.cu", "wbvh.cu", "env.cu", "render.cu", "wave.cu", "noalloc.cu", "denoise.cu",
+         "regular.cu", "peaks.cu"]
 HEADERS = ["device.cuh", "path.cuh", "internal.h", "render.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

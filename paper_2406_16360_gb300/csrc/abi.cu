@@ -66,6 +66,8 @@ SceneDev mr_scene_dev(const mirres_scene* s)
     d.gvn = s->normals ? s->gvn : nullptr;
     d.err = s->ctx->counters + CNT_ERROR;
     d.trav_cap = 0;
+    d.wnodes = (s->traversal == MIRRES_TRAVERSAL_WIDE && s->built) ? s->wnodes : nullptr;
+    d.wtri = (s->traversal == MIRRES_TRAVERSAL_WIDE && s->built) ? s->wtri : nullptr;
     return d;
 }
 
@@ -158,6 +160,7 @@ static mirres_status check_scenes(mirres_context* ctx, mirres_scene* const* scen
         }
         out[(size_t)i] = mr_scene_dev(scenes[i]);
         out[(size_t)i].trav_cap = trav_cap;
+
     }
     return MIRRES_OK;
 }
@@ -296,6 +299,19 @@ extern "C" mirres_status mirres_scene_set_normals(mirres_scene* s, int32_t mode)
     return MIRRES_OK;
 }
 
+extern "C" mirres_status mirres_scene_set_traversal(mirres_scene* s, int32_t mode)
+{
+    if (!s) return arg_error("scene is NULL");
+    if (mode != MIRRES_TRAVERSAL_BINARY && mode != MIRRES_TRAVERSAL_WIDE) return arg_error("unknown traversal");
+    MR_CUDA(cudaSetDevice(s->ctx->device));
+    s->traversal = mode;
+    if (mode == MIRRES_TRAVERSAL_WIDE && s->built) {
+        MR_TRY(mr_wide_build(s, nullptr));
+        MR_CUDA(cudaStreamSynchronize(nullptr));
+    }
+    return MIRRES_OK;
+}
+
 extern "C" mirres_status mirres_bvh_set_builder(mirres_scene* s, int32_t builder)
 {
     if (!s) return arg_error("scene is NULL");
@@ -390,11 +406,21 @@ static Rng make_rng(const mirres_params* p)
 }
 
 // samples per wave of the batched wavefront (queues take 256 bytes per sample of a wave)
-#ifndef MR_WAVE_LOG2
-#define MR_WAVE_LOG2 25
-#endif
-static_assert(MR_WAVE_LOG2 >= 10 && MR_WAVE_LOG2 <= 28, "wave size out of range");
-static const uint64_t kWave = 1ull << MR_WAVE_LOG2;
+// the default wavefront shape (mirres_wave_shape): 2^25 samples per wave, 256 threads and 8
+// blocks per SM for every stage
+static mirres_wave_shape default_wave_shape() { return mirres_wave_shape{25, {256, 256, 256, 256}, {8, 8, 8, 8}}; }
+
+static mirres_status check_wave_shape(const mirres_wave_shape& w)
+{
+    if (w.wave_log2 < 16 || w.wave_log2 > 28) return arg_error("wave_log2 must be in [16, 28]");
+    for (int k = 0; k < 4; ++k) {
+        if (w.block[k] != 64 && w.block[k] != 128 && w.block[k] != 256)
+            return arg_error("block[" + std::to_string(k) + "] must be 64, 128 or 256");
+        if (w.blocks_per_sm[k] < 1 || w.blocks_per_sm[k] > 64)
+            return arg_error("blocks_per_sm[" + std::to_string(k) + "] must be in [1, 64]");
+    }
+    return MIRRES_OK;
+}
 
 struct GraphKey {
     uint64_t total, total_pix, wave;
@@ -405,6 +431,7 @@ struct GraphKey {
     const void* tape;
     const void* ws;
     size_t ws_bytes;
+    mirres_wave_shape shape;
 };
 
 // The host-side choices baked into a captured forward: every view's size, samples, bounces and
@@ -426,7 +453,8 @@ static uint64_t layout_digest(const std::vector<ViewDev>& vdev, const std::vecto
         mix(((uint64_t)(uint32_t)v.spp << 32) | (uint32_t)v.bounces);
         mix((uint64_t)(uint32_t)v.scene);
     }
-    for (const SceneDev& sc : sdev) mix(((uint64_t)(uint32_t)sc.n_tris << 1) | (sc.vnrm != nullptr ? 1u : 0u));
+    for (const SceneDev& sc : sdev)
+        mix(((uint64_t)(uint32_t)sc.n_tris << 2) | (sc.wnodes != nullptr ? 2u : 0u) | (sc.vnrm != nullptr ? 1u : 0u));
     return h;
 }
 
@@ -464,6 +492,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         pixoff[(size_t)i] = total_pix;
         total_pix += (uint64_t)vdev[(size_t)i].width * vdev[(size_t)i].height;
     }
+    const uint64_t kWave = 1ull << ctx->wave_shape.wave_log2;
     const uint64_t wave = std::min<uint64_t>(total, kWave);
     // wave boundaries: every kWave samples, or with spatial reuse whole views per wave (a
     // pixel's neighbours must have been shaded in the same wave)
@@ -554,6 +583,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     key.tape = tp;
     key.ws = ctx->ws.ptr;
     key.ws_bytes = ctx->ws.bytes;
+    key.shape = ctx->wave_shape;
     static_assert(sizeof(GraphKey) <= sizeof(ctx->graph_key), "graph key too large");
     if (!ctx->graph || std::memcmp(ctx->graph_key, &key, sizeof(key)) != 0) {
         if (ctx->graph) {
@@ -568,7 +598,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
                        qc, tp, ctx->counters, d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
                        (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr, nvx,
                        (flags & 2) != 0, reuse_k, reuse_radius, res, temporal, temporal_cap, hist, vdev.data(),
-                       sdev.data(), (flags & 4) != 0);
+                       sdev.data(), (flags & 4) != 0, ctx->wave_shape);
         ctx->stage_pairs = (flags & 1) ? pairs : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -812,6 +842,157 @@ extern "C" mirres_status mirres_set_launch(mirres_context* ctx, int32_t block, i
     if (chunk < 1) return arg_error("chunk must be >= 1");
     ctx->tuned_variant = mr_persistent_pick(block, blocks_per_sm);
     ctx->tuned_chunk = (unsigned int)chunk;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_set_wave_shape(mirres_context* ctx, const mirres_wave_shape* shape)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    const mirres_wave_shape w = shape ? *shape : default_wave_shape();
+    MR_TRY(check_wave_shape(w));
+    ctx->wave_shape = w;
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_get_wave_shape(mirres_context* ctx, mirres_wave_shape* out)
+{
+    if (!ctx || !out) return arg_error("ctx and out must not be NULL");
+    *out = ctx->wave_shape;
+    return MIRRES_OK;
+}
+
+// per-stage times (0 closest, 1 shade, 2 shadow, 3 raygen) of the last render captured with
+// stage events
+static mirres_status stage_sums(mirres_context* ctx, double ms[4])
+{
+    for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+    for (int p = 0; p < ctx->stage_pairs; ++p) {
+        MR_CUDA(cudaEventSynchronize(ctx->stage_events[2 * p + 1]));
+        float t = 0.0f;
+        MR_CUDA(cudaEventElapsedTime(&t, ctx->stage_events[2 * p], ctx->stage_events[2 * p + 1]));
+        ms[ctx->stage_kind[p]] += t;
+    }
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_autotune_wave(mirres_context* ctx, mirres_scene* const* scenes, int32_t n_scenes,
+                                              const mirres_view* views, int32_t n_views, const mirres_params* params,
+                                              void* tape, size_t tape_bytes, uint64_t budget_samples,
+                                              mirres_wave_shape* out, float* out_ms, void* stream)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    MR_TRY(check_params(params));
+    std::vector<SceneDev> sdev;
+    MR_TRY(check_scenes(ctx, scenes, n_scenes, sdev, params->max_visits));
+    std::vector<ViewDev> vdev;
+    uint64_t total = 0, max_view = 0;
+    MR_TRY(check_views(views, n_views, n_scenes, vdev, total, max_view));
+    MR_TRY(check_full(params, views, n_views));
+    const int nvx = full_vertices(views, n_views, params->grad_mode);
+    // the first views up to the budget (at least one)
+    const uint64_t budget = budget_samples ? budget_samples : total;
+    uint64_t sub_total = 0;
+    size_t nv = 0;
+    while (nv < vdev.size()) {
+        const ViewDev& v = vdev[nv];
+        const uint64_t n = (uint64_t)v.width * v.height * v.spp;
+        if (nv > 0 && sub_total + n > budget) break;
+        sub_total += n;
+        ++nv;
+    }
+    vdev.resize(nv);
+    if (!tape || tape_bytes < tape_bytes_per_sample(nvx) * sub_total)
+        return arg_error("mirres_autotune_wave needs a tape of the tuned views");
+    if (reinterpret_cast<uintptr_t>(tape) & 15) return arg_error("tape must be 16-byte aligned");
+    MR_CUDA(cudaSetDevice(ctx->device));
+    const cudaStream_t st = as_stream(stream);
+    ctx->last_stream = st;
+    // temporary images of the tuned views
+    std::vector<float*> imgs(nv, nullptr);
+    float* img_buf = nullptr;
+    uint64_t pix = 0;
+    for (size_t i = 0; i < nv; ++i) pix += (uint64_t)vdev[i].width * vdev[i].height;
+    if (cudaMalloc((void**)&img_buf, sizeof(float) * 3 * pix) != cudaSuccess) {
+        cudaGetLastError();
+        g_err = "mirres_autotune_wave: image allocation failed";
+        return MIRRES_ERR_OOM;
+    }
+    for (size_t i = 0, off = 0; i < nv; ++i) {
+        imgs[i] = img_buf + 3 * off;
+        off += (uint64_t)vdev[i].width * vdev[i].height;
+    }
+    const Rng rng = make_rng(params);
+    const mirres_wave_shape keep = ctx->wave_shape;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    mirres_status status = MIRRES_OK;
+    auto run = [&](const mirres_wave_shape& w, double stage_ms[4], float* total_ms) -> mirres_status {
+        ctx->wave_shape = w;
+        for (int rep = 0; rep < 2; ++rep) {  // the first replay captures the graph and warms caches and clocks
+            MR_CUDA(cudaEventRecord(e0, st));
+            MR_TRY(render_wave(ctx, sdev, vdev, sub_total, imgs.data(), tape, params->ris_m, rng, 1, nvx, 0, 1, 0, 1,
+                               nullptr, st));
+            MR_CUDA(cudaEventRecord(e1, st));
+        }
+        MR_CUDA(cudaEventSynchronize(e1));
+        MR_CUDA(cudaEventElapsedTime(total_ms, e0, e1));
+        return stage_sums(ctx, stage_ms);
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        status = mr_cuda_status(cudaErrorMemoryAllocation, "mirres_autotune_wave: events");
+    }
+    // (threads per block, blocks per SM) pairs tried for every stage at once
+    static const int kCand[][2] = {{256, 4}, {256, 8}, {256, 16}, {128, 8}, {128, 16}, {128, 32}, {64, 32}};
+    const int n_cand = (int)(sizeof(kCand) / sizeof(kCand[0]));
+    mirres_wave_shape best = default_wave_shape();
+    // the largest tried wave that the tuned views fill
+    int wave_top = 23;
+    while (wave_top < 25 && (1ull << wave_top) < sub_total) ++wave_top;
+    best.wave_log2 = wave_top;
+    double best_stage[4] = {1e300, 1e300, 1e300, 1e300};
+    for (int c = 0; c < n_cand && status == MIRRES_OK; ++c) {
+        mirres_wave_shape w = best;
+        for (int k = 0; k < 4; ++k) {
+            w.block[k] = kCand[c][0];
+            w.blocks_per_sm[k] = kCand[c][1];
+        }
+        double ms[4];
+        float tot = 0.0f;
+        status = run(w, ms, &tot);
+        if (status != MIRRES_OK) break;
+        for (int k = 0; k < 4; ++k) {
+            if (ms[k] < best_stage[k]) {
+                best_stage[k] = ms[k];
+                best.block[k] = kCand[c][0];
+                best.blocks_per_sm[k] = kCand[c][1];
+            }
+        }
+    }
+    float best_ms = 1e30f;
+    int best_wave = wave_top;
+    for (int wl = 23; wl <= wave_top && status == MIRRES_OK; ++wl) {
+        mirres_wave_shape w = best;
+        w.wave_log2 = wl;
+        double ms[4];
+        float tot = 0.0f;
+        status = run(w, ms, &tot);
+        if (status == MIRRES_OK && tot < best_ms) {
+            best_ms = tot;
+            best_wave = wl;
+        }
+    }
+    best.wave_log2 = best_wave;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(img_buf);
+    if (status != MIRRES_OK) {
+        ctx->wave_shape = keep;
+        return status;
+    }
+    ctx->wave_shape = best;
+    if (out) *out = best;
+    if (out_ms) *out_ms = best_ms;
     return MIRRES_OK;
 }
 
@@ -1206,10 +1387,11 @@ extern "C" mirres_status mirres_mesh_regularizers(mirres_context* ctx, mirres_sc
 extern "C" mirres_status mirres_material_smoothness(mirres_context* ctx, const mirres_scene* scene,
                                                     const mirres_view* view, int32_t view_index,
                                                     const mirres_lk_params* params, float* loss, float* grad_albedo,
-                                                    float* grad_roughness, void* stream)
+                                                    float* grad_roughness, float* grad_verts, void* stream)
 {
     if (!ctx || !scene || !view || !params) return arg_error("ctx, scene, view and params required");
-    if (!(params->sigma > 0.0f) || !(params->w_albedo >= 0.0f) || !(params->w_roughness >= 0.0f))
+    if (!(params->sigma > 0.0f) || !(params->w_albedo >= 0.0f) || !(params->w_roughness >= 0.0f) ||
+        !(params->w_normal >= 0.0f))
         return arg_error("sigma must be > 0 and the weights >= 0");
     if (view_index < 0 || view_index > 65535) return arg_error("view_index outside [0, 65535]");
     if (!scene->built) {
@@ -1221,21 +1403,33 @@ extern "C" mirres_status mirres_material_smoothness(mirres_context* ctx, const m
     std::vector<ViewDev> vdev;
     uint64_t total = 0, max_view = 0;
     MR_TRY(check_views(&one, 1, 1, vdev, total, max_view));
-    if (!loss && !grad_albedo && !grad_roughness) return MIRRES_OK;
+    if (!loss && !grad_albedo && !grad_roughness && !grad_verts) return MIRRES_OK;
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
     const size_t npx = (size_t)view->width * view->height;
-    MR_TRY(ws_reserve(ctx, sizeof(float4) * npx + 256));
-    float4* rec = reinterpret_cast<float4*>(ctx->ws.ptr);
-    unsigned int* n_hit = reinterpret_cast<unsigned int*>(rec + npx);
+    Carver plan(nullptr);
+    plan.take<float4>(npx);
+    plan.take<float2>(npx);
+    plan.take<unsigned int>(1);
+    MR_TRY(ws_reserve(ctx, plan.off));
+    Carver cv(ctx->ws.ptr);
+    float4* rec = cv.take<float4>(npx);
+    float2* bary = cv.take<float2>(npx);
+    unsigned int* n_hit = cv.take<unsigned int>(1);
     MR_CUDA(cudaMemsetAsync(n_hit, 0, sizeof(unsigned int), st));
+    // the normal term (interpolated normals only) accumulates d loss / d vertex normal in the
+    // scene's per-vertex accumulator, then takes it to the vertices of the faces around
+    const bool normal = params->w_normal > 0.0f && scene->normals && scene->gvn && scene->desc.n_verts > 0;
+    if (normal && grad_verts)
+        MR_CUDA(cudaMemsetAsync(scene->gvn, 0, sizeof(float) * 3 * (size_t)scene->desc.n_verts, st));
     Rng rng;
     rng.set(params->seed_lo, params->seed_hi);
     mr_launch_material_smoothness(mr_scene_dev(scene), vdev[0], (uint32_t)view_index, rng, params->sigma,
-                                  params->w_albedo, params->w_roughness, rec, n_hit, loss, grad_albedo,
-                                  grad_roughness, ctx->sm_count, st);
+                                  params->w_albedo, params->w_roughness, normal ? params->w_normal : 0.0f, rec, bary,
+                                  n_hit, loss, grad_albedo, grad_roughness, normal && grad_verts, ctx->sm_count, st);
+    if (normal && grad_verts) mr_launch_normals_adjoint(scene, grad_verts, ctx->sm_count, st);
     MR_CUDA(cudaGetLastError());
-    ctx->host_launches += 2;
+    ctx->host_launches += 2 + (normal && grad_verts ? 1 : 0);
     return MIRRES_OK;
 }
 

@@ -302,7 +302,7 @@ __global__ void k_bottom_up(const float* __restrict__ verts, const int32_t* __re
                             const int32_t* __restrict__ perm, const int32_t* __restrict__ left,
                             const int32_t* __restrict__ right, const int32_t* __restrict__ parent,
                             float* lo, float* hi, int32_t* flags, float4* __restrict__ nodes,
-                            float4* __restrict__ ptri, int32_t* __restrict__ leaf_of)
+                            float4* __restrict__ ptri, int32_t* __restrict__ leaf_of, int2* __restrict__ range)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= F) return;
@@ -352,6 +352,12 @@ __global__ void k_bottom_up(const float* __restrict__ verts, const int32_t* __re
         nodes[4 * (size_t)p + 1] = make_float4(bl[4], bl[5], br[0], br[1]);
         nodes[4 * (size_t)p + 2] = make_float4(br[2], br[3], br[4], br[5]);
         nodes[4 * (size_t)p + 3] = make_float4(__int_as_float(cl), __int_as_float(cr), 0.0f, 0.0f);
+        // (first leaf position, leaf count) under p: the count is exact for every builder, the
+        // first position delimits the subtree only for the Karras tree (clustering may pair
+        // clusters that are not neighbours)
+        const int2 rl = cl >= 0 ? __ldcg(range + cl) : make_int2(~cl, 1);
+        const int2 rr = cr >= 0 ? __ldcg(range + cr) : make_int2(~cr, 1);
+        __stcg(range + p, make_int2(min(rl.x, rr.x), rl.y + rr.y));
         p = parent[p];
     }
 }
@@ -701,6 +707,7 @@ mirres_status mr_bvh_alloc(mirres_scene* s)
     MR_TRY(mr_alloc(&s->nodes, 4 * (F > 1 ? F - 1 : 1)));
     MR_TRY(mr_alloc(&s->ptri, 3 * F));
     MR_TRY(mr_alloc(&s->leaf_of, F));
+    MR_TRY(mr_alloc(&s->range, F > 1 ? F - 1 : 1));
     MR_TRY(mr_alloc(&s->cent, 3 * F));
     MR_TRY(mr_alloc(&s->codes[0], F));
     MR_TRY(mr_alloc(&s->codes[1], F));
@@ -718,9 +725,10 @@ void mr_bvh_free(mirres_scene* s)
     void* ptrs[] = {s->keys, s->perm, s->left, s->right, s->parent, s->lo, s->hi, s->flags, s->nodes, s->ptri,
                     s->leaf_of, s->cent, s->codes[0], s->codes[1], s->vals[0], s->vals[1], s->hist, s->bounds,
                     s->tmin, s->bad, s->ploc_box, s->ploc_node, s->ploc_nn, s->ploc_part, s->ploc_state,
-                    s->vacc, s->vnrm, s->gvn};
+                    s->vacc, s->vnrm, s->gvn, s->range};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    mr_wide_free(s);
 }
 
 static mirres_status bottom_up(mirres_scene* s, cudaStream_t st)
@@ -730,7 +738,7 @@ static mirres_status bottom_up(mirres_scene* s, cudaStream_t st)
     if (F > 1) MR_CUDA(cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (size_t)(F - 1), st));
     k_bottom_up<<<grid_for(F, 256), 256, 0, st>>>(s->desc.verts, s->desc.tris, F, s->desc.n_verts, s->perm, s->left,
                                                  s->right, s->parent, s->lo, s->hi, s->flags, s->nodes, s->ptri,
-                                                 s->leaf_of);
+                                                 s->leaf_of, s->range);
     MR_CUDA(cudaGetLastError());
     return MIRRES_OK;
 }
@@ -842,6 +850,7 @@ mirres_status mr_bvh_build(mirres_scene* s, cudaStream_t st)
         if (karras) k_karras<<<grid_for(F - 1, 256), 256, 0, st>>>(s->keys, F, s->left, s->right, s->parent);
         MR_CUDA(cudaGetLastError());
         MR_TRY(bottom_up(s, st));
+        if (s->traversal == MIRRES_TRAVERSAL_WIDE) MR_TRY(mr_wide_build(s, st));
     }
     if (s->normals) MR_TRY(mr_vertex_normals(s, st));
     return MIRRES_OK;
@@ -872,6 +881,7 @@ mirres_status mr_bvh_refit(mirres_scene* s, cudaStream_t st)
 {
     MR_TRY(bounds(s, st, 0));
     MR_TRY(bottom_up(s, st));
+    if (s->desc.n_tris > 0 && s->traversal == MIRRES_TRAVERSAL_WIDE) MR_TRY(mr_wide_build(s, st));
     if (s->normals) MR_TRY(mr_vertex_normals(s, st));
     return MIRRES_OK;
 }

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) k_eawt_level_adjoint(const float4* __rest
 // and hit position; 0 for both where the ray escapes
 __global__ void __launch_bounds__(256) k_gbuffer(SceneDev s, ViewDev v, float* __restrict__ nrm, float* __restrict__ pos)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const int64_t npx = (int64_t)v.width * v.height;
     const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
     const float tmin = *s.tmin_dev;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_gbuffer(SceneDev s, ViewDev v, float* _
         const int px = (int)(p % v.width), py = (int)(p / v.width);
         const float3 d = camera_dir(v, px, py, 0.5f, 0.5f);
         Hit h;
-        traverse<false>(s, o, d, -1, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x);
+        trace<false>(s, o, d, -1, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x);
         float3 n = f3(0.f, 0.f, 0.f), x = n;
         if (h.tri >= 0) {
             float3 v0, e1, e2;

@@ -55,6 +55,12 @@
 #endif
 #define MR_LSTACK (64 - MR_SSTACK)
 static_assert(MR_SSTACK >= 8 && MR_SSTACK <= 56, "MR_SSTACK out of range");
+// the wide traversal's stack of 8-byte node groups: the first MR_SSTACK / 2 in the same shared
+// memory column, the rest local; a wide tree is at most as deep as its binary tree (<= 63)
+#define MR_WSSTACK (MR_SSTACK / 2)
+#define MR_WLSTACK (64 - MR_WSSTACK)
+// launches of the wide-BVH collapse (one per level of the wide tree)
+#define MR_WIDE_LEVELS 64
 
 // ---------------------------------------------------------------------------------------
 // scene as seen by the kernels
@@ -87,6 +93,9 @@ struct SceneDev {
     // error counter, read back by mirres_get_counters)
     unsigned long long* err;
     int32_t trav_cap;
+    // the 8-wide BVH the traversal runs (null: the binary tree's traversal); see wbvh.cu
+    const uint4* wnodes;   // [][5] 80-byte nodes
+    const float4* wtri;    // [F][3] packed triangles in the wide leaves' order
 };
 
 // iteration cap of one traversal
@@ -193,7 +202,8 @@ __device__ __forceinline__ int search_le(const uint32_t* __restrict__ a, int n, 
 __device__ __forceinline__ int env_texel_of(const SceneDev& s, float3 d)
 {
     const float u = atan2f(d.x, -d.z) * (0.5f * MR_INV_PI) + 0.5f;
-    const float v = acosf(fminf(1.0f, fmaxf(-1.0f, d.y))) * MR_INV_PI;
+    // the polar angle from atan2(sin, cos): acos of d.y loses most of its digits near the poles
+    const float v = atan2f(sqrtf(d.x * d.x + d.z * d.z), d.y) * MR_INV_PI;
     int c = (int)floorf(u * (float)s.ew), r = (int)floorf(v * (float)s.eh);
     c = min(max(c, 0), s.ew - 1);
     r = min(max(r, 0), s.eh - 1);
@@ -202,7 +212,9 @@ __device__ __forceinline__ int env_texel_of(const SceneDev& s, float3 d)
 
 __device__ __forceinline__ float env_pdf_dir(const SceneDev& s, float3 d, int texel)
 {
-    const float st = sqrtf(fmaxf(0.0f, 1.0f - d.y * d.y));
+    // sin(theta) of a unit direction as |(x, z)|: sqrt(1 - y^2) cancels catastrophically near
+    // the poles, where the pdf grows like 1 / sin(theta)
+    const float st = sqrtf(d.x * d.x + d.z * d.z);
     if (!(st > 0.0f)) return 0.0f;
     return __ldg(&s.env_texel[texel].w) / (2.0f * MR_PI * MR_PI * st);
 }
@@ -628,6 +640,185 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
         }
     }
     return visited;
+}
+
+// ---------------------------------------------------------------------------------------
+// traversal of the 8-wide BVH (layout in wbvh.cu)
+// ---------------------------------------------------------------------------------------
+// byte k of a word as a float (exact: 2^23 + q, minus 2^23)
+__device__ __forceinline__ float qbyte(uint32_t word, uint32_t k)
+{
+    return __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u | k)) - 8388608.0f;
+}
+
+// one triangle of the wide leaves; closest: smallest t, ties -> smaller id; returns a hit
+__device__ __forceinline__ bool test_wtri(const SceneDev& s, uint32_t k, float3 o, float3 d, int skip, float tmin,
+                                          Hit& best)
+{
+    const float4 a = __ldg(s.wtri + 3 * (size_t)k);
+    const int tri = __float_as_int(a.w);
+    if (tri == skip) return false;
+    const float4 b = __ldg(s.wtri + 3 * (size_t)k + 1);
+    const float4 c = __ldg(s.wtri + 3 * (size_t)k + 2);
+    float t, u, v;
+    if (!tri_solve(o, d, xyz(a), xyz(b), xyz(c), t, u, v)) return false;
+    if (!(u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t > tmin)) return false;
+    if (t < best.t || (t == best.t && tri < best.tri)) {
+        best.t = t;
+        best.u = u;
+        best.v = v;
+        best.tri = tri;
+        return true;
+    }
+    return false;
+}
+
+// Expand one wide node: test its eight child boxes (t entry <= best.t, the binary traversal's
+// rule, with the same few-ulp slack), return the node children hit as bits in visit order
+// (slot ^ oct) in bits 0-7 with the node-slot mask in bits 8-15, and the leaf triangles hit as
+// bits (offset) of *tbits; *cbase / *tbase receive the node's first child and first triangle.
+__device__ __forceinline__ uint32_t wide_expand(const SceneDev& s, uint32_t node, float3 o, float3 inv, uint32_t oct,
+                                                float tmin, float tmax, uint32_t& cbase, uint32_t& tbase,
+                                                uint32_t& tbits)
+{
+    const uint4* np = s.wnodes + 5 * (size_t)node;
+    const uint4 w0 = __ldg(np), w1 = __ldg(np + 1), w2 = __ldg(np + 2), w3 = __ldg(np + 3), w4 = __ldg(np + 4);
+    // t of a plane at p + q 2^e: q (2^e inv) + (p - o) inv
+    const float ax = __uint_as_float((w0.w & 0xffu) << 23) * inv.x;
+    const float ay = __uint_as_float(((w0.w >> 8) & 0xffu) << 23) * inv.y;
+    const float az = __uint_as_float(((w0.w >> 16) & 0xffu) << 23) * inv.z;
+    const float bx = (__uint_as_float(w0.x) - o.x) * inv.x;
+    const float by = (__uint_as_float(w0.y) - o.y) * inv.y;
+    const float bz = (__uint_as_float(w0.z) - o.z) * inv.z;
+    // the near plane of each axis is the low one for a positive direction, the high one otherwise
+    const uint32_t nx0 = (oct & 1u) ? w3.z : w2.x, nx1 = (oct & 1u) ? w3.w : w2.y;
+    const uint32_t fx0 = (oct & 1u) ? w2.x : w3.z, fx1 = (oct & 1u) ? w2.y : w3.w;
+    const uint32_t ny0 = (oct & 2u) ? w4.x : w2.z, ny1 = (oct & 2u) ? w4.y : w2.w;
+    const uint32_t fy0 = (oct & 2u) ? w2.z : w4.x, fy1 = (oct & 2u) ? w2.w : w4.y;
+    const uint32_t nz0 = (oct & 4u) ? w4.z : w3.x, nz1 = (oct & 4u) ? w4.w : w3.y;
+    const uint32_t fz0 = (oct & 4u) ? w3.x : w4.z, fz1 = (oct & 4u) ? w3.y : w4.w;
+    cbase = w1.x;
+    tbase = w1.y;
+    const uint32_t imask = w0.w >> 24;
+    uint32_t hits = 0, tb = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t k = (uint32_t)(i & 3);
+        const uint32_t meta = ((i < 4 ? w1.z : w1.w) >> (8 * k)) & 0xffu;
+        const float tnx = fmaf(qbyte(i < 4 ? nx0 : nx1, k), ax, bx);
+        const float tny = fmaf(qbyte(i < 4 ? ny0 : ny1, k), ay, by);
+        const float tnz = fmaf(qbyte(i < 4 ? nz0 : nz1, k), az, bz);
+        const float tfx = fmaf(qbyte(i < 4 ? fx0 : fx1, k), ax, bx);
+        const float tfy = fmaf(qbyte(i < 4 ? fy0 : fy1, k), ay, by);
+        const float tfz = fmaf(qbyte(i < 4 ? fz0 : fz1, k), az, bz);
+        const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, tmin));
+        const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tmax));
+        if (meta != 0u && tn <= tf * 1.0000005f + 1e-30f) {
+            if (meta & 0x80u) hits |= 1u << ((uint32_t)i ^ oct);
+            else tb |= ((1u << (meta >> 5)) - 1u) << (meta & 31u);
+        }
+    }
+    tbits = tb;
+    return hits | (imask << 8);
+}
+
+// Closest (any = false) or any hit with t in (tmin, tmax) through the wide BVH: the same
+// contract as traverse() (returns the nodes visited, -1 on a cap or stack overflow, triangle
+// tests added to *ntri). `sstk` = this thread's shared column of 8-byte entries (stride
+// `sstride`).
+template <bool ANY>
+__device__ __forceinline__ int wtraverse(const SceneDev& s, float3 o, float3 d, int skip, float tmin, float tmax,
+                                         Hit& best, uint2* sstk, int sstride, int* ntri = nullptr)
+{
+    best.t = tmax;
+    best.tri = -1;
+    best.u = best.v = 0.0f;
+    const int F = s.n_tris;
+    if (F <= 0) return 0;
+    if (F == 1) {
+        if (ntri) ++*ntri;
+        test_leaf(s, 0, o, d, skip, tmin, best);
+        return 0;
+    }
+    const float3 inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    const uint32_t oct = (d.x < 0.0f ? 1u : 0u) | (d.y < 0.0f ? 2u : 0u) | (d.z < 0.0f ? 4u : 0u);
+    uint2 lstk[MR_WLSTACK];
+    int sp = 0;
+    int visited = 0;
+    const int cap = trav_cap_of(s);
+    uint32_t node = 0;
+    while (true) {
+        // a wide tree has fewer than F nodes and exactly F triangles: an index outside that
+        // (a malformed tree) ends the ray like the iteration cap instead of reading past it
+        if (++visited > cap || node >= (uint32_t)F) {
+            best.tri = -1;
+            trav_fail(s);
+            return -1;
+        }
+        uint32_t cbase, tbase, tbits;
+        uint32_t group = wide_expand(s, node, o, inv, oct, tmin, best.t, cbase, tbase, tbits);
+        if (tbits && tbase + (uint32_t)(31 - __clz(tbits)) >= (uint32_t)F) {
+            best.tri = -1;
+            trav_fail(s);
+            return -1;
+        }
+        while (tbits) {
+            const uint32_t k = (uint32_t)(__ffs(tbits) - 1);
+            tbits &= tbits - 1u;
+            if (ntri) ++*ntri;
+            if (test_wtri(s, tbase + k, o, d, skip, tmin, best) && ANY) return visited;
+        }
+        if ((group & 0xffu) == 0u) {
+            if (sp == 0) break;
+            --sp;
+            const uint2 e = sp < MR_WSSTACK ? sstk[sp * sstride] : lstk[sp - MR_WSSTACK];
+            cbase = e.x;
+            group = e.y;
+        }
+        const uint32_t bit = (uint32_t)(__ffs(group & 0xffu) - 1);
+        group &= ~(1u << bit);
+        const uint32_t slot = bit ^ oct;
+        node = cbase + (uint32_t)__popc((group >> 8) & ((1u << slot) - 1u));
+        if (group & 0xffu) {
+            if (sp < MR_WSSTACK) {
+                sstk[sp * sstride] = make_uint2(cbase, group);
+            } else if (sp < MR_WSSTACK + MR_WLSTACK) {
+                lstk[sp - MR_WSSTACK] = make_uint2(cbase, group);
+            } else {
+                best.tri = -1;
+                trav_fail(s);
+                return -1;
+            }
+            ++sp;
+        }
+    }
+    return visited;
+}
+
+// the scene's traversal: the wide BVH when it has one, else the binary tree. `sstk` is the
+// thread's column of MR_SSTACK 32-bit words in a shared buffer whose base is 8-byte aligned:
+// sstk = base + threadIdx.x, stride blockDim.x (the wide traversal reads the same buffer as
+// MR_WSSTACK 8-byte words per thread, base + threadIdx.x in 8-byte units)
+template <bool ANY>
+__device__ __forceinline__ int trace(const SceneDev& s, float3 o, float3 d, int skip, float tmin, float tmax, Hit& best,
+                                     uint32_t* sstk, int* ntri = nullptr)
+{
+    if (s.wnodes)
+        return wtraverse<ANY>(s, o, d, skip, tmin, tmax, best,
+                              reinterpret_cast<uint2*>(sstk - threadIdx.x) + threadIdx.x, blockDim.x, ntri);
+    return traverse<ANY>(s, o, d, skip, tmin, tmax, best, sstk, blockDim.x, ntri);
+}
+
+// the same with the tree chosen at compile time (WIDE: the scene must have a wide BVH), for the
+// stage kernels whose registers are tight: each variant carries one traversal only
+template <bool ANY, bool WIDE>
+__device__ __forceinline__ int trace_as(const SceneDev& s, float3 o, float3 d, int skip, float tmin, float tmax,
+                                        Hit& best, uint32_t* sstk, int* ntri = nullptr)
+{
+    if (WIDE)
+        return wtraverse<ANY>(s, o, d, skip, tmin, tmax, best,
+                              reinterpret_cast<uint2*>(sstk - threadIdx.x) + threadIdx.x, blockDim.x, ntri);
+    return traverse<ANY>(s, o, d, skip, tmin, tmax, best, sstk, blockDim.x, ntri);
 }
 
 // The same traversal as a resumable state, for kernels that interleave the rays of a warp's

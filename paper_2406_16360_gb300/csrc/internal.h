@@ -43,7 +43,8 @@ struct mirres_context {
     // batched wavefront: the captured forward and the arguments it was captured for
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
-    unsigned char graph_key[128] = {};
+    unsigned char graph_key[192] = {};
+    mirres_wave_shape wave_shape = {25, {256, 256, 256, 256}, {8, 8, 8, 8}};  // batched wavefront launch shape
     unsigned long long graph_launches = 0;  // kernel launches inside the graph
     cudaEvent_t* stage_events = nullptr;     // [n_stage_events]: (start, end) pairs per stage launch
     int n_stage_events = 0;
@@ -67,6 +68,12 @@ struct mirres_scene {
     float4* nodes = nullptr;         // [F-1][4]
     float4* ptri = nullptr;          // [F][3]
     int32_t* leaf_of = nullptr;      // [F]
+    int2* range = nullptr;           // [F-1] (first leaf position, leaf count) under each internal node
+    // the 8-wide BVH the traversal runs (collapsed from the binary tree after every build / refit)
+    uint4* wnodes = nullptr;         // [F][5] 80-byte nodes with quantised child boxes
+    float4* wtri = nullptr;          // [F][3] packed triangles in the wide leaves' order
+    int2* wqueue = nullptr;          // [2][F] collapse work queues (binary node, wide node)
+    unsigned int* wcnt = nullptr;    // [2 + MR_WIDE_LEVELS + 1] allocation counters, queue lengths
     float* cent = nullptr;           // [3][F] centroids (build scratch)
     uint32_t* codes[2] = {nullptr, nullptr};
     int32_t* vals[2] = {nullptr, nullptr};
@@ -82,6 +89,9 @@ struct mirres_scene {
     float* gvn = nullptr;    // [V][3] adjoint accumulator of d loss / d vertex normal
     // hierarchy builder: MIRRES_BVH_LBVH (Karras) or MIRRES_BVH_PLOC (clustering); PLOC scratch
     int32_t builder = 0;
+    // the tree the traversal runs: MIRRES_TRAVERSAL_BINARY (default) or MIRRES_TRAVERSAL_WIDE
+    // (the 8-wide BVH, collapsed after every build and refit)
+    int32_t traversal = 0;
     float4* ploc_box = nullptr;      // [2][2][F] cluster boxes (lo, hi), ping-pong
     int32_t* ploc_node = nullptr;    // [2][F] cluster node ids, ping-pong
     int32_t* ploc_nn = nullptr;      // [F] nearest neighbour of each cluster
@@ -128,6 +138,9 @@ mirres_status mr_normals_alloc(mirres_scene* s);
 mirres_status mr_vertex_normals(mirres_scene* s, cudaStream_t st);
 void mr_launch_normals_adjoint(const mirres_scene* s, float* grad_verts, int sms, cudaStream_t st);
 mirres_status mr_bvh_refit(mirres_scene* s, cudaStream_t st);
+// wbvh.cu: the 8-wide BVH collapsed from the binary tree (allocated on first use)
+mirres_status mr_wide_build(mirres_scene* s, cudaStream_t st);
+void mr_wide_free(mirres_scene* s);
 // regular.cu
 mirres_status mr_edges_build(mirres_scene* s, cudaStream_t st);
 void mr_edges_free(mirres_scene* s);

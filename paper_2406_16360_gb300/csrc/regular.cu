@@ -129,9 +129,9 @@ __global__ void __launch_bounds__(256) k_offset(const float* __restrict__ verts,
 // one closest-hit ray through each pixel centre: (triangle, s, t) of its hit; triangle -1 where
 // the ray escapes. Hits are counted per warp (one atomic per warp and iteration).
 __global__ void __launch_bounds__(256) k_lk_hits(SceneDev s, ViewDev v, float4* __restrict__ rec,
-                                                 unsigned int* __restrict__ n_hit)
+                                                 float2* __restrict__ bary, unsigned int* __restrict__ n_hit)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const int64_t npx = (int64_t)v.width * v.height;
     const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
     const float tmin = *s.tmin_dev;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_lk_hits(SceneDev s, ViewDev v, float4* 
             const int px = (int)(p % v.width), py = (int)(p / v.width);
             const float3 d = camera_dir(v, px, py, 0.5f, 0.5f);
             Hit h;
-            traverse<false>(s, o, d, -1, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x);
+            trace<false>(s, o, d, -1, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x);
             float4 r = make_float4(__int_as_float(-1), 0.0f, 0.0f, 0.0f);
             if (h.tri >= 0) {
                 const float* uv = s.tri_uv + 6 * (size_t)h.tri;
@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(256) k_lk_hits(SceneDev s, ViewDev v, float4* 
                 hit = true;
             }
             rec[p] = r;
+            bary[p] = make_float2(h.u, h.v);
         }
         const unsigned b = __ballot_sync(MR_FULL, hit);
         if (lane_id() == 0 && b) atomicAdd(n_hit, (unsigned)__popc(b));
@@ -176,14 +177,70 @@ struct EmitLk {
 
 __device__ __forceinline__ float sgn(float x) { return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f); }
 
-__global__ void __launch_bounds__(256) k_lk_apply(SceneDev s, const float4* __restrict__ rec, int64_t npx,
+struct EmitVn {
+    float* g;
+    __device__ void operator()(int key, const float (&v)[3]) const
+    {
+        atomicAdd(g + 3 * (size_t)key, v[0]);
+        atomicAdd(g + 3 * (size_t)key + 1, v[1]);
+        atomicAdd(g + 3 * (size_t)key + 2, v[2]);
+    }
+};
+
+// the normal term of one hit (interpolated vertex normals): n0 = S0 / |S0| at the hit's
+// barycentrics, n1 = S1 / |S1| at those moved by J^-1 eps (J the triangle's texture map);
+// returns sum_c |n0_c - n1_c| and, scaled by cn, the gradient with respect to the three vertex
+// normals (vid -1 where the term is absent: singular texture map or a vanishing blend)
+__device__ __forceinline__ float lk_normal(const SceneDev& s, int tri, float u, float v, float es, float et, float cn,
+                                           bool grad, int (&vid)[3], float (&gvn)[3][3])
+{
+    const float* uv = s.tri_uv + 6 * (size_t)tri;
+    const float j00 = __ldg(uv + 2) - __ldg(uv + 0), j01 = __ldg(uv + 4) - __ldg(uv + 0);
+    const float j10 = __ldg(uv + 3) - __ldg(uv + 1), j11 = __ldg(uv + 5) - __ldg(uv + 1);
+    const float det = j00 * j11 - j01 * j10;
+    if (!(det != 0.0f)) return 0.0f;
+    const float du = (j11 * es - j01 * et) / det, dv = (j00 * et - j10 * es) / det;
+    int ix[3];
+    float3 vn[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ix[c] = __ldg(s.tris + 3 * (size_t)tri + c);
+        vn[c] = xyz(__ldg(s.vnrm + ix[c]));
+    }
+    const float w0 = 1.0f - u - v;
+    const float b0[3] = {w0, u, v}, b1[3] = {w0 - du - dv, u + du, v + dv};
+    const float3 S0 = add(add(mul(vn[0], b0[0]), mul(vn[1], b0[1])), mul(vn[2], b0[2]));
+    const float3 S1 = add(add(mul(vn[0], b1[0]), mul(vn[1], b1[1])), mul(vn[2], b1[2]));
+    const float l0 = sqrtf(dot(S0, S0)), l1 = sqrtf(dot(S1, S1));
+    if (!(l0 > 0.0f) || !(l1 > 0.0f)) return 0.0f;
+    const float3 n0 = mul(S0, 1.0f / l0), n1 = mul(S1, 1.0f / l1);
+    const float3 df = sub(n0, n1);
+    if (grad) {
+        const float3 g = f3(cn * sgn(df.x), cn * sgn(df.y), cn * sgn(df.z));
+        const float3 gS0 = mul(sub(g, mul(n0, dot(n0, g))), 1.0f / l0);
+        const float3 gS1 = mul(sub(mul(n1, dot(n1, g)), g), 1.0f / l1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            vid[c] = ix[c];
+            gvn[c][0] = b0[c] * gS0.x + b1[c] * gS1.x;
+            gvn[c][1] = b0[c] * gS0.y + b1[c] * gS1.y;
+            gvn[c][2] = b0[c] * gS0.z + b1[c] * gS1.z;
+        }
+    }
+    return fabsf(df.x) + fabsf(df.y) + fabsf(df.z);
+}
+
+__global__ void __launch_bounds__(256) k_lk_apply(SceneDev s, const float4* __restrict__ rec,
+                                                  const float2* __restrict__ bary, int64_t npx,
                                                   const unsigned int* __restrict__ n_hit, Rng rng, uint32_t view_index,
-                                                  float sigma, float wa, float wr, float* loss, float* ga, float* gr)
+                                                  float sigma, float wa, float wr, float wn, float* loss, float* ga,
+                                                  float* gr, float* gvn_out)
 {
     const unsigned int n = *n_hit;
     if (n == 0) return;  // uniform
     const float inv = 1.0f / (float)n;
-    const float ca = wa * inv * (1.0f / 3.0f), cr = wr * inv;
+    const float ca = wa * inv * (1.0f / 3.0f), cr = wr * inv, cn = wn * inv * (1.0f / 3.0f);
+    const bool normal = wn > 0.0f && s.vnrm != nullptr;
     const bool want_grad = ga || gr;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     float acc = 0.0f;
@@ -198,9 +255,15 @@ __global__ void __launch_bounds__(256) k_lk_apply(SceneDev s, const float4* __re
         }
         Taps t[2] = {};
         float sa[3] = {0.f, 0.f, 0.f}, sr = 0.0f;
+        int vid[3] = {-1, -1, -1};
+        float gvn[3][3] = {};
         if (tri >= 0) {
             const uint4 x = rng.draw((uint32_t)p, 0u, view_index, 0u, PURPOSE_SMOOTH, 0u);
             const float es = sigma * (2.0f * u24(x.x) - 1.0f), et = sigma * (2.0f * u24(x.y) - 1.0f);
+            if (normal) {
+                const float2 b = __ldg(bary + p);
+                acc += cn * lk_normal(s, tri, b.x, b.y, es, et, cn, gvn_out != nullptr, vid, gvn);
+            }
             taps_at(s.tw, s.th, r.y, r.z, t[0]);
             taps_at(s.tw, s.th, r.y + es, r.z + et, t[1]);
             float da[3] = {0.f, 0.f, 0.f}, dr = 0.0f;
@@ -231,6 +294,10 @@ __global__ void __launch_bounds__(256) k_lk_apply(SceneDev s, const float4* __re
                     scatter_agg<4>(tri >= 0 ? t[j].idx[k] : -1, vals, EmitLk{ga, gr});
                 }
             }
+        }
+        if (normal && gvn_out) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) scatter_agg<3>(vid[c], gvn[c], EmitVn{gvn_out});
         }
     }
     if (loss) flush_loss(loss, acc);
@@ -359,12 +426,14 @@ void mr_edges_free(mirres_scene* s)
 }
 
 void mr_launch_material_smoothness(const SceneDev& s, const ViewDev& v, uint32_t view_index, const Rng& rng,
-                                   float sigma, float wa, float wr, float4* rec, unsigned int* n_hit, float* loss,
-                                   float* ga, float* gr, int sms, cudaStream_t st)
+                                   float sigma, float wa, float wr, float wn, float4* rec, float2* bary,
+                                   unsigned int* n_hit, float* loss, float* ga, float* gr, bool grad_normals, int sms,
+                                   cudaStream_t st)
 {
     const int64_t npx = (int64_t)v.width * v.height;
-    k_lk_hits<<<grid_of(npx, sms), 256, sizeof(uint32_t) * MR_SSTACK * 256, st>>>(s, v, rec, n_hit);
-    k_lk_apply<<<grid_of(npx, sms), 256, 0, st>>>(s, rec, npx, n_hit, rng, view_index, sigma, wa, wr, loss, ga, gr);
+    k_lk_hits<<<grid_of(npx, sms), 256, sizeof(uint32_t) * MR_SSTACK * 256, st>>>(s, v, rec, bary, n_hit);
+    k_lk_apply<<<grid_of(npx, sms), 256, 0, st>>>(s, rec, bary, npx, n_hit, rng, view_index, sigma, wa, wr, wn, loss,
+                                                  ga, gr, grad_normals ? s.gvn : nullptr);
 }
 
 void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_smooth, float w_offset, float* loss,

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_closest(SceneDev s, ViewDev v, int b, Q
                                                  unsigned int count_fixed, QueueDev hq, unsigned int* count_hit,
                                                  void* tape, uint64_t ntot)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const TapeDev tp = tape_of(tape, ntot);
     const unsigned int n = count ? *count : count_fixed;
     const float tmin = *s.tmin_dev;
@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(256) k_closest(SceneDev s, ViewDev v, int b, Q
         if (i < n) {
             const float4 a = q.o[i];
             qd = q.d[i];
-            traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), tmin, __int_as_float(0x7f800000), h,
-                            sstk + threadIdx.x, blockDim.x);
+            trace<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), tmin, __int_as_float(0x7f800000), h,
+                         sstk + threadIdx.x);
             if (h.tri < 0 && b == 0) {
                 const uint64_t g = v.offset + __float_as_uint(qd.w);
                 const float4 L = __ldg(s.env_texel + env_texel_of(s, xyz(qd)));
@@ -151,15 +151,15 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_shade(SceneDev s, ViewDe
 __global__ void __launch_bounds__(256) k_shadow(SceneDev s, ViewDev v, int b, ShadowDev sq,
                                                 const unsigned int* count, void* tape, uint64_t ntot, int nvx)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count;
     const float tmin = *s.tmin_dev;
     for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 a = sq.o[i], dd = sq.d[i];
         Hit h;
-        traverse<true>(s, xyz(a), xyz(dd), __float_as_int(a.w), tmin, __int_as_float(0x7f800000), h,
-                       sstk + threadIdx.x, blockDim.x);
+        trace<true>(s, xyz(a), xyz(dd), __float_as_int(a.w), tmin, __int_as_float(0x7f800000), h,
+                    sstk + threadIdx.x);
         const uint64_t g = v.offset + __float_as_uint(dd.w);
         if (h.tri < 0) {
             const float4 ad = sq.add[i], ai = sq.addi[i];
@@ -205,11 +205,10 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
                                                 Rng rng, int M, unsigned long long* work, uint32_t chunk,
                                                 void* tape, int nvx, unsigned long long* counters)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const TapeDev tp = tape_of(tape, total, nvx);
     const int lane = lane_id();
     uint32_t* mystk = sstk + threadIdx.x;
-    const int sstride = blockDim.x;
 
     bool has_path = false, has_hit = false;
     uint64_t g = 0;
@@ -277,7 +276,7 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
             const bool need = has_path && !has_hit;
             if (!__any_sync(MR_FULL, need)) break;
             if (need) {
-                traverse<false>(*sp, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk, sstride);
+                trace<false>(*sp, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk);
                 if (h.tri >= 0) {
                     has_hit = true;
                 } else {
@@ -324,7 +323,7 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
         if (out.shadow) {
             ++n_shadow;
             Hit hs;
-            traverse<true>(*sp, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk, sstride);
+            trace<true>(*sp, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk);
             if (hs.tri < 0) {
                 rad = add_rn(rad, out.add_rad);
                 if (b >= 1) lind = add_rn(lind, out.add_lind);
@@ -1147,15 +1146,15 @@ __global__ void __launch_bounds__(256) k_trace_rays(SceneDev s, const float* __r
                                                     const int32_t* __restrict__ skip, int64_t n, int any,
                                                     int32_t* __restrict__ hit_tri, float* __restrict__ hit_tuv)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const float tmin = *s.tmin_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float3 o = f3(rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]);
         const float3 d = f3(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5]);
         const int sk = skip ? skip[i] : -1;
         Hit h;
-        if (any) traverse<true>(s, o, d, sk, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x);
-        else traverse<false>(s, o, d, sk, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x);
+        if (any) trace<true>(s, o, d, sk, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x);
+        else trace<false>(s, o, d, sk, tmin, __int_as_float(0x7f800000), h, sstk + threadIdx.x);
         hit_tri[i] = any ? (h.tri >= 0 ? 1 : -1) : h.tri;
         if (hit_tuv && !any) {
             hit_tuv[3 * i] = h.tri >= 0 ? h.t : 0.0f;

@@ -109,8 +109,9 @@ void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const floa
 void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* pos, int sms, cudaStream_t st);
 // regular.cu: mesh regularisers over the scene's edge list (built by mr_edges_build)
 void mr_launch_material_smoothness(const SceneDev& s, const ViewDev& v, uint32_t view_index, const Rng& rng,
-                                   float sigma, float wa, float wr, float4* rec, unsigned int* n_hit, float* loss,
-                                   float* ga, float* gr, int sms, cudaStream_t st);
+                                   float sigma, float wa, float wr, float wn, float4* rec, float2* bary,
+                                   unsigned int* n_hit, float* loss, float* ga, float* gr, bool grad_normals, int sms,
+                                   cudaStream_t st);
 void mr_launch_regularizers(const mirres_scene* s, const float* rest, float w_smooth, float w_offset, float* loss,
                             float* grad, int sms, cudaStream_t st);
 // L_light from the demodulated lighting: loss[0] += w mean |Y(c) - V(ref)| over the covered
@@ -125,6 +126,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
                     unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
                     int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
-                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist, const ViewDev* hviews, const SceneDev* hscenes, bool raster);
+                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist,
+                    const ViewDev* hviews, const SceneDev* hscenes, bool raster, const mirres_wave_shape& shape);
 int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal, int raster_launches);
 int mr_wave_stage_pairs(int n_waves, int max_bounces);

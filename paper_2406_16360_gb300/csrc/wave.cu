@@ -51,14 +51,14 @@ __global__ void __launch_bounds__(256) k_wraygen(const ViewDev* __restrict__ vie
     }
 }
 
-template <bool COUNT, bool RASTER>
+template <bool COUNT, bool RASTER, bool WIDE>
 __global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
                                                   const ViewDev* __restrict__ views, int b, QueueDev q,
                                                   const unsigned int* count, unsigned int count_fixed, QueueDev hq,
                                                   unsigned int* count_hit, void* tape, uint64_t ntot,
                                                   unsigned long long* counters, const unsigned long long* raster)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const TapeDev tp = tape_of(tape, ntot);
     const unsigned int n = count ? *count : count_fixed;
     unsigned int n_box = 0;
@@ -91,10 +91,18 @@ __global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
                     h.tri = tri;
                 }
             } else {
-                const int nodes = traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), *s.tmin_dev,
-                                                  __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x,
-                                                  COUNT ? &n_tri : nullptr);
-                if (COUNT) n_box += 2u * (unsigned int)max(nodes, 0);
+                // the counting variant counts the binary tree's work (the algorithmic work of the
+                // path: two box tests per node visit, one solve per triangle), the timed one runs
+                // the scene's wide BVH
+                if (COUNT) {
+                    const int nodes = traverse<false>(s, xyz(a), xyz(qd), __float_as_int(a.w), *s.tmin_dev,
+                                                      __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x,
+                                                      &n_tri);
+                    n_box += 2u * (unsigned int)max(nodes, 0);
+                } else {
+                    trace_as<false, WIDE>(s, xyz(a), xyz(qd), __float_as_int(a.w), *s.tmin_dev,
+                                          __int_as_float(0x7f800000), h, sstk + threadIdx.x);
+                }
             }
             if (h.tri < 0 && b == 0) {
                 const uint64_t g = v.offset + __float_as_uint(qd.w);
@@ -194,13 +202,13 @@ __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* _
     if (lane_id() == 0 && n_cand) atomicAdd(counters + 5, n_cand);
 }
 
-template <bool COUNT>
+template <bool COUNT, bool WIDE>
 __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ scenes,
                                                  const ViewDev* __restrict__ views, int b, ShadowDev sq,
                                                  const unsigned int* count, void* tape, uint64_t ntot, int nvx,
                                                  unsigned long long* counters)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count;
     unsigned int n_box = 0;
@@ -210,10 +218,14 @@ __global__ void __launch_bounds__(256) k_wshadow(const SceneDev* __restrict__ sc
         const ViewDev& v = views[__float_as_int(ad.w)];
         const SceneDev& s = scenes[v.scene];
         Hit h;
-        const int nodes = traverse<true>(s, xyz(a), xyz(dd), __float_as_int(a.w), *s.tmin_dev,
-                                         __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x,
-                                         COUNT ? &n_tri : nullptr);
-        if (COUNT) n_box += 2u * (unsigned int)max(nodes, 0);
+        if (COUNT) {
+            const int nodes = traverse<true>(s, xyz(a), xyz(dd), __float_as_int(a.w), *s.tmin_dev,
+                                             __int_as_float(0x7f800000), h, sstk + threadIdx.x, blockDim.x, &n_tri);
+            n_box += 2u * (unsigned int)max(nodes, 0);
+        } else {
+            trace_as<true, WIDE>(s, xyz(a), xyz(dd), __float_as_int(a.w), *s.tmin_dev, __int_as_float(0x7f800000), h,
+                                 sstk + threadIdx.x);
+        }
         const uint64_t g = v.offset + __float_as_uint(dd.w);
         if (h.tri < 0) {
             const float4 ai = sq.addi[i];
@@ -453,7 +465,7 @@ __global__ void __launch_bounds__(256) k_wclosest_refill(const SceneDev* __restr
                                                          unsigned int* count_hit, unsigned int* fetch,
                                                          unsigned long long* counters)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const unsigned int n = *count;
     uint32_t lstk[MR_LSTACK];
     Trav T;
@@ -506,7 +518,7 @@ __global__ void MR_TRACE_BOUNDS k_wshadow_refill(const SceneDev* __restrict__ sc
                                                         const unsigned int* count, unsigned int* fetch, void* tape,
                                                         uint64_t ntot, int nvx, unsigned long long* counters)
 {
-    extern __shared__ uint32_t sstk[];
+    extern __shared__ __align__(16) uint32_t sstk[];
     const TapeDev tp = tape_of(tape, ntot, nvx);
     const unsigned int n = *count;
     uint32_t lstk[MR_LSTACK];
@@ -710,11 +722,20 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
                     int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
                     int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist,
-                    const ViewDev* hviews, const SceneDev* hscenes, bool raster)
+                    const ViewDev* hviews, const SceneDev* hscenes, bool raster, const mirres_wave_shape& shape)
 {
+    // per stage (0 closest, 1 shade, 2 shadow, 3 raygen): threads per block and the grid cap
+    const int blk_c = shape.block[0], blk_h = shape.block[1], blk_s = shape.block[2], blk_g = shape.block[3];
+    const int cap_c = sms * shape.blocks_per_sm[0], cap_h = sms * shape.blocks_per_sm[1];
+    const int cap_s = sms * shape.blocks_per_sm[2], cap_g = sms * shape.blocks_per_sm[3];
     bool interp = false;  // any scene with interpolated normals
-    for (int i = 0; i < n_views; ++i) interp = interp || hscenes[hviews[i].scene].vnrm != nullptr;
-    const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;
+    bool wide = true;     // every scene traversed through a wide BVH: no lane refill (binary only)
+    for (int i = 0; i < n_views; ++i) {
+        interp = interp || hscenes[hviews[i].scene].vnrm != nullptr;
+        wide = wide && (hscenes[hviews[i].scene].wnodes != nullptr || hscenes[hviews[i].scene].n_tris < 2);
+    }
+    const size_t smem = sizeof(uint32_t) * MR_SSTACK * 256;  // the refilling kernels run 256 threads
+    const size_t stack_c = sizeof(uint32_t) * MR_SSTACK * (size_t)blk_c, stack_s = sizeof(uint32_t) * MR_SSTACK * (size_t)blk_s;
     // the refilling kernels run one resident wave of blocks
     int occ_c = 0, occ_s = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, count ? k_wclosest_refill<true> : k_wclosest_refill<false>,
@@ -736,8 +757,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         const uint32_t n = (uint32_t)((wv + 1 < n_waves ? wave_first[wv + 1] : total) - first);
         cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (5 * max_bounces + 3), st);
         mark(3, true);
-        k_wraygen<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(views, n_views, rng, first, n, qa, tape, total, nvx,
-                                                             res);
+        k_wraygen<<<grid_cap(n, blk_g, cap_g), blk_g, 0, st>>>(views, n_views, rng, first, n, qa, tape, total, nvx,
+                                                               res);
         mark(3, false);
         QueueDev cur = qa, nxt = qb;
         for (int b = 0; b < max_bounces; ++b) {
@@ -762,36 +783,39 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                         scenes, views, vi, first, n, cur.d, keys, counters);
                 }
             }
-            if (MR_REFILL_CLOSEST && b > 0)  // primary rays stay coherent in the plain stage kernel
+            if (MR_REFILL_CLOSEST && b > 0 && !wide)  // primary rays stay coherent in the plain stage kernel
                 (count ? k_wclosest_refill<true> : k_wclosest_refill<false>)<<<grid_c, 256, smem, st>>>(
                     scenes, views, cur, cnt_in, hq, qc + 3 * b, fetch + 2 * b, counters);
             else
-                (keys ? (count ? k_wclosest<true, true> : k_wclosest<false, true>)
-                      : (count ? k_wclosest<true, false> : k_wclosest<false, false>))<<<grid_cap(n, 256, sms * 8), 256,
-                                                                                        smem, st>>>(
+                (keys ? (count ? k_wclosest<true, true, false>
+                               : (wide ? k_wclosest<false, true, true> : k_wclosest<false, true, false>))
+                      : (count ? k_wclosest<true, false, false>
+                               : (wide ? k_wclosest<false, false, true> : k_wclosest<false, false, false>)))<<<
+                    grid_cap(n, blk_c, cap_c), blk_c, stack_c, st>>>(
                     scenes, views, b, cur, cnt_in, n, hq, qc + 3 * b, tape, total, counters, keys);
             mark(0, false);
             mark(1, true);
             const bool reuse_b = b == 0 && res.ytex != nullptr;
             (reuse_b ? (interp ? k_wshade<true, true> : k_wshade<true, false>)
-                     : (interp ? k_wshade<false, true> : k_wshade<false, false>))<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(
+                     : (interp ? k_wshade<false, true> : k_wshade<false, false>))<<<grid_cap(n, blk_h, cap_h), blk_h, 0, st>>>(
                 scenes, views, rng, b, M, hq, qc + 3 * b, nxt, qc + 3 * b + 1, sq, qc + 3 * b + 2, tape, total, nvx,
                 res, counters);
             if (reuse_b && temporal == 2)
-                k_wtemporal<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, M, temporal_cap, hq, qc,
-                                                                       res, hist);
+                k_wtemporal<<<grid_cap(n, blk_h, cap_h), blk_h, 0, st>>>(scenes, views, rng, M, temporal_cap, hq, qc,
+                                                                         res, hist);
             if (reuse_b)
-                k_wreuse<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(scenes, views, rng, M, reuse_k, reuse_radius, hq,
-                                                                    qc, sq, qc + 2, res, hist, tape, total, nvx);
+                k_wreuse<<<grid_cap(n, blk_h, cap_h), blk_h, 0, st>>>(scenes, views, rng, M, reuse_k, reuse_radius, hq,
+                                                                      qc, sq, qc + 2, res, hist, tape, total, nvx);
             if (reuse_b && temporal)
-                k_whist_miss<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(first, n, tape, total, hist);
+                k_whist_miss<<<grid_cap(n, blk_h, cap_h), blk_h, 0, st>>>(first, n, tape, total, hist);
             mark(1, false);
             mark(2, true);
-            if (MR_REFILL)
+            if (MR_REFILL && !wide)
                 (count ? k_wshadow_refill<true> : k_wshadow_refill<false>)<<<grid_s, 256, smem, st>>>(
                     scenes, views, b, sq, qc + 3 * b + 2, fetch + 2 * b + 1, tape, total, nvx, counters);
             else
-                (count ? k_wshadow<true> : k_wshadow<false>)<<<grid_cap(n, 256, sms * 8), 256, smem, st>>>(
+                (count ? k_wshadow<true, false> : (wide ? k_wshadow<false, true> : k_wshadow<false, false>))<<<
+                    grid_cap(n, blk_s, cap_s), blk_s, stack_s, st>>>(
                     scenes, views, b, sq, qc + 3 * b + 2, tape, total, nvx, counters);
             mark(2, false);
             QueueDev t = cur;

@@ -17,12 +17,13 @@ from . import build as _build
 
 __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_view", "make_params",
            "mirres_context_create", "mirres_context_destroy", "mirres_scene_create", "mirres_scene_destroy",
-           "mirres_scene_validate",
+           "mirres_scene_validate", "mirres_scene_set_traversal", "MIRRES_TRAVERSAL_BINARY", "MIRRES_TRAVERSAL_WIDE",
            "mirres_bvh_build", "mirres_bvh_refit", "mirres_bvh_set_builder", "MIRRES_BVH_LBVH", "MIRRES_BVH_PLOC",
            "mirres_scene_set_normals", "MIRRES_NORMALS_FACE", "MIRRES_NORMALS_INTERPOLATED", "mirres_tape_bytes", "mirres_tape_bytes_mode",
            "mirres_reuse_history_bytes", "mirres_render",
            "mirres_render_noalloc",
            "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
+           "WaveShape", "mirres_set_wave_shape", "mirres_get_wave_shape", "mirres_autotune_wave",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_env_export_flat",
            "mirres_get_counters",
            "mirres_get_work_counters", "EawtParams", "mirres_eawt_record_bytes", "mirres_gbuffer", "mirres_eawt",
@@ -38,6 +39,8 @@ MIRRES_FULL_MAX_BOUNCES = 16
 GRAD_PRIMARY, GRAD_FULL = 0, 1
 MIRRES_BVH_LBVH, MIRRES_BVH_PLOC = 0, 1
 MIRRES_NORMALS_FACE, MIRRES_NORMALS_INTERPOLATED = 0, 1
+MIRRES_FLAG_STAGE_EVENTS, MIRRES_FLAG_COUNT_WORK, MIRRES_FLAG_RASTER = 1, 2, 4
+MIRRES_TRAVERSAL_BINARY, MIRRES_TRAVERSAL_WIDE = 0, 1
 MIRRES_NOALLOC_SCRATCH_BYTES = 512 * 1024
 MIRRES_NOALLOC_MAX_VIEWS = 4096
 MIRRES_NOALLOC_MAX_SCENES = 256
@@ -72,13 +75,30 @@ class Params(C.Structure):
                 ("reuse_history_bytes", C.c_uint64), ("max_visits", C.c_int32)]
 
 
+class WaveShape(C.Structure):
+    _fields_ = [("wave_log2", C.c_int32), ("block", C.c_int32 * 4), ("blocks_per_sm", C.c_int32 * 4)]
+
+
+WAVE_STAGES = ("closest", "shade", "shadow", "raygen")  # index order of WaveShape.block / blocks_per_sm
+
+
+def _shape_dict(w: WaveShape):
+    return dict(wave_log2=int(w.wave_log2), block=[int(x) for x in w.block],
+                blocks_per_sm=[int(x) for x in w.blocks_per_sm])
+
+
+def _shape_struct(d):
+    return WaveShape(int(d["wave_log2"]), (C.c_int32 * 4)(*[int(x) for x in d["block"]]),
+                     (C.c_int32 * 4)(*[int(x) for x in d["blocks_per_sm"]]))
+
+
 class EawtParams(C.Structure):
     _fields_ = [("sigma_rt", C.c_float), ("sigma_n", C.c_float), ("sigma_x", C.c_float), ("levels", C.c_int32)]
 
 
 class LkParams(C.Structure):
     _fields_ = [("sigma", C.c_float), ("w_albedo", C.c_float), ("w_roughness", C.c_float), ("seed_lo", C.c_uint32),
-                ("seed_hi", C.c_uint32)]
+                ("seed_hi", C.c_uint32), ("w_normal", C.c_float)]
 
 
 class Grads(C.Structure):
@@ -112,6 +132,7 @@ def lib():
                 "mirres_bvh_build": (st, [vp, vp]),
                 "mirres_bvh_refit": (st, [vp, vp]),
                 "mirres_bvh_set_builder": (st, [vp, i32]),
+                "mirres_scene_set_traversal": (st, [vp, i32]),
                 "mirres_scene_set_normals": (st, [vp, i32]),
                 "mirres_tape_bytes": (sz, [C.POINTER(View), i32]),
                 "mirres_tape_bytes_mode": (sz, [C.POINTER(View), i32, i32]),
@@ -122,6 +143,10 @@ def lib():
                                          C.c_uint64, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                          C.POINTER(C.c_float), vp]),
                 "mirres_set_launch": (st, [vp, i32, i32, i32]),
+                "mirres_set_wave_shape": (st, [vp, C.POINTER(WaveShape)]),
+                "mirres_get_wave_shape": (st, [vp, C.POINTER(WaveShape)]),
+                "mirres_autotune_wave": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params), vp,
+                                              sz, C.c_uint64, C.POINTER(WaveShape), C.POINTER(C.c_float), vp]),
                 "mirres_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(i32)]),
                 "mirres_render_noalloc": (st, [C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
                                                C.POINTER(vp), vp, sz, vp]),
@@ -135,7 +160,7 @@ def lib():
                 "mirres_eawt_backward": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, sz, vp, vp]),
                 "mirres_mesh_regularizers": (st, [vp, vp, vp, C.c_float, C.c_float, vp, vp, vp]),
                 "mirres_material_smoothness": (st, [vp, vp, C.POINTER(View), i32, C.POINTER(LkParams), vp, vp, vp,
-                                                    vp]),
+                                                    vp, vp]),
                 "mirres_light_demod": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params), vp,
                                             sz, C.POINTER(vp), vp]),
                 "mirres_light_loss": (st, [vp, C.POINTER(View), i32, C.POINTER(vp), C.POINTER(vp), C.c_float, vp,
@@ -275,6 +300,10 @@ def mirres_bvh_refit(scene: Scene, stream=None):
     _check("mirres_bvh_refit", lib().mirres_bvh_refit(scene.handle, _stream(stream)))
 
 
+def mirres_scene_set_traversal(scene: Scene, mode: int):
+    _check("mirres_scene_set_traversal", lib().mirres_scene_set_traversal(scene.handle, int(mode)))
+
+
 def mirres_bvh_set_builder(scene: Scene, builder: int):
     _check("mirres_bvh_set_builder", lib().mirres_bvh_set_builder(scene.handle, int(builder)))
 
@@ -321,6 +350,31 @@ def mirres_autotune(ctx: Context, scenes, views, params: Params, tape, budget_sa
 
 def mirres_set_launch(ctx: Context, block, blocks_per_sm, chunk):
     _check("mirres_set_launch", lib().mirres_set_launch(ctx.handle, int(block), int(blocks_per_sm), int(chunk)))
+
+
+def mirres_set_wave_shape(ctx: Context, shape=None):
+    """shape = dict(wave_log2, block[4], blocks_per_sm[4]) (stages in WAVE_STAGES order), None = default"""
+    w = None if shape is None else C.byref(_shape_struct(shape))
+    _check("mirres_set_wave_shape", lib().mirres_set_wave_shape(ctx.handle, w))
+
+
+def mirres_get_wave_shape(ctx: Context):
+    w = WaveShape()
+    _check("mirres_get_wave_shape", lib().mirres_get_wave_shape(ctx.handle, C.byref(w)))
+    return _shape_dict(w)
+
+
+def mirres_autotune_wave(ctx: Context, scenes, views, params: Params, tape, budget_samples=0, stream=None):
+    """Tunes the batched wavefront's launch shape; returns dict(wave_log2, block, blocks_per_sm, ms)."""
+    vs = _views(views)
+    sc = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    w, ms = WaveShape(), C.c_float()
+    nbytes = tape.numel() * tape.element_size()
+    _check("mirres_autotune_wave", lib().mirres_autotune_wave(ctx.handle, sc, len(scenes), vs, len(vs),
+                                                              C.byref(params), _ptr(tape), nbytes,
+                                                              int(budget_samples), C.byref(w), C.byref(ms),
+                                                              _stream(stream)))
+    return dict(_shape_dict(w), ms=ms.value)
 
 
 def mirres_stage_times(ctx: Context):
@@ -434,13 +488,14 @@ def mirres_mesh_regularizers(ctx: Context, scene: Scene, rest_verts, w_smooth, w
 
 
 def mirres_material_smoothness(ctx: Context, scene: Scene, view, view_index, params: LkParams, loss=None,
-                               grad_albedo=None, grad_roughness=None, stream=None):
-    """adds w_albedo L_albedo + w_roughness L_roughness of one view's pixel-centre hits to loss[0]
-    and its gradient to the texture gradients (float32 CUDA tensors; any may be None)"""
+                               grad_albedo=None, grad_roughness=None, grad_verts=None, stream=None):
+    """adds w_albedo L_albedo + w_roughness L_roughness + w_normal L_normal of one view's
+    pixel-centre hits to loss[0] and its gradient to the texture and vertex gradients (float32
+    CUDA tensors; any may be None)"""
     vs = _views([view])
     _check("mirres_material_smoothness", lib().mirres_material_smoothness(
         ctx.handle, scene.handle, vs, int(view_index), C.byref(params), _ptr(loss), _ptr(grad_albedo),
-        _ptr(grad_roughness), _stream(stream)))
+        _ptr(grad_roughness), _ptr(grad_verts), _stream(stream)))
 
 
 def mirres_bvh_export(scene: Scene, keys=None, left=None, right=None, parent=None, lo=None, hi=None, stream=None):

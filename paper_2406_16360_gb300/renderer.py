@@ -20,7 +20,7 @@ class DeviceScene:
     """Scene inputs as CUDA tensors plus the library scene handle (LBVH and env tables built)."""
 
     def __init__(self, ctx: M.Context, scene, device="cuda", builder=M.MIRRES_BVH_LBVH,
-                 normals=M.MIRRES_NORMALS_FACE):
+                 normals=M.MIRRES_NORMALS_FACE, traversal=M.MIRRES_TRAVERSAL_BINARY):
         self.device = torch.device(device)
         self.verts = _dev(scene.verts, torch.float32, self.device)
         self.tris = _dev(scene.tris, torch.int32, self.device)
@@ -33,6 +33,7 @@ class DeviceScene:
                                             self.metallic, self.env)
         M.mirres_bvh_set_builder(self.handle, builder)
         M.mirres_scene_set_normals(self.handle, normals)
+        M.mirres_scene_set_traversal(self.handle, traversal)
         M.mirres_bvh_build(self.handle)
         self._versions = self._param_versions()
 
@@ -57,11 +58,12 @@ class DeviceScene:
 class GpuWorkload:
     """A synthetic workload resident on one GPU."""
 
-    def __init__(self, workload, device=0, ctx=None, builder=M.MIRRES_BVH_LBVH, normals=M.MIRRES_NORMALS_FACE):
+    def __init__(self, workload, device=0, ctx=None, builder=M.MIRRES_BVH_LBVH, normals=M.MIRRES_NORMALS_FACE,
+                 traversal=M.MIRRES_TRAVERSAL_BINARY):
         self.workload = workload
         self.ctx = ctx or M.mirres_context_create(device)
         self.device = torch.device("cuda", device)
-        self.scenes = [DeviceScene(self.ctx, s, self.device, builder=builder, normals=normals)
+        self.scenes = [DeviceScene(self.ctx, s, self.device, builder=builder, normals=normals, traversal=traversal)
                        for s in workload.scenes]
         self.views = list(workload.views)
         self.samples = workload.samples
@@ -102,8 +104,10 @@ class GpuWorkload:
                          f"{len(self.scenes)} scenes", f"{self.samples} samples", f"M={self.workload.ris_m}"])
 
     def autotune(self, tape=None, budget=32_000_000, cache=None):
-        """Pick the batched launch shape: from the JSON cache if this (GPU, workload shape) was
-        tuned before, else by timing every compiled variant (mirres_autotune) and caching it."""
+        """Pick the launch shapes of the batched launches: from the JSON cache if this (GPU,
+        workload shape) was tuned before, else by timing them -- the persistent kernel's compiled
+        variants and chunk (mirres_autotune) and the wavefront's wave size and per-stage block
+        shape (mirres_autotune_wave) -- and caching both."""
         path = cache or os.environ.get("MIRRES_TUNE_CACHE") or os.path.join(
             os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json")
         key = self.tune_key()
@@ -113,12 +117,17 @@ class GpuWorkload:
                 data = json.load(open(path))
             except (OSError, ValueError):
                 data = {}
-        if key in data:
+        if key in data and "wave" in data[key]:
             e = data[key]
             M.mirres_set_launch(self.ctx, e["block"], e["blocks_per_sm"], e["chunk"])
+            M.mirres_set_wave_shape(self.ctx, e["wave"])
             return dict(e, cached=True)
         tape = tape if tape is not None else self.new_tape()
-        res = M.mirres_autotune(self.ctx, [s.handle for s in self.scenes], self.views, self.params(1), tape, budget)
+        scenes = [s.handle for s in self.scenes]
+        res = M.mirres_autotune(self.ctx, scenes, self.views, self.params(1), tape, budget)
+        wave = M.mirres_autotune_wave(self.ctx, scenes, self.views, self.params(1), tape, budget)
+        res["wave_ms"] = wave.pop("ms")
+        res["wave"] = wave
         data[key] = res
         os.makedirs(os.path.dirname(path), exist_ok=True)
         tmp = path + f".tmp{os.getpid()}"

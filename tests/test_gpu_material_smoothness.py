@@ -113,3 +113,62 @@ def test_argument_checks(M, ctx):
     with pytest.raises(M.MirresError):
         M.mirres_material_smoothness(ctx, ds.handle, view, 70000, M.LkParams(0.1, 1.0, 1.0, 0, 0), L)
     ds.close()
+
+
+@pytest.mark.parametrize("res,vi,seed,sigma", [((64, 64), 0, 3, 0.01), ((41, 27), 9, 2 ** 33 + 5, 0.05)])
+def test_normal_term_matches_oracle(M, ctx, res, vi, seed, sigma):
+    """the normal term of L_k (interpolated vertex normals, the texture-space offset carried into
+    the hit triangle by its texture map): loss and vertex gradient against the oracle, alone and
+    added to the albedo / roughness terms of the same call"""
+    from paper_2406_16360_gb300.renderer import DeviceScene
+    w = synth.config2(res=res[0], n_views=1, tex=32, spp=1)
+    sc = w.scenes[0]
+    K, c2w = synth.look_at((0.3, 1.2, 3.2), (0.0, 0.0, 0.0), res[0], res[1], 40.0)
+    view = synth.View(K, c2w, res[0], res[1], 1, 1)
+    ds = DeviceScene(ctx, sc, normals=M.MIRRES_NORMALS_INTERPOLATED)
+    wn = 0.7
+    L = torch.zeros(1, device="cuda")
+    gv = torch.zeros_like(ds.verts)
+    M.mirres_material_smoothness(ctx, ds.handle, view, vi, M.LkParams(sigma, 0.0, 0.0, seed & 0xFFFFFFFF,
+                                                                          seed >> 32, wn), L, None, None, gv)
+    torch.cuda.synchronize()
+    osc = O.OracleScene(sc, normals=1)
+    Lr, gvr, info = S.material_smoothness_normal(osc, view, vi, sigma, wn, seed=seed)
+    assert info["n_normal"] > 0.5 * info["n_points"] > 100
+    # a pixel whose hit is a grazing decision may take another triangle: its term (at most
+    # 2 w / |X| for unit normals) and its gradient are left out of the bar
+    n_flag = int(info["flagged"].sum())
+    n = info["n_points"]
+    assert abs(float(L) - Lr) <= 1e-3 * abs(Lr) + 2.0 * wn * n_flag / n + 1e-7, (float(L), Lr, n_flag)
+    # vertex gradients away from the flagged pixels: a grazing hit may land on the neighbouring
+    # triangle, whose normal terms reach the vertices two rings around it (the vertex normals'
+    # normalisation spreads them over the faces around each vertex)
+    g = gv.cpu().numpy().astype(np.float64)
+    keep = np.ones(sc.verts.shape[0], dtype=bool)
+    if n_flag:
+        tri_of, _, _ = S.pixel_centre_hits(osc, view)
+        ring = np.unique(sc.tris[tri_of[info["flagged"]]])
+        for _ in range(2):
+            ring = np.unique(sc.tris[np.isin(sc.tris, ring).any(axis=1)])
+        keep[ring] = False
+    tol = 1e-3 * np.abs(gvr) + 1e-4 * np.abs(gvr).max() + 1e-5 * info["abs_verts"]
+    bad = (np.abs(g - gvr) > tol).any(axis=1) & keep
+    assert not bad.any(), (int(bad.sum()), np.abs(g - gvr)[bad].max(), np.abs(gvr).max())
+    assert keep.sum() > 0.9 * keep.size
+    # the normal term adds to the texture terms of the same call; face normals give no normal term
+    L2 = torch.zeros(1, device="cuda")
+    M.mirres_material_smoothness(ctx, ds.handle, view, vi, M.LkParams(sigma, 1.0, 1.0, seed & 0xFFFFFFFF,
+                                                                          seed >> 32, wn), L2)
+    L3 = torch.zeros(1, device="cuda")
+    M.mirres_material_smoothness(ctx, ds.handle, view, vi, M.LkParams(sigma, 1.0, 1.0, seed & 0xFFFFFFFF,
+                                                                          seed >> 32, 0.0), L3)
+    torch.cuda.synchronize()
+    assert abs(float(L2) - float(L3) - float(L)) <= 1e-5 * float(L2) + 1e-7
+    ds.close()
+    df = DeviceScene(ctx, sc)
+    L4 = torch.zeros(1, device="cuda")
+    gv4 = torch.zeros_like(df.verts)
+    M.mirres_material_smoothness(ctx, df.handle, view, vi, M.LkParams(sigma, 0.0, 0.0, 0, 0, wn), L4, None, None, gv4)
+    torch.cuda.synchronize()
+    assert float(L4) == 0.0 and float(gv4.abs().max()) == 0.0
+    df.close()

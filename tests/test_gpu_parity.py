@@ -316,3 +316,65 @@ def test_config2_reduced_forward_backward(M, ctx):
     gw = _gw(ctx, w)
     images, tape, st = _check_forward(gw, w, 1)
     _grad_check(gw, w, images, tape)
+
+
+def _wide_workloads():
+    return {"config1": synth.config1(),
+            "config2_reduced": synth.config2(res=40, n_views=2, tex=64, spp=4),
+            "scenes3": synth.config5(seed=3, n_scenes=3, max_tris=6000, res_choices=(16, 24), spp_choices=(2, 3),
+                                     tex=16)}
+
+
+def _defined_words_differ(a, b):
+    """per sample: any tape word that both renders define differs (words 9-12 are defined where a
+    candidate was selected, 13-16 where L_ind != 0; the rest always)"""
+    fa, fb = a.view(np.float32), b.view(np.float32)
+    differ = np.any(a[:9] != b[:9], axis=0)
+    sel = (a[1].view(np.int32) >= 0) | (b[1].view(np.int32) >= 0)
+    differ |= sel & np.any(a[9:13] != b[9:13], axis=0)
+    ind = np.any(fa[3:6] != 0.0, axis=0) | np.any(fb[3:6] != 0.0, axis=0)
+    differ |= ind & np.any(a[13:17] != b[13:17], axis=0)
+    return differ
+
+
+@pytest.mark.parametrize("name", list(_wide_workloads().keys()))
+@pytest.mark.parametrize("launch", [0, 1, 2])
+def test_wide_bvh_takes_the_binary_trees_hits(M, ctx, name, launch):
+    """the 8-wide BVH (quantised child boxes rounded outwards) and the binary tree it was
+    collapsed from find the same closest hits: renders through either agree word for word on
+    every sample, except samples with a grazing decision the oracle flags (a ray that touches a
+    binary box within rounding may be culled by the binary tree's exact box, not by the wide
+    tree's wider one); also after the vertices moved and both trees were refitted"""
+    from paper_2406_16360_gb300.renderer import GpuWorkload
+    w = _wide_workloads()[name]
+    gb = GpuWorkload(w, 0, ctx=ctx)
+    gw = GpuWorkload(w, 0, ctx=ctx, traversal=M.MIRRES_TRAVERSAL_WIDE)
+    n = w.samples
+    for moved in (False, True):
+        scenes = w.scenes
+        if moved:
+            rng = np.random.Generator(np.random.PCG64(8))
+            scenes = []
+            for sb, sw, sc in zip(gb.scenes, gw.scenes, w.scenes):
+                v = (sc.verts + rng.normal(scale=0.003, size=sc.verts.shape)).astype(np.float32)
+                for ds in (sb, sw):
+                    with torch.no_grad():
+                        ds.verts.copy_(torch.as_tensor(v, device="cuda"))
+                    M.mirres_bvh_refit(ds.handle)
+                scenes.append(synth.Scene(v, sc.tris, sc.tri_uv, sc.albedo, sc.roughness, sc.metallic, sc.env))
+        _, tape_w = gw.render(launch=launch)
+        _, tape_b = gb.render(launch=launch)
+        torch.cuda.synchronize()
+        a = tape_w.cpu().numpy().view(np.uint32).reshape(-1, n)[:17]
+        b = tape_b.cpu().numpy().view(np.uint32).reshape(-1, n)[:17]
+        differ = _defined_words_differ(a, b)
+        if differ.any():
+            margins = np.concatenate([O.render_samples(O.OracleScene(scenes[v.scene]), v, vi, w.ris_m, seed=w.seed)
+                                      ["sample_margin"].reshape(-1) for vi, v in enumerate(w.views)])
+            assert np.all(margins[differ] < 1.0), (name, launch, moved, int(differ.sum()),
+                                                   margins[differ].max())
+        assert differ.mean() < 1e-3, (name, launch, moved, int(differ.sum()))
+    c = M.mirres_get_counters(ctx)  # no traversal reached a cap or overflowed
+    assert c[7] == 0
+    for s in gb.scenes + gw.scenes:
+        s.close()

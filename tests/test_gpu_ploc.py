@@ -60,9 +60,9 @@ def _export(M, ds, F):
                 hi=hi.cpu().numpy())
 
 
-def _scene(ctx, M, sc, builder):
+def _scene(ctx, M, sc, builder, traversal=0):
     from paper_2406_16360_gb300.renderer import DeviceScene
-    return DeviceScene(ctx, sc, builder=builder)
+    return DeviceScene(ctx, sc, builder=builder, traversal=traversal)
 
 
 def _check_tree(g, sc):
@@ -122,7 +122,11 @@ def test_ploc_refit_equals_rebuild(M, ctx):
     ds.close()
 
 
-def test_ploc_hits_equal_lbvh_hits(M, ctx):
+@pytest.mark.parametrize("traversal", [0, 1])
+def test_ploc_hits_equal_lbvh_hits(M, ctx, traversal):
+    """hits do not depend on the hierarchy: the clustering tree and the Karras tree give the
+    same closest and any hits, through the binary trees and through the 8-wide BVHs collapsed
+    from them (a clustering tree's small subtrees need not cover consecutive leaves)"""
     sc = synth.object_scene(200, 100, 4, 8, 16, 8)
     rng = np.random.Generator(np.random.PCG64(5))
     n = 200000
@@ -133,7 +137,7 @@ def test_ploc_hits_equal_lbvh_hits(M, ctx):
     rays = torch.as_tensor(np.concatenate([o, d], 1).astype(np.float32), device=dev).contiguous()
     out = {}
     for b in (M.MIRRES_BVH_LBVH, M.MIRRES_BVH_PLOC):
-        ds = _scene(ctx, M, sc, b)
+        ds = _scene(ctx, M, sc, b, traversal)
         tri = torch.zeros(n, dtype=torch.int32, device=dev)
         tuv = torch.zeros((n, 3), dtype=torch.float32, device=dev)
         anyh = torch.zeros(n, dtype=torch.int32, device=dev)

@@ -138,3 +138,86 @@ def test_central_differences_on_a_mesh():
             assert abs(fd - flat[idx]) <= 1e-6 * max(1.0, abs(fd)), (field, idx, fd, flat[idx])
             checked += 1
     assert checked >= 10
+
+
+# ---------------------------------------------------------------------------------------
+# the normal term of L_k (interpolated vertex normals)
+# ---------------------------------------------------------------------------------------
+def _tetra():
+    v = np.array([[1.0, 1.0, 1.0], [1.0, -1.0, -1.0], [-1.0, 1.0, -1.0], [-1.0, -1.0, 1.0]])
+    t = np.array([[0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]])  # outward
+    uv = np.tile(np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), (4, 1, 1))
+    return v, t, uv
+
+
+def test_vertex_normals_of_a_regular_tetrahedron_point_from_the_centre():
+    from oracle.material_smoothness import vertex_normals
+    v, t, _ = _tetra()
+    VN, _ = vertex_normals(v, t)
+    np.testing.assert_allclose(VN, v / np.linalg.norm(v, axis=1, keepdims=True), atol=1e-14)
+
+
+def test_normal_term_worked_example_at_a_vertex():
+    """a hit at vertex a (u = v = 0) of a face whose texture map is the identity, offset (1, 0):
+    the offset point is vertex b, so the term is w / 3 sum_c |VN_a - VN_b|_c with the
+    tetrahedron's radial normals"""
+    from oracle.material_smoothness import normal_term
+    v, t, uv = _tetra()
+    loss, g, counted, _ = normal_term(v, t, uv, np.array([0]), np.array([0.0]), np.array([0.0]),
+                                      np.array([[1.0, 0.0]]), 1, 0.6)
+    na, nb = v[0] / np.sqrt(3.0), v[1] / np.sqrt(3.0)
+    assert counted == 1
+    assert abs(loss - 0.6 / 3.0 * np.abs(na - nb).sum()) < 1e-14
+    # an offset of (0, 1) reaches vertex c; a half offset lands between a and b
+    loss_c, _, _, _ = normal_term(v, t, uv, np.array([0]), np.array([0.0]), np.array([0.0]),
+                                  np.array([[0.0, 1.0]]), 1, 0.6)
+    assert abs(loss_c - 0.2 * np.abs(na - v[2] / np.sqrt(3.0)).sum()) < 1e-14
+    loss_h, _, _, _ = normal_term(v, t, uv, np.array([0]), np.array([0.0]), np.array([0.0]),
+                                  np.array([[0.5, 0.0]]), 1, 0.6)
+    mid = (na + nb) / np.linalg.norm(na + nb)
+    assert abs(loss_h - 0.2 * np.abs(na - mid).sum()) < 1e-14
+
+
+def test_normal_term_vanishes_on_a_flat_mesh_and_for_a_singular_texture_map():
+    from oracle.material_smoothness import normal_term
+    rng = np.random.Generator(np.random.PCG64(3))
+    v = np.array([[0.0, 0, 0], [1, 0, 0], [0, 0, 1], [1, 0, 1]])
+    t = np.array([[0, 2, 1], [1, 2, 3]])
+    uv = rng.uniform(size=(2, 3, 2))
+    loss, g, counted, _ = normal_term(v, t, uv, np.array([0, 1, 1]), rng.uniform(0, 0.5, 3), rng.uniform(0, 0.5, 3),
+                                      rng.uniform(-0.1, 0.1, (3, 2)), 3, 1.0)
+    assert counted == 3 and loss == 0.0 and np.all(g == 0.0)
+    vt, tt, uvt = _tetra()
+    uvt[1] = [[0.0, 0.0], [1.0, 1.0], [2.0, 2.0]]  # collinear texture coordinates
+    loss, g, counted, _ = normal_term(vt, tt, uvt, np.array([1]), np.array([0.2]), np.array([0.3]),
+                                      np.array([[0.05, 0.0]]), 1, 1.0)
+    assert counted == 0 and loss == 0.0 and np.all(g == 0.0)
+
+
+def test_normal_term_gradient_matches_central_differences():
+    """the hit (triangle, barycentrics) and the offsets held fixed, L_normal is a smooth function
+    of the vertex positions away from sign changes: d L / d vertex against central differences"""
+    from oracle.material_smoothness import normal_term
+    from paper_2406_16360_gb300 import synth
+    sc = synth.config1().scenes[0]
+    v = sc.verts.astype(np.float64)[:642]  # the icosphere (the ground quad's vertices follow)
+    t = sc.tris[:1280].astype(np.int64)
+    uv = sc.tri_uv[:1280].astype(np.float64)
+    rng = np.random.Generator(np.random.PCG64(11))
+    v = v + rng.normal(scale=0.02, size=v.shape)  # away from the symmetric sphere
+    n = 200
+    tri = rng.integers(0, t.shape[0], n)
+    u = rng.uniform(0.05, 0.45, n)
+    w = rng.uniform(0.05, 0.45, n)
+    eps = rng.uniform(-0.01, 0.01, (n, 2))
+    loss, g, counted, _ = normal_term(v, t, uv, tri, u, w, eps, n, 0.7)
+    assert counted > 0.9 * n and loss > 0
+    touched = np.flatnonzero(np.abs(g).sum(1) > 0)
+    for k in rng.choice(touched, size=12, replace=False):
+        for c in range(3):
+            h = 1e-6
+            vp, vm = v.copy(), v.copy()
+            vp[k, c] += h
+            vm[k, c] -= h
+            fd = (normal_term(vp, t, uv, tri, u, w, eps, n, 0.7)[0] - normal_term(vm, t, uv, tri, u, w, eps, n, 0.7)[0]) / (2 * h)
+            assert abs(fd - g[k, c]) <= 1e-5 * abs(fd) + 1e-8, (k, c, fd, g[k, c])
