@@ -536,7 +536,8 @@ mirres_status mirres_material_smoothness(mirres_context* ctx, const mirres_scene
  * mirres_light_demod: demod[v] device [height][width][4] (16-byte aligned), overwritten with
  *   (c_d + c_s (3 channels), fraction of the pixel's samples whose primary ray hit). scenes,
  *   views, params and tape are those of the render (any launch; any grad_mode, whose tape
- *   size is checked); one thread per pixel, samples summed in order.
+ *   size is checked); each pixel's samples summed in order (blocks take tiles of whole pixels and
+ *   read the tape's sample-major words coalesced).
  * mirres_light_loss: loss[0] += weight L_light (device float, FP32 sums in no fixed order;
  *   may be NULL) and, if d_demod is not NULL, d_demod[v] device [height][width][3] overwritten
  *   with d(weight L_light) / d(c_d + c_s) = weight sign(Y - V) / (3 |P|) per channel (0 outside

@@ -34,6 +34,7 @@
 #define TAU_FRAME 1e-5  /* |n.z| in the orthonormal-basis sign choice */
 #define TAU_GRAZE 2e-3  /* cos of the viewing angle at the primary vertex: below it an FP32
                          * evaluation of the BRDF carries a relative error above ~3e-5 */
+#define U32 (1.0 / 16777216.0) /* the FP32 unit roundoff scale 2^-24 (test tolerances) */
 #define TAU_LEAK 1e-5   /* |dir . n_face| of a light or continuation direction when shading
                          * normals are interpolated (directions below the face are dropped) */
 
@@ -1059,6 +1060,7 @@ typedef struct {
     const orc_view* v;
     const orc_params* p;
     double R[9], o[3];
+    int want_sens; /* accumulate the FP32 sensitivity of each sample's radiance (test tolerance only) */
 } Ctx;
 
 typedef struct {
@@ -1100,6 +1102,7 @@ static void rng(const Ctx* c, uint32_t pixel, uint32_t sample, uint32_t bounce, 
 static void ctx_init(Ctx* c, const orc_scene* s, const orc_view* v, const orc_params* p)
 {
     c->s = s; c->v = v; c->p = p;
+    c->want_sens = 0;
     for (int i = 0; i < 3; ++i) {
         for (int j = 0; j < 3; ++j) c->R[3 * i + j] = v->c2w[4 * i + j];
         c->o[i] = v->c2w[4 * i + 3];
@@ -1165,9 +1168,9 @@ static void ris_at(const Ctx* c, uint32_t pix, int smp, int b, const Shade* sh, 
         double gamma = phat / q;                      /* gamma_s = p_hat / q_dir */
         double ua = orc_uniform(x[2]);
         /* relative FP32 error of gamma: the glossy lobe's conditioning (test tolerance only) */
-        double eg = gamma > 0.0 ? spec_share(sh->n, wo, dir, sh->alb, sh->rgh, sh->met, kind) *
-                                      ggx_slope(sh->n, wo, dir, a) * DTH
-                                : 0.0;
+        double eg = (gamma > 0.0 && (mg || c->want_sens))
+                        ? spec_share(sh->n, wo, dir, sh->alb, sh->rgh, sh->met, kind) * ggx_slope(sh->n, wo, dir, a) * DTH
+                        : 0.0;
         if (cnt) cnt[5]++;
         if (wrs_update(&rs, gamma, ua, j)) {
             r->y = dir; r->ytex = tex; r->ysub = x[3]; r->phat = phat;
@@ -1395,7 +1398,7 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         if (!(pind > 0.0) || (fc[0] <= 0.0 && fc[1] <= 0.0 && fc[2] <= 0.0)) break;
         if (b == 0) { rec->has_cont = 1; rec->wc = wc; rec->p_ind = pind; }
         if (b < ORC_MAXB) { rec->vx[b].has_cont = 1; rec->vx[b].wc = wc; rec->vx[b].p_ind = pind; }
-        {
+        if (c->want_sens) {
             /* FP32 error of f cos / p_ind: the GGX D in f and in the VNDF part of the mixture pdf
              * cancel to the extent their shares agree (test tolerance only) */
             Mix mx = mixture(s, sh.alb, sh.met);
@@ -1419,6 +1422,72 @@ static void path_sample(const Ctx* c, int px, int py, int smp, Rec* rec, Margin*
         plen += nh.t;
     }
     for (int k = 0; k < 3; ++k) { rec->rgb[k] = L[k]; rec->Lind[k] = Lind[k]; }
+}
+
+/* The radiance of a recorded path re-evaluated with every decision (hit triangles, selected
+ * candidates and their V W, continuation directions and pdfs) held, and the barycentrics of
+ * vertex `bp` moved by (du, dv) (test tolerance only). */
+static void path_value(const Ctx* c, const Rec* rec, int bp, double du, double dv, double out[3])
+{
+    const orc_scene* s = c->s;
+    const int kind = c->p->brdf_kind;
+    double beta[3] = {1, 1, 1};
+    out[0] = out[1] = out[2] = 0.0;
+    for (int b = 0; b < rec->nv && b < ORC_MAXB; ++b) {
+        const double u = rec->vx[b].u + (b == bp ? du : 0.0), v = rec->vx[b].v + (b == bp ? dv : 0.0);
+        Shade sh;
+        shade_at(s, rec->vx[b].tri, u, v, rec->vx[b].t, rec->vx[b].d, &sh, NULL);
+        v3 wo = vscale(rec->vx[b].d, -1.0);
+        if (rec->vx[b].sel >= 0 && rec->vx[b].WV != 0.0) {
+            double fc[3];
+            brdf_cos(sh.n, wo, rec->vx[b].y, sh.alb, sh.rgh, sh.met, kind, fc);
+            for (int k = 0; k < 3; ++k) out[k] += beta[k] * rec->vx[b].WV * s->env[3 * rec->vx[b].y_texel + k] * fc[k];
+        }
+        if (!rec->vx[b].has_cont) break;
+        double fc[3];
+        brdf_cos(sh.n, wo, rec->vx[b].wc, sh.alb, sh.rgh, sh.met, kind, fc);
+        for (int k = 0; k < 3; ++k) beta[k] *= fc[k] / rec->vx[b].p_ind;
+    }
+}
+
+/* FP32 sensitivity of a sample's radiance to the rounding of its hit points (test tolerance
+ * only): every vertex's barycentrics moved by +- the FP32 error of a single-precision solve of
+ * its ray, whose origin carries the rounding of the path before it (the lever); the material
+ * lookups, the shading normal and the shading point follow. Sum over vertices and the two
+ * barycentrics of the larger change of the largest channel. */
+static double path_hit_sens(const Ctx* c, const Rec* rec)
+{
+    if (rec->prim_tri < 0 || rec->nv < 1) return 0.0;
+    const orc_scene* s = c->s;
+    double base[3];
+    path_value(c, rec, -1, 0.0, 0.0, base);
+    v3 o = vload(c->o);
+    double lever = 0.0, sens = 0.0;
+    for (int b = 0; b < rec->nv && b < ORC_MAXB; ++b) {
+        v3 a, bb, cc;
+        tri_verts(s, rec->vx[b].tri, &a, &bb, &cc);
+        v3 e1 = vsub(bb, a), e2 = vsub(cc, a), md = vscale(rec->vx[b].d, -1.0);
+        v3 r0 = vcross(e2, md), r1 = vcross(md, e1);
+        double det = fabs(vdot(e1, r0));
+        if (det > 0.0) {
+            double l = 3.0 * U32 * (vlen(vsub(o, a)) + vlen(o) + lever) / det;
+            const double dbary[2] = {l * vlen(r0), l * vlen(r1)};
+            for (int comp = 0; comp < 2; ++comp) {
+                double worst = 0.0;
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    double o3[3];
+                    path_value(c, rec, b, comp == 0 ? sg * dbary[0] : 0.0, comp == 1 ? sg * dbary[1] : 0.0, o3);
+                    for (int k = 0; k < 3; ++k) worst = dmax(worst, fabs(o3[k] - base[k]));
+                }
+                sens += worst;
+            }
+        }
+        /* the next ray starts at this vertex's hit point */
+        lever += rec->vx[b].t;
+        o = vadd(a, vadd(vscale(e1, rec->vx[b].u), vscale(e2, rec->vx[b].v)));
+        if (!rec->vx[b].has_cont) break;
+    }
+    return sens;
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -1457,7 +1526,6 @@ static void sp_put(Sparse* sp, int buf, int64_t idx, double val)
  * intersection, du / dv); 5-7: the selected light direction; 8-10: the continuation direction;
  * 11-13: the shading normal; sgn = +1 or -1. */
 typedef struct { int comp; double sgn, du, dv, dn; } Pert;
-#define U32 (1.0 / 16777216.0)
 
 /* a unit vector with component k moved by rel, renormalised */
 static v3 nudge(v3 a, int k, double rel)
@@ -1872,7 +1940,7 @@ static void* job_run(void* arg)
             if (jb->mode == 0 && !jb->demod && jb->out_srgb) {
                 for (int k = 0; k < 3; ++k) jb->out_srgb[3 * ((size_t)i * spp + smp) + k] = rec.rgb[k];
                 if (jb->out_smargin) jb->out_smargin[(size_t)i * spp + smp] = pmg ? smg.m : INFINITY;
-                if (jb->out_ssens) jb->out_ssens[(size_t)i * spp + smp] = rec.sens;
+                if (jb->out_ssens) jb->out_ssens[(size_t)i * spp + smp] = rec.sens + path_hit_sens(c, &rec);
             }
             if (jb->mode == 0 && jb->demod) {
                 double o3[3];
@@ -1937,6 +2005,7 @@ static int run_jobs(int mode, int demod, const orc_scene* s, const orc_scene* ev
         jb->i1 = (int32_t)((int64_t)n * (t + 1) / nt);
         jb->out_rgb = out_rgb; jb->out_margin = out_margin; jb->out_prim = out_prim;
         jb->out_srgb = out_srgb; jb->out_smargin = out_smargin; jb->out_ssens = out_ssens;
+        jb->c.want_sens = out_ssens != NULL;
         jb->d_rgb = d_rgb;
     }
     if (nt == 1) job_run(&jobs[0]);

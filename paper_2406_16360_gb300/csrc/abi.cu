@@ -1131,30 +1131,35 @@ extern "C" mirres_status mirres_light_demod(mirres_context* ctx, mirres_scene* c
     MR_TRY(check_full(params, views, n_views));
     if (tape_bytes < tape_bytes_per_sample(full_vertices(views, n_views, params->grad_mode)) * total)
         return arg_error("tape_bytes is smaller than mirres_tape_bytes_mode(views, grad_mode)");
-    uint64_t total_pix = 0;
-    const std::vector<uint64_t> pix_off = pixel_offsets(vdev, total_pix);
+    // tiles of whole pixels per view (the kernel's work units)
+    std::vector<uint64_t> tile_off((size_t)n_views + 1, 0);
+    for (int i = 0; i < n_views; ++i) {
+        const uint64_t npx = (uint64_t)vdev[(size_t)i].width * vdev[(size_t)i].height;
+        const uint64_t P = (uint64_t)mr_light_tile_pixels(vdev[(size_t)i].spp);
+        tile_off[(size_t)i + 1] = tile_off[(size_t)i] + (npx + P - 1) / P;
+    }
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
     ctx->last_stream = st;
     Carver plan(nullptr);
     plan.take<ViewDev>((size_t)n_views);
     plan.take<SceneDev>((size_t)n_scenes);
-    plan.take<uint64_t>((size_t)n_views);
+    plan.take<uint64_t>((size_t)n_views + 1);
     plan.take<float*>((size_t)n_views);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
     ViewDev* d_views = cv.take<ViewDev>((size_t)n_views);
     SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
-    uint64_t* d_pixoff = cv.take<uint64_t>((size_t)n_views);
+    uint64_t* d_tiles = cv.take<uint64_t>((size_t)n_views + 1);
     float** d_out = cv.take<float*>((size_t)n_views);
     MR_CUDA(cudaMemcpyAsync(d_views, vdev.data(), sizeof(ViewDev) * vdev.size(), cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_scenes, sdev.data(), sizeof(SceneDev) * sdev.size(), cudaMemcpyHostToDevice, st));
-    MR_CUDA(cudaMemcpyAsync(d_pixoff, pix_off.data(), sizeof(uint64_t) * pix_off.size(), cudaMemcpyHostToDevice, st));
+    MR_CUDA(cudaMemcpyAsync(d_tiles, tile_off.data(), sizeof(uint64_t) * tile_off.size(), cudaMemcpyHostToDevice, st));
     MR_CUDA(cudaMemcpyAsync(d_out, demod, sizeof(float*) * (size_t)n_views, cudaMemcpyHostToDevice, st));
     bool interp = false;
     for (int i = 0; i < n_scenes; ++i) interp = interp || scenes[i]->normals != 0;
-    mr_launch_light_demod(d_scenes, d_views, d_pixoff, n_views, total_pix, total, make_rng(params), tape, d_out,
-                          ctx->sm_count, st, interp);
+    mr_launch_light_demod(d_scenes, d_views, d_tiles, n_views, tile_off[(size_t)n_views], total, make_rng(params),
+                          tape, d_out, ctx->sm_count, st, interp);
     MR_CUDA(cudaGetLastError());
     ctx->host_launches += 1;
     return MIRRES_OK;

@@ -902,65 +902,119 @@ __global__ void __launch_bounds__(256, MINB) k_backward(const SceneDev* __restri
 
 // ---------------------------------------------------------------------------------------
 // Monochrome light regulariser (Appendix A, L_light): the demodulated diffuse + specular
-// lighting at each pixel's primary vertex, from the tape of the render. One thread per pixel
-// (flattened over the views: pix_off[i] is view i's first pixel, views[i].offset its first
-// sample) sums its samples in order: out[view][pixel] = (mean c_d + c_s, fraction of samples
-// whose primary ray hit). The primary vertex is replayed as the adjoint does.
+// lighting at each pixel's primary vertex, from the tape of the render: out[view][pixel] = (mean
+// c_d + c_s, fraction of samples whose primary ray hit). The primary vertex is replayed as the
+// adjoint does. A block takes a tile of whole pixels of one view (P = floor(256 / spp) pixels,
+// one pixel in passes of 256 samples when spp > 256): its threads replay consecutive samples, so
+// that every tape word is read coalesced, and each pixel's samples are then summed in order
+// from shared memory. tile_off[i] is view i's first tile (tile_off[n_views] = all tiles).
 // ---------------------------------------------------------------------------------------
+constexpr int LD_BLOCK = 256;
+
+__device__ __forceinline__ int light_tile_pixels(int spp) { return spp <= LD_BLOCK ? LD_BLOCK / spp : 1; }
+
+// c_d + c_s of one sample (0 where its primary ray escaped); *hit = 1 where it hit
 template <bool INTERP>
-__global__ void __launch_bounds__(256) k_light_demod(const SceneDev* __restrict__ scenes,
-                                                     const ViewDev* __restrict__ views,
-                                                     const uint64_t* __restrict__ pix_off, int n_views,
-                                                     uint64_t total_pixels, uint64_t total, Rng rng,
-                                                     const void* tape, float* const* __restrict__ out)
+__device__ __forceinline__ float3 light_sample(const SceneDev& s, const ViewDev& v, const TapeDev& tp, Rng rng,
+                                               uint32_t pixel, uint32_t smp, uint64_t g, float& hit)
 {
+    float3 acc = f3(0.f, 0.f, 0.f);
+    hit = 0.0f;
+    const int tri = tp.tri[g];
+    if (tri < 0) return acc;
+    hit = 1.0f;
+    const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
+    const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
+    const uint4 xc = rng.draw(pixel, smp, (uint32_t)v.index, 0u, PURPOSE_CAMERA, 0u);
+    const float3 d = camera_dir(v, px, py, u24(xc.x), u24(xc.y));
+    float3 v0, e1, e2;
+    int tchk;
+    load_tri(s, __ldg(s.leaf_of + tri), v0, e1, e2, tchk);
+    float t, u, vv;
+    tri_solve(o, d, v0, e1, e2, t, u, vv);
+    Shade sh;
+    shade_at<INTERP>(s, tri, u, vv, d, sh);
+    const float3 wo = f3(-d.x, -d.y, -d.z);
+    const float wv = tp.wv[g];
+    if (tp.cand[g] >= 0 && wv != 0.0f) {
+        const float3 fc = brdf_cos<true>(sh.n, wo, f3(tp.y[0][g], tp.y[1][g], tp.y[2][g]), sh.m);
+        const float4 L = __ldg(s.env_texel + tp.ytex[g]);
+        acc = add(acc, f3(wv * L.x * fc.x, wv * L.y * fc.y, wv * L.z * fc.z));
+    }
+    const float3 li = f3(tp.lind[0][g], tp.lind[1][g], tp.lind[2][g]);
+    const float pind = tp.pind[g];
+    if (v.bounces > 1 && (li.x != 0.0f || li.y != 0.0f || li.z != 0.0f) && pind > 0.0f) {
+        const float3 fc = brdf_cos<true>(sh.n, wo, f3(tp.wc[0][g], tp.wc[1][g], tp.wc[2][g]), sh.m);
+        acc = add(acc, f3(fc.x / pind * li.x, fc.y / pind * li.y, fc.z / pind * li.z));
+    }
+    return acc;
+}
+
+template <bool INTERP>
+__global__ void __launch_bounds__(LD_BLOCK) k_light_demod(const SceneDev* __restrict__ scenes,
+                                                          const ViewDev* __restrict__ views,
+                                                          const uint64_t* __restrict__ tile_off, int n_views,
+                                                          uint64_t total, Rng rng, const void* tape,
+                                                          float* const* __restrict__ out)
+{
+    __shared__ float4 part[LD_BLOCK];
     const TapeDev tp = tape_of(const_cast<void*>(tape), total, 0);
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < total_pixels; p += stride) {
+    const uint64_t n_tiles = tile_off[n_views];
+    const int tid = threadIdx.x;
+    // block-uniform loops: every __syncthreads below is reached by the whole block
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         int vi = 0, hi = n_views - 1;
         while (vi < hi) {
             const int mid = (vi + hi + 1) >> 1;
-            if (pix_off[mid] <= p) vi = mid;
+            if (tile_off[mid] <= tile) vi = mid;
             else hi = mid - 1;
         }
         const ViewDev& v = views[vi];
         const SceneDev s = scenes[v.scene];
-        const uint32_t pixel = (uint32_t)(p - pix_off[vi]);
-        const int px = (int)(pixel % (uint32_t)v.width), py = (int)(pixel / (uint32_t)v.width);
-        const float3 o = f3(v.c2w[3], v.c2w[7], v.c2w[11]);
-        float3 acc = f3(0.f, 0.f, 0.f);
-        int hits = 0;
-        for (int smp = 0; smp < v.spp; ++smp) {
-            const uint64_t g = v.offset + (uint64_t)pixel * (uint64_t)v.spp + (uint64_t)smp;
-            const int tri = tp.tri[g];
-            if (tri < 0) continue;
-            ++hits;
-            const uint4 xc = rng.draw(pixel, (uint32_t)smp, (uint32_t)v.index, 0u, PURPOSE_CAMERA, 0u);
-            const float3 d = camera_dir(v, px, py, u24(xc.x), u24(xc.y));
-            float3 v0, e1, e2;
-            int tchk;
-            load_tri(s, __ldg(s.leaf_of + tri), v0, e1, e2, tchk);
-            float t, u, vv;
-            tri_solve(o, d, v0, e1, e2, t, u, vv);
-            Shade sh;
-            shade_at<INTERP>(s, tri, u, vv, d, sh);
-            const float3 wo = f3(-d.x, -d.y, -d.z);
-            const float wv = tp.wv[g];
-            if (tp.cand[g] >= 0 && wv != 0.0f) {
-                const float3 fc = brdf_cos<true>(sh.n, wo, f3(tp.y[0][g], tp.y[1][g], tp.y[2][g]), sh.m);
-                const float4 L = __ldg(s.env_texel + tp.ytex[g]);
-                acc = add(acc, f3(wv * L.x * fc.x, wv * L.y * fc.y, wv * L.z * fc.z));
+        const int spp = v.spp;
+        const uint32_t npx = (uint32_t)v.width * (uint32_t)v.height;
+        const uint32_t P = (uint32_t)light_tile_pixels(spp);
+        const uint32_t first = (uint32_t)(tile - tile_off[vi]) * P;
+        const uint32_t tpx = min(P, npx - first);
+        const uint32_t nsamp = tpx * (uint32_t)spp;
+        const uint64_t g0 = v.offset + (uint64_t)first * (uint64_t)spp;
+        float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);  // thread 0, one pixel over several passes
+        for (uint32_t base = 0; base < nsamp; base += LD_BLOCK) {
+            const uint32_t idx = base + (uint32_t)tid;
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (idx < nsamp) {
+                const uint32_t pixel = first + idx / (uint32_t)spp, smp = idx % (uint32_t)spp;
+                float h;
+                const float3 a = light_sample<INTERP>(s, v, tp, rng, pixel, smp, g0 + idx, h);
+                c = make_float4(a.x, a.y, a.z, h);
             }
-            const float3 li = f3(tp.lind[0][g], tp.lind[1][g], tp.lind[2][g]);
-            const float pind = tp.pind[g];
-            if (v.bounces > 1 && (li.x != 0.0f || li.y != 0.0f || li.z != 0.0f) && pind > 0.0f) {
-                const float3 fc = brdf_cos<true>(sh.n, wo, f3(tp.wc[0][g], tp.wc[1][g], tp.wc[2][g]), sh.m);
-                acc = add(acc, f3(fc.x / pind * li.x, fc.y / pind * li.y, fc.z / pind * li.z));
+            part[tid] = c;
+            __syncthreads();
+            if (spp <= LD_BLOCK) {
+                if ((uint32_t)tid < tpx) {
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int k = 0; k < spp; ++k) {  // the pixel's samples in order
+                        const float4 q = part[tid * spp + k];
+                        acc = make_float4(acc.x + q.x, acc.y + q.y, acc.z + q.z, acc.w + q.w);
+                    }
+                    const float inv_spp = 1.0f / (float)spp;
+                    reinterpret_cast<float4*>(out[vi])[first + (uint32_t)tid] =
+                        make_float4(acc.x * inv_spp, acc.y * inv_spp, acc.z * inv_spp, acc.w * inv_spp);
+                }
+            } else if (tid == 0) {
+                const uint32_t m = min((uint32_t)LD_BLOCK, nsamp - base);
+                for (uint32_t k = 0; k < m; ++k) {
+                    const float4 q = part[k];
+                    carry = make_float4(carry.x + q.x, carry.y + q.y, carry.z + q.z, carry.w + q.w);
+                }
             }
+            __syncthreads();
         }
-        const float inv_spp = 1.0f / (float)v.spp;
-        float4* o4 = reinterpret_cast<float4*>(out[vi]) + pixel;
-        *o4 = make_float4(acc.x * inv_spp, acc.y * inv_spp, acc.z * inv_spp, (float)hits * inv_spp);
+        if (spp > LD_BLOCK && tid == 0) {
+            const float inv_spp = 1.0f / (float)spp;
+            reinterpret_cast<float4*>(out[vi])[first] =
+                make_float4(carry.x * inv_spp, carry.y * inv_spp, carry.z * inv_spp, carry.w * inv_spp);
+        }
     }
 }
 
@@ -1334,13 +1388,16 @@ void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_view
 #endif
 }
 
-void mr_launch_light_demod(const SceneDev* scenes, const ViewDev* views, const uint64_t* pix_off, int n_views,
-                           uint64_t total_pixels, uint64_t total, Rng rng, const void* tape, float* const* out,
-                           int sms, cudaStream_t st, bool interp)
+int mr_light_tile_pixels(int spp) { return spp <= LD_BLOCK ? LD_BLOCK / spp : 1; }
+
+void mr_launch_light_demod(const SceneDev* scenes, const ViewDev* views, const uint64_t* tile_off, int n_views,
+                           uint64_t n_tiles, uint64_t total, Rng rng, const void* tape, float* const* out, int sms,
+                           cudaStream_t st, bool interp)
 {
-    if (total_pixels == 0) return;
-    (interp ? k_light_demod<true> : k_light_demod<false>)<<<grid_cap(total_pixels, 256, sms * 8), 256, 0, st>>>(
-        scenes, views, pix_off, n_views, total_pixels, total, rng, tape, out);
+    if (n_tiles == 0) return;
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_tiles, (uint64_t)sms * 8);
+    (interp ? k_light_demod<true> : k_light_demod<false>)<<<grid, LD_BLOCK, 0, st>>>(scenes, views, tile_off, n_views,
+                                                                                   total, rng, tape, out);
 }
 
 void mr_launch_light_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,

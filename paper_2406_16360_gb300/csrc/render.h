@@ -90,9 +90,12 @@ void mr_launch_backward(const SceneDev* scenes, const ViewDev* views, int n_view
 void mr_launch_l2(const float* img, const float* ref, int64_t n, float* dimg, float* loss, int sms, cudaStream_t st);
 // monochrome light regulariser: the demodulated lighting per pixel (out[view] [h][w][4]) and
 // the PRIMARY-mode adjoint of it (d_demod[view] [h][w][3])
-void mr_launch_light_demod(const SceneDev* scenes, const ViewDev* views, const uint64_t* pix_off, int n_views,
-                           uint64_t total_pixels, uint64_t total, Rng rng, const void* tape, float* const* out,
-                           int sms, cudaStream_t st, bool interp);
+// pixels per tile of the demodulated-lighting kernel for a view of `spp` samples per pixel; the
+// launch takes tile_off [n_views + 1] = the prefix sums of each view's ceil(pixels / tile)
+int mr_light_tile_pixels(int spp);
+void mr_launch_light_demod(const SceneDev* scenes, const ViewDev* views, const uint64_t* tile_off, int n_views,
+                           uint64_t n_tiles, uint64_t total, Rng rng, const void* tape, float* const* out, int sms,
+                           cudaStream_t st, bool interp);
 void mr_launch_light_backward(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, Rng rng,
                               const float* const* d_demod, const GradDev* grads, const void* tape,
                               unsigned long long* counters, int sms, cudaStream_t st, bool interp);

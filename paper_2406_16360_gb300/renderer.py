@@ -178,27 +178,53 @@ class GpuWorkload:
 
 
 class MirresRender(torch.autograd.Function):
-    """images = MirresRender.apply(gw, launch, seed, albedo, roughness, metallic, env, verts)
+    """images = MirresRender.apply(gw, launch, seed, *params)
 
-    The parameter tensors must be the ones the GpuWorkload's single scene borrows (updated in
-    place by the optimiser). Backward is the PRIMARY-mode adjoint of the paper (indirect rays
-    detached), replayed from the tape the forward wrote.
+    params = (albedo, roughness, metallic, env, verts) of every scene of the GpuWorkload, scene
+    after scene: the tensors the scenes borrow (updated in place by the optimiser). Returns the
+    images of all views stacked when they share one size, else concatenated flat ([sum H W, 3]).
+    Backward is the PRIMARY-mode adjoint of the paper (indirect rays detached), replayed from the
+    tape the forward wrote, for every scene at once.
     """
 
+    NAMES = ("albedo", "roughness", "metallic", "env", "verts")
+
     @staticmethod
-    def forward(ctx, gw, launch, seed, albedo, roughness, metallic, env, verts):
-        scene = gw.scenes[0]
-        for name, t in dict(albedo=albedo, roughness=roughness, metallic=metallic, env=env, verts=verts).items():
-            if t.data_ptr() != getattr(scene, name).data_ptr():
-                raise ValueError(f"{name} is not the tensor the scene borrows")
-        scene.refresh()
+    def forward(ctx, gw, launch, seed, *params):
+        if len(params) != 5 * len(gw.scenes):
+            raise ValueError("expected (albedo, roughness, metallic, env, verts) for every scene")
+        for si, scene in enumerate(gw.scenes):
+            for k, name in enumerate(MirresRender.NAMES):
+                if params[5 * si + k].data_ptr() != getattr(scene, name).data_ptr():
+                    raise ValueError(f"scene {si}: {name} is not the tensor the scene borrows")
+            scene.refresh()
         images, tape = gw.render(launch=launch, seed=seed)
         ctx.gw, ctx.launch, ctx.seed, ctx.tape = gw, launch, seed, tape
-        return torch.stack(images) if len(images) > 1 else images[0].unsqueeze(0)
+        ctx.shapes = [tuple(im.shape) for im in images]
+        if len(set(ctx.shapes)) == 1:
+            ctx.stacked = True
+            return torch.stack(images)
+        ctx.stacked = False
+        return torch.cat([im.reshape(-1, 3) for im in images])
 
     @staticmethod
     def backward(ctx, grad_images):
         gw = ctx.gw
-        d = [grad_images[i].contiguous() for i in range(grad_images.shape[0])]
-        g = gw.backward(d, ctx.tape, launch=ctx.launch, seed=ctx.seed)[0]
-        return None, None, None, g["albedo"], g["roughness"], g["metallic"], g["env"], g["verts"]
+        if ctx.stacked:
+            d = [grad_images[i].contiguous() for i in range(grad_images.shape[0])]
+        else:
+            d, off = [], 0
+            for shp in ctx.shapes:
+                n = shp[0] * shp[1]
+                d.append(grad_images[off:off + n].reshape(shp).contiguous())
+                off += n
+        g = gw.backward(d, ctx.tape, launch=ctx.launch, seed=ctx.seed)
+        out = [None, None, None]
+        for gs in g:
+            out += [gs[name] for name in MirresRender.NAMES]
+        return tuple(out)
+
+
+def scene_params(gw):
+    """the flat parameter list MirresRender.apply expects after (gw, launch, seed)"""
+    return [getattr(s, name) for s in gw.scenes for name in MirresRender.NAMES]

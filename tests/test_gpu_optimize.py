@@ -1,0 +1,165 @@
+"""The optimisation loop on the library (config 4's shape): checkpoint and resume, the autograd
+Function over several scenes, and -- opt-in, MIRRES_LONG=1 -- config 4 at its stated size next to
+the same loop at 64 x 64 driven by the FP64 oracle's gradients."""
+import copy
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2406_16360_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_16360_gb300 import mirres
+    return mirres
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.mirres_context_create(0)
+    yield c
+    c.close()
+
+
+def _small(res=40, pool=6):
+    from paper_2406_16360_gb300.optimize import config4_setup
+    truth = synth.config2(res=res, n_views=1, tex=32, spp=2, bounces=2).scenes[0]
+    init = copy.deepcopy(truth)
+    init.albedo[:] = 0.5
+    init.roughness[:] = 0.5
+    init.env[:] = 1.0
+    views = synth.hemisphere_views(pool, res, 2, 2, 7)
+    return truth, init, views
+
+
+def test_checkpoint_and_resume_continue_the_same_loop(M, ctx, tmp_path):
+    from paper_2406_16360_gb300.optimize import Loop
+    truth, init, views = _small()
+    a = Loop(truth, init, views, 3, 2e-2, 8, ctx=ctx)
+    for _ in range(8):
+        a.step()
+    full = list(a.curve)
+    pa = {k: getattr(a.scene, k).detach().clone() for k in ("albedo", "roughness", "env")}
+    a.close()
+    assert full[-1] < full[0]
+    b = Loop(truth, init, views, 3, 2e-2, 8, ctx=ctx)
+    for _ in range(4):
+        b.step()
+    path = str(tmp_path / "ck.pt")
+    b.save(path)
+    b.close()
+    c = Loop(truth, init, views, 3, 2e-2, 8, ctx=ctx)
+    c.load(path)
+    assert c.step_no == 4
+    for _ in range(4):
+        c.step()
+    # the same views, seeds and Adam state: the same curve up to the FP32 atomics' order
+    np.testing.assert_allclose(c.curve, full, rtol=1e-4)
+    for k, v in pa.items():
+        np.testing.assert_allclose(getattr(c.scene, k).detach().cpu().numpy(), v.cpu().numpy(), rtol=1e-3, atol=1e-5)
+    c.close()
+
+
+def test_autograd_over_several_scenes(M, ctx):
+    """MirresRender takes the parameters of every scene of a batch: its gradients are those of
+    one mirres_backward over the whole batch"""
+    from paper_2406_16360_gb300.renderer import GpuWorkload, MirresRender, scene_params
+    w = synth.config5(seed=3, n_scenes=3, max_tris=6000, res_choices=(16, 24), spp_choices=(2, 3), tex=16)
+    gw = GpuWorkload(w, 0, ctx=ctx)
+    params = scene_params(gw)
+    for p in params:
+        p.requires_grad_(True)
+    img = MirresRender.apply(gw, 1, 5, *params)
+    rng = np.random.Generator(np.random.PCG64(2))
+    g_img = torch.as_tensor(rng.normal(size=img.shape), dtype=torch.float32, device="cuda")
+    (img * g_img).sum().backward()
+    got = [p.grad.clone() for p in params]
+    for p in params:
+        p.requires_grad_(False)
+    # the same render and adjoint through the binding directly
+    images, tape = gw.render(launch=1, seed=5)
+    d, off = [], 0
+    for im in images:
+        n = im.shape[0] * im.shape[1]
+        d.append(g_img.reshape(-1, 3)[off:off + n].reshape(im.shape).contiguous() if img.dim() == 2
+                 else g_img[len(d)].contiguous())
+        off += n
+    ref = gw.backward(d, tape, launch=1, seed=5)
+    torch.cuda.synchronize()
+    k = 0
+    for gs in ref:
+        for name in MirresRender.NAMES:
+            np.testing.assert_allclose(got[k].cpu().numpy(), gs[name].cpu().numpy(), rtol=1e-4, atol=1e-6)
+            k += 1
+    for s in gw.scenes:
+        s.close()
+
+
+@pytest.mark.skipif(os.environ.get("MIRRES_LONG") != "1", reason="long optimisation runs: set MIRRES_LONG=1")
+def test_config4_stated_size_and_oracle_driven_loop(M, ctx):
+    """config 4 as stated (300 Adam steps at lr 1e-2 on the config-2 scene's textures and env from
+    a flat start, 8 random views of 800 x 800 per step, 4 bounces, 8 spp), and the same loop at
+    64 x 64 once with the library's gradients and once with the FP64 oracle's (same views, seeds
+    and targets): both loss curves fall and follow each other"""
+    from paper_2406_16360_gb300.optimize import Loop, config4_setup
+    steps = int(os.environ.get("MIRRES_CONFIG4_STEPS", "300"))
+    out = {}
+    truth, init, views = config4_setup(800, 8, 4, 32)
+    big = Loop(truth, init, views, 8, 1e-2, 32, ctx=ctx)
+    for _ in range(steps):
+        big.step()
+    out["800"] = big.curve
+    big.close()
+    truth, init, views = config4_setup(64, 8, 4, 32)
+    gpu = Loop(truth, init, views, 8, 1e-2, 32, ctx=ctx)
+    ora = Loop(truth, init, views, 8, 1e-2, 32, ctx=ctx)
+    for it in range(steps):
+        gpu.step()
+        # the oracle-driven step: the same views, seed and targets, FP64 gradients
+        idx = ora.choose(ora.step_no)
+        sc = ora.scene
+        cur = synth._scene(truth.verts, truth.tris, truth.tri_uv, sc.albedo.detach().cpu().numpy(),
+                           sc.roughness.detach().cpu().numpy(), sc.metallic.detach().cpu().numpy(),
+                           sc.env.detach().cpu().numpy())
+        osc = O.OracleScene(cur)
+        ora.opt.zero_grad()
+        tot = 0.0
+        grads = {k: np.zeros(getattr(sc, k).shape) for k in ("albedo", "roughness", "env")}
+        for vi, pi in enumerate(idx):
+            v = ora.pool[pi]
+            r = O.render(osc, v, vi, 32, seed=ora.seed + ora.step_no, margins=False)["rgb"]
+            diff = r - ora.targets[pi].double().cpu().numpy().reshape(-1, 3)
+            tot += float((diff ** 2).sum())
+            g = O.backward(osc, v, vi, 32, 2 * diff, seed=ora.seed + ora.step_no, want_abs=False)
+            for k in grads:
+                grads[k] += g[k]
+        for k in grads:
+            getattr(sc, k).grad = torch.as_tensor(grads[k], dtype=torch.float32, device="cuda")
+        ora.opt.step()
+        with torch.no_grad():
+            sc.albedo.clamp_(0.0, 1.0)
+            sc.roughness.clamp_(0.02, 1.0)
+            sc.env.clamp_(min=0.0)
+        ora.curve.append(tot)
+        ora.step_no += 1
+    out["64_gpu"], out["64_oracle"] = gpu.curve, ora.curve
+    gpu.close()
+    ora.close()
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open("gpurun_out/config4_curves.json", "w") as f:
+        json.dump(out, f)
+    a800, ag, ao = (np.array(out[k]) for k in ("800", "64_gpu", "64_oracle"))
+    print("config4 800x800: first", a800[:3], "last", a800[-3:])
+    print("64x64 library / oracle: first", ag[:2], ao[:2], "last", ag[-2:], ao[-2:])
+    assert a800[-10:].mean() < 0.5 * a800[:10].mean()
+    assert ag[-10:].mean() < 0.5 * ag[:10].mean()
+    np.testing.assert_allclose(ag, ao, rtol=2e-2)
