@@ -1452,9 +1452,10 @@ static void path_value(const Ctx* c, const Rec* rec, int bp, double du, double d
 
 /* FP32 sensitivity of a sample's radiance to the rounding of its hit points (test tolerance
  * only): every vertex's barycentrics moved by +- the FP32 error of a single-precision solve of
- * its ray, whose origin carries the rounding of the path before it (the lever); the material
- * lookups, the shading normal and the shading point follow. Sum over vertices and the two
- * barycentrics of the larger change of the largest channel. */
+ * its ray, 8 u (|o - v0| + |o| + lever) |row of A^-1| / |det| as for the texel sensitivity,
+ * whose origin carries the rounding of the path before it (the lever, its path length); the
+ * material lookups, the shading normal and the shading point follow. Sum over vertices and the
+ * two barycentrics of the larger change of the largest channel. */
 static double path_hit_sens(const Ctx* c, const Rec* rec)
 {
     if (rec->prim_tri < 0 || rec->nv < 1) return 0.0;
@@ -1470,7 +1471,7 @@ static double path_hit_sens(const Ctx* c, const Rec* rec)
         v3 r0 = vcross(e2, md), r1 = vcross(md, e1);
         double det = fabs(vdot(e1, r0));
         if (det > 0.0) {
-            double l = 3.0 * U32 * (vlen(vsub(o, a)) + vlen(o) + lever) / det;
+            double l = 8.0 * U32 * (vlen(vsub(o, a)) + vlen(o) + lever) / det;
             const double dbary[2] = {l * vlen(r0), l * vlen(r1)};
             for (int comp = 0; comp < 2; ++comp) {
                 double worst = 0.0;
