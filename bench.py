@@ -309,7 +309,16 @@ def main():
     samples = w.samples
     stream = torch.cuda.current_stream()
     scenes = [s.handle for s in gw.scenes]
-    images = gw.new_images()
+    # views of one size render into one [N][H][W][3] stack (the denoiser then takes the stack
+    # in one launch per level)
+    sizes = {(v.width, v.height) for v in gw.views}
+    uniform = len(sizes) == 1
+    if uniform:
+        (W0, H0), = sizes
+        img_stack = torch.empty((len(gw.views), H0, W0, 3), device=dev)
+        images = list(img_stack.unbind(0))
+    else:
+        images = gw.new_images()
     # one tape for every arm: FULL-mode size when it fits (a FULL tape also serves PRIMARY mode),
     # leaving room for the wavefront queues and the workspace
     full_bytes = M.mirres_tape_bytes_mode(gw.views, M.GRAD_FULL)
@@ -325,7 +334,11 @@ def main():
     # reference images: the same scene rendered with another seed
     refs, _ = gw.render(launch=1, seed=w.seed + 1, tape=tape)
     refs = [r.clone() for r in refs]
-    d_images = [torch.empty_like(r) for r in refs]
+    if uniform:
+        d_stack = torch.empty_like(img_stack)
+        d_images = list(d_stack.unbind(0))
+    else:
+        d_images = [torch.empty_like(r) for r in refs]
     loss = torch.zeros(1, device=dev)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
 
@@ -473,21 +486,30 @@ def main():
     eawt = None
     if not args.no_eawt:
         ep = M.EawtParams(EAWT_SIGMAS[0], EAWT_SIGMAS[1], EAWT_SIGMAS[2], 3)
-        gbn = [torch.empty_like(im) for im in images]
-        gbx = [torch.empty_like(im) for im in images]
-        dn_out = [torch.empty_like(im) for im in images]
-        dn_grad = [torch.empty_like(im) for im in images]
-        recs = [torch.empty(M.mirres_eawt_record_bytes(v.width, v.height, 3) // 4, device=dev) for v in gw.views]
+        if uniform:  # the whole stack per level
+            gbn_s, gbx_s, out_s, grad_s = (torch.empty_like(img_stack) for _ in range(4))
+            gbn, gbx = list(gbn_s.unbind(0)), list(gbx_s.unbind(0))
+            rec_s = torch.empty(len(gw.views) * M.mirres_eawt_record_bytes(W0, H0, 3) // 4, device=dev)
+        else:
+            gbn = [torch.empty_like(im) for im in images]
+            gbx = [torch.empty_like(im) for im in images]
+            dn_out = [torch.empty_like(im) for im in images]
+            dn_grad = [torch.empty_like(im) for im in images]
+            recs = [torch.empty(M.mirres_eawt_record_bytes(v.width, v.height, 3) // 4, device=dev) for v in gw.views]
 
         def eawt_pass(ev=None):
             for vi, v in enumerate(gw.views):
                 M.mirres_gbuffer(gw.ctx, gw.scenes[v.scene].handle, v, gbn[vi], gbx[vi])
             if ev is not None:
                 ev[0].record()
-            for vi in range(len(gw.views)):
-                M.mirres_eawt(gw.ctx, images[vi], gbn[vi], gbx[vi], ep, dn_out[vi], recs[vi])
-            for vi in range(len(gw.views)):
-                M.mirres_eawt_backward(gw.ctx, d_images[vi], gbn[vi], gbx[vi], ep, recs[vi], dn_grad[vi])
+            if uniform:
+                M.mirres_eawt_batch(gw.ctx, img_stack, gbn_s, gbx_s, ep, out_s, rec_s)
+                M.mirres_eawt_batch_backward(gw.ctx, d_stack, gbn_s, gbx_s, ep, rec_s, grad_s)
+            else:
+                for vi in range(len(gw.views)):
+                    M.mirres_eawt(gw.ctx, images[vi], gbn[vi], gbx[vi], ep, dn_out[vi], recs[vi])
+                for vi in range(len(gw.views)):
+                    M.mirres_eawt_backward(gw.ctx, d_images[vi], gbn[vi], gbx[vi], ep, recs[vi], dn_grad[vi])
             if ev is not None:
                 ev[1].record()
 
@@ -511,6 +533,7 @@ def main():
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK, "unit": "GB/s",
                              "frac": ach / HBM_PEAK, "traffic": None, "bytes_per_pixel": bytes_px,
                              "kernel": "k_eawt_level + k_eawt_level_adjoint",
+                             "launches_per_level": 1 if uniform else len(gw.views),
                              "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}}
 
     # mesh regularisers added to the loss (L_smooth + L_offset, Appendix A) on every scene: one

@@ -317,6 +317,9 @@ typedef struct {
     int32_t wave_log2;        /* samples per wave = 2^wave_log2, in [16, 28] */
     int32_t block[4];         /* 64, 128 or 256 */
     int32_t blocks_per_sm[4]; /* in [1, 64] */
+    int32_t branches;         /* in [1, 4]: waves go round-robin to this many chains, each with
+                                 its own ray queues (256 bytes per sample of a wave) and stream,
+                                 so that the stages of different waves overlap; default 1 */
 } mirres_wave_shape;
 
 /* Set (shape = NULL: restore the default) or read the context's wavefront shape; used by every
@@ -329,7 +332,9 @@ mirres_status mirres_get_wave_shape(mirres_context* ctx, mirres_wave_shape* out)
  * budget_samples samples, at least one view; 0 = all) with the wavefront and CUDA events around
  * every stage, for each of a set of (threads per block, blocks per SM) pairs applied to all
  * stages at once; keeps the fastest pair per stage, then times the wave sizes 2^23, 2^24 and
- * 2^25 (those the budget fills) with the chosen stage shapes and keeps the fastest forward.
+ * 2^25 (those the budget fills) with the chosen stage shapes and keeps the fastest forward,
+ * then two chains of waves (branches = 2) at the chosen wave size and at half of it, where the
+ * tuned views fill two waves, kept if faster still.
  * The result becomes the context's shape (mirres_set_wave_shape) and is written to *out, the
  * tuned forward's time to *out_ms. The tape must hold these views (it is overwritten); the
  * renders write temporary images (allocated and freed here). params as for mirres_render
@@ -445,8 +450,8 @@ typedef struct {
 } mirres_eawt_params;
 
 /* Bytes of the record mirres_eawt writes for mirres_eawt_backward: (32 + 20 * levels) * width *
- * height (the packed G-buffer, each level's input image and normaliser). 0 for invalid
- * arguments. The record must be 16-byte aligned. */
+ * height (the packed G-buffer, each level's input image and reciprocal normaliser 1 / k). 0 for
+ * invalid arguments. The record must be 16-byte aligned. */
 size_t mirres_eawt_record_bytes(int32_t width, int32_t height, int32_t levels);
 
 /* G-buffer of one view: the primary hit through each pixel centre (camera as in mirres_render,
@@ -473,6 +478,22 @@ mirres_status mirres_eawt_backward(mirres_context* ctx, const float* d_out, cons
                                    const float* position, int32_t width, int32_t height,
                                    const mirres_eawt_params* params, const void* record, size_t record_bytes,
                                    float* d_image, void* stream);
+
+/* mirres_eawt and mirres_eawt_backward over a stack of n_images images of the same size (the
+ * views of a batch): image, normal, position, out, d_out and d_image are [n_images][height]
+ * [width][3] device, contiguous; the record holds n_images * mirres_eawt_record_bytes(width,
+ * height, levels) bytes. Every level is one launch over the whole stack; each image is filtered
+ * on its own (no tap crosses into another image), with the results of one mirres_eawt call per
+ * image. MIRRES_ERR_ARG as for the single-image calls, and for n_images < 1 or a stack of more
+ * than 2^31 pixels. */
+mirres_status mirres_eawt_batch(mirres_context* ctx, int32_t n_images, const float* image, const float* normal,
+                                const float* position, int32_t width, int32_t height,
+                                const mirres_eawt_params* params, float* out, void* record, size_t record_bytes,
+                                void* stream);
+mirres_status mirres_eawt_batch_backward(mirres_context* ctx, int32_t n_images, const float* d_out,
+                                         const float* normal, const float* position, int32_t width, int32_t height,
+                                         const mirres_eawt_params* params, const void* record, size_t record_bytes,
+                                         float* d_image, void* stream);
 
 /* Mesh regularisers added to the rendering loss while the geometry is refined (Appendix A,
  * "Training details"):

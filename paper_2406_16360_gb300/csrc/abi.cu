@@ -220,6 +220,10 @@ extern "C" mirres_status mirres_context_destroy(mirres_context* ctx)
     delete[] ctx->stage_events;
     delete[] ctx->stage_kind;
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    for (int b = 0; b < 4; ++b) {
+        if (ctx->branch_stream[b]) cudaStreamDestroy(ctx->branch_stream[b]);
+        if (ctx->branch_event[b]) cudaEventDestroy(ctx->branch_event[b]);
+    }
     if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->queue_cnt) cudaFree(ctx->queue_cnt);
@@ -405,10 +409,9 @@ static Rng make_rng(const mirres_params* p)
     return r;
 }
 
-// samples per wave of the batched wavefront (queues take 256 bytes per sample of a wave)
-// the default wavefront shape (mirres_wave_shape): 2^25 samples per wave, 256 threads and 8
-// blocks per SM for every stage
-static mirres_wave_shape default_wave_shape() { return mirres_wave_shape{25, {256, 256, 256, 256}, {8, 8, 8, 8}}; }
+// the default wavefront shape (mirres_wave_shape): 2^25 samples per wave (the queues take 256
+// bytes per sample of a wave), 256 threads and 8 blocks per SM for every stage, one chain
+static mirres_wave_shape default_wave_shape() { return mirres_wave_shape{25, {256, 256, 256, 256}, {8, 8, 8, 8}, 1}; }
 
 static mirres_status check_wave_shape(const mirres_wave_shape& w)
 {
@@ -419,6 +422,7 @@ static mirres_status check_wave_shape(const mirres_wave_shape& w)
         if (w.blocks_per_sm[k] < 1 || w.blocks_per_sm[k] > 64)
             return arg_error("blocks_per_sm[" + std::to_string(k) + "] must be in [1, 64]");
     }
+    if (w.branches < 1 || w.branches > 4) return arg_error("branches must be in [1, 4]");
     return MIRRES_OK;
 }
 
@@ -515,14 +519,17 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         for (uint64_t f = 0; f < total; f += wave) wave_first.push_back(f);
     }
     const int n_waves = (int)wave_first.size();
+    const int nb = std::min(ctx->wave_shape.branches, n_waves);  // chains of waves
     Carver plan(nullptr);
     plan.take<char>(tape ? 0 : tape_bytes_per_sample(nvx) * total);
     plan.take<ViewDev>((size_t)n_views);
     plan.take<SceneDev>((size_t)n_scenes);
     plan.take<float*>((size_t)n_views);
     plan.take<uint64_t>((size_t)n_views);
-    plan.take<unsigned int>(5 * (size_t)max_b + 3);
-    plan.take<float4>(16ull * wave);
+    for (int b = 0; b < nb; ++b) {
+        plan.take<unsigned int>(5 * (size_t)max_b + 3);
+        for (int k = 0; k < 16; ++k) plan.take<float4>(wave);
+    }
     for (int k = 0; k < 6; ++k) plan.take<uint32_t>(reuse ? total : 0);
     MR_TRY(ws_reserve(ctx, plan.off));
     Carver cv(ctx->ws.ptr);
@@ -532,11 +539,14 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     SceneDev* d_scenes = cv.take<SceneDev>((size_t)n_scenes);
     float** d_images = cv.take<float*>((size_t)n_views);
     uint64_t* d_pixoff = cv.take<uint64_t>((size_t)n_views);
-    unsigned int* qc = cv.take<unsigned int>(5 * (size_t)max_b + 3);
-    QueueDev qa{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
-    QueueDev qb{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
-    QueueDev hq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
-    ShadowDev sq{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+    WaveBranch br[4];
+    for (int b = 0; b < nb; ++b) {
+        br[b].qc = cv.take<unsigned int>(5 * (size_t)max_b + 3);
+        br[b].qa = QueueDev{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+        br[b].qb = QueueDev{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+        br[b].hq = QueueDev{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+        br[b].sq = ShadowDev{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+    }
     ResDev res{};
     if (reuse) {
         res.ytex = reinterpret_cast<int32_t*>(cv.take<uint32_t>(total));
@@ -591,14 +601,22 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
             ctx->graph = nullptr;
         }
         if (!ctx->capture_stream) MR_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        br[0].st = ctx->capture_stream;
+        for (int b = 0; b < nb; ++b) {
+            if (b > 0 && !ctx->branch_stream[b])
+                MR_CUDA(cudaStreamCreateWithFlags(&ctx->branch_stream[b], cudaStreamNonBlocking));
+            if (nb > 1 && !ctx->branch_event[b])
+                MR_CUDA(cudaEventCreateWithFlags(&ctx->branch_event[b], cudaEventDisableTiming));
+            if (b > 0) br[b].st = ctx->branch_stream[b];
+        }
         const int pairs = mr_wave_stage_pairs(n_waves, max_b);
         if (flags & 1) MR_TRY(stage_events(ctx, pairs));
         MR_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave_first.data(), n_waves, qa, qb, hq, sq,
-                       qc, tp, ctx->counters, d_pixoff, total_pix, d_images, ctx->sm_count, ctx->capture_stream,
-                       (flags & 1) ? ctx->stage_events : nullptr, (flags & 1) ? ctx->stage_kind : nullptr, nvx,
-                       (flags & 2) != 0, reuse_k, reuse_radius, res, temporal, temporal_cap, hist, vdev.data(),
-                       sdev.data(), (flags & 4) != 0, ctx->wave_shape);
+        mr_wave_record(d_scenes, d_views, n_views, total, max_b, rng, M, wave_first.data(), n_waves, br, nb,
+                       ctx->branch_event[0], ctx->branch_event, tp, ctx->counters, d_pixoff, total_pix, d_images,
+                       ctx->sm_count, (flags & 1) ? ctx->stage_events : nullptr,
+                       (flags & 1) ? ctx->stage_kind : nullptr, nvx, (flags & 2) != 0, reuse_k, reuse_radius, res,
+                       temporal, temporal_cap, hist, vdev.data(), sdev.data(), (flags & 4) != 0, ctx->wave_shape);
         ctx->stage_pairs = (flags & 1) ? pairs : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -982,6 +1000,23 @@ extern "C" mirres_status mirres_autotune_wave(mirres_context* ctx, mirres_scene*
         }
     }
     best.wave_log2 = best_wave;
+    // then two concurrent chains of waves, at the chosen wave size and at half of it (only where
+    // the tuned views fill at least two waves)
+    const int one_chain_wave = best_wave;
+    for (int wl = one_chain_wave - 1; wl <= one_chain_wave && status == MIRRES_OK; ++wl) {
+        if (wl < 23 || (1ull << wl) >= sub_total) continue;
+        mirres_wave_shape w = best;
+        w.wave_log2 = wl;
+        w.branches = 2;
+        double ms[4];
+        float tot = 0.0f;
+        status = run(w, ms, &tot);
+        if (status == MIRRES_OK && tot < best_ms) {
+            best_ms = tot;
+            best.wave_log2 = wl;
+            best.branches = 2;
+        }
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(st);
@@ -1288,11 +1323,12 @@ extern "C" mirres_status mirres_gbuffer(mirres_context* ctx, const mirres_scene*
     return MIRRES_OK;
 }
 
-// record layout (16-byte aligned): packed normal and position [H][W] float4, the levels' inputs
-// c_i [levels][H][W] float4, their normalisers k_i [levels][H][W] float
+// record layout (16-byte aligned) for a stack of n images of npx pixels: packed normals and
+// positions [n][H][W] float4, the levels' inputs c_i [levels][n][H][W] float4, their reciprocal
+// normalisers 1 / k_i [levels][n][H][W] float
 struct EawtRecord {
     float4 *n, *x, *c;
-    float* k;
+    float* ik;
 };
 
 static EawtRecord eawt_record(void* base, size_t npx, int L)
@@ -1301,20 +1337,29 @@ static EawtRecord eawt_record(void* base, size_t npx, int L)
     return EawtRecord{f, f + npx, f + 2 * npx, reinterpret_cast<float*>(f + (2 + (size_t)L) * npx)};
 }
 
-extern "C" mirres_status mirres_eawt(mirres_context* ctx, const float* image, const float* normal,
-                                     const float* position, int32_t width, int32_t height,
-                                     const mirres_eawt_params* params, float* out, void* record,
-                                     size_t record_bytes, void* stream)
+static mirres_status eawt_args(int32_t n_images, int32_t width, int32_t height, const mirres_eawt_params* params,
+                               const void* record, size_t record_bytes)
+{
+    if (n_images < 1) return arg_error("n_images must be >= 1");
+    MR_TRY(check_eawt(width, height, params));
+    if ((int64_t)width * height * n_images > (int64_t)1 << 31) return arg_error("image stack larger than 2^31 pixels");
+    if (record_bytes / (size_t)n_images < mirres_eawt_record_bytes(width, height, params->levels))
+        return arg_error("record_bytes is smaller than n_images * mirres_eawt_record_bytes");
+    if (reinterpret_cast<uintptr_t>(record) & 15) return arg_error("record must be 16-byte aligned");
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_eawt_batch(mirres_context* ctx, int32_t n_images, const float* image,
+                                           const float* normal, const float* position, int32_t width, int32_t height,
+                                           const mirres_eawt_params* params, float* out, void* record,
+                                           size_t record_bytes, void* stream)
 {
     if (!ctx || !image || !normal || !position || !out || !record)
         return arg_error("ctx, image, normal, position, out and record required");
-    MR_TRY(check_eawt(width, height, params));
-    if (record_bytes < mirres_eawt_record_bytes(width, height, params->levels))
-        return arg_error("record_bytes is smaller than mirres_eawt_record_bytes");
-    if (reinterpret_cast<uintptr_t>(record) & 15) return arg_error("record must be 16-byte aligned");
+    MR_TRY(eawt_args(n_images, width, height, params, record, record_bytes));
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
-    const size_t npx = (size_t)width * height;
+    const size_t npx = (size_t)width * height * n_images;
     const int L = params->levels, sms = ctx->sm_count;
     const EawtRecord r = eawt_record(record, npx, L);
     mr_launch_eawt_pack(normal, r.n, (int64_t)npx, sms, st);
@@ -1325,29 +1370,37 @@ extern "C" mirres_status mirres_eawt(mirres_context* ctx, const float* image, co
         const int step = 1 << i;
         const float srt = params->sigma_rt / (float)step;
         const bool last = i + 1 == L;
-        mr_launch_eawt_level(r.c + npx * (size_t)i, r.n, r.x, width, height, step, 1.0f / (srt * srt), in2, ix2,
-                             last ? nullptr : r.c + npx * (size_t)(i + 1), last ? out : nullptr, r.k + npx * (size_t)i,
-                             sms, st);
+        mr_launch_eawt_level(r.c + npx * (size_t)i, r.n, r.x, n_images, width, height, step, 1.0f / (srt * srt), in2,
+                             ix2, last ? nullptr : r.c + npx * (size_t)(i + 1), last ? out : nullptr,
+                             r.ik + npx * (size_t)i, sms, st);
     }
     MR_CUDA(cudaGetLastError());
     ctx->host_launches += (unsigned long long)L + 3;
     return MIRRES_OK;
 }
 
-extern "C" mirres_status mirres_eawt_backward(mirres_context* ctx, const float* d_out, const float* normal,
-                                              const float* position, int32_t width, int32_t height,
-                                              const mirres_eawt_params* params, const void* record,
-                                              size_t record_bytes, float* d_image, void* stream)
+extern "C" mirres_status mirres_eawt(mirres_context* ctx, const float* image, const float* normal,
+                                     const float* position, int32_t width, int32_t height,
+                                     const mirres_eawt_params* params, float* out, void* record,
+                                     size_t record_bytes, void* stream)
 {
+    return mirres_eawt_batch(ctx, 1, image, normal, position, width, height, params, out, record, record_bytes,
+                             stream);
+}
+
+extern "C" mirres_status mirres_eawt_batch_backward(mirres_context* ctx, int32_t n_images, const float* d_out,
+                                                    const float* normal, const float* position, int32_t width,
+                                                    int32_t height, const mirres_eawt_params* params,
+                                                    const void* record, size_t record_bytes, float* d_image,
+                                                    void* stream)
+{
+    // (normal and position are the forward's; the record holds them packed)
     if (!ctx || !d_out || !normal || !position || !record || !d_image)
         return arg_error("ctx, d_out, normal, position, record and d_image required");
-    MR_TRY(check_eawt(width, height, params));
-    if (record_bytes < mirres_eawt_record_bytes(width, height, params->levels))
-        return arg_error("record_bytes is smaller than mirres_eawt_record_bytes");
-    if (reinterpret_cast<uintptr_t>(record) & 15) return arg_error("record must be 16-byte aligned");
+    MR_TRY(eawt_args(n_images, width, height, params, record, record_bytes));
     MR_CUDA(cudaSetDevice(ctx->device));
     const cudaStream_t st = as_stream(stream);
-    const size_t npx = (size_t)width * height;
+    const size_t npx = (size_t)width * height * n_images;
     const int L = params->levels, sms = ctx->sm_count;
     MR_TRY(ws_reserve(ctx, sizeof(float4) * 2 * npx + 256));
     float4* tmp[2] = {reinterpret_cast<float4*>(ctx->ws.ptr), reinterpret_cast<float4*>(ctx->ws.ptr) + npx};
@@ -1358,14 +1411,23 @@ extern "C" mirres_status mirres_eawt_backward(mirres_context* ctx, const float* 
     for (int i = L - 1; i >= 0; --i) {
         const int step = 1 << i;
         const float srt = params->sigma_rt / (float)step;
-        mr_launch_eawt_level_adjoint(tmp[cur], r.c + npx * (size_t)i, r.k + npx * (size_t)i, r.n, r.x, width, height,
-                                     step, 1.0f / (srt * srt), in2, ix2, i == 0 ? nullptr : tmp[cur ^ 1],
-                                     i == 0 ? d_image : nullptr, sms, st);
+        mr_launch_eawt_level_adjoint(tmp[cur], r.c + npx * (size_t)i, r.ik + npx * (size_t)i, r.n, r.x, n_images,
+                                     width, height, step, 1.0f / (srt * srt), in2, ix2,
+                                     i == 0 ? nullptr : tmp[cur ^ 1], i == 0 ? d_image : nullptr, sms, st);
         cur ^= 1;
     }
     MR_CUDA(cudaGetLastError());
     ctx->host_launches += (unsigned long long)L + 1;
     return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_eawt_backward(mirres_context* ctx, const float* d_out, const float* normal,
+                                              const float* position, int32_t width, int32_t height,
+                                              const mirres_eawt_params* params, const void* record,
+                                              size_t record_bytes, float* d_image, void* stream)
+{
+    return mirres_eawt_batch_backward(ctx, 1, d_out, normal, position, width, height, params, record, record_bytes,
+                                      d_image, stream);
 }
 
 extern "C" mirres_status mirres_mesh_regularizers(mirres_context* ctx, mirres_scene* scene,

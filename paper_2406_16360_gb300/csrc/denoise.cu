@@ -6,7 +6,7 @@
 // w(p, q) = exp(-|c_i(p) - c_i(q)|^2 / sigma_rt_i^2 - |n_p - n_q|^2 / sigma_n^2 - |x_p - x_q|^2 / sigma_x^2),
 // sigma_rt_i = sigma_rt / 2^i and k(p) = sum_q h w; taps outside the image are left out. The
 // adjoint holds the weights fixed: since h w(p, q) is symmetric in p and q, the transpose of a
-// level is the same stencil applied to g / k. One thread per pixel; the taps are L1/L2 hits.
+// level is the same stencil applied to g / k. Every launch covers a stack of images of one size.
 #include "render.h"
 
 namespace {
@@ -38,70 +38,145 @@ __device__ __forceinline__ void store(float4* o4, float* o3, int64_t p, float x,
     }
 }
 
-// forward level: cin -> cout (packed, or [H][W][3] when out3 is given), and the normaliser k
-__global__ void __launch_bounds__(256) k_eawt_level(const float4* __restrict__ cin, const float4* __restrict__ nrm,
-                                                    const float4* __restrict__ pos, int W, int H, int step,
-                                                    float inv_rt2, float inv_n2, float inv_x2, float4* __restrict__ cout,
-                                                    float* __restrict__ out3, float* __restrict__ kout)
+// The level kernels run over a stack of N images of W x H. A thread takes a strip of EAWT_R
+// output pixels of one column spaced `step` rows apart (rows y0 + j step): their 5 x 5 footprints
+// overlap in all but the first and last rows, so the strip reads its (EAWT_R + 4) x 5 taps once
+// each and applies every tap to the outputs it falls on -- (EAWT_R + 4) 5 / EAWT_R tap reads per
+// output instead of 25. Consecutive threads take consecutive columns of the same rows (coalesced
+// tap rows). Each output still sums its taps row by row, column by column.
+constexpr int EAWT_R = 4;
+
+struct Strip {
+    int img, x, y0;
+};
+
+// strip t of the stack: image, column, first row (row block B of EAWT_R step rows, residue ry)
+__device__ __forceinline__ Strip strip_of(int64_t t, int W, int step, int64_t per_img)
 {
-    const int64_t npx = (int64_t)W * H;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(p / W), x = (int)(p % W);
-        const float4 cp = __ldg(cin + p), np_ = __ldg(nrm + p), xp = __ldg(pos + p);
-        float ax = 0.f, ay = 0.f, az = 0.f, k = 0.f;
-        for (int a = 0; a < 5; ++a) {
-            const int qy = y + (a - 2) * step;
+    Strip s;
+    s.img = (int)(t / per_img);
+    const int64_t r = t - (int64_t)s.img * per_img;
+    s.x = (int)(r % W);
+    const int64_t sr = r / W;
+    s.y0 = (int)(sr / step) * (EAWT_R * step) + (int)(sr % step);
+    return s;
+}
+
+__device__ __forceinline__ int64_t strips_per_image(int W, int H, int step)
+{
+    return (int64_t)((H + EAWT_R * step - 1) / (EAWT_R * step)) * step * W;
+}
+
+// forward level: cin -> cout (packed, or [N][H][W][3] when out3 is given), and 1 / k
+__global__ void __launch_bounds__(256) k_eawt_level(const float4* __restrict__ cin, const float4* __restrict__ nrm,
+                                                    const float4* __restrict__ pos, int N, int W, int H, int step,
+                                                    float inv_rt2, float inv_n2, float inv_x2, float4* __restrict__ cout,
+                                                    float* __restrict__ out3, float* __restrict__ ikout)
+{
+    const int64_t npx = (int64_t)W * H, per_img = strips_per_image(W, H, step), total = per_img * N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const Strip sp = strip_of(t, W, step, per_img);
+        if (sp.y0 >= H) continue;
+        const int64_t base = (int64_t)sp.img * npx;
+        float4 cp[EAWT_R], np_[EAWT_R], xp[EAWT_R];
+        float ax[EAWT_R], ay[EAWT_R], az[EAWT_R], k[EAWT_R];
+#pragma unroll
+        for (int j = 0; j < EAWT_R; ++j) {
+            const int y = sp.y0 + j * step;
+            const int64_t p = base + (int64_t)min(y, H - 1) * W + sp.x;
+            cp[j] = __ldg(cin + p);
+            np_[j] = __ldg(nrm + p);
+            xp[j] = __ldg(pos + p);
+            ax[j] = ay[j] = az[j] = k[j] = 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < EAWT_R + 4; ++m) {
+            const int qy = sp.y0 + (m - 2) * step;
             if (qy < 0 || qy >= H) continue;
 #pragma unroll
             for (int b = 0; b < 5; ++b) {
-                const int qx = x + (b - 2) * step;
+                const int qx = sp.x + (b - 2) * step;
                 if (qx < 0 || qx >= W) continue;
-                const int64_t q = (int64_t)qy * W + qx;
-                const float4 cq = __ldg(cin + q);
-                const float e = d2(cp, cq) * inv_rt2 + d2(np_, __ldg(nrm + q)) * inv_n2 + d2(xp, __ldg(pos + q)) * inv_x2;
-                const float w = kB3[a] * kB3[b] * __expf(-e);
-                ax += w * cq.x;
-                ay += w * cq.y;
-                az += w * cq.z;
-                k += w;
+                const int64_t q = base + (int64_t)qy * W + qx;
+                const float4 cq = __ldg(cin + q), nq = __ldg(nrm + q), xq = __ldg(pos + q);
+#pragma unroll
+                for (int j = 0; j < EAWT_R; ++j) {
+                    const int a = m - j;  // the tap's row in output j's footprint
+                    if (a < 0 || a > 4) continue;
+                    const float e = d2(cp[j], cq) * inv_rt2 + d2(np_[j], nq) * inv_n2 + d2(xp[j], xq) * inv_x2;
+                    const float w = kB3[a] * kB3[b] * __expf(-e);
+                    ax[j] += w * cq.x;
+                    ay[j] += w * cq.y;
+                    az[j] += w * cq.z;
+                    k[j] += w;
+                }
             }
         }
-        const float ik = 1.0f / k;  // k >= (6/16)^2: the centre tap has weight 1
-        store(cout, out3, p, ax * ik, ay * ik, az * ik);
-        kout[p] = k;
+#pragma unroll
+        for (int j = 0; j < EAWT_R; ++j) {
+            const int y = sp.y0 + j * step;
+            if (y >= H) break;
+            const int64_t p = base + (int64_t)y * W + sp.x;
+            const float ik = 1.0f / k[j];  // k >= (6/16)^2: the centre tap has weight 1
+            store(cout, out3, p, ax[j] * ik, ay[j] * ik, az[j] * ik);
+            ikout[p] = ik;
+        }
     }
 }
 
 // adjoint level: gout(q) = sum over taps of h w(q, q + tap) gin(q + tap) / k(q + tap), the
-// weights recomputed from the level's recorded input c
+// weights recomputed from the level's recorded input c, 1 / k read from the record
 __global__ void __launch_bounds__(256) k_eawt_level_adjoint(const float4* __restrict__ gin, const float4* __restrict__ c,
-                                                            const float* __restrict__ kin, const float4* __restrict__ nrm,
-                                                            const float4* __restrict__ pos, int W, int H, int step,
+                                                            const float* __restrict__ ikin, const float4* __restrict__ nrm,
+                                                            const float4* __restrict__ pos, int N, int W, int H, int step,
                                                             float inv_rt2, float inv_n2, float inv_x2,
                                                             float4* __restrict__ gout, float* __restrict__ out3)
 {
-    const int64_t npx = (int64_t)W * H;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(p / W), x = (int)(p % W);
-        const float4 cp = __ldg(c + p), np_ = __ldg(nrm + p), xp = __ldg(pos + p);
-        float ax = 0.f, ay = 0.f, az = 0.f;
-        for (int a = 0; a < 5; ++a) {
-            const int qy = y + (a - 2) * step;
+    const int64_t npx = (int64_t)W * H, per_img = strips_per_image(W, H, step), total = per_img * N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const Strip sp = strip_of(t, W, step, per_img);
+        if (sp.y0 >= H) continue;
+        const int64_t base = (int64_t)sp.img * npx;
+        float4 cp[EAWT_R], np_[EAWT_R], xp[EAWT_R];
+        float ax[EAWT_R], ay[EAWT_R], az[EAWT_R];
+#pragma unroll
+        for (int j = 0; j < EAWT_R; ++j) {
+            const int y = sp.y0 + j * step;
+            const int64_t p = base + (int64_t)min(y, H - 1) * W + sp.x;
+            cp[j] = __ldg(c + p);
+            np_[j] = __ldg(nrm + p);
+            xp[j] = __ldg(pos + p);
+            ax[j] = ay[j] = az[j] = 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < EAWT_R + 4; ++m) {
+            const int qy = sp.y0 + (m - 2) * step;
             if (qy < 0 || qy >= H) continue;
 #pragma unroll
             for (int b = 0; b < 5; ++b) {
-                const int qx = x + (b - 2) * step;
+                const int qx = sp.x + (b - 2) * step;
                 if (qx < 0 || qx >= W) continue;
-                const int64_t q = (int64_t)qy * W + qx;
-                const float e = d2(cp, __ldg(c + q)) * inv_rt2 + d2(np_, __ldg(nrm + q)) * inv_n2 + d2(xp, __ldg(pos + q)) * inv_x2;
-                const float w = kB3[a] * kB3[b] * __expf(-e) / __ldg(kin + q);
-                const float4 g = __ldg(gin + q);
-                ax += w * g.x;
-                ay += w * g.y;
-                az += w * g.z;
+                const int64_t q = base + (int64_t)qy * W + qx;
+                const float4 cq = __ldg(c + q), nq = __ldg(nrm + q), xq = __ldg(pos + q), g = __ldg(gin + q);
+                const float ik = __ldg(ikin + q);
+#pragma unroll
+                for (int j = 0; j < EAWT_R; ++j) {
+                    const int a = m - j;
+                    if (a < 0 || a > 4) continue;
+                    const float e = d2(cp[j], cq) * inv_rt2 + d2(np_[j], nq) * inv_n2 + d2(xp[j], xq) * inv_x2;
+                    const float w = kB3[a] * kB3[b] * __expf(-e) * ik;
+                    ax[j] += w * g.x;
+                    ay[j] += w * g.y;
+                    az[j] += w * g.z;
+                }
             }
         }
-        store(gout, out3, p, ax, ay, az);
+#pragma unroll
+        for (int j = 0; j < EAWT_R; ++j) {
+            const int y = sp.y0 + j * step;
+            if (y >= H) break;
+            store(gout, out3, base + (int64_t)y * W + sp.x, ax[j], ay[j], az[j]);
+        }
     }
 }
 
@@ -150,19 +225,25 @@ void mr_launch_eawt_pack(const float* a, float4* out, int64_t npx, int sms, cuda
     k_eawt_pack<<<grid_for_pixels(npx, sms), 256, 0, st>>>(a, out, npx);
 }
 
-void mr_launch_eawt_level(const float4* cin, const float4* nrm, const float4* pos, int W, int H, int step, float inv_rt2,
-                          float inv_n2, float inv_x2, float4* cout, float* out3, float* kout, int sms, cudaStream_t st)
+static int64_t level_strips(int N, int W, int H, int step)
 {
-    k_eawt_level<<<grid_for_pixels((int64_t)W * H, sms), 256, 0, st>>>(cin, nrm, pos, W, H, step, inv_rt2, inv_n2,
-                                                                      inv_x2, cout, out3, kout);
+    return (int64_t)N * ((H + EAWT_R * step - 1) / (EAWT_R * step)) * step * W;
 }
 
-void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const float* kin, const float4* nrm,
-                                  const float4* pos, int W, int H, int step, float inv_rt2, float inv_n2, float inv_x2,
-                                  float4* gout, float* out3, int sms, cudaStream_t st)
+void mr_launch_eawt_level(const float4* cin, const float4* nrm, const float4* pos, int N, int W, int H, int step,
+                          float inv_rt2, float inv_n2, float inv_x2, float4* cout, float* out3, float* ikout, int sms,
+                          cudaStream_t st)
 {
-    k_eawt_level_adjoint<<<grid_for_pixels((int64_t)W * H, sms), 256, 0, st>>>(gin, c, kin, nrm, pos, W, H, step,
-                                                                              inv_rt2, inv_n2, inv_x2, gout, out3);
+    k_eawt_level<<<grid_for_pixels(level_strips(N, W, H, step), sms), 256, 0, st>>>(
+        cin, nrm, pos, N, W, H, step, inv_rt2, inv_n2, inv_x2, cout, out3, ikout);
+}
+
+void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const float* ikin, const float4* nrm,
+                                  const float4* pos, int N, int W, int H, int step, float inv_rt2, float inv_n2,
+                                  float inv_x2, float4* gout, float* out3, int sms, cudaStream_t st)
+{
+    k_eawt_level_adjoint<<<grid_for_pixels(level_strips(N, W, H, step), sms), 256, 0, st>>>(
+        gin, c, ikin, nrm, pos, N, W, H, step, inv_rt2, inv_n2, inv_x2, gout, out3);
 }
 
 void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* pos, int sms, cudaStream_t st)

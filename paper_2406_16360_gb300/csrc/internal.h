@@ -44,7 +44,9 @@ struct mirres_context {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     unsigned char graph_key[192] = {};
-    mirres_wave_shape wave_shape = {25, {256, 256, 256, 256}, {8, 8, 8, 8}};  // batched wavefront launch shape
+    mirres_wave_shape wave_shape = {25, {256, 256, 256, 256}, {8, 8, 8, 8}, 1};  // batched wavefront launch shape
+    cudaStream_t branch_stream[4] = {};  // [1..3]: the streams of wave chains 1..3 during capture
+    cudaEvent_t branch_event[4] = {};    // [0]: fork, [1..3]: join of chains 1..3
     unsigned long long graph_launches = 0;  // kernel launches inside the graph
     cudaEvent_t* stage_events = nullptr;     // [n_stage_events]: (start, end) pairs per stage launch
     int n_stage_events = 0;

@@ -1190,9 +1190,10 @@ __global__ void k_account(unsigned long long* counters, const unsigned int* __re
         cont += qcnt[3 * b + 1];
         shadow += qcnt[3 * b + 2];
     }
-    counters[0] += primary;
-    counters[1] += cont;
-    counters[2] += shadow;
+    // atomics: the accounting of concurrent wave chains may overlap
+    atomicAdd(&counters[0], (unsigned long long)primary);
+    atomicAdd(&counters[1], cont);
+    atomicAdd(&counters[2], shadow);
 }
 
 // ray queries for mirres_trace

@@ -104,11 +104,12 @@ void mr_launch_trace_rays(const SceneDev& s, const float* rays, const int32_t* s
 
 // denoise.cu: EAWT levels, their adjoints, the pixel-centre G-buffer
 void mr_launch_eawt_pack(const float* a, float4* out, int64_t npx, int sms, cudaStream_t st);
-void mr_launch_eawt_level(const float4* cin, const float4* nrm, const float4* pos, int W, int H, int step, float inv_rt2,
-                          float inv_n2, float inv_x2, float4* cout, float* out3, float* kout, int sms, cudaStream_t st);
-void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const float* kin, const float4* nrm,
-                                  const float4* pos, int W, int H, int step, float inv_rt2, float inv_n2, float inv_x2,
-                                  float4* gout, float* out3, int sms, cudaStream_t st);
+void mr_launch_eawt_level(const float4* cin, const float4* nrm, const float4* pos, int N, int W, int H, int step,
+                          float inv_rt2, float inv_n2, float inv_x2, float4* cout, float* out3, float* ikout, int sms,
+                          cudaStream_t st);
+void mr_launch_eawt_level_adjoint(const float4* gin, const float4* c, const float* ikin, const float4* nrm,
+                                  const float4* pos, int N, int W, int H, int step, float inv_rt2, float inv_n2,
+                                  float inv_x2, float4* gout, float* out3, int sms, cudaStream_t st);
 void mr_launch_gbuffer(const SceneDev& s, const ViewDev& v, float* nrm, float* pos, int sms, cudaStream_t st);
 // regular.cu: mesh regularisers over the scene's edge list (built by mr_edges_build)
 void mr_launch_material_smoothness(const SceneDev& s, const ViewDev& v, uint32_t view_index, const Rng& rng,
@@ -123,13 +124,20 @@ cudaError_t mr_launch_light_loss(const uint64_t* pix_off, int n_views, uint64_t 
                           const float* const* demod, const float* const* ref, float w, unsigned int* count,
                           float* loss, float* const* d_demod, int sms, cudaStream_t st);
 
-// wave.cu: the batched wavefront forward (recorded on a stream, captured as a graph)
+// wave.cu: the batched wavefront forward (recorded on a stream, captured as a graph). A chain of
+// waves: its ray queues, its stage counters [5 max_bounces + 3] and the stream it is recorded on.
+struct WaveBranch {
+    QueueDev qa, qb, hq;
+    ShadowDev sq;
+    unsigned int* qc;
+    cudaStream_t st;
+};
 void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,
-                    Rng rng, int M, const uint64_t* wave_first, int n_waves, const QueueDev& qa, const QueueDev& qb,
-                    const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
-                    unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
-                    int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
-                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist,
-                    const ViewDev* hviews, const SceneDev* hscenes, bool raster, const mirres_wave_shape& shape);
+                    Rng rng, int M, const uint64_t* wave_first, int n_waves, const WaveBranch* branches,
+                    int n_branches, cudaEvent_t fork, cudaEvent_t* join, void* tape, unsigned long long* counters,
+                    const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaEvent_t* ev,
+                    int* kind, int nvx, bool count, int reuse_k, int reuse_radius, const ResDev& res, int temporal,
+                    int temporal_cap, const HistDev& hist, const ViewDev* hviews, const SceneDev* hscenes, bool raster,
+                    const mirres_wave_shape& shape);
 int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal, int raster_launches);
 int mr_wave_stage_pairs(int n_waves, int max_bounces);

@@ -717,13 +717,21 @@ unsigned grid_cap(uint64_t n, int block, int cap)
 // With `ev` non-null, an event pair is recorded around every stage launch: ev[2k], ev[2k+1]
 // for pair k, whose stage kind (0 closest, 1 shade, 2 shadow, 3 raygen) goes to kind[k].
 void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,
-                    Rng rng, int M, const uint64_t* wave_first, int n_waves, const QueueDev& qa, const QueueDev& qb,
-                    const QueueDev& hq, const ShadowDev& sq, unsigned int* qc, void* tape,
-                    unsigned long long* counters, const uint64_t* pix_off, uint64_t total_pix, float* const* images,
-                    int sms, cudaStream_t st, cudaEvent_t* ev, int* kind, int nvx, bool count, int reuse_k,
-                    int reuse_radius, const ResDev& res, int temporal, int temporal_cap, const HistDev& hist,
-                    const ViewDev* hviews, const SceneDev* hscenes, bool raster, const mirres_wave_shape& shape)
+                    Rng rng, int M, const uint64_t* wave_first, int n_waves, const WaveBranch* branches,
+                    int n_branches, cudaEvent_t fork, cudaEvent_t* join, void* tape, unsigned long long* counters,
+                    const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaEvent_t* ev,
+                    int* kind, int nvx, bool count, int reuse_k, int reuse_radius, const ResDev& res, int temporal,
+                    int temporal_cap, const HistDev& hist, const ViewDev* hviews, const SceneDev* hscenes, bool raster,
+                    const mirres_wave_shape& shape)
 {
+    // waves go round-robin to `n_branches` chains of their own (queues, counters, stream): chain
+    // 0 on the recording stream, the others forked from it and joined back before the resolve,
+    // so that the stages of different waves overlap on the GPU
+    const cudaStream_t st_main = branches[0].st;
+    if (n_branches > 1) {
+        cudaEventRecord(fork, st_main);
+        for (int b = 1; b < n_branches; ++b) cudaStreamWaitEvent(branches[b].st, fork, 0);
+    }
     // per stage (0 closest, 1 shade, 2 shadow, 3 raygen): threads per block and the grid cap
     const int blk_c = shape.block[0], blk_h = shape.block[1], blk_s = shape.block[2], blk_g = shape.block[3];
     const int cap_c = sms * shape.blocks_per_sm[0], cap_h = sms * shape.blocks_per_sm[1];
@@ -744,8 +752,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                                                   256, smem);
     const unsigned grid_c = (unsigned)(sms * (occ_c > 0 ? occ_c : 1));
     const unsigned grid_s = (unsigned)(sms * (occ_s > 0 ? occ_s : 1));
-    unsigned int* fetch = qc + 3 * max_bounces + 3;  // [2 * max_bounces]: closest, shadow per bounce
     int pair = 0;
+    cudaStream_t st = st_main;
     auto mark = [&](int k, bool start) {
         if (!ev) return;
         if (start) kind[pair] = k;
@@ -753,6 +761,12 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         if (!start) ++pair;
     };
     for (int wv = 0; wv < n_waves; ++wv) {
+        const WaveBranch& br = branches[wv % n_branches];
+        st = br.st;
+        const QueueDev &qa = br.qa, &qb = br.qb, &hq = br.hq;
+        const ShadowDev& sq = br.sq;
+        unsigned int* qc = br.qc;
+        unsigned int* fetch = qc + 3 * max_bounces + 3;  // [2 * max_bounces]: closest, shadow per bounce
         const uint64_t first = wave_first[wv];
         const uint32_t n = (uint32_t)((wv + 1 < n_waves ? wave_first[wv + 1] : total) - first);
         cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (5 * max_bounces + 3), st);
@@ -824,7 +838,11 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         }
         mr_launch_account(counters, qc, max_bounces, n, st);
     }
-    mr_launch_resolve_all(views, n_views, pix_off, total_pix, images, tape, total, sms, st);
+    for (int b = 1; b < n_branches; ++b) {
+        cudaEventRecord(join[b], branches[b].st);
+        cudaStreamWaitEvent(st_main, join[b], 0);
+    }
+    mr_launch_resolve_all(views, n_views, pix_off, total_pix, images, tape, total, sms, st_main);
 }
 
 int mr_wave_stage_pairs(int n_waves, int max_bounces) { return n_waves * (1 + 3 * max_bounces); }

@@ -27,7 +27,7 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_env_export_flat",
            "mirres_get_counters",
            "mirres_get_work_counters", "EawtParams", "mirres_eawt_record_bytes", "mirres_gbuffer", "mirres_eawt",
-           "mirres_eawt_backward", "mirres_mesh_regularizers", "LkParams", "mirres_material_smoothness",
+           "mirres_eawt_backward", "mirres_eawt_batch", "mirres_eawt_batch_backward", "mirres_mesh_regularizers", "LkParams", "mirres_material_smoothness",
            "mirres_light_demod", "mirres_light_loss", "mirres_light_backward",
            "mirres_reset_counters", "mirres_last_error", "library_path", "mirres_peak_fp32", "mirres_peak_l2"]
 
@@ -76,7 +76,8 @@ class Params(C.Structure):
 
 
 class WaveShape(C.Structure):
-    _fields_ = [("wave_log2", C.c_int32), ("block", C.c_int32 * 4), ("blocks_per_sm", C.c_int32 * 4)]
+    _fields_ = [("wave_log2", C.c_int32), ("block", C.c_int32 * 4), ("blocks_per_sm", C.c_int32 * 4),
+                ("branches", C.c_int32)]
 
 
 WAVE_STAGES = ("closest", "shade", "shadow", "raygen")  # index order of WaveShape.block / blocks_per_sm
@@ -84,12 +85,12 @@ WAVE_STAGES = ("closest", "shade", "shadow", "raygen")  # index order of WaveSha
 
 def _shape_dict(w: WaveShape):
     return dict(wave_log2=int(w.wave_log2), block=[int(x) for x in w.block],
-                blocks_per_sm=[int(x) for x in w.blocks_per_sm])
+                blocks_per_sm=[int(x) for x in w.blocks_per_sm], branches=int(w.branches))
 
 
 def _shape_struct(d):
     return WaveShape(int(d["wave_log2"]), (C.c_int32 * 4)(*[int(x) for x in d["block"]]),
-                     (C.c_int32 * 4)(*[int(x) for x in d["blocks_per_sm"]]))
+                     (C.c_int32 * 4)(*[int(x) for x in d["blocks_per_sm"]]), int(d.get("branches", 1)))
 
 
 class EawtParams(C.Structure):
@@ -158,6 +159,9 @@ def lib():
                 "mirres_gbuffer": (st, [vp, vp, C.POINTER(View), vp, vp, vp]),
                 "mirres_eawt": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, vp, sz, vp]),
                 "mirres_eawt_backward": (st, [vp, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, sz, vp, vp]),
+                "mirres_eawt_batch": (st, [vp, i32, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, vp, sz, vp]),
+                "mirres_eawt_batch_backward": (st, [vp, i32, vp, vp, vp, i32, i32, C.POINTER(EawtParams), vp, sz, vp,
+                                                    vp]),
                 "mirres_mesh_regularizers": (st, [vp, vp, vp, C.c_float, C.c_float, vp, vp, vp]),
                 "mirres_material_smoothness": (st, [vp, vp, C.POINTER(View), i32, C.POINTER(LkParams), vp, vp, vp,
                                                     vp, vp]),
@@ -353,7 +357,8 @@ def mirres_set_launch(ctx: Context, block, blocks_per_sm, chunk):
 
 
 def mirres_set_wave_shape(ctx: Context, shape=None):
-    """shape = dict(wave_log2, block[4], blocks_per_sm[4]) (stages in WAVE_STAGES order), None = default"""
+    """shape = dict(wave_log2, block[4], blocks_per_sm[4], branches=1) (stages in WAVE_STAGES order),
+    None = default"""
     w = None if shape is None else C.byref(_shape_struct(shape))
     _check("mirres_set_wave_shape", lib().mirres_set_wave_shape(ctx.handle, w))
 
@@ -365,7 +370,8 @@ def mirres_get_wave_shape(ctx: Context):
 
 
 def mirres_autotune_wave(ctx: Context, scenes, views, params: Params, tape, budget_samples=0, stream=None):
-    """Tunes the batched wavefront's launch shape; returns dict(wave_log2, block, blocks_per_sm, ms)."""
+    """Tunes the batched wavefront's launch shape; returns dict(wave_log2, block, blocks_per_sm,
+    branches, ms)."""
     vs = _views(views)
     sc = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
     w, ms = WaveShape(), C.c_float()
@@ -476,6 +482,22 @@ def mirres_eawt_backward(ctx: Context, d_out, normal, position, params: EawtPara
                                                               W, H, C.byref(params), _ptr(record),
                                                               record.numel() * record.element_size(), _ptr(d_image),
                                                               _stream(stream)))
+
+
+def mirres_eawt_batch(ctx: Context, images, normal, position, params: EawtParams, out, record, stream=None):
+    """the denoiser over a stack [N][H][W][3] of images of one size, one launch per level"""
+    N, H, W = images.shape[0], images.shape[1], images.shape[2]
+    _check("mirres_eawt_batch", lib().mirres_eawt_batch(ctx.handle, N, _ptr(images), _ptr(normal), _ptr(position), W,
+                                                        H, C.byref(params), _ptr(out), _ptr(record),
+                                                        record.numel() * record.element_size(), _stream(stream)))
+
+
+def mirres_eawt_batch_backward(ctx: Context, d_out, normal, position, params: EawtParams, record, d_image,
+                               stream=None):
+    N, H, W = d_out.shape[0], d_out.shape[1], d_out.shape[2]
+    _check("mirres_eawt_batch_backward", lib().mirres_eawt_batch_backward(
+        ctx.handle, N, _ptr(d_out), _ptr(normal), _ptr(position), W, H, C.byref(params), _ptr(record),
+        record.numel() * record.element_size(), _ptr(d_image), _stream(stream)))
 
 
 def mirres_mesh_regularizers(ctx: Context, scene: Scene, rest_verts, w_smooth, w_offset, loss, grad_verts,

@@ -79,6 +79,21 @@ class Loop:
         self.step_no += 1
         return self.curve[-1]
 
+    @torch.no_grad()
+    def eval_loss(self, n_views=None, seed=12345):
+        """the L2 image loss of the current parameters on a fixed set of cameras (the first
+        `n_views` of the pool, default views_per_step) with a fixed random stream: comparable
+        across steps, free of the per-step camera choice"""
+        chosen = self.gw.views
+        idx = list(range(min(n_views or self.views_per_step, len(self.pool))))
+        self.gw.views = [self.pool[i] for i in idx]
+        images, _ = self.gw.render(launch=1, seed=seed)
+        tot = 0.0
+        for i, im in zip(idx, images):
+            tot += float(((im - self.targets[i]) ** 2).sum())
+        self.gw.views = chosen
+        return tot
+
     def save(self, path):
         torch.save({"step": self.step_no, "curve": self.curve, "opt": self.opt.state_dict(),
                     "params": {k: getattr(self.scene, k).detach().clone() for k in TRAINED}}, path)
@@ -132,6 +147,7 @@ def main():
     loop = Loop(truth, init, views, args.views, args.lr, synth.config2().ris_m)
     if args.resume and args.checkpoint and os.path.exists(args.checkpoint):
         loop.load(args.checkpoint)
+    eval0 = loop.eval_loss()
     t0 = time.perf_counter()
     while loop.step_no < args.steps:
         loop.step()
@@ -140,7 +156,8 @@ def main():
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     out = {"steps": loop.step_no, "res": args.res, "views_per_step": args.views, "spp": args.spp,
-           "bounces": args.bounces, "lr": args.lr, "seconds": dt, "curve": loop.curve}
+           "bounces": args.bounces, "lr": args.lr, "seconds": dt, "eval_loss": [eval0, loop.eval_loss()],
+           "curve": loop.curve}
     if args.out:
         with open(args.out, "w") as f:
             json.dump(out, f)

@@ -124,3 +124,40 @@ def test_eawt_argument_checks(M, ctx):
         M.mirres_eawt(ctx, img, img, img, M.EawtParams(1.0, 1.0, 1.0, 3), img.clone(), small)
     assert M.mirres_eawt_record_bytes(4, 4, 3) == (32 + 20 * 3) * 16
     assert M.mirres_eawt_record_bytes(0, 4, 3) == 0
+
+
+@pytest.mark.parametrize("N,H,W,levels", [(3, 37, 50, 3), (2, 9, 4, 4), (5, 1, 13, 2)])
+def test_eawt_batch_filters_each_image_on_its_own(M, ctx, N, H, W, levels):
+    """a stack of N images in one launch per level: each image the oracle's result on its own
+    (no tap reaches into a neighbouring image), and bit for bit the single-image calls"""
+    rng = np.random.Generator(np.random.PCG64(N * 1000 + H))
+    ins = [_inputs(M, ctx, 77 + i, H, W) for i in range(N)]
+    d = rng.normal(size=(N, H, W, 3)).astype(np.float32)
+    sig = (0.7, 0.5, 1.2)
+    p = M.EawtParams(sig[0], sig[1], sig[2], levels)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    img, nrm, pos = (t(np.stack([a[k] for a in ins])) for k in range(3))
+    out = torch.empty_like(img)
+    rec = torch.empty(N * M.mirres_eawt_record_bytes(W, H, levels) // 4, device="cuda")
+    M.mirres_eawt_batch(ctx, img, nrm, pos, p, out, rec)
+    g = torch.empty_like(img)
+    M.mirres_eawt_batch_backward(ctx, t(d), nrm, pos, p, rec, g)
+    torch.cuda.synchronize()
+    out, g = out.cpu().numpy(), g.cpu().numpy()
+    for i, (im, n, x) in enumerate(ins):
+        ref, orec = E.eawt(im, n, x, *sig, levels=levels)
+        gref = E.eawt_backward(d[i], orec)
+        assert np.abs(out[i] - ref).max() <= 2e-5 * max(1.0, np.abs(ref).max())
+        assert np.abs(g[i] - gref).max() <= 2e-5 * max(1.0, np.abs(gref).max())
+        o1, g1 = _run(M, ctx, im, n, x, sig, levels, d[i])
+        assert np.array_equal(o1, out[i]) and np.array_equal(g1, g[i])
+
+
+def test_eawt_batch_argument_checks(M, ctx):
+    img = torch.zeros((2, 4, 4, 3), device="cuda")
+    p = M.EawtParams(1.0, 1.0, 1.0, 3)
+    one = torch.empty(M.mirres_eawt_record_bytes(4, 4, 3) // 4, device="cuda")
+    with pytest.raises(M.MirresError):
+        M.mirres_eawt_batch(ctx, img, img, img, p, img.clone(), one)  # a record for one image only
+    with pytest.raises(M.MirresError):
+        M.mirres_eawt_batch(ctx, img[:0], img[:0], img[:0], p, img[:0].clone(), one)

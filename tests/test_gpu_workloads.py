@@ -420,26 +420,33 @@ def test_wavefront_autotune_and_shapes(M, ctx):
     """the batched wavefront's launch shape (wave size = queue capacity, per-stage block and grid)
     is tuned on the first views of a batch, becomes the context's shape, and changes nothing but
     the time: renders under the tuned, the default and small odd shapes (waves that split views,
-    64-thread blocks, one block per SM) write the same tape word for word"""
+    64-thread blocks, one block per SM, waves spread over 2 and 3 concurrent chains) write the
+    same tape word for word and count the same rays"""
     w = synth.config5(seed=5, n_scenes=3, max_tris=6000, res_choices=(96, 128), spp_choices=(3, 4), tex=16)
     assert w.samples > 1 << 16  # several waves of 2^16 samples below
     gw = _gw(ctx, w)
     M.mirres_set_wave_shape(ctx, None)
+    M.mirres_reset_counters(ctx)
     ref, reft = gw.render(launch=1)
     torch.cuda.synchronize()
     ref_t = reft.cpu().numpy().copy()
+    ref_rays = M.mirres_get_counters(ctx)[:3]
     tape = gw.new_tape()
     res = M.mirres_autotune_wave(ctx, [s.handle for s in gw.scenes], gw.views, gw.params(1), tape, 0)
     assert res["ms"] > 0 and 16 <= res["wave_log2"] <= 25
     assert all(b in (64, 128, 256) for b in res["block"]) and all(1 <= g <= 64 for g in res["blocks_per_sm"])
-    assert M.mirres_get_wave_shape(ctx) == {k: res[k] for k in ("wave_log2", "block", "blocks_per_sm")}
+    assert M.mirres_get_wave_shape(ctx) == {k: res[k] for k in ("wave_log2", "block", "blocks_per_sm", "branches")}
     shapes = [None, dict(wave_log2=16, block=[64, 128, 256, 64], blocks_per_sm=[1, 2, 3, 64]),
+              dict(wave_log2=16, block=[256] * 4, blocks_per_sm=[8] * 4, branches=2),
+              dict(wave_log2=17, block=[128, 256, 64, 256], blocks_per_sm=[16, 8, 32, 8], branches=3),
               M.mirres_get_wave_shape(ctx)]
     for sh in shapes:
         if sh is not None:
             M.mirres_set_wave_shape(ctx, sh)
+        M.mirres_reset_counters(ctx)
         img, t = gw.render(launch=1)
         torch.cuda.synchronize()
+        assert M.mirres_get_counters(ctx)[:3] == ref_rays, sh
         # every defined tape word equal (words without a defined value are left unwritten)
         compare_tapes(t.cpu().numpy().view(np.uint32).reshape(TAPE_WORDS, -1),
                       ref_t.view(np.uint32).reshape(TAPE_WORDS, -1), rtol=0)
@@ -449,6 +456,8 @@ def test_wavefront_autotune_and_shapes(M, ctx):
         M.mirres_set_wave_shape(ctx, dict(wave_log2=12, block=[256] * 4, blocks_per_sm=[8] * 4))
     with pytest.raises(M.MirresError):
         M.mirres_set_wave_shape(ctx, dict(wave_log2=20, block=[96, 256, 256, 256], blocks_per_sm=[8] * 4))
+    with pytest.raises(M.MirresError):
+        M.mirres_set_wave_shape(ctx, dict(wave_log2=20, block=[256] * 4, blocks_per_sm=[8] * 4, branches=5))
     M.mirres_set_wave_shape(ctx, None)
     for s in gw.scenes:
         s.close()
