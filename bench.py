@@ -414,6 +414,11 @@ def main():
     clk = clocks.stop()
     backward_ms = timed.backward_ms
     stages = M.mirres_stage_times(gw.ctx)  # stage times of the last timed batched render
+    by_bounce = {}
+    for name, b, ms in M.mirres_stage_trace(gw.ctx):
+        if b >= 0:
+            by_bounce.setdefault(name, {}).setdefault(b, 0.0)
+            by_bounce[name][b] += ms
     ms_b = max_over_ranks(ms_b)
     # traversal work of one render, counted outside the timed region by the separately compiled
     # counting variant of the traversal kernels (deterministic: the same rays visit the same
@@ -421,6 +426,20 @@ def main():
     w0 = M.mirres_get_work_counters(gw.ctx)
     M.mirres_render(gw.ctx, scenes, gw.views, gw.params(1, flags=2), images, tape)
     work = [b - a for a, b in zip(w0, M.mirres_get_work_counters(gw.ctx))]
+    # per-launch stage times for the rooflines: with concurrent wave chains (branches > 1) the
+    # launches of different chains overlap and each one's event span includes the other's work,
+    # so the stages are re-timed in an untimed render whose chains run one at a time
+    shape = M.mirres_get_wave_shape(gw.ctx)
+    stages_roof, roof_basis = stages, "stage events of the last timed render"
+    if shape.get("branches", 1) > 1:
+        M.mirres_set_wave_shape(gw.ctx, dict(shape, branches=1))
+        for _ in range(2):  # the first render captures the graph
+            M.mirres_render(gw.ctx, scenes, gw.views, gw.params(1, flags=1), images, tape)
+        torch.cuda.synchronize()
+        stages_roof = M.mirres_stage_times(gw.ctx)
+        roof_basis = ("stage events of an untimed render with the same shape but one wave chain (branches = 1): "
+                      "the timed render's concurrent chains overlap their launches")
+        M.mirres_set_wave_shape(gw.ctx, shape)
 
     def arm(launch):
         ms, msr, rays, launches, _ = timed(launch, args.steps, args.warmup)
@@ -692,7 +711,9 @@ def main():
                         "launch_shape": M.mirres_get_wave_shape(gw.ctx),
                         "launch_shape_stages": list(M.WAVE_STAGES),
                         "stage_ms_per_render": {k: v[0] for k, v in stages.items()},
-                        "stage_launches_per_render": {k: v[1] for k, v in stages.items()}},
+                        "stage_ms_by_bounce": {k: [v[b] for b in sorted(v)] for k, v in by_bounce.items()},
+                        "stage_launches_per_render": {k: v[1] for k, v in stages.items()},
+                        "stage_ms_per_render_one_chain": {k: v[0] for k, v in stages_roof.items()}},
             "plain": plain,
             "persistent": persistent,
             "full_adjoint": full,
@@ -719,7 +740,7 @@ def main():
     per_cand = 60 + 2 * math.log2(env_texels)
     cand_per_render = cnt_b[5] / args.steps
     peak = peaks["fp32_tflops"]
-    total_stage_ms = max(sum(v[0] for v in stages.values()), 1e-9)
+    total_stage_ms = max(sum(v[0] for v in stages_roof.values()), 1e-9)
     stage_flops = {"shade": cand_per_render * per_cand,
                    "closest": 12.0 * work[0] + 27.0 * work[1],
                    "shadow": 12.0 * work[2] + 27.0 * work[3]}
@@ -730,7 +751,7 @@ def main():
     traffic_ok = _traffic_valid()
     roofs = {}
     for k in ("closest", "shade", "shadow"):
-        ms_k, launches_k = stages[k]
+        ms_k, launches_k = stages_roof[k]
         achieved = stage_flops[k] / (ms_k / 1e3) / 1e12
         traffic = (TRAFFIC_PER_UNIT[k] * units_per_render[k] / max(launches_k, 1)) if traffic_ok else None
         roofs[k] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -738,6 +759,7 @@ def main():
                     "traffic_basis": "ncu DRAM bytes per unit on a 2-view capture x units per launch",
                     "kernel": names[k], "kernel_ms_per_launch": ms_k / max(launches_k, 1),
                     "kernel_share_of_render": ms_k / total_stage_ms, "flops_per_render": stage_flops[k],
+                    "timing_basis": roof_basis,
                     "peak_basis": "measured FP32 FMA rate of this device (peaks.fp32_basis), non-tensor"}
         if k in ("closest", "shadow"):
             # the memory side: the traversal's algorithmic bytes (32 B per box test, i.e. per
@@ -752,7 +774,7 @@ def main():
     roofs["shade"].update(flops_per_candidate=per_cand, candidates_per_render=cand_per_render)
     roofs["closest"].update(box_tests_per_render=work[0], triangle_tests_per_render=work[1])
     roofs["shadow"].update(box_tests_per_render=work[2], triangle_tests_per_render=work[3])
-    dominant = max(("closest", "shade", "shadow"), key=lambda k: stages[k][0])
+    dominant = max(("closest", "shade", "shadow"), key=lambda k: stages_roof[k][0])
     line["roofline"] = dict(roofs[dominant])
     line["stage_rooflines"] = roofs
     if rank == 0 and not args.no_cpu:

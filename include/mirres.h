@@ -349,6 +349,14 @@ mirres_status mirres_autotune_wave(mirres_context* ctx, mirres_scene* const* sce
  * shadow rays, ray generation; out_launches likewise. Synchronises on those events. */
 mirres_status mirres_stage_times(mirres_context* ctx, double out_ms[4], int32_t out_launches[4]);
 
+/* The same events one by one, in the order the render issued them: out_ms[i] the device time
+ * of stage launch i (within its wave's chain), out_stage[i] its stage (index as above),
+ * out_bounce[i] its bounce (-1 for ray generation); at most `cap` entries are written, *out_n
+ * receives how many there are. MIRRES_ERR_STATE when no render with flags bit 0 was captured.
+ * Synchronises on those events. */
+mirres_status mirres_stage_trace(mirres_context* ctx, int32_t cap, float* out_ms, int32_t* out_stage,
+                                 int32_t* out_bounce, int32_t* out_n);
+
 /* ---- forward without device allocation ------------------------------------------------ */
 
 #define MIRRES_NOALLOC_SCRATCH_BYTES (512u * 1024u) /* static scratch per GPU, held until exit */

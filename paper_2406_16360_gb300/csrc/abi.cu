@@ -888,7 +888,7 @@ static mirres_status stage_sums(mirres_context* ctx, double ms[4])
         MR_CUDA(cudaEventSynchronize(ctx->stage_events[2 * p + 1]));
         float t = 0.0f;
         MR_CUDA(cudaEventElapsedTime(&t, ctx->stage_events[2 * p], ctx->stage_events[2 * p + 1]));
-        ms[ctx->stage_kind[p]] += t;
+        ms[ctx->stage_kind[p] & 15] += t;
     }
     return MIRRES_OK;
 }
@@ -1047,8 +1047,28 @@ extern "C" mirres_status mirres_stage_times(mirres_context* ctx, double out_ms[4
         MR_CUDA(cudaEventSynchronize(ctx->stage_events[2 * p + 1]));
         float ms = 0.0f;
         MR_CUDA(cudaEventElapsedTime(&ms, ctx->stage_events[2 * p], ctx->stage_events[2 * p + 1]));
-        out_ms[ctx->stage_kind[p]] += ms;
-        if (out_launches) out_launches[ctx->stage_kind[p]] += 1;
+        out_ms[ctx->stage_kind[p] & 15] += ms;
+        if (out_launches) out_launches[ctx->stage_kind[p] & 15] += 1;
+    }
+    return MIRRES_OK;
+}
+
+extern "C" mirres_status mirres_stage_trace(mirres_context* ctx, int32_t cap, float* out_ms, int32_t* out_stage,
+                                            int32_t* out_bounce, int32_t* out_n)
+{
+    if (!ctx || !out_n || cap < 0 || (cap > 0 && (!out_ms || !out_stage || !out_bounce)))
+        return arg_error("ctx and out_n required; out_ms, out_stage and out_bounce when cap > 0");
+    *out_n = ctx->stage_pairs;
+    if (ctx->stage_pairs == 0) {
+        g_err = "mirres_stage_trace: no batched render with params.flags bit 0 was captured";
+        return MIRRES_ERR_STATE;
+    }
+    MR_CUDA(cudaSetDevice(ctx->device));
+    for (int p = 0; p < ctx->stage_pairs && p < cap; ++p) {
+        MR_CUDA(cudaEventSynchronize(ctx->stage_events[2 * p + 1]));
+        MR_CUDA(cudaEventElapsedTime(&out_ms[p], ctx->stage_events[2 * p], ctx->stage_events[2 * p + 1]));
+        out_stage[p] = ctx->stage_kind[p] & 15;
+        out_bounce[p] = (ctx->stage_kind[p] >> 4) - 1;
     }
     return MIRRES_OK;
 }

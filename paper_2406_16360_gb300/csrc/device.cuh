@@ -410,11 +410,37 @@ __device__ __forceinline__ float3 vndf_local(float3 ve, float a, float u1, float
     const float r = sqrtf(u1);
     float sp, cp;
     sincospif(2.0f * u2, &sp, &cp);
-    const float p1 = r * cp;
-    float p2 = r * sp;
-    const float s = 0.5f * (1.0f + vh.z);
-    p2 = (1.0f - s) * sqrtf(fmaxf(0.0f, 1.0f - p1 * p1)) + s * p2;
-    const float3 nh = add(add(mul(t1, p1), mul(t2, p2)), mul(vh, sqrtf(fmaxf(0.0f, 1.0f - p1 * p1 - p2 * p2))));
+    const float p1 = r * cp, p2 = r * sp;
+    const float s = 0.5f * (1.0f + vh.z), s1 = 0.5f * (1.0f - vh.z);
+    // The disc point (p1, p2) is warped to (p1, p2') with p2' = (1 - s) q + s p2, q = sqrt(1 - p1^2),
+    // and lifted by sqrt(1 - p1^2 - p2'^2). Near the rim of the disc (u1 -> 1) both square roots
+    // cancel catastrophically when taken as written; they are rewritten through om = 1 - u1 (exact
+    // for a 24-bit uniform): q^2 = om + p2^2, (q - p2)(q + p2) = om, and
+    // q^2 - p2'^2 = (q - p2')(q + p2') = s (q - p2) (2 (1 - s) q + s (q + p2)), every factor a sum of
+    // non-negative terms or a quotient of them.
+    const float om = 1.0f - u1;
+    const float q = sqrtf(om + p2 * p2);
+    float e, d;  // e = q + p2, d = q - p2, both >= 0 with e d = om
+    if (p2 >= 0.0f) {
+        e = q + p2;
+        d = om / e;
+    } else {
+        d = q - p2;
+        e = om / d;
+    }
+    const float p2w = s1 * q + s * p2;
+    const float z = sqrtf(fmaxf(0.0f, s * d * (2.0f * s1 * q + s * e)));
+    float3 nh = add(add(mul(t1, p1), mul(t2, p2w)), mul(vh, z));
+    // The normal's height above the surface, len p2' + vh.z z (t1.z = 0, t2.z = len = |vh.xy|),
+    // cancels near the visible horizon when p2' < 0; there it equals, with |vh| = 1 and
+    // vh.z q - |p2'| = s (q + p2), s e (vh.z q + |p2'|) / (vh.z z + len |p2'|).
+    const float len = sqrtf(lensq);
+    if (p2w < 0.0f) {
+        const float den = vh.z * z - len * p2w;
+        nh.z = den > 0.0f ? s * e * (vh.z * q - p2w) / den : 0.0f;
+    } else {
+        nh.z = len * p2w + vh.z * z;
+    }
     return normalize(f3(a * nh.x, a * nh.y, fmaxf(0.0f, nh.z)));
 }
 

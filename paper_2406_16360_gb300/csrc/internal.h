@@ -51,7 +51,8 @@ struct mirres_context {
     cudaEvent_t* stage_events = nullptr;     // [n_stage_events]: (start, end) pairs per stage launch
     int n_stage_events = 0;
     int stage_pairs = 0;                     // pairs recorded by the current graph
-    int* stage_kind = nullptr;               // [n_stage_events / 2]: 0 closest, 1 shade, 2 shadow, 3 raygen
+    int* stage_kind = nullptr;               // [n_stage_events / 2]: bits 0-3 the stage (0 closest, 1 shade,
+                                             // 2 shadow, 3 raygen), above them the bounce + 1
 };
 
 struct mirres_scene {

@@ -752,11 +752,11 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                                                   256, smem);
     const unsigned grid_c = (unsigned)(sms * (occ_c > 0 ? occ_c : 1));
     const unsigned grid_s = (unsigned)(sms * (occ_s > 0 ? occ_s : 1));
-    int pair = 0;
+    int pair = 0, cur_b = -1;  // cur_b: the bounce being recorded (-1: ray generation)
     cudaStream_t st = st_main;
     auto mark = [&](int k, bool start) {
         if (!ev) return;
-        if (start) kind[pair] = k;
+        if (start) kind[pair] = k | ((cur_b + 1) << 4);  // stage in bits 0-3, bounce + 1 above
         cudaEventRecordWithFlags(ev[2 * pair + (start ? 0 : 1)], st, cudaEventRecordExternal);
         if (!start) ++pair;
     };
@@ -770,6 +770,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         const uint64_t first = wave_first[wv];
         const uint32_t n = (uint32_t)((wv + 1 < n_waves ? wave_first[wv + 1] : total) - first);
         cudaMemsetAsync(qc, 0, sizeof(unsigned int) * (5 * max_bounces + 3), st);
+        cur_b = -1;
         mark(3, true);
         k_wraygen<<<grid_cap(n, blk_g, cap_g), blk_g, 0, st>>>(views, n_views, rng, first, n, qa, tape, total, nvx,
                                                                res);
@@ -777,6 +778,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
         QueueDev cur = qa, nxt = qb;
         for (int b = 0; b < max_bounces; ++b) {
             const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
+            cur_b = b;
             mark(0, true);
             unsigned long long* keys = nullptr;
             if (raster && b == 0) {

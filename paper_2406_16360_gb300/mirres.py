@@ -22,7 +22,7 @@ __all__ = ["MirresError", "Context", "Scene", "View", "Params", "Grads", "make_v
            "mirres_scene_set_normals", "MIRRES_NORMALS_FACE", "MIRRES_NORMALS_INTERPOLATED", "mirres_tape_bytes", "mirres_tape_bytes_mode",
            "mirres_reuse_history_bytes", "mirres_render",
            "mirres_render_noalloc",
-           "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_backward",
+           "mirres_autotune", "mirres_set_launch", "mirres_stage_times", "mirres_stage_trace", "mirres_backward",
            "WaveShape", "mirres_set_wave_shape", "mirres_get_wave_shape", "mirres_autotune_wave",
            "mirres_l2_loss", "mirres_trace", "mirres_bvh_export", "mirres_env_export", "mirres_env_export_flat",
            "mirres_get_counters",
@@ -149,6 +149,8 @@ def lib():
                 "mirres_autotune_wave": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params), vp,
                                               sz, C.c_uint64, C.POINTER(WaveShape), C.POINTER(C.c_float), vp]),
                 "mirres_stage_times": (st, [vp, C.POINTER(C.c_double), C.POINTER(i32)]),
+                "mirres_stage_trace": (st, [vp, i32, C.POINTER(C.c_float), C.POINTER(i32), C.POINTER(i32),
+                                            C.POINTER(i32)]),
                 "mirres_render_noalloc": (st, [C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
                                                C.POINTER(vp), vp, sz, vp]),
                 "mirres_backward": (st, [vp, C.POINTER(vp), i32, C.POINTER(View), i32, C.POINTER(Params),
@@ -390,6 +392,18 @@ def mirres_stage_times(ctx: Context):
     _check("mirres_stage_times", lib().mirres_stage_times(ctx.handle, ms, n))
     names = ("closest", "shade", "shadow", "raygen")
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(names)}
+
+
+def mirres_stage_trace(ctx: Context):
+    """every stage launch of the last event-recording batched render, in issue order:
+    list of (stage name, bounce (-1: ray generation), ms)"""
+    n = C.c_int32()
+    lib().mirres_stage_trace(ctx.handle, 0, None, None, None, C.byref(n))
+    cap = n.value
+    ms, stg, bnc = (C.c_float * max(cap, 1))(), (C.c_int32 * max(cap, 1))(), (C.c_int32 * max(cap, 1))()
+    _check("mirres_stage_trace", lib().mirres_stage_trace(ctx.handle, cap, ms, stg, bnc, C.byref(n)))
+    names = ("closest", "shade", "shadow", "raygen")
+    return [(names[stg[i]], int(bnc[i]), float(ms[i])) for i in range(min(cap, n.value))]
 
 
 def mirres_render_noalloc(scenes, views, params: Params, images, tape, stream=None):

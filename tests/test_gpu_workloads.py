@@ -463,6 +463,32 @@ def test_wavefront_autotune_and_shapes(M, ctx):
         s.close()
 
 
+def test_stage_trace_lists_every_stage_launch(M, ctx):
+    """the stage events of a batched render one by one: ray generation then (closest, shade,
+    shadow) per bounce for every wave, summing per stage to mirres_stage_times"""
+    w = synth.config5(seed=6, n_scenes=2, max_tris=4000, res_choices=(96,), spp_choices=(4,), tex=16)
+    gw = _gw(ctx, w)
+    M.mirres_set_wave_shape(ctx, dict(wave_log2=16, block=[256] * 4, blocks_per_sm=[8] * 4, branches=2))
+    gw.render(launch=1, flags=1)
+    torch.cuda.synchronize()
+    tr = M.mirres_stage_trace(ctx)
+    sums = M.mirres_stage_times(ctx)
+    B = max(v.bounces for v in w.views)
+    n_waves = -(-w.samples // (1 << 16))
+    assert len(tr) == n_waves * (1 + 3 * B)
+    for k in range(n_waves):
+        chunk = tr[k * (1 + 3 * B):(k + 1) * (1 + 3 * B)]
+        assert chunk[0][:2] == ("raygen", -1)
+        assert [c[:2] for c in chunk[1:]] == [(s, b) for b in range(B) for s in ("closest", "shade", "shadow")]
+    for name, (ms, n) in sums.items():
+        part = [c[2] for c in tr if c[0] == name]
+        assert len(part) == n and abs(sum(part) - ms) <= 1e-6 * max(ms, 1.0) + 1e-9
+        assert all(t >= 0.0 for t in part)
+    M.mirres_set_wave_shape(ctx, None)
+    for s in gw.scenes:
+        s.close()
+
+
 # ---------------------------------------------------------------------------------------
 # FULL-mode adjoint (the gradients of the indirect rays at every vertex)
 # ---------------------------------------------------------------------------------------
