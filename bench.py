@@ -260,6 +260,8 @@ def main():
     ap.add_argument("--traversal", default="binary", choices=["binary", "wide"],
                     help="ray traversal through the binary tree (default) or the 8-wide BVH collapsed from it")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--bin", action="store_true",
+                    help="batched launch: bin continuation rays by origin cell and direction octant")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     args = ap.parse_args()
@@ -271,6 +273,7 @@ def main():
 
     import numpy as np
     import torch
+    BIN_FLAG = 8 if args.bin else 0
     import torch.distributed as dist
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -355,7 +358,7 @@ def main():
             ev_render[0].record()
         # the batched wavefront records stage events (graph event nodes) for the roofline
         M.mirres_render(gw.ctx, scenes, gw.views, gw.params(launch, block=args.block, blocks_per_sm=args.blocks_per_sm,
-                                                            flags=1 if launch == 1 else 0,
+                                                            flags=(1 | BIN_FLAG) if launch == 1 else 0,
                                                             grad_mode=grad_mode, reuse=reuse, temporal=temporal,
                                                             history=history),
                         images, tape)
@@ -709,6 +712,7 @@ def main():
             "batched": {"value": value, "ms_per_step": ms_b / args.steps, "mrays_per_s": mrays,
                         "launch": "batched wavefront, one CUDA graph per forward",
                         "launch_shape": M.mirres_get_wave_shape(gw.ctx),
+                        "binned_continuation_rays": bool(args.bin),
                         "launch_shape_stages": list(M.WAVE_STAGES),
                         "stage_ms_per_render": {k: v[0] for k, v in stages.items()},
                         "stage_ms_by_bounce": {k: [v[b] for b in sorted(v)] for k, v in by_bounce.items()},

@@ -135,7 +135,10 @@ typedef struct {
  *            batched wavefront resolves primary visibility by rasterisation (each triangle
  *            projected into the view, each camera sample in its screen box tested with the
  *            traversal's FP32 ray/triangle solve, closest by a 64-bit atomicMin on (t, triangle)),
- *            as the paper does with a rasteriser, instead of tracing primary rays
+ *            as the paper does with a rasteriser, instead of tracing primary rays; bit 3: the
+ *            batched wavefront bins each bounce's continuation rays by origin cell (8 x 8 x 8
+ *            over the scene's bounds) and direction octant before tracing them (a counting
+ *            sort of the ray queue; the results are unchanged, only the rays' order in the queue)
  *   max_visits  failure detection: every ray traversal is a bounded loop of at most max_visits
  *            node visits (0 = 4 n_tris + 64, more than any well-formed tree needs) on a bounded
  *            stack; a traversal that reaches either bound ends as a miss and raises the
@@ -161,6 +164,7 @@ typedef struct {
 #define MIRRES_FLAG_STAGE_EVENTS 1
 #define MIRRES_FLAG_COUNT_WORK 2
 #define MIRRES_FLAG_RASTER 4
+#define MIRRES_FLAG_BIN 8
 
 /* Gradient destinations for one scene (device pointers, shapes of the scene's inputs).
  * Accumulated (+=); a NULL pointer skips that parameter. */

@@ -968,7 +968,11 @@ int32_t orc_wrs(const double* gamma, const double* u, int32_t m, double* w_sum)
 /* ---------------------------------------------------------------------------------------
  * materials: bilinear texture lookup, texel centres at (i + 0.5) / w, clamp to edge
  * ------------------------------------------------------------------------------------- */
-typedef struct { int idx[4]; double w[4]; double dw_dx[4], dw_dy[4]; } Taps;
+typedef struct {
+    int idx[4]; double w[4]; double dw_dx[4], dw_dy[4];
+    int w_tex, h_tex, ix0, iy0; /* texture size and the footprint's unclamped corner */
+    double fx, fy;              /* fractional position inside the footprint */
+} Taps;
 
 static void taps_at(int w, int h, double su, double sv, Taps* tp)
 {
@@ -988,6 +992,35 @@ static void taps_at(int w, int h, double su, double sv, Taps* tp)
     /* derivatives w.r.t. the texture coordinate (su, sv) */
     tp->dw_dx[0] = -(1 - fy) * w; tp->dw_dx[1] = (1 - fy) * w; tp->dw_dx[2] = -fy * w; tp->dw_dx[3] = fy * w;
     tp->dw_dy[0] = -(1 - fx) * h; tp->dw_dy[1] = -fx * h; tp->dw_dy[2] = (1 - fx) * h; tp->dw_dy[3] = fx * h;
+    tp->w_tex = w; tp->h_tex = h; tp->ix0 = (int)x0; tp->iy0 = (int)y0; tp->fx = fx; tp->fy = fy;
+}
+
+/* Texels whose bilinear weight an FP32 evaluation of this lookup may change (test tolerance
+ * only): the four taps, and where the fractional position lies within (dfx, dfy) texels of a
+ * texel centre, the row or column beyond it -- a single-precision lookup on the other side of
+ * the centre takes its footprint one texel further. Returns the count written to idx (<= 16;
+ * indices clamped to the texture as the lookup clamps them). */
+static int taps_reach(const Taps* tp, double dfx, double dfy, int idx[16])
+{
+    int xs[4], ys[4], nx = 0, ny = 0, n = 0;
+    if (tp->fx < dfx) xs[nx++] = tp->ix0 - 1;
+    xs[nx++] = tp->ix0;
+    xs[nx++] = tp->ix0 + 1;
+    if (1.0 - tp->fx < dfx) xs[nx++] = tp->ix0 + 2;
+    if (tp->fy < dfy) ys[ny++] = tp->iy0 - 1;
+    ys[ny++] = tp->iy0;
+    ys[ny++] = tp->iy0 + 1;
+    if (1.0 - tp->fy < dfy) ys[ny++] = tp->iy0 + 2;
+    for (int b = 0; b < ny; ++b) {
+        int y = ys[b] < 0 ? 0 : (ys[b] > tp->h_tex - 1 ? tp->h_tex - 1 : ys[b]);
+        for (int a = 0; a < nx; ++a) {
+            int x = xs[a] < 0 ? 0 : (xs[a] > tp->w_tex - 1 ? tp->w_tex - 1 : xs[a]);
+            int id = y * tp->w_tex + x, dup = 0;
+            for (int k = 0; k < n; ++k) dup |= idx[k] == id;
+            if (!dup) idx[n++] = id;
+        }
+    }
+    return n;
 }
 
 typedef struct {
@@ -1592,8 +1625,10 @@ static void prim_grad(const Ctx* c, const Rec* rec, const double g[3], int kind,
         double dfx = s->tw * (fabs(uv[2] - uv[0]) * du + fabs(uv[4] - uv[0]) * dv);
         double dfy = s->th * (fabs(uv[3] - uv[1]) * du + fabs(uv[5] - uv[1]) * dv);
         double dw = dfx + dfy;
-        for (int k = 0; k < 4; ++k) {
-            int i = sh.tp.idx[k];
+        int reach[16];
+        int nr = taps_reach(&sh.tp, dfx, dfy, reach);
+        for (int k = 0; k < nr; ++k) {
+            int i = reach[k];
             for (int ch = 0; ch < 3; ++ch) sp_add(sp, GB_ALB_S, 3 * (int64_t)i + ch, dw * fabs(gm[ch]));
             sp_add(sp, GB_RGH_S, i, dw * fabs(gm[3]));
             sp_add(sp, GB_MET_S, i, dw * fabs(gm[4]));
@@ -1816,8 +1851,10 @@ static void sample_grad_secondary(const Ctx* c, const Rec* rec, const double g[3
             double dfx = s->tw * (fabs(uv[2] - uv[0]) * du + fabs(uv[4] - uv[0]) * dv);
             double dfy = s->th * (fabs(uv[3] - uv[1]) * du + fabs(uv[5] - uv[1]) * dv);
             double dw = dfx + dfy;
-            for (int k = 0; k < 4; ++k) {
-                int i = h->tp.idx[k];
+            int reach[16];
+            int nr = taps_reach(&h->tp, dfx, dfy, reach);
+            for (int k = 0; k < nr; ++k) {
+                int i = reach[k];
                 for (int ch = 0; ch < 3; ++ch) sp_add(sp, GB_ALB_S, 3 * (int64_t)i + ch, dw * fabs(gm[ch]));
                 sp_add(sp, GB_RGH_S, i, dw * fabs(gm[3]));
                 sp_add(sp, GB_MET_S, i, dw * fabs(gm[4]));

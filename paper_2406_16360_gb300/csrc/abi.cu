@@ -526,9 +526,12 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     plan.take<SceneDev>((size_t)n_scenes);
     plan.take<float*>((size_t)n_views);
     plan.take<uint64_t>((size_t)n_views);
+    const bool bin = (flags & 8) != 0 && max_b > 1;
     for (int b = 0; b < nb; ++b) {
         plan.take<unsigned int>(5 * (size_t)max_b + 3);
         for (int k = 0; k < 16; ++k) plan.take<float4>(wave);
+        plan.take<uint16_t>(bin ? wave : 0);
+        plan.take<unsigned int>(bin ? 4096 : 0);
     }
     for (int k = 0; k < 6; ++k) plan.take<uint32_t>(reuse ? total : 0);
     MR_TRY(ws_reserve(ctx, plan.off));
@@ -546,6 +549,8 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         br[b].qb = QueueDev{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
         br[b].hq = QueueDev{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
         br[b].sq = ShadowDev{cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave), cv.take<float4>(wave)};
+        br[b].bkey = cv.take<uint16_t>(bin ? wave : 0);
+        br[b].bhist = cv.take<unsigned int>(bin ? 4096 : 0);
     }
     ResDev res{};
     if (reuse) {
@@ -581,7 +586,7 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
     key.max_b = max_b;
     key.M = M;
     key.sms = ctx->sm_count;
-    key.flags = flags & 7;
+    key.flags = flags & 15;
     key.nvx = nvx;
     key.reuse_k = reuse_k;
     key.reuse_radius = reuse_radius;
@@ -616,7 +621,8 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
                        ctx->branch_event[0], ctx->branch_event, tp, ctx->counters, d_pixoff, total_pix, d_images,
                        ctx->sm_count, (flags & 1) ? ctx->stage_events : nullptr,
                        (flags & 1) ? ctx->stage_kind : nullptr, nvx, (flags & 2) != 0, reuse_k, reuse_radius, res,
-                       temporal, temporal_cap, hist, vdev.data(), sdev.data(), (flags & 4) != 0, ctx->wave_shape);
+                       temporal, temporal_cap, hist, vdev.data(), sdev.data(), (flags & 4) != 0, bin,
+                       ctx->wave_shape);
         ctx->stage_pairs = (flags & 1) ? pairs : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &g);
@@ -642,7 +648,8 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
                 }
             }
         }
-        ctx->graph_launches = (unsigned long long)mr_wave_launches(n_waves, max_b, reuse, temporal, raster_launches);
+        ctx->graph_launches =
+            (unsigned long long)mr_wave_launches(n_waves, max_b, reuse, temporal, raster_launches, bin);
     }
     MR_CUDA(cudaGraphLaunch(ctx->graph, st));
     ctx->host_launches += ctx->graph_launches;

@@ -130,6 +130,8 @@ struct WaveBranch {
     QueueDev qa, qb, hq;
     ShadowDev sq;
     unsigned int* qc;
+    uint16_t* bkey;      // [wave] binning keys (flags bit 3)
+    unsigned int* bhist; // [4096] binning histogram / cursors
     cudaStream_t st;
 };
 void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total, int max_bounces,
@@ -138,6 +140,6 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaEvent_t* ev,
                     int* kind, int nvx, bool count, int reuse_k, int reuse_radius, const ResDev& res, int temporal,
                     int temporal_cap, const HistDev& hist, const ViewDev* hviews, const SceneDev* hscenes, bool raster,
-                    const mirres_wave_shape& shape);
-int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal, int raster_launches);
+                    bool bin, const mirres_wave_shape& shape);
+int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal, int raster_launches, bool bin);
 int mr_wave_stage_pairs(int n_waves, int max_bounces);

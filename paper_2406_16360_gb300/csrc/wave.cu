@@ -124,6 +124,115 @@ __global__ void MR_TRACE_BOUNDS k_wclosest(const SceneDev* __restrict__ scenes,
     if (COUNT) flush_work(counters, CNT_CBOX, n_box, (unsigned int)n_tri);
 }
 
+// ---- binning of a ray queue by origin cell and direction octant ----------------------------
+// A queue of secondary rays (4 float4 arrays; the third one's w holds the view index) is
+// reordered so that rays whose origins share a cell of an 8 x 8 x 8 grid over their scene's
+// bounds (Morton order) and whose directions share an octant sit next to each other: a warp of
+// neighbouring rays then descends the same subtrees. Counting sort on the 12-bit key: a block
+// histogram flushed to a global one, an exclusive scan, and a scatter whose warps reserve
+// their slots per key with one atomic per distinct key. The order within a key is arbitrary
+// (as the order of the queues already is); each ray's record moves unchanged.
+constexpr int BIN_KEYS = 4096;
+
+__device__ __forceinline__ uint32_t spread3(uint32_t x)  // 3 bits -> every third bit
+{
+    return (x & 1u) | ((x & 2u) << 2) | ((x & 4u) << 4);
+}
+
+__device__ __forceinline__ uint32_t bin_key(const SceneDev& s, float3 o, float3 d)
+{
+    const uint32_t oct = (d.x < 0.0f ? 1u : 0u) | (d.y < 0.0f ? 2u : 0u) | (d.z < 0.0f ? 4u : 0u);
+    uint32_t cell = 0;
+    if (s.n_tris >= 2) {  // the root node's two child boxes span the scene
+        const float4 a = __ldg(s.nodes), b = __ldg(s.nodes + 1), c = __ldg(s.nodes + 2);
+        const float lx = fminf(a.x, b.z), ly = fminf(a.y, b.w), lz = fminf(a.z, c.x);
+        const float hx = fmaxf(a.w, c.y), hy = fmaxf(b.x, c.z), hz = fmaxf(b.y, c.w);
+        auto q = [](float v, float lo, float hi) {
+            const float f = (v - lo) / fmaxf(hi - lo, 1e-30f) * 8.0f;
+            return (uint32_t)min(max((int)f, 0), 7);  // NaN -> 0
+        };
+        cell = (spread3(q(o.x, lx, hx)) << 2) | (spread3(q(o.y, ly, hy)) << 1) | spread3(q(o.z, lz, hz));
+    }
+    return (cell << 3) | oct;
+}
+
+__global__ void __launch_bounds__(256) k_bin_hist(const SceneDev* __restrict__ scenes,
+                                                  const ViewDev* __restrict__ views, QueueDev q,
+                                                  const unsigned int* __restrict__ count, uint16_t* __restrict__ keys,
+                                                  unsigned int* __restrict__ hist)
+{
+    __shared__ unsigned int h[BIN_KEYS];
+    for (int k = threadIdx.x; k < BIN_KEYS; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    const unsigned int n = *count;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 o = q.o[i], d = q.d[i];
+        const int vi = __float_as_int(q.b[i].w);
+        const uint32_t k = bin_key(scenes[views[vi].scene], xyz(o), xyz(d));
+        keys[i] = (uint16_t)k;
+        atomicAdd(&h[k], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < BIN_KEYS; k += blockDim.x)
+        if (h[k]) atomicAdd(&hist[k], h[k]);
+}
+
+// exclusive scan of the BIN_KEYS counts in place (one block of 1024 threads, 4 keys each)
+__global__ void __launch_bounds__(1024) k_bin_scan(unsigned int* __restrict__ hist)
+{
+    __shared__ unsigned int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint4 v = reinterpret_cast<const uint4*>(hist)[t];
+    const unsigned int s = v.x + v.y + v.z + v.w;
+    unsigned int x = s;
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int y = __shfl_up_sync(MR_FULL, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned int w = wsum[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned int y = __shfl_up_sync(MR_FULL, w, off);
+            if (lane >= off) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const unsigned int base = x - s + (warp > 0 ? wsum[warp - 1] : 0u);
+    reinterpret_cast<uint4*>(hist)[t] = make_uint4(base, base + v.x, base + v.x + v.y, base + v.x + v.y + v.z);
+}
+
+// every lane of every warp runs the same number of rounds (the match and shuffle need the
+// full warp); `cursor` holds each key's next free slot
+__global__ void __launch_bounds__(256) k_bin_scatter(QueueDev in, QueueDev out, const unsigned int* __restrict__ count,
+                                                     const uint16_t* __restrict__ keys,
+                                                     unsigned int* __restrict__ cursor)
+{
+    const unsigned int n = *count;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    const unsigned int rounds = (n + stride - 1) / stride;
+    const int lane = lane_id();
+    for (unsigned int r = 0; r < rounds; ++r) {
+        const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t k = valid ? (uint32_t)keys[i] : 0xFFFFFFFFu;
+        const unsigned int peers = __match_any_sync(MR_FULL, k);
+        const int leader = __ffs(peers) - 1;
+        unsigned int base = 0;
+        if (valid && lane == leader) base = atomicAdd(&cursor[k], (unsigned int)__popc(peers));
+        base = __shfl_sync(MR_FULL, base, leader);
+        if (valid) {
+            const unsigned int dst = base + (unsigned int)__popc(peers & lanemask_lt());
+            out.o[dst] = in.o[i];
+            out.d[dst] = in.d[i];
+            out.b[dst] = in.b[i];
+            out.bi[dst] = in.bi[i];
+        }
+    }
+}
+
 template <bool REUSE, bool INTERP>
 __global__ void __launch_bounds__(256, MR_SHADE_MINB) k_wshade(const SceneDev* __restrict__ scenes,
                                                 const ViewDev* __restrict__ views, Rng rng, int b, int M,
@@ -722,7 +831,7 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
                     const uint64_t* pix_off, uint64_t total_pix, float* const* images, int sms, cudaEvent_t* ev,
                     int* kind, int nvx, bool count, int reuse_k, int reuse_radius, const ResDev& res, int temporal,
                     int temporal_cap, const HistDev& hist, const ViewDev* hviews, const SceneDev* hscenes, bool raster,
-                    const mirres_wave_shape& shape)
+                    bool bin, const mirres_wave_shape& shape)
 {
     // waves go round-robin to `n_branches` chains of their own (queues, counters, stream): chain
     // 0 on the recording stream, the others forked from it and joined back before the resolve,
@@ -780,6 +889,17 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
             const unsigned int* cnt_in = b == 0 ? nullptr : qc + 3 * (b - 1) + 1;
             cur_b = b;
             mark(0, true);
+            if (bin && b > 0) {
+                // the continuation rays shade wrote (cur) binned into the free queue (nxt),
+                // which becomes this bounce's input
+                cudaMemsetAsync(br.bhist, 0, sizeof(unsigned int) * BIN_KEYS, st);
+                k_bin_hist<<<grid_cap(n, 256, sms * 4), 256, 0, st>>>(scenes, views, cur, cnt_in, br.bkey, br.bhist);
+                k_bin_scan<<<1, 1024, 0, st>>>(br.bhist);
+                k_bin_scatter<<<grid_cap(n, 256, sms * 8), 256, 0, st>>>(cur, nxt, cnt_in, br.bkey, br.bhist);
+                const QueueDev t = cur;
+                cur = nxt;
+                nxt = t;
+            }
             unsigned long long* keys = nullptr;
             if (raster && b == 0) {
                 // the next-bounce queue is free until shading fills it: its last array holds
@@ -849,8 +969,8 @@ void mr_wave_record(const SceneDev* scenes, const ViewDev* views, int n_views, u
 
 int mr_wave_stage_pairs(int n_waves, int max_bounces) { return n_waves * (1 + 3 * max_bounces); }
 
-int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal, int raster_launches)
+int mr_wave_launches(int n_waves, int max_bounces, bool reuse, int temporal, int raster_launches, bool bin)
 {
-    const int extra = (reuse ? 1 : 0) + (temporal == 2 ? 1 : 0) + (temporal ? 1 : 0);
+    const int extra = (reuse ? 1 : 0) + (temporal == 2 ? 1 : 0) + (temporal ? 1 : 0) + (bin ? 3 * (max_bounces - 1) : 0);
     return n_waves * (2 + 3 * max_bounces + extra) + 1 + raster_launches;
 }

@@ -39,7 +39,7 @@ MIRRES_FULL_MAX_BOUNCES = 16
 GRAD_PRIMARY, GRAD_FULL = 0, 1
 MIRRES_BVH_LBVH, MIRRES_BVH_PLOC = 0, 1
 MIRRES_NORMALS_FACE, MIRRES_NORMALS_INTERPOLATED = 0, 1
-MIRRES_FLAG_STAGE_EVENTS, MIRRES_FLAG_COUNT_WORK, MIRRES_FLAG_RASTER = 1, 2, 4
+MIRRES_FLAG_STAGE_EVENTS, MIRRES_FLAG_COUNT_WORK, MIRRES_FLAG_RASTER, MIRRES_FLAG_BIN = 1, 2, 4, 8
 MIRRES_TRAVERSAL_BINARY, MIRRES_TRAVERSAL_WIDE = 0, 1
 MIRRES_NOALLOC_SCRATCH_BYTES = 512 * 1024
 MIRRES_NOALLOC_MAX_VIEWS = 4096

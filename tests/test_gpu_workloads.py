@@ -463,6 +463,30 @@ def test_wavefront_autotune_and_shapes(M, ctx):
         s.close()
 
 
+@pytest.mark.parametrize("branches", [1, 2])
+def test_binned_continuation_rays_change_nothing_but_order(M, ctx, branches):
+    """flags bit 3 reorders each bounce's continuation rays by origin cell and direction octant
+    before tracing them: the tape, the images and the ray counts are those of the unbinned
+    render (multi-scene batch, mixed bounces, waves that split views)"""
+    w = synth.config5(seed=8, n_scenes=3, max_tris=6000, res_choices=(64, 96), spp_choices=(3, 4), tex=16)
+    gw = _gw(ctx, w)
+    M.mirres_set_wave_shape(ctx, dict(wave_log2=16, block=[256] * 4, blocks_per_sm=[8] * 4, branches=branches))
+    out = []
+    for flags in (0, M.MIRRES_FLAG_BIN):
+        M.mirres_reset_counters(ctx)
+        img, t = gw.render(launch=1, flags=flags)
+        torch.cuda.synchronize()
+        out.append(([i.clone() for i in img], t.cpu().numpy().copy(), M.mirres_get_counters(ctx)[:3]))
+    (ia, ta, ca), (ib, tb, cb) = out
+    assert ca == cb
+    compare_tapes(tb.view(np.uint32).reshape(TAPE_WORDS, -1), ta.view(np.uint32).reshape(TAPE_WORDS, -1), rtol=0)
+    for a, b in zip(ia, ib):
+        assert torch.equal(a, b)
+    M.mirres_set_wave_shape(ctx, None)
+    for s in gw.scenes:
+        s.close()
+
+
 def test_stage_trace_lists_every_stage_launch(M, ctx):
     """the stage events of a batched render one by one: ray generation then (closest, shade,
     shadow) per bounce for every wave, summing per stage to mirres_stage_times"""
