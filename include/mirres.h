@@ -119,7 +119,8 @@ typedef struct {
  *            u w_sum < weight with u from the third word; the merged reservoir counts ris_m
  *            candidates per reservoir (own and neighbours that hit), W = w_sum / (m p_hat(y)).
  *            The paper gives no MIS weights: this is the biased 1/m combination. Batched
- *            launch only (whole views per wave); reuse_k in [0, 64], reuse_radius >= 1.
+ *            launch only (whole views per wave, a wave enlarged to hold the largest view);
+ *            reuse_k in [0, 64], reuse_radius >= 1.
  *   temporal, temporal_cap, reuse_history  temporal reuse (Appendix A: reservoirs of previous
  *            frames merged): with temporal = 2 every primary vertex first merges the reservoir
  *            its sample left in reuse_history (candidate count capped at temporal_cap * ris_m,
@@ -383,7 +384,7 @@ mirres_status mirres_stage_trace(mirres_context* ctx, int32_t cap, float* out_ms
  *   - n_views > MIRRES_NOALLOC_MAX_VIEWS or n_scenes > MIRRES_NOALLOC_MAX_SCENES is rejected
  *     with MIRRES_ERR_ARG and a message naming the limit; all scenes share one context.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture begins.
+ *     with that device current.
  *   - Every call shares the one array, which keeps the last call's contents; the call resets
  *     what must start at zero (the work counter). Calls whose work overlaps on the GPU (on
  *     different streams, or from several host threads without ordering) race on the array:

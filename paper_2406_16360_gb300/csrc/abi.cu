@@ -411,6 +411,14 @@ static Rng make_rng(const mirres_params* p)
 
 // the default wavefront shape (mirres_wave_shape): 2^25 samples per wave (the queues take 256
 // bytes per sample of a wave), 256 threads and 8 blocks per SM for every stage, one chain
+// any scene traversed through its 8-wide BVH (the persistent kernel then runs its wide variant)
+static bool any_wide(const std::vector<SceneDev>& sdev)
+{
+    for (const SceneDev& d : sdev)
+        if (d.wnodes) return true;
+    return false;
+}
+
 static mirres_wave_shape default_wave_shape() { return mirres_wave_shape{25, {256, 256, 256, 256}, {8, 8, 8, 8}, 1}; }
 
 static mirres_status check_wave_shape(const mirres_wave_shape& w)
@@ -496,19 +504,20 @@ static mirres_status render_wave(mirres_context* ctx, const std::vector<SceneDev
         pixoff[(size_t)i] = total_pix;
         total_pix += (uint64_t)vdev[(size_t)i].width * vdev[(size_t)i].height;
     }
-    const uint64_t kWave = 1ull << ctx->wave_shape.wave_log2;
+    uint64_t kWave = 1ull << ctx->wave_shape.wave_log2;
+    if (reuse) {
+        // waves hold whole views (a pixel's neighbours must have been shaded in the same wave):
+        // a view larger than the shape's wave gets a wave of its own size
+        for (const ViewDev& v : vdev) kWave = std::max<uint64_t>(kWave, (uint64_t)v.width * v.height * v.spp);
+    }
     const uint64_t wave = std::min<uint64_t>(total, kWave);
-    // wave boundaries: every kWave samples, or with spatial reuse whole views per wave (a
-    // pixel's neighbours must have been shaded in the same wave)
+    // wave boundaries: every kWave samples, or with spatial reuse whole views per wave
     std::vector<uint64_t> wave_first;
     if (reuse) {
         uint64_t in_wave = 0;
         for (int i = 0; i < n_views; ++i) {
             const ViewDev& v = vdev[(size_t)i];
             const uint64_t nv = (uint64_t)v.width * v.height * v.spp;
-            if (nv > kWave)
-                return arg_error("spatial reuse needs every view to fit one wave (" + std::to_string(kWave) +
-                                 " samples); view " + std::to_string(i) + " has " + std::to_string(nv));
             if (wave_first.empty() || in_wave + nv > kWave) {
                 wave_first.push_back(v.offset);
                 in_wave = 0;
@@ -736,7 +745,7 @@ extern "C" mirres_status mirres_render(mirres_context* ctx, mirres_scene* const*
         }
         const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy_v(var);
         MR_CUDA(mr_launch_persistent_v(var, d_scenes, d_views, n_views, total, rng, M, d_work, chunk_w, tp,
-                                       ctx->counters, per_sm * sms, st, nvx));
+                                       ctx->counters, per_sm * sms, st, nvx, any_wide(sdev)));
         mr_launch_resolve_all(d_views, n_views, d_pixoff, tp_pix, d_images, tp, total, sms, st);
         MR_CUDA(cudaGetLastError());
         ctx->host_launches += 2;
@@ -824,7 +833,7 @@ extern "C" mirres_status mirres_autotune(mirres_context* ctx, mirres_scene* cons
                 if (e == cudaSuccess) e = cudaEventRecord(e0, st);
                 if (e == cudaSuccess)
                     e = mr_launch_persistent_v(v, d_scenes, d_views, n_views, n, rng, params->ris_m, d_work, c, tape,
-                                               ctx->counters, blocks, st);
+                                               ctx->counters, blocks, st, 0, any_wide(sdev));
                 if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);

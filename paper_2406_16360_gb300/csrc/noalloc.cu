@@ -153,8 +153,10 @@ extern "C" mirres_status mirres_render_noalloc(mirres_scene* const* scenes, int3
         chunk_w = ctx->tuned_chunk;
     }
     const int per_sm = params->blocks_per_sm ? params->blocks_per_sm : mr_persistent_occupancy_v(var);
+    bool wide = false;
+    for (int i = 0; i < n_scenes; ++i) wide = wide || g_scenes[i].wnodes != nullptr;
     MR_CUDA(mr_launch_persistent_v(var, d_scenes, d_views, n_views, total, rng, params->ris_m, d_work, chunk_w, tape,
-                                   ctx->counters, per_sm * ctx->sm_count, s));
+                                   ctx->counters, per_sm * ctx->sm_count, s, 0, wide));
     mr_launch_resolve_all(d_views, n_views, d_pixoff, total_pix, d_images, tape, total, ctx->sm_count, s);
     MR_CUDA(cudaGetLastError());
     return MIRRES_OK;

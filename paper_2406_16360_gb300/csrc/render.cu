@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(256) k_resolve(ViewDev v, const void* tape, ui
 // take the next one), so that the expensive part -- shading with RIS over M candidates --
 // runs on full warps; then the shadow rays of those vertices are traced.
 // ---------------------------------------------------------------------------------------
+template <bool WIDE>
 __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ scenes,
                                                 const ViewDev* __restrict__ views, int n_views, uint64_t total,
                                                 Rng rng, int M, unsigned long long* work, uint32_t chunk,
@@ -276,7 +277,7 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
             const bool need = has_path && !has_hit;
             if (!__any_sync(MR_FULL, need)) break;
             if (need) {
-                trace<false>(*sp, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk);
+                trace_as<false, WIDE>(*sp, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk);
                 if (h.tri >= 0) {
                     has_hit = true;
                 } else {
@@ -323,7 +324,7 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
         if (out.shadow) {
             ++n_shadow;
             Hit hs;
-            trace<true>(*sp, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk);
+            trace_as<true, WIDE>(*sp, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk);
             if (hs.tri < 0) {
                 rad = add_rn(rad, out.add_rad);
                 if (b >= 1) lind = add_rn(lind, out.add_lind);
@@ -373,14 +374,15 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
 }
 
 // launch-shape variants: the register cap of each (block size, resident blocks per SM)
-// pair is set by __launch_bounds__; the autotuner times them on the workload
-template <int BLOCK, int MINB>
+// pair is set by __launch_bounds__; the autotuner times them on the workload. WIDE: every
+// traversal through the 8-wide BVHs (one variant; the binary ones keep their register budget)
+template <int BLOCK, int MINB, bool WIDE = false>
 __global__ void __launch_bounds__(BLOCK, MINB)
     k_persistent(const SceneDev* __restrict__ scenes, const ViewDev* __restrict__ views, int n_views, uint64_t total,
                  Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape, int nvx,
                  unsigned long long* counters)
 {
-    persistent_body(scenes, views, n_views, total, rng, M, work, chunk, tape, nvx, counters);
+    persistent_body<WIDE>(scenes, views, n_views, total, rng, M, work, chunk, tape, nvx, counters);
 }
 
 // resolve every view of a batch in one launch: one thread per pixel over all views
@@ -1320,11 +1322,14 @@ int mr_persistent_occupancy_v(int v)
     return n < 1 ? 1 : n;
 }
 
+static const PersistentVariant kWideVariant = {128, 3, k_persistent<128, 3, true>};
+
 cudaError_t mr_launch_persistent_v(int v, const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total,
                                    Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
-                                   unsigned long long* counters, int blocks, cudaStream_t st, int nvx)
+                                   unsigned long long* counters, int blocks, cudaStream_t st, int nvx, bool wide)
 {
-    const PersistentVariant& pv = kVariants[v];
+    // (with wide BVHs the one wide variant runs; extra blocks find no work left and exit)
+    const PersistentVariant& pv = wide ? kWideVariant : kVariants[v];
     const size_t smem = stack_bytes(pv.block);
     cudaError_t e = cudaFuncSetAttribute(pv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1339,7 +1344,7 @@ cudaError_t mr_launch_persistent(const SceneDev* scenes, const ViewDev* views, i
 {
     const int v = mr_persistent_pick(block, 0);
     return mr_launch_persistent_v(v, scenes, views, n_views, total, rng, M, work, chunk, tape, counters, blocks, st,
-                                  nvx);
+                                  nvx, false);
 }
 
 int mr_persistent_occupancy(int block) { return mr_persistent_occupancy_v(mr_persistent_pick(block, 0)); }

@@ -74,9 +74,10 @@ int mr_persistent_variants();
 void mr_persistent_variant_shape(int v, int* block, int* minb);
 int mr_persistent_pick(int block, int per_sm);
 int mr_persistent_occupancy_v(int v);
+// wide: the scenes are traversed through their 8-wide BVHs (one kernel for every v)
 cudaError_t mr_launch_persistent_v(int v, const SceneDev* scenes, const ViewDev* views, int n_views, uint64_t total,
                                    Rng rng, int M, unsigned long long* work, uint32_t chunk, void* tape,
-                                   unsigned long long* counters, int blocks, cudaStream_t st, int nvx = 0);
+                                   unsigned long long* counters, int blocks, cudaStream_t st, int nvx, bool wide);
 void mr_launch_resolve_all(const ViewDev* views, int n_views, const uint64_t* pix_off, uint64_t total_pix,
                            float* const* images, const void* tape, uint64_t ntot, int sms, cudaStream_t st);
 // nvx = 0: PRIMARY-mode adjoint; nvx > 0: FULL mode over vertex records 1 .. nvx
