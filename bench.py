@@ -40,12 +40,12 @@ DEMOD_REPS = 5
 # DRAM bytes per unit of the three stage kernels (closest-hit ray, RIS candidate, shadow ray),
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the first render's
 # launches on config 3 reduced to 2 views, divided by that render's unit counts; the 1-view
-# capture gives per-unit figures within 8%, so traffic is taken to grow in proportion and is
+# capture gives per-unit figures within 2%, so traffic is taken to grow in proportion and is
 # scaled to the bench's launches by their unit counts. Valid only for the kernel sources they
 # were measured on (SHA-256 prefix of wave.cu, device.cuh, path.cuh, bvh.cu); otherwise null.
 TRAFFIC_SOURCES = ("wave.cu", "device.cuh", "path.cuh", "bvh.cu")
-TRAFFIC_SHA = "ce343adad802fa22"
-TRAFFIC_PER_UNIT = {"closest": 97.89, "shade": 11.63, "shadow": 150.74}
+TRAFFIC_SHA = "5c62f7ab5d4f313f"
+TRAFFIC_PER_UNIT = {"closest": 81.53, "shade": 9.93, "shadow": 124.87}
 
 
 def _traffic_valid():
