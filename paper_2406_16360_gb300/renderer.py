@@ -90,7 +90,10 @@ class GpuWorkload:
                grad_mode=0, reuse=(0, 0), temporal=0, temporal_cap=20, history=None, max_visits=0):
         """Forward render; grad_mode 1 (FULL) also records every vertex for the FULL adjoint;
         reuse = (neighbours, radius) turns on spatial reuse at the primary vertex; temporal = 1
-        records the reservoir history into `history`, 2 merges it first."""
+        records the reservoir history into `history`, 2 merges it first. Scenes whose vertices
+        or env were changed in place are refitted (and their env tables rebuilt) first."""
+        for s in self.scenes:
+            s.refresh()
         images = images if images is not None else self.new_images()
         tape = tape if tape is not None else self.new_tape(grad_mode)
         M.mirres_render(self.ctx, [s.handle for s in self.scenes], self.views,
