@@ -277,7 +277,10 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
             const bool need = has_path && !has_hit;
             if (!__any_sync(MR_FULL, need)) break;
             if (need) {
-                trace_as<false, WIDE>(*sp, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk);
+                if (WIDE)  // per scene: its 8-wide BVH, or the binary tree of a scene below two triangles
+                    trace<false>(*sp, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk);
+                else
+                    trace_as<false, false>(*sp, o, d, origin, tmin, __int_as_float(0x7f800000), h, mystk);
                 if (h.tri >= 0) {
                     has_hit = true;
                 } else {
@@ -324,7 +327,10 @@ __device__ __forceinline__ void persistent_body(const SceneDev* __restrict__ sce
         if (out.shadow) {
             ++n_shadow;
             Hit hs;
-            trace_as<true, WIDE>(*sp, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk);
+            if (WIDE)
+                trace<true>(*sp, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk);
+            else
+                trace_as<true, false>(*sp, out.sh_o, out.sh_d, h.tri, tmin, __int_as_float(0x7f800000), hs, mystk);
             if (hs.tri < 0) {
                 rad = add_rn(rad, out.add_rad);
                 if (b >= 1) lind = add_rn(lind, out.add_lind);

@@ -325,15 +325,24 @@ def _wide_workloads():
                                      tex=16)}
 
 
-def _defined_words_differ(a, b):
+def _defined_words_differ(a, b, rtol=0.0):
     """per sample: any tape word that both renders define differs (words 9-12 are defined where a
-    candidate was selected, 13-16 where L_ind != 0; the rest always)"""
-    fa, fb = a.view(np.float32), b.view(np.float32)
-    differ = np.any(a[:9] != b[:9], axis=0)
+    candidate was selected, 13-16 where L_ind != 0; the rest always). The integer words (hit
+    triangle, selected candidate, env texel) must be equal; with rtol > 0 the float words may
+    differ by that relative amount (kernels compiled apart may contract multiply-adds
+    differently), else they must be equal too."""
+    fa, fb = a.view(np.float32).astype(np.float64), b.view(np.float32).astype(np.float64)
+
+    def fdiff(rows):
+        if rtol == 0.0:
+            return np.any(a[rows] != b[rows], axis=0)
+        return np.any(np.abs(fa[rows] - fb[rows]) > rtol * np.maximum(np.abs(fa[rows]), np.abs(fb[rows])), axis=0)
+
+    differ = np.any(a[:2] != b[:2], axis=0) | fdiff(slice(2, 9))
     sel = (a[1].view(np.int32) >= 0) | (b[1].view(np.int32) >= 0)
-    differ |= sel & np.any(a[9:13] != b[9:13], axis=0)
+    differ |= sel & ((a[9] != b[9]) | fdiff(slice(10, 13)))
     ind = np.any(fa[3:6] != 0.0, axis=0) | np.any(fb[3:6] != 0.0, axis=0)
-    differ |= ind & np.any(a[13:17] != b[13:17], axis=0)
+    differ |= ind & fdiff(slice(13, 17))
     return differ
 
 
@@ -344,7 +353,9 @@ def test_wide_bvh_takes_the_binary_trees_hits(M, ctx, name, launch):
     collapsed from find the same closest hits: renders through either agree word for word on
     every sample, except samples with a grazing decision the oracle flags (a ray that touches a
     binary box within rounding may be culled by the binary tree's exact box, not by the wide
-    tree's wider one); also after the vertices moved and both trees were refitted"""
+    tree's wider one); also after the vertices moved and both trees were refitted. (The
+    persistent launch compiles its wide-BVH variant as a kernel of its own, whose shading may
+    round differently: there the float words agree to 1e-5, the decisions exactly.)"""
     from paper_2406_16360_gb300.renderer import GpuWorkload
     w = _wide_workloads()[name]
     gb = GpuWorkload(w, 0, ctx=ctx)
@@ -367,7 +378,7 @@ def test_wide_bvh_takes_the_binary_trees_hits(M, ctx, name, launch):
         torch.cuda.synchronize()
         a = tape_w.cpu().numpy().view(np.uint32).reshape(-1, n)[:17]
         b = tape_b.cpu().numpy().view(np.uint32).reshape(-1, n)[:17]
-        differ = _defined_words_differ(a, b)
+        differ = _defined_words_differ(a, b, rtol=1e-5 if launch == 2 else 0.0)
         if differ.any():
             margins = np.concatenate([O.render_samples(O.OracleScene(scenes[v.scene]), v, vi, w.ris_m, seed=w.seed)
                                       ["sample_margin"].reshape(-1) for vi, v in enumerate(w.views)])
