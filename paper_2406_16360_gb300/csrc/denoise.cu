@@ -42,9 +42,18 @@ __device__ __forceinline__ void store(float4* o4, float* o3, int64_t p, float x,
 // output pixels of one column spaced `step` rows apart (rows y0 + j step): their 5 x 5 footprints
 // overlap in all but the first and last rows, so the strip reads its (EAWT_R + 4) x 5 taps once
 // each and applies every tap to the outputs it falls on -- (EAWT_R + 4) 5 / EAWT_R tap reads per
-// output instead of 25. Consecutive threads take consecutive columns of the same rows (coalesced
+// output instead of 25 (15 for strips of two). Consecutive threads take consecutive columns of the same rows (coalesced
 // tap rows). Each output still sums its taps row by row, column by column.
-constexpr int EAWT_R = 4;
+// Measured on 20 views of config 3 (forward + adjoint, 3 levels): strips of 2 at 64 registers
+// (4 blocks per SM) 5.29 ms; 4 at 80 (3 blocks, spilling) 5.61; 4 at 128 (2 blocks) 5.59;
+// 2 at 2 blocks 6.18; 8 at 1 block 8.97.
+#ifndef MR_EAWT_R
+#define MR_EAWT_R 2  // outputs per strip
+#endif
+#ifndef MR_EAWT_MINB
+#define MR_EAWT_MINB 4  // resident 256-thread blocks per SM the register cap aims at
+#endif
+constexpr int EAWT_R = MR_EAWT_R;
 
 struct Strip {
     int img, x, y0;
@@ -68,7 +77,7 @@ __device__ __forceinline__ int64_t strips_per_image(int W, int H, int step)
 }
 
 // forward level: cin -> cout (packed, or [N][H][W][3] when out3 is given), and 1 / k
-__global__ void __launch_bounds__(256) k_eawt_level(const float4* __restrict__ cin, const float4* __restrict__ nrm,
+__global__ void __launch_bounds__(256, MR_EAWT_MINB) k_eawt_level(const float4* __restrict__ cin, const float4* __restrict__ nrm,
                                                     const float4* __restrict__ pos, int N, int W, int H, int step,
                                                     float inv_rt2, float inv_n2, float inv_x2, float4* __restrict__ cout,
                                                     float* __restrict__ out3, float* __restrict__ ikout)
@@ -126,7 +135,7 @@ __global__ void __launch_bounds__(256) k_eawt_level(const float4* __restrict__ c
 
 // adjoint level: gout(q) = sum over taps of h w(q, q + tap) gin(q + tap) / k(q + tap), the
 // weights recomputed from the level's recorded input c, 1 / k read from the record
-__global__ void __launch_bounds__(256) k_eawt_level_adjoint(const float4* __restrict__ gin, const float4* __restrict__ c,
+__global__ void __launch_bounds__(256, MR_EAWT_MINB) k_eawt_level_adjoint(const float4* __restrict__ gin, const float4* __restrict__ c,
                                                             const float* __restrict__ ikin, const float4* __restrict__ nrm,
                                                             const float4* __restrict__ pos, int N, int W, int H, int step,
                                                             float inv_rt2, float inv_n2, float inv_x2,

@@ -161,3 +161,29 @@ def test_temporal_reuse_argument_checks(M, ctx):
     assert M.mirres_reuse_history_bytes(gw.views) == 20 * w.samples
     for s in gw.scenes:
         s.close()
+
+
+def test_reuse_under_wave_chains_and_views_larger_than_a_wave(M, ctx):
+    """spatial + temporal reuse with the waves dealt to two concurrent chains and a wave size
+    below the largest view (the wave grows to hold it): the same images, tape and history as the
+    default launch shape"""
+    from tests.parity import compare_tapes
+    w = synth.config5(seed=9, n_scenes=3, max_tris=5000, res_choices=(96, 160), spp_choices=(3, 4), tex=16)
+    assert max(v.width * v.height * v.spp for v in w.views) > 1 << 16
+    gw = _gw(ctx, w)
+    out = []
+    for shape in (None, dict(wave_log2=16, block=[128] * 4, blocks_per_sm=[16] * 4, branches=2)):
+        M.mirres_set_wave_shape(ctx, shape)
+        hist = gw.new_history()
+        gw.render(launch=1, reuse=(4, 3), temporal=1, history=hist)
+        img, tape = gw.render(launch=1, seed=w.seed + 3, reuse=(4, 3), temporal=2, history=hist)
+        torch.cuda.synchronize()
+        out.append(([i.clone() for i in img], tape.cpu().numpy().copy(), hist.cpu().numpy().copy()))
+    M.mirres_set_wave_shape(ctx, None)
+    (ia, ta, ha), (ib, tb, hb) = out
+    compare_tapes(tb.view(np.uint32).reshape(M.TAPE_WORDS, -1), ta.view(np.uint32).reshape(M.TAPE_WORDS, -1), rtol=0)
+    assert np.array_equal(ha, hb)
+    for a, b in zip(ia, ib):
+        assert torch.equal(a, b)
+    for s in gw.scenes:
+        s.close()
