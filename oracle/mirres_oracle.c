@@ -1023,6 +1023,16 @@ static int taps_reach(const Taps* tp, double dfx, double dfy, int idx[16])
     return n;
 }
 
+int32_t orc_taps_reach(int32_t w, int32_t h, double su, double sv, double dfx, double dfy, int32_t* out)
+{
+    Taps tp;
+    taps_at(w, h, su, sv, &tp);
+    int idx[16];
+    int n = taps_reach(&tp, dfx, dfy, idx);
+    for (int k = 0; k < n; ++k) out[k] = idx[k];
+    return n;
+}
+
 typedef struct {
     int tri;
     double u, v, t;

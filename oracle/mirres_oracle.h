@@ -198,6 +198,10 @@ int32_t orc_env_texel(const orc_scene* s, const double dir[3]);
 /* streaming WRS over m candidates with weights gamma and accept uniforms u:
  * returns selected index (-1 none), writes w_sum */
 int32_t orc_wrs(const double* gamma, const double* u, int32_t m, double* w_sum);
+/* the texels of a w x h texture whose bilinear weight a lookup at texture coordinate (su, sv)
+ * computed with a fractional-position error up to (dfx, dfy) texels may change (test tolerance
+ * only): writes up to 16 indices, returns their count */
+int32_t orc_taps_reach(int32_t w, int32_t h, double su, double sv, double dfx, double dfy, int32_t* out);
 
 #ifdef __cplusplus
 }

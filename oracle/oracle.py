@@ -116,6 +116,8 @@ def lib():
             L.orc_env_texel.argtypes = [vp, vp]
             L.orc_wrs.restype = i32
             L.orc_wrs.argtypes = [vp, vp, i32, vp]
+            L.orc_taps_reach.restype = i32
+            L.orc_taps_reach.argtypes = [i32, i32, dbl, dbl, dbl, dbl, vp]
             _lib = L
     return _lib
 
@@ -440,6 +442,14 @@ def env_pdf(osc, d):
 
 def env_texel(osc, d):
     return lib().orc_env_texel(osc.h, _p(_f64(d)))
+
+
+def taps_reach(w, h, su, sv, dfx, dfy):
+    """texels whose bilinear weight an FP32 lookup at (su, sv) within (dfx, dfy) texels of its
+    fractional position may change (the texel-gradient sensitivity's support), as a sorted list"""
+    out = np.zeros(16, dtype=np.int32)
+    n = lib().orc_taps_reach(int(w), int(h), float(su), float(sv), float(dfx), float(dfy), _p(out))
+    return sorted(int(x) for x in out[:n])
 
 
 def wrs(gamma, u):
