@@ -737,7 +737,8 @@ def main():
     # roofline of the dominant stage kernel of the batched forward. All three are bound by FP32
     # arithmetic (their data is L2-resident, no tensor-core work); algorithmic FLOPs per unit:
     # shade (k_wshade): per RIS candidate 60 (BRDF luminance and cosine) + 2 log2(env texels)
-    # (the two CDF inversions); closest hit and shadow rays (k_wclosest, k_wshadow): 12 per box
+    # (the two CDF inversions); closest hit and shadow rays (k_wclosest / k_wclosest_refill,
+    # k_wshadow_refill): 12 per box
     # test (slab) + 27 per triangle test. Candidates and box / triangle tests are counted by the
     # library; times come from the stage events captured in the graph.
     env_texels = sum(s.env.shape[0] * s.env.shape[1] for s in w.scenes) / len(w.scenes)
@@ -748,7 +749,8 @@ def main():
     stage_flops = {"shade": cand_per_render * per_cand,
                    "closest": 12.0 * work[0] + 27.0 * work[1],
                    "shadow": 12.0 * work[2] + 27.0 * work[3]}
-    names = {"shade": "k_wshade (shade + RIS stage)", "closest": "k_wclosest (closest-hit stage)",
+    names = {"shade": "k_wshade (shade + RIS stage)",
+             "closest": "k_wclosest + k_wclosest_refill (closest-hit stage: primary, then continuation rays)",
              "shadow": "k_wshadow (shadow-ray stage)"}
     units_per_render = {"closest": (cnt_b[0] + cnt_b[1]) / args.steps, "shade": cand_per_render,
                         "shadow": cnt_b[2] / args.steps}

@@ -568,7 +568,7 @@ __device__ __forceinline__ long long refill(RefillPool& rp, bool has, unsigned i
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(256) k_wclosest_refill(const SceneDev* __restrict__ scenes,
+__global__ void __launch_bounds__(256, MR_CLOSEST_REFILL_MINB) k_wclosest_refill(const SceneDev* __restrict__ scenes,
                                                          const ViewDev* __restrict__ views, QueueDev q,
                                                          const unsigned int* count, QueueDev hq,
                                                          unsigned int* count_hit, unsigned int* fetch,
