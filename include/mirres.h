@@ -338,8 +338,10 @@ mirres_status mirres_get_wave_shape(mirres_context* ctx, mirres_wave_shape* out)
  * every stage, for each of a set of (threads per block, blocks per SM) pairs applied to all
  * stages at once; keeps the fastest pair per stage, then times the wave sizes 2^23, 2^24 and
  * 2^25 (those the budget fills) with the chosen stage shapes and keeps the fastest forward,
- * then two chains of waves (branches = 2) at the chosen wave size and at half of it, where the
- * tuned views fill two waves, kept if faster still.
+ * then two and three chains of waves (branches = 2, 3) at the chosen wave size and at half of
+ * it, where the tuned views fill as many waves as chains, kept if faster still. Each shape is
+ * rendered once to capture its graph, then timed (the fastest of two renders for the wave sizes
+ * and chains).
  * The result becomes the context's shape (mirres_set_wave_shape) and is written to *out, the
  * tuned forward's time to *out_ms. The tape must hold these views (it is overwritten); the
  * renders write temporary images (allocated and freed here). params as for mirres_render

@@ -959,16 +959,23 @@ extern "C" mirres_status mirres_autotune_wave(mirres_context* ctx, mirres_scene*
     const mirres_wave_shape keep = ctx->wave_shape;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     mirres_status status = MIRRES_OK;
-    auto run = [&](const mirres_wave_shape& w, double stage_ms[4], float* total_ms) -> mirres_status {
+    // one render that captures the graph and warms caches and clocks, then `timed` renders of
+    // which the fastest counts (the stage times are those of the last)
+    auto run = [&](const mirres_wave_shape& w, double stage_ms[4], float* total_ms, int timed) -> mirres_status {
         ctx->wave_shape = w;
-        for (int rep = 0; rep < 2; ++rep) {  // the first replay captures the graph and warms caches and clocks
+        *total_ms = 1e30f;
+        for (int rep = 0; rep <= timed; ++rep) {
             MR_CUDA(cudaEventRecord(e0, st));
             MR_TRY(render_wave(ctx, sdev, vdev, sub_total, imgs.data(), tape, params->ris_m, rng, 1, nvx, 0, 1, 0, 1,
                                nullptr, st));
             MR_CUDA(cudaEventRecord(e1, st));
+            if (rep > 0) {
+                float ms = 0.0f;
+                MR_CUDA(cudaEventSynchronize(e1));
+                MR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                *total_ms = std::min(*total_ms, ms);
+            }
         }
-        MR_CUDA(cudaEventSynchronize(e1));
-        MR_CUDA(cudaEventElapsedTime(total_ms, e0, e1));
         return stage_sums(ctx, stage_ms);
     };
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -992,7 +999,7 @@ extern "C" mirres_status mirres_autotune_wave(mirres_context* ctx, mirres_scene*
         }
         double ms[4];
         float tot = 0.0f;
-        status = run(w, ms, &tot);
+        status = run(w, ms, &tot, 1);
         if (status != MIRRES_OK) break;
         for (int k = 0; k < 4; ++k) {
             if (ms[k] < best_stage[k]) {
@@ -1009,28 +1016,30 @@ extern "C" mirres_status mirres_autotune_wave(mirres_context* ctx, mirres_scene*
         w.wave_log2 = wl;
         double ms[4];
         float tot = 0.0f;
-        status = run(w, ms, &tot);
+        status = run(w, ms, &tot, 2);
         if (status == MIRRES_OK && tot < best_ms) {
             best_ms = tot;
             best_wave = wl;
         }
     }
     best.wave_log2 = best_wave;
-    // then two concurrent chains of waves, at the chosen wave size and at half of it (only where
-    // the tuned views fill at least two waves)
+    // then two and three concurrent chains of waves, at the chosen wave size and at half of it
+    // (only where the tuned views fill at least as many waves as chains)
     const int one_chain_wave = best_wave;
-    for (int wl = one_chain_wave - 1; wl <= one_chain_wave && status == MIRRES_OK; ++wl) {
-        if (wl < 23 || (1ull << wl) >= sub_total) continue;
-        mirres_wave_shape w = best;
-        w.wave_log2 = wl;
-        w.branches = 2;
-        double ms[4];
-        float tot = 0.0f;
-        status = run(w, ms, &tot);
-        if (status == MIRRES_OK && tot < best_ms) {
-            best_ms = tot;
-            best.wave_log2 = wl;
-            best.branches = 2;
+    for (int nb = 2; nb <= 3 && status == MIRRES_OK; ++nb) {
+        for (int wl = one_chain_wave - 1; wl <= one_chain_wave && status == MIRRES_OK; ++wl) {
+            if (wl < 23 || ((uint64_t)(nb - 1) << wl) >= sub_total) continue;
+            mirres_wave_shape w = best;
+            w.wave_log2 = wl;
+            w.branches = nb;
+            double ms[4];
+            float tot = 0.0f;
+            status = run(w, ms, &tot, 2);
+            if (status == MIRRES_OK && tot < best_ms) {
+                best_ms = tot;
+                best.wave_log2 = wl;
+                best.branches = nb;
+            }
         }
     }
     if (e0) cudaEventDestroy(e0);
