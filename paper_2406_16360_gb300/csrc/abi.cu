@@ -39,7 +39,7 @@ static const size_t kQueueCnt = 1024;
 SceneDev mr_scene_dev(const mirres_scene* s)
 {
     SceneDev d;
-    d.nodes = s->nodes;
+    d.nodes = MR_DFS_NODES ? s->dnodes : s->nodes;
     d.ptri = s->ptri;
     d.leaf_of = s->leaf_of;
     d.tris = s->desc.tris;

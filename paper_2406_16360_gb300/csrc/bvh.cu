@@ -362,6 +362,47 @@ __global__ void k_bottom_up(const float* __restrict__ verts, const int32_t* __re
     }
 }
 
+// ---- depth-first traversal layout -------------------------------------------------------------
+// The traversal reads the internal nodes in depth-first preorder, left child first: a node's
+// left child is the next node in memory, so a ray that descends left reads the 64 bytes after
+// the ones it just read, and every subtree is one contiguous block. Preorder position of a node:
+// its parent's plus 1 when it is the left child, plus 1 + (internal nodes of the left sibling's
+// subtree) = the left sibling's leaf count (1 for a leaf) when it is the right child; each
+// thread sums these up its path to the root. The boxes are copied unchanged, the children's
+// node ids mapped to their positions (leaf children keep their leaf positions).
+__global__ void k_dfs_index(const int32_t* __restrict__ parent, const int32_t* __restrict__ left,
+                            const int2* __restrict__ range, int F, int32_t* __restrict__ dfs)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= F - 1) return;
+    int idx = 0, c = n;
+    for (int depth = 0; c != 0 && depth < 2 * F; ++depth) {  // every kept tree is at most 64 deep
+        const int p = parent[c];
+        if (p < 0) break;
+        const int l = left[p];
+        idx += (l == c) ? 1 : (l >= 0 ? range[l].y : 1);
+        c = p;
+    }
+    dfs[n] = idx;
+}
+
+__global__ void k_dfs_gather(const float4* __restrict__ nodes, const int32_t* __restrict__ dfs, int F,
+                             float4* __restrict__ dnodes)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= F - 1) return;
+    const int q = dfs[n];
+    if (q < 0 || q >= F - 1) return;  // (not for a well-formed tree: its positions are a permutation)
+    dnodes[4 * (size_t)q] = nodes[4 * (size_t)n];
+    dnodes[4 * (size_t)q + 1] = nodes[4 * (size_t)n + 1];
+    dnodes[4 * (size_t)q + 2] = nodes[4 * (size_t)n + 2];
+    const float4 ch = nodes[4 * (size_t)n + 3];
+    int cl = __float_as_int(ch.x), cr = __float_as_int(ch.y);
+    if (cl >= 0) cl = dfs[cl];
+    if (cr >= 0) cr = dfs[cr];
+    dnodes[4 * (size_t)q + 3] = make_float4(__int_as_float(cl), __int_as_float(cr), 0.0f, 0.0f);
+}
+
 // ---- PLOC hierarchy: parallel locally-ordered clustering (Meister and Bittner 2018) ------
 // The clusters start as the leaves in Morton order. In every iteration each cluster finds,
 // among the PLOC_R clusters on either side of it, the one whose union box has the smallest
@@ -705,6 +746,8 @@ mirres_status mr_bvh_alloc(mirres_scene* s)
     MR_TRY(mr_alloc(&s->hi, 3 * (F > 0 ? 2 * F - 1 : 1)));
     MR_TRY(mr_alloc(&s->flags, F > 1 ? F - 1 : 1));
     MR_TRY(mr_alloc(&s->nodes, 4 * (F > 1 ? F - 1 : 1)));
+    MR_TRY(mr_alloc(&s->dnodes, 4 * (F > 1 ? F - 1 : 1)));
+    MR_TRY(mr_alloc(&s->dfs, F > 1 ? F - 1 : 1));
     MR_TRY(mr_alloc(&s->ptri, 3 * F));
     MR_TRY(mr_alloc(&s->leaf_of, F));
     MR_TRY(mr_alloc(&s->range, F > 1 ? F - 1 : 1));
@@ -725,7 +768,7 @@ void mr_bvh_free(mirres_scene* s)
     void* ptrs[] = {s->keys, s->perm, s->left, s->right, s->parent, s->lo, s->hi, s->flags, s->nodes, s->ptri,
                     s->leaf_of, s->cent, s->codes[0], s->codes[1], s->vals[0], s->vals[1], s->hist, s->bounds,
                     s->tmin, s->bad, s->ploc_box, s->ploc_node, s->ploc_nn, s->ploc_part, s->ploc_state,
-                    s->vacc, s->vnrm, s->gvn, s->range};
+                    s->vacc, s->vnrm, s->gvn, s->range, s->dnodes, s->dfs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     mr_wide_free(s);
@@ -739,6 +782,10 @@ static mirres_status bottom_up(mirres_scene* s, cudaStream_t st)
     k_bottom_up<<<grid_for(F, 256), 256, 0, st>>>(s->desc.verts, s->desc.tris, F, s->desc.n_verts, s->perm, s->left,
                                                  s->right, s->parent, s->lo, s->hi, s->flags, s->nodes, s->ptri,
                                                  s->leaf_of, s->range);
+    if (F > 1) {
+        k_dfs_index<<<grid_for(F - 1, 256), 256, 0, st>>>(s->parent, s->left, s->range, F, s->dfs);
+        k_dfs_gather<<<grid_for(F - 1, 256), 256, 0, st>>>(s->nodes, s->dfs, F, s->dnodes);
+    }
     MR_CUDA(cudaGetLastError());
     return MIRRES_OK;
 }

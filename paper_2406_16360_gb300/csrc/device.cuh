@@ -34,6 +34,9 @@
 #ifndef MR_REFILL_CLOSEST
 #define MR_REFILL_CLOSEST 1  // ... and continuation rays (at 64 registers: 6-8% faster than k_wclosest)
 #endif
+#ifndef MR_DFS_NODES
+#define MR_DFS_NODES 1  // traversal nodes in depth-first preorder (else the builders' order)
+#endif
 #ifndef MR_CLOSEST_REFILL_MINB
 #define MR_CLOSEST_REFILL_MINB 4  // its register cap: four 256-thread blocks per SM (64 registers)
 #endif

@@ -68,7 +68,9 @@ struct mirres_scene {
     float* lo = nullptr;             // [2F-1][3]
     float* hi = nullptr;             // [2F-1][3]
     int32_t* flags = nullptr;        // [F-1] bottom-up arrival counters
-    float4* nodes = nullptr;         // [F-1][4]
+    float4* nodes = nullptr;         // [F-1][4] by internal node id (the builders' layout)
+    float4* dnodes = nullptr;        // [F-1][4] the same nodes in depth-first preorder (traversal)
+    int32_t* dfs = nullptr;          // [F-1] internal node id -> its position in dnodes
     float4* ptri = nullptr;          // [F][3]
     int32_t* leaf_of = nullptr;      // [F]
     int2* range = nullptr;           // [F-1] (first leaf position, leaf count) under each internal node
