@@ -44,8 +44,8 @@ DEMOD_REPS = 5
 # scaled to the bench's launches by their unit counts. Valid only for the kernel sources they
 # were measured on (SHA-256 prefix of wave.cu, device.cuh, path.cuh, bvh.cu); otherwise null.
 TRAFFIC_SOURCES = ("wave.cu", "device.cuh", "path.cuh", "bvh.cu")
-TRAFFIC_SHA = "4d77a3a45e290138"
-TRAFFIC_PER_UNIT = {"closest": 81.58, "shade": 9.91, "shadow": 124.74}
+TRAFFIC_SHA = "9650bc697458471b"
+TRAFFIC_PER_UNIT = {"closest": 81.75, "shade": 9.86, "shadow": 124.96}
 
 
 def _traffic_valid():
