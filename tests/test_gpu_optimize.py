@@ -165,9 +165,11 @@ def test_config4_stated_size_and_oracle_driven_loop(M, ctx):
     out["64_gpu_eval"], out["64_oracle_eval"] = [ev0, gpu.eval_loss()], [ev0, ora.eval_loss()]
     gpu.close()
     ora.close()
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open("gpurun_out/config4_curves.json", "w") as f:
-        json.dump(out, f)
+    path = os.environ.get("MIRRES_CURVES_OUT")  # optional JSON file for the loss curves
+    if path:
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(out, f)
     a800, ag, ao = (np.array(out[k]) for k in ("800", "64_gpu", "64_oracle"))
     print("config4 800x800: first", a800[:3], "last", a800[-3:], "eval", out["800_eval"],
           "seconds", out["800_seconds"])
