@@ -513,6 +513,16 @@ def test_stage_trace_lists_every_stage_launch(M, ctx):
         s.close()
 
 
+def test_stage_times_need_an_event_recording_render(M):
+    """a context that has not rendered with flags bit 0 has no stage events to report"""
+    c = M.mirres_context_create(0)
+    with pytest.raises(M.MirresError):
+        M.mirres_stage_times(c)
+    with pytest.raises(M.MirresError):
+        M.mirres_stage_trace(c)
+    c.close()
+
+
 # ---------------------------------------------------------------------------------------
 # FULL-mode adjoint (the gradients of the indirect rays at every vertex)
 # ---------------------------------------------------------------------------------------
