@@ -317,7 +317,10 @@ mirres_status mirres_set_launch(mirres_context* ctx, int32_t block, int32_t bloc
  * -- samples per wave, which is the capacity of every ray queue -- and, per stage kernel
  * (index = stage: 0 closest hit, 1 shade + RIS (and the reuse kernels), 2 shadow rays, 3 ray
  * generation), the threads per block and the grid of its grid-stride loop in blocks per SM.
- * Default: 2^25 samples, 256 threads and 8 blocks per SM for every stage. */
+ * The lane-refilling kernels that trace continuation rays (bounces >= 1) and shadow rays run
+ * 256 threads in one resident wave of blocks whatever the shape; the shape sets the primary
+ * rays' closest-hit kernel, shading and ray generation (and shadow rays on 8-wide BVHs).
+ * Default: 2^25 samples, 256 threads and 8 blocks per SM for every stage, one chain. */
 typedef struct {
     int32_t wave_log2;        /* samples per wave = 2^wave_log2, in [16, 28] */
     int32_t block[4];         /* 64, 128 or 256 */
