@@ -323,9 +323,11 @@ __global__ void k_bottom_up(const float* __restrict__ verts, const int32_t* __re
     hi[3 * L] = fmaxf(fmaxf(a.x, b.x), c.x);
     hi[3 * L + 1] = fmaxf(fmaxf(a.y, b.y), c.y);
     hi[3 * L + 2] = fmaxf(fmaxf(a.z, b.z), c.z);
-    ptri[3 * (size_t)j] = make_float4(a.x, a.y, a.z, __int_as_float(t));
-    ptri[3 * (size_t)j + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, 0.0f);
-    ptri[3 * (size_t)j + 2] = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, 0.0f);
+    float4* pt = ptri + MR_TRI_STRIDE * (size_t)j;
+    pt[0] = make_float4(a.x, a.y, a.z, __int_as_float(t));
+    pt[1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, 0.0f);
+    pt[2] = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, 0.0f);
+    if (MR_TRI_STRIDE == 4) pt[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     leaf_of[t] = j;
     int p = parent[L];
     while (p >= 0) {
@@ -748,7 +750,7 @@ mirres_status mr_bvh_alloc(mirres_scene* s)
     MR_TRY(mr_alloc(&s->nodes, 4 * (F > 1 ? F - 1 : 1)));
     MR_TRY(mr_alloc(&s->dnodes, 4 * (F > 1 ? F - 1 : 1)));
     MR_TRY(mr_alloc(&s->dfs, F > 1 ? F - 1 : 1));
-    MR_TRY(mr_alloc(&s->ptri, 3 * F));
+    MR_TRY(mr_alloc(&s->ptri, MR_TRI_STRIDE * F));
     MR_TRY(mr_alloc(&s->leaf_of, F));
     MR_TRY(mr_alloc(&s->range, F > 1 ? F - 1 : 1));
     MR_TRY(mr_alloc(&s->cent, 3 * F));

@@ -37,6 +37,13 @@
 #ifndef MR_DFS_NODES
 #define MR_DFS_NODES 1  // traversal nodes in depth-first preorder (else the builders' order)
 #endif
+#ifndef MR_NODE_LD256
+#define MR_NODE_LD256 1  // traversal nodes read with two 256-bit loads (2.5% faster traversal stages)
+#endif
+#ifndef MR_TRI_LD256
+#define MR_TRI_LD256 0  // packed triangles padded to 64 bytes and read with two 256-bit loads
+#endif
+#define MR_TRI_STRIDE (MR_TRI_LD256 ? 4 : 3)  // float4 per packed triangle
 #ifndef MR_CLOSEST_REFILL_MINB
 #define MR_CLOSEST_REFILL_MINB 4  // its register cap: four 256-thread blocks per SM (64 registers)
 #endif
@@ -549,9 +556,18 @@ __device__ __forceinline__ bool tri_solve(float3 o, float3 d, float3 v0, float3 
 
 __device__ __forceinline__ void load_tri(const SceneDev& s, int leaf, float3& v0, float3& e1, float3& e2, int& tri)
 {
-    const float4 a = __ldg(s.ptri + 3 * (size_t)leaf);
-    const float4 b = __ldg(s.ptri + 3 * (size_t)leaf + 1);
-    const float4 c = __ldg(s.ptri + 3 * (size_t)leaf + 2);
+    const float4* p = s.ptri + MR_TRI_STRIDE * (size_t)leaf;
+#if MR_TRI_LD256
+    float4 a, b, c, pad;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w), "=f"(pad.x), "=f"(pad.y), "=f"(pad.z), "=f"(pad.w)
+        : "l"(p + 2));
+#else
+    const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+#endif
     v0 = xyz(a);
     tri = __float_as_int(a.w);
     e1 = xyz(b);
@@ -597,6 +613,27 @@ __device__ __forceinline__ float slab(float3 lo, float3 hi, float3 oi, float3 in
     return (tn <= tf * 1.0000005f + 1e-30f) ? tn : __int_as_float(0x7fffffff);
 }
 
+// One traversal node (64 bytes, 64-byte aligned): the two child boxes and the child codes. With
+// MR_NODE_LD256 as two 32-byte loads (ld.global.nc.v8.f32, sm_100 and later) instead of four.
+__device__ __forceinline__ void load_node(const float4* p, float4& n0, float4& n1, float4& n2, int2& ch)
+{
+#if MR_NODE_LD256
+    float4 n3;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(n0.x), "=f"(n0.y), "=f"(n0.z), "=f"(n0.w), "=f"(n1.x), "=f"(n1.y), "=f"(n1.z), "=f"(n1.w)
+        : "l"(p));
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(n2.x), "=f"(n2.y), "=f"(n2.z), "=f"(n2.w), "=f"(n3.x), "=f"(n3.y), "=f"(n3.z), "=f"(n3.w)
+        : "l"(p + 2));
+    ch = make_int2(__float_as_int(n3.x), __float_as_int(n3.y));
+#else
+    n0 = __ldg(p);
+    n1 = __ldg(p + 1);
+    n2 = __ldg(p + 2);
+    ch = *reinterpret_cast<const int2*>(p + 3);
+#endif
+}
+
 // Closest (any = false) or any hit with t in (tmin, tmax). `sstk` = this thread's shared
 // stack column (stride `sstride`). Returns the number of nodes visited (two box tests each),
 // or -1 if the iteration cap was reached or the stack overflowed (a malformed tree: the ray
@@ -629,10 +666,9 @@ __device__ __forceinline__ int traverse(const SceneDev& s, float3 o, float3 d, i
             trav_fail(s);
             return -1;
         }
-        const float4 n0 = __ldg(s.nodes + 4 * (size_t)node);
-        const float4 n1 = __ldg(s.nodes + 4 * (size_t)node + 1);
-        const float4 n2 = __ldg(s.nodes + 4 * (size_t)node + 2);
-        const int2 ch = *reinterpret_cast<const int2*>(&s.nodes[4 * (size_t)node + 3]);
+        float4 n0, n1, n2;
+        int2 ch;
+        load_node(s.nodes + 4 * (size_t)node, n0, n1, n2, ch);
         const float tl = slab(f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), oi, inv, tmin, best.t);
         const float tr = slab(f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), oi, inv, tmin, best.t);
         bool gl = tl <= best.t, gr = tr <= best.t;
@@ -903,10 +939,9 @@ __device__ __forceinline__ bool trav_run(const SceneDev& s, Trav& T, uint32_t* s
             return true;
         }
         const int node = T.node;
-        const float4 n0 = __ldg(s.nodes + 4 * (size_t)node);
-        const float4 n1 = __ldg(s.nodes + 4 * (size_t)node + 1);
-        const float4 n2 = __ldg(s.nodes + 4 * (size_t)node + 2);
-        const int2 ch = *reinterpret_cast<const int2*>(&s.nodes[4 * (size_t)node + 3]);
+        float4 n0, n1, n2;
+        int2 ch;
+        load_node(s.nodes + 4 * (size_t)node, n0, n1, n2, ch);
         const float tl = slab(f3(n0.x, n0.y, n0.z), f3(n0.w, n1.x, n1.y), T.oi, T.inv, T.tmin, T.best.t);
         const float tr = slab(f3(n1.z, n1.w, n2.x), f3(n2.y, n2.z, n2.w), T.oi, T.inv, T.tmin, T.best.t);
         bool gl = tl <= T.best.t, gr = tr <= T.best.t;

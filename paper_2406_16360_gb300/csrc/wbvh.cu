@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kBlock) k_wide_level(const int32_t* __restrict
                 }
                 m = ((uint32_t)nl << 5) | (uint32_t)offset;
                 for (int t = 0; t < nl; ++t) {
-                    const size_t src = 3 * (size_t)leaf[t], dst = 3 * ((size_t)tri_base + offset + t);
+                    const size_t src = MR_TRI_STRIDE * (size_t)leaf[t], dst = 3 * ((size_t)tri_base + offset + t);
                     wtri[dst] = ptri[src];
                     wtri[dst + 1] = ptri[src + 1];
                     wtri[dst + 2] = ptri[src + 2];
