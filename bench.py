@@ -44,8 +44,8 @@ DEMOD_REPS = 5
 # scaled to the bench's launches by their unit counts. Valid only for the kernel sources they
 # were measured on (SHA-256 prefix of wave.cu, device.cuh, path.cuh, bvh.cu); otherwise null.
 TRAFFIC_SOURCES = ("wave.cu", "device.cuh", "path.cuh", "bvh.cu")
-TRAFFIC_SHA = "9650bc697458471b"
-TRAFFIC_PER_UNIT = {"closest": 81.75, "shade": 9.86, "shadow": 124.96}
+TRAFFIC_SHA = "3c1678626260466e"
+TRAFFIC_PER_UNIT = {"closest": 81.70, "shade": 9.85, "shadow": 125.09}
 
 
 def _traffic_valid():
