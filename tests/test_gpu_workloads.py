@@ -272,6 +272,43 @@ def test_config3_full_size_sampled(M, ctx):
         s.close()
 
 
+def test_config5_full_size_sampled(M, ctx):
+    """config 5 at full size (64 scenes, 1k-1M triangles each, 9.5 M in all, views of 128-1024
+    squared pixels with 4-32 spp and 2-5 bounces, one batched launch): 1024 pixels (all of
+    smaller views) on six views sample by sample -- the scene with the most triangles, the
+    largest view and four drawn at random -- and the adjoint of 768 pixels of one of them"""
+    w = synth.config5()
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1)
+    torch.cuda.synchronize()
+    osc_cache = {}
+
+    def osc_of(si):
+        if si not in osc_cache:
+            osc_cache[si] = O.OracleScene(w.scenes[si])
+        return osc_cache[si]
+
+    rng = np.random.Generator(np.random.PCG64(13))
+    biggest = int(np.argmax([s.n_tris for s in w.scenes]))
+    largest = int(np.argmax([v.width * v.height * v.spp for v in w.views]))
+    chosen = {biggest, largest}
+    while len(chosen) < 6:
+        chosen.add(int(rng.integers(0, len(w.views))))
+    picks = {}
+    for vi in sorted(chosen):
+        npx = w.views[vi].width * w.views[vi].height
+        picks[vi] = np.sort(rng.choice(npx, size=min(1024, npx), replace=False)).astype(np.int32)
+    _sample_parity(images, tape, w, osc_of, sorted(picks), picks.get)
+    vi = largest
+    npx = w.views[vi].width * w.views[vi].height
+    seeded = _seeded_adjoint(gw, w, tape, osc_of(w.views[vi].scene), vi,
+                             np.sort(rng.choice(npx, size=768, replace=False)).astype(np.int32), seed=14)
+    print("adjoint pixels seeded (unflagged):", seeded)
+    assert seeded >= 256
+    for s in gw.scenes:
+        s.close()
+
+
 def test_config2_full_size(M, ctx):
     """config 2 at its stated size (49,956 triangles, 4 views at 256x256, 512x512 textures, 8 spp,
     3 bounces, M = 32): every sample of every pixel, and the adjoint of all pixels of two views"""
