@@ -272,6 +272,19 @@ def test_config3_full_size_sampled(M, ctx):
         s.close()
 
 
+def test_config3_full_adjoint_at_full_view_size(M, ctx):
+    """the FULL-mode adjoint (every vertex of every path) at config 3's per-view size (499,036
+    triangles, 800x800, 16 spp, 4 bounces, M = 32; four of its views, a 7.2 GB tape): 384 seeded
+    pixels per view against the oracle's FULL adjoint"""
+    w = synth.config3(n_views=4)
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1, grad_mode=1)
+    torch.cuda.synchronize()
+    _grad_parity(gw, w, tape, pixels_per_view=384, grad_mode=1)
+    for s in gw.scenes:
+        s.close()
+
+
 def test_config5_full_size_sampled(M, ctx):
     """config 5 at full size (64 scenes, 1k-1M triangles each, 9.5 M in all, views of 128-1024
     squared pixels with 4-32 spp and 2-5 bounces, one batched launch): 1024 pixels (all of
