@@ -233,10 +233,11 @@ def sample_record(osc, view, index, ris_m, pixel, sample, seed=0):
                 y=out[10:13], wc=out[13:16], p_ind=out[16], vertices=out[18:18 + 12 * nv].reshape(nv, 12))
 
 
-def render_samples(osc, view, index, ris_m, seed=0, pixels=None, threads=None):
+def render_samples(osc, view, index, ris_m, seed=0, pixels=None, threads=None, reuse=(0, 0)):
     """Render pixels of one view with every sample's own radiance, decision margin and FP32
     sensitivity: dict(rgb [n,3], margin [n], sample_rgb [n,spp,3], sample_margin [n,spp],
-    sample_sens [n,spp], sens [n] = the mean of the samples')."""
+    sample_sens [n,spp], sens [n] = the mean of the samples'). reuse = (neighbours, radius) as
+    for render (spatial reuse at the primary vertex)."""
     L = lib()
     n = view.width * view.height if pixels is None else len(pixels)
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int32)
@@ -247,7 +248,7 @@ def render_samples(osc, view, index, ris_m, seed=0, pixels=None, threads=None):
     sse = np.zeros((n, view.spp))
     cnt = np.zeros(8, dtype=np.int64)
     v = make_view(view, index)
-    p = make_params(ris_m, seed, threads, 0, 1)
+    p = make_params(ris_m, seed, threads, 0, 1, reuse=reuse)
     if L.orc_render_samples(osc.h, C.byref(v), C.byref(p), _p(pix), n, _p(rgb), _p(mg), _p(srgb), _p(smg), _p(sse),
                             _p(cnt)):
         raise ValueError("orc_render_samples rejected its arguments")

@@ -184,7 +184,7 @@ def _tape_sample_rgb(tape, n_total, gids):
     return out.astype(np.float64)
 
 
-def _sample_parity(images, tape, w, osc_of, views, pixels_of):
+def _sample_parity(images, tape, w, osc_of, views, pixels_of, reuse=(0, 0), max_flagged=MAX_FLAGGED_SAMPLES):
     """per view: every sample of the chosen pixels against the oracle (unflagged samples within
     1e-4 of the sample's largest channel), the unflagged pixels' means within 1e-4; returns the
     oracle renders and the flagged counts"""
@@ -193,7 +193,7 @@ def _sample_parity(images, tape, w, osc_of, views, pixels_of):
     for vi in views:
         v = w.views[vi]
         pix = pixels_of(vi)
-        q = O.render_samples(osc_of(v.scene), v, vi, w.ris_m, seed=w.seed, pixels=pix)
+        q = O.render_samples(osc_of(v.scene), v, vi, w.ris_m, seed=w.seed, pixels=pix, reuse=reuse)
         npx = len(pix) if pix is not None else v.width * v.height
         pid = np.arange(npx) if pix is None else pix.astype(np.int64)
         first = sum(u.width * u.height * u.spp for u in w.views[:vi])  # the view's first sample
@@ -228,7 +228,7 @@ def _sample_parity(images, tape, w, osc_of, views, pixels_of):
         out[vi] = q
     frac = flagged / max(n_smp, 1)
     print(f"samples compared {n_smp}, flagged {flagged} ({100 * frac:.2f}%)")
-    assert frac <= MAX_FLAGGED_SAMPLES, (flagged, n_smp)
+    assert frac <= max_flagged, (flagged, n_smp)
     return out
 
 
@@ -281,6 +281,25 @@ def test_config3_full_adjoint_at_full_view_size(M, ctx):
     images, tape = gw.render(launch=1, grad_mode=1)
     torch.cuda.synchronize()
     _grad_parity(gw, w, tape, pixels_per_view=384, grad_mode=1)
+    for s in gw.scenes:
+        s.close()
+
+
+def test_config3_spatial_reuse_at_full_view_size(M, ctx):
+    """spatial reuse as the benchmark runs it (4 neighbours within radius 8) at config 3's
+    per-view size (499,036 triangles, 800x800, 16 spp, 4 bounces; two views): 1024 pixels per
+    view sample by sample against the oracle's reuse. A reused sample carries the decisions of
+    five reservoirs (its own and four neighbours', each with its candidates' accepts and the
+    neighbour's primary hit), so up to 15% of samples may sit within a margin, as in the
+    smaller reuse tests; every other sample is held to the usual bound."""
+    w = synth.config3(n_views=2)
+    gw = _gw(ctx, w)
+    images, tape = gw.render(launch=1, reuse=(4, 8))
+    torch.cuda.synchronize()
+    osc = O.OracleScene(w.scenes[0])
+    rng = np.random.Generator(np.random.PCG64(15))
+    picks = {vi: np.sort(rng.choice(640000, size=1024, replace=False)).astype(np.int32) for vi in (0, 1)}
+    _sample_parity(images, tape, w, lambda si: osc, (0, 1), picks.get, reuse=(4, 8), max_flagged=0.15)
     for s in gw.scenes:
         s.close()
 
