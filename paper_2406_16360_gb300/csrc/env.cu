@@ -8,7 +8,7 @@
 // so the search needs no FP64 arithmetic. The texel table packs (r, g, b, P * W * H).
 // The draw inverts the CDF over all texels in row-major order, (rows before + texels before in
 // the row) / total, as 53-bit thresholds ceil(cdf * 2^53) for a 53-bit uniform made of two
-// random words, through a guide with about two buckets per texel: one short search instead of
+// random words, through a guide with about eight buckets per texel: one short search instead of
 // a row search followed by a column search.
 #include "internal.h"
 
@@ -177,15 +177,22 @@ static void guide_shape(int n, int& g, int& shift)
     shift = 24 - lg;
 }
 
+// guide buckets per texel of the flat CDF: with 8 only ~12% of the draws on config 3's env land
+// in a bucket that holds a CDF boundary (and so read a threshold), against ~36% with 2; the
+// shade stage measured 85.3 / 82.1 / 80.0 / 81.5 / 85.8 ms per 20-view render at 2 / 4 / 8 / 16 / 32
+#ifndef MR_GUIDE_PER_TEXEL
+#define MR_GUIDE_PER_TEXEL 8
+#endif
+
 mirres_status mr_env_alloc(mirres_scene* s)
 {
     const size_t W = (size_t)s->desc.env_w, H = (size_t)s->desc.env_h;
     guide_shape((int)H, s->gm, s->gm_shift);
     guide_shape((int)W, s->gc, s->gc_shift);
     {
-        // about two guide buckets per texel over the 53-bit uniform
+        // about MR_GUIDE_PER_TEXEL guide buckets per texel over the 53-bit uniform
         int lg = 1;
-        while (((size_t)1 << lg) < 2 * W * H && lg < 30) ++lg;
+        while (((size_t)1 << lg) < (size_t)MR_GUIDE_PER_TEXEL * W * H && lg < 30) ++lg;
         s->gf = 1 << lg;
         s->gf_shift = 53 - lg;
     }
