@@ -42,10 +42,11 @@ DEMOD_REPS = 5
 # launches on config 3 reduced to 2 views, divided by that render's unit counts; the 1-view
 # capture gives per-unit figures within 2%, so traffic is taken to grow in proportion and is
 # scaled to the bench's launches by their unit counts. Valid only for the kernel sources they
-# were measured on (SHA-256 prefix of wave.cu, device.cuh, path.cuh, bvh.cu); otherwise null.
-TRAFFIC_SOURCES = ("wave.cu", "device.cuh", "path.cuh", "bvh.cu")
-TRAFFIC_SHA = "3c1678626260466e"
-TRAFFIC_PER_UNIT = {"closest": 81.70, "shade": 9.85, "shadow": 125.09}
+# were measured on (SHA-256 prefix of wave.cu, device.cuh, path.cuh, bvh.cu, env.cu); otherwise
+# null.
+TRAFFIC_SOURCES = ("wave.cu", "device.cuh", "path.cuh", "bvh.cu", "env.cu")
+TRAFFIC_SHA = "618e3614140c8c45"
+TRAFFIC_PER_UNIT = {"closest": 81.75, "shade": 12.09, "shadow": 125.11}
 
 
 def _traffic_valid():
